@@ -1,0 +1,200 @@
+/*
+ * trx — recursive triangular matrix multiply (TRMM) and triangular solve
+ * (TRSM) for NVIDIA GB300 (sm_103a). C ABI.
+ *
+ * The operations are those of Section 2.1 of "Toward Portable GPU Performance:
+ * Julia Recursive Implementation of TRMM and TRSM" (arXiv 2504.13821):
+ *
+ *   TRMM   B := alpha * op(A) * B      side = 'L'   (Eq. 1)
+ *          B := alpha * B * op(A)      side = 'R'   (Eq. 2)
+ *   TRSM   op(A) * X = alpha * B       side = 'L'   (Eq. 3)
+ *          X * op(A) = alpha * B       side = 'R'   (Eq. 4), X overwrites B
+ *
+ * computed by the recursive scheme of Section 3.1: A is split into A11, A21,
+ * A22, the recursion descends on the diagonal blocks down to a leaf tile
+ * solved/multiplied in shared memory (Section 3.3) and the off-diagonal
+ * blocks become in-place GEMM updates (e.g. B2 -= A21 * X1).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Storage is BLAS column-major: element (i,j) of A is A[i + j*lda], of B is
+ *   B[i + j*ldb]. B is m x n; A is k x k with k = m (side 'L') or k = n
+ *   (side 'R'). Both pointers are DEVICE pointers on the handle's device,
+ *   owned by the caller. A is read only; only its uplo triangle is read and,
+ *   with diag = 'U', not its diagonal (taken as 1). B is overwritten.
+ *   A must not overlap B (undefined result, as in BLAS).
+ * - side in {'L','R'}, uplo in {'L','U'}, transa in {'N','T','C'} ('C' means
+ *   'T' for real data), diag in {'N','U'}; case-insensitive.
+ * - The call is asynchronous on `stream` (a cudaStream_t; NULL is the legacy
+ *   default stream) and returns once the work is enqueued. It allocates no
+ *   device memory: the tensor-core FP32 path uses the handle's workspace.
+ * - Return codes: 0 on success; -i if the i-th BLAS argument is illegal
+ *   (side=1, uplo=2, transa=3, diag=4, m=5, n=6, alpha=7, A=8, lda=9, B=10,
+ *   ldb=11), checked before anything else and before the handle is used;
+ *   a positive TRX_ERR_* code otherwise. On any error nothing is enqueued.
+ * - m == 0 or n == 0 returns at once. alpha == 0 sets B to zero and does not
+ *   read A (the BLAS quick return). A zero on a non-unit diagonal is not
+ *   checked; Inf/NaN propagate.
+ * - A handle is not thread-safe: calls sharing one handle must be issued from
+ *   one host thread, and calls on different streams that share one handle
+ *   must not overlap on the device (they share its workspace).
+ */
+#ifndef TRX_H_
+#define TRX_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct trx_handle_s* trx_handle_t;
+
+/* Positive error codes (negative codes are BLAS argument positions). */
+enum {
+    TRX_SUCCESS = 0,
+    TRX_ERR_HANDLE = 1,        /* null or destroyed handle                  */
+    TRX_ERR_CUDA = 2,          /* a CUDA runtime/driver call failed         */
+    TRX_ERR_WORKSPACE = 3,     /* workspace missing or smaller than needed  */
+    TRX_ERR_TIMEOUT = 4,       /* a bounded device-side wait gave up        */
+    TRX_ERR_DEVICE = 5,        /* device is not sm_103 (GB300)              */
+    TRX_ERR_ALLOC = 6,         /* host or device allocation failed          */
+    TRX_ERR_INVALID_VALUE = 7  /* bad option or option value                */
+};
+
+/* Options for trx_set_option(). */
+enum {
+    TRX_OPT_LEAF = 1,      /* leaf cutoff b (Section 3.1 "chosen threshold"):
+                              16, 32, 64 or 128; 0 = automatic (default)   */
+    TRX_OPT_GEMM = 2,      /* FP32 GEMM-update engine: 0 automatic, 1 CUDA
+                              cores (FP32 FMA), 2 tensor cores (tcgen05,
+                              3-term split BF16, FP32 accumulation)         */
+    TRX_OPT_GRAPH = 3,     /* 1 (default): replay the launch chain as a
+                              cached CUDA graph; 0: launch directly         */
+    TRX_OPT_PROFILE = 4,   /* 1: time every launch with CUDA events and
+                              accumulate into trx_profile_t (launches
+                              directly, no graph); 0 (default): off        */
+    TRX_OPT_WAIT_LIMIT = 5 /* nanoseconds a device-side wait may spin
+                              before it gives up and the launch reports
+                              TRX_ERR_TIMEOUT (default 2e9, minimum 1000) */
+};
+
+/* Kernel classes reported by trx_get_profile(). */
+enum {
+    TRX_KERNEL_LEAF_TRSM = 0,
+    TRX_KERNEL_LEAF_TRMM = 1,
+    TRX_KERNEL_GEMM_TC = 2,    /* tcgen05 GEMM update                     */
+    TRX_KERNEL_GEMM_SIMT = 3,  /* CUDA-core GEMM update                   */
+    TRX_KERNEL_CONVERT = 4,    /* FP32 -> split BF16 operand planes       */
+    TRX_KERNEL_OTHER = 5,      /* scale / zero                            */
+    TRX_KERNEL_CLASSES = 6
+};
+
+/* Per-class accumulated device time (CUDA events around each launch on the
+ * call's stream), launch count and algorithmic work: flops = 2*M*N*K for a
+ * GEMM update and the exact multiply-add count for a leaf; bytes = the
+ * minimum bytes a launch must move (operands read once, outputs written
+ * once). Only filled while TRX_OPT_PROFILE is 1. */
+typedef struct {
+    double ms[TRX_KERNEL_CLASSES];
+    double flops[TRX_KERNEL_CLASSES];
+    double bytes[TRX_KERNEL_CLASSES];
+    int64_t launches[TRX_KERNEL_CLASSES];
+} trx_profile_t;
+
+/* Create a handle on CUDA device `device` (that device becomes current for
+ * the calling thread). workspace_bytes > 0 makes the handle allocate and own
+ * a workspace of that size; 0 allocates none (see trx_set_workspace).
+ * Returns TRX_ERR_DEVICE if the device is not compute capability 10.3. */
+int trx_create(trx_handle_t* handle, int device, size_t workspace_bytes);
+
+/* Destroy a handle: synchronises the device, frees what the handle owns
+ * (its workspace, cached graphs, events). NULL is accepted. */
+int trx_destroy(trx_handle_t handle);
+
+/* Give the handle a caller-owned device workspace (replaces, and frees, any
+ * workspace the handle owned). The memory must stay valid until it is
+ * replaced or the handle destroyed. ptr must be 256-byte aligned. */
+int trx_set_workspace(trx_handle_t handle, void* ptr, size_t bytes);
+
+/* Bytes of workspace a call needs. elem_bytes is 4 (FP32) or 8 (FP64);
+ * op is 'S' (TRSM) or 'M' (TRMM), for which side/m/n are the call's; or 'G'
+ * for a tensor-core trx_sgemm_update, with m = M + K and n = N (side 'L').
+ * Depends on the handle's options (the CUDA-core and FP64 paths need none).
+ * Returns 0 and sets *bytes, or an argument code as for the compute calls. */
+int trx_workspace_size(trx_handle_t handle, char op, char side, int64_t m,
+                       int64_t n, int elem_bytes, size_t* bytes);
+
+/* TRSM (Eq. 3-4), FP32 and FP64. B (m x n) is overwritten by X. */
+int trx_strsm(trx_handle_t handle, char side, char uplo, char transa,
+              char diag, int64_t m, int64_t n, float alpha, const float* A,
+              int64_t lda, float* B, int64_t ldb, void* stream);
+int trx_dtrsm(trx_handle_t handle, char side, char uplo, char transa,
+              char diag, int64_t m, int64_t n, double alpha, const double* A,
+              int64_t lda, double* B, int64_t ldb, void* stream);
+
+/* TRMM (Eq. 1-2), FP32 and FP64. B (m x n) is overwritten by the product. */
+int trx_strmm(trx_handle_t handle, char side, char uplo, char transa,
+              char diag, int64_t m, int64_t n, float alpha, const float* A,
+              int64_t lda, float* B, int64_t ldb, void* stream);
+int trx_dtrmm(trx_handle_t handle, char side, char uplo, char transa,
+              char diag, int64_t m, int64_t n, double alpha, const double* A,
+              int64_t lda, double* B, int64_t ldb, void* stream);
+
+/* The recursion's off-diagonal step on its own (Section 3.1, e.g.
+ * B2 := B2 - A21 * X1), FP32, column-major device arrays:
+ *   C := beta * C + gamma * A * Y,  A M x K, Y K x N, C M x N (C must not
+ *   overlap A or Y).
+ * engine 1: CUDA cores (FP32 FMA); engine 2: tensor cores (3-term split
+ * BF16 products, FP32 accumulation; K must be a multiple of 64 and the
+ * handle's workspace at least trx_workspace_size('G', 'L', M + K, N)).
+ * Returns 0, -i for an illegal i-th argument (handle = 1, M = 2, N = 3,
+ * K = 4, beta = 5, gamma = 6, A = 7, lda = 8, Y = 9, ldy = 10, C = 11,
+ * ldc = 12, engine = 13), or a TRX_ERR_* code. Asynchronous on stream. */
+int trx_sgemm_update(trx_handle_t handle, int64_t M, int64_t N, int64_t K,
+                     float beta, float gamma, const float* A, int64_t lda,
+                     const float* Y, int64_t ldy, float* C, int64_t ldc,
+                     int engine, void* stream);
+
+/* Set / read an option (TRX_OPT_*). Unknown options or values return
+ * TRX_ERR_INVALID_VALUE. */
+int trx_set_option(trx_handle_t handle, int option, int64_t value);
+int trx_get_option(trx_handle_t handle, int option, int64_t* value);
+
+/* Read (and with reset != 0 clear) the accumulated profile. Blocks until
+ * the profiled launches have finished. */
+int trx_get_profile(trx_handle_t handle, trx_profile_t* out, int reset);
+
+/* Read and clear the handle's device error word: returns TRX_SUCCESS or
+ * TRX_ERR_TIMEOUT if a bounded wait in an earlier launch gave up (that
+ * launch's output is then invalid). Synchronises the handle's device. */
+int trx_check_device_error(trx_handle_t handle);
+
+/* Static description of an error code. Never NULL. */
+const char* trx_error_string(int code);
+
+/* Detail of the last positive error returned on the calling thread (the
+ * failing CUDA call and its message, or the workspace size needed). Never
+ * NULL; empty if there was none. */
+const char* trx_last_error_detail(void);
+
+/* Diagnostic, host only (no device work, no handle): write into buf the
+ * launch sequence a call would enqueue for the given problem, one step per
+ * line ("conv_m", "conv_y", "leaf ...", "gemm ..." with their row ranges in
+ * the canonical lower-triangular order), for alpha = 2. elem_bytes 4 or 8,
+ * leaf as TRX_OPT_LEAF, gemm_mode as TRX_OPT_GEMM, op 'S' (TRSM) or 'M'
+ * (TRMM). Returns an argument code, TRX_ERR_INVALID_VALUE if buf is too
+ * small, or 0. */
+int trx_debug_plan(char op, char side, char uplo, char transa, char diag,
+                   int64_t m, int64_t n, int elem_bytes, int leaf,
+                   int gemm_mode, char* buf, size_t buflen);
+
+/* Library version as major*10000 + minor*100 + patch. */
+int trx_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TRX_H_ */

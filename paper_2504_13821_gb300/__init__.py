@@ -1,0 +1,16 @@
+"""trx — recursive TRSM / TRMM for NVIDIA GB300 (sm_103a).
+
+Implements the recursive scheme of arXiv 2504.13821 (Section 3.1: split the
+triangle, recurse on the diagonal blocks, GEMM-update the off-diagonal block,
+small base kernels at the leaves) as hand-written CUDA behind the C ABI in
+include/trx.h. This package is the thin Python binding (argument marshalling
+over torch tensors); the CUDA library is built in-tree by ``build.py``.
+"""
+from ._binding import (  # noqa: F401
+    GEMM_AUTO, GEMM_SIMT, GEMM_TC, OPT_GEMM, OPT_GRAPH, OPT_LEAF, OPT_PROFILE,
+    OPT_WAIT_LIMIT, Handle, TrxError, debug_plan, default_handle, gemm_update, header_functions,
+    load_library, to_colmajor, trmm, trsm,
+)
+
+__all__ = ["trsm", "trmm", "Handle", "TrxError", "default_handle", "debug_plan",
+           "load_library", "to_colmajor"]

@@ -1,0 +1,289 @@
+"""Thin ctypes binding over the trx C ABI (include/trx.h).
+
+Argument marshalling only: torch tensors supply device pointers, leading
+dimensions and the current CUDA stream; every step of TRSM/TRMM runs in the
+library's own CUDA kernels. There is no fallback of any kind: if libtrx.so is
+missing or the device is not a GB300 (sm_103), calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+import threading
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libtrx.so")
+HEADER = os.path.join(os.path.dirname(_PKG), "include", "trx.h")
+
+# Option and kernel-class codes (mirrors include/trx.h).
+OPT_LEAF, OPT_GEMM, OPT_GRAPH, OPT_PROFILE, OPT_WAIT_LIMIT = 1, 2, 3, 4, 5
+GEMM_AUTO, GEMM_SIMT, GEMM_TC = 0, 1, 2
+KERNEL_CLASSES = ("leaf_trsm", "leaf_trmm", "gemm_tc", "gemm_simt", "convert", "other")
+ERR_TIMEOUT = 4
+
+_lock = threading.Lock()
+_lib = None
+
+
+class TrxError(RuntimeError):
+    """A trx call returned a non-zero status."""
+
+    def __init__(self, code: int, where: str, detail: str = ""):
+        self.code = code
+        msg = f"{where}: trx error {code}"
+        if _lib is not None:
+            msg += f" ({_lib.trx_error_string(code).decode()})"
+        if detail:
+            msg += f": {detail}"
+        super().__init__(msg)
+
+
+class _Profile(ctypes.Structure):
+    _fields_ = [("ms", ctypes.c_double * 6), ("flops", ctypes.c_double * 6),
+                ("bytes", ctypes.c_double * 6), ("launches", ctypes.c_int64 * 6)]
+
+
+def load_library() -> ctypes.CDLL:
+    """Load libtrx.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(
+                f"trx CUDA library not built ({LIB_PATH} missing): run "
+                "`python -c 'import __graft_entry__ as g; g.build()'`")
+        lib = ctypes.CDLL(LIB_PATH)
+        vp, i64, c = ctypes.c_void_p, ctypes.c_int64, ctypes.c_char
+        lib.trx_create.argtypes = [ctypes.POINTER(vp), ctypes.c_int, ctypes.c_size_t]
+        lib.trx_destroy.argtypes = [vp]
+        lib.trx_set_workspace.argtypes = [vp, vp, ctypes.c_size_t]
+        lib.trx_workspace_size.argtypes = [vp, c, c, i64, i64, ctypes.c_int,
+                                           ctypes.POINTER(ctypes.c_size_t)]
+        for name, real in (("trx_strsm", ctypes.c_float), ("trx_strmm", ctypes.c_float),
+                           ("trx_dtrsm", ctypes.c_double), ("trx_dtrmm", ctypes.c_double)):
+            getattr(lib, name).argtypes = [vp, c, c, c, c, i64, i64, real, vp, i64, vp, i64, vp]
+        lib.trx_set_option.argtypes = [vp, ctypes.c_int, i64]
+        lib.trx_get_option.argtypes = [vp, ctypes.c_int, ctypes.POINTER(i64)]
+        lib.trx_get_profile.argtypes = [vp, ctypes.POINTER(_Profile), ctypes.c_int]
+        lib.trx_check_device_error.argtypes = [vp]
+        lib.trx_error_string.argtypes = [ctypes.c_int]
+        lib.trx_error_string.restype = ctypes.c_char_p
+        lib.trx_last_error_detail.argtypes = []
+        lib.trx_last_error_detail.restype = ctypes.c_char_p
+        lib.trx_debug_plan.argtypes = [c, c, c, c, c, i64, i64, ctypes.c_int, ctypes.c_int,
+                                       ctypes.c_int, ctypes.c_char_p, ctypes.c_size_t]
+        lib.trx_sgemm_update.argtypes = [vp, i64, i64, i64, ctypes.c_float, ctypes.c_float,
+                                         vp, i64, vp, i64, vp, i64, ctypes.c_int, vp]
+        lib.trx_version.argtypes = []
+        _lib = lib
+        return lib
+
+
+def header_functions() -> list[str]:
+    """Names of the functions include/trx.h declares."""
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(trx_[a-z0-9_]+)\s*\(", text)))
+
+
+def _check(code: int, where: str):
+    if code != 0:
+        detail = _lib.trx_last_error_detail().decode() if code > 0 else ""
+        raise TrxError(code, where, detail)
+
+
+def _char(x: str) -> bytes:
+    if not isinstance(x, str) or len(x) != 1:
+        raise ValueError(f"expected a one-character flag, got {x!r}")
+    return x.encode()
+
+
+class Handle:
+    """A trx handle on one CUDA device, with a torch-allocated workspace."""
+
+    def __init__(self, device=None):
+        import torch
+        lib = load_library()
+        self.device = torch.device("cuda", torch.cuda.current_device()
+                                   if device is None else torch.device(device).index or 0)
+        self._h = ctypes.c_void_p()
+        _check(lib.trx_create(ctypes.byref(self._h), self.device.index, 0), "trx_create")
+        self._ws = None
+        self._ws_bytes = 0
+
+    @property
+    def ptr(self):
+        return self._h
+
+    def close(self):
+        if self._h:
+            load_library().trx_destroy(self._h)
+            self._h = ctypes.c_void_p()
+            self._ws = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_option(self, option: int, value: int):
+        _check(load_library().trx_set_option(self._h, option, int(value)), "trx_set_option")
+
+    def get_option(self, option: int) -> int:
+        v = ctypes.c_int64()
+        _check(load_library().trx_get_option(self._h, option, ctypes.byref(v)), "trx_get_option")
+        return v.value
+
+    def workspace_size(self, op: str, side: str, m: int, n: int, elem_bytes: int) -> int:
+        out = ctypes.c_size_t()
+        _check(load_library().trx_workspace_size(self._h, _char(op), _char(side), m, n,
+                                                 elem_bytes, ctypes.byref(out)),
+               "trx_workspace_size")
+        return out.value
+
+    def ensure_workspace(self, nbytes: int):
+        """Grow the torch-owned workspace to at least nbytes."""
+        import torch
+        if nbytes <= self._ws_bytes:
+            return
+        ws = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+        _check(load_library().trx_set_workspace(self._h, ws.data_ptr(), nbytes),
+               "trx_set_workspace")
+        self._ws, self._ws_bytes = ws, nbytes
+
+    def profile(self, reset: bool = False) -> dict:
+        p = _Profile()
+        _check(load_library().trx_get_profile(self._h, ctypes.byref(p), int(reset)),
+               "trx_get_profile")
+        return {name: {"ms": p.ms[i], "flops": p.flops[i], "bytes": p.bytes[i],
+                       "launches": p.launches[i]} for i, name in enumerate(KERNEL_CLASSES)}
+
+    def check_device_error(self) -> int:
+        """0, or the error code a bounded device-side wait left behind."""
+        code = load_library().trx_check_device_error(self._h)
+        if code not in (0, ERR_TIMEOUT):
+            _check(code, "trx_check_device_error")
+        return code
+
+
+_handles: dict = {}
+
+
+def default_handle(device=None) -> Handle:
+    import torch
+    idx = torch.cuda.current_device() if device is None else torch.device(device).index or 0
+    h = _handles.get(idx)
+    if h is None:
+        h = _handles[idx] = Handle(idx)
+    return h
+
+
+def _colmajor(t, name: str):
+    """(pointer, leading dimension) of a column-major 2-D tensor view."""
+    if t.dim() != 2:
+        raise ValueError(f"{name} must be 2-D, got shape {tuple(t.shape)}")
+    rows, cols = t.shape
+    if rows > 1 and t.stride(0) != 1:
+        raise ValueError(f"{name} must be column-major (stride(0) == 1); "
+                         f"use a transposed contiguous tensor, e.g. x.t().contiguous().t()")
+    ld = t.stride(1) if cols > 1 else max(1, rows)
+    if ld < max(1, rows):
+        raise ValueError(f"{name}: leading dimension {ld} < rows {rows}")
+    return t.data_ptr(), ld
+
+
+def _call(op: str, side, uplo, trans, diag, alpha, A, B, handle=None, stream=None):
+    import torch
+    lib = load_library()
+    if not (isinstance(A, torch.Tensor) and isinstance(B, torch.Tensor)):
+        raise TypeError("A and B must be torch tensors")
+    if A.dtype != B.dtype or A.dtype not in (torch.float32, torch.float64):
+        raise TypeError(f"A and B must both be float32 or both float64 "
+                        f"(got {A.dtype}, {B.dtype})")
+    if not (A.is_cuda and B.is_cuda) or A.device != B.device:
+        raise ValueError("A and B must be CUDA tensors on one device")
+    m, n = B.shape
+    k = m if side.upper() == "L" else n
+    if tuple(A.shape) != (k, k):
+        raise ValueError(f"A must be {k}x{k} for side {side!r} and B {m}x{n}")
+    a_ptr, lda = _colmajor(A, "A")
+    b_ptr, ldb = _colmajor(B, "B")
+    h = handle if handle is not None else default_handle(B.device)
+    elem = B.element_size()
+    h.ensure_workspace(h.workspace_size("S" if op == "trsm" else "M", side, m, n, elem))
+    if stream is None:
+        stream = torch.cuda.current_stream(B.device)
+    s_ptr = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+    fn = getattr(lib, ("trx_s" if elem == 4 else "trx_d") + op)
+    rc = fn(h.ptr, _char(side), _char(uplo), _char(trans), _char(diag), m, n, float(alpha),
+            a_ptr, lda, b_ptr, ldb, s_ptr)
+    _check(rc, fn.__name__)
+    return B
+
+
+def trsm(side: str, uplo: str, trans: str, diag: str, alpha: float, A, B, *,
+         handle: Handle | None = None, stream=None):
+    """Solve op(A) X = alpha B (side 'L') or X op(A) = alpha B (side 'R') in
+    place: B (column-major CUDA tensor) is overwritten by X. Paper Eq. 3-4."""
+    return _call("trsm", side, uplo, trans, diag, alpha, A, B, handle, stream)
+
+
+def trmm(side: str, uplo: str, trans: str, diag: str, alpha: float, A, B, *,
+         handle: Handle | None = None, stream=None):
+    """B := alpha op(A) B (side 'L') or alpha B op(A) (side 'R') in place.
+    Paper Eq. 1-2."""
+    return _call("trmm", side, uplo, trans, diag, alpha, A, B, handle, stream)
+
+
+def debug_plan(op: str, side, uplo, trans, diag, m, n, elem_bytes=4, leaf=0, gemm=0) -> list:
+    """The launch sequence the library would enqueue, parsed (host only, no
+    GPU needed): a list of dicts with the step kind and its row ranges."""
+    lib = load_library()
+    buf = ctypes.create_string_buffer(1 << 22)
+    rc = lib.trx_debug_plan(_char(op), _char(side), _char(uplo), _char(trans), _char(diag),
+                            m, n, elem_bytes, leaf, gemm, buf, len(buf))
+    _check(rc, "trx_debug_plan")
+    steps = []
+    for line in buf.value.decode().splitlines():
+        kind, *kv = line.split()
+        d = {"kind": kind}
+        for item in kv:
+            key, val = item.split("=")
+            d[key] = float(val) if "." in val or "e" in val else int(val)
+        steps.append(d)
+    return steps
+
+
+def gemm_update(beta: float, gamma: float, A, Y, C, *, engine: int = GEMM_TC,
+                handle: Handle | None = None, stream=None):
+    """C := beta C + gamma A Y (FP32, column-major CUDA tensors): the
+    recursion's off-diagonal update alone (Section 3.1)."""
+    import torch
+    lib = load_library()
+    for t in (A, Y, C):
+        if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float32):
+            raise TypeError("A, Y, C must be float32 CUDA tensors")
+    M, K = A.shape
+    K2, N = Y.shape
+    if K2 != K or tuple(C.shape) != (M, N):
+        raise ValueError("shape mismatch")
+    a, lda = _colmajor(A, "A")
+    y, ldy = _colmajor(Y, "Y")
+    c, ldc = _colmajor(C, "C")
+    h = handle if handle is not None else default_handle(C.device)
+    if engine == GEMM_TC:
+        h.ensure_workspace(h.workspace_size("G", "L", M + K, N, 4))
+    if stream is None:
+        stream = torch.cuda.current_stream(C.device)
+    s_ptr = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+    _check(lib.trx_sgemm_update(h.ptr, M, N, K, float(beta), float(gamma), a, lda, y, ldy,
+                                c, ldc, engine, s_ptr), "trx_sgemm_update")
+    return C
+
+
+def to_colmajor(x):
+    """Column-major copy of a 2-D tensor (same shape)."""
+    return x.t().contiguous().t()

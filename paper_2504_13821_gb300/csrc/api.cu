@@ -1,0 +1,825 @@
+// C-ABI of the trx library: argument checking, canonical form, recursion
+// planner and launch-chain execution (direct or as a cached CUDA graph).
+//
+// The recursion is the one of Section 3.1 (split the triangle at about half,
+// recurse on the diagonal blocks, GEMM-update the off-diagonal block, base
+// kernels below a cutoff), written once for the canonical lower form of
+// common.cuh. Each of the 16 variants of Eq. 1-4 reaches it by a stride
+// mapping (side 'R' solves with op(A)^T on B^T; an effectively-upper triangle
+// is index-reversed), so no variant needs its own kernels.
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+#include "trx.h"
+
+namespace trx {
+// Leaf kernels set their shared-memory limits once per device (leaf.cu).
+cudaError_t leaf_configure_all();
+}  // namespace trx
+
+using namespace trx;
+
+namespace {
+
+constexpr int kMagic = 0x54525831;  // "TRX1"
+constexpr int kDefaultLeaf = 64;
+constexpr long long kDefaultWaitNs = 2000000000LL;   // 2 s
+constexpr int64_t kTcMinOrder = 256;                 // auto: tensor cores from this order
+constexpr size_t kGraphCacheSize = 16;
+
+thread_local char g_detail[256] = "";
+
+int fail_cuda(cudaError_t e, const char* what) {
+    snprintf(g_detail, sizeof(g_detail), "%s: %s", what, cudaGetErrorString(e));
+    return TRX_ERR_CUDA;
+}
+
+int upc(char c) { return (c >= 'a' && c <= 'z') ? c - 'a' + 'A' : c; }
+
+int check_args(char side, char uplo, char transa, char diag, int64_t m, int64_t n,
+               const void* A, int64_t lda, const void* B, int64_t ldb) {
+    const int s = upc(side), u = upc(uplo), t = upc(transa), d = upc(diag);
+    if (s != 'L' && s != 'R') return -1;
+    if (u != 'L' && u != 'U') return -2;
+    if (t != 'N' && t != 'T' && t != 'C') return -3;
+    if (d != 'N' && d != 'U') return -4;
+    if (m < 0) return -5;
+    if (n < 0) return -6;
+    const int64_t k = (s == 'L') ? m : n;
+    if (m > 0 && n > 0 && A == nullptr) return -8;
+    if (lda < std::max<int64_t>(1, k)) return -9;
+    if (m > 0 && n > 0 && B == nullptr) return -10;
+    if (ldb < std::max<int64_t>(1, m)) return -11;
+    return 0;
+}
+
+int64_t round_up(int64_t x, int64_t q) { return (x + q - 1) / q * q; }
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// Section 3.1 splits at n = N/2. For orders that are not powers of two the
+// split is rounded up to a multiple of max(b, 64) (so every tensor-core GEMM
+// update has K a multiple of its K tile, and every node starts on a multiple
+// of b), or of b where that would leave the second half empty.
+int64_t split_point(int64_t s, int b) {
+    const int64_t half = (s + 1) / 2;
+    const int64_t q = std::max<int64_t>(b, kTcKQuantum);
+    int64_t s1 = round_up(half, q);
+    if (s1 >= s) s1 = round_up(half, b);
+    return s1;
+}
+
+enum StepKind { kLeaf, kGemm, kConvM, kConvY };
+
+struct Step {
+    StepKind kind;
+    bool trsm = true;        // leaf: TRSM or TRMM
+    int64_t r0 = 0;          // leaf: first row
+    int b = 0;               // leaf: size (and stride of batched leaves)
+    int64_t nleaves = 1;
+    double alpha = 1.0;      // leaf scale
+    bool planes = false;     // TRSM leaf writes Y planes
+    bool tc = false;         // GEMM on tensor cores
+    std::vector<TcGemm> gemms;
+    double beta = 1.0, gamma = 1.0;
+};
+
+struct Plan {
+    std::vector<Step> steps;
+    bool tc = false;
+};
+
+void plan_trsm(Plan& pl, int64_t r0, int64_t s, bool first, int b, double alpha) {
+    if (s <= b) {
+        Step st{kLeaf};
+        st.trsm = true;
+        st.r0 = r0;
+        st.b = (int)s;
+        st.alpha = first ? alpha : 1.0;
+        st.planes = pl.tc;
+        pl.steps.push_back(st);
+        return;
+    }
+    const int64_t s1 = split_point(s, b);
+    plan_trsm(pl, r0, s1, first, b, alpha);
+    Step g{kGemm};
+    g.tc = pl.tc && (s1 % kTcKQuantum == 0);
+    g.gemms.push_back(TcGemm{r0 + s1, s - s1, r0, s1});
+    g.beta = first ? alpha : 1.0;
+    g.gamma = -1.0;
+    pl.steps.push_back(g);
+    plan_trsm(pl, r0 + s1, s - s1, false, b, alpha);
+}
+
+// Paper order for TRMM (lower): C2 := M22 C2, C2 += M21 C1, C1 := M11 C1, so
+// every GEMM reads C1 before it is overwritten.
+void plan_trmm_seq(Plan& pl, int64_t r0, int64_t s, int b, double alpha) {
+    if (s <= b) {
+        Step st{kLeaf};
+        st.trsm = false;
+        st.r0 = r0;
+        st.b = (int)s;
+        st.alpha = alpha;
+        pl.steps.push_back(st);
+        return;
+    }
+    const int64_t s1 = split_point(s, b);
+    plan_trmm_seq(pl, r0 + s1, s - s1, b, alpha);
+    Step g{kGemm};
+    g.tc = pl.tc && (s1 % kTcKQuantum == 0);
+    g.gemms.push_back(TcGemm{r0 + s1, s - s1, r0, s1});
+    g.beta = 1.0;
+    g.gamma = alpha;
+    pl.steps.push_back(g);
+    plan_trmm_seq(pl, r0, s1, b, alpha);
+}
+
+// TRMM with the original right-hand side kept in the Y planes: no GEMM update
+// reads a row another step writes, so the same recursion tree runs as one
+// launch for all leaves followed by one grouped launch per recursion level
+// (the updates of one level write disjoint rows).
+void plan_trmm_levels(Plan& pl, int64_t k, int b, double alpha) {
+    Step lf{kLeaf};
+    lf.trsm = false;
+    lf.r0 = 0;
+    lf.b = b;
+    lf.nleaves = (k + b - 1) / b;
+    lf.alpha = alpha;
+    pl.steps.push_back(lf);
+    std::vector<std::pair<int64_t, int64_t>> level{{0, k}}, next;
+    while (!level.empty()) {
+        Step g{kGemm};
+        g.tc = true;
+        g.beta = 1.0;
+        g.gamma = alpha;
+        next.clear();
+        for (auto& nd : level) {
+            const int64_t r0 = nd.first, s = nd.second;
+            if (s <= b) continue;
+            const int64_t s1 = split_point(s, b);
+            g.gemms.push_back(TcGemm{r0 + s1, s - s1, r0, s1});
+            next.push_back({r0, s1});
+            next.push_back({r0 + s1, s - s1});
+        }
+        if (!g.gemms.empty()) pl.steps.push_back(g);
+        level.swap(next);
+    }
+}
+
+// The whole launch sequence of one call: operand planes (tensor-core path),
+// then the recursion of Section 3.1.
+void make_plan(Plan& plan, bool trsm, int64_t k, int b, double alpha) {
+    if (plan.tc) plan.steps.push_back(Step{kConvM});
+    if (trsm) {
+        plan_trsm(plan, 0, k, true, b, alpha);
+    } else {
+        if (plan.tc) plan.steps.push_back(Step{kConvY});
+        if (plan.tc && b % kTcKQuantum == 0) plan_trmm_levels(plan, k, b, alpha);
+        else plan_trmm_seq(plan, 0, k, b, alpha);
+    }
+}
+
+template <typename T>
+Canon<T> canonicalize(char side, char uplo, char transa, char diag, int64_t m, int64_t n,
+                      const T* A, int64_t lda, T* B, int64_t ldb) {
+    const bool left = upc(side) == 'L', lower = upc(uplo) == 'L';
+    const bool trans = upc(transa) != 'N', unit = upc(diag) == 'U';
+    Canon<T> c;
+    c.k = left ? m : n;
+    c.nrhs = left ? n : m;
+    c.unit = unit;
+    int64_t rs, cs;
+    bool eff_lower;
+    if (left) {                  // M = op(A), C = B
+        rs = trans ? lda : 1;
+        cs = trans ? 1 : lda;
+        eff_lower = lower != trans;
+        c.c_rs = 1;
+        c.c_cs = ldb;
+    } else {                     // M = op(A)^T, C = B^T
+        rs = trans ? 1 : lda;
+        cs = trans ? lda : 1;
+        eff_lower = lower == trans;
+        c.c_rs = ldb;
+        c.c_cs = 1;
+    }
+    c.A = A;
+    c.a_rs = rs;
+    c.a_cs = cs;
+    c.C = B;
+    if (!eff_lower) {            // reverse the index order: upper -> lower
+        c.A = A + (c.k - 1) * (rs + cs);
+        c.a_rs = -rs;
+        c.a_cs = -cs;
+        c.C = B + (c.k - 1) * c.c_rs;
+        c.c_rs = -c.c_rs;
+    }
+    return c;
+}
+
+struct WsLayout {
+    int64_t ldm = 0, ldy = 0;
+    size_t m_bytes = 0, y_bytes = 0, total = 0;
+};
+
+WsLayout ws_layout(int64_t k, int64_t nrhs) {
+    WsLayout w;
+    w.ldm = round_up(std::max<int64_t>(k, 1), 64);
+    w.ldy = w.ldm;
+    w.m_bytes = align256((size_t)k * w.ldm * 2);
+    w.y_bytes = align256((size_t)nrhs * w.ldy * 2);
+    w.total = 2 * w.m_bytes + 2 * w.y_bytes;
+    return w;
+}
+
+}  // namespace
+
+struct trx_handle_s {
+    int magic = kMagic;
+    int device = 0, num_sms = 0;
+    void* ws = nullptr;
+    size_t ws_bytes = 0;
+    bool ws_owned = false;
+    int64_t opt_leaf = 0, opt_gemm = 0, opt_graph = 1, opt_profile = 0;
+    long long wait_ns = kDefaultWaitNs;
+    int* d_err = nullptr;
+    cudaStream_t cap_stream = nullptr;
+    trx_profile_t prof{};
+    struct Pending {
+        int cls;
+        double flops, bytes;
+        cudaEvent_t e0, e1;
+    };
+    std::vector<Pending> pending;
+    std::vector<cudaEvent_t> free_events;
+    struct GraphEntry {
+        std::string key;
+        cudaGraphExec_t exec;
+        uint64_t used;
+    };
+    std::vector<GraphEntry> graphs;
+    uint64_t tick = 0;
+    std::vector<unsigned char> maps;
+};
+
+namespace {
+
+bool valid(trx_handle_t h) { return h != nullptr && h->magic == kMagic; }
+
+cudaEvent_t get_event(trx_handle_t h) {
+    if (!h->free_events.empty()) {
+        cudaEvent_t e = h->free_events.back();
+        h->free_events.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+int leaf_for(trx_handle_t h, int64_t k) {
+    int b = h->opt_leaf > 0 ? (int)h->opt_leaf : kDefaultLeaf;
+    return (int)std::min<int64_t>(b, std::max<int64_t>(k, 1));
+}
+
+bool use_tc_mode(int elem, int64_t gemm_mode, int64_t k, int b) {
+    if (elem != 4 || gemm_mode == 1) return false;
+    if (gemm_mode == 2) return k > b;
+    return k >= kTcMinOrder;
+}
+
+template <typename T>
+bool use_tc(trx_handle_t h, int64_t k) {
+    return use_tc_mode((int)sizeof(T), h->opt_gemm, k, leaf_for(h, k));
+}
+
+template <typename T>
+struct Exec {
+    trx_handle_t h;
+    Canon<T> c;
+    Planes pl;
+    const void* maps = nullptr;
+    cudaStream_t s;
+    bool profile;
+
+    int run(const Plan& plan) {
+        for (const Step& st : plan.steps) {
+            int cls = TRX_KERNEL_OTHER;
+            double flops = 0, bytes = 0;
+            const double w = sizeof(T);
+            cudaEvent_t e0 = nullptr, e1 = nullptr;
+            if (profile) {
+                e0 = get_event(h);
+                e1 = get_event(h);
+                cudaEventRecord(e0, s);
+            }
+            cudaError_t e = cudaSuccess;
+            switch (st.kind) {
+                case kLeaf: {
+                    e = launch_leaf<T>(st.trsm, c, st.r0, st.b, st.nleaves, (T)st.alpha,
+                                       st.planes ? &pl : nullptr, h->num_sms, s);
+                    cls = st.trsm ? TRX_KERNEL_LEAF_TRSM : TRX_KERNEL_LEAF_TRMM;
+                    const int64_t rows = std::min<int64_t>(st.b * st.nleaves, c.k - st.r0);
+                    const double bb = st.b;
+                    flops = (double)rows * bb * c.nrhs;                   // ~b^2 n per leaf
+                    bytes = w * (2.0 * rows * c.nrhs + rows * (bb + 1) / 2);
+                    break;
+                }
+                case kGemm: {
+                    if (st.tc) {
+                        e = launch_gemm_tc(*reinterpret_cast<const Canon<float>*>(&c), maps,
+                                           st.gemms.data(), (int)st.gemms.size(), (float)st.beta,
+                                           (float)st.gamma, h->d_err, h->wait_ns, h->num_sms, s);
+                        cls = TRX_KERNEL_GEMM_TC;
+                    } else {
+                        for (const TcGemm& g : st.gemms) {
+                            e = launch_gemm_simt<T>(c, c.C, c.c_rs, c.c_cs, g.rc, g.mlen, g.rk,
+                                                    g.klen, (T)st.beta, (T)st.gamma, s);
+                            if (e != cudaSuccess) break;
+                        }
+                        cls = TRX_KERNEL_GEMM_SIMT;
+                    }
+                    for (const TcGemm& g : st.gemms) {
+                        flops += 2.0 * g.mlen * g.klen * c.nrhs;
+                        bytes += w * ((double)g.mlen * g.klen + 2.0 * g.mlen * c.nrhs +
+                                      (double)g.klen * c.nrhs);
+                    }
+                    break;
+                }
+                case kConvM:
+                    e = launch_convert_m(*reinterpret_cast<const Canon<float>*>(&c), pl, s);
+                    cls = TRX_KERNEL_CONVERT;
+                    bytes = 8.0 * c.k * (c.k - 1) / 2;
+                    break;
+                case kConvY:
+                    e = launch_convert_y(*reinterpret_cast<const Canon<float>*>(&c), pl, s);
+                    cls = TRX_KERNEL_CONVERT;
+                    bytes = 8.0 * c.k * c.nrhs;
+                    break;
+            }
+            if (e != cudaSuccess) return fail_cuda(e, "kernel launch");
+            if (profile) {
+                cudaEventRecord(e1, s);
+                h->pending.push_back({cls, flops, bytes, e0, e1});
+            }
+        }
+        return TRX_SUCCESS;
+    }
+};
+
+struct GraphKey {
+    int op, elem, tc, b;
+    int64_t k, nrhs, a_rs, a_cs, c_rs, c_cs, unit;
+    const void* A;
+    const void* C;
+    const void* ws;
+    double alpha;
+    long long wait_ns;
+};
+
+template <typename T>
+int execute(trx_handle_t h, bool trsm, char side, char uplo, char transa, char diag, int64_t m,
+            int64_t n, T alpha, const T* A, int64_t lda, T* B, int64_t ldb, void* stream) {
+    const int info = check_args(side, uplo, transa, diag, m, n, A, lda, B, ldb);
+    if (info) return info;
+    if (!valid(h)) return TRX_ERR_HANDLE;
+    if (m == 0 || n == 0) return TRX_SUCCESS;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaSetDevice(h->device);
+    if (e != cudaSuccess) return fail_cuda(e, "cudaSetDevice");
+    if (alpha == T(0)) {
+        e = launch_zero<T>(B, m, n, ldb, s);
+        return e == cudaSuccess ? TRX_SUCCESS : fail_cuda(e, "zero");
+    }
+    Exec<T> ex;
+    ex.h = h;
+    ex.c = canonicalize<T>(side, uplo, transa, diag, m, n, A, lda, B, ldb);
+    ex.s = s;
+    ex.profile = h->opt_profile != 0;
+    const int64_t k = ex.c.k;
+    const int b = leaf_for(h, k);
+
+    Plan plan;
+    plan.tc = use_tc<T>(h, k);
+    if (plan.tc) {
+        const WsLayout w = ws_layout(k, ex.c.nrhs);
+        if (h->ws == nullptr || h->ws_bytes < w.total) {
+            snprintf(g_detail, sizeof(g_detail), "workspace of %zu bytes needed, %zu set",
+                     w.total, h->ws_bytes);
+            return TRX_ERR_WORKSPACE;
+        }
+        char* base = static_cast<char*>(h->ws);
+        ex.pl.ldm = w.ldm;
+        ex.pl.ldy = w.ldy;
+        ex.pl.m_hi = reinterpret_cast<__nv_bfloat16*>(base);
+        ex.pl.m_lo = reinterpret_cast<__nv_bfloat16*>(base + w.m_bytes);
+        ex.pl.y_hi = reinterpret_cast<__nv_bfloat16*>(base + 2 * w.m_bytes);
+        ex.pl.y_lo = reinterpret_cast<__nv_bfloat16*>(base + 2 * w.m_bytes + w.y_bytes);
+        h->maps.resize(tc_maps_size());
+        e = tc_make_maps(ex.pl, k, ex.c.nrhs, h->maps.data());
+        if (e != cudaSuccess) return fail_cuda(e, "tensor map encode");
+        ex.maps = h->maps.data();
+    }
+    make_plan(plan, trsm, k, b, (double)alpha);
+
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    e = cudaStreamIsCapturing(s, &cap);
+    if (e != cudaSuccess) return fail_cuda(e, "cudaStreamIsCapturing");
+    if (ex.profile || !h->opt_graph || cap != cudaStreamCaptureStatusNone) return ex.run(plan);
+
+    GraphKey key;
+    std::memset(&key, 0, sizeof(key));
+    key.op = trsm;
+    key.elem = sizeof(T);
+    key.tc = plan.tc;
+    key.b = b;
+    key.k = k;
+    key.nrhs = ex.c.nrhs;
+    key.a_rs = ex.c.a_rs;
+    key.a_cs = ex.c.a_cs;
+    key.c_rs = ex.c.c_rs;
+    key.c_cs = ex.c.c_cs;
+    key.unit = ex.c.unit;
+    key.A = ex.c.A;
+    key.C = ex.c.C;
+    key.ws = plan.tc ? h->ws : nullptr;
+    key.alpha = (double)alpha;
+    key.wait_ns = h->wait_ns;
+    const std::string ks(reinterpret_cast<const char*>(&key), sizeof(key));
+    ++h->tick;
+    for (auto& g : h->graphs) {
+        if (g.key == ks) {
+            g.used = h->tick;
+            e = cudaGraphLaunch(g.exec, s);
+            return e == cudaSuccess ? TRX_SUCCESS : fail_cuda(e, "cudaGraphLaunch");
+        }
+    }
+    ex.s = h->cap_stream;
+    e = cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return fail_cuda(e, "cudaStreamBeginCapture");
+    const int rc = ex.run(plan);
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamEndCapture(h->cap_stream, &graph);
+    if (rc != TRX_SUCCESS) {
+        if (graph) cudaGraphDestroy(graph);
+        return rc;
+    }
+    if (e != cudaSuccess) return fail_cuda(e, "cudaStreamEndCapture");
+    cudaGraphExec_t exec = nullptr;
+    e = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return fail_cuda(e, "cudaGraphInstantiate");
+    if (h->graphs.size() >= kGraphCacheSize) {
+        auto old = std::min_element(h->graphs.begin(), h->graphs.end(),
+                                    [](const auto& a, const auto& b) { return a.used < b.used; });
+        cudaGraphExecDestroy(old->exec);
+        h->graphs.erase(old);
+    }
+    h->graphs.push_back({ks, exec, h->tick});
+    e = cudaGraphLaunch(exec, s);
+    return e == cudaSuccess ? TRX_SUCCESS : fail_cuda(e, "cudaGraphLaunch");
+}
+
+void free_owned_ws(trx_handle_t h) {
+    if (h->ws_owned && h->ws) cudaFree(h->ws);
+    h->ws = nullptr;
+    h->ws_bytes = 0;
+    h->ws_owned = false;
+}
+
+void drop_graphs(trx_handle_t h) {
+    for (auto& g : h->graphs) cudaGraphExecDestroy(g.exec);
+    h->graphs.clear();
+}
+
+}  // namespace
+
+extern "C" {
+
+int trx_create(trx_handle_t* handle, int device, size_t workspace_bytes) {
+    if (!handle) return TRX_ERR_HANDLE;
+    *handle = nullptr;
+    int count = 0;
+    cudaError_t e = cudaGetDeviceCount(&count);
+    if (e != cudaSuccess) return fail_cuda(e, "cudaGetDeviceCount");
+    if (device < 0 || device >= count) return TRX_ERR_DEVICE;
+    cudaDeviceProp prop;
+    e = cudaGetDeviceProperties(&prop, device);
+    if (e != cudaSuccess) return fail_cuda(e, "cudaGetDeviceProperties");
+    if (prop.major != 10 || prop.minor != 3) {
+        snprintf(g_detail, sizeof(g_detail), "device %d is sm_%d%d, the kernels are sm_103a",
+                 device, prop.major, prop.minor);
+        return TRX_ERR_DEVICE;
+    }
+    e = cudaSetDevice(device);
+    if (e != cudaSuccess) return fail_cuda(e, "cudaSetDevice");
+    trx_handle_t h = new (std::nothrow) trx_handle_s;
+    if (!h) return TRX_ERR_ALLOC;
+    h->device = device;
+    h->num_sms = prop.multiProcessorCount;
+    if ((e = cudaMalloc(&h->d_err, 256)) != cudaSuccess ||
+        (e = cudaMemset(h->d_err, 0, 256)) != cudaSuccess ||
+        (e = cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking)) != cudaSuccess ||
+        (e = leaf_configure_all()) != cudaSuccess) {
+        trx_destroy(h);
+        return fail_cuda(e, "handle setup");
+    }
+    if (workspace_bytes > 0) {
+        e = cudaMalloc(&h->ws, workspace_bytes);
+        if (e != cudaSuccess) {
+            h->ws = nullptr;
+            trx_destroy(h);
+            snprintf(g_detail, sizeof(g_detail), "workspace cudaMalloc: %s", cudaGetErrorString(e));
+            return TRX_ERR_ALLOC;
+        }
+        h->ws_bytes = workspace_bytes;
+        h->ws_owned = true;
+    }
+    *handle = h;
+    return TRX_SUCCESS;
+}
+
+int trx_destroy(trx_handle_t h) {
+    if (h == nullptr) return TRX_SUCCESS;
+    if (!valid(h)) return TRX_ERR_HANDLE;
+    cudaSetDevice(h->device);
+    cudaDeviceSynchronize();
+    drop_graphs(h);
+    for (auto& p : h->pending) {
+        cudaEventDestroy(p.e0);
+        cudaEventDestroy(p.e1);
+    }
+    for (auto ev : h->free_events) cudaEventDestroy(ev);
+    free_owned_ws(h);
+    if (h->d_err) cudaFree(h->d_err);
+    if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+    h->magic = 0;
+    delete h;
+    return TRX_SUCCESS;
+}
+
+int trx_set_workspace(trx_handle_t h, void* ptr, size_t bytes) {
+    if (!valid(h)) return TRX_ERR_HANDLE;
+    if ((reinterpret_cast<uintptr_t>(ptr) & 255) != 0) return TRX_ERR_INVALID_VALUE;
+    if (ptr == h->ws && bytes == h->ws_bytes) return TRX_SUCCESS;
+    cudaSetDevice(h->device);
+    cudaDeviceSynchronize();
+    drop_graphs(h);   // cached graphs point into the old workspace
+    free_owned_ws(h);
+    h->ws = ptr;
+    h->ws_bytes = ptr ? bytes : 0;
+    return TRX_SUCCESS;
+}
+
+int trx_workspace_size(trx_handle_t h, char op, char side, int64_t m, int64_t n, int elem_bytes,
+                       size_t* bytes) {
+    if (upc(side) != 'L' && upc(side) != 'R') return -1;
+    if (m < 0) return -5;
+    if (n < 0) return -6;
+    if (!valid(h)) return TRX_ERR_HANDLE;
+    if ((elem_bytes != 4 && elem_bytes != 8) || (upc(op) != 'S' && upc(op) != 'M' && upc(op) != 'G') || !bytes)
+        return TRX_ERR_INVALID_VALUE;
+    int64_t k = upc(side) == 'L' ? m : n, nrhs = upc(side) == 'L' ? n : m;
+    bool tc = elem_bytes == 4 ? use_tc<float>(h, k) : false;
+    if (upc(op) == 'G') {   // tensor-core trx_sgemm_update: m = M + K rows, n = N
+        k = m;
+        nrhs = n;
+        tc = true;
+    }
+    *bytes = (tc && k > 0 && nrhs > 0) ? ws_layout(k, nrhs).total : 0;
+    return TRX_SUCCESS;
+}
+
+int trx_strsm(trx_handle_t h, char side, char uplo, char transa, char diag, int64_t m, int64_t n,
+              float alpha, const float* A, int64_t lda, float* B, int64_t ldb, void* stream) {
+    return execute<float>(h, true, side, uplo, transa, diag, m, n, alpha, A, lda, B, ldb, stream);
+}
+int trx_dtrsm(trx_handle_t h, char side, char uplo, char transa, char diag, int64_t m, int64_t n,
+              double alpha, const double* A, int64_t lda, double* B, int64_t ldb, void* stream) {
+    return execute<double>(h, true, side, uplo, transa, diag, m, n, alpha, A, lda, B, ldb, stream);
+}
+int trx_strmm(trx_handle_t h, char side, char uplo, char transa, char diag, int64_t m, int64_t n,
+              float alpha, const float* A, int64_t lda, float* B, int64_t ldb, void* stream) {
+    return execute<float>(h, false, side, uplo, transa, diag, m, n, alpha, A, lda, B, ldb, stream);
+}
+int trx_dtrmm(trx_handle_t h, char side, char uplo, char transa, char diag, int64_t m, int64_t n,
+              double alpha, const double* A, int64_t lda, double* B, int64_t ldb, void* stream) {
+    return execute<double>(h, false, side, uplo, transa, diag, m, n, alpha, A, lda, B, ldb,
+                           stream);
+}
+
+int trx_sgemm_update(trx_handle_t h, int64_t M, int64_t N, int64_t K, float beta, float gamma,
+                     const float* A, int64_t lda, const float* Y, int64_t ldy, float* C,
+                     int64_t ldc, int engine, void* stream) {
+    if (M < 0) return -2;
+    if (N < 0) return -3;
+    if (K < 0) return -4;
+    if (M > 0 && K > 0 && A == nullptr) return -7;
+    if (lda < std::max<int64_t>(1, M)) return -8;
+    if (K > 0 && N > 0 && Y == nullptr) return -9;
+    if (ldy < std::max<int64_t>(1, K)) return -10;
+    if (M > 0 && N > 0 && C == nullptr) return -11;
+    if (ldc < std::max<int64_t>(1, M)) return -12;
+    if (engine != 1 && engine != 2) return -13;
+    if (!valid(h)) return TRX_ERR_HANDLE;
+    if (M == 0 || N == 0) return TRX_SUCCESS;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaSetDevice(h->device);
+    if (e != cudaSuccess) return fail_cuda(e, "cudaSetDevice");
+    // Canonical frame: rows [0, K) hold Y, rows [K, K+M) hold C, and
+    // M(K+i, l) = A(i, l); the update is rc = K, rk = 0.
+    Canon<float> c;
+    c.k = K + M;
+    c.nrhs = N;
+    c.A = A - K;
+    c.a_rs = 1;
+    c.a_cs = lda;
+    c.C = C - K;
+    c.c_rs = 1;
+    c.c_cs = ldc;
+    if (engine == 1 || K == 0) {
+        e = launch_gemm_simt<float>(c, Y, 1, ldy, K, M, 0, K, beta, K == 0 ? 0.f : gamma, s);
+        return e == cudaSuccess ? TRX_SUCCESS : fail_cuda(e, "gemm_simt");
+    }
+    if (K % kTcKQuantum != 0) return -4;
+    const WsLayout w = ws_layout(K + M, N);
+    if (h->ws == nullptr || h->ws_bytes < w.total) {
+        snprintf(g_detail, sizeof(g_detail), "workspace of %zu bytes needed, %zu set", w.total,
+                 h->ws_bytes);
+        return TRX_ERR_WORKSPACE;
+    }
+    char* base = static_cast<char*>(h->ws);
+    Planes pl;
+    pl.ldm = w.ldm;
+    pl.ldy = w.ldy;
+    pl.m_hi = reinterpret_cast<__nv_bfloat16*>(base);
+    pl.m_lo = reinterpret_cast<__nv_bfloat16*>(base + w.m_bytes);
+    pl.y_hi = reinterpret_cast<__nv_bfloat16*>(base + 2 * w.m_bytes);
+    pl.y_lo = reinterpret_cast<__nv_bfloat16*>(base + 2 * w.m_bytes + w.y_bytes);
+    if ((e = launch_convert_rect(A, 1, lda, M, K, pl.m_hi + K * pl.ldm, pl.m_lo + K * pl.ldm,
+                                 pl.ldm, true, s)) != cudaSuccess ||
+        (e = launch_convert_rect(Y, 1, ldy, K, N, pl.y_hi, pl.y_lo, pl.ldy, false, s)) !=
+            cudaSuccess)
+        return fail_cuda(e, "convert");
+    h->maps.resize(tc_maps_size());
+    if ((e = tc_make_maps(pl, K + M, N, h->maps.data())) != cudaSuccess)
+        return fail_cuda(e, "tensor map encode");
+    const TcGemm g{K, M, 0, K};
+    e = launch_gemm_tc(c, h->maps.data(), &g, 1, beta, gamma, h->d_err, h->wait_ns, h->num_sms, s);
+    return e == cudaSuccess ? TRX_SUCCESS : fail_cuda(e, "gemm_tc");
+}
+
+int trx_set_option(trx_handle_t h, int option, int64_t value) {
+    if (!valid(h)) return TRX_ERR_HANDLE;
+    switch (option) {
+        case TRX_OPT_LEAF:
+            if (value != 0 && value != 16 && value != 32 && value != 64 && value != 128)
+                return TRX_ERR_INVALID_VALUE;
+            h->opt_leaf = value;
+            break;
+        case TRX_OPT_GEMM:
+            if (value < 0 || value > 2) return TRX_ERR_INVALID_VALUE;
+            h->opt_gemm = value;
+            break;
+        case TRX_OPT_GRAPH:
+            if (value != 0 && value != 1) return TRX_ERR_INVALID_VALUE;
+            h->opt_graph = value;
+            break;
+        case TRX_OPT_PROFILE:
+            if (value != 0 && value != 1) return TRX_ERR_INVALID_VALUE;
+            h->opt_profile = value;
+            break;
+        case TRX_OPT_WAIT_LIMIT:
+            if (value < 1000) return TRX_ERR_INVALID_VALUE;
+            h->wait_ns = value;
+            break;
+        default:
+            return TRX_ERR_INVALID_VALUE;
+    }
+    return TRX_SUCCESS;
+}
+
+int trx_get_option(trx_handle_t h, int option, int64_t* value) {
+    if (!valid(h)) return TRX_ERR_HANDLE;
+    if (!value) return TRX_ERR_INVALID_VALUE;
+    switch (option) {
+        case TRX_OPT_LEAF: *value = h->opt_leaf; break;
+        case TRX_OPT_GEMM: *value = h->opt_gemm; break;
+        case TRX_OPT_GRAPH: *value = h->opt_graph; break;
+        case TRX_OPT_PROFILE: *value = h->opt_profile; break;
+        case TRX_OPT_WAIT_LIMIT: *value = h->wait_ns; break;
+        default: return TRX_ERR_INVALID_VALUE;
+    }
+    return TRX_SUCCESS;
+}
+
+int trx_get_profile(trx_handle_t h, trx_profile_t* out, int reset) {
+    if (!valid(h)) return TRX_ERR_HANDLE;
+    cudaSetDevice(h->device);
+    for (auto& p : h->pending) {
+        cudaError_t e = cudaEventSynchronize(p.e1);
+        if (e != cudaSuccess) return fail_cuda(e, "cudaEventSynchronize");
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, p.e0, p.e1);
+        h->prof.ms[p.cls] += ms;
+        h->prof.flops[p.cls] += p.flops;
+        h->prof.bytes[p.cls] += p.bytes;
+        h->prof.launches[p.cls] += 1;
+        h->free_events.push_back(p.e0);
+        h->free_events.push_back(p.e1);
+    }
+    h->pending.clear();
+    if (out) *out = h->prof;
+    if (reset) std::memset(&h->prof, 0, sizeof(h->prof));
+    return TRX_SUCCESS;
+}
+
+int trx_check_device_error(trx_handle_t h) {
+    if (!valid(h)) return TRX_ERR_HANDLE;
+    cudaSetDevice(h->device);
+    int v = 0;
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return fail_cuda(e, "cudaDeviceSynchronize");
+    e = cudaMemcpy(&v, h->d_err, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return fail_cuda(e, "read error word");
+    if (v != 0) {
+        cudaMemset(h->d_err, 0, sizeof(int));
+        return v;
+    }
+    return TRX_SUCCESS;
+}
+
+const char* trx_error_string(int code) {
+    if (code < 0 && code >= -11) {
+        static const char* names[] = {"side", "uplo", "transa", "diag", "m", "n",
+                                      "alpha", "A", "lda", "B", "ldb"};
+        static thread_local char buf[64];
+        snprintf(buf, sizeof(buf), "illegal argument %d (%s)", -code, names[-code - 1]);
+        return buf;
+    }
+    switch (code) {
+        case TRX_SUCCESS: return "success";
+        case TRX_ERR_HANDLE: return "invalid handle";
+        case TRX_ERR_CUDA: return "CUDA error";
+        case TRX_ERR_WORKSPACE: return "workspace missing or too small";
+        case TRX_ERR_TIMEOUT: return "a bounded device-side wait timed out";
+        case TRX_ERR_DEVICE: return "device is not sm_103 (GB300)";
+        case TRX_ERR_ALLOC: return "allocation failed";
+        case TRX_ERR_INVALID_VALUE: return "invalid option or value";
+        default: return "unknown error";
+    }
+}
+
+const char* trx_last_error_detail(void) { return g_detail; }
+
+int trx_debug_plan(char op, char side, char uplo, char transa, char diag, int64_t m, int64_t n,
+                   int elem_bytes, int leaf, int gemm_mode, char* buf, size_t buflen) {
+    const int info = check_args(side, uplo, transa, diag, m, n, "", std::max<int64_t>(1, upc(side) == 'L' ? m : n),
+                                "", std::max<int64_t>(1, m));
+    if (info) return info;
+    if ((upc(op) != 'S' && upc(op) != 'M') || (elem_bytes != 4 && elem_bytes != 8) ||
+        (leaf != 0 && leaf != 16 && leaf != 32 && leaf != 64 && leaf != 128) || gemm_mode < 0 ||
+        gemm_mode > 2 || !buf || buflen == 0)
+        return TRX_ERR_INVALID_VALUE;
+    buf[0] = 0;
+    const int64_t k = upc(side) == 'L' ? m : n;
+    if (m == 0 || n == 0) return TRX_SUCCESS;
+    const int b = (int)std::min<int64_t>(leaf > 0 ? leaf : kDefaultLeaf, std::max<int64_t>(k, 1));
+    Plan plan;
+    plan.tc = use_tc_mode(elem_bytes, gemm_mode, k, b);
+    make_plan(plan, upc(op) == 'S', k, b, 2.0);
+    std::string out;
+    char line[256];
+    for (const Step& st : plan.steps) {
+        switch (st.kind) {
+            case kConvM: out += "conv_m\n"; break;
+            case kConvY: out += "conv_y\n"; break;
+            case kLeaf:
+                snprintf(line, sizeof(line), "leaf trsm=%d r0=%lld b=%d nleaves=%lld alpha=%.17g planes=%d\n",
+                         (int)st.trsm, (long long)st.r0, st.b, (long long)st.nleaves, st.alpha,
+                         (int)st.planes);
+                out += line;
+                break;
+            case kGemm:
+                for (size_t i = 0; i < st.gemms.size(); ++i) {
+                    const TcGemm& g = st.gemms[i];
+                    snprintf(line, sizeof(line),
+                             "gemm tc=%d member=%zu rc=%lld mlen=%lld rk=%lld klen=%lld beta=%.17g gamma=%.17g\n",
+                             (int)st.tc, i, (long long)g.rc, (long long)g.mlen, (long long)g.rk,
+                             (long long)g.klen, st.beta, st.gamma);
+                    out += line;
+                }
+                break;
+        }
+    }
+    if (out.size() + 1 > buflen) return TRX_ERR_INVALID_VALUE;
+    std::memcpy(buf, out.c_str(), out.size() + 1);
+    return TRX_SUCCESS;
+}
+
+int trx_version(void) { return 100; }
+
+}  // extern "C"

@@ -1,0 +1,107 @@
+// Internal declarations shared by the trx CUDA sources.
+//
+// Every kernel works on one canonical form of the problem. The C-ABI layer
+// (api.cu) maps each of the 16 side/uplo/trans/diag variants of Eq. 1-4
+// (Section 2.1) onto it:
+//
+//   * M is a k x k LOWER triangular matrix read through signed strides,
+//     M(i,l) = A[i*a_rs + l*a_cs]. op(A) is used directly for side 'L'
+//     (op(A) X = alpha B) and op(A)^T for side 'R' (X op(A) = alpha B is
+//     op(A)^T X^T = alpha B^T); an effectively-upper matrix is turned into a
+//     lower one by reversing the index order (i -> k-1-i), which makes the
+//     back substitution a forward one.
+//   * C is the k x nrhs right-hand side / result, C(i,j) = C[i*c_rs + j*c_cs]
+//     (B itself for side 'L', B^T for side 'R', row-reversed with M).
+//
+// So the recursion of Section 3.1 is written once, for the lower case:
+// TRSM solves M11 X1 = C1, updates C2 -= M21 X1 (GEMM), solves M22 X2 = C2;
+// TRMM forms C2 := M22 C2 + M21 C1 and C1 := M11 C1.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+namespace trx {
+
+template <typename T>
+struct Canon {
+    int64_t k = 0;       // order of M
+    int64_t nrhs = 0;    // right-hand sides (columns of C)
+    const T* A = nullptr;
+    int64_t a_rs = 0, a_cs = 0;
+    T* C = nullptr;
+    int64_t c_rs = 0, c_cs = 0;
+    int unit = 0;        // diag == 'U': M(i,i) taken as 1, never read
+};
+
+// Split-BF16 operand planes of the tensor-core FP32 path (canonical order).
+//   M planes: strictly-lower part of M, element (i, l) at i*ldm + l
+//             (K-major A operand of the GEMM update).
+//   Y planes: the GEMM's B operand, element (l, j) at j*ldy + l
+//             (K-major): the solved X rows for TRSM, the original C for TRMM.
+// hi = bf16(x), lo = bf16(x - hi); x = hi + lo to about 2^-17 relative.
+struct Planes {
+    __nv_bfloat16* m_hi = nullptr;
+    __nv_bfloat16* m_lo = nullptr;
+    int64_t ldm = 0;
+    __nv_bfloat16* y_hi = nullptr;
+    __nv_bfloat16* y_lo = nullptr;
+    int64_t ldy = 0;
+};
+
+// ---- launchers (host) --------------------------------------------------------
+
+// Leaf TRSM / TRMM (Section 3.3) on rows [r0 + t*b, r0 + t*b + b) for
+// t = 0 .. nleaves-1 (clipped to k), all right-hand sides. alpha scales the
+// right-hand side (TRSM) or the product (TRMM). With planes != nullptr the
+// TRSM leaf also writes its solved rows into the Y planes.
+template <typename T>
+cudaError_t launch_leaf(bool trsm, const Canon<T>& p, int64_t r0, int b,
+                        int64_t nleaves, T alpha, const Planes* planes,
+                        int num_sms, cudaStream_t s);
+
+// Largest leaf the kernels support.
+constexpr int kMaxLeaf = 128;
+
+// CUDA-core GEMM update on the canonical matrices:
+//   C[rc+i, j] = beta*C[rc+i, j] + gamma * sum_l M(rc+i, rk+l) * Y[rk+l, j]
+// for i < mlen, l < klen, j < nrhs, Y(l, j) = Y[l*y_rs + j*y_cs]. In the
+// recursion Y is C itself and rows [rc, rc+mlen), [rk, rk+klen) are disjoint.
+template <typename T>
+cudaError_t launch_gemm_simt(const Canon<T>& p, const T* Y, int64_t y_rs, int64_t y_cs,
+                             int64_t rc, int64_t mlen, int64_t rk, int64_t klen, T beta,
+                             T gamma, cudaStream_t s);
+
+// B := 0 over an m x n column-major block (alpha == 0 quick return).
+template <typename T>
+cudaError_t launch_zero(T* B, int64_t m, int64_t n, int64_t ldb, cudaStream_t s);
+
+// Split-BF16 planes of the strictly-lower part of M (rows/cols [0,k)).
+cudaError_t launch_convert_m(const Canon<float>& p, const Planes& pl, cudaStream_t s);
+// Split-BF16 planes of C rows [0,k), all columns (TRMM's original values).
+cudaError_t launch_convert_y(const Canon<float>& p, const Planes& pl, cudaStream_t s);
+// Split-BF16 planes of a rows x cols block, src(r, c) = src[r*rs + c*cs];
+// dst(r, c) at dst[r*ld + c] (row_major) or dst[c*ld + r] (otherwise).
+cudaError_t launch_convert_rect(const float* src, int64_t rs, int64_t cs, int64_t rows,
+                                int64_t cols, __nv_bfloat16* hi, __nv_bfloat16* lo,
+                                int64_t ld, bool row_major, cudaStream_t s);
+
+// Tensor-core GEMM update, one launch for a group of updates that write
+// disjoint row ranges (FP32 in/out, 3-term split BF16 products, FP32
+// accumulation in TMEM):
+//   C[rc+i, j] = beta*C[rc+i, j] + gamma * sum_l M(rc+i, rk+l) Y(rk+l, j)
+struct TcGemm {
+    int64_t rc, mlen, rk, klen;
+};
+struct TcMaps;   // opaque: tensor maps over the planes (gemm_tc.cu)
+int tc_maps_size();
+cudaError_t tc_make_maps(const Planes& pl, int64_t k, int64_t nrhs, void* maps_out);
+cudaError_t launch_gemm_tc(const Canon<float>& p, const void* maps,
+                           const TcGemm* gemms, int ngemms, float beta,
+                           float gamma, int* err_word, long long wait_limit,
+                           int num_sms, cudaStream_t s);
+// K granularity the tensor-core GEMM needs (klen and rk multiples of this).
+constexpr int kTcKQuantum = 64;
+
+}  // namespace trx

@@ -1,0 +1,154 @@
+// Operand preparation for the tensor-core FP32 path, and the alpha == 0
+// quick return.
+//
+// The tcgen05 GEMM update multiplies BF16 operands. An FP32 value x is carried
+// as two BF16 planes, hi = bf16(x) and lo = bf16(x - hi) (x = hi + lo to about
+// 2^-17 relative), and a product as hi*hi + hi*lo + lo*hi with FP32
+// accumulation (the lo*lo term is below that error). These kernels write the
+// planes in the canonical K-major order the GEMM's TMA loads expect:
+//   M planes: strictly-lower part of M, (i, l) at i*ldm + l
+//   Y planes: C (TRMM's original right-hand side), (l, j) at j*ldy + l
+// 32x32 tiles go through shared memory, so reads are coalesced along
+// whichever index is contiguous in the caller's storage and writes along the
+// planes' contiguous index.
+#include "common.cuh"
+
+namespace trx {
+namespace {
+
+__device__ __forceinline__ void split_bf16(float x, __nv_bfloat16& hi, __nv_bfloat16& lo) {
+    hi = __float2bfloat16_rn(x);
+    lo = __float2bfloat16_rn(x - __bfloat162float(hi));
+}
+
+__global__ void __launch_bounds__(256) convert_m_kernel(Canon<float> p, Planes pl) {
+    __shared__ float tile[32][33];
+    const int64_t ti = blockIdx.y, tl = blockIdx.x;
+    if (tl > ti) return;                        // entirely above the diagonal
+    const int64_t i0 = ti * 32, l0 = tl * 32;
+    const bool row_fast = (p.a_rs == 1 || p.a_rs == -1);
+    for (int r = threadIdx.y; r < 32; r += 8) {
+        const int x = threadIdx.x;
+        const int ii = row_fast ? x : r, ll = row_fast ? r : x;
+        const int64_t i = i0 + ii, l = l0 + ll;
+        float v = 0.f;
+        if (i < p.k && l < i) v = p.A[i * p.a_rs + l * p.a_cs];
+        tile[ii][ll] = v;
+    }
+    __syncthreads();
+    for (int r = threadIdx.y; r < 32; r += 8) {
+        const int64_t i = i0 + r, l = l0 + threadIdx.x;
+        if (i < p.k && l < p.k) {
+            __nv_bfloat16 hi, lo;
+            split_bf16(tile[r][threadIdx.x], hi, lo);
+            pl.m_hi[i * pl.ldm + l] = hi;
+            pl.m_lo[i * pl.ldm + l] = lo;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(256) convert_y_kernel(Canon<float> p, Planes pl) {
+    __shared__ float tile[32][33];              // tile[jj][ll]
+    const int64_t l0 = (int64_t)blockIdx.x * 32, j0 = (int64_t)blockIdx.y * 32;
+    const bool row_fast = (p.c_rs == 1 || p.c_rs == -1);
+    for (int r = threadIdx.y; r < 32; r += 8) {
+        const int x = threadIdx.x;
+        const int ll = row_fast ? x : r, jj = row_fast ? r : x;
+        const int64_t l = l0 + ll, j = j0 + jj;
+        float v = 0.f;
+        if (l < p.k && j < p.nrhs) v = p.C[l * p.c_rs + j * p.c_cs];
+        tile[jj][ll] = v;
+    }
+    __syncthreads();
+    for (int r = threadIdx.y; r < 32; r += 8) {
+        const int64_t j = j0 + r, l = l0 + threadIdx.x;
+        if (l < p.k && j < p.nrhs) {
+            __nv_bfloat16 hi, lo;
+            split_bf16(tile[r][threadIdx.x], hi, lo);
+            pl.y_hi[j * pl.ldy + l] = hi;
+            pl.y_lo[j * pl.ldy + l] = lo;
+        }
+    }
+}
+
+// Generic block: tile[rr][cc] staged so that both sides are coalesced.
+__global__ void __launch_bounds__(256) convert_rect_kernel(const float* src, int64_t rs,
+                                                           int64_t cs, int64_t rows, int64_t cols,
+                                                           __nv_bfloat16* hi, __nv_bfloat16* lo,
+                                                           int64_t ld, int row_major) {
+    __shared__ float tile[32][33];
+    const int64_t r0 = (int64_t)blockIdx.y * 32, c0 = (int64_t)blockIdx.x * 32;
+    const bool src_row_fast = (rs == 1 || rs == -1);
+    for (int t = threadIdx.y; t < 32; t += 8) {
+        const int rr = src_row_fast ? threadIdx.x : t, cc = src_row_fast ? t : threadIdx.x;
+        const int64_t r = r0 + rr, c = c0 + cc;
+        tile[rr][cc] = (r < rows && c < cols) ? src[r * rs + c * cs] : 0.f;
+    }
+    __syncthreads();
+    for (int t = threadIdx.y; t < 32; t += 8) {
+        // destination contiguous index runs along threadIdx.x
+        const int rr = row_major ? t : threadIdx.x, cc = row_major ? threadIdx.x : t;
+        const int64_t r = r0 + rr, c = c0 + cc;
+        if (r < rows && c < cols) {
+            __nv_bfloat16 h, l;
+            split_bf16(tile[rr][cc], h, l);
+            const int64_t o = row_major ? r * ld + c : c * ld + r;
+            hi[o] = h;
+            lo[o] = l;
+        }
+    }
+}
+
+template <typename T>
+__global__ void zero_kernel(T* B, int64_t m, int64_t n, int64_t ldb) {
+    const int64_t total = m * n;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = e % m, j = e / m;
+        B[i + j * ldb] = T(0);
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_convert_m(const Canon<float>& p, const Planes& pl, cudaStream_t s) {
+    if (p.k <= 1) return cudaSuccess;
+    const int64_t t = (p.k + 31) / 32;
+    if (t > 65535) return cudaErrorInvalidValue;
+    convert_m_kernel<<<dim3((unsigned)t, (unsigned)t), dim3(32, 8), 0, s>>>(p, pl);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_convert_y(const Canon<float>& p, const Planes& pl, cudaStream_t s) {
+    if (p.k <= 0 || p.nrhs <= 0) return cudaSuccess;
+    const int64_t tl = (p.k + 31) / 32, tj = (p.nrhs + 31) / 32;
+    if (tj > 65535) return cudaErrorInvalidValue;
+    convert_y_kernel<<<dim3((unsigned)tl, (unsigned)tj), dim3(32, 8), 0, s>>>(p, pl);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_convert_rect(const float* src, int64_t rs, int64_t cs, int64_t rows,
+                                int64_t cols, __nv_bfloat16* hi, __nv_bfloat16* lo,
+                                int64_t ld, bool row_major, cudaStream_t s) {
+    if (rows <= 0 || cols <= 0) return cudaSuccess;
+    const int64_t gy = (rows + 31) / 32, gx = (cols + 31) / 32;
+    if (gy > 65535) return cudaErrorInvalidValue;
+    convert_rect_kernel<<<dim3((unsigned)gx, (unsigned)gy), dim3(32, 8), 0, s>>>(
+        src, rs, cs, rows, cols, hi, lo, ld, row_major ? 1 : 0);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_zero(T* B, int64_t m, int64_t n, int64_t ldb, cudaStream_t s) {
+    if (m <= 0 || n <= 0) return cudaSuccess;
+    const int64_t total = m * n;
+    int64_t blocks = (total + 255) / 256;
+    if (blocks > 65536) blocks = 65536;
+    zero_kernel<T><<<(unsigned)blocks, 256, 0, s>>>(B, m, n, ldb);
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_zero<float>(float*, int64_t, int64_t, int64_t, cudaStream_t);
+template cudaError_t launch_zero<double>(double*, int64_t, int64_t, int64_t, cudaStream_t);
+
+}  // namespace trx

@@ -1,0 +1,452 @@
+// Tensor-core GEMM update for the FP32 path (tcgen05 + TMEM + TMA, sm_103a).
+//
+//   C[rc+i, j] = beta * C[rc+i, j] + gamma * sum_l M(rc+i, rk+l) * Y(rk+l, j)
+//
+// This is the off-diagonal step of the recursion of Section 3.1 (TRSM:
+// B2 := beta*B2 - M21 X1; TRMM: B2 += alpha M21 B1), where the paper's
+// speed comes from (Section 3.3: the base kernels must stay small next to the
+// GEMMs). FP32 operands are carried as split BF16 planes (convert.cu, leaf
+// kernels) and every product is formed as hi*hi + hi*lo + lo*hi with FP32
+// accumulation in tensor memory, which keeps the update at about 2^-16
+// relative error per product instead of BF16's 2^-8.
+//
+// One launch handles a group of updates whose output rows are disjoint (one
+// recursion node for TRSM, one whole recursion level for TRMM); the tiles of
+// all of them form one persistent tile sequence.
+//
+// Structure (one CTA per SM, 192 threads, warp-specialised):
+//   warp 0     TMA producer: 4 tiles per K step (A hi/lo 128x32, Y hi/lo
+//              256x32, 64-byte swizzle) into a 4-stage shared-memory ring
+//   warp 1     TMEM allocator and MMA issuer: per K step 2 x 3
+//              tcgen05.mma (M=128, N=256, K=16, BF16 in, FP32 accumulate),
+//              tcgen05.commit frees the ring slot
+//   warps 2-5  epilogue: tcgen05.ld of the accumulator (warp w reads TMEM
+//              lanes 32*(w%4) ..), read-modify-write of C in global memory
+// Two 256-column accumulators (all 512 TMEM columns) let the epilogue of one
+// tile overlap the main loop of the next.
+//
+// Every wait on an mbarrier is bounded by a wall-clock budget: past it the
+// kernel writes TRX_ERR_TIMEOUT to the error word, stops issuing work, drains
+// the copies and MMAs it has in flight (again with a bound), frees its TMEM
+// and returns.
+#include <cuda.h>
+#include <stdint.h>
+
+#include "common.cuh"
+
+namespace trx {
+namespace tc {
+
+constexpr int BM = 128, BN = 256, BK = 32;          // BK in BF16 elements (64 B)
+constexpr int STAGES = 4;
+constexpr int A_TILE = BM * BK * 2;                 // 8 KiB
+constexpr int B_TILE = BN * BK * 2;                 // 16 KiB
+constexpr int STAGE_BYTES = 2 * A_TILE + 2 * B_TILE; // 48 KiB
+constexpr int MAXG = 256;
+constexpr int NTHREADS = 192;
+constexpr int TMEM_COLS = 512;
+constexpr int SMEM_BYTES = 1024 + STAGES * STAGE_BYTES + 256;
+constexpr int kTimeout = 4;                          // TRX_ERR_TIMEOUT
+
+// kind::f16 instruction descriptor: FP32 accumulator, BF16 A and B, both
+// K-major, N = 256, M = 128.
+constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) |
+                           ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+
+struct Maps {
+    CUtensorMap a_hi, a_lo, b_hi, b_lo;
+};
+
+struct Params {
+    Maps maps;
+    float* C;
+    int64_t c_rs, c_cs, nrhs;
+    float beta, gamma;
+    int ngemms, n_tiles_n, total_tiles;
+    int* err;
+    long long wait_ns;
+    int tile_start[MAXG + 1];
+    TcGemm g[MAXG];
+};
+
+// ---- PTX wrappers ---------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ uint64_t gtimer() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, uint32_t bar,
+                                            int x, int y) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%3, %4}], [%2];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(bar), "r"(x), "r"(y)
+        : "memory");
+}
+// Shared-memory matrix descriptor, K-major operand in the 64-byte swizzle
+// layout TMA writes: 8-row core-matrix groups 512 B apart (stride byte
+// offset), leading byte offset unused for swizzled K-major, version 1.
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
+    return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)1 << 16) |
+           ((uint64_t)(512 >> 4) << 32) | ((uint64_t)1 << 46) | ((uint64_t)4 << 61);
+}
+__device__ __forceinline__ void umma(uint32_t d, uint64_t a, uint64_t b, uint32_t accum) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d),
+        "l"(a), "l"(b), "r"(IDESC), "r"(accum));
+}
+__device__ __forceinline__ void umma_commit(uint32_t bar) {
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+        : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+        "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+          "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),
+          "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+          "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
+          "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+struct Smem {
+    uint64_t full[STAGES], empty[STAGES], acc_full[2], acc_empty[2], drain;
+    uint32_t tmem_base;
+    int abort;
+};
+
+// Wait for phase `parity` of an mbarrier, bounded: false on timeout (the
+// error word and the CTA's abort flag are set) or when another role of the
+// CTA has already aborted.
+// Drains (honour_abort == false) wait at least 1 s whatever the configured
+// budget, so in-flight copies and MMAs land before the CTA exits.
+__device__ bool wait_bounded(uint32_t bar, uint32_t parity, const Params& p, volatile int* abort,
+                             bool honour_abort = true) {
+    if (mbar_try(bar, parity)) return true;
+    const uint64_t t0 = gtimer();
+    const uint64_t limit = honour_abort ? (uint64_t)p.wait_ns
+                                        : max((uint64_t)p.wait_ns, (uint64_t)1000000000ull);
+    while (true) {
+        if (mbar_try(bar, parity)) return true;
+        if (honour_abort && *abort) return false;
+        if (gtimer() - t0 > limit) {
+            *abort = 1;
+            atomicExch(p.err, kTimeout);
+            return false;
+        }
+    }
+}
+
+struct Tile {
+    int g, m, n;
+};
+
+// Tile t of the group: find its update (prefix sums), then raster the
+// update's (m, n) tiles in bands of 8 M-tiles so that the CTAs running at one
+// time share operand rows and columns in L2.
+__device__ __forceinline__ Tile map_tile(const Params& p, int t) {
+    int lo = 0, hi = p.ngemms - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (p.tile_start[mid] <= t) lo = mid; else hi = mid - 1;
+    }
+    const int local = t - p.tile_start[lo];
+    const int mt = (int)((p.g[lo].mlen + BM - 1) / BM);
+    constexpr int GM = 8;
+    const int band = local / (GM * p.n_tiles_n);
+    const int first = band * GM;
+    const int gm = min(GM, mt - first);
+    const int idx = local - band * GM * p.n_tiles_n;
+    Tile r;
+    r.g = lo;
+    r.m = first + idx % gm;
+    r.n = idx / gm;
+    return r;
+}
+
+__global__ void __launch_bounds__(NTHREADS, 1) gemm_tc_kernel(const __grid_constant__ Params p) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    // Stage buffers must sit on a 1024-byte boundary (swizzle atom repeat).
+    const uint32_t raw = smem_u32(smem_raw);
+    const uint32_t ring = (raw + 1023u) & ~1023u;
+    Smem* sm = reinterpret_cast<Smem*>(smem_raw + (ring - raw) + STAGES * STAGE_BYTES);
+    volatile int* abort = &sm->abort;
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(smem_u32(&sm->full[s]), 1);
+            mbar_init(smem_u32(&sm->empty[s]), 1);
+        }
+        for (int a = 0; a < 2; ++a) {
+            mbar_init(smem_u32(&sm->acc_full[a]), 1);
+            mbar_init(smem_u32(&sm->acc_empty[a]), 4);
+        }
+        mbar_init(smem_u32(&sm->drain), 1);
+        sm->abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(&sm->tmem_base)),
+                     "r"(TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = sm->tmem_base;
+
+    if (warp == 0 && lane == 0) {
+        // ---------------- TMA producer ----------------
+        int stage = 0, issued = 0;
+        uint32_t phase = 0;
+        for (int t = blockIdx.x; t < p.total_tiles && !*abort; t += gridDim.x) {
+            const Tile ti = map_tile(p, t);
+            const TcGemm& G = p.g[ti.g];
+            const int nkb = (int)(G.klen / BK);
+            const int ya = (int)(G.rc + (int64_t)ti.m * BM);
+            const int yb = ti.n * BN;
+            for (int kb = 0; kb < nkb; ++kb) {
+                const uint32_t fb = smem_u32(&sm->full[stage]);
+                if (!wait_bounded(smem_u32(&sm->empty[stage]), phase ^ 1u, p, abort)) break;
+                mbar_expect_tx(fb, STAGE_BYTES);
+                const int x = (int)(G.rk + (int64_t)kb * BK);
+                const uint32_t base = ring + stage * STAGE_BYTES;
+                tma_load_2d(base, &p.maps.a_hi, fb, x, ya);
+                tma_load_2d(base + A_TILE, &p.maps.a_lo, fb, x, ya);
+                tma_load_2d(base + 2 * A_TILE, &p.maps.b_hi, fb, x, yb);
+                tma_load_2d(base + 2 * A_TILE + B_TILE, &p.maps.b_lo, fb, x, yb);
+                ++issued;
+                if (++stage == STAGES) { stage = 0; phase ^= 1u; }
+            }
+        }
+        // Copies still in flight must land before the CTA exits.
+        for (int i = 0; i < STAGES && i < issued; ++i) {
+            if (--stage < 0) { stage = STAGES - 1; phase ^= 1u; }
+            wait_bounded(smem_u32(&sm->full[stage]), phase, p, abort, false);
+        }
+    } else if (warp == 1 && lane == 0) {
+        // ---------------- MMA issuer ----------------
+        int stage = 0, acc = 0;
+        uint32_t phase = 0, acc_phase = 0;
+        for (int t = blockIdx.x; t < p.total_tiles && !*abort; t += gridDim.x) {
+            const Tile ti = map_tile(p, t);
+            const int nkb = (int)(p.g[ti.g].klen / BK);
+            if (!wait_bounded(smem_u32(&sm->acc_empty[acc]), acc_phase ^ 1u, p, abort)) break;
+            tc_fence_after();
+            const uint32_t d = tmem + (uint32_t)(acc * BN);
+            bool ok = true;
+            for (int kb = 0; kb < nkb; ++kb) {
+                if (!wait_bounded(smem_u32(&sm->full[stage]), phase, p, abort)) { ok = false; break; }
+                tc_fence_after();
+                const uint32_t base = ring + stage * STAGE_BYTES;
+#pragma unroll
+                for (int kk = 0; kk < BK / 16; ++kk) {
+                    const uint64_t ahi = sdesc(base + kk * 32);
+                    const uint64_t alo = sdesc(base + A_TILE + kk * 32);
+                    const uint64_t bhi = sdesc(base + 2 * A_TILE + kk * 32);
+                    const uint64_t blo = sdesc(base + 2 * A_TILE + B_TILE + kk * 32);
+                    umma(d, ahi, bhi, (kb | kk) != 0 ? 1u : 0u);
+                    umma(d, ahi, blo, 1u);
+                    umma(d, alo, bhi, 1u);
+                }
+                umma_commit(smem_u32(&sm->empty[stage]));
+                if (++stage == STAGES) { stage = 0; phase ^= 1u; }
+            }
+            if (!ok) break;
+            umma_commit(smem_u32(&sm->acc_full[acc]));
+            if (++acc == 2) { acc = 0; acc_phase ^= 1u; }
+        }
+        // All MMAs issued by this CTA complete before TMEM is released.
+        umma_commit(smem_u32(&sm->drain));
+        wait_bounded(smem_u32(&sm->drain), 0, p, abort, false);
+    } else if (warp >= 2) {
+        // ---------------- epilogue ----------------
+        const int q = warp & 3;                 // TMEM lanes 32q .. 32q+31
+        int acc = 0;
+        uint32_t acc_phase = 0;
+        for (int t = blockIdx.x; t < p.total_tiles; t += gridDim.x) {
+            const Tile ti = map_tile(p, t);
+            const TcGemm& G = p.g[ti.g];
+            // One lane waits and the warp follows its verdict, so the
+            // warp-collective TMEM loads below never run on a partial warp.
+            int ok = 1;
+            if (lane == 0) ok = wait_bounded(smem_u32(&sm->acc_full[acc]), acc_phase, p, abort);
+            ok = __shfl_sync(0xffffffffu, ok, 0);
+            if (!ok) break;
+            tc_fence_after();
+            const int64_t row = (int64_t)ti.m * BM + q * 32 + lane;
+            const bool row_ok = row < G.mlen;
+            float* crow = p.C + (G.rc + row) * p.c_rs;
+            const int64_t jbase = (int64_t)ti.n * BN;
+#pragma unroll 1
+            for (int ch = 0; ch < BN / 32; ++ch) {
+                float v[32];
+                tmem_ld32(tmem + (uint32_t)(acc * BN + ch * 32) + ((uint32_t)(q * 32) << 16), v);
+                if (ch == BN / 32 - 1) {
+                    tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(smem_u32(&sm->acc_empty[acc]));
+                }
+                if (row_ok) {
+                    const int64_t j0 = jbase + ch * 32;
+#pragma unroll
+                    for (int c = 0; c < 32; ++c) {
+                        const int64_t j = j0 + c;
+                        if (j < p.nrhs) {
+                            float* cp = crow + j * p.c_cs;
+                            *cp = fmaf(p.beta, *cp, p.gamma * v[c]);
+                        }
+                    }
+                }
+            }
+            if (++acc == 2) { acc = 0; acc_phase ^= 1u; }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 1) {
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                     "r"(TMEM_COLS)
+                     : "memory");
+    }
+}
+
+// ---- host ------------------------------------------------------------------
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                  const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                  const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn encode_fn() {
+    static EncodeTiledFn fn = nullptr;
+    if (!fn) {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000,
+                                             cudaEnableDefault, &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            return nullptr;
+        fn = reinterpret_cast<EncodeTiledFn>(f);
+    }
+    return fn;
+}
+
+static bool encode(CUtensorMap* m, void* base, uint64_t inner, uint64_t outer, uint64_t ld,
+                   uint32_t box_outer) {
+    EncodeTiledFn fn = encode_fn();
+    if (!fn) return false;
+    const cuuint64_t dims[2] = {inner, outer};
+    const cuuint64_t strides[1] = {ld * 2};
+    const cuuint32_t box[2] = {(cuuint32_t)BK, box_outer};
+    const cuuint32_t estr[2] = {1, 1};
+    return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, base, dims, strides, box, estr,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
+              CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+}  // namespace tc
+
+int tc_maps_size() { return (int)sizeof(tc::Maps); }
+
+cudaError_t tc_configure() {
+    return cudaFuncSetAttribute(tc::gemm_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                tc::SMEM_BYTES);
+}
+
+cudaError_t tc_make_maps(const Planes& pl, int64_t k, int64_t nrhs, void* out) {
+    tc::Maps* m = reinterpret_cast<tc::Maps*>(out);
+    if (k <= 0 || nrhs <= 0) return cudaErrorInvalidValue;
+    if (!tc::encode(&m->a_hi, pl.m_hi, k, k, pl.ldm, tc::BM) ||
+        !tc::encode(&m->a_lo, pl.m_lo, k, k, pl.ldm, tc::BM) ||
+        !tc::encode(&m->b_hi, pl.y_hi, k, nrhs, pl.ldy, tc::BN) ||
+        !tc::encode(&m->b_lo, pl.y_lo, k, nrhs, pl.ldy, tc::BN))
+        return cudaErrorInvalidValue;
+    return cudaSuccess;
+}
+
+cudaError_t launch_gemm_tc(const Canon<float>& p, const void* maps, const TcGemm* gemms,
+                           int ngemms, float beta, float gamma, int* err_word,
+                           long long wait_ns, int num_sms, cudaStream_t s) {
+    using namespace tc;
+    for (int g0 = 0; g0 < ngemms; g0 += MAXG) {
+        const int ng = (ngemms - g0) < MAXG ? (ngemms - g0) : MAXG;
+        static thread_local Params prm;
+        prm.maps = *reinterpret_cast<const Maps*>(maps);
+        prm.C = p.C;
+        prm.c_rs = p.c_rs;
+        prm.c_cs = p.c_cs;
+        prm.nrhs = p.nrhs;
+        prm.beta = beta;
+        prm.gamma = gamma;
+        prm.ngemms = ng;
+        prm.n_tiles_n = (int)((p.nrhs + BN - 1) / BN);
+        prm.err = err_word;
+        prm.wait_ns = wait_ns;
+        int64_t tiles = 0;
+        for (int i = 0; i < ng; ++i) {
+            const TcGemm& G = gemms[g0 + i];
+            if (G.klen <= 0 || G.klen % BK != 0 || G.rk % 8 != 0) return cudaErrorInvalidValue;
+            prm.g[i] = G;
+            prm.tile_start[i] = (int)tiles;
+            tiles += ((G.mlen + BM - 1) / BM) * (int64_t)prm.n_tiles_n;
+        }
+        prm.tile_start[ng] = (int)tiles;
+        if (tiles <= 0) continue;
+        if (tiles > (int64_t)1 << 30) return cudaErrorInvalidValue;
+        prm.total_tiles = (int)tiles;
+        const int grid = (int)(tiles < num_sms ? tiles : num_sms);
+        gemm_tc_kernel<<<grid, NTHREADS, SMEM_BYTES, s>>>(prm);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+}  // namespace trx

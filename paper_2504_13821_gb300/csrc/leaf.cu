@@ -1,0 +1,63 @@
+// Leaf kernels: lane-count choice and dispatch. The kernels themselves are in
+// leaf_impl.cuh.
+#include "leaf_impl.cuh"
+
+namespace trx {
+
+// One translation unit per (type, operation) keeps the unrolled sweeps'
+// compile time in parallel; leaf_*.cu instantiate these.
+template <typename T, bool TRSM>
+cudaError_t leaf_dispatch(const LeafArgs<T>& a, int64_t nleaves, int G, cudaStream_t s);
+extern template cudaError_t leaf_dispatch<float, true>(const LeafArgs<float>&, int64_t, int, cudaStream_t);
+extern template cudaError_t leaf_dispatch<float, false>(const LeafArgs<float>&, int64_t, int, cudaStream_t);
+extern template cudaError_t leaf_dispatch<double, true>(const LeafArgs<double>&, int64_t, int, cudaStream_t);
+extern template cudaError_t leaf_dispatch<double, false>(const LeafArgs<double>&, int64_t, int, cudaStream_t);
+
+template <typename T, bool TRSM>
+cudaError_t leaf_configure();
+extern template cudaError_t leaf_configure<float, true>();
+extern template cudaError_t leaf_configure<float, false>();
+extern template cudaError_t leaf_configure<double, true>();
+extern template cudaError_t leaf_configure<double, false>();
+
+cudaError_t tc_configure();
+
+cudaError_t leaf_configure_all() {
+    cudaError_t e;
+    if ((e = leaf_configure<float, true>()) != cudaSuccess) return e;
+    if ((e = leaf_configure<float, false>()) != cudaSuccess) return e;
+    if ((e = leaf_configure<double, true>()) != cudaSuccess) return e;
+    if ((e = leaf_configure<double, false>()) != cudaSuccess) return e;
+    return tc_configure();
+}
+
+template <typename T>
+cudaError_t launch_leaf(bool trsm, const Canon<T>& p, int64_t r0, int b,
+                        int64_t nleaves, T alpha, const Planes* planes,
+                        int num_sms, cudaStream_t s) {
+    if (b < 1 || b > kMaxLeaf || nleaves < 1 || nleaves > 65535) return cudaErrorInvalidValue;
+    if (p.nrhs <= 0) return cudaSuccess;
+    LeafArgs<T> a;
+    a.p = p;
+    a.r0 = r0;
+    a.b = b;
+    a.alpha = alpha;
+    a.planes = planes != nullptr;
+    if (planes) a.pl = *planes;
+    // Lanes per right-hand side: enough threads in flight to fill the GPU
+    // (about 4 CTAs of 128 per SM), as few as possible otherwise.
+    const int64_t want = (int64_t)num_sms * 512;
+    const int64_t cols = p.nrhs * nleaves;
+    int G = 1;
+    if (cols < want) G = (cols * 4 >= want) ? 4 : 16;
+    const int bb = b <= 16 ? 16 : b <= 32 ? 32 : b <= 64 ? 64 : 128;
+    if (bb == 128 && G == 1) G = 4;   // registers (and FP64 shared memory)
+    return trsm ? leaf_dispatch<T, true>(a, nleaves, G, s) : leaf_dispatch<T, false>(a, nleaves, G, s);
+}
+
+template cudaError_t launch_leaf<float>(bool, const Canon<float>&, int64_t, int, int64_t, float,
+                                        const Planes*, int, cudaStream_t);
+template cudaError_t launch_leaf<double>(bool, const Canon<double>&, int64_t, int, int64_t, double,
+                                         const Planes*, int, cudaStream_t);
+
+}  // namespace trx

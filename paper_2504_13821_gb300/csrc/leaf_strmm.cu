@@ -1,0 +1,7 @@
+// Instantiation of the leaf kernels for float TRMM.
+#include "leaf_impl.cuh"
+
+namespace trx {
+template cudaError_t leaf_dispatch<float, false>(const LeafArgs<float>&, int64_t, int, cudaStream_t);
+template cudaError_t leaf_configure<float, false>();
+}  // namespace trx

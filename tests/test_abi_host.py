@@ -1,0 +1,98 @@
+"""The C ABI without a GPU: the library loads, exports every function
+include/trx.h declares, and checks its arguments (BLAS positions) before it
+touches a handle or the device."""
+import ctypes
+
+import pytest
+import torch
+
+from paper_2504_13821_gb300 import _binding, build
+
+ALL = ("trx_strsm", "trx_dtrsm", "trx_strmm", "trx_dtrmm")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return _binding.load_library()
+
+
+def test_exports_every_declared_function(lib):
+    names = _binding.header_functions()
+    assert len(names) >= 15
+    missing = [n for n in names if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def call(lib, name, side="L", uplo="L", trans="N", diag="N", m=4, n=3, A=1, lda=4, B=1, ldb=4,
+         handle=None):
+    return getattr(lib, name)(handle, side.encode(), uplo.encode(), trans.encode(),
+                              diag.encode(), m, n, 1.0, A, lda, B, ldb, None)
+
+
+@pytest.mark.parametrize("name", ALL)
+def test_argument_positions(lib, name):
+    assert call(lib, name, side="X") == -1
+    assert call(lib, name, uplo="X") == -2
+    assert call(lib, name, trans="X") == -3
+    assert call(lib, name, diag="X") == -4
+    assert call(lib, name, m=-1) == -5
+    assert call(lib, name, n=-1) == -6
+    assert call(lib, name, A=None) == -8
+    assert call(lib, name, lda=3) == -9
+    assert call(lib, name, side="R", lda=2) == -9
+    assert call(lib, name, side="R", lda=3) == 1          # valid args, no handle
+    assert call(lib, name, B=None) == -10
+    assert call(lib, name, ldb=3) == -11
+    # case-insensitive flags, 'C' accepted; then the missing handle is reported
+    assert call(lib, name, side="l", uplo="u", trans="c", diag="u") == 1
+    # empty problems skip the pointer checks but still need a handle
+    assert call(lib, name, m=0, A=None, B=None, lda=1, ldb=1) == 1
+
+
+def test_gemm_update_argument_positions(lib):
+    f = lib.trx_sgemm_update
+    ok = dict(M=4, N=3, K=64, A=1, lda=4, Y=1, ldy=64, C=1, ldc=4, engine=2)
+
+    def g(**kw):
+        a = dict(ok, **kw)
+        return f(None, a["M"], a["N"], a["K"], 1.0, 1.0, a["A"], a["lda"], a["Y"], a["ldy"],
+                 a["C"], a["ldc"], a["engine"], None)
+    assert g(M=-1) == -2 and g(N=-1) == -3 and g(K=-1) == -4
+    assert g(A=None) == -7 and g(lda=3) == -8 and g(Y=None) == -9 and g(ldy=63) == -10
+    assert g(C=None) == -11 and g(ldc=3) == -12 and g(engine=0) == -13
+    assert g() == 1
+
+
+def test_error_strings(lib):
+    assert lib.trx_error_string(0) == b"success"
+    assert b"uplo" in lib.trx_error_string(-2)
+    assert b"ldb" in lib.trx_error_string(-11)
+    for code in range(1, 8):
+        assert lib.trx_error_string(code) not in (b"", b"unknown error")
+    assert lib.trx_error_string(99) == b"unknown error"
+    assert lib.trx_version() >= 100
+
+
+def test_handle_calls_reject_null(lib):
+    assert lib.trx_set_option(None, 1, 64) == 1
+    assert lib.trx_destroy(None) == 0
+    assert lib.trx_check_device_error(None) == 1
+    out = ctypes.c_size_t()
+    assert lib.trx_workspace_size(None, b"S", b"L", 4, 4, 4, ctypes.byref(out)) == 1
+
+
+@pytest.mark.skipif(torch.cuda.is_available(), reason="host without a GPU only")
+def test_create_fails_cleanly_without_gpu(lib):
+    h = ctypes.c_void_p()
+    rc = lib.trx_create(ctypes.byref(h), 0, 0)
+    assert rc != 0 and not h.value
+
+
+def test_binding_rejects_bad_tensors():
+    import paper_2504_13821_gb300 as trx
+    A = torch.zeros(4, 4)
+    with pytest.raises((TypeError, ValueError)):
+        trx.trsm("L", "L", "N", "N", 1.0, A, torch.zeros(4, 3))   # CPU tensors
+    with pytest.raises(TypeError):
+        trx.trsm("L", "L", "N", "N", 1.0, A, torch.zeros(4, 3, dtype=torch.float64))

@@ -1,0 +1,147 @@
+"""CUDA path against the FP64 CPU oracle, element by element through the
+normwise criteria of the problem statement: TRSM backward error
+||op(A) X - alpha B|| / (||op(A)|| ||X||) <= 8 k u, TRMM
+||C - C_oracle|| / (|alpha| ||op(A)|| ||B||) <= 8 k u (u of the working
+precision, k the order of A, infinity norms). Inputs are the seeded
+generator of paper_2504_13821_gb300.inputs (unreferenced triangle and, for
+unit diagonals, the diagonal filled with NaN; ldb padding with a sentinel).
+"""
+import numpy as np
+import pytest
+
+from helpers import SENTINEL, bound, run_case, to_dev
+import oracle
+from paper_2504_13821_gb300 import inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+VARIANTS = inputs.VARIANTS
+SHAPES = [(1, 5), (17, 3), (64, 64), (129, 40), (300, 257)]
+
+
+@pytest.fixture(scope="module")
+def trx():
+    import paper_2504_13821_gb300 as trx
+    return trx
+
+
+@pytest.mark.parametrize("dtype", [np.float32, np.float64], ids=["f32", "f64"])
+@pytest.mark.parametrize("op", ["trsm", "trmm"])
+@pytest.mark.parametrize("side,uplo,trans,diag", VARIANTS)
+def test_all_variants(trx, op, side, uplo, trans, diag, dtype):
+    for i, (m, n) in enumerate(SHAPES):
+        run_case(op, side, uplo, trans, diag, m, n, 1.5, dtype,
+                 seed=inputs.variant_seed(m * 1000 + n, VARIANTS.index((side, uplo, trans, diag))))
+
+
+@pytest.mark.parametrize("op", ["trsm", "trmm"])
+@pytest.mark.parametrize("engine", [1, 2], ids=["cuda_cores", "tensor_cores"])
+@pytest.mark.parametrize("leaf", [16, 32, 64, 128])
+@pytest.mark.parametrize("variant", [("L", "L", "N", "N"), ("R", "U", "T", "U"),
+                                     ("L", "U", "N", "U"), ("R", "L", "N", "N")])
+def test_leaf_and_engine_sweep(trx, op, engine, leaf, variant):
+    h = trx.Handle(0)
+    h.set_option(trx.OPT_LEAF, leaf)
+    h.set_option(trx.OPT_GEMM, engine)
+    side = variant[0]
+    m, n = (1000, 300) if side == "L" else (300, 1000)
+    run_case(op, *variant, m, n, -2.0, np.float32, seed=leaf + engine, handle=h)
+    h.close()
+
+
+@pytest.mark.parametrize("op", ["trsm", "trmm"])
+@pytest.mark.parametrize("dtype", [np.float32, np.float64], ids=["f32", "f64"])
+def test_padded_leading_dimensions(trx, op, dtype):
+    for side, uplo, trans, diag in (("L", "U", "T", "N"), ("R", "L", "N", "U")):
+        run_case(op, side, uplo, trans, diag, 333, 270, 0.5, dtype, seed=3,
+                 lda_pad=13, ldb_pad=5)
+
+
+@pytest.mark.parametrize("op", ["trsm", "trmm"])
+def test_alpha_zero_reads_no_a(trx, op):
+    dev = torch.device("cuda", 0)
+    A = torch.full((300, 300), float("nan"), device=dev)
+    B = torch.randn(300, 40, device=dev).t().contiguous().t()
+    getattr(trx, op)("L", "L", "N", "N", 0.0, A, B)
+    torch.cuda.synchronize()
+    assert torch.count_nonzero(B).item() == 0
+
+
+def test_empty_problems(trx):
+    dev = torch.device("cuda", 0)
+    trx.trsm("L", "L", "N", "N", 1.0, torch.zeros(0, 0, device=dev), torch.zeros(0, 5, device=dev))
+    trx.trmm("R", "L", "N", "N", 1.0, torch.zeros(0, 0, device=dev), torch.zeros(4, 0, device=dev))
+
+
+def test_config1_exact(trx):
+    """1024 x 256 FP32 TRSM (L, L, N, N), alpha = 1, seed 0."""
+    eta, tol, _ = run_case("trsm", "L", "L", "N", "N", 1024, 256, 1.0, np.float32, seed=0)
+    assert eta <= tol
+
+
+@pytest.mark.parametrize("op", ["trsm", "trmm"])
+def test_deterministic_and_graph_equals_direct(trx, op):
+    outs = []
+    for graph in (1, 1, 0):
+        h = trx.Handle(0)
+        h.set_option(trx.OPT_GRAPH, graph)
+        _, _, X = run_case(op, "R", "U", "N", "N", 700, 900, 1.5, np.float32, seed=9, handle=h)
+        outs.append(X)
+        h.close()
+    assert np.array_equal(outs[0], outs[1]) and np.array_equal(outs[0], outs[2])
+
+
+def test_profile_counts_launches(trx):
+    h = trx.Handle(0)
+    h.set_option(trx.OPT_PROFILE, 1)
+    run_case("trsm", "L", "L", "N", "N", 1024, 512, 1.0, np.float32, seed=1, handle=h)
+    p = h.profile(reset=True)
+    assert p["gemm_tc"]["launches"] == 15 and p["leaf_trsm"]["launches"] == 16
+    assert p["gemm_tc"]["ms"] > 0 and p["gemm_tc"]["flops"] > 0
+    assert h.profile()["gemm_tc"]["launches"] == 0
+    h.close()
+
+
+def sampled_case(op, side, k, nrhs, cols, dtype, seed, handle=None):
+    """Full-size call, oracle on a sample of independent right-hand sides
+    (columns for side L, rows for side R)."""
+    import paper_2504_13821_gb300 as trx
+    m, n = (k, nrhs) if side == "L" else (nrhs, k)
+    A, B = inputs.problem(side, "L", m, n, seed=seed, dtype=dtype)
+    dev = torch.device("cuda", 0)
+    At, Bt = to_dev(A, dev), to_dev(B, dev)
+    getattr(trx, op)(side, "L", "N", "N", 1.5, At, Bt, handle=handle)
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(seed)
+    idx = np.sort(rng.choice(nrhs, size=min(cols, nrhs), replace=False))
+    idx_t = torch.from_numpy(idx).to(dev)
+    if side == "L":
+        X = np.asfortranarray(Bt.index_select(1, idx_t).cpu().numpy())
+        B0 = np.asfortranarray(B[:, idx])
+    else:
+        X = np.asfortranarray(Bt.index_select(0, idx_t).cpu().numpy())
+        B0 = np.asfortranarray(B[idx, :])
+    del Bt
+    if op == "trsm":
+        metric = oracle.trsm_backward_error(side, "L", "N", "N", 1.5, A, X, B0)["eta"]
+    else:
+        ref = oracle.trmm(side, "L", "N", "N", 1.5, A, B0)
+        metric = oracle.trmm_error(side, "L", "N", "N", 1.5, A, X, ref, B0)
+    assert metric <= bound(k, dtype), f"{op} k={k}: {metric:.3e}"
+    return metric
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("op", ["trsm", "trmm"])
+def test_large_sampled_4096(trx, op):
+    sampled_case(op, "L", 4096, 4096, 64, np.float32, seed=4096)
+    sampled_case(op, "R", 4096, 1024, 32, np.float64, seed=4097)
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("op", ["trsm", "trmm"])
+def test_bench_size_16384_sampled(trx, op):
+    """The benchmark's workload (m = n = 16384, FP32, L L N N, alpha 1.5,
+    default handle: tensor cores, cached graph), 32 sampled columns."""
+    sampled_case(op, "L", 16384, 16384, 32, np.float32, seed=16384)

@@ -1,0 +1,162 @@
+"""Host logic of the recursion planner (Section 3.1), no GPU needed.
+
+The library reports the launch sequence it would enqueue (trx_debug_plan).
+These tests check its structure (the diagonal leaf blocks and the GEMM
+update blocks tile the triangle exactly once; every update reads rows
+already final and writes rows not yet final; tensor-core updates have K a
+multiple of the K tile; alpha enters exactly once) and replay the sequence
+in FP64 numpy on a canonical lower triangle, which must reproduce the
+oracle's result.
+"""
+import numpy as np
+import pytest
+import scipy.linalg as sla
+
+import oracle
+from paper_2504_13821_gb300 import build, debug_plan, inputs
+
+SIZES = [1, 2, 17, 63, 64, 65, 128, 255, 256, 300, 1000, 1024]
+LEAVES = [16, 32, 64, 128]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    build.build()
+
+
+def leaves_of(steps):
+    out = []
+    for s in steps:
+        if s["kind"] == "leaf":
+            for t in range(s["nleaves"]):
+                out.append((s["r0"] + t * s["b"], s["b"]))
+    return out
+
+
+def coverage(k, steps):
+    """Count how often each (i, l), l <= i, is covered by a leaf diagonal
+    block or a GEMM block."""
+    cnt = np.zeros((k, k), dtype=np.int32)
+    for r, b in leaves_of(steps):
+        e = min(k, r + b)
+        blk = np.tril(np.ones((e - r, e - r), dtype=np.int32))
+        cnt[r:e, r:e] += blk
+    for s in steps:
+        if s["kind"] == "gemm":
+            cnt[s["rc"]:s["rc"] + s["mlen"], s["rk"]:s["rk"] + s["klen"]] += 1
+    return cnt
+
+
+@pytest.mark.parametrize("op", ["S", "M"])
+@pytest.mark.parametrize("gemm", [1, 2])
+@pytest.mark.parametrize("b", LEAVES)
+@pytest.mark.parametrize("k", SIZES + [4097])
+def test_blocks_tile_the_triangle_once(op, gemm, b, k):
+    steps = debug_plan(op, "L", "L", "N", "N", k, 5, 4, b, gemm)
+    cnt = coverage(k, steps)
+    low = np.tril(np.ones((k, k), dtype=bool))
+    assert np.all(cnt[low] == 1)
+    assert np.all(cnt[~low] == 0)
+    for s in steps:
+        if s["kind"] == "gemm":
+            assert s["rk"] + s["klen"] <= s["rc"]           # strictly below
+            if s["tc"]:
+                assert s["klen"] % 64 == 0 and s["rk"] % 8 == 0
+        if s["kind"] == "leaf":
+            assert s["b"] <= 128 and s["r0"] % min(b, max(k, 1)) == 0
+
+
+@pytest.mark.parametrize("b", LEAVES)
+@pytest.mark.parametrize("k", SIZES)
+def test_trsm_dependency_order_and_alpha(b, k):
+    steps = debug_plan("S", "L", "L", "N", "N", k, 5, 4, b, 2)
+    solved = np.zeros(k, dtype=bool)
+    touched = np.zeros(k, dtype=bool)   # has alpha been applied to the row
+    for s in steps:
+        if s["kind"] == "leaf":
+            r, e = s["r0"], min(k, s["r0"] + s["b"])
+            assert not solved[r:e].any()
+            # alpha is applied by the leaf iff no update has touched the rows
+            assert (s["alpha"] == 2.0) == (not touched[r:e].any())
+            assert touched[r:e].all() or not touched[r:e].any()
+            solved[r:e] = touched[r:e] = True
+        elif s["kind"] == "gemm":
+            rc, re_ = s["rc"], s["rc"] + s["mlen"]
+            assert solved[s["rk"]:s["rk"] + s["klen"]].all()       # reads final X
+            assert not solved[rc:re_].any()                          # writes pending rows
+            assert (s["beta"] == 2.0) == (not touched[rc:re_].any())
+            assert touched[rc:re_].all() or not touched[rc:re_].any()
+            touched[rc:re_] = True
+    assert solved.all()
+
+
+def replay(op, steps, M, C, alpha_seen=2.0):
+    """Execute a plan in FP64 on the canonical lower matrix M (k x k)."""
+    C = C.copy()
+    k = M.shape[0]
+    Y = C.copy()                     # tensor-core Y planes
+    for s in steps:
+        if s["kind"] == "conv_y":
+            Y = C.copy()
+        elif s["kind"] == "leaf":
+            for t in range(s["nleaves"]):
+                r = s["r0"] + t * s["b"]
+                e = min(k, r + s["b"])
+                if r >= k:
+                    continue
+                L = np.tril(M[r:e, r:e])
+                if s["trsm"]:
+                    C[r:e] = sla.solve_triangular(L, s["alpha"] * C[r:e], lower=True)
+                    Y[r:e] = C[r:e]
+                else:
+                    C[r:e] = s["alpha"] * (L @ C[r:e])
+        elif s["kind"] == "gemm":
+            src = Y if (s["tc"] and op == "M") else C
+            rc, rk = s["rc"], s["rk"]
+            C[rc:rc + s["mlen"]] = (s["beta"] * C[rc:rc + s["mlen"]] + s["gamma"] *
+                                    M[rc:rc + s["mlen"], rk:rk + s["klen"]] @ src[rk:rk + s["klen"]])
+    return C
+
+
+@pytest.mark.parametrize("op", ["S", "M"])
+@pytest.mark.parametrize("gemm", [1, 2])
+@pytest.mark.parametrize("b", LEAVES)
+@pytest.mark.parametrize("k", [1, 17, 65, 255, 300, 513])
+def test_replay_matches_oracle(op, gemm, b, k):
+    n = 7
+    A, B = inputs.problem("L", "L", k, n, seed=k + b, dtype=np.float64)
+    M = np.where(np.isnan(A), 0.0, A)
+    steps = debug_plan(op, "L", "L", "N", "N", k, n, 4, b, gemm)
+    got = replay(op, steps, M, B)
+    want = (oracle.trsm if op == "S" else oracle.trmm)("L", "L", "N", "N", 2.0, A, B)
+    np.testing.assert_allclose(got, want, rtol=1e-10, atol=1e-10 * np.abs(want).max())
+
+
+def test_trmm_level_batching():
+    # b a multiple of the K tile on the tensor-core path: one launch for all
+    # leaves, then one grouped launch per level with disjoint output rows.
+    steps = debug_plan("M", "L", "L", "N", "N", 16384, 16384, 4, 64, 0)
+    kinds = [s["kind"] for s in steps]
+    assert kinds[:3] == ["conv_m", "conv_y", "leaf"] and steps[2]["nleaves"] == 256
+    gemms = [s for s in steps if s["kind"] == "gemm"]
+    assert len(gemms) == 255
+    groups, cur = [], []
+    for s in gemms:
+        if s["member"] == 0 and cur:
+            groups.append(cur)
+            cur = []
+        cur.append(s)
+    groups.append(cur)
+    assert [len(g) for g in groups] == [2 ** d for d in range(8)]
+    for g in groups:
+        rows = np.zeros(16384, dtype=int)
+        for s in g:
+            rows[s["rc"]:s["rc"] + s["mlen"]] += 1
+        assert rows.max() == 1
+
+
+def test_fp64_and_small_orders_use_cuda_cores():
+    assert all(not s.get("tc", 0) for s in debug_plan("S", "L", "L", "N", "N", 4096, 8, 8, 0, 0))
+    assert all(s["kind"] not in ("conv_m", "conv_y")
+               for s in debug_plan("S", "L", "L", "N", "N", 200, 8, 4, 0, 0))
+    assert any(s.get("tc", 0) for s in debug_plan("S", "L", "L", "N", "N", 256, 8, 4, 0, 0))
