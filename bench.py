@@ -1,0 +1,352 @@
+"""Benchmark: recursive FP32 TRSM + TRMM at m = n = 16384 on one GB300.
+
+One step = TRSM (side L, lower, no transpose, non-unit, alpha = 1.5) followed
+by TRMM with the same factor and alpha = 1/1.5 on the same right-hand side,
+so B returns to itself (up to rounding) and the run can repeat without
+re-staging. Both calls walk the whole hot path: operand planes, leaf kernels,
+tensor-core GEMM updates. Metric: TFLOP/s with the m^2 n convention per call
+(2 * 16384^3 flop per step).
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+For N > 1 launch under torch.distributed.run; every rank runs its own copy
+of the workload (right-hand sides of TRSM/TRMM are independent, so the work
+shards with no exchange) and rank 0 prints one JSON line.
+
+--impl reference times the FP64 CPU oracle (plain substitution / triple
+loop, OpenMP) on a bounded sample of the same workload's right-hand sides.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "TRSM/TRMM TFLOP/s (m^2n, % of peak) at n=16384; served solves/s, p50/p99 ms"
+K_ORDER = 16384
+NRHS = 16384
+ALPHA = 1.5
+SEED = 16384
+CPU_SAMPLE_COLS = 32      # cpu_baseline sample (right-hand sides)
+REF_SAMPLE_COLS = 16      # per step of --impl reference
+
+
+def flops_per_call(k, nrhs):
+    return float(k) * k * nrhs
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0,
+                "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+# ---- clocks ---------------------------------------------------------------
+class ClockSampler:
+    """nvidia-smi sampling during the timed region (every 200 ms)."""
+    FIELDS = ("uuid,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid: str | None):
+        self.uuid = uuid
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, power, reasons = [], [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            if self.uuid and parts[0] != self.uuid:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+                power.append(float(parts[3]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        os.unlink(self.path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
+                "power_w_max": max(power), "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ---- distributed helpers ----------------------------------------------------
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def max_over_ranks(value: float, world: int) -> float:
+    """Max of a per-rank float over all ranks (identity for one rank)."""
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    dev = torch.device("cuda", torch.cuda.current_device()) \
+        if dist.get_backend() == "nccl" else torch.device("cpu")
+    t = torch.tensor([value], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world: int):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+# ---- CPU oracle timing --------------------------------------------------------
+def oracle_sample(A, B, cols):
+    """One TRSM + TRMM of the workload on `cols` right-hand sides (FP64
+    oracle). Returns (seconds, flops)."""
+    import oracle
+    Bs = np.asfortranarray(B[:, :cols])
+    t0 = time.perf_counter()
+    X = oracle.trsm("L", "L", "N", "N", ALPHA, A, Bs)
+    oracle.trmm("L", "L", "N", "N", 1.0 / ALPHA, A, X)
+    dt = time.perf_counter() - t0
+    return dt, 2.0 * flops_per_call(A.shape[0], cols)
+
+
+def host_inputs():
+    from paper_2504_13821_gb300 import inputs
+    return inputs.problem("L", "L", K_ORDER, NRHS, seed=SEED, dtype=np.float32)
+
+
+def run_reference(args):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    import oracle
+    oracle.build()
+    A, B = host_inputs()
+    for _ in range(args.warmup):
+        oracle_sample(A, B, REF_SAMPLE_COLS)
+    total, flops = 0.0, 0.0
+    for _ in range(args.steps):
+        dt, fl = oracle_sample(A, B, REF_SAMPLE_COLS)
+        total += dt
+        flops += fl
+    value = flops / total / 1e12
+    cores = oracle.nthreads()
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "TFLOP/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": workload_config(),
+        "cpu_baseline": {"value": value, "unit": "TFLOP/s", "cores": cores, "kind": "oracle",
+                         "sample": f"per step: TRSM + TRMM of the 16384x16384 factor on "
+                                   f"{REF_SAMPLE_COLS} of the 16384 right-hand sides"},
+        "e2e": {"value": value, "unit": "TFLOP/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def workload_config():
+    return {"workload": "FP32 TRSM(alpha=1.5) then TRMM(alpha=1/1.5), side L, lower, "
+                        "no transpose, non-unit, m=n=16384, column-major",
+            "m": K_ORDER, "n": NRHS, "leaf": 64,
+            "gemm": "tcgen05 kind::f16, 3-term split BF16, FP32 accumulation",
+            "graph": "cached CUDA graph per call",
+            "l2": "inputs larger than L2 (A 1 GiB, B 1 GiB); no flush"}
+
+
+# ---- GPU arm ----------------------------------------------------------------------
+def run_gpu(args):
+    import torch
+    world, rank, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", torch.cuda.current_device())
+    import paper_2504_13821_gb300 as trx
+    from paper_2504_13821_gb300 import _binding
+
+    A_np, B_np = host_inputs()
+    k, n = K_ORDER, NRHS
+    colmajor = trx.to_colmajor
+    A = colmajor(torch.from_numpy(A_np).to(dev))
+    B = colmajor(torch.from_numpy(B_np).to(dev))
+    h = trx.Handle(dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step(Bt):
+        trx.trsm("L", "L", "N", "N", ALPHA, A, Bt, handle=h, stream=stream)
+        trx.trmm("L", "L", "N", "N", 1.0 / ALPHA, A, Bt, handle=h, stream=stream)
+
+    for _ in range(max(args.warmup, 0)):
+        step(B)
+    torch.cuda.synchronize()
+    uuid = None
+    try:
+        uuid = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:
+        pass
+    clocks = ClockSampler(uuid)
+    barrier(world)
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.3)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        step(B)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    barrier(world)
+    ms_total = max_over_ranks(ev0.elapsed_time(ev1), world)
+    ms_step = ms_total / args.steps
+    flops_step = 2.0 * flops_per_call(k, n)
+    value = world * flops_step * args.steps / (ms_total * 1e-3) / 1e12
+
+    # Per-kernel durations: one instrumented step (direct launches with a
+    # CUDA event pair around every launch on the call's stream).
+    h.set_option(trx.OPT_PROFILE, 1)
+    h.profile(reset=True)
+    step(B)
+    prof = h.profile(reset=True)
+    h.set_option(trx.OPT_PROFILE, 0)
+    launches_step = sum(v["launches"] for v in prof.values())
+    g = prof["gemm_tc"]
+    peaks, src = load_peaks()
+    peak_tc = peaks["bf16_tflops_sustained"] / 3.0
+    achieved = g["flops"] / (g["ms"] * 1e-3) / 1e12 if g["ms"] > 0 else 0.0
+    kern_ms = sum(v["ms"] for v in prof.values())
+    roofline = {
+        "bound": "tensor", "kernel": "gemm_tc_kernel (GEMM update)",
+        "achieved": achieved, "peak": peak_tc, "unit": "TFLOP/s",
+        "frac": achieved / peak_tc if peak_tc else None, "traffic": None,
+        "peak_source": f"{src} bf16 sustained {peaks['bf16_tflops_sustained']} TFLOP/s / 3 "
+                       f"split-product terms",
+        "launches_per_step": g["launches"],
+        "share_of_kernel_time": g["ms"] / kern_ms if kern_ms else None,
+        "per_class_ms": {kk: round(v["ms"], 4) for kk, v in prof.items() if v["launches"]},
+        "whole_step_frac": (flops_step / (ms_step * 1e-3) / 1e12) / peak_tc,
+    }
+
+    # End to end through the public API: pinned host buffers, H2D of A and B,
+    # TRSM + TRMM, D2H of the result, every step.
+    e2e = None
+    if not args.no_e2e:
+        A_h = torch.from_numpy(A_np).pin_memory()
+        B_h = torch.from_numpy(B_np).pin_memory()
+        out_h = torch.empty_like(B_h).pin_memory()
+        Ad = torch.empty_like(A)
+        Bd = torch.empty_like(B)
+
+        def e2e_step():
+            Ad.copy_(A_h, non_blocking=True)
+            Bd.copy_(B_h, non_blocking=True)
+            trx.trsm("L", "L", "N", "N", ALPHA, Ad, Bd, handle=h, stream=stream)
+            trx.trmm("L", "L", "N", "N", 1.0 / ALPHA, Ad, Bd, handle=h, stream=stream)
+            out_h.copy_(Bd, non_blocking=True)
+
+        e2e_step()
+        torch.cuda.synchronize()
+        e_steps = max(1, min(args.steps, 5))
+        barrier(world)
+        t0 = time.perf_counter()
+        for _ in range(e_steps):
+            e2e_step()
+        torch.cuda.synchronize()
+        dt = max_over_ranks(time.perf_counter() - t0, world)
+        nbytes = A_h.numel() * 4
+        e2e = {"value": world * flops_step * e_steps / dt / 1e12, "unit": "TFLOP/s",
+               "h2d_bytes_per_step": 2 * nbytes, "d2h_bytes_per_step": nbytes,
+               "ms_per_step": 1e3 * dt / e_steps}
+        del Ad, Bd
+
+    # Correctness of the timed data: after the round trips B is back to the
+    # original up to rounding (TRMM undoes TRSM).
+    drift = float((B.cpu() - torch.from_numpy(B_np)).abs().max() /
+                  torch.from_numpy(B_np).abs().max())
+
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        import oracle
+        oracle.build()
+        dt, fl = oracle_sample(A_np, B_np, CPU_SAMPLE_COLS)
+        cpu = {"value": fl / dt / 1e12, "unit": "TFLOP/s", "cores": oracle.nthreads(),
+               "kind": "oracle",
+               "sample": f"TRSM + TRMM of the 16384x16384 factor on {CPU_SAMPLE_COLS} of the "
+                         f"16384 right-hand sides ({dt:.1f} s)"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic", "config": workload_config(),
+            "clocks": clk, "gpu_launches": launches_step * args.steps,
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "round_trip_drift": drift,
+        }
+        print(json.dumps(line), flush=True)
+    h.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="trx", choices=["trx", "reference"])
+    ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
+    args = ap.parse_args(argv)
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -61,7 +61,7 @@ def test_padded_leading_dimensions(trx, op, dtype):
 @pytest.mark.parametrize("op", ["trsm", "trmm"])
 def test_alpha_zero_reads_no_a(trx, op):
     dev = torch.device("cuda", 0)
-    A = torch.full((300, 300), float("nan"), device=dev)
+    A = trx.to_colmajor(torch.full((300, 300), float("nan"), device=dev))
     B = torch.randn(300, 40, device=dev).t().contiguous().t()
     getattr(trx, op)("L", "L", "N", "N", 0.0, A, B)
     torch.cuda.synchronize()
