@@ -312,6 +312,31 @@ __global__ void __launch_bounds__(NTHREADS, 1) gemm_tc_kernel(const __grid_const
         for (int t = blockIdx.x; t < p.total_tiles; t += gridDim.x) {
             const Tile ti = map_tile(p, t);
             const TcGemm& G = p.g[ti.g];
+            const int64_t row = (int64_t)ti.m * BM + q * 32 + lane;
+            const bool row_ok = row < G.mlen;
+            const float* crow = p.C + (G.rc + row) * p.c_rs;
+            float* wrow = p.C + (G.rc + row) * p.c_rs;
+            const int64_t jbase = (int64_t)ti.n * BN;
+            // C is read ahead of use, two 32-column chunks deep, the first
+            // two before the accumulator is even ready: the loads of a chunk
+            // are all in flight together instead of one load-store pair at a
+            // time (a store to C could alias any later load as far as the
+            // compiler knows).
+            auto load_chunk = [&](int ch, float (&dst)[32]) {
+                const int64_t j0 = jbase + ch * 32;
+                const float* src = crow + j0 * p.c_cs;
+                if (row_ok && j0 + 32 <= p.nrhs) {
+#pragma unroll
+                    for (int c = 0; c < 32; ++c) dst[c] = __ldcg(src + c * p.c_cs);
+                } else {
+#pragma unroll
+                    for (int c = 0; c < 32; ++c)
+                        dst[c] = (row_ok && j0 + c < p.nrhs) ? __ldcg(src + c * p.c_cs) : 0.f;
+                }
+            };
+            float c0[32], c1[32];
+            load_chunk(0, c0);
+            load_chunk(1, c1);
             // One lane waits and the warp follows its verdict, so the
             // warp-collective TMEM loads below never run on a partial warp.
             int ok = 1;
@@ -319,12 +344,10 @@ __global__ void __launch_bounds__(NTHREADS, 1) gemm_tc_kernel(const __grid_const
             ok = __shfl_sync(0xffffffffu, ok, 0);
             if (!ok) break;
             tc_fence_after();
-            const int64_t row = (int64_t)ti.m * BM + q * 32 + lane;
-            const bool row_ok = row < G.mlen;
-            float* crow = p.C + (G.rc + row) * p.c_rs;
-            const int64_t jbase = (int64_t)ti.n * BN;
 #pragma unroll 1
             for (int ch = 0; ch < BN / 32; ++ch) {
+                float c2[32];
+                if (ch + 2 < BN / 32) load_chunk(ch + 2, c2);
                 float v[32];
                 tmem_ld32(tmem + (uint32_t)(acc * BN + ch * 32) + ((uint32_t)(q * 32) << 16), v);
                 if (ch == BN / 32 - 1) {
@@ -332,16 +355,20 @@ __global__ void __launch_bounds__(NTHREADS, 1) gemm_tc_kernel(const __grid_const
                     __syncwarp();
                     if (lane == 0) mbar_arrive(smem_u32(&sm->acc_empty[acc]));
                 }
-                if (row_ok) {
-                    const int64_t j0 = jbase + ch * 32;
+                const int64_t j0 = jbase + ch * 32;
+                float* dst = wrow + j0 * p.c_cs;
+                if (row_ok && j0 + 32 <= p.nrhs) {
 #pragma unroll
-                    for (int c = 0; c < 32; ++c) {
-                        const int64_t j = j0 + c;
-                        if (j < p.nrhs) {
-                            float* cp = crow + j * p.c_cs;
-                            *cp = fmaf(p.beta, *cp, p.gamma * v[c]);
-                        }
-                    }
+                    for (int c = 0; c < 32; ++c) dst[c * p.c_cs] = fmaf(p.beta, c0[c], p.gamma * v[c]);
+                } else if (row_ok) {
+#pragma unroll
+                    for (int c = 0; c < 32; ++c)
+                        if (j0 + c < p.nrhs) dst[c * p.c_cs] = fmaf(p.beta, c0[c], p.gamma * v[c]);
+                }
+#pragma unroll
+                for (int c = 0; c < 32; ++c) {
+                    c0[c] = c1[c];
+                    c1[c] = c2[c];
                 }
             }
             if (++acc == 2) { acc = 0; acc_phase ^= 1u; }

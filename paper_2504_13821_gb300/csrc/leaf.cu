@@ -45,8 +45,9 @@ cudaError_t launch_leaf(bool trsm, const Canon<T>& p, int64_t r0, int b,
     a.planes = planes != nullptr;
     if (planes) a.pl = *planes;
     // Lanes per right-hand side: enough threads in flight to fill the GPU
-    // (about 4 CTAs of 128 per SM), as few as possible otherwise.
-    const int64_t want = (int64_t)num_sms * 512;
+    // (about 2 CTAs of 128 per SM), as few as possible otherwise (each extra
+    // lane adds a shuffle per step).
+    const int64_t want = (int64_t)num_sms * 256;
     const int64_t cols = p.nrhs * nleaves;
     int G = 1;
     if (cols < want) G = (cols * 4 >= want) ? 4 : 16;

@@ -75,7 +75,10 @@ leaf_kernel(LeafArgs<T> a) {
     const int64_t j0 = (int64_t)blockIdx.x * S::NCOL;
 
     // Diagonal block of M: strictly-lower part and diagonal.
+    // Every staging loop is unrolled (compile-time trip counts) so all of
+    // its global loads are in flight together.
     const bool a_row_fast = (p.a_rs == 1 || p.a_rs == -1);
+#pragma unroll
     for (int idx = tid; idx < B * B; idx += S::NT) {
         int i, l;
         if (a_row_fast) { i = idx % B; l = idx / B; } else { l = idx % B; i = idx / B; }
@@ -91,6 +94,7 @@ leaf_kernel(LeafArgs<T> a) {
     }
     // Right-hand-side panel.
     const bool c_row_fast = (p.c_rs == 1 || p.c_rs == -1);
+#pragma unroll
     for (int idx = tid; idx < B * S::NCOL; idx += S::NT) {
         int i, c;
         if (c_row_fast) { i = idx % B; c = idx / B; } else { c = idx % S::NCOL; i = idx / S::NCOL; }
@@ -146,6 +150,7 @@ leaf_kernel(LeafArgs<T> a) {
 #pragma unroll
     for (int q = 0; q < S::RPL; ++q) sC[c * S::LDS + q * G + g] = r[q];
     __syncthreads();
+#pragma unroll
     for (int idx = tid; idx < B * S::NCOL; idx += S::NT) {
         int i, cc;
         if (c_row_fast) { i = idx % B; cc = idx / B; } else { cc = idx % S::NCOL; i = idx / S::NCOL; }
@@ -155,6 +160,7 @@ leaf_kernel(LeafArgs<T> a) {
     if constexpr (std::is_same<T, float>::value) {
         if (TRSM && a.planes) {
             // Y planes, element (l, j) at j*ldy + l: rows fastest.
+#pragma unroll
             for (int idx = tid; idx < B * S::NCOL; idx += S::NT) {
                 const int i = idx % B, cc = idx / B;
                 const int64_t j = j0 + cc;
