@@ -185,10 +185,13 @@ def run_reference(args):
     return 0
 
 
+LEAF_USED = 64
+
+
 def workload_config():
     return {"workload": "FP32 TRSM(alpha=1.5) then TRMM(alpha=1/1.5), side L, lower, "
                         "no transpose, non-unit, m=n=16384, column-major",
-            "m": K_ORDER, "n": NRHS, "leaf": 64,
+            "m": K_ORDER, "n": NRHS, "leaf": LEAF_USED,
             "gemm": "tcgen05 kind::f16, 3-term split BF16, FP32 accumulation",
             "graph": "cached CUDA graph per call",
             "l2": "inputs larger than L2 (A 1 GiB, B 1 GiB); no flush"}
@@ -212,6 +215,10 @@ def run_gpu(args):
     A = colmajor(torch.from_numpy(A_np).to(dev))
     B = colmajor(torch.from_numpy(B_np).to(dev))
     h = trx.Handle(dev)
+    if args.leaf:
+        h.set_option(trx.OPT_LEAF, args.leaf)
+        global LEAF_USED
+        LEAF_USED = args.leaf
     stream = torch.cuda.current_stream(dev)
 
     def step(Bt):
@@ -342,6 +349,7 @@ def main(argv=None):
     ap.add_argument("--impl", default="trx", choices=["trx", "reference"])
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
+    ap.add_argument("--leaf", type=int, default=0, help="recursion cutoff b (0: library default)")
     args = ap.parse_args(argv)
     if args.impl == "reference":
         return run_reference(args)

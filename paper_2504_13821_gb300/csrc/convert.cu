@@ -21,32 +21,72 @@ __device__ __forceinline__ void split_bf16(float x, __nv_bfloat16& hi, __nv_bflo
     lo = __float2bfloat16_rn(x - __bfloat162float(hi));
 }
 
+// M planes: 64x64 tiles of the lower triangle (tiles above it exit at once),
+// read along A's contiguous index, written as BF16 pairs along l.
 __global__ void __launch_bounds__(256) convert_m_kernel(Canon<float> p, Planes pl) {
-    __shared__ float tile[32][33];
+    __shared__ float tile[64][65];
     const int64_t ti = blockIdx.y, tl = blockIdx.x;
-    if (tl > ti) return;                        // entirely above the diagonal
-    const int64_t i0 = ti * 32, l0 = tl * 32;
+    if (tl > ti) return;
+    const int64_t i0 = ti * 64, l0 = tl * 64;
+    const int tid = threadIdx.x;
     const bool row_fast = (p.a_rs == 1 || p.a_rs == -1);
-    for (int r = threadIdx.y; r < 32; r += 8) {
-        const int x = threadIdx.x;
-        const int ii = row_fast ? x : r, ll = row_fast ? r : x;
+#pragma unroll
+    for (int u = 0; u < 16; ++u) {
+        const int e = tid + 256 * u;
+        const int ii = row_fast ? (e & 63) : (e >> 6), ll = row_fast ? (e >> 6) : (e & 63);
         const int64_t i = i0 + ii, l = l0 + ll;
-        float v = 0.f;
-        if (i < p.k && l < i) v = p.A[i * p.a_rs + l * p.a_cs];
-        tile[ii][ll] = v;
+        tile[ii][ll] = (i < p.k && l < i) ? p.A[i * p.a_rs + l * p.a_cs] : 0.f;
     }
     __syncthreads();
-    for (int r = threadIdx.y; r < 32; r += 8) {
-        const int64_t i = i0 + r, l = l0 + threadIdx.x;
-        if (i < p.k && l < p.k) {
-            __nv_bfloat16 hi, lo;
-            split_bf16(tile[r][threadIdx.x], hi, lo);
-            pl.m_hi[i * pl.ldm + l] = hi;
-            pl.m_lo[i * pl.ldm + l] = lo;
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+        const int e = tid + 256 * u;
+        const int ii = e >> 5, lp = (e & 31) * 2;
+        const int64_t i = i0 + ii, l = l0 + lp;
+        if (i >= p.k || l >= p.k) continue;
+        __nv_bfloat16 h0, o0, h1, o1;
+        split_bf16(tile[ii][lp], h0, o0);
+        const int64_t off = i * pl.ldm + l;
+        if (l + 1 < p.k) {
+            split_bf16(tile[ii][lp + 1], h1, o1);
+            *reinterpret_cast<__nv_bfloat162*>(pl.m_hi + off) = __halves2bfloat162(h0, h1);
+            *reinterpret_cast<__nv_bfloat162*>(pl.m_lo + off) = __halves2bfloat162(o0, o1);
+        } else {
+            pl.m_hi[off] = h0;
+            pl.m_lo[off] = o0;
         }
     }
 }
 
+// Y planes when C's rows are contiguous (side L): no transpose, four
+// consecutive rows per thread, 8-byte stores.
+__global__ void __launch_bounds__(256) convert_y_contig_kernel(Canon<float> p, Planes pl) {
+    const int64_t l = ((int64_t)blockIdx.x * 256 + threadIdx.x) * 4;
+    if (l >= p.k) return;
+    for (int64_t j = blockIdx.y; j < p.nrhs; j += gridDim.y) {
+        const float* src = p.C + j * p.c_cs;
+        float v[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) v[q] = (l + q < p.k) ? src[(l + q) * p.c_rs] : 0.f;
+        __nv_bfloat16 h[4], o[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) split_bf16(v[q], h[q], o[q]);
+        const int64_t off = j * pl.ldy + l;
+        if (l + 3 < p.k) {
+            __nv_bfloat162 hv[2] = {__halves2bfloat162(h[0], h[1]), __halves2bfloat162(h[2], h[3])};
+            __nv_bfloat162 ov[2] = {__halves2bfloat162(o[0], o[1]), __halves2bfloat162(o[2], o[3])};
+            *reinterpret_cast<uint2*>(pl.y_hi + off) = *reinterpret_cast<uint2*>(hv);
+            *reinterpret_cast<uint2*>(pl.y_lo + off) = *reinterpret_cast<uint2*>(ov);
+        } else {
+            for (int q = 0; l + q < p.k; ++q) {
+                pl.y_hi[off + q] = h[q];
+                pl.y_lo[off + q] = o[q];
+            }
+        }
+    }
+}
+
+// Y planes when C's columns are contiguous (side R): 32x32 transpose tiles.
 __global__ void __launch_bounds__(256) convert_y_kernel(Canon<float> p, Planes pl) {
     __shared__ float tile[32][33];              // tile[jj][ll]
     const int64_t l0 = (int64_t)blockIdx.x * 32, j0 = (int64_t)blockIdx.y * 32;
@@ -113,14 +153,20 @@ __global__ void zero_kernel(T* B, int64_t m, int64_t n, int64_t ldb) {
 
 cudaError_t launch_convert_m(const Canon<float>& p, const Planes& pl, cudaStream_t s) {
     if (p.k <= 1) return cudaSuccess;
-    const int64_t t = (p.k + 31) / 32;
+    const int64_t t = (p.k + 63) / 64;
     if (t > 65535) return cudaErrorInvalidValue;
-    convert_m_kernel<<<dim3((unsigned)t, (unsigned)t), dim3(32, 8), 0, s>>>(p, pl);
+    convert_m_kernel<<<dim3((unsigned)t, (unsigned)t), 256, 0, s>>>(p, pl);
     return cudaGetLastError();
 }
 
 cudaError_t launch_convert_y(const Canon<float>& p, const Planes& pl, cudaStream_t s) {
     if (p.k <= 0 || p.nrhs <= 0) return cudaSuccess;
+    if (p.c_rs == 1 || p.c_rs == -1) {
+        const int64_t gx = (p.k + 1023) / 1024;
+        const int64_t gy = p.nrhs < 65535 ? p.nrhs : 65535;
+        convert_y_contig_kernel<<<dim3((unsigned)gx, (unsigned)gy), 256, 0, s>>>(p, pl);
+        return cudaGetLastError();
+    }
     const int64_t tl = (p.k + 31) / 32, tj = (p.nrhs + 31) / 32;
     if (tj > 65535) return cudaErrorInvalidValue;
     convert_y_kernel<<<dim3((unsigned)tl, (unsigned)tj), dim3(32, 8), 0, s>>>(p, pl);

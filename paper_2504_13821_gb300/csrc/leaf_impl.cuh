@@ -31,9 +31,6 @@
 #include "common.cuh"
 
 namespace trx {
-namespace {
-
-}  // namespace
 
 template <typename T>
 struct LeafArgs {
@@ -55,6 +52,7 @@ struct LeafShape {
     static constexpr int LDS = B + PAD;
     static constexpr int RPL = B / G;               // rows per lane
     static constexpr size_t smem = sizeof(T) * (size_t)(B * B + B + NCOL * LDS);
+    static_assert((B * B) % NT == 0 && (B * NCOL) % NT == 0, "staging loops assume whole passes");
 };
 
 template <typename T, int B, int G, bool TRSM>
@@ -79,7 +77,8 @@ leaf_kernel(LeafArgs<T> a) {
     // its global loads are in flight together.
     const bool a_row_fast = (p.a_rs == 1 || p.a_rs == -1);
 #pragma unroll
-    for (int idx = tid; idx < B * B; idx += S::NT) {
+    for (int u = 0; u < B * B / S::NT; ++u) {
+        const int idx = tid + u * S::NT;
         int i, l;
         if (a_row_fast) { i = idx % B; l = idx / B; } else { l = idx % B; i = idx / B; }
         T v = T(0);
@@ -95,7 +94,8 @@ leaf_kernel(LeafArgs<T> a) {
     // Right-hand-side panel.
     const bool c_row_fast = (p.c_rs == 1 || p.c_rs == -1);
 #pragma unroll
-    for (int idx = tid; idx < B * S::NCOL; idx += S::NT) {
+    for (int u = 0; u < B * S::NCOL / S::NT; ++u) {
+        const int idx = tid + u * S::NT;
         int i, c;
         if (c_row_fast) { i = idx % B; c = idx / B; } else { c = idx % S::NCOL; i = idx / S::NCOL; }
         const int64_t j = j0 + c;
@@ -151,7 +151,8 @@ leaf_kernel(LeafArgs<T> a) {
     for (int q = 0; q < S::RPL; ++q) sC[c * S::LDS + q * G + g] = r[q];
     __syncthreads();
 #pragma unroll
-    for (int idx = tid; idx < B * S::NCOL; idx += S::NT) {
+    for (int u = 0; u < B * S::NCOL / S::NT; ++u) {
+        const int idx = tid + u * S::NT;
         int i, cc;
         if (c_row_fast) { i = idx % B; cc = idx / B; } else { cc = idx % S::NCOL; i = idx / S::NCOL; }
         const int64_t j = j0 + cc;
@@ -161,7 +162,8 @@ leaf_kernel(LeafArgs<T> a) {
         if (TRSM && a.planes) {
             // Y planes, element (l, j) at j*ldy + l: rows fastest.
 #pragma unroll
-            for (int idx = tid; idx < B * S::NCOL; idx += S::NT) {
+            for (int u = 0; u < B * S::NCOL / S::NT; ++u) {
+                const int idx = tid + u * S::NT;
                 const int i = idx % B, cc = idx / B;
                 const int64_t j = j0 + cc;
                 if (i < bs && j < p.nrhs) {
