@@ -190,6 +190,36 @@ int trx_debug_plan(char op, char side, char uplo, char transa, char diag,
                    int64_t m, int64_t n, int elem_bytes, int leaf,
                    int gemm_mode, char* buf, size_t buflen);
 
+/* Size of the static device scratch behind trx_strsm_noalloc (64 MiB). */
+#define TRX_NOALLOC_SCRATCH_BYTES ((size_t)64 << 20)
+
+/* FP32 TRSM (same arguments and result as trx_strsm with a default handle)
+ * for callers that cannot allocate device memory where they solve: a solve
+ * issued while the stream is being captured into a CUDA graph (cudaMalloc
+ * cannot be captured), code inside a framework that hands out device memory
+ * only from its own pool, or a latency-bound loop that must not pay
+ * cudaMalloc's implicit synchronisation or risk its out-of-memory failure.
+ * The paper has no counterpart; it is a packaging of the same kernels.
+ *
+ * No handle: it runs on the calling thread's current device, launches
+ * directly onto `stream` and calls no cudaMalloc/cudaFree. The tensor-core
+ * path's scratch is one file-scope __device__ array of
+ * TRX_NOALLOC_SCRATCH_BYTES that every device using this library holds
+ * until the process exits; problems needing more (about 4*k*(k + nrhs)
+ * bytes, k the order of A, nrhs the other dimension of B, both rounded up to
+ * 64) return TRX_ERR_WORKSPACE before anything is enqueued.
+ * The first call on a device sets that device up (looks up the array's
+ * device address, sets kernel attributes): make that first call outside any
+ * stream capture. All calls share the one array, so calls whose work
+ * overlaps on the GPU (other streams, other host threads) race: serialise
+ * them on one stream. A device-side wait that runs out of time (see
+ * TRX_OPT_WAIT_LIMIT, fixed here at 2 s) leaves B invalid and is not
+ * reported by this entry point. Returns 0, -i for an illegal i-th argument
+ * (BLAS numbering as trx_strsm without the handle), or a TRX_ERR_* code. */
+int trx_strsm_noalloc(char side, char uplo, char transa, char diag, int64_t m,
+                      int64_t n, float alpha, const float* A, int64_t lda,
+                      float* B, int64_t ldb, void* stream);
+
 /* Library version as major*10000 + minor*100 + patch. */
 int trx_version(void);
 

@@ -33,6 +33,17 @@ constexpr size_t kGraphCacheSize = 16;
 
 thread_local char g_detail[256] = "";
 
+}  // namespace
+
+namespace trx {
+const char* set_detail(const char* msg) {
+    snprintf(g_detail, sizeof(g_detail), "%s", msg);
+    return g_detail;
+}
+}  // namespace trx
+
+namespace {
+
 int fail_cuda(cudaError_t e, const char* what) {
     snprintf(g_detail, sizeof(g_detail), "%s: %s", what, cudaGetErrorString(e));
     return TRX_ERR_CUDA;
@@ -482,6 +493,44 @@ int execute(trx_handle_t h, bool trsm, char side, char uplo, char transa, char d
     e = cudaGraphLaunch(exec, s);
     return e == cudaSuccess ? TRX_SUCCESS : fail_cuda(e, "cudaGraphLaunch");
 }
+
+}  // namespace
+
+namespace trx {
+
+// For trx_strsm_noalloc (noalloc.cu): BLAS argument check, the scratch a
+// call needs on the tensor-core path, and the call itself with a caller-
+// supplied scratch and error word, on a handle that lives on the stack
+// (no device allocation, no graph: launches go straight onto the stream).
+int noalloc_check_args(char side, char uplo, char transa, char diag, int64_t m, int64_t n,
+                       const void* A, int64_t lda, const void* B, int64_t ldb) {
+    return check_args(side, uplo, transa, diag, m, n, A, lda, B, ldb);
+}
+
+size_t noalloc_scratch_bytes(char side, int64_t m, int64_t n) {
+    const int64_t k = upc(side) == 'L' ? m : n, nrhs = upc(side) == 'L' ? n : m;
+    if (k <= 0 || nrhs <= 0) return 0;
+    const int b = (int)std::min<int64_t>(kDefaultLeaf, k);
+    return use_tc_mode(4, 0, k, b) ? ws_layout(k, nrhs).total : 0;
+}
+
+int noalloc_strsm(int device, int num_sms, void* scratch, size_t scratch_bytes, int* err_word,
+                  char side, char uplo, char transa, char diag, int64_t m, int64_t n, float alpha,
+                  const float* A, int64_t lda, float* B, int64_t ldb, void* stream) {
+    trx_handle_s hs;
+    hs.device = device;
+    hs.num_sms = num_sms;
+    hs.ws = scratch;
+    hs.ws_bytes = scratch_bytes;
+    hs.d_err = err_word;
+    hs.opt_graph = 0;
+    return execute<float>(&hs, true, side, uplo, transa, diag, m, n, alpha, A, lda, B, ldb,
+                          stream);
+}
+
+}  // namespace trx
+
+namespace {
 
 void free_owned_ws(trx_handle_t h) {
     if (h->ws_owned && h->ws) cudaFree(h->ws);
