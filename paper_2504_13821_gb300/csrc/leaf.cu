@@ -7,11 +7,12 @@ namespace trx {
 // One translation unit per (type, operation) keeps the unrolled sweeps'
 // compile time in parallel; leaf_*.cu instantiate these.
 template <typename T, bool TRSM>
-cudaError_t leaf_dispatch(const LeafArgs<T>& a, int64_t nleaves, int G, cudaStream_t s);
-extern template cudaError_t leaf_dispatch<float, true>(const LeafArgs<float>&, int64_t, int, cudaStream_t);
-extern template cudaError_t leaf_dispatch<float, false>(const LeafArgs<float>&, int64_t, int, cudaStream_t);
-extern template cudaError_t leaf_dispatch<double, true>(const LeafArgs<double>&, int64_t, int, cudaStream_t);
-extern template cudaError_t leaf_dispatch<double, false>(const LeafArgs<double>&, int64_t, int, cudaStream_t);
+cudaError_t leaf_dispatch(const LeafArgs<T>& a, int64_t nleaves, int G, int64_t max_ctas,
+                          cudaStream_t s);
+extern template cudaError_t leaf_dispatch<float, true>(const LeafArgs<float>&, int64_t, int, int64_t, cudaStream_t);
+extern template cudaError_t leaf_dispatch<float, false>(const LeafArgs<float>&, int64_t, int, int64_t, cudaStream_t);
+extern template cudaError_t leaf_dispatch<double, true>(const LeafArgs<double>&, int64_t, int, int64_t, cudaStream_t);
+extern template cudaError_t leaf_dispatch<double, false>(const LeafArgs<double>&, int64_t, int, int64_t, cudaStream_t);
 
 template <typename T, bool TRSM>
 cudaError_t leaf_configure();
@@ -44,16 +45,17 @@ cudaError_t launch_leaf(bool trsm, const Canon<T>& p, int64_t r0, int b,
     a.alpha = alpha;
     a.planes = planes != nullptr;
     if (planes) a.pl = *planes;
-    // Lanes per right-hand side: enough threads in flight to fill the GPU
-    // (about 2 CTAs of 128 per SM), as few as possible otherwise (each extra
-    // lane adds a shuffle per step).
-    const int64_t want = (int64_t)num_sms * 256;
-    const int64_t cols = p.nrhs * nleaves;
-    int G = 1;
-    if (cols < want) G = (cols * 4 >= want) ? 4 : 16;
-    const int bb = b <= 16 ? 16 : b <= 32 ? 32 : b <= 64 ? 64 : 128;
-    if (bb == 128 && G == 1) G = 4;   // registers (and FP64 shared memory)
-    return trsm ? leaf_dispatch<T, true>(a, nleaves, G, s) : leaf_dispatch<T, false>(a, nleaves, G, s);
+    // Lanes per right-hand side, from the right-hand sides per SM: one lane
+    // per column when there are many (no shuffles, widest vector reuse),
+    // more lanes when there are few, to keep enough warps in flight.
+    const int64_t cols_per_sm = p.nrhs * nleaves / (num_sms > 0 ? num_sms : 1);
+    int G = 16;
+    if (cols_per_sm >= 2048) G = 1;
+    else if (cols_per_sm >= 512) G = 4;
+    else if (cols_per_sm >= 64) G = 8;
+    const int64_t max_ctas = (int64_t)(num_sms > 0 ? num_sms : 1) * 4;
+    return trsm ? leaf_dispatch<T, true>(a, nleaves, G, max_ctas, s)
+                : leaf_dispatch<T, false>(a, nleaves, G, max_ctas, s);
 }
 
 template cudaError_t launch_leaf<float>(bool, const Canon<float>&, int64_t, int, int64_t, float,

@@ -2,6 +2,6 @@
 #include "leaf_impl.cuh"
 
 namespace trx {
-template cudaError_t leaf_dispatch<double, true>(const LeafArgs<double>&, int64_t, int, cudaStream_t);
+template cudaError_t leaf_dispatch<double, true>(const LeafArgs<double>&, int64_t, int, int64_t, cudaStream_t);
 template cudaError_t leaf_configure<double, true>();
 }  // namespace trx

@@ -2,6 +2,6 @@
 #include "leaf_impl.cuh"
 
 namespace trx {
-template cudaError_t leaf_dispatch<float, true>(const LeafArgs<float>&, int64_t, int, cudaStream_t);
+template cudaError_t leaf_dispatch<float, true>(const LeafArgs<float>&, int64_t, int, int64_t, cudaStream_t);
 template cudaError_t leaf_configure<float, true>();
 }  // namespace trx
