@@ -14,15 +14,17 @@
 // recursion node for TRSM, one whole recursion level for TRMM); the tiles of
 // all of them form one persistent tile sequence.
 //
-// Structure (one CTA per SM, 192 threads, warp-specialised):
+// Structure (one CTA per SM, 192 threads, warp-specialised), for an output
+// tile of 128 rows x BN right-hand sides (BN = 256, or 128 / 64 when the
+// group has too few tiles to cover the SMs):
 //   warp 0     TMA producer: 4 tiles per K step (A hi/lo 128x32, Y hi/lo
-//              256x32, 64-byte swizzle) into a 4-stage shared-memory ring
+//              BNx32, 64-byte swizzle) into a 4-stage shared-memory ring
 //   warp 1     TMEM allocator and MMA issuer: per K step 2 x 3
-//              tcgen05.mma (M=128, N=256, K=16, BF16 in, FP32 accumulate),
+//              tcgen05.mma (M=128, N=BN, K=16, BF16 in, FP32 accumulate),
 //              tcgen05.commit frees the ring slot
 //   warps 2-5  epilogue: tcgen05.ld of the accumulator (warp w reads TMEM
 //              lanes 32*(w%4) ..), read-modify-write of C in global memory
-// Two 256-column accumulators (all 512 TMEM columns) let the epilogue of one
+// Two BN-column accumulators (2*BN TMEM columns) let the epilogue of one
 // tile overlap the main loop of the next.
 //
 // Every wait on an mbarrier is bounded by a wall-clock budget: past it the
@@ -37,24 +39,32 @@
 namespace trx {
 namespace tc {
 
-constexpr int BM = 128, BN = 256, BK = 32;          // BK in BF16 elements (64 B)
+constexpr int BM = 128, BK = 32;                    // BK in BF16 elements (64 B)
 constexpr int STAGES = 4;
 constexpr int A_TILE = BM * BK * 2;                 // 8 KiB
-constexpr int B_TILE = BN * BK * 2;                 // 16 KiB
-constexpr int STAGE_BYTES = 2 * A_TILE + 2 * B_TILE; // 48 KiB
 constexpr int MAXG = 256;
 constexpr int NTHREADS = 192;
-constexpr int TMEM_COLS = 512;
-constexpr int SMEM_BYTES = 1024 + STAGES * STAGE_BYTES + 256;
 constexpr int kTimeout = 4;                          // TRX_ERR_TIMEOUT
 
-// kind::f16 instruction descriptor: FP32 accumulator, BF16 A and B, both
-// K-major, N = 256, M = 128.
-constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) |
-                           ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+// Per N tile (256, 128 or 64 columns of the right-hand side): ring-stage
+// size, tensor memory (two accumulators of BN FP32 columns) and the
+// kind::f16 instruction descriptor (FP32 accumulator, BF16 A and B, both
+// K-major, M = 128, N = BN).
+template <int BN>
+struct Cfg {
+    static constexpr int B_TILE = BN * BK * 2;
+    static constexpr int STAGE_BYTES = 2 * A_TILE + 2 * B_TILE;
+    static constexpr int TMEM_COLS = 2 * BN;
+    static constexpr int SMEM_BYTES = 1024 + STAGES * STAGE_BYTES + 256;
+    static constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) |
+                                      ((uint32_t)(BN >> 3) << 17) |
+                                      ((uint32_t)(BM >> 4) << 24);
+    static constexpr int MAP = BN == 256 ? 0 : BN == 128 ? 1 : 2;
+};
 
 struct Maps {
-    CUtensorMap a_hi, a_lo, b_hi, b_lo;
+    CUtensorMap a_hi, a_lo;
+    CUtensorMap b_hi[3], b_lo[3];   // boxes of 256, 128, 64 rows
 };
 
 struct Params {
@@ -114,12 +124,13 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
     return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)1 << 16) |
            ((uint64_t)(512 >> 4) << 32) | ((uint64_t)1 << 46) | ((uint64_t)4 << 61);
 }
-__device__ __forceinline__ void umma(uint32_t d, uint64_t a, uint64_t b, uint32_t accum) {
+__device__ __forceinline__ void umma(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc,
+                                     uint32_t accum) {
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
         "setp.ne.b32 p, %4, 0;\n\t"
         "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d),
-        "l"(a), "l"(b), "r"(IDESC), "r"(accum));
+        "l"(a), "l"(b), "r"(idesc), "r"(accum));
 }
 __device__ __forceinline__ void umma_commit(uint32_t bar) {
     asm volatile(
@@ -205,7 +216,12 @@ __device__ __forceinline__ Tile map_tile(const Params& p, int t) {
     return r;
 }
 
+template <int BN>
 __global__ void __launch_bounds__(NTHREADS, 1) gemm_tc_kernel(const __grid_constant__ Params p) {
+    using C = Cfg<BN>;
+    constexpr int STAGE_BYTES = C::STAGE_BYTES;
+    constexpr int B_TILE = C::B_TILE;
+    constexpr int TMEM_COLS = C::TMEM_COLS;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     // Stage buffers must sit on a 1024-byte boundary (swizzle atom repeat).
     const uint32_t raw = smem_u32(smem_raw);
@@ -258,8 +274,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) gemm_tc_kernel(const __grid_const
                 const uint32_t base = ring + stage * STAGE_BYTES;
                 tma_load_2d(base, &p.maps.a_hi, fb, x, ya);
                 tma_load_2d(base + A_TILE, &p.maps.a_lo, fb, x, ya);
-                tma_load_2d(base + 2 * A_TILE, &p.maps.b_hi, fb, x, yb);
-                tma_load_2d(base + 2 * A_TILE + B_TILE, &p.maps.b_lo, fb, x, yb);
+                tma_load_2d(base + 2 * A_TILE, &p.maps.b_hi[C::MAP], fb, x, yb);
+                tma_load_2d(base + 2 * A_TILE + B_TILE, &p.maps.b_lo[C::MAP], fb, x, yb);
                 ++issued;
                 if (++stage == STAGES) { stage = 0; phase ^= 1u; }
             }
@@ -290,9 +306,9 @@ __global__ void __launch_bounds__(NTHREADS, 1) gemm_tc_kernel(const __grid_const
                     const uint64_t alo = sdesc(base + A_TILE + kk * 32);
                     const uint64_t bhi = sdesc(base + 2 * A_TILE + kk * 32);
                     const uint64_t blo = sdesc(base + 2 * A_TILE + B_TILE + kk * 32);
-                    umma(d, ahi, bhi, (kb | kk) != 0 ? 1u : 0u);
-                    umma(d, ahi, blo, 1u);
-                    umma(d, alo, bhi, 1u);
+                    umma(d, ahi, bhi, C::IDESC, (kb | kk) != 0 ? 1u : 0u);
+                    umma(d, ahi, blo, C::IDESC, 1u);
+                    umma(d, alo, bhi, C::IDESC, 1u);
                 }
                 umma_commit(smem_u32(&sm->empty[stage]));
                 if (++stage == STAGES) { stage = 0; phase ^= 1u; }
@@ -423,8 +439,17 @@ static bool encode(CUtensorMap* m, void* base, uint64_t inner, uint64_t outer, u
 int tc_maps_size() { return (int)sizeof(tc::Maps); }
 
 cudaError_t tc_configure() {
-    return cudaFuncSetAttribute(tc::gemm_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                tc::SMEM_BYTES);
+    cudaError_t e;
+    if ((e = cudaFuncSetAttribute(tc::gemm_tc_kernel<256>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  tc::Cfg<256>::SMEM_BYTES)) != cudaSuccess)
+        return e;
+    if ((e = cudaFuncSetAttribute(tc::gemm_tc_kernel<128>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  tc::Cfg<128>::SMEM_BYTES)) != cudaSuccess)
+        return e;
+    return cudaFuncSetAttribute(tc::gemm_tc_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                tc::Cfg<64>::SMEM_BYTES);
 }
 
 cudaError_t tc_make_maps(const Planes& pl, int64_t k, int64_t nrhs, void* out) {
@@ -432,8 +457,12 @@ cudaError_t tc_make_maps(const Planes& pl, int64_t k, int64_t nrhs, void* out) {
     if (k <= 0 || nrhs <= 0) return cudaErrorInvalidValue;
     if (!tc::encode(&m->a_hi, pl.m_hi, k, k, pl.ldm, tc::BM) ||
         !tc::encode(&m->a_lo, pl.m_lo, k, k, pl.ldm, tc::BM) ||
-        !tc::encode(&m->b_hi, pl.y_hi, k, nrhs, pl.ldy, tc::BN) ||
-        !tc::encode(&m->b_lo, pl.y_lo, k, nrhs, pl.ldy, tc::BN))
+        !tc::encode(&m->b_hi[0], pl.y_hi, k, nrhs, pl.ldy, 256) ||
+        !tc::encode(&m->b_lo[0], pl.y_lo, k, nrhs, pl.ldy, 256) ||
+        !tc::encode(&m->b_hi[1], pl.y_hi, k, nrhs, pl.ldy, 128) ||
+        !tc::encode(&m->b_lo[1], pl.y_lo, k, nrhs, pl.ldy, 128) ||
+        !tc::encode(&m->b_hi[2], pl.y_hi, k, nrhs, pl.ldy, 64) ||
+        !tc::encode(&m->b_lo[2], pl.y_lo, k, nrhs, pl.ldy, 64))
         return cudaErrorInvalidValue;
     return cudaSuccess;
 }
@@ -444,6 +473,14 @@ cudaError_t launch_gemm_tc(const Canon<float>& p, const void* maps, const TcGemm
     using namespace tc;
     for (int g0 = 0; g0 < ngemms; g0 += MAXG) {
         const int ng = (ngemms - g0) < MAXG ? (ngemms - g0) : MAXG;
+        // N tile: the widest whose tile count still covers every SM (wide
+        // tiles feed the tensor pipe best; small updates are epilogue-bound
+        // and want all SMs on them).
+        int64_t mtiles = 0;
+        for (int i = 0; i < ng; ++i) mtiles += (gemms[g0 + i].mlen + BM - 1) / BM;
+        int bn = 64;
+        if (mtiles * ((p.nrhs + 255) / 256) >= num_sms) bn = 256;
+        else if (mtiles * ((p.nrhs + 127) / 128) >= num_sms) bn = 128;
         static thread_local Params prm;
         prm.maps = *reinterpret_cast<const Maps*>(maps);
         prm.C = p.C;
@@ -453,7 +490,7 @@ cudaError_t launch_gemm_tc(const Canon<float>& p, const void* maps, const TcGemm
         prm.beta = beta;
         prm.gamma = gamma;
         prm.ngemms = ng;
-        prm.n_tiles_n = (int)((p.nrhs + BN - 1) / BN);
+        prm.n_tiles_n = (int)((p.nrhs + bn - 1) / bn);
         prm.err = err_word;
         prm.wait_ns = wait_ns;
         int64_t tiles = 0;
@@ -469,7 +506,12 @@ cudaError_t launch_gemm_tc(const Canon<float>& p, const void* maps, const TcGemm
         if (tiles > (int64_t)1 << 30) return cudaErrorInvalidValue;
         prm.total_tiles = (int)tiles;
         const int grid = (int)(tiles < num_sms ? tiles : num_sms);
-        gemm_tc_kernel<<<grid, NTHREADS, SMEM_BYTES, s>>>(prm);
+        if (bn == 256)
+            gemm_tc_kernel<256><<<grid, NTHREADS, Cfg<256>::SMEM_BYTES, s>>>(prm);
+        else if (bn == 128)
+            gemm_tc_kernel<128><<<grid, NTHREADS, Cfg<128>::SMEM_BYTES, s>>>(prm);
+        else
+            gemm_tc_kernel<64><<<grid, NTHREADS, Cfg<64>::SMEM_BYTES, s>>>(prm);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }

@@ -1,5 +1,7 @@
 // Leaf kernels: lane-count choice and dispatch. The kernels themselves are in
 // leaf_impl.cuh.
+#include <cstdlib>
+
 #include "leaf_impl.cuh"
 
 namespace trx {
@@ -53,6 +55,12 @@ cudaError_t launch_leaf(bool trsm, const Canon<T>& p, int64_t r0, int b,
     if (cols_per_sm >= 2048) G = 1;
     else if (cols_per_sm >= 512) G = 4;
     else if (cols_per_sm >= 64) G = 8;
+    // TRX_LEAF_LANES (1, 4, 8 or 16) overrides the choice, for tuning runs.
+    static const int forced = [] {
+        const char* e = std::getenv("TRX_LEAF_LANES");
+        return e ? std::atoi(e) : 0;
+    }();
+    if (forced == 1 || forced == 4 || forced == 8 || forced == 16) G = forced;
     const int64_t max_ctas = (int64_t)(num_sms > 0 ? num_sms : 1) * 4;
     return trsm ? leaf_dispatch<T, true>(a, nleaves, G, max_ctas, s)
                 : leaf_dispatch<T, false>(a, nleaves, G, max_ctas, s);

@@ -199,8 +199,8 @@ leaf_kernel(LeafArgs<T> a) {
                         r[q] = fma(-t[e], xj, r[q]);
                     }
                 }
-                // Keep the next step's shared-memory loads from being hoisted
-                // across steps (they would pile up in registers).
+                // Keep later steps' shared-memory loads from being hoisted
+                // across steps (they would pile up in registers and spill).
                 asm volatile("" ::: "memory");
             }
         } else {
