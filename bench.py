@@ -215,6 +215,8 @@ def run_gpu(args):
     A = colmajor(torch.from_numpy(A_np).to(dev))
     B = colmajor(torch.from_numpy(B_np).to(dev))
     h = trx.Handle(dev)
+    if args.no_pdl:
+        h.set_option(trx.OPT_PDL, 0)
     if args.leaf:
         h.set_option(trx.OPT_LEAF, args.leaf)
         global LEAF_USED
@@ -350,6 +352,7 @@ def main(argv=None):
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
     ap.add_argument("--leaf", type=int, default=0, help="recursion cutoff b (0: library default)")
+    ap.add_argument("--no-pdl", action="store_true", help="launch without programmatic dependent launch")
     args = ap.parse_args(argv)
     if args.impl == "reference":
         return run_reference(args)

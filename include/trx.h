@@ -75,9 +75,13 @@ enum {
     TRX_OPT_PROFILE = 4,   /* 1: time every launch with CUDA events and
                               accumulate into trx_profile_t (launches
                               directly, no graph); 0 (default): off        */
-    TRX_OPT_WAIT_LIMIT = 5 /* nanoseconds a device-side wait may spin
+    TRX_OPT_WAIT_LIMIT = 5,/* nanoseconds a device-side wait may spin
                               before it gives up and the launch reports
                               TRX_ERR_TIMEOUT (default 2e9, minimum 1000) */
+    TRX_OPT_PDL = 6        /* 1 (default): launch the chain's kernels with
+                              programmatic dependent launch, so each one's
+                              prologue overlaps the previous one's tail;
+                              0: plain stream order                        */
 };
 
 /* Kernel classes reported by trx_get_profile(). */

@@ -36,6 +36,11 @@ thread_local char g_detail[256] = "";
 }  // namespace
 
 namespace trx {
+bool& pdl_enabled() {
+    static thread_local bool on = true;
+    return on;
+}
+
 const char* set_detail(const char* msg) {
     snprintf(g_detail, sizeof(g_detail), "%s", msg);
     return g_detail;
@@ -254,7 +259,7 @@ struct trx_handle_s {
     void* ws = nullptr;
     size_t ws_bytes = 0;
     bool ws_owned = false;
-    int64_t opt_leaf = 0, opt_gemm = 0, opt_graph = 1, opt_profile = 0;
+    int64_t opt_leaf = 0, opt_gemm = 0, opt_graph = 1, opt_profile = 0, opt_pdl = 1;
     long long wait_ns = kDefaultWaitNs;
     int* d_err = nullptr;
     cudaStream_t cap_stream = nullptr;
@@ -389,6 +394,7 @@ struct GraphKey {
     const void* ws;
     double alpha;
     long long wait_ns;
+    int pdl;
 };
 
 template <typename T>
@@ -401,6 +407,7 @@ int execute(trx_handle_t h, bool trsm, char side, char uplo, char transa, char d
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     cudaError_t e = cudaSetDevice(h->device);
     if (e != cudaSuccess) return fail_cuda(e, "cudaSetDevice");
+    pdl_enabled() = h->opt_pdl != 0;
     if (alpha == T(0)) {
         e = launch_zero<T>(B, m, n, ldb, s);
         return e == cudaSuccess ? TRX_SUCCESS : fail_cuda(e, "zero");
@@ -459,6 +466,7 @@ int execute(trx_handle_t h, bool trsm, char side, char uplo, char transa, char d
     key.ws = plan.tc ? h->ws : nullptr;
     key.alpha = (double)alpha;
     key.wait_ns = h->wait_ns;
+    key.pdl = (int)h->opt_pdl;
     const std::string ks(reinterpret_cast<const char*>(&key), sizeof(key));
     ++h->tick;
     for (auto& g : h->graphs) {
@@ -745,6 +753,10 @@ int trx_set_option(trx_handle_t h, int option, int64_t value) {
             if (value < 1000) return TRX_ERR_INVALID_VALUE;
             h->wait_ns = value;
             break;
+        case TRX_OPT_PDL:
+            if (value != 0 && value != 1) return TRX_ERR_INVALID_VALUE;
+            h->opt_pdl = value;
+            break;
         default:
             return TRX_ERR_INVALID_VALUE;
     }
@@ -760,6 +772,7 @@ int trx_get_option(trx_handle_t h, int option, int64_t* value) {
         case TRX_OPT_GRAPH: *value = h->opt_graph; break;
         case TRX_OPT_PROFILE: *value = h->opt_profile; break;
         case TRX_OPT_WAIT_LIMIT: *value = h->wait_ns; break;
+        case TRX_OPT_PDL: *value = h->opt_pdl; break;
         default: return TRX_ERR_INVALID_VALUE;
     }
     return TRX_SUCCESS;

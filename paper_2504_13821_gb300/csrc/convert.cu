@@ -24,6 +24,8 @@ __device__ __forceinline__ void split_bf16(float x, __nv_bfloat16& hi, __nv_bflo
 // M planes: 64x64 tiles of the lower triangle (tiles above it exit at once),
 // read along A's contiguous index, written as BF16 pairs along l.
 __global__ void __launch_bounds__(256) convert_m_kernel(Canon<float> p, Planes pl) {
+    pdl_trigger();
+    pdl_wait();
     __shared__ float tile[64][65];
     const int64_t ti = blockIdx.y, tl = blockIdx.x;
     if (tl > ti) return;
@@ -61,6 +63,8 @@ __global__ void __launch_bounds__(256) convert_m_kernel(Canon<float> p, Planes p
 // Y planes when C's rows are contiguous (side L): no transpose, four
 // consecutive rows per thread, 8-byte stores.
 __global__ void __launch_bounds__(256) convert_y_contig_kernel(Canon<float> p, Planes pl) {
+    pdl_trigger();
+    pdl_wait();
     const int64_t l = ((int64_t)blockIdx.x * 256 + threadIdx.x) * 4;
     if (l >= p.k) return;
     for (int64_t j = blockIdx.y; j < p.nrhs; j += gridDim.y) {
@@ -88,6 +92,8 @@ __global__ void __launch_bounds__(256) convert_y_contig_kernel(Canon<float> p, P
 
 // Y planes when C's columns are contiguous (side R): 32x32 transpose tiles.
 __global__ void __launch_bounds__(256) convert_y_kernel(Canon<float> p, Planes pl) {
+    pdl_trigger();
+    pdl_wait();
     __shared__ float tile[32][33];              // tile[jj][ll]
     const int64_t l0 = (int64_t)blockIdx.x * 32, j0 = (int64_t)blockIdx.y * 32;
     const bool row_fast = (p.c_rs == 1 || p.c_rs == -1);
@@ -116,6 +122,8 @@ __global__ void __launch_bounds__(256) convert_rect_kernel(const float* src, int
                                                            int64_t cs, int64_t rows, int64_t cols,
                                                            __nv_bfloat16* hi, __nv_bfloat16* lo,
                                                            int64_t ld, int row_major) {
+    pdl_trigger();
+    pdl_wait();
     __shared__ float tile[32][33];
     const int64_t r0 = (int64_t)blockIdx.y * 32, c0 = (int64_t)blockIdx.x * 32;
     const bool src_row_fast = (rs == 1 || rs == -1);
@@ -141,6 +149,8 @@ __global__ void __launch_bounds__(256) convert_rect_kernel(const float* src, int
 
 template <typename T>
 __global__ void zero_kernel(T* B, int64_t m, int64_t n, int64_t ldb) {
+    pdl_trigger();
+    pdl_wait();
     const int64_t total = m * n;
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
          e += (int64_t)gridDim.x * blockDim.x) {
@@ -155,8 +165,7 @@ cudaError_t launch_convert_m(const Canon<float>& p, const Planes& pl, cudaStream
     if (p.k <= 1) return cudaSuccess;
     const int64_t t = (p.k + 63) / 64;
     if (t > 65535) return cudaErrorInvalidValue;
-    convert_m_kernel<<<dim3((unsigned)t, (unsigned)t), 256, 0, s>>>(p, pl);
-    return cudaGetLastError();
+    return launch_kernel(convert_m_kernel, dim3((unsigned)t, (unsigned)t), dim3(256), 0, s, p, pl);
 }
 
 cudaError_t launch_convert_y(const Canon<float>& p, const Planes& pl, cudaStream_t s) {
@@ -164,13 +173,13 @@ cudaError_t launch_convert_y(const Canon<float>& p, const Planes& pl, cudaStream
     if (p.c_rs == 1 || p.c_rs == -1) {
         const int64_t gx = (p.k + 1023) / 1024;
         const int64_t gy = p.nrhs < 65535 ? p.nrhs : 65535;
-        convert_y_contig_kernel<<<dim3((unsigned)gx, (unsigned)gy), 256, 0, s>>>(p, pl);
-        return cudaGetLastError();
+        return launch_kernel(convert_y_contig_kernel, dim3((unsigned)gx, (unsigned)gy), dim3(256),
+                             0, s, p, pl);
     }
     const int64_t tl = (p.k + 31) / 32, tj = (p.nrhs + 31) / 32;
     if (tj > 65535) return cudaErrorInvalidValue;
-    convert_y_kernel<<<dim3((unsigned)tl, (unsigned)tj), dim3(32, 8), 0, s>>>(p, pl);
-    return cudaGetLastError();
+    return launch_kernel(convert_y_kernel, dim3((unsigned)tl, (unsigned)tj), dim3(32, 8), 0, s, p,
+                         pl);
 }
 
 cudaError_t launch_convert_rect(const float* src, int64_t rs, int64_t cs, int64_t rows,
@@ -179,9 +188,8 @@ cudaError_t launch_convert_rect(const float* src, int64_t rs, int64_t cs, int64_
     if (rows <= 0 || cols <= 0) return cudaSuccess;
     const int64_t gy = (rows + 31) / 32, gx = (cols + 31) / 32;
     if (gy > 65535) return cudaErrorInvalidValue;
-    convert_rect_kernel<<<dim3((unsigned)gx, (unsigned)gy), dim3(32, 8), 0, s>>>(
-        src, rs, cs, rows, cols, hi, lo, ld, row_major ? 1 : 0);
-    return cudaGetLastError();
+    return launch_kernel(convert_rect_kernel, dim3((unsigned)gx, (unsigned)gy), dim3(32, 8), 0, s,
+                         src, rs, cs, rows, cols, hi, lo, ld, row_major ? 1 : 0);
 }
 
 template <typename T>
@@ -190,8 +198,7 @@ cudaError_t launch_zero(T* B, int64_t m, int64_t n, int64_t ldb, cudaStream_t s)
     const int64_t total = m * n;
     int64_t blocks = (total + 255) / 256;
     if (blocks > 65536) blocks = 65536;
-    zero_kernel<T><<<(unsigned)blocks, 256, 0, s>>>(B, m, n, ldb);
-    return cudaGetLastError();
+    return launch_kernel(zero_kernel<T>, dim3((unsigned)blocks), dim3(256), 0, s, B, m, n, ldb);
 }
 
 template cudaError_t launch_zero<float>(float*, int64_t, int64_t, int64_t, cudaStream_t);

@@ -33,6 +33,8 @@ template <typename T>
 __global__ void __launch_bounds__(NT) gemm_simt_kernel(GemmArgs<T> g) {
     __shared__ T sA[2][BK][BM + 4];   // sA[l][i] = M(rc+i0+i, rk+l0+l)
     __shared__ T sB[2][BK][BN + 4];   // sB[l][j] = C(rk+l0+l, j0+j)
+    pdl_trigger();
+    pdl_wait();
     const Canon<T>& p = g.p;
     const int tid = threadIdx.x;
     const int tx = tid % 16, ty = tid / 16;
@@ -134,8 +136,7 @@ cudaError_t launch_gemm_simt(const Canon<T>& p, const T* Y, int64_t y_rs, int64_
     g.gamma = gamma;
     const int64_t gy = (mlen + BM - 1) / BM, gx = (p.nrhs + BN - 1) / BN;
     if (gy > 65535) return cudaErrorInvalidValue;
-    gemm_simt_kernel<T><<<dim3((unsigned)gx, (unsigned)gy), NT, 0, s>>>(g);
-    return cudaGetLastError();
+    return launch_kernel(gemm_simt_kernel<T>, dim3((unsigned)gx, (unsigned)gy), dim3(NT), 0, s, g);
 }
 
 template cudaError_t launch_gemm_simt<float>(const Canon<float>&, const float*, int64_t, int64_t,

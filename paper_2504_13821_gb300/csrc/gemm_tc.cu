@@ -255,6 +255,10 @@ __global__ void __launch_bounds__(NTHREADS, 1) gemm_tc_kernel(const __grid_const
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = sm->tmem_base;
+    // Prologue done (barriers, TMEM); from here on the previous kernel's
+    // results (planes, C) are read.
+    pdl_trigger();
+    pdl_wait();
 
     if (warp == 0 && lane == 0) {
         // ---------------- TMA producer ----------------
@@ -506,13 +510,13 @@ cudaError_t launch_gemm_tc(const Canon<float>& p, const void* maps, const TcGemm
         if (tiles > (int64_t)1 << 30) return cudaErrorInvalidValue;
         prm.total_tiles = (int)tiles;
         const int grid = (int)(tiles < num_sms ? tiles : num_sms);
+        cudaError_t e;
         if (bn == 256)
-            gemm_tc_kernel<256><<<grid, NTHREADS, Cfg<256>::SMEM_BYTES, s>>>(prm);
+            e = launch_kernel(gemm_tc_kernel<256>, dim3(grid), dim3(NTHREADS), Cfg<256>::SMEM_BYTES, s, prm);
         else if (bn == 128)
-            gemm_tc_kernel<128><<<grid, NTHREADS, Cfg<128>::SMEM_BYTES, s>>>(prm);
+            e = launch_kernel(gemm_tc_kernel<128>, dim3(grid), dim3(NTHREADS), Cfg<128>::SMEM_BYTES, s, prm);
         else
-            gemm_tc_kernel<64><<<grid, NTHREADS, Cfg<64>::SMEM_BYTES, s>>>(prm);
-        cudaError_t e = cudaGetLastError();
+            e = launch_kernel(gemm_tc_kernel<64>, dim3(grid), dim3(NTHREADS), Cfg<64>::SMEM_BYTES, s, prm);
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;

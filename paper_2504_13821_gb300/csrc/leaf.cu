@@ -51,10 +51,12 @@ cudaError_t launch_leaf(bool trsm, const Canon<T>& p, int64_t r0, int b,
     // per column when there are many (no shuffles, widest vector reuse),
     // more lanes when there are few, to keep enough warps in flight.
     const int64_t cols_per_sm = p.nrhs * nleaves / (num_sms > 0 ? num_sms : 1);
+    // (Measured at b = 64, 16384 right-hand sides: 4 lanes beat 8 and 16;
+    // one lane per column is used where its registers allow, b <= 32.)
     int G = 16;
-    if (cols_per_sm >= 2048) G = 1;
-    else if (cols_per_sm >= 512) G = 4;
-    else if (cols_per_sm >= 64) G = 8;
+    if (cols_per_sm >= 2048 && b <= 32) G = 1;
+    else if (cols_per_sm >= 64) G = 4;
+    else if (cols_per_sm >= 16) G = 8;
     // TRX_LEAF_LANES (1, 4, 8 or 16) overrides the choice, for tuning runs.
     static const int forced = [] {
         const char* e = std::getenv("TRX_LEAF_LANES");

@@ -100,6 +100,8 @@ leaf_kernel(LeafArgs<T> a) {
     T* sD = sT + B * S::LDT;                   // 1/M(i,i) (TRSM) or M(i,i) (TRMM)
     T* sC = sD + B;                            // panel: C(r0+i, j0+c) at c*LDS + i
 
+    pdl_trigger();
+    pdl_wait();
     const int tid = threadIdx.x;
     const Canon<T>& p = a.p;
     const int64_t r0 = a.r0 + (int64_t)blockIdx.y * a.b;
@@ -281,8 +283,7 @@ cudaError_t launch_one(const LeafArgs<T>& a, int64_t nleaves, int64_t max_ctas, 
     if (per_leaf < 1) per_leaf = 1;
     const int64_t nx = npanels < per_leaf ? npanels : per_leaf;
     dim3 grid((unsigned)nx, (unsigned)nleaves);
-    leaf_kernel<T, B, G, TRSM><<<grid, S::NT, S::smem, s>>>(a);
-    return cudaGetLastError();
+    return launch_kernel(leaf_kernel<T, B, G, TRSM>, grid, dim3(S::NT), S::smem, s, a);
 }
 
 template <typename T, int B, bool TRSM>
