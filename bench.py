@@ -148,9 +148,12 @@ def oracle_sample(A, B, cols):
     return dt, 2.0 * flops_per_call(A.shape[0], cols)
 
 
+DTYPE = np.float32
+
+
 def host_inputs():
     from paper_2504_13821_gb300 import inputs
-    return inputs.problem("L", "L", K_ORDER, NRHS, seed=SEED, dtype=np.float32)
+    return inputs.problem("L", "L", K_ORDER, NRHS, seed=SEED, dtype=DTYPE)
 
 
 def run_reference(args):
@@ -176,8 +179,8 @@ def run_reference(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": workload_config(),
         "cpu_baseline": {"value": value, "unit": "TFLOP/s", "cores": cores, "kind": "oracle",
-                         "sample": f"per step: TRSM + TRMM of the 16384x16384 factor on "
-                                   f"{REF_SAMPLE_COLS} of the 16384 right-hand sides"},
+                         "sample": f"per step: TRSM + TRMM of the {K_ORDER}x{K_ORDER} factor "
+                                   f"on {REF_SAMPLE_COLS} of the {NRHS} right-hand sides"},
         "e2e": {"value": value, "unit": "TFLOP/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
@@ -189,10 +192,12 @@ LEAF_USED = 64
 
 
 def workload_config():
-    return {"workload": "FP32 TRSM(alpha=1.5) then TRMM(alpha=1/1.5), side L, lower, "
-                        "no transpose, non-unit, m=n=16384, column-major",
+    prec = "FP32" if DTYPE == np.float32 else "FP64"
+    return {"workload": f"{prec} TRSM(alpha=1.5) then TRMM(alpha=1/1.5), side L, lower, "
+                        f"no transpose, non-unit, m={K_ORDER} n={NRHS}, column-major",
             "m": K_ORDER, "n": NRHS, "leaf": LEAF_USED,
-            "gemm": "tcgen05 kind::f16, 3-term split BF16, FP32 accumulation",
+            "gemm": ("tcgen05 kind::f16, 3-term split BF16, FP32 accumulation"
+                     if DTYPE == np.float32 else "CUDA-core DFMA"),
             "graph": "cached CUDA graph per call",
             "l2": "inputs larger than L2 (A 1 GiB, B 1 GiB); no flush"}
 
@@ -215,8 +220,8 @@ def run_gpu(args):
     A = colmajor(torch.from_numpy(A_np).to(dev))
     B = colmajor(torch.from_numpy(B_np).to(dev))
     h = trx.Handle(dev)
-    if args.no_pdl:
-        h.set_option(trx.OPT_PDL, 0)
+    if args.pdl:
+        h.set_option(trx.OPT_PDL, 1)
     if args.leaf:
         h.set_option(trx.OPT_LEAF, args.leaf)
         global LEAF_USED
@@ -261,17 +266,26 @@ def run_gpu(args):
     prof = h.profile(reset=True)
     h.set_option(trx.OPT_PROFILE, 0)
     launches_step = sum(v["launches"] for v in prof.values())
-    g = prof["gemm_tc"]
     peaks, src = load_peaks()
-    peak_tc = peaks["bf16_tflops_sustained"] / 3.0
+    if DTYPE == np.float32:
+        g = prof["gemm_tc"]
+        kname = "gemm_tc_kernel (GEMM update, tcgen05)"
+        peak_tc = peaks["bf16_tflops_sustained"] / 3.0
+        peak_src = (f"{src} bf16 sustained {peaks['bf16_tflops_sustained']} TFLOP/s / 3 "
+                    f"split-product terms")
+    else:
+        g = prof["gemm_simt"]
+        kname = "gemm_simt_kernel<double> (GEMM update, DFMA)"
+        peak_tc = 1.25
+        peak_src = "nominal GB300 FP64 1.25 TFLOP/s (not measured)"
     achieved = g["flops"] / (g["ms"] * 1e-3) / 1e12 if g["ms"] > 0 else 0.0
     kern_ms = sum(v["ms"] for v in prof.values())
     roofline = {
-        "bound": "tensor", "kernel": "gemm_tc_kernel (GEMM update)",
+        "bound": "tensor" if DTYPE == np.float32 else "fp64",
+        "kernel": kname,
         "achieved": achieved, "peak": peak_tc, "unit": "TFLOP/s",
         "frac": achieved / peak_tc if peak_tc else None, "traffic": None,
-        "peak_source": f"{src} bf16 sustained {peaks['bf16_tflops_sustained']} TFLOP/s / 3 "
-                       f"split-product terms",
+        "peak_source": peak_src,
         "launches_per_step": g["launches"],
         "share_of_kernel_time": g["ms"] / kern_ms if kern_ms else None,
         "per_class_ms": {kk: round(v["ms"], 4) for kk, v in prof.items() if v["launches"]},
@@ -322,15 +336,16 @@ def run_gpu(args):
         dt, fl = oracle_sample(A_np, B_np, CPU_SAMPLE_COLS)
         cpu = {"value": fl / dt / 1e12, "unit": "TFLOP/s", "cores": oracle.nthreads(),
                "kind": "oracle",
-               "sample": f"TRSM + TRMM of the 16384x16384 factor on {CPU_SAMPLE_COLS} of the "
-                         f"16384 right-hand sides ({dt:.1f} s)"}
+               "sample": f"TRSM + TRMM of the {K_ORDER}x{K_ORDER} factor on {CPU_SAMPLE_COLS} "
+                         f"of the {NRHS} right-hand sides ({dt:.1f} s)"}
 
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32", "data": "synthetic", "config": workload_config(),
+            "dtype": "f32" if DTYPE == np.float32 else "f64", "data": "synthetic",
+            "config": workload_config(),
             "clocks": clk, "gpu_launches": launches_step * args.steps,
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
             "round_trip_drift": drift,
@@ -352,8 +367,15 @@ def main(argv=None):
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
     ap.add_argument("--leaf", type=int, default=0, help="recursion cutoff b (0: library default)")
-    ap.add_argument("--no-pdl", action="store_true", help="launch without programmatic dependent launch")
+    ap.add_argument("--pdl", action="store_true", help="launch with programmatic dependent launch")
+    ap.add_argument("--k", type=int, default=K_ORDER,
+                    help="order of A (default 16384; smaller only for profiling runs)")
+    ap.add_argument("--nrhs", type=int, default=NRHS, help="right-hand sides (default 16384)")
+    ap.add_argument("--dtype", default="f32", choices=["f32", "f64"])
     args = ap.parse_args(argv)
+    global K_ORDER, NRHS, DTYPE
+    K_ORDER, NRHS = args.k, args.nrhs
+    DTYPE = np.float32 if args.dtype == "f32" else np.float64
     if args.impl == "reference":
         return run_reference(args)
     return run_gpu(args)

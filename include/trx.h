@@ -78,10 +78,10 @@ enum {
     TRX_OPT_WAIT_LIMIT = 5,/* nanoseconds a device-side wait may spin
                               before it gives up and the launch reports
                               TRX_ERR_TIMEOUT (default 2e9, minimum 1000) */
-    TRX_OPT_PDL = 6        /* 1 (default): launch the chain's kernels with
+    TRX_OPT_PDL = 6        /* 1: launch the chain's kernels with
                               programmatic dependent launch, so each one's
                               prologue overlaps the previous one's tail;
-                              0: plain stream order                        */
+                              0 (default): plain stream order              */
 };
 
 /* Kernel classes reported by trx_get_profile(). */

@@ -37,7 +37,7 @@ thread_local char g_detail[256] = "";
 
 namespace trx {
 bool& pdl_enabled() {
-    static thread_local bool on = true;
+    static thread_local bool on = false;
     return on;
 }
 
@@ -259,7 +259,7 @@ struct trx_handle_s {
     void* ws = nullptr;
     size_t ws_bytes = 0;
     bool ws_owned = false;
-    int64_t opt_leaf = 0, opt_gemm = 0, opt_graph = 1, opt_profile = 0, opt_pdl = 1;
+    int64_t opt_leaf = 0, opt_gemm = 0, opt_graph = 1, opt_profile = 0, opt_pdl = 0;
     long long wait_ns = kDefaultWaitNs;
     int* d_err = nullptr;
     cudaStream_t cap_stream = nullptr;

@@ -8,7 +8,7 @@
 // Work split. G lanes of one warp share a right-hand side; lane g owns the
 // rows g, g+G, g+2G, ... of its column (interleaved, so the shrinking active
 // set of a forward sweep stays balanced across the lanes) and holds them in
-// registers. A CTA of 256 threads covers NCOL = 256/G right-hand sides at a
+// registers. A CTA of 128 threads covers NCOL = 128/G right-hand sides at a
 // time and is persistent: it stages the triangle once and then walks panels
 // of NCOL columns (each staged through shared memory with coalesced loads
 // along whichever index is contiguous in C), so the triangle is read from L2
@@ -67,7 +67,7 @@ struct Vec<double> {
 
 template <typename T, int B, int G>
 struct LeafShape {
-    static constexpr int NT = 256;
+    static constexpr int NT = 128;
     static constexpr int NCOL = NT / G;
     static constexpr int RPL = B / G;                        // rows per lane
     static constexpr int VN = Vec<T>::n;
@@ -90,11 +90,25 @@ __device__ __forceinline__ void vload(const T* p, T (&v)[Vec<T>::n]) {
     }
 }
 
+// The vector groups of column l that a sweep step needs (rows at or below
+// the step's own row block), into v[q] for this lane's rows q.
+template <typename T, typename S>
+__device__ __forceinline__ void load_col(const T* my, int l, T (&v)[S::RPL]) {
+    const int first = ((l / (S::NT / S::NCOL)) / S::VN) * S::VN;   // l / G, rounded to a group
+#pragma unroll
+    for (int q0 = 0; q0 < S::RPL; q0 += S::VN) {
+        if (q0 < first) continue;
+        T t[S::VN];
+        vload(my + l * S::LDT + q0, t);
+#pragma unroll
+        for (int e = 0; e < S::VN; ++e) v[q0 + e] = t[e];
+    }
+}
+
 template <typename T, int B, int G, bool TRSM>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(128)
 leaf_kernel(LeafArgs<T> a) {
     using S = LeafShape<T, B, G>;
-    constexpr int VN = S::VN;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* sT = reinterpret_cast<T*>(smem_raw);   // M(r0+i, r0+l) at l*LDT + (i%G)*RPLP + i/G
     T* sD = sT + B * S::LDT;                   // 1/M(i,i) (TRSM) or M(i,i) (TRMM)
@@ -175,12 +189,20 @@ leaf_kernel(LeafArgs<T> a) {
 #pragma unroll
         for (int q = 0; q < S::RPL; ++q) r[q] = sC[c * S::LDS + q * G + g];
 
+        // Column jj of the triangle is consumed from registers loaded one
+        // step earlier (cur), while the next column's loads (nxt) are in
+        // flight: the shared-memory latency hides behind a step of FMAs.
+        // The compiler barrier at the end of a step stops it from hoisting
+        // more columns than that into registers.
+        T cur[S::RPL], nxt[S::RPL];
         if (TRSM) {
 #pragma unroll
             for (int q = 0; q < S::RPL; ++q) r[q] *= a.alpha;
+            load_col<T, S>(my, 0, cur);
 #pragma unroll
             for (int jj = 0; jj < B; ++jj) {
                 const int qj = jj / G, gj = jj % G;
+                if (jj + 1 < B) load_col<T, S>(my, jj + 1, nxt);
                 const T v = r[qj] * sD[jj];
                 T xj;
                 if (G == 1) {
@@ -191,37 +213,29 @@ leaf_kernel(LeafArgs<T> a) {
                     if (g == gj) r[qj] = v;
                 }
 #pragma unroll
-                for (int q0 = (qj / VN) * VN; q0 < S::RPL; q0 += VN) {
-                    T t[VN];
-                    vload(my + jj * S::LDT + q0, t);
-#pragma unroll
-                    for (int e = 0; e < VN; ++e) {
-                        const int q = q0 + e;
-                        if (q < qj || (q == qj && g <= gj)) continue;
-                        r[q] = fma(-t[e], xj, r[q]);
-                    }
+                for (int q = qj; q < S::RPL; ++q) {
+                    if (q == qj && g <= gj) continue;
+                    r[q] = fma(-cur[q], xj, r[q]);
                 }
-                // Keep later steps' shared-memory loads from being hoisted
-                // across steps (they would pile up in registers and spill).
+#pragma unroll
+                for (int q = 0; q < S::RPL; ++q) cur[q] = nxt[q];
                 asm volatile("" ::: "memory");
             }
         } else {
+            load_col<T, S>(my, B - 1, cur);
 #pragma unroll
             for (int jj = B - 1; jj >= 0; --jj) {
                 const int qj = jj / G, gj = jj % G;
+                if (jj > 0) load_col<T, S>(my, jj - 1, nxt);
                 const T xj = (G == 1) ? r[qj] : __shfl_sync(0xffffffffu, r[qj], gj, G);
 #pragma unroll
-                for (int q0 = (qj / VN) * VN; q0 < S::RPL; q0 += VN) {
-                    T t[VN];
-                    vload(my + jj * S::LDT + q0, t);
-#pragma unroll
-                    for (int e = 0; e < VN; ++e) {
-                        const int q = q0 + e;
-                        if (q < qj || (q == qj && g <= gj)) continue;
-                        r[q] = fma(t[e], xj, r[q]);
-                    }
+                for (int q = qj; q < S::RPL; ++q) {
+                    if (q == qj && g <= gj) continue;
+                    r[q] = fma(cur[q], xj, r[q]);
                 }
                 if (g == gj) r[qj] = sD[jj] * xj;
+#pragma unroll
+                for (int q = 0; q < S::RPL; ++q) cur[q] = nxt[q];
                 asm volatile("" ::: "memory");
             }
 #pragma unroll
