@@ -368,9 +368,9 @@ def main(argv=None):
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
     ap.add_argument("--leaf", type=int, default=0, help="recursion cutoff b (0: library default)")
     ap.add_argument("--pdl", action="store_true", help="launch with programmatic dependent launch")
-    ap.add_argument("--k", type=int, default=K_ORDER,
+    ap.add_argument("--k", type=int, default=16384,
                     help="order of A (default 16384; smaller only for profiling runs)")
-    ap.add_argument("--nrhs", type=int, default=NRHS, help="right-hand sides (default 16384)")
+    ap.add_argument("--nrhs", type=int, default=16384, help="right-hand sides (default 16384)")
     ap.add_argument("--dtype", default="f32", choices=["f32", "f64"])
     args = ap.parse_args(argv)
     global K_ORDER, NRHS, DTYPE
