@@ -25,12 +25,23 @@ extern template cudaError_t leaf_configure<double, false>();
 
 cudaError_t tc_configure();
 
+template <typename T>
+cudaError_t leaf_blocked_configure();
+template <typename T>
+cudaError_t leaf_blocked_launch(const LeafArgs<T>& a, int64_t max_ctas, cudaStream_t s);
+extern template cudaError_t leaf_blocked_configure<float>();
+extern template cudaError_t leaf_blocked_configure<double>();
+extern template cudaError_t leaf_blocked_launch<float>(const LeafArgs<float>&, int64_t, cudaStream_t);
+extern template cudaError_t leaf_blocked_launch<double>(const LeafArgs<double>&, int64_t, cudaStream_t);
+
 cudaError_t leaf_configure_all() {
     cudaError_t e;
     if ((e = leaf_configure<float, true>()) != cudaSuccess) return e;
     if ((e = leaf_configure<float, false>()) != cudaSuccess) return e;
     if ((e = leaf_configure<double, true>()) != cudaSuccess) return e;
     if ((e = leaf_configure<double, false>()) != cudaSuccess) return e;
+    if ((e = leaf_blocked_configure<float>()) != cudaSuccess) return e;
+    if ((e = leaf_blocked_configure<double>()) != cudaSuccess) return e;
     return tc_configure();
 }
 
@@ -47,6 +58,16 @@ cudaError_t launch_leaf(bool trsm, const Canon<T>& p, int64_t r0, int b,
     a.alpha = alpha;
     a.planes = planes != nullptr;
     if (planes) a.pl = *planes;
+    // A single TRSM leaf of 33..128 rows with many right-hand sides takes the
+    // blocked kernel (16-row substitutions + rank-16 updates); the lane-split
+    // sweep below covers the rest. TRX_LEAF_BLOCKED=0 turns it off.
+    static const bool blocked_on = [] {
+        const char* e = std::getenv("TRX_LEAF_BLOCKED");
+        return !(e && e[0] == '0');
+    }();
+    if (blocked_on && trsm && nleaves == 1 && b > 32 && p.nrhs >= 1024)
+        return leaf_blocked_launch<T>(a, (int64_t)(num_sms > 0 ? num_sms : 1) * 2, s);
+
     // Lanes per right-hand side, from the right-hand sides per SM: one lane
     // per column when there are many (no shuffles, widest vector reuse),
     // more lanes when there are few, to keep enough warps in flight.

@@ -1,7 +1,10 @@
 // Instantiation of the leaf kernels for float TRSM.
+#include "leaf_blocked.cuh"
 #include "leaf_impl.cuh"
 
 namespace trx {
 template cudaError_t leaf_dispatch<float, true>(const LeafArgs<float>&, int64_t, int, int64_t, cudaStream_t);
 template cudaError_t leaf_configure<float, true>();
+template cudaError_t leaf_blocked_configure<float>();
+template cudaError_t leaf_blocked_launch<float>(const LeafArgs<float>&, int64_t, cudaStream_t);
 }  // namespace trx
