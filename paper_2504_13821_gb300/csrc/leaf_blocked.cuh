@@ -40,7 +40,7 @@ struct BlkShape {
 };
 
 template <typename T, int B>
-__global__ void __launch_bounds__(256) leaf_trsm_blocked_kernel(LeafArgs<T> a) {
+__global__ void __launch_bounds__(256, B == 64 ? 2 : 1) leaf_trsm_blocked_kernel(LeafArgs<T> a) {
     using S = BlkShape<T, B>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* sT = reinterpret_cast<T*>(smem_raw);   // M(r0+i, r0+l) at l*B + i (i > l, else 0)
@@ -55,21 +55,49 @@ __global__ void __launch_bounds__(256) leaf_trsm_blocked_kernel(LeafArgs<T> a) {
     if (rem <= 0) return;
     const int bs = rem < a.b ? (int)rem : a.b;
 
+    // Panel staging map: each thread keeps the index that is contiguous in C
+    // (`fi`) and walks the other (`w = wi + u*adv`, u < PL) with a pointer.
+    const bool c_row_fast = (p.c_rs == 1 || p.c_rs == -1);
+    constexpr int PL = B * S::NCOL / S::NT;
+    const int fmod = c_row_fast ? B : S::NCOL;
+    const int fi = tid % fmod, wi = tid / fmod, adv = S::NT / fmod;
+    const int64_t st_walk = c_row_fast ? p.c_cs : p.c_rs;
+    const int64_t npanels = (p.nrhs + S::NCOL - 1) / S::NCOL;
+    auto panel_base = [&](int64_t j0) {
+        return p.C + (c_row_fast ? (r0 + fi) * p.c_rs + (j0 + wi) * p.c_cs
+                                 : (r0 + wi) * p.c_rs + (j0 + fi) * p.c_cs);
+    };
+    auto load_panel = [&](int64_t j0, T (&v)[PL]) {
+        const T* src = panel_base(j0);
+#pragma unroll
+        for (int u = 0; u < PL; ++u) {
+            const int w = wi + u * adv;
+            const int i = c_row_fast ? fi : w, c = c_row_fast ? w : fi;
+            v[u] = (i < bs && j0 + c < p.nrhs) ? a.alpha * *src : T(0);
+            src += adv * st_walk;
+        }
+    };
+    // The first panel's loads go out before the triangle's, so the two
+    // global-memory latencies overlap.
+    T pre[PL];
+    int64_t panel = blockIdx.x;
+    if (panel < npanels) load_panel(panel * S::NCOL, pre);
+
     // Triangle, read along A's contiguous index (one fixed index per thread).
     {
         const bool a_row_fast = (p.a_rs == 1 || p.a_rs == -1);
         constexpr int ADV = S::NT / B;
+        constexpr int TP = B / ADV;
         const int fixed = tid % B, first = tid / B;
         const int64_t st_fixed = a_row_fast ? p.a_rs : p.a_cs;
-        const int64_t st_walk = a_row_fast ? p.a_cs : p.a_rs;
-        const T* src = p.A + (r0 + fixed) * st_fixed + (r0 + first) * st_walk;
-#pragma unroll 4
-        for (int w = first; w < B; w += ADV) {
+        const int64_t st_walk_a = a_row_fast ? p.a_cs : p.a_rs;
+        const T* src = p.A + (r0 + fixed) * st_fixed + (r0 + first) * st_walk_a;
+#pragma unroll 8
+        for (int u = 0; u < TP; ++u) {
+            const int w = first + u * ADV;
             const int i = a_row_fast ? fixed : w, l = a_row_fast ? w : fixed;
-            T v = T(0);
-            if (i < bs && l < i) v = *src;
-            sT[l * B + i] = v;
-            src += ADV * st_walk;
+            sT[l * B + i] = (i < bs && l < i) ? *src : T(0);
+            src += ADV * st_walk_a;
         }
         for (int i = tid; i < B; i += S::NT) {
             T d = T(1);
@@ -77,33 +105,21 @@ __global__ void __launch_bounds__(256) leaf_trsm_blocked_kernel(LeafArgs<T> a) {
             sD[i] = d;
         }
     }
-    __syncthreads();
 
-    const bool c_row_fast = (p.c_rs == 1 || p.c_rs == -1);
-    const int64_t npanels = (p.nrhs + S::NCOL - 1) / S::NCOL;
     // update-phase tile: row group rg (rows rg, rg+RG, ...), columns 4*cg..4*cg+3
     const int cg = tid % S::CG, rg = tid / S::CG;
 #pragma unroll 1
-    for (int64_t panel = blockIdx.x; panel < npanels; panel += gridDim.x) {
+    for (; panel < npanels; panel += gridDim.x) {
         const int64_t j0 = panel * S::NCOL;
-        // stage the panel (alpha applied), coalesced along C's contiguous index
-        {
-            const int fmod = c_row_fast ? B : S::NCOL;
-            const int fi = tid % fmod, wi = tid / fmod, adv = S::NT / fmod;
-            const int64_t st_walk = c_row_fast ? p.c_cs : p.c_rs;
-            const T* src = p.C + (c_row_fast ? (r0 + fi) * p.c_rs + (j0 + wi) * p.c_cs
-                                             : (r0 + wi) * p.c_rs + (j0 + fi) * p.c_cs);
-            const int wmax = c_row_fast ? S::NCOL : B;
-#pragma unroll 4
-            for (int w = wi; w < wmax; w += adv) {
-                const int i = c_row_fast ? fi : w, c = c_row_fast ? w : fi;
-                T v = T(0);
-                if (i < bs && j0 + c < p.nrhs) v = a.alpha * *src;
-                sC[i * S::LDC + c] = v;
-                src += adv * st_walk;
-            }
+#pragma unroll
+        for (int u = 0; u < PL; ++u) {
+            const int w = wi + u * adv;
+            const int i = c_row_fast ? fi : w, c = c_row_fast ? w : fi;
+            sC[i * S::LDC + c] = pre[u];
         }
         __syncthreads();
+        // next panel's loads in flight during this panel's sweep
+        if (panel + gridDim.x < npanels) load_panel((panel + gridDim.x) * S::NCOL, pre);
 #pragma unroll
         for (int s0 = 0; s0 < B; s0 += S::SB) {
             // 1. substitution on rows s0 .. s0+15, one thread per column
@@ -160,14 +176,10 @@ __global__ void __launch_bounds__(256) leaf_trsm_blocked_kernel(LeafArgs<T> a) {
         }
         // write back (and the Y planes on the tensor-core path)
         {
-            const int fmod = c_row_fast ? B : S::NCOL;
-            const int fi = tid % fmod, wi = tid / fmod, adv = S::NT / fmod;
-            const int64_t st_walk = c_row_fast ? p.c_cs : p.c_rs;
-            T* dst = p.C + (c_row_fast ? (r0 + fi) * p.c_rs + (j0 + wi) * p.c_cs
-                                       : (r0 + wi) * p.c_rs + (j0 + fi) * p.c_cs);
-            const int wmax = c_row_fast ? S::NCOL : B;
-#pragma unroll 4
-            for (int w = wi; w < wmax; w += adv) {
+            T* dst = panel_base(j0);
+#pragma unroll
+            for (int u = 0; u < PL; ++u) {
+                const int w = wi + u * adv;
                 const int i = c_row_fast ? fi : w, c = c_row_fast ? w : fi;
                 if (i < bs && j0 + c < p.nrhs) *dst = sC[i * S::LDC + c];
                 dst += adv * st_walk;
@@ -177,7 +189,7 @@ __global__ void __launch_bounds__(256) leaf_trsm_blocked_kernel(LeafArgs<T> a) {
             if (a.planes) {
                 const int pi = tid % B, pc = tid / B;
                 constexpr int PADV = S::NT / B;
-#pragma unroll 4
+#pragma unroll
                 for (int c = pc; c < S::NCOL; c += PADV) {
                     if (pi < bs && j0 + c < p.nrhs) {
                         const float xval = sC[pi * S::LDC + c];
