@@ -358,6 +358,69 @@ def run_gpu(args):
     return 0
 
 
+def run_batched(args):
+    """Batched uneven workload: 4096 independent TRSM/TRMM problems, order
+    log-uniform 16..512, 1..64 right-hand sides, random side and uplo, one
+    persistent launch (cached graph), against a loop of single calls."""
+    import torch
+    import paper_2504_13821_gb300 as trx
+    from paper_2504_13821_gb300 import inputs
+    dev = torch.device("cuda", 0)
+    rng = np.random.default_rng(4096)
+    probs, flops = [], 0.0
+    for i in range(args.count):
+        k = int(round(np.exp(rng.uniform(np.log(16), np.log(512)))))
+        nrhs = int(rng.integers(1, 65))
+        side, uplo = str(rng.choice(["L", "R"])), str(rng.choice(["L", "U"]))
+        op = "S" if i % 2 == 0 else "M"
+        m, n = (k, nrhs) if side == "L" else (nrhs, k)
+        A, B = inputs.problem(side, uplo, m, n, seed=4096 * 1000 + i, dtype=DTYPE)
+        At = trx.to_colmajor(torch.from_numpy(A).to(dev))
+        Bt = trx.to_colmajor(torch.from_numpy(B).to(dev))
+        probs.append((op, side, uplo, "N", "N", 1.5 if op == "S" else 1 / 1.5, At, Bt))
+        flops += float(k) * k * nrhs
+    h = trx.Handle(dev)
+    scratch = [(o, s_, u, t, d, a, A, B.clone()) for (o, s_, u, t, d, a, A, B) in probs]
+    table = trx.batched_autotune(scratch, handle=h)
+    del scratch
+    stream = torch.cuda.current_stream(dev)
+
+    def timed(fn, reps):
+        for _ in range(max(args.warmup, 1)):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    ms_batched = timed(lambda: trx.batched(probs, handle=h, stream=stream), args.steps)
+
+    def loop():
+        for (o, s_, u, t, d, a, A, B) in probs:
+            (trx.trsm if o == "S" else trx.trmm)(s_, u, t, d, a, A, B, handle=h, stream=stream)
+    ms_loop = timed(loop, max(1, min(args.steps, 2)))
+    line = {
+        "metric": "batched uneven TRSM/TRMM problems/s", "value": args.count / (ms_batched * 1e-3),
+        "unit": "problems/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms_batched, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32" if DTYPE == np.float32 else "f64",
+        "data": "synthetic",
+        "config": {"workload": f"{args.count} problems, order log-uniform 16..512, 1..64 "
+                               "right-hand sides, random side/uplo, TRSM/TRMM alternating",
+                   "tflops_m2n": flops / (ms_batched * 1e-3) / 1e12,
+                   "autotune": table},
+        "loop_of_single_calls": {"ms": ms_loop, "problems_per_s": args.count / (ms_loop * 1e-3)},
+        "speedup_vs_loop": ms_loop / ms_batched,
+    }
+    print(json.dumps(line), flush=True)
+    h.close()
+    return 0
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -372,12 +435,18 @@ def main(argv=None):
                     help="order of A (default 16384; smaller only for profiling runs)")
     ap.add_argument("--nrhs", type=int, default=16384, help="right-hand sides (default 16384)")
     ap.add_argument("--dtype", default="f32", choices=["f32", "f64"])
+    ap.add_argument("--workload", default="square", choices=["square", "batched"],
+                    help="square: the n=16384 TRSM+TRMM step (default); batched: "
+                         "4096 small uneven problems in one launch")
+    ap.add_argument("--count", type=int, default=4096, help="problems (batched workload)")
     args = ap.parse_args(argv)
     global K_ORDER, NRHS, DTYPE
     K_ORDER, NRHS = args.k, args.nrhs
     DTYPE = np.float32 if args.dtype == "f32" else np.float64
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batched":
+        return run_batched(args)
     return run_gpu(args)
 
 

@@ -161,6 +161,46 @@ int trx_sgemm_update(trx_handle_t handle, int64_t M, int64_t N, int64_t K,
                      const float* Y, int64_t ldy, float* C, int64_t ldc,
                      int engine, void* stream);
 
+/* ---- batched uneven problems (one persistent launch) --------------------
+ * One TRSM or TRMM of the kind above per entry; all entries of a call share
+ * the element type. Pointers are device pointers; problems must not overlap
+ * each other's B. Orders k (m for side 'L', n for side 'R') up to
+ * TRX_BATCH_MAX_K; larger problems belong to trx_?trsm / trx_?trmm. */
+#define TRX_BATCH_MAX_K 512
+
+typedef struct {
+    char op;                 /* 'S' TRSM, 'M' TRMM                         */
+    char side, uplo, transa, diag;
+    int64_t m, n;
+    double alpha;            /* converted to the element type              */
+    const void* A;
+    int64_t lda;
+    void* B;
+    int64_t ldb;
+} trx_problem_t;
+
+/* Run `count` problems (host array) in one persistent launch: problems are
+ * mapped to the library's canonical form, sorted largest first and taken by
+ * the CTAs from a shared counter; the launch is replayed from a cached CUDA
+ * graph. elem_bytes is 4 (FP32) or 8 (FP64). Returns 0, or
+ * TRX_ERR_INVALID_VALUE if a problem is malformed or too large (the detail
+ * string names it), or another TRX_ERR_* code; nothing is enqueued then.
+ * The handle keeps (and grows on demand) a device descriptor array and a
+ * pinned host staging buffer for the batch; a call waits for the previous
+ * batched call's descriptor upload before reusing the staging buffer. */
+int trx_batched(trx_handle_t handle, int elem_bytes, int64_t count,
+                const trx_problem_t* problems, void* stream);
+
+/* Time the batch with each sub-block height (8, 16, 32 rows) per order
+ * bucket (k <= 64, 128, 256, 512), keep the fastest per bucket in the
+ * handle for later trx_batched calls, and write the table as JSON into
+ * json (if not NULL). The problems' B arrays are overwritten (the batch
+ * runs several times): tune on representative scratch data. Synchronises
+ * the stream. */
+int trx_batched_autotune(trx_handle_t handle, int elem_bytes, int64_t count,
+                         const trx_problem_t* problems, void* stream,
+                         char* json, size_t json_len);
+
 /* Set / read an option (TRX_OPT_*). Unknown options or values return
  * TRX_ERR_INVALID_VALUE. */
 int trx_set_option(trx_handle_t handle, int option, int64_t value);

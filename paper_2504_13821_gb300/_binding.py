@@ -39,6 +39,15 @@ class TrxError(RuntimeError):
         super().__init__(msg)
 
 
+class Problem(ctypes.Structure):
+    """trx_problem_t: one entry of a batched call."""
+    _fields_ = [("op", ctypes.c_char), ("side", ctypes.c_char), ("uplo", ctypes.c_char),
+                ("transa", ctypes.c_char), ("diag", ctypes.c_char),
+                ("m", ctypes.c_int64), ("n", ctypes.c_int64), ("alpha", ctypes.c_double),
+                ("A", ctypes.c_void_p), ("lda", ctypes.c_int64),
+                ("B", ctypes.c_void_p), ("ldb", ctypes.c_int64)]
+
+
 class _Profile(ctypes.Structure):
     _fields_ = [("ms", ctypes.c_double * 6), ("flops", ctypes.c_double * 6),
                 ("bytes", ctypes.c_double * 6), ("launches", ctypes.c_int64 * 6)]
@@ -76,6 +85,9 @@ def load_library() -> ctypes.CDLL:
                                        ctypes.c_int, ctypes.c_char_p, ctypes.c_size_t]
         lib.trx_sgemm_update.argtypes = [vp, i64, i64, i64, ctypes.c_float, ctypes.c_float,
                                          vp, i64, vp, i64, vp, i64, ctypes.c_int, vp]
+        lib.trx_batched.argtypes = [vp, ctypes.c_int, i64, ctypes.POINTER(Problem), vp]
+        lib.trx_batched_autotune.argtypes = [vp, ctypes.c_int, i64, ctypes.POINTER(Problem), vp,
+                                             ctypes.c_char_p, ctypes.c_size_t]
         lib.trx_version.argtypes = []
         _lib = lib
         return lib
@@ -282,6 +294,61 @@ def gemm_update(beta: float, gamma: float, A, Y, C, *, engine: int = GEMM_TC,
     _check(lib.trx_sgemm_update(h.ptr, M, N, K, float(beta), float(gamma), a, lda, y, ldy,
                                 c, ldc, engine, s_ptr), "trx_sgemm_update")
     return C
+
+
+def _problem_array(problems):
+    """ctypes array of trx_problem_t from (op, side, uplo, trans, diag, alpha,
+    A, B) tuples of column-major CUDA tensors; also returns the element size."""
+    import torch
+    arr = (Problem * max(1, len(problems)))()
+    elem = None
+    for i, (op, side, uplo, trans, diag, alpha, A, B) in enumerate(problems):
+        if A.dtype != B.dtype or A.dtype not in (torch.float32, torch.float64):
+            raise TypeError(f"problem {i}: A and B must share float32/float64")
+        if elem is None:
+            elem = A.element_size()
+        elif A.element_size() != elem:
+            raise TypeError("all problems of a batch share one element type")
+        a, lda = _colmajor(A, "A")
+        b, ldb = _colmajor(B, "B")
+        m, n = B.shape
+        arr[i] = Problem(_char(op), _char(side), _char(uplo), _char(trans), _char(diag),
+                         m, n, float(alpha), a, lda, b, ldb)
+    return arr, (elem or 4)
+
+
+def batched(problems, *, handle: Handle | None = None, stream=None):
+    """Run many small TRSM ('S') / TRMM ('M') problems in one persistent
+    launch. problems: list of (op, side, uplo, trans, diag, alpha, A, B)."""
+    import torch
+    lib = load_library()
+    if not problems:
+        return
+    arr, elem = _problem_array(problems)
+    dev = problems[0][7].device
+    h = handle if handle is not None else default_handle(dev)
+    if stream is None:
+        stream = torch.cuda.current_stream(dev)
+    s_ptr = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+    _check(lib.trx_batched(h.ptr, elem, len(problems), arr, s_ptr), "trx_batched")
+
+
+def batched_autotune(problems, *, handle: Handle | None = None, stream=None) -> dict:
+    """Tune the batched kernel's sub-block height per order bucket on these
+    problems (their B arrays are overwritten) and return the table."""
+    import json
+    import torch
+    lib = load_library()
+    arr, elem = _problem_array(problems)
+    dev = problems[0][7].device
+    h = handle if handle is not None else default_handle(dev)
+    if stream is None:
+        stream = torch.cuda.current_stream(dev)
+    s_ptr = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+    buf = ctypes.create_string_buffer(4096)
+    _check(lib.trx_batched_autotune(h.ptr, elem, len(problems), arr, s_ptr, buf, len(buf)),
+           "trx_batched_autotune")
+    return json.loads(buf.value.decode())
 
 
 def to_colmajor(x):

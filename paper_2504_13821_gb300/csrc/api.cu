@@ -19,6 +19,19 @@
 namespace trx {
 // Leaf kernels set their shared-memory limits once per device (leaf.cu).
 cudaError_t leaf_configure_all();
+
+struct BatchDesc {
+    int64_t k, nrhs;
+    const void* A;
+    int64_t a_rs, a_cs;
+    void* C;
+    int64_t c_rs, c_cs;
+    double alpha;
+    int unit, trsm, sb, pad;
+};
+cudaError_t batched_configure();
+cudaError_t launch_batched(int elem_bytes, const BatchDesc* descs, int64_t count, int* counter,
+                           int grid_ctas, cudaStream_t s);
 }  // namespace trx
 
 using namespace trx;
@@ -30,6 +43,7 @@ constexpr int kDefaultLeaf = 64;
 constexpr long long kDefaultWaitNs = 2000000000LL;   // 2 s
 constexpr int64_t kTcMinOrder = 256;                 // auto: tensor cores from this order
 constexpr size_t kGraphCacheSize = 16;
+constexpr int64_t kBatchMaxK = TRX_BATCH_MAX_K;
 
 thread_local char g_detail[256] = "";
 
@@ -279,6 +293,13 @@ struct trx_handle_s {
     std::vector<GraphEntry> graphs;
     uint64_t tick = 0;
     std::vector<unsigned char> maps;
+    // batched path: device descriptors + counter, pinned staging, tuning
+    BatchDesc* b_dev = nullptr;
+    int* b_counter = nullptr;
+    BatchDesc* b_host = nullptr;
+    int64_t b_cap = 0;
+    cudaEvent_t b_uploaded = nullptr;
+    int tune_sb[2][4] = {{16, 16, 16, 16}, {16, 16, 16, 16}};
 };
 
 namespace {
@@ -552,9 +573,214 @@ void drop_graphs(trx_handle_t h) {
     h->graphs.clear();
 }
 
+int bucket_of(int64_t k) { return k <= 64 ? 0 : k <= 128 ? 1 : k <= 256 ? 2 : 3; }
+
+// Validate and map the problems to sorted canonical descriptors (host).
+int batch_descs(trx_handle_t h, int elem_bytes, int64_t count, const trx_problem_t* probs,
+                std::vector<BatchDesc>& out, const int* sb_override) {
+    out.clear();
+    out.reserve((size_t)count);
+    for (int64_t i = 0; i < count; ++i) {
+        const trx_problem_t& q = probs[i];
+        const int op = upc(q.op);
+        int info = (op == 'S' || op == 'M') ? 0 : -100;
+        if (!info)
+            info = check_args(q.side, q.uplo, q.transa, q.diag, q.m, q.n, q.A, q.lda, q.B, q.ldb);
+        const int64_t k = upc(q.side) == 'L' ? q.m : q.n;
+        if (!info && k > kBatchMaxK) info = -200;
+        if (info) {
+            snprintf(g_detail, sizeof(g_detail),
+                     "batched problem %lld: %s", (long long)i,
+                     info == -100 ? "op must be 'S' or 'M'"
+                     : info == -200 ? "order above TRX_BATCH_MAX_K"
+                                    : trx_error_string(info));
+            return TRX_ERR_INVALID_VALUE;
+        }
+        if (q.m == 0 || q.n == 0) continue;
+        BatchDesc d;
+        std::memset(&d, 0, sizeof(d));
+        if (elem_bytes == 4) {
+            const Canon<float> c = canonicalize<float>(q.side, q.uplo, q.transa, q.diag, q.m, q.n,
+                                                       static_cast<const float*>(q.A), q.lda,
+                                                       static_cast<float*>(q.B), q.ldb);
+            d.k = c.k; d.nrhs = c.nrhs; d.A = c.A; d.a_rs = c.a_rs; d.a_cs = c.a_cs;
+            d.C = c.C; d.c_rs = c.c_rs; d.c_cs = c.c_cs; d.unit = c.unit;
+        } else {
+            const Canon<double> c = canonicalize<double>(q.side, q.uplo, q.transa, q.diag, q.m,
+                                                         q.n, static_cast<const double*>(q.A),
+                                                         q.lda, static_cast<double*>(q.B), q.ldb);
+            d.k = c.k; d.nrhs = c.nrhs; d.A = c.A; d.a_rs = c.a_rs; d.a_cs = c.a_cs;
+            d.C = c.C; d.c_rs = c.c_rs; d.c_cs = c.c_cs; d.unit = c.unit;
+        }
+        d.alpha = q.alpha;
+        d.trsm = q.alpha == 0.0 ? 2 : (op == 'S' ? 1 : 0);   // 2: B := 0, A not read
+        const int b = bucket_of(d.k);
+        d.sb = sb_override ? sb_override[b] : h->tune_sb[elem_bytes == 4 ? 0 : 1][b];
+        out.push_back(d);
+    }
+    std::stable_sort(out.begin(), out.end(), [](const BatchDesc& x, const BatchDesc& y) {
+        return (double)x.k * x.k * x.nrhs > (double)y.k * y.k * y.nrhs;
+    });
+    return TRX_SUCCESS;
+}
+
+// Upload descriptors through the pinned staging buffer and launch; with
+// use_graph the launch (counter reset + kernel) replays from a cached graph.
+int batch_run(trx_handle_t h, int elem_bytes, const std::vector<BatchDesc>& d, cudaStream_t s,
+              bool use_graph) {
+    const int64_t n = (int64_t)d.size();
+    if (n == 0) return TRX_SUCCESS;
+    cudaError_t e;
+    if (n > h->b_cap) {
+        if (h->b_uploaded) cudaEventSynchronize(h->b_uploaded);
+        if (h->b_dev) cudaFree(h->b_dev);
+        if (h->b_host) cudaFreeHost(h->b_host);
+        h->b_dev = nullptr;
+        h->b_host = nullptr;
+        h->b_cap = 0;
+        const int64_t cap = std::max<int64_t>(n, 1024);
+        if ((e = cudaMalloc(&h->b_dev, cap * sizeof(BatchDesc))) != cudaSuccess ||
+            (e = cudaMallocHost(&h->b_host, cap * sizeof(BatchDesc))) != cudaSuccess)
+            return fail_cuda(e, "batch buffers");
+        h->b_cap = cap;
+        drop_graphs(h);
+    }
+    if (!h->b_counter && (e = cudaMalloc(&h->b_counter, 256)) != cudaSuccess)
+        return fail_cuda(e, "batch counter");
+    if (!h->b_uploaded &&
+        (e = cudaEventCreateWithFlags(&h->b_uploaded, cudaEventDisableTiming)) != cudaSuccess)
+        return fail_cuda(e, "batch event");
+    if ((e = cudaEventSynchronize(h->b_uploaded)) != cudaSuccess)
+        return fail_cuda(e, "batch staging wait");
+    std::memcpy(h->b_host, d.data(), n * sizeof(BatchDesc));
+    if ((e = cudaMemcpyAsync(h->b_dev, h->b_host, n * sizeof(BatchDesc), cudaMemcpyHostToDevice,
+                             s)) != cudaSuccess ||
+        (e = cudaEventRecord(h->b_uploaded, s)) != cudaSuccess)
+        return fail_cuda(e, "batch upload");
+    const int grid = h->num_sms * 2;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    cudaStreamIsCapturing(s, &cap);
+    if (!use_graph || cap != cudaStreamCaptureStatusNone) {
+        e = launch_batched(elem_bytes, h->b_dev, n, h->b_counter, grid, s);
+        return e == cudaSuccess ? TRX_SUCCESS : fail_cuda(e, "batched launch");
+    }
+    char kbuf[64];
+    snprintf(kbuf, sizeof(kbuf), "batched:%d:%lld:%p", elem_bytes, (long long)n, (void*)h->b_dev);
+    const std::string ks(kbuf);
+    ++h->tick;
+    for (auto& g : h->graphs) {
+        if (g.key == ks) {
+            g.used = h->tick;
+            e = cudaGraphLaunch(g.exec, s);
+            return e == cudaSuccess ? TRX_SUCCESS : fail_cuda(e, "cudaGraphLaunch");
+        }
+    }
+    if ((e = cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal)) !=
+        cudaSuccess)
+        return fail_cuda(e, "cudaStreamBeginCapture");
+    const cudaError_t le = launch_batched(elem_bytes, h->b_dev, n, h->b_counter, grid, h->cap_stream);
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamEndCapture(h->cap_stream, &graph);
+    if (le != cudaSuccess || e != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        return fail_cuda(le != cudaSuccess ? le : e, "batched capture");
+    }
+    cudaGraphExec_t exec = nullptr;
+    e = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return fail_cuda(e, "cudaGraphInstantiate");
+    if (h->graphs.size() >= kGraphCacheSize) {
+        auto old = std::min_element(h->graphs.begin(), h->graphs.end(),
+                                    [](const auto& a, const auto& b) { return a.used < b.used; });
+        cudaGraphExecDestroy(old->exec);
+        h->graphs.erase(old);
+    }
+    h->graphs.push_back({ks, exec, h->tick});
+    e = cudaGraphLaunch(exec, s);
+    return e == cudaSuccess ? TRX_SUCCESS : fail_cuda(e, "cudaGraphLaunch");
+}
+
 }  // namespace
 
 extern "C" {
+
+int trx_batched(trx_handle_t h, int elem_bytes, int64_t count, const trx_problem_t* problems,
+                void* stream) {
+    if (!valid(h)) return TRX_ERR_HANDLE;
+    if ((elem_bytes != 4 && elem_bytes != 8) || count < 0 || (count > 0 && !problems))
+        return TRX_ERR_INVALID_VALUE;
+    cudaError_t e = cudaSetDevice(h->device);
+    if (e != cudaSuccess) return fail_cuda(e, "cudaSetDevice");
+    pdl_enabled() = h->opt_pdl != 0;
+    std::vector<BatchDesc> d;
+    const int rc = batch_descs(h, elem_bytes, count, problems, d, nullptr);
+    if (rc != TRX_SUCCESS) return rc;
+    return batch_run(h, elem_bytes, d, reinterpret_cast<cudaStream_t>(stream), h->opt_graph != 0);
+}
+
+int trx_batched_autotune(trx_handle_t h, int elem_bytes, int64_t count,
+                         const trx_problem_t* problems, void* stream, char* json,
+                         size_t json_len) {
+    if (!valid(h)) return TRX_ERR_HANDLE;
+    if ((elem_bytes != 4 && elem_bytes != 8) || count < 0 || (count > 0 && !problems))
+        return TRX_ERR_INVALID_VALUE;
+    cudaError_t e = cudaSetDevice(h->device);
+    if (e != cudaSuccess) return fail_cuda(e, "cudaSetDevice");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const int sbs[3] = {8, 16, 32};
+    double best_ms[4] = {1e30, 1e30, 1e30, 1e30}, all_ms[4][3];
+    int best[4] = {16, 16, 16, 16};
+    cudaEvent_t e0 = get_event(h), e1 = get_event(h);
+    for (int bkt = 0; bkt < 4; ++bkt) {
+        for (int v = 0; v < 3; ++v) {
+            int ov[4] = {sbs[v], sbs[v], sbs[v], sbs[v]};
+            std::vector<BatchDesc> all, mine;
+            int rc = batch_descs(h, elem_bytes, count, problems, all, ov);
+            if (rc != TRX_SUCCESS) return rc;
+            for (auto& x : all)
+                if (bucket_of(x.k) == bkt) mine.push_back(x);
+            all_ms[bkt][v] = 0.0;
+            if (mine.empty()) continue;
+            double ms_sum = 0.0;
+            for (int rep = 0; rep < 4; ++rep) {
+                cudaEventRecord(e0, s);
+                rc = batch_run(h, elem_bytes, mine, s, false);
+                if (rc != TRX_SUCCESS) return rc;
+                cudaEventRecord(e1, s);
+                if ((e = cudaEventSynchronize(e1)) != cudaSuccess) return fail_cuda(e, "autotune");
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (rep > 0) ms_sum += ms;   // first run warms up
+            }
+            all_ms[bkt][v] = ms_sum / 3.0;
+            if (all_ms[bkt][v] < best_ms[bkt]) {
+                best_ms[bkt] = all_ms[bkt][v];
+                best[bkt] = sbs[v];
+            }
+        }
+    }
+    h->free_events.push_back(e0);
+    h->free_events.push_back(e1);
+    const int t = elem_bytes == 4 ? 0 : 1;
+    for (int bkt = 0; bkt < 4; ++bkt) h->tune_sb[t][bkt] = best[bkt];
+    drop_graphs(h);
+    if (json && json_len) {
+        std::string out = std::string("{\"dtype\": \"") + (t ? "f64" : "f32") + "\", \"buckets\": [";
+        const int kmax[4] = {64, 128, 256, 512};
+        char buf[256];
+        for (int bkt = 0; bkt < 4; ++bkt) {
+            snprintf(buf, sizeof(buf),
+                     "%s{\"kmax\": %d, \"sb\": %d, \"ms\": {\"8\": %.5f, \"16\": %.5f, \"32\": %.5f}}",
+                     bkt ? ", " : "", kmax[bkt], best[bkt], all_ms[bkt][0], all_ms[bkt][1],
+                     all_ms[bkt][2]);
+            out += buf;
+        }
+        out += "]}";
+        if (out.size() + 1 > json_len) return TRX_ERR_INVALID_VALUE;
+        std::memcpy(json, out.c_str(), out.size() + 1);
+    }
+    return TRX_SUCCESS;
+}
 
 int trx_create(trx_handle_t* handle, int device, size_t workspace_bytes) {
     if (!handle) return TRX_ERR_HANDLE;
@@ -580,7 +806,7 @@ int trx_create(trx_handle_t* handle, int device, size_t workspace_bytes) {
     if ((e = cudaMalloc(&h->d_err, 256)) != cudaSuccess ||
         (e = cudaMemset(h->d_err, 0, 256)) != cudaSuccess ||
         (e = cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking)) != cudaSuccess ||
-        (e = leaf_configure_all()) != cudaSuccess) {
+        (e = leaf_configure_all()) != cudaSuccess || (e = batched_configure()) != cudaSuccess) {
         trx_destroy(h);
         return fail_cuda(e, "handle setup");
     }
@@ -610,6 +836,10 @@ int trx_destroy(trx_handle_t h) {
         cudaEventDestroy(p.e1);
     }
     for (auto ev : h->free_events) cudaEventDestroy(ev);
+    if (h->b_dev) cudaFree(h->b_dev);
+    if (h->b_counter) cudaFree(h->b_counter);
+    if (h->b_host) cudaFreeHost(h->b_host);
+    if (h->b_uploaded) cudaEventDestroy(h->b_uploaded);
     free_owned_ws(h);
     if (h->d_err) cudaFree(h->d_err);
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);

@@ -1,0 +1,217 @@
+// Batched uneven TRSM / TRMM: thousands of small independent problems
+// (order k <= 512) in one persistent launch.
+//
+// Each problem is first mapped on the host to the canonical lower form of
+// common.cuh (any side/uplo/trans/diag, TRSM or TRMM). The descriptors are
+// sorted by cost (k^2 * nrhs, largest first) and the CTAs of one persistent
+// grid take them from an atomic counter, so big problems start first and
+// the tail is filled with small ones.
+//
+// Inside a CTA a problem runs the same blocked scheme as the blocked leaf:
+// the right-hand sides are staged in shared memory in chunks of NC columns
+// (k rows x NC, row-major), and the rows are taken sb at a time
+// (sb = 8, 16 or 32, per problem from the tuning table):
+//   TRSM (forward): substitution on the sb-row diagonal block (one thread per
+//     column), then a rank-sb update of every row below it;
+//   TRMM: row blocks from the bottom up, each new block
+//     alpha * sum_{l <= i} M(i,l) C(l,:) formed from rows that are still
+//     original (all rows above it), then written in place.
+// M is read through the read-only cache (its rows are reused across the
+// column groups of a CTA). Problems with k > 512 belong to the plain
+// recursive entry points.
+#include <algorithm>
+
+#include "common.cuh"
+
+namespace trx {
+
+struct BatchDesc {
+    int64_t k, nrhs;
+    const void* A;
+    int64_t a_rs, a_cs;
+    void* C;
+    int64_t c_rs, c_cs;
+    double alpha;
+    int unit, trsm, sb, pad;
+};
+
+constexpr int kBatchMaxK = 512;
+
+namespace {
+
+template <typename T>
+struct BShape {
+    static constexpr int NT = 256;
+    static constexpr int NC = sizeof(T) == 4 ? 32 : 16;    // columns per chunk
+    static constexpr int LDC = NC + 4;
+    static constexpr int CG = NC / 4;                      // column groups of 4
+    static constexpr int RG = NT / CG;                     // row groups
+    static constexpr size_t smem = sizeof(T) * ((size_t)kBatchMaxK * LDC + kBatchMaxK);
+};
+
+template <typename T>
+__device__ __forceinline__ T ldA(const T* A, int64_t i, int64_t l, int64_t rs, int64_t cs) {
+    return __ldg(A + i * rs + l * cs);
+}
+
+template <typename T, int SB>
+__device__ void trsm_chunk(const BatchDesc& d, T* sC, const T* sD, int k) {
+    using S = BShape<T>;
+    const int tid = threadIdx.x;
+    const T* A = static_cast<const T*>(d.A);
+    const int cg = tid % S::CG, rg = tid / S::CG;
+    for (int s0 = 0; s0 < k; s0 += SB) {
+        const int sbn = min(SB, k - s0);
+        if (tid < S::NC) {
+            T x[SB];
+#pragma unroll
+            for (int q = 0; q < SB; ++q) x[q] = q < sbn ? sC[(s0 + q) * S::LDC + tid] : T(0);
+            // Rows past k (a ragged last block) stay zero: their diagonal
+            // factor is 1 and their entries of M are not read.
+#pragma unroll
+            for (int jj = 0; jj < SB; ++jj) {
+                x[jj] *= (jj < sbn) ? sD[s0 + jj] : T(1);
+#pragma unroll
+                for (int q = jj + 1; q < SB; ++q) {
+                    const T t = (q < sbn) ? ldA(A, s0 + q, s0 + jj, d.a_rs, d.a_cs) : T(0);
+                    x[q] = fma(-t, x[jj], x[q]);
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < SB; ++q)
+                if (q < sbn) sC[(s0 + q) * S::LDC + tid] = x[q];
+        }
+        __syncthreads();
+        for (int i = s0 + SB + rg; i < k; i += S::RG) {
+            T acc[4] = {T(0), T(0), T(0), T(0)};
+#pragma unroll
+            for (int kk = 0; kk < SB; ++kk) {
+                const T t = ldA(A, i, s0 + kk, d.a_rs, d.a_cs);
+#pragma unroll
+                for (int v = 0; v < 4; ++v) acc[v] = fma(t, sC[(s0 + kk) * S::LDC + 4 * cg + v], acc[v]);
+            }
+#pragma unroll
+            for (int v = 0; v < 4; ++v) sC[i * S::LDC + 4 * cg + v] -= acc[v];
+        }
+        __syncthreads();
+    }
+}
+
+template <typename T, int SB>
+__device__ void trmm_chunk(const BatchDesc& d, T* sC, const T* sD, int k, T alpha) {
+    using S = BShape<T>;
+    const int tid = threadIdx.x;
+    const T* A = static_cast<const T*>(d.A);
+    const int cg = tid % S::CG, rg = tid / S::CG;
+    const int nblk = (k + SB - 1) / SB;
+    for (int bi = nblk - 1; bi >= 0; --bi) {
+        const int s0 = bi * SB;
+        const int sbn = min(SB, k - s0);
+        // rows s0 .. s0+sbn-1, one row per row group (SB <= RG)
+        T acc[4] = {T(0), T(0), T(0), T(0)};
+        const int i = s0 + rg;
+        if (rg < sbn) {
+            for (int l = 0; l < i; ++l) {
+                const T t = ldA(A, i, l, d.a_rs, d.a_cs);
+#pragma unroll
+                for (int v = 0; v < 4; ++v) acc[v] = fma(t, sC[l * S::LDC + 4 * cg + v], acc[v]);
+            }
+#pragma unroll
+            for (int v = 0; v < 4; ++v) acc[v] = fma(sD[i], sC[i * S::LDC + 4 * cg + v], acc[v]);
+        }
+        __syncthreads();   // every read of the block's original rows is done
+        if (rg < sbn) {
+#pragma unroll
+            for (int v = 0; v < 4; ++v) sC[i * S::LDC + 4 * cg + v] = alpha * acc[v];
+        }
+        __syncthreads();
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) batched_kernel(const BatchDesc* descs, int64_t count,
+                                                      int* counter) {
+    using S = BShape<T>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* sC = reinterpret_cast<T*>(smem_raw);         // panel: row i, column c at i*LDC + c
+    T* sD = sC + (size_t)kBatchMaxK * S::LDC;         // reciprocal (TRSM) or plain (TRMM) diagonal
+    __shared__ int s_next;
+    pdl_trigger();
+    pdl_wait();
+    const int tid = threadIdx.x;
+    while (true) {
+        if (tid == 0) s_next = atomicAdd(counter, 1);
+        __syncthreads();
+        const int64_t idx = s_next;
+        __syncthreads();
+        if (idx >= count) break;
+        const BatchDesc d = descs[idx];
+        const int k = (int)d.k;
+        const T* A = static_cast<const T*>(d.A);
+        T* C = static_cast<T*>(d.C);
+        if (d.trsm == 2) {   // alpha == 0: B := 0, A is not read
+            for (int64_t e = tid; e < d.k * d.nrhs; e += S::NT)
+                C[(e % d.k) * d.c_rs + (e / d.k) * d.c_cs] = T(0);
+            continue;
+        }
+        for (int i = tid; i < k; i += S::NT) {
+            T dg = T(1);
+            if (!d.unit) dg = A[(int64_t)i * (d.a_rs + d.a_cs)];
+            sD[i] = d.trsm ? T(1) / dg : dg;
+        }
+        for (int64_t c0 = 0; c0 < d.nrhs; c0 += S::NC) {
+            const int ncols = (int)min((int64_t)S::NC, d.nrhs - c0);
+            // stage the chunk; rows fastest when C's rows are contiguous
+            const bool row_fast = (d.c_rs == 1 || d.c_rs == -1);
+            for (int e = tid; e < k * S::NC; e += S::NT) {
+                const int i = row_fast ? e % k : e / S::NC, c = row_fast ? e / k : e % S::NC;
+                T v = T(0);
+                if (c < ncols) v = C[i * d.c_rs + (c0 + c) * d.c_cs];
+                sC[i * S::LDC + c] = d.trsm ? (T)d.alpha * v : v;
+            }
+            __syncthreads();
+            if (d.trsm) {
+                if (d.sb == 8) trsm_chunk<T, 8>(d, sC, sD, k);
+                else if (d.sb == 32) trsm_chunk<T, 32>(d, sC, sD, k);
+                else trsm_chunk<T, 16>(d, sC, sD, k);
+            } else {
+                if (d.sb == 8) trmm_chunk<T, 8>(d, sC, sD, k, (T)d.alpha);
+                else if (d.sb == 32) trmm_chunk<T, 32>(d, sC, sD, k, (T)d.alpha);
+                else trmm_chunk<T, 16>(d, sC, sD, k, (T)d.alpha);
+            }
+            for (int e = tid; e < k * S::NC; e += S::NT) {
+                const int i = row_fast ? e % k : e / S::NC, c = row_fast ? e / k : e % S::NC;
+                if (c < ncols) C[i * d.c_rs + (c0 + c) * d.c_cs] = sC[i * S::LDC + c];
+            }
+            __syncthreads();
+        }
+    }
+}
+
+}  // namespace
+
+cudaError_t batched_configure() {
+    cudaError_t e = cudaFuncSetAttribute(batched_kernel<float>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)BShape<float>::smem);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(batched_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)BShape<double>::smem);
+}
+
+// descs: device array of `count` descriptors sorted largest first; counter:
+// device int, zeroed here before the launch. grid_ctas persistent CTAs.
+cudaError_t launch_batched(int elem_bytes, const BatchDesc* descs, int64_t count, int* counter,
+                           int grid_ctas, cudaStream_t s) {
+    if (count <= 0) return cudaSuccess;
+    cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(int), s);
+    if (e != cudaSuccess) return e;
+    const int grid = (int)std::min<int64_t>(grid_ctas, count);
+    if (elem_bytes == 4)
+        return launch_kernel(batched_kernel<float>, dim3(grid), dim3(256), BShape<float>::smem, s,
+                             descs, count, counter);
+    return launch_kernel(batched_kernel<double>, dim3(grid), dim3(256), BShape<double>::smem, s,
+                         descs, count, counter);
+}
+
+}  // namespace trx

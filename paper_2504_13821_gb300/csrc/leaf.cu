@@ -84,7 +84,10 @@ cudaError_t launch_leaf(bool trsm, const Canon<T>& p, int64_t r0, int b,
         return e ? std::atoi(e) : 0;
     }();
     if (forced == 1 || forced == 4 || forced == 8 || forced == 16) G = forced;
-    const int64_t max_ctas = (int64_t)(num_sms > 0 ? num_sms : 1) * 4;
+    // One leaf: a few CTAs per SM walk its panels. Many leaves at once (the
+    // level-batched TRMM): enough CTAs that panel latencies overlap across
+    // CTAs instead of queueing inside each.
+    const int64_t max_ctas = (int64_t)(num_sms > 0 ? num_sms : 1) * (nleaves > 1 ? 32 : 4);
     return trsm ? leaf_dispatch<T, true>(a, nleaves, G, max_ctas, s)
                 : leaf_dispatch<T, false>(a, nleaves, G, max_ctas, s);
 }
