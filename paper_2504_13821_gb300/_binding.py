@@ -317,20 +317,38 @@ def _problem_array(problems):
     return arr, (elem or 4)
 
 
+class Batch:
+    """A batch of (op, side, uplo, trans, diag, alpha, A, B) problems with
+    its trx_problem_t array built once; run() can be called repeatedly
+    (the tensors are referenced, not copied)."""
+
+    def __init__(self, problems):
+        self.problems = list(problems)
+        self.array, self.elem = _problem_array(self.problems)
+        self.device = self.problems[0][7].device if self.problems else None
+
+    def __len__(self):
+        return len(self.problems)
+
+    def run(self, *, handle: Handle | None = None, stream=None):
+        import torch
+        if not self.problems:
+            return
+        lib = load_library()
+        h = handle if handle is not None else default_handle(self.device)
+        if stream is None:
+            stream = torch.cuda.current_stream(self.device)
+        s_ptr = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+        _check(lib.trx_batched(h.ptr, self.elem, len(self.problems), self.array, s_ptr),
+               "trx_batched")
+
+
 def batched(problems, *, handle: Handle | None = None, stream=None):
     """Run many small TRSM ('S') / TRMM ('M') problems in one persistent
-    launch. problems: list of (op, side, uplo, trans, diag, alpha, A, B)."""
-    import torch
-    lib = load_library()
-    if not problems:
-        return
-    arr, elem = _problem_array(problems)
-    dev = problems[0][7].device
-    h = handle if handle is not None else default_handle(dev)
-    if stream is None:
-        stream = torch.cuda.current_stream(dev)
-    s_ptr = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
-    _check(lib.trx_batched(h.ptr, elem, len(problems), arr, s_ptr), "trx_batched")
+    launch. problems: list of (op, side, uplo, trans, diag, alpha, A, B), or
+    a prepared Batch."""
+    b = problems if isinstance(problems, Batch) else Batch(problems)
+    b.run(handle=handle, stream=stream)
 
 
 def batched_autotune(problems, *, handle: Handle | None = None, stream=None) -> dict:
