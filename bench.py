@@ -459,13 +459,15 @@ def run_serving(args):
             live[fid] = [A, int(rng.integers(1, 51)), dtype, k, uplo]
         live[fid][1] -= 1
         k = live[fid][3]
-        if live[fid][1] == 0:
-            srv.release(fid)        # freed once its submitted requests complete
+        last_use = live[fid][1] == 0
+        if last_use:
             live.pop(fid)
         nrhs = int(round(np.exp(rng.uniform(0, np.log(1024)))))
         op = "S" if rng.random() < 0.7 else "M"
         B = torch.randn(nrhs, k, device=dev, dtype=dtype).t()     # column-major k x nrhs
         srv.submit(serving.Request(submitted, fid, op, "L", 1.5, B, t_arr))
+        if last_use:
+            srv.release(fid)        # freed once its submitted requests complete
         submitted += 1
         flops += float(k) * k * nrhs
         while time.perf_counter() < t_arr - 0.002:
