@@ -66,7 +66,10 @@ enum {
 /* Options for trx_set_option(). */
 enum {
     TRX_OPT_LEAF = 1,      /* leaf cutoff b (Section 3.1 "chosen threshold"):
-                              16, 32, 64 or 128; 0 = automatic (default)   */
+                              16, 32, 64, 128 or 256 (TRSM only; TRMM
+                              stops at 128); 0 = automatic (default): 64,
+                              or 256 for TRSM with >= 4096 right-hand
+                              sides (block leaves)                         */
     TRX_OPT_GEMM = 2,      /* FP32 GEMM-update engine: 0 automatic, 1 CUDA
                               cores (FP32 FMA), 2 tensor cores (tcgen05,
                               3-term split BF16, FP32 accumulation)         */

@@ -40,6 +40,7 @@ namespace {
 
 constexpr int kMagic = 0x54525831;  // "TRX1"
 constexpr int kDefaultLeaf = 64;
+constexpr int64_t kBlockLeafMinRhs = 4096;
 constexpr long long kDefaultWaitNs = 2000000000LL;   // 2 s
 constexpr int64_t kTcMinOrder = 256;                 // auto: tensor cores from this order
 constexpr size_t kGraphCacheSize = 16;
@@ -317,8 +318,15 @@ cudaEvent_t get_event(trx_handle_t h) {
     return e;
 }
 
-int leaf_for(trx_handle_t h, int64_t k) {
-    int b = h->opt_leaf > 0 ? (int)h->opt_leaf : kDefaultLeaf;
+// Recursion cutoff: the handle's TRX_OPT_LEAF, else 64 — or 256 for a TRSM
+// with many right-hand sides, whose leaves then run as block leaves (one
+// launch replaces the bottom three recursion levels). TRMM leaves stop at
+// 128 rows.
+int leaf_for(trx_handle_t h, int64_t k, bool trsm = false, int64_t nrhs = 0) {
+    int b = kDefaultLeaf;
+    if (h->opt_leaf > 0) b = (int)h->opt_leaf;
+    else if (trsm && nrhs >= kBlockLeafMinRhs) b = kMaxBlockLeaf;
+    if (!trsm && b > kMaxLeaf) b = kMaxLeaf;
     return (int)std::min<int64_t>(b, std::max<int64_t>(k, 1));
 }
 
@@ -439,7 +447,7 @@ int execute(trx_handle_t h, bool trsm, char side, char uplo, char transa, char d
     ex.s = s;
     ex.profile = h->opt_profile != 0;
     const int64_t k = ex.c.k;
-    const int b = leaf_for(h, k);
+    const int b = leaf_for(h, k, trsm, ex.c.nrhs);
 
     Plan plan;
     plan.tc = use_tc<T>(h, k);
@@ -963,7 +971,8 @@ int trx_set_option(trx_handle_t h, int option, int64_t value) {
     if (!valid(h)) return TRX_ERR_HANDLE;
     switch (option) {
         case TRX_OPT_LEAF:
-            if (value != 0 && value != 16 && value != 32 && value != 64 && value != 128)
+            if (value != 0 && value != 16 && value != 32 && value != 64 && value != 128 &&
+                value != 256)
                 return TRX_ERR_INVALID_VALUE;
             h->opt_leaf = value;
             break;
@@ -1073,13 +1082,18 @@ int trx_debug_plan(char op, char side, char uplo, char transa, char diag, int64_
                                 "", std::max<int64_t>(1, m));
     if (info) return info;
     if ((upc(op) != 'S' && upc(op) != 'M') || (elem_bytes != 4 && elem_bytes != 8) ||
-        (leaf != 0 && leaf != 16 && leaf != 32 && leaf != 64 && leaf != 128) || gemm_mode < 0 ||
+        (leaf != 0 && leaf != 16 && leaf != 32 && leaf != 64 && leaf != 128 && leaf != 256) ||
+        gemm_mode < 0 ||
         gemm_mode > 2 || !buf || buflen == 0)
         return TRX_ERR_INVALID_VALUE;
     buf[0] = 0;
     const int64_t k = upc(side) == 'L' ? m : n;
     if (m == 0 || n == 0) return TRX_SUCCESS;
-    const int b = (int)std::min<int64_t>(leaf > 0 ? leaf : kDefaultLeaf, std::max<int64_t>(k, 1));
+    const bool is_trsm = upc(op) == 'S';
+    const int64_t nrhs = upc(side) == 'L' ? n : m;
+    int b = leaf > 0 ? leaf : (is_trsm && nrhs >= kBlockLeafMinRhs ? kMaxBlockLeaf : kDefaultLeaf);
+    if (!is_trsm && b > kMaxLeaf) b = kMaxLeaf;
+    b = (int)std::min<int64_t>(b, std::max<int64_t>(k, 1));
     Plan plan;
     plan.tc = use_tc_mode(elem_bytes, gemm_mode, k, b);
     make_plan(plan, upc(op) == 'S', k, b, 2.0);

@@ -96,8 +96,10 @@ cudaError_t launch_leaf(bool trsm, const Canon<T>& p, int64_t r0, int b,
                         int64_t nleaves, T alpha, const Planes* planes,
                         int num_sms, cudaStream_t s);
 
-// Largest leaf the kernels support.
+// Largest leaf the kernels support; single TRSM leaves go up to
+// kMaxBlockLeaf rows (the block-leaf kernel).
 constexpr int kMaxLeaf = 128;
+constexpr int kMaxBlockLeaf = 256;
 
 // CUDA-core GEMM update on the canonical matrices:
 //   C[rc+i, j] = beta*C[rc+i, j] + gamma * sum_l M(rc+i, rk+l) * Y[rk+l, j]

@@ -34,6 +34,15 @@ extern template cudaError_t leaf_blocked_configure<double>();
 extern template cudaError_t leaf_blocked_launch<float>(const LeafArgs<float>&, int64_t, cudaStream_t);
 extern template cudaError_t leaf_blocked_launch<double>(const LeafArgs<double>&, int64_t, cudaStream_t);
 
+template <typename T>
+cudaError_t leaf_b256_configure();
+template <typename T>
+cudaError_t leaf_b256_launch(const LeafArgs<T>& a, cudaStream_t s);
+extern template cudaError_t leaf_b256_configure<float>();
+extern template cudaError_t leaf_b256_configure<double>();
+extern template cudaError_t leaf_b256_launch<float>(const LeafArgs<float>&, cudaStream_t);
+extern template cudaError_t leaf_b256_launch<double>(const LeafArgs<double>&, cudaStream_t);
+
 cudaError_t leaf_configure_all() {
     cudaError_t e;
     if ((e = leaf_configure<float, true>()) != cudaSuccess) return e;
@@ -42,6 +51,8 @@ cudaError_t leaf_configure_all() {
     if ((e = leaf_configure<double, false>()) != cudaSuccess) return e;
     if ((e = leaf_blocked_configure<float>()) != cudaSuccess) return e;
     if ((e = leaf_blocked_configure<double>()) != cudaSuccess) return e;
+    if ((e = leaf_b256_configure<float>()) != cudaSuccess) return e;
+    if ((e = leaf_b256_configure<double>()) != cudaSuccess) return e;
     return tc_configure();
 }
 
@@ -49,7 +60,8 @@ template <typename T>
 cudaError_t launch_leaf(bool trsm, const Canon<T>& p, int64_t r0, int b,
                         int64_t nleaves, T alpha, const Planes* planes,
                         int num_sms, cudaStream_t s) {
-    if (b < 1 || b > kMaxLeaf || nleaves < 1 || nleaves > 65535) return cudaErrorInvalidValue;
+    if (b < 1 || nleaves < 1 || nleaves > 65535) return cudaErrorInvalidValue;
+    if (b > kMaxLeaf && !(trsm && nleaves == 1 && b <= kMaxBlockLeaf)) return cudaErrorInvalidValue;
     if (p.nrhs <= 0) return cudaSuccess;
     LeafArgs<T> a;
     a.p = p;
@@ -65,6 +77,7 @@ cudaError_t launch_leaf(bool trsm, const Canon<T>& p, int64_t r0, int b,
         const char* e = std::getenv("TRX_LEAF_BLOCKED");
         return !(e && e[0] == '0');
     }();
+    if (trsm && b > kMaxLeaf) return leaf_b256_launch<T>(a, s);   // block leaf, 129..256 rows
     if (blocked_on && trsm && nleaves == 1 && b > 32 && p.nrhs >= 1024)
         return leaf_blocked_launch<T>(a, (int64_t)(num_sms > 0 ? num_sms : 1) * 2, s);
 

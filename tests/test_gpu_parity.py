@@ -37,7 +37,7 @@ def test_all_variants(trx, op, side, uplo, trans, diag, dtype):
 
 @pytest.mark.parametrize("op", ["trsm", "trmm"])
 @pytest.mark.parametrize("engine", [1, 2], ids=["cuda_cores", "tensor_cores"])
-@pytest.mark.parametrize("leaf", [16, 32, 64, 128])
+@pytest.mark.parametrize("leaf", [16, 32, 64, 128, 256])
 @pytest.mark.parametrize("variant", [("L", "L", "N", "N"), ("R", "U", "T", "U"),
                                      ("L", "U", "N", "U"), ("R", "L", "N", "N")])
 def test_leaf_and_engine_sweep(trx, op, engine, leaf, variant):
@@ -48,6 +48,16 @@ def test_leaf_and_engine_sweep(trx, op, engine, leaf, variant):
     m, n = (1000, 300) if side == "L" else (300, 1000)
     run_case(op, *variant, m, n, -2.0, np.float32, seed=leaf + engine, handle=h)
     h.close()
+
+
+@pytest.mark.parametrize("dtype", [np.float32, np.float64], ids=["f32", "f64"])
+@pytest.mark.parametrize("side,uplo,trans,diag", VARIANTS)
+def test_block_leaves_all_variants(trx, side, uplo, trans, diag, dtype):
+    """TRSM with >= 4096 right-hand sides takes 256-row block leaves (and a
+    ragged last one: k = 600)."""
+    m, n = (600, 4200) if side == "L" else (4200, 600)
+    run_case("trsm", side, uplo, trans, diag, m, n, 1.5, dtype,
+             seed=inputs.variant_seed(600, VARIANTS.index((side, uplo, trans, diag))))
 
 
 @pytest.mark.parametrize("op", ["trsm", "trmm"])

@@ -49,10 +49,12 @@ def coverage(k, steps):
 
 @pytest.mark.parametrize("op", ["S", "M"])
 @pytest.mark.parametrize("gemm", [1, 2])
-@pytest.mark.parametrize("b", LEAVES)
+@pytest.mark.parametrize("b", LEAVES + [256])
 @pytest.mark.parametrize("k", SIZES + [4097])
 def test_blocks_tile_the_triangle_once(op, gemm, b, k):
     steps = debug_plan(op, "L", "L", "N", "N", k, 5, 4, b, gemm)
+    if op == "M":
+        b = min(b, 128)          # TRMM leaves stop at 128 rows
     cnt = coverage(k, steps)
     low = np.tril(np.ones((k, k), dtype=bool))
     assert np.all(cnt[low] == 1)
@@ -63,10 +65,11 @@ def test_blocks_tile_the_triangle_once(op, gemm, b, k):
             if s["tc"]:
                 assert s["klen"] % 64 == 0 and s["rk"] % 8 == 0
         if s["kind"] == "leaf":
-            assert s["b"] <= 128 and s["r0"] % min(b, max(k, 1)) == 0
+            assert s["b"] <= (256 if op == "S" else 128)
+            assert s["r0"] % min(b, max(k, 1)) == 0
 
 
-@pytest.mark.parametrize("b", LEAVES)
+@pytest.mark.parametrize("b", LEAVES + [256])
 @pytest.mark.parametrize("k", SIZES)
 def test_trsm_dependency_order_and_alpha(b, k):
     steps = debug_plan("S", "L", "L", "N", "N", k, 5, 4, b, 2)
@@ -153,6 +156,19 @@ def test_trmm_level_batching():
         for s in g:
             rows[s["rc"]:s["rc"] + s["mlen"]] += 1
         assert rows.max() == 1
+
+
+def test_trsm_block_leaves_for_many_rhs():
+    # auto cutoff: 256-row block leaves once there are >= 4096 right-hand sides
+    leaves = [s for s in debug_plan("S", "L", "L", "N", "N", 16384, 16384, 4, 0, 0)
+              if s["kind"] == "leaf"]
+    assert len(leaves) == 64 and all(s["b"] == 256 for s in leaves)
+    leaves = [s for s in debug_plan("S", "L", "L", "N", "N", 16384, 256, 4, 0, 0)
+              if s["kind"] == "leaf"]
+    assert len(leaves) == 256
+    leaves = [s for s in debug_plan("M", "L", "L", "N", "N", 16384, 16384, 4, 0, 0)
+              if s["kind"] == "leaf"]
+    assert leaves[0]["b"] == 64
 
 
 def test_fp64_and_small_orders_use_cuda_cores():
