@@ -222,6 +222,8 @@ def run_gpu(args):
     h = trx.Handle(dev)
     if args.pdl:
         h.set_option(trx.OPT_PDL, 1)
+    if args.panels:
+        h.set_option(trx.OPT_PANELS, args.panels)
     if args.leaf:
         h.set_option(trx.OPT_LEAF, args.leaf)
         global LEAF_USED
@@ -444,7 +446,7 @@ def run_serving(args):
         t_arr += rng.exponential(1.0 / args.rate)
         if t_arr - t_start > args.duration:
             break
-        dtype = torch.float32 if rng.random() < 0.5 else torch.float64
+        dtype = torch.float64 if rng.random() < args.fp64_share else torch.float32
         cands = [f for f, v in live.items() if v[2] == dtype and v[1] > 0]
         if cands and rng.random() < 0.9:
             fid = cands[int(rng.integers(len(cands)))]
@@ -481,8 +483,8 @@ def run_serving(args):
             "dtype": "f32+f64", "data": "synthetic",
             "config": {"workload": f"Poisson {args.rate}/s for {args.duration} s, 70% TRSM, "
                                    "m log-uniform 64..8192, nrhs log-uniform 1..1024, "
-                                   "half FP32 half FP64, factors reused 1..50 times, "
-                                   "150 GB admission cap",
+                                   f"{args.fp64_share:.0%} FP64 (rest FP32), factors reused "
+                                   "1..50 times, 150 GB admission cap",
                        "requests": submitted, "offered_tflops": flops / args.duration / 1e12},
             "latency": st}
     print(json.dumps(line), flush=True)
@@ -500,12 +502,15 @@ def main(argv=None):
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
     ap.add_argument("--leaf", type=int, default=0, help="recursion cutoff b (0: library default)")
     ap.add_argument("--pdl", action="store_true", help="launch with programmatic dependent launch")
+    ap.add_argument("--panels", type=int, default=0, help="TRSM column-panel branches (0: auto)")
     ap.add_argument("--k", type=int, default=16384,
                     help="order of A (default 16384; smaller only for profiling runs)")
     ap.add_argument("--nrhs", type=int, default=16384, help="right-hand sides (default 16384)")
     ap.add_argument("--dtype", default="f32", choices=["f32", "f64"])
     ap.add_argument("--rate", type=float, default=2000.0, help="serving: arrivals per second")
     ap.add_argument("--duration", type=float, default=60.0, help="serving: seconds of arrivals")
+    ap.add_argument("--fp64-share", type=float, default=0.5,
+                    help="serving: fraction of FP64 requests (the rest FP32)")
     ap.add_argument("--workload", default="square", choices=["square", "batched", "serving"],
                     help="square: the n=16384 TRSM+TRMM step (default); batched: "
                          "4096 small uneven problems in one launch")

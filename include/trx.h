@@ -66,10 +66,9 @@ enum {
 /* Options for trx_set_option(). */
 enum {
     TRX_OPT_LEAF = 1,      /* leaf cutoff b (Section 3.1 "chosen threshold"):
-                              16, 32, 64, 128 or 256 (TRSM only; TRMM
-                              stops at 128); 0 = automatic (default): 64,
-                              or 256 for TRSM with >= 4096 right-hand
-                              sides (block leaves)                         */
+                              16, 32, 64, 128 or 256 (256: TRSM block
+                              leaves; TRMM stops at 128); 0 = automatic
+                              (default, 64)                                */
     TRX_OPT_GEMM = 2,      /* FP32 GEMM-update engine: 0 automatic, 1 CUDA
                               cores (FP32 FMA), 2 tensor cores (tcgen05,
                               3-term split BF16, FP32 accumulation)         */
@@ -81,6 +80,11 @@ enum {
     TRX_OPT_WAIT_LIMIT = 5,/* nanoseconds a device-side wait may spin
                               before it gives up and the launch reports
                               TRX_ERR_TIMEOUT (default 2e9, minimum 1000) */
+    TRX_OPT_PANELS = 7,    /* TRSM column-panel branches (right-hand sides
+                              are independent; each panel runs its own
+                              recursion chain on its own stream, all in one
+                              graph): 1..4, 0 = automatic (default: one per
+                              4096 right-hand sides, at most 4)            */
     TRX_OPT_PDL = 6        /* 1: launch the chain's kernels with
                               programmatic dependent launch, so each one's
                               prologue overlaps the previous one's tail;

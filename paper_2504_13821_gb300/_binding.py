@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(_PKG, "libtrx.so")
 HEADER = os.path.join(os.path.dirname(_PKG), "include", "trx.h")
 
 # Option and kernel-class codes (mirrors include/trx.h).
-OPT_LEAF, OPT_GEMM, OPT_GRAPH, OPT_PROFILE, OPT_WAIT_LIMIT, OPT_PDL = 1, 2, 3, 4, 5, 6
+OPT_LEAF, OPT_GEMM, OPT_GRAPH, OPT_PROFILE, OPT_WAIT_LIMIT, OPT_PDL, OPT_PANELS = 1, 2, 3, 4, 5, 6, 7
 GEMM_AUTO, GEMM_SIMT, GEMM_TC = 0, 1, 2
 KERNEL_CLASSES = ("leaf_trsm", "leaf_trmm", "gemm_tc", "gemm_simt", "convert", "other")
 ERR_TIMEOUT = 4

@@ -40,11 +40,15 @@ namespace {
 
 constexpr int kMagic = 0x54525831;  // "TRX1"
 constexpr int kDefaultLeaf = 64;
-constexpr int64_t kBlockLeafMinRhs = 4096;
+// Auto cutoff never picks block leaves (measured slower than 64-row leaves
+// plus small updates at 16384 right-hand sides); TRX_OPT_LEAF = 256 does.
+constexpr int64_t kBlockLeafMinRhs = INT64_MAX;
 constexpr long long kDefaultWaitNs = 2000000000LL;   // 2 s
 constexpr int64_t kTcMinOrder = 256;                 // auto: tensor cores from this order
 constexpr size_t kGraphCacheSize = 16;
 constexpr int64_t kBatchMaxK = TRX_BATCH_MAX_K;
+constexpr int kMaxPanels = 4;
+constexpr int64_t kPanelMinCols = 4096;   // auto: a branch per 4096 right-hand sides
 
 thread_local char g_detail[256] = "";
 
@@ -202,8 +206,8 @@ void plan_trmm_levels(Plan& pl, int64_t k, int b, double alpha) {
 
 // The whole launch sequence of one call: operand planes (tensor-core path),
 // then the recursion of Section 3.1.
-void make_plan(Plan& plan, bool trsm, int64_t k, int b, double alpha) {
-    if (plan.tc) plan.steps.push_back(Step{kConvM});
+void make_plan(Plan& plan, bool trsm, int64_t k, int b, double alpha, bool conv_m = true) {
+    if (plan.tc && conv_m) plan.steps.push_back(Step{kConvM});
     if (trsm) {
         plan_trsm(plan, 0, k, true, b, alpha);
     } else {
@@ -301,6 +305,10 @@ struct trx_handle_s {
     int64_t b_cap = 0;
     cudaEvent_t b_uploaded = nullptr;
     int tune_sb[2][4] = {{16, 16, 16, 16}, {16, 16, 16, 16}};
+    // column-panel branches of a TRSM: streams and fork/join events
+    int64_t opt_panels = 0;
+    cudaStream_t aux[kMaxPanels] = {};
+    cudaEvent_t fork_ev = nullptr, join_ev[kMaxPanels] = {};
 };
 
 namespace {
@@ -318,9 +326,8 @@ cudaEvent_t get_event(trx_handle_t h) {
     return e;
 }
 
-// Recursion cutoff: the handle's TRX_OPT_LEAF, else 64 — or 256 for a TRSM
-// with many right-hand sides, whose leaves then run as block leaves (one
-// launch replaces the bottom three recursion levels). TRMM leaves stop at
+// Recursion cutoff: the handle's TRX_OPT_LEAF, else 64. With 256 a TRSM's
+// leaves run as block leaves (one launch per 256 rows); TRMM leaves stop at
 // 128 rows.
 int leaf_for(trx_handle_t h, int64_t k, bool trsm = false, int64_t nrhs = 0) {
     int b = kDefaultLeaf;
@@ -423,7 +430,7 @@ struct GraphKey {
     const void* ws;
     double alpha;
     long long wait_ns;
-    int pdl;
+    int pdl, panels;
 };
 
 template <typename T>
@@ -465,17 +472,68 @@ int execute(trx_handle_t h, bool trsm, char side, char uplo, char transa, char d
         ex.pl.m_lo = reinterpret_cast<__nv_bfloat16*>(base + w.m_bytes);
         ex.pl.y_hi = reinterpret_cast<__nv_bfloat16*>(base + 2 * w.m_bytes);
         ex.pl.y_lo = reinterpret_cast<__nv_bfloat16*>(base + 2 * w.m_bytes + w.y_bytes);
-        h->maps.resize(tc_maps_size());
-        e = tc_make_maps(ex.pl, k, ex.c.nrhs, h->maps.data());
-        if (e != cudaSuccess) return fail_cuda(e, "tensor map encode");
-        ex.maps = h->maps.data();
     }
-    make_plan(plan, trsm, k, b, (double)alpha);
+    // TRSM right-hand sides are independent: with many of them the chain runs
+    // as P column-panel branches (forked streams, one graph), so the
+    // latency-bound bottom of the recursion of one panel overlaps the others'.
+    int P = 1;
+    if (trsm) {
+        if (h->opt_panels > 0) P = (int)h->opt_panels;
+        else P = (int)std::min<int64_t>(kMaxPanels, std::max<int64_t>(1, ex.c.nrhs / kPanelMinCols));
+        const int64_t step = round_up((ex.c.nrhs + P - 1) / P, 256);
+        P = (int)std::max<int64_t>(1, (ex.c.nrhs + step - 1) / step);
+    }
+    std::vector<Exec<T>> parts((size_t)P, ex);
+    std::vector<std::vector<unsigned char>> maps((size_t)P);
+    {
+        const int64_t step = P > 1 ? round_up((ex.c.nrhs + P - 1) / P, 256) : ex.c.nrhs;
+        for (int i = 0; i < P; ++i) {
+            const int64_t j0 = step * i;
+            Exec<T>& x = parts[i];
+            x.c.C = ex.c.C + j0 * ex.c.c_cs;
+            x.c.nrhs = std::min<int64_t>(step, ex.c.nrhs - j0);
+            if (plan.tc) {
+                x.pl.y_hi = ex.pl.y_hi + j0 * ex.pl.ldy;
+                x.pl.y_lo = ex.pl.y_lo + j0 * ex.pl.ldy;
+                maps[i].resize(tc_maps_size());
+                e = tc_make_maps(x.pl, k, x.c.nrhs, maps[i].data());
+                if (e != cudaSuccess) return fail_cuda(e, "tensor map encode");
+                x.maps = maps[i].data();
+            }
+        }
+    }
+    Plan pre, body;
+    pre.tc = body.tc = plan.tc;
+    if (plan.tc) pre.steps.push_back(Step{kConvM});
+    make_plan(body, trsm, k, b, (double)alpha, /*conv_m=*/false);
+
+    // The whole call on stream st: prelude, then the panels (forked when P > 1).
+    auto run_all = [&](cudaStream_t st) -> int {
+        ex.s = st;
+        int rc = ex.run(pre);
+        if (rc != TRX_SUCCESS) return rc;
+        if (P == 1) {
+            parts[0].s = st;
+            return parts[0].run(body);
+        }
+        cudaError_t ee = cudaEventRecord(h->fork_ev, st);
+        if (ee != cudaSuccess) return fail_cuda(ee, "fork");
+        for (int i = 0; i < P; ++i) {
+            if ((ee = cudaStreamWaitEvent(h->aux[i], h->fork_ev, 0)) != cudaSuccess)
+                return fail_cuda(ee, "fork wait");
+            parts[i].s = h->aux[i];
+            if ((rc = parts[i].run(body)) != TRX_SUCCESS) return rc;
+            if ((ee = cudaEventRecord(h->join_ev[i], h->aux[i])) != cudaSuccess ||
+                (ee = cudaStreamWaitEvent(st, h->join_ev[i], 0)) != cudaSuccess)
+                return fail_cuda(ee, "join");
+        }
+        return TRX_SUCCESS;
+    };
 
     cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
     e = cudaStreamIsCapturing(s, &cap);
     if (e != cudaSuccess) return fail_cuda(e, "cudaStreamIsCapturing");
-    if (ex.profile || !h->opt_graph || cap != cudaStreamCaptureStatusNone) return ex.run(plan);
+    if (ex.profile || !h->opt_graph || cap != cudaStreamCaptureStatusNone) return run_all(s);
 
     GraphKey key;
     std::memset(&key, 0, sizeof(key));
@@ -496,6 +554,7 @@ int execute(trx_handle_t h, bool trsm, char side, char uplo, char transa, char d
     key.alpha = (double)alpha;
     key.wait_ns = h->wait_ns;
     key.pdl = (int)h->opt_pdl;
+    key.panels = P;
     const std::string ks(reinterpret_cast<const char*>(&key), sizeof(key));
     ++h->tick;
     for (auto& g : h->graphs) {
@@ -505,10 +564,9 @@ int execute(trx_handle_t h, bool trsm, char side, char uplo, char transa, char d
             return e == cudaSuccess ? TRX_SUCCESS : fail_cuda(e, "cudaGraphLaunch");
         }
     }
-    ex.s = h->cap_stream;
     e = cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return fail_cuda(e, "cudaStreamBeginCapture");
-    const int rc = ex.run(plan);
+    const int rc = run_all(h->cap_stream);
     cudaGraph_t graph = nullptr;
     e = cudaStreamEndCapture(h->cap_stream, &graph);
     if (rc != TRX_SUCCESS) {
@@ -561,6 +619,7 @@ int noalloc_strsm(int device, int num_sms, void* scratch, size_t scratch_bytes, 
     hs.ws_bytes = scratch_bytes;
     hs.d_err = err_word;
     hs.opt_graph = 0;
+    hs.opt_panels = 1;   // no handle streams here: one chain on the caller's stream
     return execute<float>(&hs, true, side, uplo, transa, diag, m, n, alpha, A, lda, B, ldb,
                           stream);
 }
@@ -814,9 +873,17 @@ int trx_create(trx_handle_t* handle, int device, size_t workspace_bytes) {
     if ((e = cudaMalloc(&h->d_err, 256)) != cudaSuccess ||
         (e = cudaMemset(h->d_err, 0, 256)) != cudaSuccess ||
         (e = cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking)) != cudaSuccess ||
+        (e = cudaEventCreateWithFlags(&h->fork_ev, cudaEventDisableTiming)) != cudaSuccess ||
         (e = leaf_configure_all()) != cudaSuccess || (e = batched_configure()) != cudaSuccess) {
         trx_destroy(h);
         return fail_cuda(e, "handle setup");
+    }
+    for (int i = 0; i < kMaxPanels; ++i) {
+        if ((e = cudaStreamCreateWithFlags(&h->aux[i], cudaStreamNonBlocking)) != cudaSuccess ||
+            (e = cudaEventCreateWithFlags(&h->join_ev[i], cudaEventDisableTiming)) != cudaSuccess) {
+            trx_destroy(h);
+            return fail_cuda(e, "handle streams");
+        }
     }
     if (workspace_bytes > 0) {
         e = cudaMalloc(&h->ws, workspace_bytes);
@@ -851,6 +918,11 @@ int trx_destroy(trx_handle_t h) {
     free_owned_ws(h);
     if (h->d_err) cudaFree(h->d_err);
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+    for (int i = 0; i < kMaxPanels; ++i) {
+        if (h->aux[i]) cudaStreamDestroy(h->aux[i]);
+        if (h->join_ev[i]) cudaEventDestroy(h->join_ev[i]);
+    }
+    if (h->fork_ev) cudaEventDestroy(h->fork_ev);
     h->magic = 0;
     delete h;
     return TRX_SUCCESS;
@@ -996,6 +1068,10 @@ int trx_set_option(trx_handle_t h, int option, int64_t value) {
             if (value != 0 && value != 1) return TRX_ERR_INVALID_VALUE;
             h->opt_pdl = value;
             break;
+        case TRX_OPT_PANELS:
+            if (value < 0 || value > kMaxPanels) return TRX_ERR_INVALID_VALUE;
+            h->opt_panels = value;
+            break;
         default:
             return TRX_ERR_INVALID_VALUE;
     }
@@ -1012,6 +1088,7 @@ int trx_get_option(trx_handle_t h, int option, int64_t* value) {
         case TRX_OPT_PROFILE: *value = h->opt_profile; break;
         case TRX_OPT_WAIT_LIMIT: *value = h->wait_ns; break;
         case TRX_OPT_PDL: *value = h->opt_pdl; break;
+        case TRX_OPT_PANELS: *value = h->opt_panels; break;
         default: return TRX_ERR_INVALID_VALUE;
     }
     return TRX_SUCCESS;

@@ -53,11 +53,14 @@ def test_leaf_and_engine_sweep(trx, op, engine, leaf, variant):
 @pytest.mark.parametrize("dtype", [np.float32, np.float64], ids=["f32", "f64"])
 @pytest.mark.parametrize("side,uplo,trans,diag", VARIANTS)
 def test_block_leaves_all_variants(trx, side, uplo, trans, diag, dtype):
-    """TRSM with >= 4096 right-hand sides takes 256-row block leaves (and a
-    ragged last one: k = 600)."""
+    """TRSM with the 256-row block leaves (cutoff 256; a ragged last leaf:
+    k = 600), many right-hand sides."""
+    h = trx.Handle(0)
+    h.set_option(trx.OPT_LEAF, 256)
     m, n = (600, 4200) if side == "L" else (4200, 600)
-    run_case("trsm", side, uplo, trans, diag, m, n, 1.5, dtype,
+    run_case("trsm", side, uplo, trans, diag, m, n, 1.5, dtype, handle=h,
              seed=inputs.variant_seed(600, VARIANTS.index((side, uplo, trans, diag))))
+    h.close()
 
 
 @pytest.mark.parametrize("op", ["trsm", "trmm"])

@@ -158,17 +158,17 @@ def test_trmm_level_batching():
         assert rows.max() == 1
 
 
-def test_trsm_block_leaves_for_many_rhs():
-    # auto cutoff: 256-row block leaves once there are >= 4096 right-hand sides
-    leaves = [s for s in debug_plan("S", "L", "L", "N", "N", 16384, 16384, 4, 0, 0)
+def test_trsm_block_leaves_on_request():
+    # cutoff 256 (TRSM block leaves) only when asked for; TRMM stops at 128
+    leaves = [s for s in debug_plan("S", "L", "L", "N", "N", 16384, 16384, 4, 256, 0)
               if s["kind"] == "leaf"]
     assert len(leaves) == 64 and all(s["b"] == 256 for s in leaves)
-    leaves = [s for s in debug_plan("S", "L", "L", "N", "N", 16384, 256, 4, 0, 0)
+    leaves = [s for s in debug_plan("S", "L", "L", "N", "N", 16384, 16384, 4, 0, 0)
               if s["kind"] == "leaf"]
     assert len(leaves) == 256
-    leaves = [s for s in debug_plan("M", "L", "L", "N", "N", 16384, 16384, 4, 0, 0)
+    leaves = [s for s in debug_plan("M", "L", "L", "N", "N", 16384, 16384, 4, 256, 0)
               if s["kind"] == "leaf"]
-    assert leaves[0]["b"] == 64
+    assert leaves[0]["b"] == 128
 
 
 def test_fp64_and_small_orders_use_cuda_cores():
