@@ -83,8 +83,7 @@ enum {
     TRX_OPT_PANELS = 7,    /* TRSM column-panel branches (right-hand sides
                               are independent; each panel runs its own
                               recursion chain on its own stream, all in one
-                              graph): 1..4, 0 = automatic (default: one per
-                              4096 right-hand sides, at most 4)            */
+                              graph): 1..4; 0 = automatic (default: 1)    */
     TRX_OPT_PDL = 6        /* 1: launch the chain's kernels with
                               programmatic dependent launch, so each one's
                               prologue overlaps the previous one's tail;

@@ -48,7 +48,8 @@ constexpr int64_t kTcMinOrder = 256;                 // auto: tensor cores from 
 constexpr size_t kGraphCacheSize = 16;
 constexpr int64_t kBatchMaxK = TRX_BATCH_MAX_K;
 constexpr int kMaxPanels = 4;
-constexpr int64_t kPanelMinCols = 4096;   // auto: a branch per 4096 right-hand sides
+// Auto stays at one chain: measured at m = n = 16384, 2 and 4 branches were
+// slower (the persistent GEMM update takes every SM, so branches serialise).
 
 thread_local char g_detail[256] = "";
 
@@ -479,7 +480,6 @@ int execute(trx_handle_t h, bool trsm, char side, char uplo, char transa, char d
     int P = 1;
     if (trsm) {
         if (h->opt_panels > 0) P = (int)h->opt_panels;
-        else P = (int)std::min<int64_t>(kMaxPanels, std::max<int64_t>(1, ex.c.nrhs / kPanelMinCols));
         const int64_t step = round_up((ex.c.nrhs + P - 1) / P, 256);
         P = (int)std::max<int64_t>(1, (ex.c.nrhs + step - 1) / step);
     }

@@ -105,6 +105,23 @@ def test_deterministic_and_graph_equals_direct(trx, op):
     assert np.array_equal(outs[0], outs[1]) and np.array_equal(outs[0], outs[2])
 
 
+@pytest.mark.parametrize("variant", [("L", "L", "N", "N"), ("R", "U", "T", "N")])
+def test_column_panel_branches(trx, variant):
+    """A TRSM split into column-panel branches (forked streams in one graph)
+    gives the single-chain result."""
+    outs = []
+    for panels in (1, 3, 4):
+        h = trx.Handle(0)
+        h.set_option(trx.OPT_PANELS, panels)
+        m, n = (1000, 3000) if variant[0] == "L" else (3000, 1000)
+        _, _, X = run_case("trsm", *variant, m, n, 1.5, np.float32, seed=17, handle=h)
+        outs.append(X.astype(np.float64))
+        h.close()
+    for X in outs[1:]:
+        diff = np.abs(X - outs[0]).max() / np.abs(outs[0]).max()
+        assert diff <= bound(1000, np.float32)
+
+
 def test_profile_counts_launches(trx):
     h = trx.Handle(0)
     h.set_option(trx.OPT_PROFILE, 1)
