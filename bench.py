@@ -188,14 +188,21 @@ def run_reference(args):
     return 0
 
 
-LEAF_USED = 64
+# automatic cutoffs of the library for this workload (FP32, 16384 right-hand
+# sides): TRSM 128-row leaves (wide leaf kernel), TRMM 256-row diagonal blocks
+# on the tensor cores; --leaf overrides both
+# (FP64: 64-row leaves)
+LEAF_USED = None
 
 
 def workload_config():
     prec = "FP32" if DTYPE == np.float32 else "FP64"
     return {"workload": f"{prec} TRSM(alpha=1.5) then TRMM(alpha=1/1.5), side L, lower, "
                         f"no transpose, non-unit, m={K_ORDER} n={NRHS}, column-major",
-            "m": K_ORDER, "n": NRHS, "leaf": LEAF_USED,
+            "m": K_ORDER, "n": NRHS,
+            "leaf": LEAF_USED if LEAF_USED is not None else (
+                "TRSM 128 (wide leaf), TRMM 256-row dense diagonal blocks"
+                if DTYPE == np.float32 else 64),
             "gemm": ("tcgen05 kind::f16, 3-term split BF16, FP32 accumulation"
                      if DTYPE == np.float32 else "CUDA-core DFMA"),
             "graph": "cached CUDA graph per call",

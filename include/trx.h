@@ -84,10 +84,21 @@ enum {
                               are independent; each panel runs its own
                               recursion chain on its own stream, all in one
                               graph): 1..4; 0 = automatic (default: 1)    */
-    TRX_OPT_PDL = 6        /* 1: launch the chain's kernels with
+    TRX_OPT_PDL = 6,       /* 1: launch the chain's kernels with
                               programmatic dependent launch, so each one's
                               prologue overlaps the previous one's tail;
                               0 (default): plain stream order              */
+    TRX_OPT_TRMM_DENSE = 8 /* FP32 TRMM on the tensor-core path: leaves of
+                              this many rows (64, 128, 256 or 512) formed in
+                              one grouped GEMM launch over dense diagonal
+                              blocks (the block's strictly-lower part on the
+                              tensor cores, zeros above; the diagonal term
+                              in FP32 in the epilogue), replacing the leaf
+                              kernel and the recursion levels below that
+                              size;
+                              -1 off; 0 = automatic (default: 256 rows when
+                              the order is at least 1024 and TRX_OPT_LEAF
+                              is automatic, else off)                     */
 };
 
 /* Kernel classes reported by trx_get_profile(). */
@@ -233,12 +244,12 @@ const char* trx_last_error_detail(void);
  * launch sequence a call would enqueue for the given problem, one step per
  * line ("conv_m", "conv_y", "leaf ...", "gemm ..." with their row ranges in
  * the canonical lower-triangular order), for alpha = 2. elem_bytes 4 or 8,
- * leaf as TRX_OPT_LEAF, gemm_mode as TRX_OPT_GEMM, op 'S' (TRSM) or 'M'
- * (TRMM). Returns an argument code, TRX_ERR_INVALID_VALUE if buf is too
- * small, or 0. */
+ * leaf as TRX_OPT_LEAF, gemm_mode as TRX_OPT_GEMM, trmm_dense as
+ * TRX_OPT_TRMM_DENSE, op 'S' (TRSM) or 'M' (TRMM). Returns an argument code,
+ * TRX_ERR_INVALID_VALUE if buf is too small, or 0. */
 int trx_debug_plan(char op, char side, char uplo, char transa, char diag,
                    int64_t m, int64_t n, int elem_bytes, int leaf,
-                   int gemm_mode, char* buf, size_t buflen);
+                   int gemm_mode, int trmm_dense, char* buf, size_t buflen);
 
 /* Size of the static device scratch behind trx_strsm_noalloc (64 MiB). */
 #define TRX_NOALLOC_SCRATCH_BYTES ((size_t)64 << 20)

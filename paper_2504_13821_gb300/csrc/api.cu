@@ -40,11 +40,16 @@ namespace {
 
 constexpr int kMagic = 0x54525831;  // "TRX1"
 constexpr int kDefaultLeaf = 64;
-// Auto cutoff never picks block leaves (measured slower than 64-row leaves
-// plus small updates at 16384 right-hand sides); TRX_OPT_LEAF = 256 does.
-constexpr int64_t kBlockLeafMinRhs = INT64_MAX;
+// Automatic cutoff for FP32 TRSM with many right-hand sides: 128-row leaves
+// (one wide-leaf launch in place of two 64-row leaves and the update between
+// them; measured faster at 16384 right-hand sides). Block leaves (256) are
+// never chosen automatically (measured slower); TRX_OPT_LEAF = 256 asks.
+constexpr int kWideLeaf = 128;
+constexpr int64_t kWideLeafMinRhs = 8192;
 constexpr long long kDefaultWaitNs = 2000000000LL;   // 2 s
 constexpr int64_t kTcMinOrder = 256;                 // auto: tensor cores from this order
+constexpr int64_t kTrmmDenseMinOrder = 1024;         // auto: dense TRMM diagonal blocks from here
+constexpr int kTrmmDenseRows = 256;                  // auto: their size
 constexpr size_t kGraphCacheSize = 16;
 constexpr int64_t kBatchMaxK = TRX_BATCH_MAX_K;
 constexpr int kMaxPanels = 4;
@@ -114,13 +119,16 @@ struct Step {
     StepKind kind;
     bool trsm = true;        // leaf: TRSM or TRMM
     int64_t r0 = 0;          // leaf: first row
-    int b = 0;               // leaf: size (and stride of batched leaves)
+    int b = 0;               // leaf: size (and stride of batched leaves); conv_m: diagonal
+                             // block carried densely in the planes (0: none)
     int64_t nleaves = 1;
     double alpha = 1.0;      // leaf scale
     bool planes = false;     // TRSM leaf writes Y planes
     bool tc = false;         // GEMM on tensor cores
     std::vector<TcGemm> gemms;
     double beta = 1.0, gamma = 1.0;
+    bool dense = false;      // GEMM over dense lower-triangular diagonal blocks (TRMM leaves):
+                             // row i's beta is beta * M(i, i)
 };
 
 struct Plan {
@@ -177,14 +185,35 @@ void plan_trmm_seq(Plan& pl, int64_t r0, int64_t s, int b, double alpha) {
 // reads a row another step writes, so the same recursion tree runs as one
 // launch for all leaves followed by one grouped launch per recursion level
 // (the updates of one level write disjoint rows).
-void plan_trmm_levels(Plan& pl, int64_t k, int b, double alpha) {
-    Step lf{kLeaf};
-    lf.trsm = false;
-    lf.r0 = 0;
-    lf.b = b;
-    lf.nleaves = (k + b - 1) / b;
-    lf.alpha = alpha;
-    pl.steps.push_back(lf);
+//
+// With dense = true the leaves (b a multiple of 64) run on the tensor cores
+// too: the operand planes carry each b x b diagonal block's strictly-lower
+// part with zeros on and above the diagonal, and one grouped launch forms
+// every leaf product at once,
+//   C[i] = alpha * M(i,i) * C[i] + alpha * sum_{r <= l < i} M(i,l) * Y[l],
+// the diagonal term in FP32 from C's original value (a per-row beta in the
+// GEMM epilogue) and the rest on the tensor cores.
+void plan_trmm_levels(Plan& pl, int64_t k, int b, double alpha, bool dense = false) {
+    if (dense) {
+        Step d{kGemm};
+        d.tc = true;
+        d.dense = true;
+        d.beta = alpha;
+        d.gamma = alpha;
+        for (int64_t r = 0; r < k; r += b) {
+            const int64_t len = std::min<int64_t>(b, k - r);
+            d.gemms.push_back(TcGemm{r, len, r, round_up(len, 32)});
+        }
+        pl.steps.push_back(d);
+    } else {
+        Step lf{kLeaf};
+        lf.trsm = false;
+        lf.r0 = 0;
+        lf.b = b;
+        lf.nleaves = (k + b - 1) / b;
+        lf.alpha = alpha;
+        pl.steps.push_back(lf);
+    }
     std::vector<std::pair<int64_t, int64_t>> level{{0, k}}, next;
     while (!level.empty()) {
         Step g{kGemm};
@@ -207,15 +236,33 @@ void plan_trmm_levels(Plan& pl, int64_t k, int b, double alpha) {
 
 // The whole launch sequence of one call: operand planes (tensor-core path),
 // then the recursion of Section 3.1.
-void make_plan(Plan& plan, bool trsm, int64_t k, int b, double alpha, bool conv_m = true) {
-    if (plan.tc && conv_m) plan.steps.push_back(Step{kConvM});
+// dense > 0 (TRMM on the tensor-core path only): leaves of that many rows as
+// dense diagonal-block GEMMs, in place of the leaf kernel and of the levels
+// below that size.
+void make_plan(Plan& plan, bool trsm, int64_t k, int b, double alpha, bool conv_m = true,
+               int dense = 0) {
+    if (plan.tc && conv_m) {
+        Step cm{kConvM};
+        cm.b = trsm ? 0 : dense;
+        plan.steps.push_back(cm);
+    }
     if (trsm) {
         plan_trsm(plan, 0, k, true, b, alpha);
     } else {
         if (plan.tc) plan.steps.push_back(Step{kConvY});
-        if (plan.tc && b % kTcKQuantum == 0) plan_trmm_levels(plan, k, b, alpha);
+        if (plan.tc && dense > 0) plan_trmm_levels(plan, k, dense, alpha, true);
+        else if (plan.tc && b % kTcKQuantum == 0) plan_trmm_levels(plan, k, b, alpha);
         else plan_trmm_seq(plan, 0, k, b, alpha);
     }
+}
+
+// Rows of the dense TRMM diagonal blocks: the handle's TRX_OPT_TRMM_DENSE
+// (-1 off, else the size), or automatically 256 once the order reaches 1024
+// and the leaf size was left automatic. Tensor-core path only.
+int trmm_dense_mode(int64_t opt, int64_t opt_leaf, bool tc, int64_t k) {
+    if (!tc || opt < 0) return 0;
+    if (opt > 0) return (int)opt;
+    return (opt_leaf == 0 && k >= kTrmmDenseMinOrder) ? kTrmmDenseRows : 0;
 }
 
 template <typename T>
@@ -308,6 +355,7 @@ struct trx_handle_s {
     int tune_sb[2][4] = {{16, 16, 16, 16}, {16, 16, 16, 16}};
     // column-panel branches of a TRSM: streams and fork/join events
     int64_t opt_panels = 0;
+    int64_t opt_trmm_dense = 0;
     cudaStream_t aux[kMaxPanels] = {};
     cudaEvent_t fork_ev = nullptr, join_ev[kMaxPanels] = {};
 };
@@ -327,13 +375,14 @@ cudaEvent_t get_event(trx_handle_t h) {
     return e;
 }
 
-// Recursion cutoff: the handle's TRX_OPT_LEAF, else 64. With 256 a TRSM's
-// leaves run as block leaves (one launch per 256 rows); TRMM leaves stop at
-// 128 rows.
-int leaf_for(trx_handle_t h, int64_t k, bool trsm = false, int64_t nrhs = 0) {
+
+// Recursion cutoff: TRX_OPT_LEAF when set, else 128 for FP32 TRSM with many
+// right-hand sides and 64 otherwise. With 256 a TRSM's leaves run as block
+// leaves (one launch per 256 rows); TRMM leaves stop at 128 rows.
+int leaf_for(int64_t opt_leaf, int64_t k, bool trsm, int elem, int64_t nrhs) {
     int b = kDefaultLeaf;
-    if (h->opt_leaf > 0) b = (int)h->opt_leaf;
-    else if (trsm && nrhs >= kBlockLeafMinRhs) b = kMaxBlockLeaf;
+    if (opt_leaf > 0) b = (int)opt_leaf;
+    else if (trsm && elem == 4 && nrhs >= kWideLeafMinRhs) b = kWideLeaf;
     if (!trsm && b > kMaxLeaf) b = kMaxLeaf;
     return (int)std::min<int64_t>(b, std::max<int64_t>(k, 1));
 }
@@ -345,8 +394,9 @@ bool use_tc_mode(int elem, int64_t gemm_mode, int64_t k, int b) {
 }
 
 template <typename T>
-bool use_tc(trx_handle_t h, int64_t k) {
-    return use_tc_mode((int)sizeof(T), h->opt_gemm, k, leaf_for(h, k));
+bool use_tc(trx_handle_t h, int64_t k, bool trsm, int64_t nrhs) {
+    return use_tc_mode((int)sizeof(T), h->opt_gemm, k,
+                       leaf_for(h->opt_leaf, k, trsm, (int)sizeof(T), nrhs));
 }
 
 template <typename T>
@@ -385,7 +435,8 @@ struct Exec {
                     if (st.tc) {
                         e = launch_gemm_tc(*reinterpret_cast<const Canon<float>*>(&c), maps,
                                            st.gemms.data(), (int)st.gemms.size(), (float)st.beta,
-                                           (float)st.gamma, h->d_err, h->wait_ns, h->num_sms, s);
+                                           (float)st.gamma, h->d_err, h->wait_ns, h->num_sms, s,
+                                           st.dense);
                         cls = TRX_KERNEL_GEMM_TC;
                     } else {
                         for (const TcGemm& g : st.gemms) {
@@ -396,14 +447,19 @@ struct Exec {
                         cls = TRX_KERNEL_GEMM_SIMT;
                     }
                     for (const TcGemm& g : st.gemms) {
-                        flops += 2.0 * g.mlen * g.klen * c.nrhs;
-                        bytes += w * ((double)g.mlen * g.klen + 2.0 * g.mlen * c.nrhs +
-                                      (double)g.klen * c.nrhs);
+                        if (st.dense) {      // triangular block: b^2 n
+                            flops += (double)g.mlen * g.mlen * c.nrhs;
+                            bytes += w * ((double)g.mlen * (g.mlen + 1) / 2 + 3.0 * g.mlen * c.nrhs);
+                        } else {
+                            flops += 2.0 * g.mlen * g.klen * c.nrhs;
+                            bytes += w * ((double)g.mlen * g.klen + 2.0 * g.mlen * c.nrhs +
+                                          (double)g.klen * c.nrhs);
+                        }
                     }
                     break;
                 }
                 case kConvM:
-                    e = launch_convert_m(*reinterpret_cast<const Canon<float>*>(&c), pl, s);
+                    e = launch_convert_m(*reinterpret_cast<const Canon<float>*>(&c), pl, st.b, s);
                     cls = TRX_KERNEL_CONVERT;
                     bytes = 8.0 * c.k * (c.k - 1) / 2;
                     break;
@@ -431,7 +487,7 @@ struct GraphKey {
     const void* ws;
     double alpha;
     long long wait_ns;
-    int pdl, panels;
+    int pdl, panels, dense;
 };
 
 template <typename T>
@@ -455,10 +511,10 @@ int execute(trx_handle_t h, bool trsm, char side, char uplo, char transa, char d
     ex.s = s;
     ex.profile = h->opt_profile != 0;
     const int64_t k = ex.c.k;
-    const int b = leaf_for(h, k, trsm, ex.c.nrhs);
+    const int b = leaf_for(h->opt_leaf, k, trsm, (int)sizeof(T), ex.c.nrhs);
 
     Plan plan;
-    plan.tc = use_tc<T>(h, k);
+    plan.tc = use_tc<T>(h, k, trsm, ex.c.nrhs);
     if (plan.tc) {
         const WsLayout w = ws_layout(k, ex.c.nrhs);
         if (h->ws == nullptr || h->ws_bytes < w.total) {
@@ -502,10 +558,15 @@ int execute(trx_handle_t h, bool trsm, char side, char uplo, char transa, char d
             }
         }
     }
+    const int dense = trsm ? 0 : trmm_dense_mode(h->opt_trmm_dense, h->opt_leaf, plan.tc, k);
     Plan pre, body;
     pre.tc = body.tc = plan.tc;
-    if (plan.tc) pre.steps.push_back(Step{kConvM});
-    make_plan(body, trsm, k, b, (double)alpha, /*conv_m=*/false);
+    if (plan.tc) {
+        Step cm{kConvM};
+        cm.b = dense;
+        pre.steps.push_back(cm);
+    }
+    make_plan(body, trsm, k, b, (double)alpha, /*conv_m=*/false, dense);
 
     // The whole call on stream st: prelude, then the panels (forked when P > 1).
     auto run_all = [&](cudaStream_t st) -> int {
@@ -555,6 +616,7 @@ int execute(trx_handle_t h, bool trsm, char side, char uplo, char transa, char d
     key.wait_ns = h->wait_ns;
     key.pdl = (int)h->opt_pdl;
     key.panels = P;
+    key.dense = dense;
     const std::string ks(reinterpret_cast<const char*>(&key), sizeof(key));
     ++h->tick;
     for (auto& g : h->graphs) {
@@ -605,7 +667,7 @@ int noalloc_check_args(char side, char uplo, char transa, char diag, int64_t m, 
 size_t noalloc_scratch_bytes(char side, int64_t m, int64_t n) {
     const int64_t k = upc(side) == 'L' ? m : n, nrhs = upc(side) == 'L' ? n : m;
     if (k <= 0 || nrhs <= 0) return 0;
-    const int b = (int)std::min<int64_t>(kDefaultLeaf, k);
+    const int b = leaf_for(0, k, true, 4, nrhs);
     return use_tc_mode(4, 0, k, b) ? ws_layout(k, nrhs).total : 0;
 }
 
@@ -950,7 +1012,7 @@ int trx_workspace_size(trx_handle_t h, char op, char side, int64_t m, int64_t n,
     if ((elem_bytes != 4 && elem_bytes != 8) || (upc(op) != 'S' && upc(op) != 'M' && upc(op) != 'G') || !bytes)
         return TRX_ERR_INVALID_VALUE;
     int64_t k = upc(side) == 'L' ? m : n, nrhs = upc(side) == 'L' ? n : m;
-    bool tc = elem_bytes == 4 ? use_tc<float>(h, k) : false;
+    bool tc = elem_bytes == 4 ? use_tc<float>(h, k, upc(op) == 'S', nrhs) : false;
     if (upc(op) == 'G') {   // tensor-core trx_sgemm_update: m = M + K rows, n = N
         k = m;
         nrhs = n;
@@ -1072,6 +1134,12 @@ int trx_set_option(trx_handle_t h, int option, int64_t value) {
             if (value < 0 || value > kMaxPanels) return TRX_ERR_INVALID_VALUE;
             h->opt_panels = value;
             break;
+        case TRX_OPT_TRMM_DENSE:
+            if (value != -1 && value != 0 && value != 64 && value != 128 && value != 256 &&
+                value != 512)
+                return TRX_ERR_INVALID_VALUE;
+            h->opt_trmm_dense = value;
+            break;
         default:
             return TRX_ERR_INVALID_VALUE;
     }
@@ -1089,6 +1157,7 @@ int trx_get_option(trx_handle_t h, int option, int64_t* value) {
         case TRX_OPT_WAIT_LIMIT: *value = h->wait_ns; break;
         case TRX_OPT_PDL: *value = h->opt_pdl; break;
         case TRX_OPT_PANELS: *value = h->opt_panels; break;
+        case TRX_OPT_TRMM_DENSE: *value = h->opt_trmm_dense; break;
         default: return TRX_ERR_INVALID_VALUE;
     }
     return TRX_SUCCESS;
@@ -1154,31 +1223,36 @@ const char* trx_error_string(int code) {
 const char* trx_last_error_detail(void) { return g_detail; }
 
 int trx_debug_plan(char op, char side, char uplo, char transa, char diag, int64_t m, int64_t n,
-                   int elem_bytes, int leaf, int gemm_mode, char* buf, size_t buflen) {
+                   int elem_bytes, int leaf, int gemm_mode, int trmm_dense, char* buf,
+                   size_t buflen) {
     const int info = check_args(side, uplo, transa, diag, m, n, "", std::max<int64_t>(1, upc(side) == 'L' ? m : n),
                                 "", std::max<int64_t>(1, m));
     if (info) return info;
     if ((upc(op) != 'S' && upc(op) != 'M') || (elem_bytes != 4 && elem_bytes != 8) ||
         (leaf != 0 && leaf != 16 && leaf != 32 && leaf != 64 && leaf != 128 && leaf != 256) ||
         gemm_mode < 0 ||
-        gemm_mode > 2 || !buf || buflen == 0)
+        gemm_mode > 2 || !buf || buflen == 0 ||
+        (trmm_dense != -1 && trmm_dense != 0 && trmm_dense != 64 && trmm_dense != 128 &&
+         trmm_dense != 256 && trmm_dense != 512))
         return TRX_ERR_INVALID_VALUE;
     buf[0] = 0;
     const int64_t k = upc(side) == 'L' ? m : n;
     if (m == 0 || n == 0) return TRX_SUCCESS;
     const bool is_trsm = upc(op) == 'S';
     const int64_t nrhs = upc(side) == 'L' ? n : m;
-    int b = leaf > 0 ? leaf : (is_trsm && nrhs >= kBlockLeafMinRhs ? kMaxBlockLeaf : kDefaultLeaf);
-    if (!is_trsm && b > kMaxLeaf) b = kMaxLeaf;
-    b = (int)std::min<int64_t>(b, std::max<int64_t>(k, 1));
+    const int b = leaf_for(leaf, k, is_trsm, elem_bytes, nrhs);
     Plan plan;
     plan.tc = use_tc_mode(elem_bytes, gemm_mode, k, b);
-    make_plan(plan, upc(op) == 'S', k, b, 2.0);
+    const int dense = is_trsm ? 0 : trmm_dense_mode(trmm_dense, leaf, plan.tc, k);
+    make_plan(plan, is_trsm, k, b, 2.0, true, dense);
     std::string out;
     char line[256];
     for (const Step& st : plan.steps) {
         switch (st.kind) {
-            case kConvM: out += "conv_m\n"; break;
+            case kConvM:
+                snprintf(line, sizeof(line), "conv_m diag_block=%d\n", st.b);
+                out += line;
+                break;
             case kConvY: out += "conv_y\n"; break;
             case kLeaf:
                 snprintf(line, sizeof(line), "leaf trsm=%d r0=%lld b=%d nleaves=%lld alpha=%.17g planes=%d\n",
@@ -1190,9 +1264,9 @@ int trx_debug_plan(char op, char side, char uplo, char transa, char diag, int64_
                 for (size_t i = 0; i < st.gemms.size(); ++i) {
                     const TcGemm& g = st.gemms[i];
                     snprintf(line, sizeof(line),
-                             "gemm tc=%d member=%zu rc=%lld mlen=%lld rk=%lld klen=%lld beta=%.17g gamma=%.17g\n",
+                             "gemm tc=%d member=%zu rc=%lld mlen=%lld rk=%lld klen=%lld beta=%.17g gamma=%.17g dense=%d\n",
                              (int)st.tc, i, (long long)g.rc, (long long)g.mlen, (long long)g.rk,
-                             (long long)g.klen, st.beta, st.gamma);
+                             (long long)g.klen, st.beta, st.gamma, (int)st.dense);
                     out += line;
                 }
                 break;

@@ -115,7 +115,10 @@ template <typename T>
 cudaError_t launch_zero(T* B, int64_t m, int64_t n, int64_t ldb, cudaStream_t s);
 
 // Split-BF16 planes of the strictly-lower part of M (rows/cols [0,k)).
-cudaError_t launch_convert_m(const Canon<float>& p, const Planes& pl, cudaStream_t s);
+// diag_block > 0 (a multiple of 64): the planes also carry zeros on and
+// above the diagonal within each diag_block x diag_block diagonal block.
+cudaError_t launch_convert_m(const Canon<float>& p, const Planes& pl, int diag_block,
+                             cudaStream_t s);
 // Split-BF16 planes of C rows [0,k), all columns (TRMM's original values).
 cudaError_t launch_convert_y(const Canon<float>& p, const Planes& pl, cudaStream_t s);
 // Split-BF16 planes of a rows x cols block, src(r, c) = src[r*rs + c*cs];
@@ -137,7 +140,7 @@ cudaError_t tc_make_maps(const Planes& pl, int64_t k, int64_t nrhs, void* maps_o
 cudaError_t launch_gemm_tc(const Canon<float>& p, const void* maps,
                            const TcGemm* gemms, int ngemms, float beta,
                            float gamma, int* err_word, long long wait_limit,
-                           int num_sms, cudaStream_t s);
+                           int num_sms, cudaStream_t s, bool diag_beta = false);
 // K granularity the tensor-core GEMM needs (klen and rk multiples of this).
 constexpr int kTcKQuantum = 64;
 

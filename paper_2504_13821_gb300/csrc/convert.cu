@@ -6,7 +6,10 @@
 // 2^-17 relative), and a product as hi*hi + hi*lo + lo*hi with FP32
 // accumulation (the lo*lo term is below that error). These kernels write the
 // planes in the canonical K-major order the GEMM's TMA loads expect:
-//   M planes: strictly-lower part of M, (i, l) at i*ldm + l
+//   M planes: strictly-lower part of M, (i, l) at i*ldm + l; with diagonal
+//             blocks requested, also explicit zeros on and above the
+//             diagonal inside each block, so a block can be used as a dense
+//             GEMM operand
 //   Y planes: C (TRMM's original right-hand side), (l, j) at j*ldy + l
 // 32x32 tiles go through shared memory, so reads are coalesced along
 // whichever index is contiguous in the caller's storage and writes along the
@@ -21,14 +24,15 @@ __device__ __forceinline__ void split_bf16(float x, __nv_bfloat16& hi, __nv_bflo
     lo = __float2bfloat16_rn(x - __bfloat162float(hi));
 }
 
-// M planes: 64x64 tiles of the lower triangle (tiles above it exit at once),
-// read along A's contiguous index, written as BF16 pairs along l.
-__global__ void __launch_bounds__(256) convert_m_kernel(Canon<float> p, Planes pl) {
+// M planes: 64x64 tiles of the lower triangle (tiles above it exit at once,
+// except inside a diagonal block of zdb tiles when zdb > 0), read along A's
+// contiguous index, written as BF16 pairs along l.
+__global__ void __launch_bounds__(256) convert_m_kernel(Canon<float> p, Planes pl, int zdb) {
     pdl_trigger();
     pdl_wait();
     __shared__ float tile[64][65];
     const int64_t ti = blockIdx.y, tl = blockIdx.x;
-    if (tl > ti) return;
+    if (tl > ti && (zdb == 0 || tl / zdb != ti / zdb)) return;
     const int64_t i0 = ti * 64, l0 = tl * 64;
     const int tid = threadIdx.x;
     const bool row_fast = (p.a_rs == 1 || p.a_rs == -1);
@@ -161,11 +165,13 @@ __global__ void zero_kernel(T* B, int64_t m, int64_t n, int64_t ldb) {
 
 }  // namespace
 
-cudaError_t launch_convert_m(const Canon<float>& p, const Planes& pl, cudaStream_t s) {
-    if (p.k <= 1) return cudaSuccess;
+cudaError_t launch_convert_m(const Canon<float>& p, const Planes& pl, int diag_block,
+                             cudaStream_t s) {
+    if (p.k <= 0 || (p.k <= 1 && diag_block == 0)) return cudaSuccess;
     const int64_t t = (p.k + 63) / 64;
-    if (t > 65535) return cudaErrorInvalidValue;
-    return launch_kernel(convert_m_kernel, dim3((unsigned)t, (unsigned)t), dim3(256), 0, s, p, pl);
+    if (t > 65535 || diag_block % 64 != 0) return cudaErrorInvalidValue;
+    return launch_kernel(convert_m_kernel, dim3((unsigned)t, (unsigned)t), dim3(256), 0, s, p, pl,
+                         diag_block / 64);
 }
 
 cudaError_t launch_convert_y(const Canon<float>& p, const Planes& pl, cudaStream_t s) {

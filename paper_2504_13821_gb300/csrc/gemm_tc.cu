@@ -2,6 +2,9 @@
 //
 //   C[rc+i, j] = beta * C[rc+i, j] + gamma * sum_l M(rc+i, rk+l) * Y(rk+l, j)
 //
+// (with beta == 0, C is not read: C[rc+i, j] = gamma * sum ...; with a
+// per-row beta, beta * M(rc+i, rc+i) multiplies row i's old value)
+//
 // This is the off-diagonal step of the recursion of Section 3.1 (TRSM:
 // B2 := beta*B2 - M21 X1; TRMM: B2 += alpha M21 B1), where the paper's
 // speed comes from (Section 3.3: the base kernels must stay small next to the
@@ -72,6 +75,14 @@ struct Params {
     float* C;
     int64_t c_rs, c_cs, nrhs;
     float beta, gamma;
+    int read_c;                     // 0 when beta == 0: C is written, never read
+    // diag_beta: row i's beta is beta * d_i, d_i = M's diagonal entry
+    // dA[i * d_step] (1 for a unit diagonal): TRMM's diagonal term taken in
+    // FP32 from C's original value while the strictly-lower part of a
+    // diagonal block goes through the tensor cores
+    int diag_beta, unit;
+    const float* dA;
+    int64_t d_step;
     int ngemms, n_tiles_n, total_tiles;
     int* err;
     long long wait_ns;
@@ -334,6 +345,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) gemm_tc_kernel(const __grid_const
             const TcGemm& G = p.g[ti.g];
             const int64_t row = (int64_t)ti.m * BM + q * 32 + lane;
             const bool row_ok = row < G.mlen;
+            float beta = p.beta;
+            if (p.diag_beta && row_ok && !p.unit) beta *= __ldg(p.dA + (G.rc + row) * p.d_step);
             const float* crow = p.C + (G.rc + row) * p.c_rs;
             float* wrow = p.C + (G.rc + row) * p.c_rs;
             const int64_t jbase = (int64_t)ti.n * BN;
@@ -345,7 +358,10 @@ __global__ void __launch_bounds__(NTHREADS, 1) gemm_tc_kernel(const __grid_const
             auto load_chunk = [&](int ch, float (&dst)[32]) {
                 const int64_t j0 = jbase + ch * 32;
                 const float* src = crow + j0 * p.c_cs;
-                if (row_ok && j0 + 32 <= p.nrhs) {
+                if (!p.read_c) {
+#pragma unroll
+                    for (int c = 0; c < 32; ++c) dst[c] = 0.f;
+                } else if (row_ok && j0 + 32 <= p.nrhs) {
 #pragma unroll
                     for (int c = 0; c < 32; ++c) dst[c] = __ldcg(src + c * p.c_cs);
                 } else {
@@ -379,11 +395,11 @@ __global__ void __launch_bounds__(NTHREADS, 1) gemm_tc_kernel(const __grid_const
                 float* dst = wrow + j0 * p.c_cs;
                 if (row_ok && j0 + 32 <= p.nrhs) {
 #pragma unroll
-                    for (int c = 0; c < 32; ++c) dst[c * p.c_cs] = fmaf(p.beta, c0[c], p.gamma * v[c]);
+                    for (int c = 0; c < 32; ++c) dst[c * p.c_cs] = fmaf(beta, c0[c], p.gamma * v[c]);
                 } else if (row_ok) {
 #pragma unroll
                     for (int c = 0; c < 32; ++c)
-                        if (j0 + c < p.nrhs) dst[c * p.c_cs] = fmaf(p.beta, c0[c], p.gamma * v[c]);
+                        if (j0 + c < p.nrhs) dst[c * p.c_cs] = fmaf(beta, c0[c], p.gamma * v[c]);
                 }
 #pragma unroll
                 for (int c = 0; c < 32; ++c) {
@@ -473,7 +489,7 @@ cudaError_t tc_make_maps(const Planes& pl, int64_t k, int64_t nrhs, void* out) {
 
 cudaError_t launch_gemm_tc(const Canon<float>& p, const void* maps, const TcGemm* gemms,
                            int ngemms, float beta, float gamma, int* err_word,
-                           long long wait_ns, int num_sms, cudaStream_t s) {
+                           long long wait_ns, int num_sms, cudaStream_t s, bool diag_beta) {
     using namespace tc;
     for (int g0 = 0; g0 < ngemms; g0 += MAXG) {
         const int ng = (ngemms - g0) < MAXG ? (ngemms - g0) : MAXG;
@@ -493,6 +509,11 @@ cudaError_t launch_gemm_tc(const Canon<float>& p, const void* maps, const TcGemm
         prm.nrhs = p.nrhs;
         prm.beta = beta;
         prm.gamma = gamma;
+        prm.read_c = beta != 0.f;
+        prm.diag_beta = diag_beta;
+        prm.unit = p.unit;
+        prm.dA = p.A;
+        prm.d_step = p.a_rs + p.a_cs;
         prm.ngemms = ng;
         prm.n_tiles_n = (int)((p.nrhs + bn - 1) / bn);
         prm.err = err_word;

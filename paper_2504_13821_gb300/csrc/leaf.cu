@@ -1,6 +1,7 @@
 // Leaf kernels: lane-count choice and dispatch. The kernels themselves are in
 // leaf_impl.cuh.
 #include <cstdlib>
+#include <type_traits>
 
 #include "leaf_impl.cuh"
 
@@ -43,6 +44,9 @@ extern template cudaError_t leaf_b256_configure<double>();
 extern template cudaError_t leaf_b256_launch<float>(const LeafArgs<float>&, cudaStream_t);
 extern template cudaError_t leaf_b256_launch<double>(const LeafArgs<double>&, cudaStream_t);
 
+cudaError_t leaf_wide_configure();
+cudaError_t leaf_wide_launch(const LeafArgs<float>& a, int num_sms, cudaStream_t s);
+
 cudaError_t leaf_configure_all() {
     cudaError_t e;
     if ((e = leaf_configure<float, true>()) != cudaSuccess) return e;
@@ -53,6 +57,7 @@ cudaError_t leaf_configure_all() {
     if ((e = leaf_blocked_configure<double>()) != cudaSuccess) return e;
     if ((e = leaf_b256_configure<float>()) != cudaSuccess) return e;
     if ((e = leaf_b256_configure<double>()) != cudaSuccess) return e;
+    if ((e = leaf_wide_configure()) != cudaSuccess) return e;
     return tc_configure();
 }
 
@@ -78,6 +83,12 @@ cudaError_t launch_leaf(bool trsm, const Canon<T>& p, int64_t r0, int b,
         return !(e && e[0] == '0');
     }();
     if (trsm && b > kMaxLeaf) return leaf_b256_launch<T>(a, s);   // block leaf, 129..256 rows
+    // FP32, one leaf of 65..128 rows, many right-hand sides: the wide kernel
+    // (register-resident tiles, four column groups per CTA).
+    if constexpr (std::is_same<T, float>::value) {
+        if (blocked_on && trsm && nleaves == 1 && b > 64 && p.nrhs >= 1024)
+            return leaf_wide_launch(a, num_sms, s);
+    }
     if (blocked_on && trsm && nleaves == 1 && b > 32 && p.nrhs >= 1024)
         return leaf_blocked_launch<T>(a, (int64_t)(num_sms > 0 ? num_sms : 1) * 2, s);
 

@@ -50,6 +50,53 @@ def test_leaf_and_engine_sweep(trx, op, engine, leaf, variant):
     h.close()
 
 
+@pytest.mark.parametrize("side,uplo,trans,diag", VARIANTS)
+def test_trmm_dense_diagonal_blocks_all_variants(trx, side, uplo, trans, diag):
+    """FP32 TRMM at order 1100 on a default handle: 256-row dense diagonal
+    blocks on the tensor cores (automatic from order 1024), a ragged last
+    block of 76 rows; unit diagonals poisoned with NaN in A."""
+    m, n = (1100, 300) if side == "L" else (300, 1100)
+    run_case("trmm", side, uplo, trans, diag, m, n, 1.5, np.float32,
+             seed=inputs.variant_seed(1100, VARIANTS.index((side, uplo, trans, diag))))
+
+
+@pytest.mark.parametrize("engine", [1, 2], ids=["cuda_cores", "tensor_cores"])
+@pytest.mark.parametrize("side,uplo,trans,diag", VARIANTS)
+def test_wide_leaves_all_variants(trx, side, uplo, trans, diag, engine):
+    """FP32 TRSM with 128-row leaves and many right-hand sides (the wide
+    leaf kernel): k = 600 leaves a ragged last leaf of 88 rows, 4200
+    right-hand sides a ragged last 32-column panel."""
+    h = trx.Handle(0)
+    h.set_option(trx.OPT_LEAF, 128)
+    h.set_option(trx.OPT_GEMM, engine)
+    m, n = (600, 4200) if side == "L" else (4200, 600)
+    run_case("trsm", side, uplo, trans, diag, m, n, 1.5, np.float32,
+             seed=inputs.variant_seed(600 + engine, VARIANTS.index((side, uplo, trans, diag))),
+             handle=h, ldb_pad=3)
+    h.close()
+
+
+@pytest.mark.parametrize("k", [1, 15, 100, 128])
+def test_wide_leaf_single(trx, k):
+    # one leaf of k <= 128 rows over 2050 right-hand sides, alpha applied once
+    h = trx.Handle(0)
+    h.set_option(trx.OPT_LEAF, 128)
+    run_case("trsm", "L", "L", "N", "N", k, 2050, -0.5, np.float32, seed=k, handle=h)
+    run_case("trsm", "R", "U", "T", "U", 2050, k, 3.0, np.float32, seed=k + 1, handle=h)
+    h.close()
+
+
+@pytest.mark.parametrize("dense", [-1, 64, 128, 256, 512])
+@pytest.mark.parametrize("variant", [("L", "L", "N", "N"), ("R", "U", "T", "U")])
+def test_trmm_dense_sizes(trx, dense, variant):
+    h = trx.Handle(0)
+    h.set_option(trx.OPT_GEMM, 2)
+    h.set_option(trx.OPT_TRMM_DENSE, dense)
+    m, n = (700, 200) if variant[0] == "L" else (200, 700)
+    run_case("trmm", *variant, m, n, -0.75, np.float32, seed=700 + dense, handle=h, ldb_pad=5)
+    h.close()
+
+
 @pytest.mark.parametrize("dtype", [np.float32, np.float64], ids=["f32", "f64"])
 @pytest.mark.parametrize("side,uplo,trans,diag", VARIANTS)
 def test_block_leaves_all_variants(trx, side, uplo, trans, diag, dtype):

@@ -42,7 +42,11 @@ def coverage(k, steps):
         blk = np.tril(np.ones((e - r, e - r), dtype=np.int32))
         cnt[r:e, r:e] += blk
     for s in steps:
-        if s["kind"] == "gemm":
+        if s["kind"] == "gemm" and s.get("dense"):
+            # dense diagonal block: its lower triangle with the diagonal
+            r, e = s["rc"], min(k, s["rc"] + s["mlen"])
+            cnt[r:e, r:e] += np.tril(np.ones((e - r, e - r), dtype=np.int32))
+        elif s["kind"] == "gemm":
             cnt[s["rc"]:s["rc"] + s["mlen"], s["rk"]:s["rk"] + s["klen"]] += 1
     return cnt
 
@@ -60,7 +64,10 @@ def test_blocks_tile_the_triangle_once(op, gemm, b, k):
     assert np.all(cnt[low] == 1)
     assert np.all(cnt[~low] == 0)
     for s in steps:
-        if s["kind"] == "gemm":
+        if s["kind"] == "gemm" and s["dense"]:
+            assert op == "M" and s["tc"] and s["rc"] == s["rk"] and s["beta"] == s["gamma"]
+            assert s["klen"] % 32 == 0 and s["mlen"] <= s["klen"] < s["mlen"] + 32
+        elif s["kind"] == "gemm":
             assert s["rk"] + s["klen"] <= s["rc"]           # strictly below
             if s["tc"]:
                 assert s["klen"] % 64 == 0 and s["rk"] % 8 == 0
@@ -113,6 +120,12 @@ def replay(op, steps, M, C, alpha_seen=2.0):
                     Y[r:e] = C[r:e]
                 else:
                     C[r:e] = s["alpha"] * (L @ C[r:e])
+        elif s["kind"] == "gemm" and s["dense"]:
+            # per-row beta times the diagonal on C's old value, the strictly
+            # lower part of the block from the Y planes
+            r, e = s["rc"], min(k, s["rc"] + s["mlen"])
+            d = np.diag(M[r:e, r:e])[:, None]
+            C[r:e] = s["beta"] * d * C[r:e] + s["gamma"] * (np.tril(M[r:e, r:e], -1) @ Y[r:e])
         elif s["kind"] == "gemm":
             src = Y if (s["tc"] and op == "M") else C
             rc, rk = s["rc"], s["rk"]
@@ -135,10 +148,30 @@ def test_replay_matches_oracle(op, gemm, b, k):
     np.testing.assert_allclose(got, want, rtol=1e-10, atol=1e-10 * np.abs(want).max())
 
 
+@pytest.mark.parametrize("dense", [64, 128, 256, 512])
+@pytest.mark.parametrize("k", [65, 300, 513, 1100])
+@pytest.mark.parametrize("unit", ["N", "U"])
+def test_trmm_dense_replay_matches_oracle(dense, k, unit):
+    # TRMM leaves as dense diagonal-block GEMMs (Y planes hold the original
+    # right-hand side; the diagonal term through the per-row beta)
+    n = 5
+    A, B = inputs.problem("L", "L", k, n, seed=k + dense, dtype=np.float64)
+    M = np.where(np.isnan(A), 0.0, A)
+    if unit == "U":
+        np.fill_diagonal(M, 1.0)
+    steps = debug_plan("M", "L", "L", "N", unit, k, n, 4, 0, 2, dense)
+    assert steps[0] == {"kind": "conv_m", "diag_block": dense}
+    assert any(s.get("dense") for s in steps) and not any(s["kind"] == "leaf" for s in steps)
+    assert np.all(coverage(k, steps)[np.tril(np.ones((k, k), dtype=bool))] == 1)
+    got = replay("M", steps, M, B)
+    want = oracle.trmm("L", "L", "N", unit, 2.0, A, B)
+    np.testing.assert_allclose(got, want, rtol=1e-10, atol=1e-10 * np.abs(want).max())
+
+
 def test_trmm_level_batching():
     # b a multiple of the K tile on the tensor-core path: one launch for all
     # leaves, then one grouped launch per level with disjoint output rows.
-    steps = debug_plan("M", "L", "L", "N", "N", 16384, 16384, 4, 64, 0)
+    steps = debug_plan("M", "L", "L", "N", "N", 16384, 16384, 4, 64, 0, -1)
     kinds = [s["kind"] for s in steps]
     assert kinds[:3] == ["conv_m", "conv_y", "leaf"] and steps[2]["nleaves"] == 256
     gemms = [s for s in steps if s["kind"] == "gemm"]
@@ -158,14 +191,42 @@ def test_trmm_level_batching():
         assert rows.max() == 1
 
 
+def test_trmm_dense_diagonal_blocks_by_default():
+    # automatic at order >= 1024: 256-row dense diagonal blocks in one grouped
+    # launch, then one launch per level above them (node sizes 16384 .. 512)
+    steps = debug_plan("M", "L", "L", "N", "N", 16384, 16384, 4, 0, 0)
+    assert steps[0] == {"kind": "conv_m", "diag_block": 256}
+    assert steps[1]["kind"] == "conv_y"
+    dense = [s for s in steps if s["kind"] == "gemm" and s["dense"]]
+    assert len(dense) == 64 and all(s["mlen"] == 256 and s["beta"] == 2.0 for s in dense)
+    assert not any(s["kind"] == "leaf" for s in steps)
+    levels = [s for s in steps if s["kind"] == "gemm" and not s["dense"]]
+    assert len(levels) == 63 and min(s["klen"] for s in levels) == 256
+    # below the order threshold, with an explicit leaf, or switched off: leaves
+    for args in [(1000, 0, 0), (16384, 64, 0), (16384, 0, -1)]:
+        k, leaf, dense_opt = args
+        steps = debug_plan("M", "L", "L", "N", "N", k, 64, 4, leaf, 0, dense_opt)
+        assert steps[0]["diag_block"] == 0 and any(s["kind"] == "leaf" for s in steps)
+    # TRSM never uses it
+    steps = debug_plan("S", "L", "L", "N", "N", 16384, 64, 4, 0, 0, 256)
+    assert steps[0]["diag_block"] == 0 and not any(s.get("dense") for s in steps)
+
+
 def test_trsm_block_leaves_on_request():
     # cutoff 256 (TRSM block leaves) only when asked for; TRMM stops at 128
     leaves = [s for s in debug_plan("S", "L", "L", "N", "N", 16384, 16384, 4, 256, 0)
               if s["kind"] == "leaf"]
     assert len(leaves) == 64 and all(s["b"] == 256 for s in leaves)
+    # automatic: 128-row (wide) leaves for FP32 TRSM with many right-hand
+    # sides, 64-row leaves otherwise
     leaves = [s for s in debug_plan("S", "L", "L", "N", "N", 16384, 16384, 4, 0, 0)
               if s["kind"] == "leaf"]
-    assert len(leaves) == 256
+    assert len(leaves) == 128 and all(s["b"] == 128 for s in leaves)
+    for args in [("L", 16384, 4096, 4), ("L", 16384, 16384, 8), ("R", 4096, 16384, 4)]:
+        side, m, n, elem = args
+        leaves = [s for s in debug_plan("S", side, "L", "N", "N", m, n, elem, 0, 0)
+                  if s["kind"] == "leaf"]
+        assert all(s["b"] == 64 for s in leaves), args
     leaves = [s for s in debug_plan("M", "L", "L", "N", "N", 16384, 16384, 4, 256, 0)
               if s["kind"] == "leaf"]
     assert leaves[0]["b"] == 128
