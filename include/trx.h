@@ -89,14 +89,15 @@ enum {
                               prologue overlaps the previous one's tail;
                               0 (default): plain stream order              */
     TRX_OPT_TRMM_DENSE = 8 /* FP32 TRMM on the tensor-core path: leaves of
-                              this many rows (64, 128, 256 or 512) formed in
-                              one grouped GEMM launch over dense diagonal
-                              blocks (the block's strictly-lower part on the
-                              tensor cores, zeros above; the diagonal term
-                              in FP32 in the epilogue), replacing the leaf
-                              kernel and the recursion levels below that
-                              size;
-                              -1 off; 0 = automatic (default: 256 rows when
+                              this many rows (64 .. 2048, a power of two)
+                              formed in one grouped GEMM launch over the
+                              diagonal blocks (the block's strictly-lower
+                              part on the tensor cores in 128-row tiles,
+                              each tile's K range ending at its last row;
+                              the diagonal term in FP32 in the epilogue),
+                              replacing the leaf kernel and the recursion
+                              levels below that size;
+                              -1 off; 0 = automatic (default: 1024 rows when
                               the order is at least 1024 and TRX_OPT_LEAF
                               is automatic, else off)                     */
 };

@@ -49,7 +49,7 @@ constexpr int64_t kWideLeafMinRhs = 8192;
 constexpr long long kDefaultWaitNs = 2000000000LL;   // 2 s
 constexpr int64_t kTcMinOrder = 256;                 // auto: tensor cores from this order
 constexpr int64_t kTrmmDenseMinOrder = 1024;         // auto: dense TRMM diagonal blocks from here
-constexpr int kTrmmDenseRows = 256;                  // auto: their size
+constexpr int kTrmmDenseRows = 1024;                 // auto: their size
 constexpr size_t kGraphCacheSize = 16;
 constexpr int64_t kBatchMaxK = TRX_BATCH_MAX_K;
 constexpr int kMaxPanels = 4;
@@ -192,7 +192,10 @@ void plan_trmm_seq(Plan& pl, int64_t r0, int64_t s, int b, double alpha) {
 // every leaf product at once,
 //   C[i] = alpha * M(i,i) * C[i] + alpha * sum_{r <= l < i} M(i,l) * Y[l],
 // the diagonal term in FP32 from C's original value (a per-row beta in the
-// GEMM epilogue) and the rest on the tensor cores.
+// GEMM epilogue) and the rest on the tensor cores. Each 128-row tile of a
+// block is its own group member whose K range ends at the tile's last row,
+// so no tile multiplies the zeros above the diagonal beyond its own 128
+// columns.
 void plan_trmm_levels(Plan& pl, int64_t k, int b, double alpha, bool dense = false) {
     if (dense) {
         Step d{kGemm};
@@ -202,7 +205,10 @@ void plan_trmm_levels(Plan& pl, int64_t k, int b, double alpha, bool dense = fal
         d.gamma = alpha;
         for (int64_t r = 0; r < k; r += b) {
             const int64_t len = std::min<int64_t>(b, k - r);
-            d.gemms.push_back(TcGemm{r, len, r, round_up(len, 32)});
+            for (int64_t t = 0; t < len; t += 128) {
+                const int64_t mlen = std::min<int64_t>(128, len - t);
+                d.gemms.push_back(TcGemm{r + t, mlen, r, round_up(t + mlen, 32)});
+            }
         }
         pl.steps.push_back(d);
     } else {
@@ -257,7 +263,7 @@ void make_plan(Plan& plan, bool trsm, int64_t k, int b, double alpha, bool conv_
 }
 
 // Rows of the dense TRMM diagonal blocks: the handle's TRX_OPT_TRMM_DENSE
-// (-1 off, else the size), or automatically 256 once the order reaches 1024
+// (-1 off, else the size), or automatically 1024 once the order reaches 1024
 // and the leaf size was left automatic. Tensor-core path only.
 int trmm_dense_mode(int64_t opt, int64_t opt_leaf, bool tc, int64_t k) {
     if (!tc || opt < 0) return 0;
@@ -447,9 +453,11 @@ struct Exec {
                         cls = TRX_KERNEL_GEMM_SIMT;
                     }
                     for (const TcGemm& g : st.gemms) {
-                        if (st.dense) {      // triangular block: b^2 n
-                            flops += (double)g.mlen * g.mlen * c.nrhs;
-                            bytes += w * ((double)g.mlen * (g.mlen + 1) / 2 + 3.0 * g.mlen * c.nrhs);
+                        if (st.dense) {      // rows of a triangular block: (i+1) 2n each
+                            const double i0 = (double)(g.rc - g.rk);
+                            flops += (double)c.nrhs * g.mlen * (2.0 * i0 + g.mlen + 1);
+                            bytes += w * ((double)g.mlen * (i0 + (g.mlen + 1) / 2.0) +
+                                          3.0 * g.mlen * c.nrhs);
                         } else {
                             flops += 2.0 * g.mlen * g.klen * c.nrhs;
                             bytes += w * ((double)g.mlen * g.klen + 2.0 * g.mlen * c.nrhs +
@@ -1136,7 +1144,7 @@ int trx_set_option(trx_handle_t h, int option, int64_t value) {
             break;
         case TRX_OPT_TRMM_DENSE:
             if (value != -1 && value != 0 && value != 64 && value != 128 && value != 256 &&
-                value != 512)
+                value != 512 && value != 1024 && value != 2048)
                 return TRX_ERR_INVALID_VALUE;
             h->opt_trmm_dense = value;
             break;
@@ -1233,7 +1241,7 @@ int trx_debug_plan(char op, char side, char uplo, char transa, char diag, int64_
         gemm_mode < 0 ||
         gemm_mode > 2 || !buf || buflen == 0 ||
         (trmm_dense != -1 && trmm_dense != 0 && trmm_dense != 64 && trmm_dense != 128 &&
-         trmm_dense != 256 && trmm_dense != 512))
+         trmm_dense != 256 && trmm_dense != 512 && trmm_dense != 1024 && trmm_dense != 2048))
         return TRX_ERR_INVALID_VALUE;
     buf[0] = 0;
     const int64_t k = upc(side) == 'L' ? m : n;

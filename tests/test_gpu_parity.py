@@ -86,7 +86,7 @@ def test_wide_leaf_single(trx, k):
     h.close()
 
 
-@pytest.mark.parametrize("dense", [-1, 64, 128, 256, 512])
+@pytest.mark.parametrize("dense", [-1, 64, 128, 256, 512, 1024, 2048])
 @pytest.mark.parametrize("variant", [("L", "L", "N", "N"), ("R", "U", "T", "U")])
 def test_trmm_dense_sizes(trx, dense, variant):
     h = trx.Handle(0)

@@ -43,8 +43,10 @@ def coverage(k, steps):
         cnt[r:e, r:e] += blk
     for s in steps:
         if s["kind"] == "gemm" and s.get("dense"):
-            # dense diagonal block: its lower triangle with the diagonal
+            # a tile of a dense diagonal block: the full columns left of its
+            # rows, and its own lower triangle with the diagonal
             r, e = s["rc"], min(k, s["rc"] + s["mlen"])
+            cnt[r:e, s["rk"]:r] += 1
             cnt[r:e, r:e] += np.tril(np.ones((e - r, e - r), dtype=np.int32))
         elif s["kind"] == "gemm":
             cnt[s["rc"]:s["rc"] + s["mlen"], s["rk"]:s["rk"] + s["klen"]] += 1
@@ -65,8 +67,10 @@ def test_blocks_tile_the_triangle_once(op, gemm, b, k):
     assert np.all(cnt[~low] == 0)
     for s in steps:
         if s["kind"] == "gemm" and s["dense"]:
-            assert op == "M" and s["tc"] and s["rc"] == s["rk"] and s["beta"] == s["gamma"]
-            assert s["klen"] % 32 == 0 and s["mlen"] <= s["klen"] < s["mlen"] + 32
+            assert op == "M" and s["tc"] and s["beta"] == s["gamma"]
+            assert s["mlen"] <= 128 and s["rk"] <= s["rc"] and (s["rc"] - s["rk"]) % 128 == 0
+            top = s["rc"] + s["mlen"] - s["rk"]                 # K ends at the tile's last row
+            assert s["klen"] % 32 == 0 and top <= s["klen"] < top + 32
         elif s["kind"] == "gemm":
             assert s["rk"] + s["klen"] <= s["rc"]           # strictly below
             if s["tc"]:
@@ -122,10 +126,11 @@ def replay(op, steps, M, C, alpha_seen=2.0):
                     C[r:e] = s["alpha"] * (L @ C[r:e])
         elif s["kind"] == "gemm" and s["dense"]:
             # per-row beta times the diagonal on C's old value, the strictly
-            # lower part of the block from the Y planes
-            r, e = s["rc"], min(k, s["rc"] + s["mlen"])
+            # lower part of the tile's rows (columns rk .. row) from the Y planes
+            r, e, rk = s["rc"], min(k, s["rc"] + s["mlen"]), s["rk"]
             d = np.diag(M[r:e, r:e])[:, None]
-            C[r:e] = s["beta"] * d * C[r:e] + s["gamma"] * (np.tril(M[r:e, r:e], -1) @ Y[r:e])
+            C[r:e] = s["beta"] * d * C[r:e] + s["gamma"] * (
+                M[r:e, rk:r] @ Y[rk:r] + np.tril(M[r:e, r:e], -1) @ Y[r:e])
         elif s["kind"] == "gemm":
             src = Y if (s["tc"] and op == "M") else C
             rc, rk = s["rc"], s["rk"]
@@ -148,8 +153,8 @@ def test_replay_matches_oracle(op, gemm, b, k):
     np.testing.assert_allclose(got, want, rtol=1e-10, atol=1e-10 * np.abs(want).max())
 
 
-@pytest.mark.parametrize("dense", [64, 128, 256, 512])
-@pytest.mark.parametrize("k", [65, 300, 513, 1100])
+@pytest.mark.parametrize("dense", [64, 128, 256, 512, 1024, 2048])
+@pytest.mark.parametrize("k", [65, 300, 513, 1100, 2500])
 @pytest.mark.parametrize("unit", ["N", "U"])
 def test_trmm_dense_replay_matches_oracle(dense, k, unit):
     # TRMM leaves as dense diagonal-block GEMMs (Y planes hold the original
@@ -192,16 +197,18 @@ def test_trmm_level_batching():
 
 
 def test_trmm_dense_diagonal_blocks_by_default():
-    # automatic at order >= 1024: 256-row dense diagonal blocks in one grouped
-    # launch, then one launch per level above them (node sizes 16384 .. 512)
+    # automatic at order >= 1024: 1024-row diagonal blocks in one grouped
+    # launch (128-row tiles, K up to each tile's last row), then one launch
+    # per level above them (node sizes 16384 .. 2048)
     steps = debug_plan("M", "L", "L", "N", "N", 16384, 16384, 4, 0, 0)
-    assert steps[0] == {"kind": "conv_m", "diag_block": 256}
+    assert steps[0] == {"kind": "conv_m", "diag_block": 1024}
     assert steps[1]["kind"] == "conv_y"
     dense = [s for s in steps if s["kind"] == "gemm" and s["dense"]]
-    assert len(dense) == 64 and all(s["mlen"] == 256 and s["beta"] == 2.0 for s in dense)
+    assert len(dense) == 128 and all(s["mlen"] == 128 and s["beta"] == 2.0 for s in dense)
+    assert sorted({s["klen"] for s in dense}) == list(range(128, 1025, 128))
     assert not any(s["kind"] == "leaf" for s in steps)
     levels = [s for s in steps if s["kind"] == "gemm" and not s["dense"]]
-    assert len(levels) == 63 and min(s["klen"] for s in levels) == 256
+    assert len(levels) == 15 and min(s["klen"] for s in levels) == 1024
     # below the order threshold, with an explicit leaf, or switched off: leaves
     for args in [(1000, 0, 0), (16384, 64, 0), (16384, 0, -1)]:
         k, leaf, dense_opt = args
