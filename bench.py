@@ -18,6 +18,7 @@ loop, OpenMP) on a bounded sample of the same workload's right-hand sides.
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import os
 import statistics
@@ -39,6 +40,31 @@ ALPHA = 1.5
 SEED = 16384
 CPU_SAMPLE_COLS = 32      # cpu_baseline sample (right-hand sides)
 REF_SAMPLE_COLS = 16      # per step of --impl reference
+
+
+# DRAM traffic of gemm_tc_kernel per launch on this workload, from one ncu
+# capture (dram__bytes_read.sum + dram__bytes_write.sum summed over one step's
+# gemm_tc launches, divided by their number). It holds for the sources it was
+# taken on only: when the GEMM kernel or the planner has changed since, the
+# line reports null. The capture's summary and command are in profiles/.
+TRAFFIC_SOURCES = ("paper_2504_13821_gb300/csrc/gemm_tc.cu", "paper_2504_13821_gb300/csrc/api.cu")
+TRAFFIC_CAPTURE = {"sources_sha256": "ea51c2ad45e9f526fce86860472bf4c533429f53aed48234c433124eb42c5b74",
+                   "bytes_per_launch": 260782536, "launches_per_step": 132,
+                   "profile": "profiles/gemm_tc_traffic_trsm_trmm_n16384.md"}
+
+
+def sources_sha256():
+    h = hashlib.sha256()
+    for f in TRAFFIC_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def captured_traffic():
+    if not TRAFFIC_CAPTURE or TRAFFIC_CAPTURE["sources_sha256"] != sources_sha256():
+        return None
+    return TRAFFIC_CAPTURE["bytes_per_launch"]
 
 
 def flops_per_call(k, nrhs):
@@ -189,7 +215,7 @@ def run_reference(args):
 
 
 # automatic cutoffs of the library for this workload (FP32, 16384 right-hand
-# sides): TRSM 128-row leaves (wide leaf kernel), TRMM 256-row diagonal blocks
+# sides): TRSM 128-row leaves (wide leaf kernel), TRMM 1024-row diagonal blocks
 # on the tensor cores; --leaf overrides both
 # (FP64: 64-row leaves)
 LEAF_USED = None
@@ -201,7 +227,7 @@ def workload_config():
                         f"no transpose, non-unit, m={K_ORDER} n={NRHS}, column-major",
             "m": K_ORDER, "n": NRHS,
             "leaf": LEAF_USED if LEAF_USED is not None else (
-                "TRSM 128 (wide leaf), TRMM 256-row dense diagonal blocks"
+                "TRSM 128 (wide leaf), TRMM 1024-row diagonal blocks on the tensor cores"
                 if DTYPE == np.float32 else 64),
             "gemm": ("tcgen05 kind::f16, 3-term split BF16, FP32 accumulation"
                      if DTYPE == np.float32 else "CUDA-core DFMA"),
@@ -293,7 +319,9 @@ def run_gpu(args):
         "bound": "tensor" if DTYPE == np.float32 else "fp64",
         "kernel": kname,
         "achieved": achieved, "peak": peak_tc, "unit": "TFLOP/s",
-        "frac": achieved / peak_tc if peak_tc else None, "traffic": None,
+        "frac": achieved / peak_tc if peak_tc else None,
+        "traffic": captured_traffic() if DTYPE == np.float32 else None,
+        "algorithmic_bytes_per_launch": g["bytes"] / g["launches"] if g["launches"] else None,
         "peak_source": peak_src,
         "launches_per_step": g["launches"],
         "share_of_kernel_time": g["ms"] / kern_ms if kern_ms else None,
