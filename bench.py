@@ -323,6 +323,11 @@ def run_gpu(args):
         "traffic": captured_traffic() if DTYPE == np.float32 else None,
         "algorithmic_bytes_per_launch": g["bytes"] / g["launches"] if g["launches"] else None,
         "peak_source": peak_src,
+        # the same kernel against the raw BF16 tensor peak: every algorithmic
+        # flop is three BF16 products on the pipe
+        "tensor_pipe_tflops": 3.0 * achieved if DTYPE == np.float32 else None,
+        "frac_of_raw_bf16_burst": (3.0 * achieved / peaks["bf16_tflops"]
+                                   if DTYPE == np.float32 else None),
         "launches_per_step": g["launches"],
         "share_of_kernel_time": g["ms"] / kern_ms if kern_ms else None,
         "per_class_ms": {kk: round(v["ms"], 4) for kk, v in prof.items() if v["launches"]},

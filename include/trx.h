@@ -68,7 +68,7 @@ enum {
     TRX_OPT_LEAF = 1,      /* leaf cutoff b (Section 3.1 "chosen threshold"):
                               16, 32, 64, 128 or 256 (256: TRSM block
                               leaves; TRMM stops at 128); 0 = automatic
-                              (default, 64)                                */
+                              (default: 128 for FP32 TRSM, else 64)        */
     TRX_OPT_GEMM = 2,      /* FP32 GEMM-update engine: 0 automatic, 1 CUDA
                               cores (FP32 FMA), 2 tensor cores (tcgen05,
                               3-term split BF16, FP32 accumulation)         */

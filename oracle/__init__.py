@@ -7,6 +7,11 @@ shares no code with the CUDA path. The arithmetic lives in ``trx_oracle.c``
 independent right-hand sides); this module builds it with gcc on first use
 and wraps it for numpy arrays.
 
+Also here: the 1-norm condition estimate of a factor (Hager's method with
+Higham's refinements, on the oracle's own solves) and the bisection on the
+generator's off-diagonal scale that reaches a target condition number, for
+the precision-form configuration.
+
 Parity status: pinned (see ``tests/test_oracle_pins.py``).
 """
 from __future__ import annotations
@@ -152,6 +157,79 @@ def forward_error(X_hat, X_ref) -> float:
     den = np.abs(X_ref).sum(axis=1).max()
     num = np.abs(X_hat - X_ref).sum(axis=1).max()
     return float(num / den) if den > 0 else float(num)
+
+
+def op_norm_one(uplo, trans, diag, A) -> float:
+    """||op(A)||_1 over the referenced triangle (unit diagonal counts 1):
+    the infinity norm of op(A)^T."""
+    t = {"N": "T", "T": "N", "C": "N"}[trans.upper()]
+    return op_norm_inf(uplo, t, diag, A)
+
+
+def inv_norm_one_estimate(uplo, trans, diag, A, itmax: int = 5) -> float:
+    """Lower-bound estimate of ||op(A)^-1||_1 by Hager's method with Higham's
+    refinements (Higham, "FORTRAN codes for estimating the one-norm of a real
+    or complex matrix", ACM TOMS 14, 1988): power-like iterations on the
+    convex set ||x||_1 <= 1, each one solve with op(A) and one with op(A)^T,
+    then the alternating test vector; the larger of the two estimates.
+    The solves are the oracle's own substitution."""
+    A = _f64(A)
+    k = A.shape[0]
+    if k == 0:
+        return 0.0
+    t = {"N": "T", "T": "N", "C": "N"}[trans.upper()]
+
+    def solve(op, v):
+        return trsm("L", uplo, op, diag, 1.0, A, np.asfortranarray(v.reshape(k, 1)))[:, 0]
+
+    x = np.full(k, 1.0 / k)
+    est = 0.0
+    prev_j = -1
+    for it in range(itmax):
+        y = solve(trans, x)                       # op(A) y = x
+        est_new = float(np.abs(y).sum())
+        if it > 0 and est_new <= est:
+            break
+        est = est_new
+        xi = np.where(y >= 0, 1.0, -1.0)
+        z = solve(t, xi)                          # op(A)^T z = sign(y)
+        j = int(np.argmax(np.abs(z)))
+        if np.abs(z).max() <= z @ x or j == prev_j:   # x is a local maximum
+            break
+        x = np.zeros(k)
+        x[j] = 1.0
+        prev_j = j
+    # alternating-sign vector with linearly growing entries
+    alt = np.array([(-1.0) ** i * (1.0 + i / max(k - 1, 1)) for i in range(k)])
+    est_alt = 2.0 * float(np.abs(solve(trans, alt)).sum()) / (3.0 * k)
+    return max(est, est_alt)
+
+
+def cond_one_estimate(uplo, trans, diag, A) -> float:
+    """kappa_1(op(A)) ~ ||op(A)||_1 * est ||op(A)^-1||_1 (a lower bound up to
+    rounding)."""
+    return op_norm_one(uplo, trans, diag, A) * inv_norm_one_estimate(uplo, trans, diag, A)
+
+
+def scale_for_condition(k: int, target: float, *, seed: int, uplo: str = "L",
+                        lo: float = 1e-3, hi: float = 1e4, steps: int = 40) -> float:
+    """Off-diagonal scale s of the input generator (strict triangle
+    uniform(-1,1) * s / k) whose factor has kappa_1 close to ``target``, by
+    bisection on log s with the estimator above (kappa grows with s)."""
+    from paper_2504_13821_gb300 import inputs
+
+    def kappa(s):
+        A = inputs.tri_matrix(k, uplo, seed=seed, dtype=np.float64, scale=s)
+        return cond_one_estimate(uplo, "N", "N", A)
+
+    a, b = np.log(lo), np.log(hi)
+    for _ in range(steps):
+        mid = 0.5 * (a + b)
+        if kappa(np.exp(mid)) < target:
+            a = mid
+        else:
+            b = mid
+    return float(np.exp(0.5 * (a + b)))
 
 
 def nthreads() -> int:

@@ -40,12 +40,12 @@ namespace {
 
 constexpr int kMagic = 0x54525831;  // "TRX1"
 constexpr int kDefaultLeaf = 64;
-// Automatic cutoff for FP32 TRSM with many right-hand sides: 128-row leaves
-// (one wide-leaf launch in place of two 64-row leaves and the update between
-// them; measured faster at 16384 right-hand sides). Block leaves (256) are
-// never chosen automatically (measured slower); TRX_OPT_LEAF = 256 asks.
-constexpr int kWideLeaf = 128;
-constexpr int64_t kWideLeafMinRhs = 8192;
+// Automatic cutoff for FP32 TRSM: 128-row leaves (one leaf launch in place of
+// two 64-row leaves and the update between them; measured faster at 256 ..
+// 16384 right-hand sides, with the wide leaf kernel from 1024). Block leaves
+// (256) are never chosen automatically (measured slower); TRX_OPT_LEAF = 256
+// asks.
+constexpr int kF32TrsmLeaf = 128;
 constexpr long long kDefaultWaitNs = 2000000000LL;   // 2 s
 constexpr int64_t kTcMinOrder = 256;                 // auto: tensor cores from this order
 constexpr int64_t kTrmmDenseMinOrder = 1024;         // auto: dense TRMM diagonal blocks from here
@@ -382,19 +382,20 @@ cudaEvent_t get_event(trx_handle_t h) {
 }
 
 
-// Recursion cutoff: TRX_OPT_LEAF when set, else 128 for FP32 TRSM with many
-// right-hand sides and 64 otherwise. With 256 a TRSM's leaves run as block
-// leaves (one launch per 256 rows); TRMM leaves stop at 128 rows.
+// Recursion cutoff: TRX_OPT_LEAF when set, else 128 for FP32 TRSM and 64
+// otherwise. With 256 a TRSM's leaves run as block leaves (one launch per 256
+// rows); TRMM leaves stop at 128 rows.
 int leaf_for(int64_t opt_leaf, int64_t k, bool trsm, int elem, int64_t nrhs) {
     int b = kDefaultLeaf;
     if (opt_leaf > 0) b = (int)opt_leaf;
-    else if (trsm && elem == 4 && nrhs >= kWideLeafMinRhs) b = kWideLeaf;
+    else if (trsm && elem == 4) b = kF32TrsmLeaf;
     if (!trsm && b > kMaxLeaf) b = kMaxLeaf;
+    (void)nrhs;
     return (int)std::min<int64_t>(b, std::max<int64_t>(k, 1));
 }
 
 bool use_tc_mode(int elem, int64_t gemm_mode, int64_t k, int b) {
-    if (elem != 4 || gemm_mode == 1) return false;
+    if (elem != 4 || gemm_mode == 1 || k <= b) return false;   // k <= b: one leaf, no update
     if (gemm_mode == 2) return k > b;
     return k >= kTcMinOrder;
 }

@@ -60,6 +60,31 @@ def test_trmm_dense_diagonal_blocks_all_variants(trx, side, uplo, trans, diag):
              seed=inputs.variant_seed(1100, VARIANTS.index((side, uplo, trans, diag))))
 
 
+@pytest.mark.parametrize("op", ["trsm", "trmm"])
+@pytest.mark.parametrize("side", ["L", "R"])
+def test_two_panels_equal_one_call(trx, op, side):
+    """Right-hand-side sharding (one panel per rank) run as two calls on one
+    GPU: the gathered panels equal the single call (same plan choices:
+    cutoff fixed, sizes under the automatic thresholds), bitwise."""
+    from paper_2504_13821_gb300.sharding import solve_panel
+    m, n = (2048, 4000) if side == "L" else (4000, 2048)
+    A, B = inputs.problem(side, "U", m, n, seed=4000, dtype=np.float32)
+    At = to_dev(A, "cuda:0")
+    whole, parts = to_dev(B, "cuda:0"), to_dev(B, "cuda:0")
+    h = trx.Handle(0)
+    h.set_option(trx.OPT_LEAF, 64)
+    fn = trx.trsm if op == "trsm" else trx.trmm
+    fn(side, "U", "T", "N", 1.25, At, whole, handle=h)
+    covered = []
+    for rank in range(2):
+        covered.append(solve_panel("S" if op == "trsm" else "M", side, "U", "T", "N", 1.25, At,
+                                   parts, 2, rank, handle=h))
+    torch.cuda.synchronize()
+    assert covered[0][0] == 0 and covered[0][1] == covered[1][0] and covered[1][1] == 4000
+    assert torch.equal(whole, parts)
+    h.close()
+
+
 @pytest.mark.parametrize("engine", [1, 2], ids=["cuda_cores", "tensor_cores"])
 @pytest.mark.parametrize("side,uplo,trans,diag", VARIANTS)
 def test_wide_leaves_all_variants(trx, side, uplo, trans, diag, engine):
@@ -172,11 +197,17 @@ def test_column_panel_branches(trx, variant):
 def test_profile_counts_launches(trx):
     h = trx.Handle(0)
     h.set_option(trx.OPT_PROFILE, 1)
+    h.set_option(trx.OPT_LEAF, 64)
     run_case("trsm", "L", "L", "N", "N", 1024, 512, 1.0, np.float32, seed=1, handle=h)
     p = h.profile(reset=True)
     assert p["gemm_tc"]["launches"] == 15 and p["leaf_trsm"]["launches"] == 16
     assert p["gemm_tc"]["ms"] > 0 and p["gemm_tc"]["flops"] > 0
     assert h.profile()["gemm_tc"]["launches"] == 0
+    # automatic cutoff for FP32 TRSM: 128-row leaves
+    h.set_option(trx.OPT_LEAF, 0)
+    run_case("trsm", "L", "L", "N", "N", 1024, 512, 1.0, np.float32, seed=1, handle=h)
+    p = h.profile(reset=True)
+    assert p["leaf_trsm"]["launches"] == 8 and p["gemm_tc"]["launches"] == 7
     h.close()
 
 

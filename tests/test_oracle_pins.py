@@ -303,3 +303,44 @@ def test_backward_error_residual_is_twice_working_precision():
     exact = float(max(exact_rows))
     assert exact > 0
     assert abs(r["res"] - exact) <= 1e-6 * exact
+
+
+# ---- condition estimate (inputs of the precision-form configuration) ------
+
+def _exact_kappa_one(uplo, trans, diag, A):
+    T = np.where(np.isnan(A), 0.0, np.asarray(A, dtype=np.float64))
+    T = np.tril(T) if uplo == "L" else np.triu(T)
+    if diag == "U":
+        np.fill_diagonal(T, 1.0)
+    op = T if trans == "N" else T.T
+    return np.abs(op).sum(axis=0).max() * np.abs(np.linalg.inv(op)).sum(axis=0).max()
+
+
+def test_cond_estimate_closed_forms():
+    # identity: 1; diagonal: max|d| / min|d|; unit lower bidiagonal with -1
+    # below: ||T||_1 = 2 and T^-1 is the lower triangle of ones, ||T^-1||_1 = k
+    k = 40
+    assert oracle.cond_one_estimate("L", "N", "N", np.eye(k)) == pytest.approx(1.0, rel=1e-14)
+    d = np.linspace(0.5, 8.0, k)
+    assert oracle.cond_one_estimate("U", "T", "N", np.diag(d)) == pytest.approx(16.0, rel=1e-14)
+    T = np.eye(k) - np.eye(k, k=-1)
+    assert oracle.cond_one_estimate("L", "N", "N", T) == pytest.approx(2.0 * k, rel=1e-14)
+    assert oracle.cond_one_estimate("U", "T", "U", T.T) == pytest.approx(2.0 * k, rel=1e-14)
+
+
+@pytest.mark.parametrize("k", [2, 7, 33, 120])
+@pytest.mark.parametrize("uplo,trans", [("L", "N"), ("U", "N"), ("L", "T"), ("U", "T")])
+def test_cond_estimate_is_a_close_lower_bound(k, uplo, trans):
+    A = inputs.tri_matrix(k, uplo, seed=3 * k, dtype=np.float64, scale=4.0)
+    exact = _exact_kappa_one(uplo, trans, "N", A)
+    est = oracle.cond_one_estimate(uplo, trans, "N", A)
+    assert est <= exact * (1 + 1e-10)
+    assert est >= exact / 3
+
+
+@pytest.mark.parametrize("target", [1e2, 1e4])
+def test_scale_for_condition_hits_the_target(target):
+    s = oracle.scale_for_condition(128, target, seed=5)
+    A = inputs.tri_matrix(128, "L", seed=5, dtype=np.float64, scale=s)
+    kappa = _exact_kappa_one("L", "N", "N", A)
+    assert target / 3 <= kappa <= 3 * target

@@ -224,16 +224,17 @@ def test_trsm_block_leaves_on_request():
     leaves = [s for s in debug_plan("S", "L", "L", "N", "N", 16384, 16384, 4, 256, 0)
               if s["kind"] == "leaf"]
     assert len(leaves) == 64 and all(s["b"] == 256 for s in leaves)
-    # automatic: 128-row (wide) leaves for FP32 TRSM with many right-hand
-    # sides, 64-row leaves otherwise
-    leaves = [s for s in debug_plan("S", "L", "L", "N", "N", 16384, 16384, 4, 0, 0)
-              if s["kind"] == "leaf"]
-    assert len(leaves) == 128 and all(s["b"] == 128 for s in leaves)
-    for args in [("L", 16384, 4096, 4), ("L", 16384, 16384, 8), ("R", 4096, 16384, 4)]:
-        side, m, n, elem = args
-        leaves = [s for s in debug_plan("S", side, "L", "N", "N", m, n, elem, 0, 0)
+    # automatic: 128-row leaves for FP32 TRSM (any number of right-hand
+    # sides), 64-row leaves for FP64
+    for args in [("L", 16384, 16384), ("L", 16384, 256), ("R", 300, 3000)]:
+        side, m, n = args
+        leaves = [s for s in debug_plan("S", side, "L", "N", "N", m, n, 4, 0, 0)
                   if s["kind"] == "leaf"]
-        assert all(s["b"] == 64 for s in leaves), args
+        k = m if side == "L" else n
+        assert len(leaves) == -(-k // 128) and leaves[0]["b"] == 128, args
+    leaves = [s for s in debug_plan("S", "L", "L", "N", "N", 16384, 16384, 8, 0, 0)
+              if s["kind"] == "leaf"]
+    assert all(s["b"] == 64 for s in leaves)
     leaves = [s for s in debug_plan("M", "L", "L", "N", "N", 16384, 16384, 4, 256, 0)
               if s["kind"] == "leaf"]
     assert leaves[0]["b"] == 128
@@ -244,3 +245,6 @@ def test_fp64_and_small_orders_use_cuda_cores():
     assert all(s["kind"] not in ("conv_m", "conv_y")
                for s in debug_plan("S", "L", "L", "N", "N", 200, 8, 4, 0, 0))
     assert any(s.get("tc", 0) for s in debug_plan("S", "L", "L", "N", "N", 256, 8, 4, 0, 0))
+    # one leaf covering the whole order: no update, so no operand planes
+    assert not any(s["kind"] in ("conv_m", "conv_y") or s.get("tc", 0)
+                   for s in debug_plan("S", "L", "L", "N", "N", 100, 8, 4, 0, 0))
