@@ -46,6 +46,22 @@ struct Wide {
     static constexpr size_t smem = sizeof(float) * ((size_t)B * B + B + (size_t)GROUPS * B * LDC);
 };
 
+// Packed FP32 pairs (Blackwell's f32x2 FMA: two independent
+// round-to-nearest FMAs per instruction).
+__device__ __forceinline__ uint64_t pack2(float a, float b) {
+    uint64_t r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ void unpack2(uint64_t r, float& a, float& b) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(r));
+}
+__device__ __forceinline__ uint64_t ffma2(uint64_t a, uint64_t b, uint64_t c) {
+    uint64_t d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+
 __device__ __forceinline__ void group_sync(int g) {
     asm volatile("bar.sync %0, %1;" ::"r"(1 + g), "r"(Wide::GT) : "memory");
 }
@@ -139,11 +155,18 @@ __global__ void __launch_bounds__(Wide::NT, 1) leaf_trsm_wide_kernel(LeafArgs<fl
         if (!first) load_panel(j0, pre);
         store_panel(pre);
         group_sync(g);
-        float x[8][4];
+        // The tile is kept negated, as pairs of rows (2u, 2u+1) per column v:
+        // y = -x, so each update y += M(i,l) X(l,:) is a plain packed FMA
+        // (and rounds exactly as x - M(i,l) X(l,:) would).
+        uint64_t y[4][4];
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
-            const float4 w = *reinterpret_cast<const float4*>(sC + (8 * rg + u) * S::LDC + 4 * cg);
-            x[u][0] = w.x; x[u][1] = w.y; x[u][2] = w.z; x[u][3] = w.w;
+        for (int u2 = 0; u2 < 4; ++u2) {
+            const float4 w0 = *reinterpret_cast<const float4*>(sC + (8 * rg + 2 * u2) * S::LDC + 4 * cg);
+            const float4 w1 = *reinterpret_cast<const float4*>(sC + (8 * rg + 2 * u2 + 1) * S::LDC + 4 * cg);
+            y[u2][0] = pack2(-w0.x, -w1.x);
+            y[u2][1] = pack2(-w0.y, -w1.y);
+            y[u2][2] = pack2(-w0.z, -w1.z);
+            y[u2][3] = pack2(-w0.w, -w1.w);
         }
 
 #pragma unroll 1
@@ -152,9 +175,15 @@ __global__ void __launch_bounds__(Wide::NT, 1) leaf_trsm_wide_kernel(LeafArgs<fl
             // 1. the block's owners publish their (fully updated) rows
             if ((rg >> 1) == s) {
 #pragma unroll
-                for (int u = 0; u < 8; ++u)
-                    *reinterpret_cast<float4*>(sC + (8 * rg + u) * S::LDC + 4 * cg) =
-                        make_float4(x[u][0], x[u][1], x[u][2], x[u][3]);
+                for (int u2 = 0; u2 < 4; ++u2) {
+                    float a[4], b[4];
+#pragma unroll
+                    for (int v = 0; v < 4; ++v) unpack2(y[u2][v], a[v], b[v]);
+                    *reinterpret_cast<float4*>(sC + (8 * rg + 2 * u2) * S::LDC + 4 * cg) =
+                        make_float4(-a[0], -a[1], -a[2], -a[3]);
+                    *reinterpret_cast<float4*>(sC + (8 * rg + 2 * u2 + 1) * S::LDC + 4 * cg) =
+                        make_float4(-b[0], -b[1], -b[2], -b[3]);
+                }
             }
             group_sync(g);
             // 2. substitution on the 16x16 diagonal block, lane = column;
@@ -197,14 +226,14 @@ __global__ void __launch_bounds__(Wide::NT, 1) leaf_trsm_wide_kernel(LeafArgs<fl
                     const float4 xv = *reinterpret_cast<const float4*>(sC + l * S::LDC + 4 * cg);
                     const float4 t0 = *reinterpret_cast<const float4*>(sT + l * S::B + 8 * rg);
                     const float4 t1 = *reinterpret_cast<const float4*>(sT + l * S::B + 8 * rg + 4);
-                    const float t[8] = {t0.x, t0.y, t0.z, t0.w, t1.x, t1.y, t1.z, t1.w};
+                    const uint64_t tp[4] = {pack2(t0.x, t0.y), pack2(t0.z, t0.w),
+                                            pack2(t1.x, t1.y), pack2(t1.z, t1.w)};
+                    const uint64_t xb[4] = {pack2(xv.x, xv.x), pack2(xv.y, xv.y),
+                                            pack2(xv.z, xv.z), pack2(xv.w, xv.w)};
 #pragma unroll
-                    for (int u = 0; u < 8; ++u) {
-                        x[u][0] = fmaf(-t[u], xv.x, x[u][0]);
-                        x[u][1] = fmaf(-t[u], xv.y, x[u][1]);
-                        x[u][2] = fmaf(-t[u], xv.z, x[u][2]);
-                        x[u][3] = fmaf(-t[u], xv.w, x[u][3]);
-                    }
+                    for (int u2 = 0; u2 < 4; ++u2)
+#pragma unroll
+                        for (int v = 0; v < 4; ++v) y[u2][v] = ffma2(tp[u2], xb[v], y[u2][v]);
                 }
             }
         }
