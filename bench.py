@@ -422,9 +422,11 @@ def run_batched(args):
         probs.append((op, side, uplo, "N", "N", 1.5 if op == "S" else 1 / 1.5, At, Bt))
         flops += float(k) * k * nrhs
     h = trx.Handle(dev)
-    scratch = [(o, s_, u, t, d, a, A, B.clone()) for (o, s_, u, t, d, a, A, B) in probs]
-    table = trx.batched_autotune(scratch, handle=h)
-    del scratch
+    table = None
+    if not args.no_autotune:
+        scratch = [(o, s_, u, t, d, a, A, B.clone()) for (o, s_, u, t, d, a, A, B) in probs]
+        table = trx.batched_autotune(scratch, handle=h)
+        del scratch
     stream = torch.cuda.current_stream(dev)
 
     def timed(fn, reps):
@@ -555,6 +557,8 @@ def main(argv=None):
                     help="square: the n=16384 TRSM+TRMM step (default); batched: "
                          "4096 small uneven problems in one launch")
     ap.add_argument("--count", type=int, default=4096, help="problems (batched workload)")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="batched workload: keep the default block sizes (for profiling runs)")
     args = ap.parse_args(argv)
     global K_ORDER, NRHS, DTYPE
     K_ORDER, NRHS = args.k, args.nrhs

@@ -7,15 +7,15 @@
 // grid take them from an atomic counter, so big problems start first and
 // the tail is filled with small ones.
 //
-// Inside a CTA a problem runs the same blocked scheme as the blocked leaf:
-// the right-hand sides are staged in shared memory in chunks of NC columns
-// (k rows x NC, row-major), and the rows are taken sb at a time
-// (sb = 8, 16 or 32, per problem from the tuning table):
-//   TRSM (forward): substitution on the sb-row diagonal block (one thread per
-//     column), then a rank-sb update of every row below it;
-//   TRMM: row blocks from the bottom up, each new block
-//     alpha * sum_{l <= i} M(i,l) C(l,:) formed from rows that are still
-//     original (all rows above it), then written in place.
+// Inside a CTA a problem runs on its right-hand side staged in shared
+// memory in chunks of NC columns (k rows x NC, row-major):
+//   TRSM (forward): rows taken sb at a time (sb = 8, 16 or 32, per problem
+//     from the tuning table): substitution on the sb-row diagonal block (one
+//     thread per column), then a rank-sb update of every row below it, each
+//     thread a register tile of 4 rows x 4 columns;
+//   TRMM: out of place, every row's alpha * sum_{l <= i} M(i,l) C(l,:)
+//     formed from the staged original columns and written straight back to
+//     global memory, again in 4 x 4 register tiles.
 // M is read through the read-only cache (its rows are reused across the
 // column groups of a CTA). Problems with k > 512 belong to the plain
 // recursive entry points.
@@ -55,7 +55,7 @@ __device__ __forceinline__ T ldA(const T* A, int64_t i, int64_t l, int64_t rs, i
 }
 
 template <typename T, int SB>
-__device__ void trsm_chunk(const BatchDesc& d, T* sC, const T* sD, int k) {
+__device__ __forceinline__ void trsm_chunk(const BatchDesc& d, T* sC, const T* sD, int k) {
     using S = BShape<T>;
     const int tid = threadIdx.x;
     const T* A = static_cast<const T*>(d.A);
@@ -82,54 +82,79 @@ __device__ void trsm_chunk(const BatchDesc& d, T* sC, const T* sD, int k) {
                 if (q < sbn) sC[(s0 + q) * S::LDC + tid] = x[q];
         }
         __syncthreads();
-        for (int i = s0 + SB + rg; i < k; i += S::RG) {
-            T acc[4] = {T(0), T(0), T(0), T(0)};
-#pragma unroll
+        // Rank-SB update of the rows below the block: each thread a tile of
+        // 4 rows x 4 columns (4 loads of M feed 16 multiply-adds).
+        for (int i0 = s0 + SB + 4 * rg; i0 < k; i0 += 4 * S::RG) {
+            T acc[4][4] = {};
+#pragma unroll 4
             for (int kk = 0; kk < SB; ++kk) {
-                const T t = ldA(A, i, s0 + kk, d.a_rs, d.a_cs);
+                const int l = s0 + kk;
+                T t[4];
 #pragma unroll
-                for (int v = 0; v < 4; ++v) acc[v] = fma(t, sC[(s0 + kk) * S::LDC + 4 * cg + v], acc[v]);
+                for (int r = 0; r < 4; ++r) t[r] = (i0 + r < k) ? ldA(A, i0 + r, l, d.a_rs, d.a_cs) : T(0);
+                T xv[4];
+#pragma unroll
+                for (int v = 0; v < 4; ++v) xv[v] = sC[l * S::LDC + 4 * cg + v];
+#pragma unroll
+                for (int r = 0; r < 4; ++r)
+#pragma unroll
+                    for (int v = 0; v < 4; ++v) acc[r][v] = fma(t[r], xv[v], acc[r][v]);
             }
 #pragma unroll
-            for (int v = 0; v < 4; ++v) sC[i * S::LDC + 4 * cg + v] -= acc[v];
+            for (int r = 0; r < 4; ++r)
+                if (i0 + r < k) {
+#pragma unroll
+                    for (int v = 0; v < 4; ++v) sC[(i0 + r) * S::LDC + 4 * cg + v] -= acc[r][v];
+                }
         }
         __syncthreads();
     }
 }
 
-template <typename T, int SB>
-__device__ void trmm_chunk(const BatchDesc& d, T* sC, const T* sD, int k, T alpha) {
+// TRMM out of place: the chunk's original columns stay in shared memory and
+// every row's new value alpha * sum_{l <= i} M(i,l) C(l,:) goes straight to
+// global memory, each thread a tile of 4 rows x 4 columns.
+template <typename T>
+__device__ __forceinline__ void trmm_chunk(const BatchDesc& d, const T* sC, const T* sD, int k, T alpha,
+                           T* C, int64_t c0, int ncols) {
     using S = BShape<T>;
     const int tid = threadIdx.x;
     const T* A = static_cast<const T*>(d.A);
     const int cg = tid % S::CG, rg = tid / S::CG;
-    const int nblk = (k + SB - 1) / SB;
-    for (int bi = nblk - 1; bi >= 0; --bi) {
-        const int s0 = bi * SB;
-        const int sbn = min(SB, k - s0);
-        // rows s0 .. s0+sbn-1, one row per row group (SB <= RG)
-        T acc[4] = {T(0), T(0), T(0), T(0)};
-        const int i = s0 + rg;
-        if (rg < sbn) {
-            for (int l = 0; l < i; ++l) {
-                const T t = ldA(A, i, l, d.a_rs, d.a_cs);
+    for (int i0 = 4 * rg; i0 < k; i0 += 4 * S::RG) {
+        T acc[4][4] = {};
+        const int lend = min(i0 + 3, k - 1);          // strictly-lower columns l < i
+#pragma unroll 2
+        for (int l = 0; l < lend; ++l) {
+            T t[4];
 #pragma unroll
-                for (int v = 0; v < 4; ++v) acc[v] = fma(t, sC[l * S::LDC + 4 * cg + v], acc[v]);
+            for (int r = 0; r < 4; ++r)
+                t[r] = (l < i0 + r && i0 + r < k) ? ldA(A, i0 + r, l, d.a_rs, d.a_cs) : T(0);
+            T xv[4];
+#pragma unroll
+            for (int v = 0; v < 4; ++v) xv[v] = sC[l * S::LDC + 4 * cg + v];
+#pragma unroll
+            for (int r = 0; r < 4; ++r)
+#pragma unroll
+                for (int v = 0; v < 4; ++v) acc[r][v] = fma(t[r], xv[v], acc[r][v]);
+        }
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const int i = i0 + r;
+            if (i >= k) break;
+#pragma unroll
+            for (int v = 0; v < 4; ++v) {
+                const int c = 4 * cg + v;
+                if (c < ncols)
+                    C[i * d.c_rs + (c0 + c) * d.c_cs] =
+                        alpha * fma(sD[i], sC[i * S::LDC + c], acc[r][v]);
             }
-#pragma unroll
-            for (int v = 0; v < 4; ++v) acc[v] = fma(sD[i], sC[i * S::LDC + 4 * cg + v], acc[v]);
         }
-        __syncthreads();   // every read of the block's original rows is done
-        if (rg < sbn) {
-#pragma unroll
-            for (int v = 0; v < 4; ++v) sC[i * S::LDC + 4 * cg + v] = alpha * acc[v];
-        }
-        __syncthreads();
     }
 }
 
 template <typename T>
-__global__ void __launch_bounds__(256) batched_kernel(const BatchDesc* descs, int64_t count,
+__global__ void __launch_bounds__(256, 2) batched_kernel(const BatchDesc* descs, int64_t count,
                                                       int* counter) {
     using S = BShape<T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -174,14 +199,12 @@ __global__ void __launch_bounds__(256) batched_kernel(const BatchDesc* descs, in
                 if (d.sb == 8) trsm_chunk<T, 8>(d, sC, sD, k);
                 else if (d.sb == 32) trsm_chunk<T, 32>(d, sC, sD, k);
                 else trsm_chunk<T, 16>(d, sC, sD, k);
+                for (int e = tid; e < k * S::NC; e += S::NT) {
+                    const int i = row_fast ? e % k : e / S::NC, c = row_fast ? e / k : e % S::NC;
+                    if (c < ncols) C[i * d.c_rs + (c0 + c) * d.c_cs] = sC[i * S::LDC + c];
+                }
             } else {
-                if (d.sb == 8) trmm_chunk<T, 8>(d, sC, sD, k, (T)d.alpha);
-                else if (d.sb == 32) trmm_chunk<T, 32>(d, sC, sD, k, (T)d.alpha);
-                else trmm_chunk<T, 16>(d, sC, sD, k, (T)d.alpha);
-            }
-            for (int e = tid; e < k * S::NC; e += S::NT) {
-                const int i = row_fast ? e % k : e / S::NC, c = row_fast ? e / k : e % S::NC;
-                if (c < ncols) C[i * d.c_rs + (c0 + c) * d.c_cs] = sC[i * S::LDC + c];
+                trmm_chunk<T>(d, sC, sD, k, (T)d.alpha, C, c0, ncols);
             }
             __syncthreads();
         }
