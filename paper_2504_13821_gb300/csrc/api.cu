@@ -32,6 +32,7 @@ struct BatchDesc {
 cudaError_t batched_configure();
 cudaError_t launch_batched(int elem_bytes, const BatchDesc* descs, int64_t count, int* counter,
                            int grid_ctas, cudaStream_t s);
+int batched_ctas_per_sm(int elem_bytes);
 }  // namespace trx
 
 using namespace trx;
@@ -795,7 +796,8 @@ int batch_run(trx_handle_t h, int elem_bytes, const std::vector<BatchDesc>& d, c
                              s)) != cudaSuccess ||
         (e = cudaEventRecord(h->b_uploaded, s)) != cudaSuccess)
         return fail_cuda(e, "batch upload");
-    const int grid = h->num_sms * 2;
+    // persistent CTAs: as many per SM as fit (shared memory bound)
+    const int grid = h->num_sms * batched_ctas_per_sm(elem_bytes);
     cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
     cudaStreamIsCapturing(s, &cap);
     if (!use_graph || cap != cudaStreamCaptureStatusNone) {

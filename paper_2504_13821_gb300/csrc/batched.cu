@@ -43,7 +43,7 @@ template <typename T>
 struct BShape {
     static constexpr int NT = 256;
     static constexpr int NC = sizeof(T) == 4 ? 32 : 16;    // columns per chunk
-    static constexpr int LDC = NC + 4;
+    static constexpr int LDC = NC + 1;                     // odd stride: three CTAs per SM
     static constexpr int CG = NC / 4;                      // column groups of 4
     static constexpr int RG = NT / CG;                     // row groups
     static constexpr size_t smem = sizeof(T) * ((size_t)kBatchMaxK * LDC + kBatchMaxK);
@@ -86,12 +86,23 @@ __device__ __forceinline__ void trsm_chunk(const BatchDesc& d, T* sC, const T* s
         // 4 rows x 4 columns (4 loads of M feed 16 multiply-adds).
         for (int i0 = s0 + SB + 4 * rg; i0 < k; i0 += 4 * S::RG) {
             T acc[4][4] = {};
+            // M(i0+r, s0+kk) by pointers walking along the block's columns
+            const T* ap[4];
+            bool ok[4];
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                ok[r] = i0 + r < k;
+                ap[r] = A + (int64_t)(ok[r] ? i0 + r : 0) * d.a_rs + (int64_t)s0 * d.a_cs;
+            }
 #pragma unroll 4
             for (int kk = 0; kk < SB; ++kk) {
                 const int l = s0 + kk;
                 T t[4];
 #pragma unroll
-                for (int r = 0; r < 4; ++r) t[r] = (i0 + r < k) ? ldA(A, i0 + r, l, d.a_rs, d.a_cs) : T(0);
+                for (int r = 0; r < 4; ++r) {
+                    t[r] = ok[r] ? __ldg(ap[r]) : T(0);
+                    ap[r] += d.a_cs;
+                }
                 T xv[4];
 #pragma unroll
                 for (int v = 0; v < 4; ++v) xv[v] = sC[l * S::LDC + 4 * cg + v];
@@ -124,12 +135,17 @@ __device__ __forceinline__ void trmm_chunk(const BatchDesc& d, const T* sC, cons
     for (int i0 = 4 * rg; i0 < k; i0 += 4 * S::RG) {
         T acc[4][4] = {};
         const int lend = min(i0 + 3, k - 1);          // strictly-lower columns l < i
+        const T* ap[4];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) ap[r] = A + (int64_t)(i0 + r < k ? i0 + r : 0) * d.a_rs;
 #pragma unroll 2
         for (int l = 0; l < lend; ++l) {
             T t[4];
 #pragma unroll
-            for (int r = 0; r < 4; ++r)
-                t[r] = (l < i0 + r && i0 + r < k) ? ldA(A, i0 + r, l, d.a_rs, d.a_cs) : T(0);
+            for (int r = 0; r < 4; ++r) {
+                t[r] = (l < i0 + r && i0 + r < k) ? __ldg(ap[r]) : T(0);
+                ap[r] += d.a_cs;
+            }
             T xv[4];
 #pragma unroll
             for (int v = 0; v < 4; ++v) xv[v] = sC[l * S::LDC + 4 * cg + v];
@@ -154,7 +170,7 @@ __device__ __forceinline__ void trmm_chunk(const BatchDesc& d, const T* sC, cons
 }
 
 template <typename T>
-__global__ void __launch_bounds__(256, 2) batched_kernel(const BatchDesc* descs, int64_t count,
+__global__ void __launch_bounds__(256, 3) batched_kernel(const BatchDesc* descs, int64_t count,
                                                       int* counter) {
     using S = BShape<T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -178,6 +194,22 @@ __global__ void __launch_bounds__(256, 2) batched_kernel(const BatchDesc* descs,
             for (int64_t e = tid; e < d.k * d.nrhs; e += S::NT)
                 C[(e % d.k) * d.c_rs + (e / d.k) * d.c_cs] = T(0);
             continue;
+        }
+        // Pull the problem's triangle toward L2 in 128-byte lines along A's
+        // contiguous index, so the blocks' first reads of M do not each wait
+        // on DRAM.
+        {
+            constexpr int LINE = 128 / (int)sizeof(T);
+            const bool rf = (d.a_rs == 1 || d.a_rs == -1);
+            const int per = (k + LINE - 1) / LINE;
+            for (int e = tid; e < k * per; e += S::NT) {
+                const int fixed = e / per, w = (e % per) * LINE;   // fixed: column (rf) or row
+                const int i = rf ? w : fixed, l = rf ? fixed : w;
+                if (i < k && l < k) {
+                    const T* ptr = A + (int64_t)i * d.a_rs + (int64_t)l * d.a_cs;
+                    asm volatile("prefetch.global.L2 [%0];" ::"l"(ptr));
+                }
+            }
         }
         for (int i = tid; i < k; i += S::NT) {
             T dg = T(1);
@@ -220,6 +252,17 @@ cudaError_t batched_configure() {
     if (e != cudaSuccess) return e;
     return cudaFuncSetAttribute(batched_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)BShape<double>::smem);
+}
+
+// Resident CTAs per SM of the batched kernel (occupancy query, at least 1).
+int batched_ctas_per_sm(int elem_bytes) {
+    int n = 0;
+    const cudaError_t e = elem_bytes == 4
+        ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batched_kernel<float>, BShape<float>::NT,
+                                                        BShape<float>::smem)
+        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batched_kernel<double>, BShape<double>::NT,
+                                                        BShape<double>::smem);
+    return (e == cudaSuccess && n > 0) ? n : 1;
 }
 
 // descs: device array of `count` descriptors sorted largest first; counter:
