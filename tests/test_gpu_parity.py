@@ -249,6 +249,14 @@ def test_large_sampled_4096(trx, op):
 
 @pytest.mark.slow
 @pytest.mark.parametrize("op", ["trsm", "trmm"])
+def test_ragged_large_sampled(trx, op):
+    # order and right-hand-side count off every tile and leaf boundary
+    sampled_case(op, "L", 4099, 16383, 32, np.float32, seed=4099)
+    sampled_case(op, "R", 3001, 9999, 32, np.float32, seed=3001)
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("op", ["trsm", "trmm"])
 def test_bench_size_16384_sampled(trx, op):
     """The benchmark's workload (m = n = 16384, FP32, L L N N, alpha 1.5,
     default handle: tensor cores, cached graph), 32 sampled columns."""
