@@ -1,0 +1,215 @@
+// Launch planning for one call: the recursion tree of Section 3.1 as an
+// ordered list of steps (operand-plane conversions, leaves, GEMM updates),
+// and the automatic choices that shape it (leaf cutoff, tensor-core engine,
+// TRMM diagonal blocks). Host code only, no device work.
+#pragma once
+#include <algorithm>
+#include <cstdint>
+#include <vector>
+
+#include "common.cuh"
+
+namespace trx {
+
+constexpr int kDefaultLeaf = 64;
+// Automatic cutoff for FP32 TRSM: 128-row leaves (one leaf launch in place of
+// two 64-row leaves and the update between them; measured faster at 256 ..
+// 16384 right-hand sides, with the wide leaf kernel from 1024). Block leaves
+// (256) are never chosen automatically (measured slower); TRX_OPT_LEAF = 256
+// asks.
+constexpr int kF32TrsmLeaf = 128;
+constexpr int64_t kTcMinOrder = 256;                 // auto: tensor cores from this order
+constexpr int64_t kTrmmDenseMinOrder = 1024;         // auto: dense TRMM diagonal blocks from here
+constexpr int kTrmmDenseRows = 1024;                 // auto: their size
+
+inline int64_t round_up(int64_t x, int64_t q) { return (x + q - 1) / q * q; }
+
+// Section 3.1 splits at n = N/2. For orders that are not powers of two the
+// split is rounded up to a multiple of max(b, 64) (so every tensor-core GEMM
+// update has K a multiple of its K tile, and every node starts on a multiple
+// of b), or of b where that would leave the second half empty.
+inline int64_t split_point(int64_t s, int b) {
+    const int64_t half = (s + 1) / 2;
+    const int64_t q = std::max<int64_t>(b, kTcKQuantum);
+    int64_t s1 = round_up(half, q);
+    if (s1 >= s) s1 = round_up(half, b);
+    return s1;
+}
+
+enum StepKind { kLeaf, kGemm, kConvM, kConvY };
+
+struct Step {
+    StepKind kind;
+    bool trsm = true;        // leaf: TRSM or TRMM
+    int64_t r0 = 0;          // leaf: first row
+    int b = 0;               // leaf: size (and stride of batched leaves); conv_m: diagonal
+                             // block carried densely in the planes (0: none)
+    int64_t nleaves = 1;
+    double alpha = 1.0;      // leaf scale
+    bool planes = false;     // TRSM leaf writes Y planes
+    bool tc = false;         // GEMM on tensor cores
+    std::vector<TcGemm> gemms;
+    double beta = 1.0, gamma = 1.0;
+    bool dense = false;      // GEMM over dense lower-triangular diagonal blocks (TRMM leaves):
+                             // row i's beta is beta * M(i, i)
+};
+
+struct Plan {
+    std::vector<Step> steps;
+    bool tc = false;
+};
+
+inline void plan_trsm(Plan& pl, int64_t r0, int64_t s, bool first, int b, double alpha) {
+    if (s <= b) {
+        Step st{kLeaf};
+        st.trsm = true;
+        st.r0 = r0;
+        st.b = (int)s;
+        st.alpha = first ? alpha : 1.0;
+        st.planes = pl.tc;
+        pl.steps.push_back(st);
+        return;
+    }
+    const int64_t s1 = split_point(s, b);
+    plan_trsm(pl, r0, s1, first, b, alpha);
+    Step g{kGemm};
+    g.tc = pl.tc && (s1 % kTcKQuantum == 0);
+    g.gemms.push_back(TcGemm{r0 + s1, s - s1, r0, s1});
+    g.beta = first ? alpha : 1.0;
+    g.gamma = -1.0;
+    pl.steps.push_back(g);
+    plan_trsm(pl, r0 + s1, s - s1, false, b, alpha);
+}
+
+// Paper order for TRMM (lower): C2 := M22 C2, C2 += M21 C1, C1 := M11 C1, so
+// every GEMM reads C1 before it is overwritten.
+inline void plan_trmm_seq(Plan& pl, int64_t r0, int64_t s, int b, double alpha) {
+    if (s <= b) {
+        Step st{kLeaf};
+        st.trsm = false;
+        st.r0 = r0;
+        st.b = (int)s;
+        st.alpha = alpha;
+        pl.steps.push_back(st);
+        return;
+    }
+    const int64_t s1 = split_point(s, b);
+    plan_trmm_seq(pl, r0 + s1, s - s1, b, alpha);
+    Step g{kGemm};
+    g.tc = pl.tc && (s1 % kTcKQuantum == 0);
+    g.gemms.push_back(TcGemm{r0 + s1, s - s1, r0, s1});
+    g.beta = 1.0;
+    g.gamma = alpha;
+    pl.steps.push_back(g);
+    plan_trmm_seq(pl, r0, s1, b, alpha);
+}
+
+// TRMM with the original right-hand side kept in the Y planes: no GEMM update
+// reads a row another step writes, so the same recursion tree runs as one
+// launch for all leaves followed by one grouped launch per recursion level
+// (the updates of one level write disjoint rows).
+//
+// With dense = true the leaves (b a multiple of 64) run on the tensor cores
+// too: the operand planes carry each b x b diagonal block's strictly-lower
+// part with zeros on and above the diagonal, and one grouped launch forms
+// every leaf product at once,
+//   C[i] = alpha * M(i,i) * C[i] + alpha * sum_{r <= l < i} M(i,l) * Y[l],
+// the diagonal term in FP32 from C's original value (a per-row beta in the
+// GEMM epilogue) and the rest on the tensor cores. Each 128-row tile of a
+// block is its own group member whose K range ends at the tile's last row,
+// so no tile multiplies the zeros above the diagonal beyond its own 128
+// columns.
+inline void plan_trmm_levels(Plan& pl, int64_t k, int b, double alpha, bool dense = false) {
+    if (dense) {
+        Step d{kGemm};
+        d.tc = true;
+        d.dense = true;
+        d.beta = alpha;
+        d.gamma = alpha;
+        for (int64_t r = 0; r < k; r += b) {
+            const int64_t len = std::min<int64_t>(b, k - r);
+            for (int64_t t = 0; t < len; t += 128) {
+                const int64_t mlen = std::min<int64_t>(128, len - t);
+                d.gemms.push_back(TcGemm{r + t, mlen, r, round_up(t + mlen, 32)});
+            }
+        }
+        pl.steps.push_back(d);
+    } else {
+        Step lf{kLeaf};
+        lf.trsm = false;
+        lf.r0 = 0;
+        lf.b = b;
+        lf.nleaves = (k + b - 1) / b;
+        lf.alpha = alpha;
+        pl.steps.push_back(lf);
+    }
+    std::vector<std::pair<int64_t, int64_t>> level{{0, k}}, next;
+    while (!level.empty()) {
+        Step g{kGemm};
+        g.tc = true;
+        g.beta = 1.0;
+        g.gamma = alpha;
+        next.clear();
+        for (auto& nd : level) {
+            const int64_t r0 = nd.first, s = nd.second;
+            if (s <= b) continue;
+            const int64_t s1 = split_point(s, b);
+            g.gemms.push_back(TcGemm{r0 + s1, s - s1, r0, s1});
+            next.push_back({r0, s1});
+            next.push_back({r0 + s1, s - s1});
+        }
+        if (!g.gemms.empty()) pl.steps.push_back(g);
+        level.swap(next);
+    }
+}
+
+// The whole launch sequence of one call: operand planes (tensor-core path),
+// then the recursion of Section 3.1.
+// dense > 0 (TRMM on the tensor-core path only): leaves of that many rows as
+// dense diagonal-block GEMMs, in place of the leaf kernel and of the levels
+// below that size.
+inline void make_plan(Plan& plan, bool trsm, int64_t k, int b, double alpha, bool conv_m = true,
+               int dense = 0) {
+    if (plan.tc && conv_m) {
+        Step cm{kConvM};
+        cm.b = trsm ? 0 : dense;
+        plan.steps.push_back(cm);
+    }
+    if (trsm) {
+        plan_trsm(plan, 0, k, true, b, alpha);
+    } else {
+        if (plan.tc) plan.steps.push_back(Step{kConvY});
+        if (plan.tc && dense > 0) plan_trmm_levels(plan, k, dense, alpha, true);
+        else if (plan.tc && b % kTcKQuantum == 0) plan_trmm_levels(plan, k, b, alpha);
+        else plan_trmm_seq(plan, 0, k, b, alpha);
+    }
+}
+
+// Rows of the dense TRMM diagonal blocks: the handle's TRX_OPT_TRMM_DENSE
+// (-1 off, else the size), or automatically 1024 once the order reaches 1024
+// and the leaf size was left automatic. Tensor-core path only.
+inline int trmm_dense_mode(int64_t opt, int64_t opt_leaf, bool tc, int64_t k) {
+    if (!tc || opt < 0) return 0;
+    if (opt > 0) return (int)opt;
+    return (opt_leaf == 0 && k >= kTrmmDenseMinOrder) ? kTrmmDenseRows : 0;
+}
+
+// Recursion cutoff: TRX_OPT_LEAF when set, else 128 for FP32 TRSM and 64
+// otherwise. With 256 a TRSM's leaves run as block leaves (one launch per 256
+// rows); TRMM leaves stop at 128 rows.
+inline int leaf_for(int64_t opt_leaf, int64_t k, bool trsm, int elem, int64_t nrhs) {
+    int b = kDefaultLeaf;
+    if (opt_leaf > 0) b = (int)opt_leaf;
+    else if (trsm && elem == 4) b = kF32TrsmLeaf;
+    if (!trsm && b > kMaxLeaf) b = kMaxLeaf;
+    (void)nrhs;
+    return (int)std::min<int64_t>(b, std::max<int64_t>(k, 1));
+}
+
+inline bool use_tc_mode(int elem, int64_t gemm_mode, int64_t k, int b) {
+    if (elem != 4 || gemm_mode == 1 || k <= b) return false;   // k <= b: one leaf, no update
+    if (gemm_mode == 2) return k > b;
+    return k >= kTcMinOrder;
+}
+
+}  // namespace trx
