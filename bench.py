@@ -441,7 +441,7 @@ def run_batched(args):
         torch.cuda.synchronize()
         return e0.elapsed_time(e1) / reps
 
-    batch = trx.Batch(probs)      # problem descriptors built once (host side)
+    batch = trx.Batch(probs, handle=h)   # prepared once: descriptors kept on the device
     ms_batched = timed(lambda: batch.run(handle=h, stream=stream), args.steps)
 
     def loop():

@@ -209,7 +209,25 @@ typedef struct {
 int trx_batched(trx_handle_t handle, int elem_bytes, int64_t count,
                 const trx_problem_t* problems, void* stream);
 
-/* Time the batch with each sub-block height (8, 16, 32 rows) per order
+/* Prepared batch: the same problems run many times (fixed pointers; the
+ * contents of A and B may change between runs). trx_batch_create checks,
+ * canonicalises and cost-sorts the problems once (with the handle's current
+ * tuning table) and keeps the descriptors on the handle's device, so a run
+ * is one counter reset and one persistent launch (replayed from a cached
+ * graph), with no host work per run. (No counterpart in the paper: the
+ * batched workload is this library's.) Argument errors as trx_batched;
+ * TRX_ERR_ALLOC if the device copy cannot be made. trx_batch_run enqueues
+ * on stream (asynchronous); runs of one batch must not overlap (its work
+ * counter is shared), different batches may run concurrently on different
+ * streams. trx_batch_destroy synchronises the device and frees the batch;
+ * NULL is accepted. A batch belongs to the handle it was created with. */
+typedef struct trx_batch_s* trx_batch_t;
+int trx_batch_create(trx_handle_t handle, int elem_bytes, int64_t count,
+                     const trx_problem_t* problems, trx_batch_t* batch);
+int trx_batch_run(trx_handle_t handle, trx_batch_t batch, void* stream);
+int trx_batch_destroy(trx_batch_t batch);
+
+/* Time the batch with each sub-block height (4, 8, 16 rows) per order
  * bucket (k <= 64, 128, 256, 512), keep the fastest per bucket in the
  * handle for later trx_batched calls, and write the table as JSON into
  * json (if not NULL). The problems' B arrays are overwritten (the batch

@@ -88,6 +88,10 @@ def load_library() -> ctypes.CDLL:
         lib.trx_sgemm_update.argtypes = [vp, i64, i64, i64, ctypes.c_float, ctypes.c_float,
                                          vp, i64, vp, i64, vp, i64, ctypes.c_int, vp]
         lib.trx_batched.argtypes = [vp, ctypes.c_int, i64, ctypes.POINTER(Problem), vp]
+        lib.trx_batch_create.argtypes = [vp, ctypes.c_int, i64, ctypes.POINTER(Problem),
+                                         ctypes.POINTER(vp)]
+        lib.trx_batch_run.argtypes = [vp, vp, vp]
+        lib.trx_batch_destroy.argtypes = [vp]
         lib.trx_batched_autotune.argtypes = [vp, ctypes.c_int, i64, ctypes.POINTER(Problem), vp,
                                              ctypes.c_char_p, ctypes.c_size_t]
         lib.trx_version.argtypes = []
@@ -321,14 +325,23 @@ def _problem_array(problems):
 
 
 class Batch:
-    """A batch of (op, side, uplo, trans, diag, alpha, A, B) problems with
-    its trx_problem_t array built once; run() can be called repeatedly
-    (the tensors are referenced, not copied)."""
+    """A batch of (op, side, uplo, trans, diag, alpha, A, B) problems,
+    prepared once on a handle (trx_batch_create: checked, canonicalised,
+    cost-sorted, descriptors kept on the device); run() can be called
+    repeatedly and does no host work (the tensors are referenced, not
+    copied: their contents may change between runs, their storage not)."""
 
-    def __init__(self, problems):
+    def __init__(self, problems, *, handle: Handle | None = None):
         self.problems = list(problems)
         self.array, self.elem = _problem_array(self.problems)
         self.device = self.problems[0][7].device if self.problems else None
+        self.handle = None
+        self._b = ctypes.c_void_p()
+        if self.problems:
+            self.handle = handle if handle is not None else default_handle(self.device)
+            _check(load_library().trx_batch_create(self.handle.ptr, self.elem, len(self.problems),
+                                                   self.array, ctypes.byref(self._b)),
+                   "trx_batch_create")
 
     def __len__(self):
         return len(self.problems)
@@ -337,21 +350,44 @@ class Batch:
         import torch
         if not self.problems:
             return
-        lib = load_library()
-        h = handle if handle is not None else default_handle(self.device)
+        if handle is not None and handle is not self.handle:
+            raise ValueError("a prepared batch runs on the handle it was created with")
         if stream is None:
             stream = torch.cuda.current_stream(self.device)
         s_ptr = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
-        _check(lib.trx_batched(h.ptr, self.elem, len(self.problems), self.array, s_ptr),
-               "trx_batched")
+        _check(load_library().trx_batch_run(self.handle.ptr, self._b, s_ptr), "trx_batch_run")
+
+    def close(self):
+        if self._b:
+            load_library().trx_batch_destroy(self._b)
+            self._b = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def batched(problems, *, handle: Handle | None = None, stream=None):
     """Run many small TRSM ('S') / TRMM ('M') problems in one persistent
-    launch. problems: list of (op, side, uplo, trans, diag, alpha, A, B), or
-    a prepared Batch."""
-    b = problems if isinstance(problems, Batch) else Batch(problems)
-    b.run(handle=handle, stream=stream)
+    launch. problems: list of (op, side, uplo, trans, diag, alpha, A, B)
+    (checked and sorted on the host for this call: trx_batched), or a
+    prepared Batch (no host work: trx_batch_run)."""
+    import torch
+    if isinstance(problems, Batch):
+        problems.run(handle=handle, stream=stream)
+        return
+    problems = list(problems)
+    if not problems:
+        return
+    arr, elem = _problem_array(problems)
+    dev = problems[0][7].device
+    h = handle if handle is not None else default_handle(dev)
+    if stream is None:
+        stream = torch.cuda.current_stream(dev)
+    s_ptr = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+    _check(load_library().trx_batched(h.ptr, elem, len(problems), arr, s_ptr), "trx_batched")
 
 
 def batched_autotune(problems, *, handle: Handle | None = None, stream=None) -> dict:

@@ -11,6 +11,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <new>
 #include <vector>
 
 #include "common.cuh"
@@ -179,7 +180,7 @@ struct trx_handle_s {
     BatchDesc* b_host = nullptr;
     int64_t b_cap = 0;
     cudaEvent_t b_uploaded = nullptr;
-    int tune_sb[2][4] = {{16, 16, 16, 16}, {16, 16, 16, 16}};
+    int tune_sb[2][4] = {{8, 8, 8, 8}, {8, 8, 8, 8}};   // autotuned on GB300: 8 everywhere
     // column-panel branches of a TRSM: streams and fork/join events
     int64_t opt_panels = 0;
     int64_t opt_trmm_dense = 0;
@@ -644,7 +645,105 @@ int batch_run(trx_handle_t h, int elem_bytes, const std::vector<BatchDesc>& d, c
 
 }  // namespace
 
+struct trx_batch_s {
+    int magic = 0;
+    int device = 0, elem = 4, grid = 0;
+    int64_t n = 0;
+    BatchDesc* d = nullptr;      // device descriptors, cost-sorted
+    int* counter = nullptr;      // device work counter
+    cudaGraphExec_t exec = nullptr;
+};
+
+namespace {
+constexpr int kBatchMagic = 0x54524231;  // "TRB1"
+}
+
 extern "C" {
+
+int trx_batch_create(trx_handle_t h, int elem_bytes, int64_t count, const trx_problem_t* problems,
+                     trx_batch_t* out) {
+    if (!out) return TRX_ERR_INVALID_VALUE;
+    *out = nullptr;
+    if (!valid(h)) return TRX_ERR_HANDLE;
+    if ((elem_bytes != 4 && elem_bytes != 8) || count < 0 || (count > 0 && !problems))
+        return TRX_ERR_INVALID_VALUE;
+    cudaError_t e = cudaSetDevice(h->device);
+    if (e != cudaSuccess) return fail_cuda(e, "cudaSetDevice");
+    std::vector<BatchDesc> d;
+    const int rc = batch_descs(h, elem_bytes, count, problems, d, nullptr);
+    if (rc != TRX_SUCCESS) return rc;
+    auto* b = new (std::nothrow) trx_batch_s;
+    if (!b) return TRX_ERR_ALLOC;
+    b->device = h->device;
+    b->elem = elem_bytes;
+    b->n = (int64_t)d.size();
+    b->grid = h->num_sms * batched_ctas_per_sm(elem_bytes);
+    if ((e = cudaMalloc(&b->counter, 256)) != cudaSuccess ||
+        (b->n > 0 && (e = cudaMalloc(&b->d, b->n * sizeof(BatchDesc))) != cudaSuccess) ||
+        (b->n > 0 &&
+         (e = cudaMemcpy(b->d, d.data(), b->n * sizeof(BatchDesc), cudaMemcpyHostToDevice)) !=
+             cudaSuccess)) {
+        if (b->d) cudaFree(b->d);
+        if (b->counter) cudaFree(b->counter);
+        delete b;
+        snprintf(g_detail, sizeof(g_detail), "batch descriptors: %s", cudaGetErrorString(e));
+        return TRX_ERR_ALLOC;
+    }
+    b->magic = kBatchMagic;
+    *out = b;
+    return TRX_SUCCESS;
+}
+
+int trx_batch_run(trx_handle_t h, trx_batch_t b, void* stream) {
+    if (!valid(h)) return TRX_ERR_HANDLE;
+    if (!b || b->magic != kBatchMagic || b->device != h->device) return TRX_ERR_INVALID_VALUE;
+    if (b->n == 0) return TRX_SUCCESS;
+    cudaError_t e = cudaSetDevice(h->device);
+    if (e != cudaSuccess) return fail_cuda(e, "cudaSetDevice");
+    pdl_enabled() = h->opt_pdl != 0;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if ((e = cudaStreamIsCapturing(s, &cap)) != cudaSuccess)
+        return fail_cuda(e, "cudaStreamIsCapturing");
+    if (!h->opt_graph || cap != cudaStreamCaptureStatusNone) {
+        e = launch_batched(b->elem, b->d, b->n, b->counter, b->grid, s);
+        return e == cudaSuccess ? TRX_SUCCESS : fail_cuda(e, "batched launch");
+    }
+    if (!b->exec) {
+        if ((e = cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal)) !=
+            cudaSuccess)
+            return fail_cuda(e, "cudaStreamBeginCapture");
+        const cudaError_t le = launch_batched(b->elem, b->d, b->n, b->counter, b->grid,
+                                              h->cap_stream);
+        cudaGraph_t graph = nullptr;
+        e = cudaStreamEndCapture(h->cap_stream, &graph);
+        if (le != cudaSuccess || e != cudaSuccess) {
+            if (graph) cudaGraphDestroy(graph);
+            return fail_cuda(le != cudaSuccess ? le : e, "batched capture");
+        }
+        e = cudaGraphInstantiate(&b->exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) {
+            b->exec = nullptr;
+            return fail_cuda(e, "cudaGraphInstantiate");
+        }
+    }
+    e = cudaGraphLaunch(b->exec, s);
+    return e == cudaSuccess ? TRX_SUCCESS : fail_cuda(e, "cudaGraphLaunch");
+}
+
+int trx_batch_destroy(trx_batch_t b) {
+    if (b == nullptr) return TRX_SUCCESS;
+    if (b->magic != kBatchMagic) return TRX_ERR_INVALID_VALUE;
+    cudaSetDevice(b->device);
+    cudaDeviceSynchronize();
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->d) cudaFree(b->d);
+    if (b->counter) cudaFree(b->counter);
+    b->magic = 0;
+    delete b;
+    return TRX_SUCCESS;
+}
 
 int trx_batched(trx_handle_t h, int elem_bytes, int64_t count, const trx_problem_t* problems,
                 void* stream) {
@@ -669,7 +768,7 @@ int trx_batched_autotune(trx_handle_t h, int elem_bytes, int64_t count,
     cudaError_t e = cudaSetDevice(h->device);
     if (e != cudaSuccess) return fail_cuda(e, "cudaSetDevice");
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-    const int sbs[3] = {8, 16, 32};
+    const int sbs[3] = {4, 8, 16};
     double best_ms[4] = {1e30, 1e30, 1e30, 1e30}, all_ms[4][3];
     int best[4] = {16, 16, 16, 16};
     cudaEvent_t e0 = get_event(h), e1 = get_event(h);
@@ -712,7 +811,7 @@ int trx_batched_autotune(trx_handle_t h, int elem_bytes, int64_t count,
         char buf[256];
         for (int bkt = 0; bkt < 4; ++bkt) {
             snprintf(buf, sizeof(buf),
-                     "%s{\"kmax\": %d, \"sb\": %d, \"ms\": {\"8\": %.5f, \"16\": %.5f, \"32\": %.5f}}",
+                     "%s{\"kmax\": %d, \"sb\": %d, \"ms\": {\"4\": %.5f, \"8\": %.5f, \"16\": %.5f}}",
                      bkt ? ", " : "", kmax[bkt], best[bkt], all_ms[bkt][0], all_ms[bkt][1],
                      all_ms[bkt][2]);
             out += buf;

@@ -9,10 +9,11 @@
 //
 // Inside a CTA a problem runs on its right-hand side staged in shared
 // memory in chunks of NC columns (k rows x NC, row-major):
-//   TRSM (forward): rows taken sb at a time (sb = 8, 16 or 32, per problem
+//   TRSM (forward): rows taken sb at a time (sb = 4, 8 or 16, per problem
 //     from the tuning table): substitution on the sb-row diagonal block (one
-//     thread per column), then a rank-sb update of every row below it, each
-//     thread a register tile of 4 rows x 4 columns;
+//     thread per column, the block's tile of M staged in shared memory during
+//     the previous block's update), then a rank-sb update of every row below
+//     it, each thread a register tile of 4 rows x 4 columns;
 //   TRMM: out of place, every row's alpha * sum_{l <= i} M(i,l) C(l,:)
 //     formed from the staged original columns and written straight back to
 //     global memory, again in 4 x 4 register tiles.
@@ -46,7 +47,10 @@ struct BShape {
     static constexpr int LDC = NC + 1;                     // odd stride: three CTAs per SM
     static constexpr int CG = NC / 4;                      // column groups of 4
     static constexpr int RG = NT / CG;                     // row groups
-    static constexpr size_t smem = sizeof(T) * ((size_t)kBatchMaxK * LDC + kBatchMaxK);
+    static constexpr int SBMAX = 16;                       // largest substitution block
+    // panel, diagonal, two staged diagonal tiles of the substitution blocks
+    static constexpr size_t smem =
+        sizeof(T) * ((size_t)kBatchMaxK * LDC + kBatchMaxK + 2 * SBMAX * SBMAX);
 };
 
 template <typename T>
@@ -55,33 +59,48 @@ __device__ __forceinline__ T ldA(const T* A, int64_t i, int64_t l, int64_t rs, i
 }
 
 template <typename T, int SB>
-__device__ __forceinline__ void trsm_chunk(const BatchDesc& d, T* sC, const T* sD, int k) {
+__device__ __forceinline__ void trsm_chunk(const BatchDesc& d, T* sC, const T* sD, T* sTile,
+                                           int k) {
     using S = BShape<T>;
+    static_assert(SB <= S::SBMAX, "substitution block above the staged tile size");
     const int tid = threadIdx.x;
     const T* A = static_cast<const T*>(d.A);
     const int cg = tid % S::CG, rg = tid / S::CG;
+    // The SB x SB diagonal tile of block s (strictly lower, zeros elsewhere)
+    // is staged in shared memory during block s-1's update, so the serial
+    // substitution reads it without waiting on global memory.
+    const bool row_fast = (d.a_rs == 1 || d.a_rs == -1);
+    auto stage_tile = [&](int s1, T* dst) {
+        for (int e = tid; e < SB * SB; e += S::NT) {
+            const int q = row_fast ? e % SB : e / SB, jj = row_fast ? e / SB : e % SB;
+            dst[q * SB + jj] = (q > jj && s1 + q < k) ? ldA(A, s1 + q, s1 + jj, d.a_rs, d.a_cs)
+                                                      : T(0);
+        }
+    };
+    stage_tile(0, sTile);
+    __syncthreads();
+    int buf = 0;
     for (int s0 = 0; s0 < k; s0 += SB) {
         const int sbn = min(SB, k - s0);
+        const T* tile = sTile + buf * S::SBMAX * S::SBMAX;
         if (tid < S::NC) {
             T x[SB];
 #pragma unroll
             for (int q = 0; q < SB; ++q) x[q] = q < sbn ? sC[(s0 + q) * S::LDC + tid] : T(0);
             // Rows past k (a ragged last block) stay zero: their diagonal
-            // factor is 1 and their entries of M are not read.
+            // factor is 1 and their tile entries are zero.
 #pragma unroll
             for (int jj = 0; jj < SB; ++jj) {
                 x[jj] *= (jj < sbn) ? sD[s0 + jj] : T(1);
 #pragma unroll
-                for (int q = jj + 1; q < SB; ++q) {
-                    const T t = (q < sbn) ? ldA(A, s0 + q, s0 + jj, d.a_rs, d.a_cs) : T(0);
-                    x[q] = fma(-t, x[jj], x[q]);
-                }
+                for (int q = jj + 1; q < SB; ++q) x[q] = fma(-tile[q * SB + jj], x[jj], x[q]);
             }
 #pragma unroll
             for (int q = 0; q < SB; ++q)
                 if (q < sbn) sC[(s0 + q) * S::LDC + tid] = x[q];
         }
         __syncthreads();
+        if (s0 + SB < k) stage_tile(s0 + SB, sTile + (buf ^ 1) * S::SBMAX * S::SBMAX);
         // Rank-SB update of the rows below the block: each thread a tile of
         // 4 rows x 4 columns (4 loads of M feed 16 multiply-adds).
         for (int i0 = s0 + SB + 4 * rg; i0 < k; i0 += 4 * S::RG) {
@@ -119,6 +138,7 @@ __device__ __forceinline__ void trsm_chunk(const BatchDesc& d, T* sC, const T* s
                 }
         }
         __syncthreads();
+        buf ^= 1;
     }
 }
 
@@ -176,6 +196,7 @@ __global__ void __launch_bounds__(256, 3) batched_kernel(const BatchDesc* descs,
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* sC = reinterpret_cast<T*>(smem_raw);         // panel: row i, column c at i*LDC + c
     T* sD = sC + (size_t)kBatchMaxK * S::LDC;         // reciprocal (TRSM) or plain (TRMM) diagonal
+    T* sTile = sD + kBatchMaxK;                        // two staged diagonal tiles
     __shared__ int s_next;
     pdl_trigger();
     pdl_wait();
@@ -228,9 +249,9 @@ __global__ void __launch_bounds__(256, 3) batched_kernel(const BatchDesc* descs,
             }
             __syncthreads();
             if (d.trsm) {
-                if (d.sb == 8) trsm_chunk<T, 8>(d, sC, sD, k);
-                else if (d.sb == 32) trsm_chunk<T, 32>(d, sC, sD, k);
-                else trsm_chunk<T, 16>(d, sC, sD, k);
+                if (d.sb == 4) trsm_chunk<T, 4>(d, sC, sD, sTile, k);
+                else if (d.sb == 8) trsm_chunk<T, 8>(d, sC, sD, sTile, k);
+                else trsm_chunk<T, 16>(d, sC, sD, sTile, k);
                 for (int e = tid; e < k * S::NC; e += S::NT) {
                     const int i = row_fast ? e % k : e / S::NC, c = row_fast ? e / k : e % S::NC;
                     if (c < ncols) C[i * d.c_rs + (c0 + c) * d.c_cs] = sC[i * S::LDC + c];

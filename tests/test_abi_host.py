@@ -82,6 +82,15 @@ def test_handle_calls_reject_null(lib):
     assert lib.trx_workspace_size(None, b"S", b"L", 4, 4, 4, ctypes.byref(out)) == 1
 
 
+def test_prepared_batch_calls_reject_null(lib):
+    import ctypes
+    out = ctypes.c_void_p(1)
+    assert lib.trx_batch_create(None, 4, 0, None, ctypes.byref(out)) == 1    # TRX_ERR_HANDLE
+    assert not out.value                                                      # cleared
+    assert lib.trx_batch_run(None, None, None) == 1
+    assert lib.trx_batch_destroy(None) == 0
+
+
 @pytest.mark.skipif(torch.cuda.is_available(), reason="host without a GPU only")
 def test_create_fails_cleanly_without_gpu(lib):
     h = ctypes.c_void_p()
