@@ -334,36 +334,78 @@ def run_gpu(args):
         "whole_step_frac": (flops_step / (ms_step * 1e-3) / 1e12) / peak_tc,
     }
 
-    # End to end through the public API: pinned host buffers, H2D of A and B,
-    # TRSM + TRMM, D2H of the result, every step.
+    # End to end through the public API: pinned host buffers, every step the
+    # H2D copy of A and B, TRSM + TRMM, and the D2H copy of the result.
+    # Pipelined over steps the way a stream of independent jobs would run:
+    # two device slots, uploads on one copy stream, compute on the call's
+    # stream, downloads on another copy stream, so step i+1's upload and step
+    # i-1's download overlap step i's compute (the first upload and the last
+    # download are in the timed region, unoverlapped). The same steps run
+    # serially on one stream as well ("serial").
     e2e = None
     if not args.no_e2e:
         A_h = torch.from_numpy(A_np).pin_memory()
         B_h = torch.from_numpy(B_np).pin_memory()
-        out_h = torch.empty_like(B_h).pin_memory()
-        Ad = torch.empty_like(A)
-        Bd = torch.empty_like(B)
+        out_h = [torch.empty_like(B_h).pin_memory() for _ in range(2)]
+        Ad = [torch.empty_like(A) for _ in range(2)]
+        Bd = [torch.empty_like(B) for _ in range(2)]
+        up, down = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
+        ev_up = [torch.cuda.Event() for _ in range(2)]
+        ev_done = [torch.cuda.Event() for _ in range(2)]
+        ev_down = [torch.cuda.Event() for _ in range(2)]
+        for i in range(2):
+            ev_down[i].record(down)
 
-        def e2e_step():
-            Ad.copy_(A_h, non_blocking=True)
-            Bd.copy_(B_h, non_blocking=True)
-            trx.trsm("L", "L", "N", "N", ALPHA, Ad, Bd, handle=h, stream=stream)
-            trx.trmm("L", "L", "N", "N", 1.0 / ALPHA, Ad, Bd, handle=h, stream=stream)
-            out_h.copy_(Bd, non_blocking=True)
+        def e2e_step(i):
+            sl = i % 2
+            up.wait_event(ev_down[sl])                 # slot's last result read back
+            with torch.cuda.stream(up):
+                Ad[sl].copy_(A_h, non_blocking=True)
+                Bd[sl].copy_(B_h, non_blocking=True)
+            ev_up[sl].record(up)
+            stream.wait_event(ev_up[sl])
+            trx.trsm("L", "L", "N", "N", ALPHA, Ad[sl], Bd[sl], handle=h, stream=stream)
+            trx.trmm("L", "L", "N", "N", 1.0 / ALPHA, Ad[sl], Bd[sl], handle=h, stream=stream)
+            ev_done[sl].record(stream)
+            down.wait_event(ev_done[sl])
+            with torch.cuda.stream(down):
+                out_h[sl].copy_(Bd[sl], non_blocking=True)
+            ev_down[sl].record(down)
 
-        e2e_step()
+        def e2e_serial_step():
+            Ad[0].copy_(A_h, non_blocking=True)
+            Bd[0].copy_(B_h, non_blocking=True)
+            trx.trsm("L", "L", "N", "N", ALPHA, Ad[0], Bd[0], handle=h, stream=stream)
+            trx.trmm("L", "L", "N", "N", 1.0 / ALPHA, Ad[0], Bd[0], handle=h, stream=stream)
+            out_h[0].copy_(Bd[0], non_blocking=True)
+
+        for i in range(2):
+            e2e_step(i)
+        e2e_serial_step()
         torch.cuda.synchronize()
-        e_steps = max(1, min(args.steps, 5))
+        nbytes = A_h.numel() * 4
+        e_steps = max(2, min(args.steps, 8))
         barrier(world)
         t0 = time.perf_counter()
-        for _ in range(e_steps):
-            e2e_step()
+        for i in range(e_steps):
+            e2e_step(i)
         torch.cuda.synchronize()
         dt = max_over_ranks(time.perf_counter() - t0, world)
-        nbytes = A_h.numel() * 4
+        s_steps = max(1, min(args.steps, 3))
+        barrier(world)
+        t0 = time.perf_counter()
+        for _ in range(s_steps):
+            e2e_serial_step()
+        torch.cuda.synchronize()
+        dts = max_over_ranks(time.perf_counter() - t0, world)
+        ok = bool(torch.equal(out_h[0], out_h[1]))    # both slots returned the same result
         e2e = {"value": world * flops_step * e_steps / dt / 1e12, "unit": "TFLOP/s",
                "h2d_bytes_per_step": 2 * nbytes, "d2h_bytes_per_step": nbytes,
-               "ms_per_step": 1e3 * dt / e_steps}
+               "ms_per_step": 1e3 * dt / e_steps, "steps": e_steps,
+               "pipelined": "upload of step i+1 and download of step i-1 overlap step i",
+               "slots_agree": ok,
+               "serial": {"value": world * flops_step * s_steps / dts / 1e12,
+                          "ms_per_step": 1e3 * dts / s_steps, "steps": s_steps}}
         del Ad, Bd
 
     # Correctness of the timed data: after the round trips B is back to the
