@@ -141,8 +141,9 @@ int trx_destroy(trx_handle_t handle);
 int trx_set_workspace(trx_handle_t handle, void* ptr, size_t bytes);
 
 /* Bytes of workspace a call needs. elem_bytes is 4 (FP32) or 8 (FP64);
- * op is 'S' (TRSM) or 'M' (TRMM), for which side/m/n are the call's; or 'G'
- * for a tensor-core trx_sgemm_update, with m = M + K and n = N (side 'L').
+ * op is 'S' (TRSM) or 'M' (TRMM), for which side/m/n are the call's; 'Y' for
+ * a call on a prepared factor (TRSM or TRMM, same side/m/n); or 'G' for a
+ * tensor-core trx_sgemm_update, with m = M + K and n = N (side 'L').
  * Depends on the handle's options (the CUDA-core and FP64 paths need none).
  * Returns 0 and sets *bytes, or an argument code as for the compute calls. */
 int trx_workspace_size(trx_handle_t handle, char op, char side, int64_t m,
@@ -208,6 +209,41 @@ typedef struct {
  * batched call's descriptor upload before reusing the staging buffer. */
 int trx_batched(trx_handle_t handle, int elem_bytes, int64_t count,
                 const trx_problem_t* problems, void* stream);
+
+/* Prepared FP32 factor (no counterpart in the paper: an interface for
+ * callers that solve with or multiply by one triangle many times). The
+ * tensor-core path multiplies split-BF16 planes of the canonical triangle
+ * (Section 3.1's off-diagonal blocks of op(A), or of op(A)^T for side 'R');
+ * a factor makes them once and every trx_s{trsm,trmm}_factor call on it skips
+ * the conversion. The factor keeps A (device pointer, lda) and reads it in
+ * every call (base kernels, TRMM's diagonal): A must stay valid, and after
+ * A's contents change trx_sfactor_update must run before the next call.
+ *
+ * trx_sfactor_create: side/uplo/transa/diag/A/lda as in trx_strsm with k the
+ * order of A; enqueues the conversion on stream and returns; the planes are
+ * owned by the factor (device memory, 4 k^2 bytes when k > 128, none
+ * otherwise). Returns -i for an illegal i-th argument of this call (side 2,
+ * uplo 3, transa 4, diag 5, k 6, A 7, lda 8), TRX_ERR_HANDLE,
+ * TRX_ERR_ALLOC, TRX_ERR_CUDA. trx_sfactor_update re-converts from A (the
+ * same layout; the pointer may change; -3 if A is NULL with k > 0) on
+ * stream. trx_strsm_factor / trx_strmm_factor: B := X or alpha op(A) B as
+ * trx_strsm / trx_strmm with the factor's side/uplo/transa/diag/A; nrhs is
+ * the number of right-hand sides (n for side 'L', m for side 'R'); B is
+ * k x nrhs (side 'L') or nrhs x k (side 'R'), column-major, leading
+ * dimension ldb; -3 for nrhs < 0, -5 for a NULL B, -6 for a bad ldb; the
+ * workspace needs only the Y planes (trx_workspace_size with op 'Y').
+ * trx_factor_destroy synchronises the device and frees the factor (NULL is
+ * accepted). A factor belongs to the device of the handle that made it. */
+typedef struct trx_factor_s* trx_factor_t;
+int trx_sfactor_create(trx_handle_t handle, char side, char uplo, char transa, char diag,
+                       int64_t k, const float* A, int64_t lda, void* stream,
+                       trx_factor_t* factor);
+int trx_sfactor_update(trx_handle_t handle, trx_factor_t factor, const float* A, void* stream);
+int trx_strsm_factor(trx_handle_t handle, trx_factor_t factor, int64_t nrhs, float alpha,
+                     float* B, int64_t ldb, void* stream);
+int trx_strmm_factor(trx_handle_t handle, trx_factor_t factor, int64_t nrhs, float alpha,
+                     float* B, int64_t ldb, void* stream);
+int trx_factor_destroy(trx_factor_t factor);
 
 /* Prepared batch: the same problems run many times (fixed pointers; the
  * contents of A and B may change between runs). trx_batch_create checks,

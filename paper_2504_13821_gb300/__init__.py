@@ -7,7 +7,7 @@ include/trx.h. This package is the thin Python binding (argument marshalling
 over torch tensors); the CUDA library is built in-tree by ``build.py``.
 """
 from ._binding import (  # noqa: F401
-    Batch, GEMM_AUTO, GEMM_SIMT, GEMM_TC, OPT_GEMM, OPT_GRAPH, OPT_LEAF, OPT_PANELS, OPT_PDL, OPT_PROFILE,
+    Batch, Factor, GEMM_AUTO, GEMM_SIMT, GEMM_TC, OPT_GEMM, OPT_GRAPH, OPT_LEAF, OPT_PANELS, OPT_PDL, OPT_PROFILE,
     OPT_TRMM_DENSE, OPT_WAIT_LIMIT, Handle, TrxError, batched, batched_autotune, debug_plan,
     default_handle,
     gemm_update, header_functions,

@@ -90,6 +90,11 @@ def load_library() -> ctypes.CDLL:
         lib.trx_batched.argtypes = [vp, ctypes.c_int, i64, ctypes.POINTER(Problem), vp]
         lib.trx_batch_create.argtypes = [vp, ctypes.c_int, i64, ctypes.POINTER(Problem),
                                          ctypes.POINTER(vp)]
+        lib.trx_sfactor_create.argtypes = [vp, c, c, c, c, i64, vp, i64, vp, ctypes.POINTER(vp)]
+        lib.trx_sfactor_update.argtypes = [vp, vp, vp, vp]
+        lib.trx_strsm_factor.argtypes = [vp, vp, i64, ctypes.c_float, vp, i64, vp]
+        lib.trx_strmm_factor.argtypes = [vp, vp, i64, ctypes.c_float, vp, i64, vp]
+        lib.trx_factor_destroy.argtypes = [vp]
         lib.trx_batch_run.argtypes = [vp, vp, vp]
         lib.trx_batch_destroy.argtypes = [vp]
         lib.trx_batched_autotune.argtypes = [vp, ctypes.c_int, i64, ctypes.POINTER(Problem), vp,
@@ -301,6 +306,80 @@ def gemm_update(beta: float, gamma: float, A, Y, C, *, engine: int = GEMM_TC,
     _check(lib.trx_sgemm_update(h.ptr, M, N, K, float(beta), float(gamma), a, lda, y, ldy,
                                 c, ldc, engine, s_ptr), "trx_sgemm_update")
     return C
+
+
+class Factor:
+    """A prepared FP32 triangle (trx_sfactor_create): its operand planes are
+    made once (and again by update()), every trsm()/trmm() on it skips the
+    conversion. A is a column-major CUDA tensor that must stay alive."""
+
+    def __init__(self, side, uplo, trans, diag, A, *, handle: Handle | None = None,
+                 stream=None):
+        import torch
+        if not (isinstance(A, torch.Tensor) and A.is_cuda and A.dtype == torch.float32):
+            raise TypeError("A must be a float32 CUDA tensor")
+        if A.shape[0] != A.shape[1]:
+            raise ValueError("A must be square")
+        self.side = side
+        self.k = A.shape[0]
+        self.A = A
+        a, lda = _colmajor(A, "A")
+        self.handle = handle if handle is not None else default_handle(A.device)
+        self._f = ctypes.c_void_p()
+        _check(load_library().trx_sfactor_create(self.handle.ptr, _char(side), _char(uplo),
+                                                 _char(trans), _char(diag), self.k, a, lda,
+                                                 _stream_ptr(stream, A.device),
+                                                 ctypes.byref(self._f)), "trx_sfactor_create")
+
+    def update(self, A=None, *, stream=None):
+        """Re-make the planes from A (default: the current tensor, e.g. after
+        its contents changed in place)."""
+        if A is not None:
+            self.A = A
+        a, _ = _colmajor(self.A, "A")
+        _check(load_library().trx_sfactor_update(self.handle.ptr, self._f, a,
+                                                 _stream_ptr(stream, self.A.device)),
+               "trx_sfactor_update")
+
+    def _call(self, fn, alpha, B, handle, stream):
+        import torch
+        if not (isinstance(B, torch.Tensor) and B.is_cuda and B.dtype == torch.float32):
+            raise TypeError("B must be a float32 CUDA tensor")
+        b, ldb = _colmajor(B, "B")
+        nrhs = B.shape[1] if self.side.upper() == "L" else B.shape[0]
+        m, n = B.shape
+        h = handle if handle is not None else self.handle
+        h.ensure_workspace(h.workspace_size("Y", self.side, m, n, 4))
+        _check(fn(h.ptr, self._f, nrhs, float(alpha), b, ldb, _stream_ptr(stream, B.device)),
+               fn.__name__)
+        return B
+
+    def trsm(self, alpha, B, *, handle: Handle | None = None, stream=None):
+        """B := X with op(A) X = alpha B (side L) or X op(A) = alpha B (side
+        R); any handle on the factor's device may run it."""
+        return self._call(load_library().trx_strsm_factor, alpha, B, handle, stream)
+
+    def trmm(self, alpha, B, *, handle: Handle | None = None, stream=None):
+        """B := alpha op(A) B (side L) or alpha B op(A) (side R)."""
+        return self._call(load_library().trx_strmm_factor, alpha, B, handle, stream)
+
+    def close(self):
+        if self._f:
+            load_library().trx_factor_destroy(self._f)
+            self._f = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _stream_ptr(stream, device):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream(device)
+    return stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
 
 
 def _problem_array(problems):

@@ -298,14 +298,38 @@ struct GraphKey {
     const void* A;
     const void* C;
     const void* ws;
+    const void* planes;
     double alpha;
     long long wait_ns;
     int pdl, panels, dense;
 };
 
+}  // namespace
+
+// A prepared FP32 factor: its canonical triangle's split-BF16 planes, made
+// once and reused by every call on it (the conversion step is skipped).
+struct trx_factor_s {
+    int magic = 0;
+    int device = 0;
+    char side = 'L', uplo = 'L', transa = 'N', diag = 'N';
+    int64_t k = 0, lda = 1;
+    const float* A = nullptr;
+    __nv_bfloat16* m_hi = nullptr;   // null when k is too small for the tensor-core path
+    __nv_bfloat16* m_lo = nullptr;
+    int64_t ldm = 0;
+};
+
+namespace {
+
+constexpr int kFactorMagic = 0x54524631;   // "TRF1"
+// Diagonal blocks zeroed above the diagonal in a factor's planes: every
+// TRMM diagonal-block size up to this one reads them as dense tiles.
+constexpr int kFactorDenseRows = 2048;
+
 template <typename T>
 int execute(trx_handle_t h, bool trsm, char side, char uplo, char transa, char diag, int64_t m,
-            int64_t n, T alpha, const T* A, int64_t lda, T* B, int64_t ldb, void* stream) {
+            int64_t n, T alpha, const T* A, int64_t lda, T* B, int64_t ldb, void* stream,
+            const trx_factor_s* f = nullptr) {
     const int info = check_args(side, uplo, transa, diag, m, n, A, lda, B, ldb);
     if (info) return info;
     if (!valid(h)) return TRX_ERR_HANDLE;
@@ -328,20 +352,30 @@ int execute(trx_handle_t h, bool trsm, char side, char uplo, char transa, char d
 
     Plan plan;
     plan.tc = use_tc<T>(h, k, trsm, ex.c.nrhs);
+    // A prepared factor supplies the M planes: the workspace holds Y only.
+    const bool factor_planes = plan.tc && f != nullptr && f->m_hi != nullptr;
     if (plan.tc) {
         const WsLayout w = ws_layout(k, ex.c.nrhs);
-        if (h->ws == nullptr || h->ws_bytes < w.total) {
+        const size_t need = factor_planes ? 2 * w.y_bytes : w.total;
+        if (h->ws == nullptr || h->ws_bytes < need) {
             snprintf(g_detail, sizeof(g_detail), "workspace of %zu bytes needed, %zu set",
-                     w.total, h->ws_bytes);
+                     need, h->ws_bytes);
             return TRX_ERR_WORKSPACE;
         }
         char* base = static_cast<char*>(h->ws);
         ex.pl.ldm = w.ldm;
         ex.pl.ldy = w.ldy;
-        ex.pl.m_hi = reinterpret_cast<__nv_bfloat16*>(base);
-        ex.pl.m_lo = reinterpret_cast<__nv_bfloat16*>(base + w.m_bytes);
-        ex.pl.y_hi = reinterpret_cast<__nv_bfloat16*>(base + 2 * w.m_bytes);
-        ex.pl.y_lo = reinterpret_cast<__nv_bfloat16*>(base + 2 * w.m_bytes + w.y_bytes);
+        if (factor_planes) {
+            ex.pl.m_hi = f->m_hi;
+            ex.pl.m_lo = f->m_lo;
+            ex.pl.y_hi = reinterpret_cast<__nv_bfloat16*>(base);
+            ex.pl.y_lo = reinterpret_cast<__nv_bfloat16*>(base + w.y_bytes);
+        } else {
+            ex.pl.m_hi = reinterpret_cast<__nv_bfloat16*>(base);
+            ex.pl.m_lo = reinterpret_cast<__nv_bfloat16*>(base + w.m_bytes);
+            ex.pl.y_hi = reinterpret_cast<__nv_bfloat16*>(base + 2 * w.m_bytes);
+            ex.pl.y_lo = reinterpret_cast<__nv_bfloat16*>(base + 2 * w.m_bytes + w.y_bytes);
+        }
     }
     // TRSM right-hand sides are independent: with many of them the chain runs
     // as P column-panel branches (forked streams, one graph), so the
@@ -374,7 +408,7 @@ int execute(trx_handle_t h, bool trsm, char side, char uplo, char transa, char d
     const int dense = trsm ? 0 : trmm_dense_mode(h->opt_trmm_dense, h->opt_leaf, plan.tc, k);
     Plan pre, body;
     pre.tc = body.tc = plan.tc;
-    if (plan.tc) {
+    if (plan.tc && !factor_planes) {
         Step cm{kConvM};
         cm.b = dense;
         pre.steps.push_back(cm);
@@ -425,6 +459,7 @@ int execute(trx_handle_t h, bool trsm, char side, char uplo, char transa, char d
     key.A = ex.c.A;
     key.C = ex.c.C;
     key.ws = plan.tc ? h->ws : nullptr;
+    key.planes = factor_planes ? f->m_hi : nullptr;
     key.alpha = (double)alpha;
     key.wait_ns = h->wait_ns;
     key.pdl = (int)h->opt_pdl;
@@ -921,10 +956,18 @@ int trx_workspace_size(trx_handle_t h, char op, char side, int64_t m, int64_t n,
     if (m < 0) return -5;
     if (n < 0) return -6;
     if (!valid(h)) return TRX_ERR_HANDLE;
-    if ((elem_bytes != 4 && elem_bytes != 8) || (upc(op) != 'S' && upc(op) != 'M' && upc(op) != 'G') || !bytes)
+    const int o = upc(op);
+    if ((elem_bytes != 4 && elem_bytes != 8) || (o != 'S' && o != 'M' && o != 'G' && o != 'Y') ||
+        !bytes)
         return TRX_ERR_INVALID_VALUE;
     int64_t k = upc(side) == 'L' ? m : n, nrhs = upc(side) == 'L' ? n : m;
-    bool tc = elem_bytes == 4 ? use_tc<float>(h, k, upc(op) == 'S', nrhs) : false;
+    if (o == 'Y') {         // factor calls (TRSM or TRMM): the Y planes only
+        const bool tc = elem_bytes == 4 &&
+                        (use_tc<float>(h, k, true, nrhs) || use_tc<float>(h, k, false, nrhs));
+        *bytes = (tc && k > 0 && nrhs > 0) ? 2 * ws_layout(k, nrhs).y_bytes : 0;
+        return TRX_SUCCESS;
+    }
+    bool tc = elem_bytes == 4 ? use_tc<float>(h, k, o == 'S', nrhs) : false;
     if (upc(op) == 'G') {   // tensor-core trx_sgemm_update: m = M + K rows, n = N
         k = m;
         nrhs = n;
@@ -950,6 +993,124 @@ int trx_dtrmm(trx_handle_t h, char side, char uplo, char transa, char diag, int6
               double alpha, const double* A, int64_t lda, double* B, int64_t ldb, void* stream) {
     return execute<double>(h, false, side, uplo, transa, diag, m, n, alpha, A, lda, B, ldb,
                            stream);
+}
+
+int trx_sfactor_create(trx_handle_t h, char side, char uplo, char transa, char diag, int64_t k,
+                       const float* A, int64_t lda, void* stream, trx_factor_t* out) {
+    if (!out) return TRX_ERR_INVALID_VALUE;
+    *out = nullptr;
+    // argument positions of this call: side 2, uplo 3, transa 4, diag 5,
+    // k 6, A 7, lda 8
+    const int info = check_args(side, uplo, transa, diag, k, k, A, lda, A, std::max<int64_t>(1, k));
+    if (info >= -4 && info <= -1) return info - 1;
+    if (info == -5 || info == -6) return -6;
+    if (info == -8) return -7;
+    if (info == -9) return -8;
+    if (!valid(h)) return TRX_ERR_HANDLE;
+    cudaError_t e = cudaSetDevice(h->device);
+    if (e != cudaSuccess) return fail_cuda(e, "cudaSetDevice");
+    auto* f = new (std::nothrow) trx_factor_s;
+    if (!f) return TRX_ERR_ALLOC;
+    f->device = h->device;
+    f->side = (char)upc(side);
+    f->uplo = (char)upc(uplo);
+    f->transa = (char)upc(transa);
+    f->diag = (char)upc(diag);
+    f->k = k;
+    f->lda = lda;
+    f->A = A;
+    if (k > kMaxLeaf) {                 // some call on it may take the tensor-core path
+        const WsLayout w = ws_layout(k, 0);
+        f->ldm = w.ldm;
+        if ((e = cudaMalloc(&f->m_hi, w.m_bytes)) != cudaSuccess ||
+            (e = cudaMalloc(&f->m_lo, w.m_bytes)) != cudaSuccess) {
+            if (f->m_hi) cudaFree(f->m_hi);
+            delete f;
+            snprintf(g_detail, sizeof(g_detail), "factor planes: %s", cudaGetErrorString(e));
+            return TRX_ERR_ALLOC;
+        }
+    }
+    f->magic = kFactorMagic;
+    const int rc = trx_sfactor_update(h, f, A, stream);
+    if (rc != TRX_SUCCESS) {
+        trx_factor_destroy(f);
+        return rc;
+    }
+    *out = f;
+    return TRX_SUCCESS;
+}
+
+int trx_sfactor_update(trx_handle_t h, trx_factor_t f, const float* A, void* stream) {
+    if (!valid(h)) return TRX_ERR_HANDLE;
+    if (!f || f->magic != kFactorMagic || f->device != h->device) return TRX_ERR_INVALID_VALUE;
+    if (A == nullptr && f->k > 0) return -3;           // A is argument 3 of this call
+    f->A = A;
+    if (!f->m_hi || f->k == 0) return TRX_SUCCESS;
+    cudaError_t e = cudaSetDevice(h->device);
+    if (e != cudaSuccess) return fail_cuda(e, "cudaSetDevice");
+    pdl_enabled() = h->opt_pdl != 0;
+    const bool left = f->side == 'L';
+    const Canon<float> c = canonicalize<float>(f->side, f->uplo, f->transa, f->diag,
+                                               left ? f->k : 1, left ? 1 : f->k, A, f->lda,
+                                               nullptr, f->k);
+    Planes pl;
+    pl.ldm = f->ldm;
+    pl.ldy = f->ldm;
+    pl.m_hi = f->m_hi;
+    pl.m_lo = f->m_lo;
+    pl.y_hi = pl.y_lo = nullptr;
+    const cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (h->opt_profile) {
+        e0 = get_event(h);
+        e1 = get_event(h);
+        cudaEventRecord(e0, s);
+    }
+    e = launch_convert_m(c, pl, kFactorDenseRows, s);
+    if (e != cudaSuccess) return fail_cuda(e, "factor planes");
+    if (h->opt_profile) {
+        cudaEventRecord(e1, s);
+        h->pending.push_back({TRX_KERNEL_CONVERT, 0.0, 8.0 * f->k * (f->k - 1) / 2, e0, e1});
+    }
+    return TRX_SUCCESS;
+}
+
+int trx_factor_destroy(trx_factor_t f) {
+    if (f == nullptr) return TRX_SUCCESS;
+    if (f->magic != kFactorMagic) return TRX_ERR_INVALID_VALUE;
+    cudaSetDevice(f->device);
+    cudaDeviceSynchronize();
+    if (f->m_hi) cudaFree(f->m_hi);
+    if (f->m_lo) cudaFree(f->m_lo);
+    f->magic = 0;
+    delete f;
+    return TRX_SUCCESS;
+}
+
+static int factor_call(trx_handle_t h, trx_factor_t f, bool trsm, int64_t nrhs, float alpha,
+                       float* B, int64_t ldb, void* stream) {
+    if (!f || f->magic != kFactorMagic) return TRX_ERR_INVALID_VALUE;
+    if (valid(h) && f->device != h->device) return TRX_ERR_INVALID_VALUE;
+    const bool left = f->side == 'L';
+    const int64_t m = left ? f->k : nrhs, n = left ? nrhs : f->k;
+    // argument positions of the factor calls: nrhs 3, B 5, ldb 6
+    const int info = check_args(f->side, f->uplo, f->transa, f->diag, m, n, f->A, f->lda, B, ldb);
+    if (info == -5 || info == -6) return -3;
+    if (info == -10) return -5;
+    if (info == -11) return -6;
+    if (info) return info;
+    return execute<float>(h, trsm, f->side, f->uplo, f->transa, f->diag, m, n, alpha, f->A,
+                          f->lda, B, ldb, stream, f);
+}
+
+int trx_strsm_factor(trx_handle_t h, trx_factor_t f, int64_t nrhs, float alpha, float* B,
+                     int64_t ldb, void* stream) {
+    return factor_call(h, f, true, nrhs, alpha, B, ldb, stream);
+}
+
+int trx_strmm_factor(trx_handle_t h, trx_factor_t f, int64_t nrhs, float alpha, float* B,
+                     int64_t ldb, void* stream) {
+    return factor_call(h, f, false, nrhs, alpha, B, ldb, stream);
 }
 
 int trx_sgemm_update(trx_handle_t h, int64_t M, int64_t N, int64_t K, float beta, float gamma,

@@ -82,6 +82,24 @@ def test_handle_calls_reject_null(lib):
     assert lib.trx_workspace_size(None, b"S", b"L", 4, 4, 4, ctypes.byref(out)) == 1
 
 
+def test_factor_calls_reject_bad_arguments(lib):
+    import ctypes
+    out = ctypes.c_void_p(1)
+    # argument checks come before the handle: bad side (position 2), order (6)
+    assert lib.trx_sfactor_create(None, b"X", b"L", b"N", b"N", 4, 1, 4, None,
+                                  ctypes.byref(out)) == -2
+    assert not out.value
+    assert lib.trx_sfactor_create(None, b"L", b"L", b"N", b"N", -1, 1, 4, None,
+                                  ctypes.byref(out)) == -6
+    assert lib.trx_sfactor_create(None, b"L", b"L", b"N", b"N", 4, 1, 2, None,
+                                  ctypes.byref(out)) == -8
+    assert lib.trx_sfactor_create(None, b"L", b"L", b"N", b"N", 4, 1, 4, None,
+                                  ctypes.byref(out)) == 1                  # TRX_ERR_HANDLE
+    assert lib.trx_strsm_factor(None, None, 4, 1.0, None, 4, None) == 7    # TRX_ERR_INVALID_VALUE
+    assert lib.trx_sfactor_update(None, None, None, None) == 1
+    assert lib.trx_factor_destroy(None) == 0
+
+
 def test_prepared_batch_calls_reject_null(lib):
     import ctypes
     out = ctypes.c_void_p(1)

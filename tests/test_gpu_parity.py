@@ -60,6 +60,39 @@ def test_trmm_dense_diagonal_blocks_all_variants(trx, side, uplo, trans, diag):
              seed=inputs.variant_seed(1100, VARIANTS.index((side, uplo, trans, diag))))
 
 
+@pytest.mark.parametrize("side,uplo,trans,diag", VARIANTS)
+def test_factor_calls_all_variants(trx, side, uplo, trans, diag):
+    """Prepared factor (planes made once): TRSM and TRMM through it equal the
+    plain calls bitwise, match the oracle, and follow A after an in-place
+    change and update()."""
+    k, nrhs = 1100, 300
+    m, n = (k, nrhs) if side == "L" else (nrhs, k)
+    vi = VARIANTS.index((side, uplo, trans, diag))
+    A, B = inputs.problem(side, uplo, m, n, seed=inputs.variant_seed(k, vi), dtype=np.float32,
+                          poison_diag=(diag == "U"))
+    dev = torch.device("cuda", 0)
+    At = to_dev(A, dev)
+    f = trx.Factor(side, uplo, trans, diag, At)
+    for op in ("trsm", "trmm"):
+        plain, via = to_dev(B, dev), to_dev(B, dev)
+        getattr(trx, op)(side, uplo, trans, diag, 0.75, At, plain)
+        getattr(f, op)(0.75, via)
+        torch.cuda.synchronize()
+        assert torch.equal(plain, via), op
+    # A changes in place: after update() the factor uses the new values
+    A2, _ = inputs.problem(side, uplo, m, n, seed=inputs.variant_seed(k + 1, vi),
+                           dtype=np.float32, poison_diag=(diag == "U"))
+    At.copy_(to_dev(A2, dev))
+    f.update()
+    X = to_dev(B, dev)
+    f.trsm(0.75, X)
+    torch.cuda.synchronize()
+    eta = oracle.trsm_backward_error(side, uplo, trans, diag, 0.75, A2,
+                                     np.asfortranarray(X.cpu().numpy()), B)["eta"]
+    assert eta <= bound(k, np.float32)
+    f.close()
+
+
 @pytest.mark.parametrize("op", ["trsm", "trmm"])
 @pytest.mark.parametrize("side", ["L", "R"])
 def test_two_panels_equal_one_call(trx, op, side):
