@@ -75,9 +75,11 @@ cudaError_t launch_leaf(bool trsm, const Canon<T>& p, int64_t r0, int b,
     a.alpha = alpha;
     a.planes = planes != nullptr;
     if (planes) a.pl = *planes;
-    // A single TRSM leaf of 33..128 rows with many right-hand sides takes the
-    // blocked kernel (16-row substitutions + rank-16 updates); the lane-split
-    // sweep below covers the rest. TRX_LEAF_BLOCKED=0 turns it off.
+    // A single TRSM leaf with at least 1024 right-hand sides takes a blocked
+    // kernel: FP32 leaves of 65..128 rows the wide kernel, other leaves of
+    // 33..128 rows the blocked kernel (16-row substitutions + rank-16
+    // updates); the lane-split sweep below covers the rest.
+    // TRX_LEAF_BLOCKED=0 turns both off.
     static const bool blocked_on = [] {
         const char* e = std::getenv("TRX_LEAF_BLOCKED");
         return !(e && e[0] == '0');
