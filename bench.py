@@ -541,6 +541,83 @@ def run_batched(args):
     return 0
 
 
+def run_refined(args):
+    """Refined FP32 TRSM (the precision form): the FP32 solve refined in FP64
+    until the normwise backward error is at the FP64 level, side L, lower,
+    on factors whose condition number is about 1e2, 1e4 and 1e6 (scales of
+    the seeded generator stored in tests/golden/condition_scales.json),
+    against the plain FP32 solve and the FP64 solve of the same data."""
+    import torch
+    import paper_2504_13821_gb300 as trx
+    from paper_2504_13821_gb300 import inputs
+    dev = torch.device("cuda", 0)
+    with open(os.path.join(ROOT, "tests", "golden", "condition_scales.json")) as f:
+        entries = [e for e in json.load(f)["entries"] if e["k"] == K_ORDER]
+    if not entries:
+        print(json.dumps({"error": f"no stored condition scales for order {K_ORDER}"}))
+        return 1
+    k, n = K_ORDER, NRHS
+    h = trx.Handle(dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def timed(fn, reps):
+        for _ in range(max(args.warmup, 1)):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    rows, total_ms = [], 0.0
+    for e in entries:
+        A, B = inputs.problem("L", "L", k, n, seed=e["seed"], dtype=np.float32, scale=e["scale"])
+        At, Bt = trx.to_colmajor(torch.from_numpy(A).to(dev)), trx.to_colmajor(
+            torch.from_numpy(B).to(dev))
+        X = torch.empty((n, k), dtype=torch.float64, device=dev).t()
+        info = {}
+
+        def refined():
+            info.update(trx.trsm_refined("L", "L", "N", "N", 1.5, At, Bt, out=X, handle=h)[1])
+        ms_ref = timed(refined, args.steps)
+        X32 = Bt.clone()
+        ms_32 = timed(lambda: trx.trsm("L", "L", "N", "N", 1.5, At, X32.copy_(Bt), handle=h),
+                      args.steps)
+        A64, B64 = At.double(), Bt.double()
+        X64 = B64.clone()
+        ms_64 = timed(lambda: trx.trsm("L", "L", "N", "N", 1.5, A64, X64.copy_(B64), handle=h),
+                      max(1, min(args.steps, 3)))
+        X32d = X32.double()
+
+        def rel(a):
+            return float((a - X64).abs().sum(dim=1).max() / X64.abs().sum(dim=1).max())
+        rows.append({"kappa_target": e["target"], "kappa_estimate": e["kappa_estimate"],
+                     "scale": e["scale"], "ms_refined": ms_ref, "ms_fp32": ms_32,
+                     "ms_fp64": ms_64, "iterations": info["iterations"],
+                     "backward_error": info["backward_error"],
+                     "backward_error_fp32": info["initial_backward_error"],
+                     "diff_vs_fp64_solve": rel(X), "diff_fp32_vs_fp64_solve": rel(X32d)})
+        total_ms += ms_ref
+        del At, Bt, X, X32, A64, B64, X64, X32d
+    line = {
+        "metric": "refined FP32 TRSM solves/s", "value": len(rows) / (total_ms * 1e-3),
+        "unit": "solves/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": total_ms / len(rows), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": f"refined TRSM side L lower, k={k}, {n} right-hand sides, "
+                               "alpha 1.5, kappa about 1e2/1e4/1e6, stop at backward error "
+                               "sqrt(k) 2^-53",
+                   "l2": "factor (k^2 FP32 = 256 MB at k = 8192) larger than L2, no flush"},
+        "per_kappa": rows,
+    }
+    print(json.dumps(line), flush=True)
+    h.close()
+    return 0
+
+
 def run_serving(args):
     """Serving workload: open-loop Poisson arrivals (args.rate per second for
     args.duration seconds), 70% TRSM / 30% TRMM, order log-uniform 64..8192,
@@ -620,23 +697,30 @@ def main(argv=None):
     ap.add_argument("--leaf", type=int, default=0, help="recursion cutoff b (0: library default)")
     ap.add_argument("--pdl", action="store_true", help="launch with programmatic dependent launch")
     ap.add_argument("--panels", type=int, default=0, help="TRSM column-panel branches (0: auto)")
-    ap.add_argument("--k", type=int, default=16384,
-                    help="order of A (default 16384; smaller only for profiling runs)")
-    ap.add_argument("--nrhs", type=int, default=16384, help="right-hand sides (default 16384)")
+    ap.add_argument("--k", type=int, default=None,
+                    help="order of A (default 16384, refined workload 8192; smaller only for "
+                         "profiling runs)")
+    ap.add_argument("--nrhs", type=int, default=None,
+                    help="right-hand sides (default 16384, refined workload 256)")
     ap.add_argument("--dtype", default="f32", choices=["f32", "f64"])
     ap.add_argument("--rate", type=float, default=2000.0, help="serving: arrivals per second")
     ap.add_argument("--duration", type=float, default=60.0, help="serving: seconds of arrivals")
     ap.add_argument("--fp64-share", type=float, default=0.5,
                     help="serving: fraction of FP64 requests (the rest FP32)")
-    ap.add_argument("--workload", default="square", choices=["square", "batched", "serving"],
+    ap.add_argument("--workload", default="square",
+                    choices=["square", "batched", "serving", "refined"],
                     help="square: the n=16384 TRSM+TRMM step (default); batched: "
-                         "4096 small uneven problems in one launch")
+                         "4096 small uneven problems in one launch; serving: Poisson "
+                         "arrivals; refined: FP32 TRSM refined in FP64 (k 8192, 256 "
+                         "right-hand sides unless --k/--nrhs say otherwise)")
     ap.add_argument("--count", type=int, default=4096, help="problems (batched workload)")
     ap.add_argument("--no-autotune", action="store_true",
                     help="batched workload: keep the default block sizes (for profiling runs)")
     args = ap.parse_args(argv)
     global K_ORDER, NRHS, DTYPE
-    K_ORDER, NRHS = args.k, args.nrhs
+    refined = args.workload == "refined"
+    K_ORDER = args.k if args.k is not None else (8192 if refined else 16384)
+    NRHS = args.nrhs if args.nrhs is not None else (256 if refined else 16384)
     DTYPE = np.float32 if args.dtype == "f32" else np.float64
     if args.impl == "reference":
         return run_reference(args)
@@ -644,6 +728,8 @@ def main(argv=None):
         return run_batched(args)
     if args.workload == "serving":
         return run_serving(args)
+    if args.workload == "refined":
+        return run_refined(args)
     return run_gpu(args)
 
 

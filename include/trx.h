@@ -210,6 +210,35 @@ typedef struct {
 int trx_batched(trx_handle_t handle, int elem_bytes, int64_t count,
                 const trx_problem_t* problems, void* stream);
 
+/* Refined FP32 TRSM (the precision form): the FP32 solve of trx_strsm, then
+ * iterative refinement in FP64: R = alpha B - op(A) X with FP64 arithmetic
+ * (FP32 data, so every product is exact; the library's own FP64 TRMM on an
+ * FP64 copy of A), a correction op(A) D = R (or D op(A) = R) solved in FP32
+ * on the same path, X += D in FP64, until the normwise backward error
+ * ||R|| / (||op(A)|| ||X||) (infinity norms) is at most tol, max_iter
+ * corrections were made, or a correction did not lower it. A (k x k) and B (m x n) are FP32 device arrays as
+ * in trx_strsm, B is not modified; X (m x n, FP64, leading dimension ldx) is
+ * the result. Synchronous: it reads the residual norm back after every
+ * step. Needs the workspace of trx_strsm (trx_workspace_size 'S') and
+ * allocates its own FP64 scratch on the handle (8 k^2 + 20 m n bytes,
+ * kept for later calls). info (may be NULL): corrections made, the final
+ * residual norm and backward error, and the backward error of the plain
+ * FP32 solve. Returns -i for an illegal i-th argument of this call (side 2,
+ * uplo 3, transa 4, diag 5, m 6, n 7, alpha 8, A 9, lda 10, B 11, ldb 12,
+ * X 13, ldx 14, max_iter < 0: 15, tol < 0 or NaN: 16), or a TRX_ERR_*
+ * code. (The paper's base solve and GEMM updates are the FP32 steps; the
+ * refinement loop around them is this library's.) */
+typedef struct {
+    int iterations;                 /* corrections applied                  */
+    double residual_norm;           /* ||alpha B - op(A) X||_inf at the end  */
+    double backward_error;          /* ||R|| / (||op(A)|| ||X||) at the end  */
+    double initial_backward_error;  /* the same for the plain FP32 solve     */
+} trx_refine_info_t;
+int trx_strsm_refined(trx_handle_t handle, char side, char uplo, char transa, char diag,
+                      int64_t m, int64_t n, float alpha, const float* A, int64_t lda,
+                      const float* B, int64_t ldb, double* X, int64_t ldx, int max_iter,
+                      double tol, trx_refine_info_t* info, void* stream);
+
 /* Prepared FP32 factor (no counterpart in the paper: an interface for
  * callers that solve with or multiply by one triangle many times). The
  * tensor-core path multiplies split-BF16 planes of the canonical triangle

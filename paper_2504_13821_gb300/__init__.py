@@ -11,8 +11,8 @@ from ._binding import (  # noqa: F401
     OPT_TRMM_DENSE, OPT_WAIT_LIMIT, Handle, TrxError, batched, batched_autotune, debug_plan,
     default_handle,
     gemm_update, header_functions,
-    load_library, to_colmajor, trmm, trsm,
+    load_library, to_colmajor, trmm, trsm, trsm_refined,
 )
 
-__all__ = ["trsm", "trmm", "Handle", "TrxError", "default_handle", "debug_plan",
+__all__ = ["trsm", "trmm", "trsm_refined", "Handle", "TrxError", "default_handle", "debug_plan",
            "load_library", "to_colmajor"]

@@ -49,6 +49,13 @@ class Problem(ctypes.Structure):
                 ("B", ctypes.c_void_p), ("ldb", ctypes.c_int64)]
 
 
+class RefineInfo(ctypes.Structure):
+    """trx_refine_info_t."""
+    _fields_ = [("iterations", ctypes.c_int), ("residual_norm", ctypes.c_double),
+                ("backward_error", ctypes.c_double),
+                ("initial_backward_error", ctypes.c_double)]
+
+
 class _Profile(ctypes.Structure):
     _fields_ = [("ms", ctypes.c_double * 6), ("flops", ctypes.c_double * 6),
                 ("bytes", ctypes.c_double * 6), ("launches", ctypes.c_int64 * 6)]
@@ -99,6 +106,9 @@ def load_library() -> ctypes.CDLL:
         lib.trx_batch_destroy.argtypes = [vp]
         lib.trx_batched_autotune.argtypes = [vp, ctypes.c_int, i64, ctypes.POINTER(Problem), vp,
                                              ctypes.c_char_p, ctypes.c_size_t]
+        lib.trx_strsm_refined.argtypes = [vp, c, c, c, c, i64, i64, ctypes.c_float, vp, i64, vp,
+                                          i64, vp, i64, ctypes.c_int, ctypes.c_double,
+                                          ctypes.POINTER(RefineInfo), vp]
         lib.trx_version.argtypes = []
         _lib = lib
         return lib
@@ -259,6 +269,52 @@ def trmm(side: str, uplo: str, trans: str, diag: str, alpha: float, A, B, *,
     """B := alpha op(A) B (side 'L') or alpha B op(A) (side 'R') in place.
     Paper Eq. 1-2."""
     return _call("trmm", side, uplo, trans, diag, alpha, A, B, handle, stream)
+
+
+def trsm_refined(side: str, uplo: str, trans: str, diag: str, alpha: float, A, B, *,
+                 out=None, max_iter: int = 10, tol: float | None = None,
+                 handle: Handle | None = None, stream=None):
+    """FP32 solve of op(A) X = alpha B (or X op(A) = alpha B) refined in FP64.
+
+    A and B are float32 CUDA tensors (B is not modified); the result is a
+    float64 column-major tensor (``out`` if given). Each step forms the
+    residual alpha B - op(A) X in FP64, solves for the correction in FP32 on
+    the recursive path (Section 3.1) and adds it in FP64. ``tol`` bounds the
+    normwise backward error ||R|| / (||op(A)|| ||X||) (infinity norms);
+    by default sqrt(k) * 2**-53. Returns (X, info) with info a dict:
+    iterations, residual_norm, backward_error, initial_backward_error.
+    """
+    import torch
+    lib = load_library()
+    if not (isinstance(A, torch.Tensor) and isinstance(B, torch.Tensor)):
+        raise TypeError("A and B must be torch tensors")
+    if A.dtype != torch.float32 or B.dtype != torch.float32:
+        raise TypeError(f"A and B must be float32 (got {A.dtype}, {B.dtype})")
+    if not (A.is_cuda and B.is_cuda) or A.device != B.device:
+        raise ValueError("A and B must be CUDA tensors on one device")
+    m, n = B.shape
+    k = m if side.upper() == "L" else n
+    if tuple(A.shape) != (k, k):
+        raise ValueError(f"A must be {k}x{k} for side {side!r} and B {m}x{n}")
+    if out is None:
+        out = torch.empty((n, m), dtype=torch.float64, device=B.device).t()
+    if out.dtype != torch.float64 or tuple(out.shape) != (m, n) or out.device != B.device:
+        raise ValueError(f"out must be a float64 {m}x{n} tensor on {B.device}")
+    a_ptr, lda = _colmajor(A, "A")
+    b_ptr, ldb = _colmajor(B, "B")
+    x_ptr, ldx = _colmajor(out, "out")
+    if tol is None:
+        tol = max(k, 1) ** 0.5 * 2.0 ** -53
+    h = handle if handle is not None else default_handle(B.device)
+    h.ensure_workspace(h.workspace_size("S", side, m, n, 4))
+    info = RefineInfo()
+    rc = lib.trx_strsm_refined(h.ptr, _char(side), _char(uplo), _char(trans), _char(diag), m, n,
+                               float(alpha), a_ptr, lda, b_ptr, ldb, x_ptr, ldx, int(max_iter),
+                               float(tol), ctypes.byref(info), _stream_ptr(stream, B.device))
+    _check(rc, "trx_strsm_refined")
+    return out, {"iterations": info.iterations, "residual_norm": info.residual_norm,
+                 "backward_error": info.backward_error,
+                 "initial_backward_error": info.initial_backward_error}
 
 
 def debug_plan(op: str, side, uplo, trans, diag, m, n, elem_bytes=4, leaf=0, gemm=0,

@@ -184,6 +184,9 @@ struct trx_handle_s {
     // column-panel branches of a TRSM: streams and fork/join events
     int64_t opt_panels = 0;
     int64_t opt_trmm_dense = 0;
+    // refined TRSM scratch (grown on demand)
+    void* rf_buf = nullptr;
+    size_t rf_bytes = 0;
     cudaStream_t aux[kMaxPanels] = {};
     cudaEvent_t fork_ev = nullptr, join_ev[kMaxPanels] = {};
 };
@@ -924,6 +927,7 @@ int trx_destroy(trx_handle_t h) {
     if (h->b_counter) cudaFree(h->b_counter);
     if (h->b_host) cudaFreeHost(h->b_host);
     if (h->b_uploaded) cudaEventDestroy(h->b_uploaded);
+    if (h->rf_buf) cudaFree(h->rf_buf);
     free_owned_ws(h);
     if (h->d_err) cudaFree(h->d_err);
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
@@ -993,6 +997,102 @@ int trx_dtrmm(trx_handle_t h, char side, char uplo, char transa, char diag, int6
               double alpha, const double* A, int64_t lda, double* B, int64_t ldb, void* stream) {
     return execute<double>(h, false, side, uplo, transa, diag, m, n, alpha, A, lda, B, ldb,
                            stream);
+}
+
+int trx_strsm_refined(trx_handle_t h, char side, char uplo, char transa, char diag, int64_t m,
+                      int64_t n, float alpha, const float* A, int64_t lda, const float* B,
+                      int64_t ldb, double* X, int64_t ldx, int max_iter, double tol,
+                      trx_refine_info_t* info, void* stream) {
+    // argument positions of this call: side 2 .. ldb 12 (the BLAS ones + 1),
+    // X 13, ldx 14, max_iter 15, tol 16
+    const int ia = check_args(side, uplo, transa, diag, m, n, A, lda, B, ldb);
+    if (ia) return ia - 1;
+    if (m > 0 && n > 0 && X == nullptr) return -13;
+    if (ldx < std::max<int64_t>(1, m)) return -14;
+    if (max_iter < 0) return -15;
+    if (!(tol >= 0.0)) return -16;
+    if (!valid(h)) return TRX_ERR_HANDLE;
+    if (info) *info = trx_refine_info_t{0, 0.0, 0.0, 0.0};
+    if (m == 0 || n == 0) return TRX_SUCCESS;
+    cudaError_t e = cudaSetDevice(h->device);
+    if (e != cudaSuccess) return fail_cuda(e, "cudaSetDevice");
+    const cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const bool left = upc(side) == 'L';
+    const int64_t k = left ? m : n;
+    // scratch: A64 (k x k), B64 and R64 (m x n, FP64), D32 (m x n), sums, norms
+    const size_t a64 = align256((size_t)k * k * 8), mn64 = align256((size_t)m * n * 8);
+    const size_t mn32 = align256((size_t)m * n * 4), sums = align256((size_t)std::max(m, k) * 8);
+    const size_t need = a64 + 2 * mn64 + mn32 + sums + 256;
+    if (h->rf_bytes < need) {
+        if (h->rf_buf) {
+            cudaStreamSynchronize(s);
+            cudaFree(h->rf_buf);
+        }
+        h->rf_buf = nullptr;
+        h->rf_bytes = 0;
+        if ((e = cudaMalloc(&h->rf_buf, need)) != cudaSuccess) {
+            snprintf(g_detail, sizeof(g_detail), "refine scratch: %s", cudaGetErrorString(e));
+            return TRX_ERR_ALLOC;
+        }
+        h->rf_bytes = need;
+    }
+    char* base = static_cast<char*>(h->rf_buf);
+    double* A64 = reinterpret_cast<double*>(base);
+    double* B64 = reinterpret_cast<double*>(base + a64);
+    double* R64 = reinterpret_cast<double*>(base + a64 + mn64);
+    float* D32 = reinterpret_cast<float*>(base + a64 + 2 * mn64);
+    double* sm = reinterpret_cast<double*>(base + a64 + 2 * mn64 + mn32);
+    double* norms = reinterpret_cast<double*>(base + a64 + 2 * mn64 + mn32 + sums);
+    const bool lower = upc(uplo) == 'L', trans = upc(transa) != 'N', unit = upc(diag) == 'U';
+    int rc;
+    // 1. the FP32 solve (the plain path), X := its result in FP64
+    if ((e = cudaMemcpy2DAsync(D32, m * 4, B, ldb * 4, m * 4, n, cudaMemcpyDeviceToDevice, s)) !=
+        cudaSuccess)
+        return fail_cuda(e, "refine copy");
+    if ((rc = execute<float>(h, true, side, uplo, transa, diag, m, n, alpha, A, lda, D32, m,
+                             stream)) != TRX_SUCCESS)
+        return rc;
+    if ((e = refine_cast_f32_f64(D32, m, X, ldx, m, n, 1.0, s)) != cudaSuccess ||
+        (e = refine_cast_f32_f64(A, lda, A64, k, k, k, 1.0, s)) != cudaSuccess ||
+        (e = refine_cast_f32_f64(B, ldb, B64, m, m, n, (double)alpha, s)) != cudaSuccess ||
+        (e = refine_op_norm_inf(A64, k, k, lower, trans, unit, sm, norms, s)) != cudaSuccess)
+        return fail_cuda(e, "refine setup");
+    double host[3] = {0, 0, 0};
+    double eta0 = 0.0, eta = 0.0, eta_prev = 0.0, rnorm = 0.0;
+    int it = 0;
+    for (;; ++it) {
+        // 2. R := alpha B - op(A) X in FP64 (products of FP32 data are exact)
+        if ((e = cudaMemcpy2DAsync(R64, m * 8, X, ldx * 8, m * 8, n, cudaMemcpyDeviceToDevice, s)) !=
+            cudaSuccess)
+            return fail_cuda(e, "refine copy");
+        if ((rc = execute<double>(h, false, side, uplo, transa, diag, m, n, 1.0, A64, k, R64, m,
+                                  stream)) != TRX_SUCCESS)
+            return rc;
+        if ((e = refine_residual(B64, m, R64, m, m, n, s)) != cudaSuccess ||
+            (e = refine_norm_inf(R64, m, m, n, sm, norms + 1, s)) != cudaSuccess ||
+            (e = refine_norm_inf(X, ldx, m, n, sm, norms + 2, s)) != cudaSuccess ||
+            (e = cudaMemcpyAsync(host, norms, 3 * sizeof(double), cudaMemcpyDeviceToHost, s)) !=
+                cudaSuccess ||
+            (e = cudaStreamSynchronize(s)) != cudaSuccess)
+            return fail_cuda(e, "refine residual");
+        rnorm = host[1];
+        const double den = host[0] * host[2];
+        eta = den > 0 ? rnorm / den : rnorm;
+        if (it == 0) eta0 = eta;
+        // stop: converged, out of corrections, NaN, or no progress
+        if (eta <= tol || it >= max_iter || !(eta == eta) || (it > 0 && eta >= eta_prev)) break;
+        eta_prev = eta;
+        // 3. correction: op(A) D = R solved in FP32, X += D
+        if ((e = refine_cast_f64_f32(R64, m, D32, m, m, n, s)) != cudaSuccess)
+            return fail_cuda(e, "refine cast");
+        if ((rc = execute<float>(h, true, side, uplo, transa, diag, m, n, 1.0f, A, lda, D32, m,
+                                 stream)) != TRX_SUCCESS)
+            return rc;
+        if ((e = refine_add(X, ldx, D32, m, m, n, s)) != cudaSuccess)
+            return fail_cuda(e, "refine update");
+    }
+    if (info) *info = trx_refine_info_t{it, rnorm, eta, eta0};
+    return TRX_SUCCESS;
 }
 
 int trx_sfactor_create(trx_handle_t h, char side, char uplo, char transa, char diag, int64_t k,

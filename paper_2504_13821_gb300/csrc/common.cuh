@@ -141,6 +141,20 @@ cudaError_t launch_gemm_tc(const Canon<float>& p, const void* maps,
                            const TcGemm* gemms, int ngemms, float beta,
                            float gamma, int* err_word, long long wait_limit,
                            int num_sms, cudaStream_t s, bool diag_beta = false);
+// Refined TRSM helpers (refine.cu): casts, residual, correction, norms.
+cudaError_t refine_cast_f32_f64(const float* src, int64_t lds, double* dst, int64_t ldd, int64_t m,
+                                int64_t n, double scale, cudaStream_t s);
+cudaError_t refine_cast_f64_f32(const double* src, int64_t lds, float* dst, int64_t ldd, int64_t m,
+                                int64_t n, cudaStream_t s);
+cudaError_t refine_residual(const double* b, int64_t ldb, double* r, int64_t ldr, int64_t m,
+                            int64_t n, cudaStream_t s);
+cudaError_t refine_add(double* x, int64_t ldx, const float* d, int64_t ldd, int64_t m, int64_t n,
+                       cudaStream_t s);
+cudaError_t refine_norm_inf(const double* a, int64_t lda, int64_t m, int64_t n, double* sums,
+                            double* out, cudaStream_t s);
+cudaError_t refine_op_norm_inf(const double* a, int64_t lda, int64_t k, bool lower, bool trans,
+                               bool unit, double* sums, double* out, cudaStream_t s);
+
 // K granularity the tensor-core GEMM needs (klen and rk multiples of this).
 constexpr int kTcKQuantum = 64;
 

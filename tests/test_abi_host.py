@@ -123,3 +123,23 @@ def test_binding_rejects_bad_tensors():
         trx.trsm("L", "L", "N", "N", 1.0, A, torch.zeros(4, 3))   # CPU tensors
     with pytest.raises(TypeError):
         trx.trsm("L", "L", "N", "N", 1.0, A, torch.zeros(4, 3, dtype=torch.float64))
+
+
+def test_refined_argument_positions(lib):
+    import ctypes
+
+    def r(side="L", m=4, n=3, A=1, lda=4, B=1, ldb=4, X=1, ldx=4, max_iter=3, tol=1e-12,
+          uplo="L"):
+        return lib.trx_strsm_refined(None, side.encode(), uplo.encode(), b"N", b"N", m, n, 1.0,
+                                     A, lda, B, ldb, X, ldx, max_iter, tol, None, None)
+    # the BLAS positions shifted by one (the handle comes first)
+    assert r(side="X") == -2 and r(uplo="X") == -3 and r(m=-1) == -6 and r(n=-1) == -7
+    assert r(A=None) == -9 and r(lda=3) == -10 and r(B=None) == -11 and r(ldb=3) == -12
+    assert r(X=None) == -13 and r(ldx=3) == -14 and r(max_iter=-1) == -15
+    assert r(tol=-1.0) == -16 and r(tol=float("nan")) == -16
+    assert r() == 1                                            # valid, no handle
+    assert r(m=0, A=None, B=None, X=None, lda=1, ldb=1, ldx=1) == 1
+    info = _binding.RefineInfo(5, 1.0, 1.0, 1.0)
+    lib.trx_strsm_refined(None, b"L", b"L", b"N", b"N", 4, 3, 1.0, 1, 4, 1, 4, 1, 4, 3, 0.0,
+                          ctypes.byref(info), None)
+    assert info.iterations == 5          # untouched when the handle is rejected
