@@ -552,7 +552,8 @@ def run_refined(args):
     from paper_2504_13821_gb300 import inputs
     dev = torch.device("cuda", 0)
     with open(os.path.join(ROOT, "tests", "golden", "condition_scales.json")) as f:
-        entries = [e for e in json.load(f)["entries"] if e["k"] == K_ORDER]
+        entries = [e for e in json.load(f)["entries"] if e["k"] == K_ORDER
+                   and (args.kappa is None or e["target"] == args.kappa)]
     if not entries:
         print(json.dumps({"error": f"no stored condition scales for order {K_ORDER}"}))
         return 1
@@ -583,6 +584,12 @@ def run_refined(args):
         def refined():
             info.update(trx.trsm_refined("L", "L", "N", "N", 1.5, At, Bt, out=X, handle=h)[1])
         ms_ref = timed(refined, args.steps)
+        info_ff, X_ff = dict(info), X.clone()
+        # the same refinement with the residual on the FP64 pipe
+        h.set_option(trx.OPT_RESIDUAL, trx.RESIDUAL_FP64)
+        ms_ref64 = timed(refined, max(1, min(args.steps, 3)))
+        info_64 = dict(info)
+        h.set_option(trx.OPT_RESIDUAL, trx.RESIDUAL_AUTO)
         X32 = Bt.clone()
         ms_32 = timed(lambda: trx.trsm("L", "L", "N", "N", 1.5, At, X32.copy_(Bt), handle=h),
                       args.steps)
@@ -596,12 +603,16 @@ def run_refined(args):
             return float((a - X64).abs().sum(dim=1).max() / X64.abs().sum(dim=1).max())
         rows.append({"kappa_target": e["target"], "kappa_estimate": e["kappa_estimate"],
                      "scale": e["scale"], "ms_refined": ms_ref, "ms_fp32": ms_32,
-                     "ms_fp64": ms_64, "iterations": info["iterations"],
-                     "backward_error": info["backward_error"],
-                     "backward_error_fp32": info["initial_backward_error"],
-                     "diff_vs_fp64_solve": rel(X), "diff_fp32_vs_fp64_solve": rel(X32d)})
+                     "ms_fp64": ms_64, "iterations": info_ff["iterations"],
+                     "backward_error": info_ff["backward_error"],
+                     "backward_error_fp32": info_ff["initial_backward_error"],
+                     "fp64_residual": {"ms_refined": ms_ref64,
+                                       "iterations": info_64["iterations"],
+                                       "backward_error": info_64["backward_error"],
+                                       "diff_vs_fp64_solve": rel(X)},
+                     "diff_vs_fp64_solve": rel(X_ff), "diff_fp32_vs_fp64_solve": rel(X32d)})
         total_ms += ms_ref
-        del At, Bt, X, X32, A64, B64, X64, X32d
+        del At, Bt, X, X_ff, X32, A64, B64, X64, X32d
     line = {
         "metric": "refined FP32 TRSM solves/s", "value": len(rows) / (total_ms * 1e-3),
         "unit": "solves/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
@@ -609,7 +620,8 @@ def run_refined(args):
         "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
         "config": {"workload": f"refined TRSM side L lower, k={k}, {n} right-hand sides, "
                                "alpha 1.5, kappa about 1e2/1e4/1e6, stop at backward error "
-                               "sqrt(k) 2^-53",
+                               "sqrt(k) 2^-53 or when a correction stops lowering it; "
+                               "float-float residual (FP64-pipe residual alongside)",
                    "l2": "factor (k^2 FP32 = 256 MB at k = 8192) larger than L2, no flush"},
         "per_kappa": rows,
     }
@@ -714,6 +726,8 @@ def main(argv=None):
                          "arrivals; refined: FP32 TRSM refined in FP64 (k 8192, 256 "
                          "right-hand sides unless --k/--nrhs say otherwise)")
     ap.add_argument("--count", type=int, default=4096, help="problems (batched workload)")
+    ap.add_argument("--kappa", type=float, default=None,
+                    help="refined workload: only the factor of this target condition number")
     ap.add_argument("--no-autotune", action="store_true",
                     help="batched workload: keep the default block sizes (for profiling runs)")
     args = ap.parse_args(argv)

@@ -88,7 +88,7 @@ enum {
                               programmatic dependent launch, so each one's
                               prologue overlaps the previous one's tail;
                               0 (default): plain stream order              */
-    TRX_OPT_TRMM_DENSE = 8 /* FP32 TRMM on the tensor-core path: leaves of
+    TRX_OPT_TRMM_DENSE = 8,/* FP32 TRMM on the tensor-core path: leaves of
                               this many rows (64 .. 2048, a power of two)
                               formed in one grouped GEMM launch over the
                               diagonal blocks (the block's strictly-lower
@@ -100,6 +100,11 @@ enum {
                               -1 off; 0 = automatic (default: 1024 rows when
                               the order is at least 1024 and TRX_OPT_LEAF
                               is automatic, else off)                     */
+    TRX_OPT_RESIDUAL = 9,  /* residual of trx_strsm_refined: 0 (automatic)
+                              or 2: float-float on the FP32 pipes (pairs of
+                              floats, exact product split and two-sum,
+                              about 2^-46 relative); 1: the library's FP64
+                              TRMM on an FP64 copy of A (FP64 pipe)        */
 };
 
 /* Kernel classes reported by trx_get_profile(). */
@@ -211,23 +216,25 @@ int trx_batched(trx_handle_t handle, int elem_bytes, int64_t count,
                 const trx_problem_t* problems, void* stream);
 
 /* Refined FP32 TRSM (the precision form): the FP32 solve of trx_strsm, then
- * iterative refinement in FP64: R = alpha B - op(A) X with FP64 arithmetic
- * (FP32 data, so every product is exact; the library's own FP64 TRMM on an
- * FP64 copy of A), a correction op(A) D = R (or D op(A) = R) solved in FP32
- * on the same path, X += D in FP64, until the normwise backward error
+ * iterative refinement towards an FP64-accurate X: the residual
+ * R = alpha B - op(A) X with more than FP32 precision (TRX_OPT_RESIDUAL:
+ * float-float on the FP32 pipes by default, or FP64 arithmetic), a
+ * correction op(A) D = R (or D op(A) = R) solved in FP32 on the same
+ * recursive path, X += D in FP64, until the normwise backward error
  * ||R|| / (||op(A)|| ||X||) (infinity norms) is at most tol, max_iter
- * corrections were made, or a correction did not lower it. A (k x k) and B (m x n) are FP32 device arrays as
- * in trx_strsm, B is not modified; X (m x n, FP64, leading dimension ldx) is
- * the result. Synchronous: it reads the residual norm back after every
- * step. Needs the workspace of trx_strsm (trx_workspace_size 'S') and
- * allocates its own FP64 scratch on the handle (8 k^2 + 20 m n bytes,
- * kept for later calls). info (may be NULL): corrections made, the final
- * residual norm and backward error, and the backward error of the plain
- * FP32 solve. Returns -i for an illegal i-th argument of this call (side 2,
- * uplo 3, transa 4, diag 5, m 6, n 7, alpha 8, A 9, lda 10, B 11, ldb 12,
- * X 13, ldx 14, max_iter < 0: 15, tol < 0 or NaN: 16), or a TRX_ERR_*
- * code. (The paper's base solve and GEMM updates are the FP32 steps; the
- * refinement loop around them is this library's.) */
+ * corrections were made, or a correction did not lower it. A (k x k) and
+ * B (m x n) are FP32 device arrays as in trx_strsm, B is not modified;
+ * X (m x n, FP64, leading dimension ldx) is the result. Synchronous: it
+ * reads the residual norm back after every step. Needs the workspace of
+ * trx_strsm (trx_workspace_size 'S') and allocates its own scratch on the
+ * handle (28 m n bytes, plus 8 k^2 for the FP64 residual; kept for later
+ * calls). info (may be NULL): corrections made, the final residual norm
+ * and backward error, and the backward error of the plain FP32 solve.
+ * Returns -i for an illegal i-th argument of this call (side 2, uplo 3,
+ * transa 4, diag 5, m 6, n 7, alpha 8, A 9, lda 10, B 11, ldb 12, X 13,
+ * ldx 14, max_iter < 0: 15, tol < 0 or NaN: 16), or a TRX_ERR_* code. (The
+ * paper's base solve and GEMM updates are the FP32 steps; the refinement
+ * loop around them is this library's.) */
 typedef struct {
     int iterations;                 /* corrections applied                  */
     double residual_norm;           /* ||alpha B - op(A) X||_inf at the end  */

@@ -19,6 +19,8 @@ HEADER = os.path.join(os.path.dirname(_PKG), "include", "trx.h")
 # Option and kernel-class codes (mirrors include/trx.h).
 OPT_LEAF, OPT_GEMM, OPT_GRAPH, OPT_PROFILE, OPT_WAIT_LIMIT, OPT_PDL, OPT_PANELS = 1, 2, 3, 4, 5, 6, 7
 OPT_TRMM_DENSE = 8
+OPT_RESIDUAL = 9
+RESIDUAL_AUTO, RESIDUAL_FP64, RESIDUAL_FLOAT_FLOAT = 0, 1, 2
 GEMM_AUTO, GEMM_SIMT, GEMM_TC = 0, 1, 2
 KERNEL_CLASSES = ("leaf_trsm", "leaf_trmm", "gemm_tc", "gemm_simt", "convert", "other")
 ERR_TIMEOUT = 4
@@ -281,7 +283,8 @@ def trsm_refined(side: str, uplo: str, trans: str, diag: str, alpha: float, A, B
     residual alpha B - op(A) X in FP64, solves for the correction in FP32 on
     the recursive path (Section 3.1) and adds it in FP64. ``tol`` bounds the
     normwise backward error ||R|| / (||op(A)|| ||X||) (infinity norms);
-    by default sqrt(k) * 2**-53. Returns (X, info) with info a dict:
+    by default sqrt(k) * 2**-53. The residual's arithmetic is the handle's
+    OPT_RESIDUAL (float-float on the FP32 pipes unless set to RESIDUAL_FP64). Returns (X, info) with info a dict:
     iterations, residual_norm, backward_error, initial_backward_error.
     """
     import torch

@@ -184,6 +184,7 @@ struct trx_handle_s {
     // column-panel branches of a TRSM: streams and fork/join events
     int64_t opt_panels = 0;
     int64_t opt_trmm_dense = 0;
+    int64_t opt_residual = 0;
     // refined TRSM scratch (grown on demand)
     void* rf_buf = nullptr;
     size_t rf_bytes = 0;
@@ -1017,12 +1018,20 @@ int trx_strsm_refined(trx_handle_t h, char side, char uplo, char transa, char di
     cudaError_t e = cudaSetDevice(h->device);
     if (e != cudaSuccess) return fail_cuda(e, "cudaSetDevice");
     const cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    // Internally always side L: X op(A) = alpha B is op(A)^T X^T = alpha B^T,
+    // so side R works on the transposes with the transpose flag flipped.
     const bool left = upc(side) == 'L';
-    const int64_t k = left ? m : n;
-    // scratch: A64 (k x k), B64 and R64 (m x n, FP64), D32 (m x n), sums, norms
-    const size_t a64 = align256((size_t)k * k * 8), mn64 = align256((size_t)m * n * 8);
-    const size_t mn32 = align256((size_t)m * n * 4), sums = align256((size_t)std::max(m, k) * 8);
-    const size_t need = a64 + 2 * mn64 + mn32 + sums + 256;
+    const int64_t k = left ? m : n, nr = left ? n : m;
+    const bool trans = upc(transa) != 'N';
+    const char transI = (left ? trans : !trans) ? 'T' : 'N';
+    const bool lower = upc(uplo) == 'L', unit = upc(diag) == 'U';
+    const bool fp64_residual = h->opt_residual == 1;
+    // scratch: Xi, B64, R64 (k x nr FP64), D32 (k x nr FP32), row/column
+    // sums, norms, and for the FP64 residual an FP64 copy of A
+    const size_t mn64 = align256((size_t)k * nr * 8), mn32 = align256((size_t)k * nr * 4);
+    const size_t sums = align256((size_t)std::max(k, nr) * 8);
+    const size_t a64 = fp64_residual ? align256((size_t)k * k * 8) : 0;
+    const size_t need = 3 * mn64 + mn32 + sums + 256 + a64;
     if (h->rf_bytes < need) {
         if (h->rf_buf) {
             cudaStreamSynchronize(s);
@@ -1037,40 +1046,56 @@ int trx_strsm_refined(trx_handle_t h, char side, char uplo, char transa, char di
         h->rf_bytes = need;
     }
     char* base = static_cast<char*>(h->rf_buf);
-    double* A64 = reinterpret_cast<double*>(base);
-    double* B64 = reinterpret_cast<double*>(base + a64);
-    double* R64 = reinterpret_cast<double*>(base + a64 + mn64);
-    float* D32 = reinterpret_cast<float*>(base + a64 + 2 * mn64);
-    double* sm = reinterpret_cast<double*>(base + a64 + 2 * mn64 + mn32);
-    double* norms = reinterpret_cast<double*>(base + a64 + 2 * mn64 + mn32 + sums);
-    const bool lower = upc(uplo) == 'L', trans = upc(transa) != 'N', unit = upc(diag) == 'U';
+    double* Xi = reinterpret_cast<double*>(base);
+    double* B64 = reinterpret_cast<double*>(base + mn64);
+    double* R64 = reinterpret_cast<double*>(base + 2 * mn64);
+    float* D32 = reinterpret_cast<float*>(base + 3 * mn64);
+    double* sm = reinterpret_cast<double*>(base + 3 * mn64 + mn32);
+    double* norms = reinterpret_cast<double*>(base + 3 * mn64 + mn32 + sums);
+    double* A64 = fp64_residual ? reinterpret_cast<double*>(base + 3 * mn64 + mn32 + sums + 256)
+                                : nullptr;
+    // infinity norms of the caller's m x n arrays: row sums of the internal
+    // k x nr array for side L, column sums for side R
+    auto norm = [&](const double* a, double* out) {
+        return left ? refine_norm_inf(a, k, k, nr, sm, out, s)
+                    : refine_norm_one(a, k, k, nr, sm, out, s);
+    };
     int rc;
-    // 1. the FP32 solve (the plain path), X := its result in FP64
-    if ((e = cudaMemcpy2DAsync(D32, m * 4, B, ldb * 4, m * 4, n, cudaMemcpyDeviceToDevice, s)) !=
-        cudaSuccess)
-        return fail_cuda(e, "refine copy");
-    if ((rc = execute<float>(h, true, side, uplo, transa, diag, m, n, alpha, A, lda, D32, m,
+    // 1. the FP32 solve (the plain recursive path), Xi := its result in FP64
+    e = left ? cudaMemcpy2DAsync(D32, k * 4, B, ldb * 4, k * 4, nr, cudaMemcpyDeviceToDevice, s)
+             : refine_transpose_f32(B, ldb, D32, k, m, n, s);
+    if (e != cudaSuccess) return fail_cuda(e, "refine copy");
+    if ((rc = execute<float>(h, true, 'L', uplo, transI, diag, k, nr, alpha, A, lda, D32, k,
                              stream)) != TRX_SUCCESS)
         return rc;
-    if ((e = refine_cast_f32_f64(D32, m, X, ldx, m, n, 1.0, s)) != cudaSuccess ||
-        (e = refine_cast_f32_f64(A, lda, A64, k, k, k, 1.0, s)) != cudaSuccess ||
-        (e = refine_cast_f32_f64(B, ldb, B64, m, m, n, (double)alpha, s)) != cudaSuccess ||
-        (e = refine_op_norm_inf(A64, k, k, lower, trans, unit, sm, norms, s)) != cudaSuccess)
+    if ((e = refine_cast_f32_f64(D32, k, Xi, k, k, nr, 1.0, s)) != cudaSuccess ||
+        (e = left ? refine_cast_f32_f64(B, ldb, B64, k, k, nr, (double)alpha, s)
+                  : refine_transpose_f32_f64(B, ldb, B64, k, m, n, (double)alpha, s)) !=
+            cudaSuccess ||
+        (fp64_residual && (e = refine_cast_f32_f64(A, lda, A64, k, k, k, 1.0, s)) != cudaSuccess))
         return fail_cuda(e, "refine setup");
+    // ||op(A)||_inf of the caller's op(A): row sums of op(A) with its own flag
+    e = refine_op_norm_inf(A, lda, k, lower, trans, unit, sm, norms, s);
+    if (e != cudaSuccess) return fail_cuda(e, "refine norm");
     double host[3] = {0, 0, 0};
     double eta0 = 0.0, eta = 0.0, eta_prev = 0.0, rnorm = 0.0;
     int it = 0;
     for (;; ++it) {
-        // 2. R := alpha B - op(A) X in FP64 (products of FP32 data are exact)
-        if ((e = cudaMemcpy2DAsync(R64, m * 8, X, ldx * 8, m * 8, n, cudaMemcpyDeviceToDevice, s)) !=
-            cudaSuccess)
-            return fail_cuda(e, "refine copy");
-        if ((rc = execute<double>(h, false, side, uplo, transa, diag, m, n, 1.0, A64, k, R64, m,
-                                  stream)) != TRX_SUCCESS)
-            return rc;
-        if ((e = refine_residual(B64, m, R64, m, m, n, s)) != cudaSuccess ||
-            (e = refine_norm_inf(R64, m, m, n, sm, norms + 1, s)) != cudaSuccess ||
-            (e = refine_norm_inf(X, ldx, m, n, sm, norms + 2, s)) != cudaSuccess ||
+        // 2. R := alpha B - op(A) X, products of FP32 data exact
+        if (fp64_residual) {
+            if ((e = cudaMemcpyAsync(R64, Xi, (size_t)k * nr * 8, cudaMemcpyDeviceToDevice, s)) !=
+                cudaSuccess)
+                return fail_cuda(e, "refine copy");
+            if ((rc = execute<double>(h, false, 'L', uplo, transI, diag, k, nr, 1.0, A64, k, R64,
+                                      k, stream)) != TRX_SUCCESS)
+                return rc;
+            e = refine_residual(B64, k, R64, k, k, nr, s);
+        } else {
+            e = refine_residual_df(A, lda, k, lower != (transI == 'T'), transI == 'T', unit, Xi, k,
+                                   B64, k, R64, k, nr, s);
+        }
+        if (e != cudaSuccess || (e = norm(R64, norms + 1)) != cudaSuccess ||
+            (e = norm(Xi, norms + 2)) != cudaSuccess ||
             (e = cudaMemcpyAsync(host, norms, 3 * sizeof(double), cudaMemcpyDeviceToHost, s)) !=
                 cudaSuccess ||
             (e = cudaStreamSynchronize(s)) != cudaSuccess)
@@ -1083,14 +1108,18 @@ int trx_strsm_refined(trx_handle_t h, char side, char uplo, char transa, char di
         if (eta <= tol || it >= max_iter || !(eta == eta) || (it > 0 && eta >= eta_prev)) break;
         eta_prev = eta;
         // 3. correction: op(A) D = R solved in FP32, X += D
-        if ((e = refine_cast_f64_f32(R64, m, D32, m, m, n, s)) != cudaSuccess)
+        if ((e = refine_cast_f64_f32(R64, k, D32, k, k, nr, s)) != cudaSuccess)
             return fail_cuda(e, "refine cast");
-        if ((rc = execute<float>(h, true, side, uplo, transa, diag, m, n, 1.0f, A, lda, D32, m,
+        if ((rc = execute<float>(h, true, 'L', uplo, transI, diag, k, nr, 1.0f, A, lda, D32, k,
                                  stream)) != TRX_SUCCESS)
             return rc;
-        if ((e = refine_add(X, ldx, D32, m, m, n, s)) != cudaSuccess)
+        if ((e = refine_add(Xi, k, D32, k, k, nr, s)) != cudaSuccess)
             return fail_cuda(e, "refine update");
     }
+    // 4. the caller's X
+    e = left ? cudaMemcpy2DAsync(X, ldx * 8, Xi, k * 8, k * 8, nr, cudaMemcpyDeviceToDevice, s)
+             : refine_transpose_f64(Xi, k, X, ldx, k, nr, s);
+    if (e != cudaSuccess) return fail_cuda(e, "refine result");
     if (info) *info = trx_refine_info_t{it, rnorm, eta, eta0};
     return TRX_SUCCESS;
 }
@@ -1313,6 +1342,10 @@ int trx_set_option(trx_handle_t h, int option, int64_t value) {
                 return TRX_ERR_INVALID_VALUE;
             h->opt_trmm_dense = value;
             break;
+        case TRX_OPT_RESIDUAL:
+            if (value < 0 || value > 2) return TRX_ERR_INVALID_VALUE;
+            h->opt_residual = value;
+            break;
         default:
             return TRX_ERR_INVALID_VALUE;
     }
@@ -1331,6 +1364,7 @@ int trx_get_option(trx_handle_t h, int option, int64_t* value) {
         case TRX_OPT_PDL: *value = h->opt_pdl; break;
         case TRX_OPT_PANELS: *value = h->opt_panels; break;
         case TRX_OPT_TRMM_DENSE: *value = h->opt_trmm_dense; break;
+        case TRX_OPT_RESIDUAL: *value = h->opt_residual; break;
         default: return TRX_ERR_INVALID_VALUE;
     }
     return TRX_SUCCESS;

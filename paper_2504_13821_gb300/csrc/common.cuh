@@ -152,7 +152,18 @@ cudaError_t refine_add(double* x, int64_t ldx, const float* d, int64_t ldd, int6
                        cudaStream_t s);
 cudaError_t refine_norm_inf(const double* a, int64_t lda, int64_t m, int64_t n, double* sums,
                             double* out, cudaStream_t s);
-cudaError_t refine_op_norm_inf(const double* a, int64_t lda, int64_t k, bool lower, bool trans,
+cudaError_t refine_transpose_f32(const float* src, int64_t lds, float* dst, int64_t ldd,
+                                 int64_t rows, int64_t cols, cudaStream_t s);
+cudaError_t refine_transpose_f32_f64(const float* src, int64_t lds, double* dst, int64_t ldd,
+                                     int64_t rows, int64_t cols, double scale, cudaStream_t s);
+cudaError_t refine_transpose_f64(const double* src, int64_t lds, double* dst, int64_t ldd,
+                                 int64_t rows, int64_t cols, cudaStream_t s);
+cudaError_t refine_residual_df(const float* A, int64_t lda, int64_t k, bool lower, bool trans,
+                               bool unit, const double* X, int64_t ldx, const double* B,
+                               int64_t ldb, double* R, int64_t ldr, int64_t n, cudaStream_t s);
+cudaError_t refine_norm_one(const double* a, int64_t lda, int64_t m, int64_t n, double* sums,
+                            double* out, cudaStream_t s);
+cudaError_t refine_op_norm_inf(const float* a, int64_t lda, int64_t k, bool lower, bool trans,
                                bool unit, double* sums, double* out, cudaStream_t s);
 
 // K granularity the tensor-core GEMM needs (klen and rk multiples of this).

@@ -64,24 +64,33 @@ __global__ void __launch_bounds__(kThreads) row_abs_sum_kernel(const double* a, 
 }
 
 // Row sums of |op(A)| over A's referenced triangle (the unit diagonal counts
-// 1), A k x k column-major: row i of op(A) is row i of A ('N') or column i.
-__global__ void __launch_bounds__(kThreads) op_row_abs_sum_kernel(const double* a, int64_t lda,
-                                                                  int64_t k, int lower, int trans,
-                                                                  int unit, double* sums) {
+// 1), A k x k FP32 column-major. Row i of op(A) is row i of A ('N': one
+// thread per row, neighbouring threads read neighbouring rows) or column i
+// (transposed: one warp per column, reading down it).
+__global__ void __launch_bounds__(kThreads) op_row_abs_sum_kernel(const float* a, int64_t lda,
+                                                                  int64_t k, int lower, int unit,
+                                                                  double* sums) {
     const int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x;
     if (i >= k) return;
-    // entries of row i of op(A): op(A)(i, l) = A(i, l) or A(l, i)
-    const bool eff_lower = (lower != 0) != (trans != 0);   // op(A) lower triangular
-    const int64_t l0 = eff_lower ? 0 : i, l1 = eff_lower ? i + 1 : k;
+    const int64_t l0 = lower ? 0 : i, l1 = lower ? i + 1 : k;
     double s = 0.0;
-    for (int64_t l = l0; l < l1; ++l) {
-        if (l == i) {
-            s += unit ? 1.0 : fabs(a[i + i * lda]);
-            continue;
-        }
-        s += fabs(trans ? a[l + i * lda] : a[i + l * lda]);
-    }
+    for (int64_t l = l0; l < l1; ++l)
+        s += (l == i) ? (unit ? 1.0 : fabs((double)a[i + i * lda])) : fabs((double)a[i + l * lda]);
     sums[i] = s;
+}
+__global__ void __launch_bounds__(kThreads) op_col_abs_sum_kernel(const float* a, int64_t lda,
+                                                                  int64_t k, int lower, int unit,
+                                                                  double* sums) {
+    const int64_t i = ((int64_t)blockIdx.x * kThreads + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (i >= k) return;
+    // column i of A holds rows i..k-1 (lower) or 0..i (upper)
+    const int64_t l0 = lower ? i : 0, l1 = lower ? k : i + 1;
+    double s = 0.0;
+    for (int64_t l = l0 + lane; l < l1; l += 32)
+        s += (l == i) ? (unit ? 1.0 : fabs((double)a[i + i * lda])) : fabs((double)a[l + i * lda]);
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) sums[i] = s;
 }
 
 // out[0] := max(v[0..n-1]) (one block).
@@ -96,6 +105,205 @@ __global__ void __launch_bounds__(kThreads) max_kernel(const double* v, int64_t 
         __syncthreads();
     }
     if (threadIdx.x == 0) out[0] = red[0];
+}
+
+// dst(j, i) := scale * src(i, j) for src rows x cols (32 x 32 tiles through
+// shared memory, both sides coalesced).
+template <typename S, typename D>
+__global__ void __launch_bounds__(256) transpose_kernel(const S* src, int64_t lds, D* dst,
+                                                        int64_t ldd, int64_t rows, int64_t cols,
+                                                        double scale) {
+    __shared__ D tile[32][33];
+    const int64_t i0 = (int64_t)blockIdx.x * 32, j0 = (int64_t)blockIdx.y * 32;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // 32 x 8
+    for (int r = ty; r < 32; r += 8) {
+        const int64_t i = i0 + tx, j = j0 + r;
+        if (i < rows && j < cols) tile[r][tx] = (D)(scale * (double)src[i + j * lds]);
+    }
+    __syncthreads();
+    for (int r = ty; r < 32; r += 8) {
+        const int64_t j = j0 + tx, i = i0 + r;
+        if (i < rows && j < cols) dst[j + i * ldd] = tile[tx][r];
+    }
+}
+
+// Column sums of |M| (m x n): one warp per column.
+__global__ void __launch_bounds__(kThreads) col_abs_sum_kernel(const double* a, int64_t lda,
+                                                               int64_t m, int64_t n,
+                                                               double* sums) {
+    const int64_t j = ((int64_t)blockIdx.x * kThreads + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (j >= n) return;
+    double s = 0.0;
+    for (int64_t i = lane; i < m; i += 32) s += fabs(a[i + j * lda]);
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) sums[j] = s;
+}
+
+// ---- residual in float-float on the FP32 pipes ------------------------------
+// R := B - op(A) X, op(A) k x k triangular (FP32, element (i, l) at
+// A[i + l lda], or A[l + i lda] when TRANS), X k x n FP64, B, R FP64.
+//
+// X is split into xh + xl (two floats, 48 significant bits). Each product
+// a xh is split exactly into p + e with one FMA (e = a xh - p); p joins
+// the running sum hi through the error-free two-sum (hi + p = t + err
+// exactly, Knuth), and err + e + a xl go to a float lo that is folded into
+// an FP64 total every kFold terms. The result keeps about 2^-46 of
+// sum |a x| per output, against 2^-24 for an FP32 dot product, at about six
+// FP32 operations per term on the packed f32x2 pipe instead of one FP64
+// FMA on GB300's far slower FP64 pipe.
+//
+// Tiles of 64 rows x 64 columns, 16 terms of l per stage, 256 threads; a
+// thread owns rows ty + 16 r and column pairs (tx + 32 c, tx + 32 c + 16).
+constexpr int kRM = 64, kRN = 64, kRK = 16, kFold = 4;   // fold every 64 terms
+
+__device__ __forceinline__ uint64_t pk(float a, float b) {
+    uint64_t d;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(d) : "f"(a), "f"(b));
+    return d;
+}
+__device__ __forceinline__ void upk(uint64_t v, float& a, float& b) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+}
+__device__ __forceinline__ uint64_t add2(uint64_t a, uint64_t b) {
+    uint64_t d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ uint64_t sub2(uint64_t a, uint64_t b) {
+    uint64_t d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ uint64_t mul2(uint64_t a, uint64_t b) {
+    uint64_t d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ uint64_t fma2(uint64_t a, uint64_t b, uint64_t c) {
+    uint64_t d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+
+template <bool TRANS>
+__global__ void __launch_bounds__(256) residual_df_kernel(const float* __restrict__ A, int64_t lda,
+                                                          int64_t k, int lower, int unit,
+                                                          const double* __restrict__ X,
+                                                          int64_t ldx, const double* __restrict__ B,
+                                                          int64_t ldb, double* __restrict__ R,
+                                                          int64_t ldr, int64_t n) {
+    __shared__ float As[kRK][kRM + 1];
+    __shared__ float4 Xs[kRK][2 * 16 + 1];   // [l][pair * 16 + tx] = (xh_a, xh_b, xl_a, xl_b)
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    const int64_t nrt = (k + kRM - 1) / kRM, nct = (n + kRN - 1) / kRN;
+    const int64_t rt_raw = blockIdx.x / nct, ct = blockIdx.x % nct;
+    // heaviest row tiles first: the last ones when lower, the first when upper
+    const int64_t rt = lower ? nrt - 1 - rt_raw : rt_raw;
+    const int64_t i0 = rt * kRM, j0 = ct * kRN;
+    const int64_t l_begin = lower ? 0 : i0;
+    const int64_t l_end = lower ? (i0 + kRM < k ? i0 + kRM : k) : k;
+
+    uint64_t hi[4][2], lo[4][2];
+    double tot[4][4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+#pragma unroll
+        for (int c = 0; c < 2; ++c) hi[r][c] = lo[r][c] = 0ull;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) tot[r][c] = 0.0;
+    }
+    int stage = 0;
+    for (int64_t l0 = l_begin; l0 < l_end; l0 += kRK) {
+        // A tile: op(A)(i0 + i, l0 + l), masked to the triangle
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            int i, l;
+            if (TRANS) {
+                l = tid & 15;
+                i = (tid >> 4) + 16 * q;
+            } else {
+                i = tid & 63;
+                l = (tid >> 6) + 4 * q;
+            }
+            const int64_t gi = i0 + i, gl = l0 + l;
+            float v = 0.0f;
+            if (gi < k && gl < k && (lower ? gl <= gi : gl >= gi)) {
+                if (gl == gi && unit) v = 1.0f;
+                else v = TRANS ? A[gl + gi * lda] : A[gi + gl * lda];
+            }
+            As[l][i] = v;
+        }
+        // X tile: rows l0 .. l0 + 15, columns j0 .. j0 + 63, split into floats
+        {
+            const int l = tid & 15, jj = tid >> 4;
+            const int64_t gl = l0 + l;
+#pragma unroll
+            for (int pc = 0; pc < 2; ++pc) {
+                const int64_t ja = j0 + jj + 32 * pc, jb = ja + 16;
+                const double xa = (gl < k && ja < n) ? X[gl + ja * ldx] : 0.0;
+                const double xb = (gl < k && jb < n) ? X[gl + jb * ldx] : 0.0;
+                const float ha = (float)xa, hb = (float)xb;
+                Xs[l][pc * 16 + jj] =
+                    make_float4(ha, hb, (float)(xa - (double)ha), (float)(xb - (double)hb));
+            }
+        }
+        __syncthreads();
+#pragma unroll 4
+        for (int l = 0; l < kRK; ++l) {
+            const float4 x0 = Xs[l][tx], x1 = Xs[l][16 + tx];
+            const uint64_t xh[2] = {pk(x0.x, x0.y), pk(x1.x, x1.y)};
+            const uint64_t xl[2] = {pk(x0.z, x0.w), pk(x1.z, x1.w)};
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                const float a = As[l][ty + 16 * r];
+                const uint64_t a2 = pk(a, a), na2 = pk(-a, -a);
+#pragma unroll
+                for (int c = 0; c < 2; ++c) {
+                    const uint64_t np = mul2(na2, xh[c]);         // -p, p = fl(a xh)
+                    const uint64_t e = fma2(a2, xh[c], np);        // a xh - p, exact
+                    const uint64_t t = sub2(hi[r][c], np);         // hi + p
+                    const uint64_t bp = sub2(t, hi[r][c]);
+                    const uint64_t q = add2(np, bp);               // -(p - bp)
+                    const uint64_t err = sub2(sub2(hi[r][c], sub2(t, bp)), q);
+                    hi[r][c] = t;
+                    lo[r][c] = fma2(a2, xl[c], add2(lo[r][c], add2(err, e)));
+                }
+            }
+        }
+        __syncthreads();
+        if (++stage == kFold) {
+            stage = 0;
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+#pragma unroll
+                for (int c = 0; c < 2; ++c) {
+                    float u, v;
+                    upk(lo[r][c], u, v);
+                    tot[r][2 * c] += (double)u;
+                    tot[r][2 * c + 1] += (double)v;
+                    lo[r][c] = 0ull;
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        const int64_t gi = i0 + ty + 16 * r;
+        if (gi >= k) continue;
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+            float h0, h1, l0f, l1f;
+            upk(hi[r][c], h0, h1);
+            upk(lo[r][c], l0f, l1f);
+            const int64_t ja = j0 + tx + 32 * c, jb = ja + 16;
+            if (ja < n)
+                R[gi + ja * ldr] = B[gi + ja * ldb] - ((double)h0 + (tot[r][2 * c] + (double)l0f));
+            if (jb < n)
+                R[gi + jb * ldr] =
+                    B[gi + jb * ldb] - ((double)h1 + (tot[r][2 * c + 1] + (double)l1f));
+        }
+    }
 }
 
 int grid_for(int64_t count) {
@@ -129,6 +337,50 @@ cudaError_t refine_add(double* x, int64_t ldx, const float* d, int64_t ldd, int6
     add_f32_kernel<<<grid_for(m * n), kThreads, 0, s>>>(x, ldx, d, ldd, m, n);
     return cudaGetLastError();
 }
+template <typename S, typename D>
+cudaError_t launch_transpose(const S* src, int64_t lds, D* dst, int64_t ldd, int64_t rows,
+                             int64_t cols, double scale, cudaStream_t s) {
+    if (rows <= 0 || cols <= 0) return cudaSuccess;
+    const dim3 grid((unsigned)((rows + 31) / 32), (unsigned)((cols + 31) / 32));
+    if (grid.y > 65535) return cudaErrorInvalidValue;
+    transpose_kernel<S, D><<<grid, 256, 0, s>>>(src, lds, dst, ldd, rows, cols, scale);
+    return cudaGetLastError();
+}
+cudaError_t refine_transpose_f32(const float* src, int64_t lds, float* dst, int64_t ldd,
+                                 int64_t rows, int64_t cols, cudaStream_t s) {
+    return launch_transpose<float, float>(src, lds, dst, ldd, rows, cols, 1.0, s);
+}
+cudaError_t refine_transpose_f32_f64(const float* src, int64_t lds, double* dst, int64_t ldd,
+                                     int64_t rows, int64_t cols, double scale, cudaStream_t s) {
+    return launch_transpose<float, double>(src, lds, dst, ldd, rows, cols, scale, s);
+}
+cudaError_t refine_transpose_f64(const double* src, int64_t lds, double* dst, int64_t ldd,
+                                 int64_t rows, int64_t cols, cudaStream_t s) {
+    return launch_transpose<double, double>(src, lds, dst, ldd, rows, cols, 1.0, s);
+}
+cudaError_t refine_residual_df(const float* A, int64_t lda, int64_t k, bool lower, bool trans,
+                               bool unit, const double* X, int64_t ldx, const double* B,
+                               int64_t ldb, double* R, int64_t ldr, int64_t n, cudaStream_t s) {
+    if (k <= 0 || n <= 0) return cudaSuccess;
+    const int64_t blocks = ((k + kRM - 1) / kRM) * ((n + kRN - 1) / kRN);
+    if (blocks > 0x7fffffff) return cudaErrorInvalidValue;
+    if (trans)
+        residual_df_kernel<true><<<(unsigned)blocks, 256, 0, s>>>(A, lda, k, lower, unit, X, ldx,
+                                                                  B, ldb, R, ldr, n);
+    else
+        residual_df_kernel<false><<<(unsigned)blocks, 256, 0, s>>>(A, lda, k, lower, unit, X, ldx,
+                                                                   B, ldb, R, ldr, n);
+    return cudaGetLastError();
+}
+// out[0] := max column sum of |M| (m x n); sums: n doubles of scratch.
+cudaError_t refine_norm_one(const double* a, int64_t lda, int64_t m, int64_t n, double* sums,
+                            double* out, cudaStream_t s) {
+    if (m <= 0 || n <= 0) return cudaMemsetAsync(out, 0, sizeof(double), s);
+    col_abs_sum_kernel<<<(unsigned)((n * 32 + kThreads - 1) / kThreads), kThreads, 0, s>>>(
+        a, lda, m, n, sums);
+    max_kernel<<<1, kThreads, 0, s>>>(sums, n, out);
+    return cudaGetLastError();
+}
 // out[0] := ||M||_inf; sums: m doubles of scratch.
 cudaError_t refine_norm_inf(const double* a, int64_t lda, int64_t m, int64_t n, double* sums,
                             double* out, cudaStream_t s) {
@@ -139,11 +391,15 @@ cudaError_t refine_norm_inf(const double* a, int64_t lda, int64_t m, int64_t n, 
     return cudaGetLastError();
 }
 // out[0] := ||op(A)||_inf over the referenced triangle; sums: k doubles.
-cudaError_t refine_op_norm_inf(const double* a, int64_t lda, int64_t k, bool lower, bool trans,
+cudaError_t refine_op_norm_inf(const float* a, int64_t lda, int64_t k, bool lower, bool trans,
                                bool unit, double* sums, double* out, cudaStream_t s) {
     if (k <= 0) return cudaMemsetAsync(out, 0, sizeof(double), s);
-    op_row_abs_sum_kernel<<<(unsigned)((k + kThreads - 1) / kThreads), kThreads, 0, s>>>(
-        a, lda, k, lower, trans, unit, sums);
+    if (trans)
+        op_col_abs_sum_kernel<<<(unsigned)((k * 32 + kThreads - 1) / kThreads), kThreads, 0, s>>>(
+            a, lda, k, lower, unit, sums);
+    else
+        op_row_abs_sum_kernel<<<(unsigned)((k + kThreads - 1) / kThreads), kThreads, 0, s>>>(
+            a, lda, k, lower, unit, sums);
     max_kernel<<<1, kThreads, 0, s>>>(sums, k, out);
     return cudaGetLastError();
 }

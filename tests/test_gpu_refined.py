@@ -39,8 +39,14 @@ def _scale(k, kappa, uplo, seed):
     return 1.0 if kappa is None else oracle.scale_for_condition(k, kappa, seed=seed, uplo=uplo)
 
 
+def _handle(trx, residual):
+    h = trx.Handle(0)
+    h.set_option(trx.OPT_RESIDUAL, residual)
+    return h
+
+
 def _refined_case(trx, side, uplo, trans, diag, m, n, alpha, kappa, seed, *, ldx_pad=0,
-                  max_iter=30):
+                  max_iter=30, handle=None):
     k = m if side == "L" else n
     s = _scale(k, kappa, uplo, seed)
     A, B = inputs.problem(side, uplo, m, n, seed=seed, dtype=np.float32, scale=s,
@@ -49,7 +55,7 @@ def _refined_case(trx, side, uplo, trans, diag, m, n, alpha, kappa, seed, *, ldx
     B_before = Bt.clone()
     Xt = torch.full((n, m + ldx_pad), SENTINEL, dtype=torch.float64, device="cuda:0").t()
     X, info = trx.trsm_refined(side, uplo, trans, diag, alpha, At, Bt, out=Xt[:m, :],
-                               max_iter=max_iter)
+                               max_iter=max_iter, handle=handle)
     torch.cuda.synchronize()
     assert torch.equal(Bt, B_before), "B modified"
     full = Xt.cpu().numpy()
@@ -59,16 +65,18 @@ def _refined_case(trx, side, uplo, trans, diag, m, n, alpha, kappa, seed, *, ldx
     return A64, B64, Xh, info, At, Bt
 
 
+@pytest.mark.parametrize("residual", [1, 2], ids=["fp64", "float_float"])
 @pytest.mark.parametrize("kappa", [1e2, 1e4, 1e6])
 @pytest.mark.parametrize("side,uplo,trans,diag", [("L", "L", "N", "N"), ("R", "U", "T", "N"),
                                                   ("L", "U", "T", "U"), ("R", "L", "N", "U")])
-def test_refined_reaches_fp64_accuracy(trx, side, uplo, trans, diag, kappa):
+def test_refined_reaches_fp64_accuracy(trx, side, uplo, trans, diag, kappa, residual):
     m, n = (700, 130) if side == "L" else (130, 700)
     k = 700
     alpha = 1.5
     seed = inputs.variant_seed(k, VARIANTS.index((side, uplo, trans, diag)))
+    h = _handle(trx, residual)
     A, B, X, info, At, Bt = _refined_case(trx, side, uplo, trans, diag, m, n, alpha, kappa, seed,
-                                          ldx_pad=3)
+                                          ldx_pad=3, handle=h)
     eta = oracle.trsm_backward_error(side, uplo, trans, diag, alpha, A, X, B)["eta"]
     assert np.isfinite(eta) and eta <= 8 * k * U64, (eta, info)
     X_ref = oracle.trsm(side, uplo, trans, diag, alpha, A, B)
@@ -85,14 +93,17 @@ def test_refined_reaches_fp64_accuracy(trx, side, uplo, trans, diag, kappa):
     assert 1 <= info["iterations"] <= 30
 
 
+@pytest.mark.parametrize("residual", [1, 2], ids=["fp64", "float_float"])
 @pytest.mark.parametrize("side,uplo,trans,diag", VARIANTS)
-def test_refined_all_variants(trx, side, uplo, trans, diag):
+def test_refined_all_variants(trx, side, uplo, trans, diag, residual):
     """Every side/uplo/trans/diag at kappa about 1e4, ragged order 300 over
-    several leaves and one tensor-core update, 257 right-hand sides."""
+    several leaves and one tensor-core update, 257 right-hand sides (ragged
+    64-row and 64-column residual tiles)."""
     m, n = (300, 257) if side == "L" else (257, 300)
     k = 300
     seed = inputs.variant_seed(301, VARIANTS.index((side, uplo, trans, diag)))
-    A, B, X, info, _, _ = _refined_case(trx, side, uplo, trans, diag, m, n, -0.75, 1e4, seed)
+    A, B, X, info, _, _ = _refined_case(trx, side, uplo, trans, diag, m, n, -0.75, 1e4, seed,
+                                        handle=_handle(trx, residual))
     eta = oracle.trsm_backward_error(side, uplo, trans, diag, -0.75, A, X, B)["eta"]
     assert np.isfinite(eta) and eta <= 8 * k * U64, (eta, info)
     assert info["iterations"] >= 1
@@ -108,17 +119,30 @@ def test_refined_is_repeatable(trx):
     assert torch.equal(X1, X2) and i1 == i2
 
 
-def test_refined_max_iter_zero_is_the_fp32_solve(trx):
-    """No corrections: X is the plain FP32 solve, widened to FP64."""
-    A, B = inputs.problem("R", "U", 90, 400, seed=4, dtype=np.float32)
+@pytest.mark.parametrize("residual", [1, 2], ids=["fp64", "float_float"])
+@pytest.mark.parametrize("side,uplo,trans", [("R", "U", "N"), ("L", "L", "T"), ("L", "U", "N"),
+                                             ("R", "L", "T")])
+def test_refined_max_iter_zero_is_the_fp32_solve(trx, side, uplo, trans, residual):
+    """No corrections: X is the plain FP32 solve widened to FP64, and the
+    residual norm the library reports is the oracle's (summed in twice the
+    working precision) to within 2^-40 ||op(A)|| ||X||: the float-float
+    residual's accuracy, measured directly."""
+    m, n = (90, 400) if side == "R" else (400, 90)
+    A, B = inputs.problem(side, uplo, m, n, seed=4, dtype=np.float32, scale=30.0)
     At, Bt = to_dev(A, "cuda:0"), to_dev(B, "cuda:0")
-    X, info = trx.trsm_refined("R", "U", "N", "N", 1.0, At, Bt, max_iter=0)
+    X, info = trx.trsm_refined(side, uplo, trans, "N", 1.25, At, Bt, max_iter=0,
+                               handle=_handle(trx, residual))
     X32 = Bt.clone()
-    trx.trsm("R", "U", "N", "N", 1.0, At, X32)
+    trx.trsm(side, uplo, trans, "N", 1.25, At, X32)
     torch.cuda.synchronize()
     assert info["iterations"] == 0
     assert torch.equal(X, X32.double())
     assert info["backward_error"] == info["initial_backward_error"]
+    ref = oracle.trsm_backward_error(side, uplo, trans, "N", 1.25, A.astype(np.float64),
+                                     np.asfortranarray(X.cpu().numpy()), B.astype(np.float64))
+    scale = ref["norm_a"] * ref["norm_x"]
+    assert abs(info["residual_norm"] - ref["res"]) <= 2.0 ** -40 * scale, (info, ref)
+    assert abs(info["backward_error"] - ref["eta"]) <= 2.0 ** -40
 
 
 def test_refined_degenerate(trx):
@@ -134,7 +158,8 @@ def test_refined_degenerate(trx):
         trx.trsm_refined("L", "L", "N", "N", 1.0, At.double(), Bt)
 
 
-def test_refined_stored_condition_scales(trx):
+@pytest.mark.parametrize("residual", [1, 2], ids=["fp64", "float_float"])
+def test_refined_stored_condition_scales(trx, residual):
     """The refined workload's inputs: order 8192, 256 right-hand sides, the
     stored scales for kappa about 1e2, 1e4, 1e6; forward and backward error
     against the FP64 oracle."""
@@ -147,7 +172,8 @@ def test_refined_stored_condition_scales(trx):
         k, n = e["k"], 256
         A, B = inputs.problem("L", "L", k, n, seed=e["seed"], dtype=np.float32, scale=e["scale"])
         At, Bt = to_dev(A, "cuda:0"), to_dev(B, "cuda:0")
-        X, info = trx.trsm_refined("L", "L", "N", "N", 1.5, At, Bt)
+        X, info = trx.trsm_refined("L", "L", "N", "N", 1.5, At, Bt,
+                                   handle=_handle(trx, residual))
         Xh = np.asfortranarray(X.cpu().numpy())
         A64, B64 = np.asfortranarray(A.astype(np.float64)), np.asfortranarray(B.astype(np.float64))
         eta = oracle.trsm_backward_error("L", "L", "N", "N", 1.5, A64, Xh, B64)["eta"]
