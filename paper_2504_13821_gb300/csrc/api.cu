@@ -1029,7 +1029,7 @@ int trx_strsm_refined(trx_handle_t h, char side, char uplo, char transa, char di
     // scratch: Xi, B64, R64 (k x nr FP64), D32 (k x nr FP32), row/column
     // sums, norms, and for the FP64 residual an FP64 copy of A
     const size_t mn64 = align256((size_t)k * nr * 8), mn32 = align256((size_t)k * nr * 4);
-    const size_t sums = align256((size_t)std::max(k, nr) * 8);
+    const size_t sums = align256(std::max((size_t)std::max(k, nr) * 8, refine_norm_scratch(k)));
     const size_t a64 = fp64_residual ? align256((size_t)k * k * 8) : 0;
     const size_t need = 3 * mn64 + mn32 + sums + 256 + a64;
     if (h->rf_bytes < need) {

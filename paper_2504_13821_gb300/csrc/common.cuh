@@ -163,6 +163,7 @@ cudaError_t refine_residual_df(const float* A, int64_t lda, int64_t k, bool lowe
                                int64_t ldb, double* R, int64_t ldr, int64_t n, cudaStream_t s);
 cudaError_t refine_norm_one(const double* a, int64_t lda, int64_t m, int64_t n, double* sums,
                             double* out, cudaStream_t s);
+size_t refine_norm_scratch(int64_t k);   // bytes refine_op_norm_inf needs at `sums`
 cudaError_t refine_op_norm_inf(const float* a, int64_t lda, int64_t k, bool lower, bool trans,
                                bool unit, double* sums, double* out, cudaStream_t s);
 

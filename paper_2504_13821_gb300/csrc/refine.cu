@@ -67,15 +67,35 @@ __global__ void __launch_bounds__(kThreads) row_abs_sum_kernel(const double* a, 
 // 1), A k x k FP32 column-major. Row i of op(A) is row i of A ('N': one
 // thread per row, neighbouring threads read neighbouring rows) or column i
 // (transposed: one warp per column, reading down it).
-__global__ void __launch_bounds__(kThreads) op_row_abs_sum_kernel(const float* a, int64_t lda,
-                                                                  int64_t k, int lower, int unit,
-                                                                  double* sums) {
+constexpr int kNormSlices = 32;   // l-slices of the row-sum partials
+__global__ void __launch_bounds__(kThreads) op_row_abs_part_kernel(const float* a, int64_t lda,
+                                                                   int64_t k, int lower, int unit,
+                                                                   double* part) {
+    // block: 64 rows x 4 phases of l; blockIdx.y: one of kNormSlices l-slices
+    __shared__ double red[4][64];
+    const int tx = threadIdx.x & 63, ph = threadIdx.x >> 6;
+    const int64_t i = (int64_t)blockIdx.x * 64 + tx;
+    const int64_t slice = (k + kNormSlices - 1) / kNormSlices;
+    const int64_t s0 = blockIdx.y * slice, s1 = s0 + slice < k ? s0 + slice : k;
+    double s = 0.0;
+    if (i < k) {
+        const int64_t l0 = lower ? s0 : (s0 > i ? s0 : i);
+        const int64_t l1 = lower ? (s1 < i + 1 ? s1 : i + 1) : s1;
+        for (int64_t l = l0 + ph; l < l1; l += 4)
+            s += (l == i) ? (unit ? 1.0 : fabs((double)a[i + i * lda]))
+                          : fabs((double)a[i + l * lda]);
+    }
+    red[ph][tx] = s;
+    __syncthreads();
+    if (ph == 0 && i < k)
+        part[blockIdx.y * k + i] = red[0][tx] + red[1][tx] + red[2][tx] + red[3][tx];
+}
+__global__ void __launch_bounds__(kThreads) part_sum_kernel(const double* part, int64_t k,
+                                                            double* sums) {
     const int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x;
     if (i >= k) return;
-    const int64_t l0 = lower ? 0 : i, l1 = lower ? i + 1 : k;
     double s = 0.0;
-    for (int64_t l = l0; l < l1; ++l)
-        s += (l == i) ? (unit ? 1.0 : fabs((double)a[i + i * lda])) : fabs((double)a[i + l * lda]);
+    for (int q = 0; q < kNormSlices; ++q) s += part[q * k + i];
     sums[i] = s;
 }
 __global__ void __launch_bounds__(kThreads) op_col_abs_sum_kernel(const float* a, int64_t lda,
@@ -193,7 +213,7 @@ __global__ void __launch_bounds__(256) residual_df_kernel(const float* __restric
                                                           int64_t ldx, const double* __restrict__ B,
                                                           int64_t ldb, double* __restrict__ R,
                                                           int64_t ldr, int64_t n) {
-    __shared__ float As[kRK][kRM + 1];
+    __shared__ float4 As[kRK][kRM];   // (a, a, -a, -a): both packed operands in one load
     __shared__ float4 Xs[kRK][2 * 16 + 1];   // [l][pair * 16 + tx] = (xh_a, xh_b, xl_a, xl_b)
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
     const int64_t nrt = (k + kRM - 1) / kRM, nct = (n + kRN - 1) / kRN;
@@ -232,7 +252,7 @@ __global__ void __launch_bounds__(256) residual_df_kernel(const float* __restric
                 if (gl == gi && unit) v = 1.0f;
                 else v = TRANS ? A[gl + gi * lda] : A[gi + gl * lda];
             }
-            As[l][i] = v;
+            As[l][i] = make_float4(v, v, -v, -v);
         }
         // X tile: rows l0 .. l0 + 15, columns j0 .. j0 + 63, split into floats
         {
@@ -256,8 +276,8 @@ __global__ void __launch_bounds__(256) residual_df_kernel(const float* __restric
             const uint64_t xl[2] = {pk(x0.z, x0.w), pk(x1.z, x1.w)};
 #pragma unroll
             for (int r = 0; r < 4; ++r) {
-                const float a = As[l][ty + 16 * r];
-                const uint64_t a2 = pk(a, a), na2 = pk(-a, -a);
+                const float4 av = As[l][ty + 16 * r];
+                const uint64_t a2 = pk(av.x, av.y), na2 = pk(av.z, av.w);
 #pragma unroll
                 for (int c = 0; c < 2; ++c) {
                     const uint64_t np = mul2(na2, xh[c]);         // -p, p = fl(a xh)
@@ -390,18 +410,24 @@ cudaError_t refine_norm_inf(const double* a, int64_t lda, int64_t m, int64_t n, 
     max_kernel<<<1, kThreads, 0, s>>>(sums, m, out);
     return cudaGetLastError();
 }
-// out[0] := ||op(A)||_inf over the referenced triangle; sums: k doubles.
+// out[0] := ||op(A)||_inf over the referenced triangle; sums: (kNormSlices +
+// 1) k doubles of scratch.
 cudaError_t refine_op_norm_inf(const float* a, int64_t lda, int64_t k, bool lower, bool trans,
                                bool unit, double* sums, double* out, cudaStream_t s) {
     if (k <= 0) return cudaMemsetAsync(out, 0, sizeof(double), s);
-    if (trans)
+    if (trans) {
         op_col_abs_sum_kernel<<<(unsigned)((k * 32 + kThreads - 1) / kThreads), kThreads, 0, s>>>(
             a, lda, k, lower, unit, sums);
-    else
-        op_row_abs_sum_kernel<<<(unsigned)((k + kThreads - 1) / kThreads), kThreads, 0, s>>>(
-            a, lda, k, lower, unit, sums);
+    } else {
+        double* part = sums + k;
+        op_row_abs_part_kernel<<<dim3((unsigned)((k + 63) / 64), kNormSlices), kThreads, 0, s>>>(
+            a, lda, k, lower, unit, part);
+        part_sum_kernel<<<(unsigned)((k + kThreads - 1) / kThreads), kThreads, 0, s>>>(part, k,
+                                                                                      sums);
+    }
     max_kernel<<<1, kThreads, 0, s>>>(sums, k, out);
     return cudaGetLastError();
 }
+size_t refine_norm_scratch(int64_t k) { return (size_t)(kNormSlices + 1) * (size_t)k * 8; }
 
 }  // namespace trx
