@@ -227,7 +227,7 @@ int trx_batched(trx_handle_t handle, int elem_bytes, int64_t count,
  * X (m x n, FP64, leading dimension ldx) is the result. Synchronous: it
  * reads the residual norm back after every step. Needs the workspace of
  * trx_strsm (trx_workspace_size 'S') and allocates its own scratch on the
- * handle (about 28 m n bytes, plus 8 k^2 for the FP64 residual; kept for later
+ * handle (about 36 m n bytes, plus 8 k^2 for the FP64 residual; kept for later
  * calls). info (may be NULL): corrections made, the final residual norm
  * and backward error, and the backward error of the plain FP32 solve.
  * Returns -i for an illegal i-th argument of this call (side 2, uplo 3,

@@ -1026,12 +1026,12 @@ int trx_strsm_refined(trx_handle_t h, char side, char uplo, char transa, char di
     const char transI = (left ? trans : !trans) ? 'T' : 'N';
     const bool lower = upc(uplo) == 'L', unit = upc(diag) == 'U';
     const bool fp64_residual = h->opt_residual == 1;
-    // scratch: Xi, B64, R64 (k x nr FP64), D32 (k x nr FP32), row/column
-    // sums, norms, and for the FP64 residual an FP64 copy of A
+    // scratch: Xi, B64, R64 (k x nr FP64), D32, Xh, Xl (k x nr FP32),
+    // row/column sums, norms, and for the FP64 residual an FP64 copy of A
     const size_t mn64 = align256((size_t)k * nr * 8), mn32 = align256((size_t)k * nr * 4);
     const size_t sums = align256(std::max((size_t)std::max(k, nr) * 8, refine_norm_scratch(k)));
     const size_t a64 = fp64_residual ? align256((size_t)k * k * 8) : 0;
-    const size_t need = 3 * mn64 + mn32 + sums + 256 + a64;
+    const size_t need = 3 * mn64 + 3 * mn32 + sums + 256 + a64;
     if (h->rf_bytes < need) {
         if (h->rf_buf) {
             cudaStreamSynchronize(s);
@@ -1050,10 +1050,13 @@ int trx_strsm_refined(trx_handle_t h, char side, char uplo, char transa, char di
     double* B64 = reinterpret_cast<double*>(base + mn64);
     double* R64 = reinterpret_cast<double*>(base + 2 * mn64);
     float* D32 = reinterpret_cast<float*>(base + 3 * mn64);
-    double* sm = reinterpret_cast<double*>(base + 3 * mn64 + mn32);
-    double* norms = reinterpret_cast<double*>(base + 3 * mn64 + mn32 + sums);
-    double* A64 = fp64_residual ? reinterpret_cast<double*>(base + 3 * mn64 + mn32 + sums + 256)
-                                : nullptr;
+    float* Xh = reinterpret_cast<float*>(base + 3 * mn64 + mn32);
+    float* Xl = reinterpret_cast<float*>(base + 3 * mn64 + 2 * mn32);
+    double* sm = reinterpret_cast<double*>(base + 3 * mn64 + 3 * mn32);
+    double* norms = reinterpret_cast<double*>(base + 3 * mn64 + 3 * mn32 + sums);
+    double* A64 =
+        fp64_residual ? reinterpret_cast<double*>(base + 3 * mn64 + 3 * mn32 + sums + 256)
+                      : nullptr;
     // infinity norms of the caller's m x n arrays: row sums of the internal
     // k x nr array for side L, column sums for side R
     auto norm = [&](const double* a, double* out) {
@@ -1091,8 +1094,10 @@ int trx_strsm_refined(trx_handle_t h, char side, char uplo, char transa, char di
                 return rc;
             e = refine_residual(B64, k, R64, k, k, nr, s);
         } else {
-            e = refine_residual_df(A, lda, k, lower != (transI == 'T'), transI == 'T', unit, Xi, k,
-                                   B64, k, R64, k, nr, s);
+            e = refine_split(Xi, k, Xh, Xl, k, k, nr, s);
+            if (e == cudaSuccess)
+                e = refine_residual_df(A, lda, k, lower != (transI == 'T'), transI == 'T', unit, Xh,
+                                       Xl, k, B64, k, R64, k, nr, s);
         }
         if (e != cudaSuccess || (e = norm(R64, norms + 1)) != cudaSuccess ||
             (e = norm(Xi, norms + 2)) != cudaSuccess ||

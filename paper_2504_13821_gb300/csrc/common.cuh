@@ -158,9 +158,12 @@ cudaError_t refine_transpose_f32_f64(const float* src, int64_t lds, double* dst,
                                      int64_t rows, int64_t cols, double scale, cudaStream_t s);
 cudaError_t refine_transpose_f64(const double* src, int64_t lds, double* dst, int64_t ldd,
                                  int64_t rows, int64_t cols, cudaStream_t s);
+cudaError_t refine_split(const double* x, int64_t ldx, float* xh, float* xl, int64_t ld,
+                         int64_t m, int64_t n, cudaStream_t s);
 cudaError_t refine_residual_df(const float* A, int64_t lda, int64_t k, bool lower, bool trans,
-                               bool unit, const double* X, int64_t ldx, const double* B,
-                               int64_t ldb, double* R, int64_t ldr, int64_t n, cudaStream_t s);
+                               bool unit, const float* Xh, const float* Xl, int64_t ldx,
+                               const double* B, int64_t ldb, double* R, int64_t ldr, int64_t n,
+                               cudaStream_t s);
 cudaError_t refine_norm_one(const double* a, int64_t lda, int64_t m, int64_t n, double* sums,
                             double* out, cudaStream_t s);
 size_t refine_norm_scratch(int64_t k);   // bytes refine_op_norm_inf needs at `sums`

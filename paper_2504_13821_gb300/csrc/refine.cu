@@ -162,20 +162,23 @@ __global__ void __launch_bounds__(kThreads) col_abs_sum_kernel(const double* a, 
 
 // ---- residual in float-float on the FP32 pipes ------------------------------
 // R := B - op(A) X, op(A) k x k triangular (FP32, element (i, l) at
-// A[i + l lda], or A[l + i lda] when TRANS), X k x n FP64, B, R FP64.
+// A[i + l lda], or A[l + i lda] when TRANS), X k x n given as two FP32
+// planes xh + xl (48 significant bits, split once per step by
+// split_kernel), B, R FP64.
 //
-// X is split into xh + xl (two floats, 48 significant bits). Each product
-// a xh is split exactly into p + e with one FMA (e = a xh - p); p joins
-// the running sum hi through the error-free two-sum (hi + p = t + err
-// exactly, Knuth), and err + e + a xl go to a float lo that is folded into
-// an FP64 total every kFold terms. The result keeps about 2^-46 of
-// sum |a x| per output, against 2^-24 for an FP32 dot product, at about six
-// FP32 operations per term on the packed f32x2 pipe instead of one FP64
-// FMA on GB300's far slower FP64 pipe.
+// Each product a xh is split exactly into p + e with one FMA
+// (e = a xh - p); p joins the running sum hi through the error-free
+// two-sum (hi + p = t + err exactly, Knuth), and err + e + a xl go to a
+// float lo. Every kFold stages lo is moved into a second float pair
+// (mid, lo2) by another two-sum, so no step of the loop touches GB300's
+// slow FP64 pipe; the four floats are added in FP64 once, at the end. The
+// result keeps about 2^-46 of sum |a x| per output, against 2^-24 for an
+// FP32 dot product, at about six FP32 operations per term on the packed
+// f32x2 path.
 //
 // Tiles of 64 rows x 64 columns, 16 terms of l per stage, 256 threads; a
 // thread owns rows ty + 16 r and column pairs (tx + 32 c, tx + 32 c + 16).
-constexpr int kRM = 64, kRN = 64, kRK = 16, kFold = 4;   // fold every 64 terms
+constexpr int kRM = 64, kRN = 64, kRK = 16, kFold = 2;   // fold every 32 terms
 
 __device__ __forceinline__ uint64_t pk(float a, float b) {
     uint64_t d;
@@ -205,15 +208,38 @@ __device__ __forceinline__ uint64_t fma2(uint64_t a, uint64_t b, uint64_t c) {
     asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
     return d;
 }
+// s + b = t + err exactly (two-sum, both lanes); returns err, s := t
+__device__ __forceinline__ uint64_t two_sum2(uint64_t& s, uint64_t b) {
+    const uint64_t t = add2(s, b);
+    const uint64_t bp = sub2(t, s);
+    const uint64_t err = add2(sub2(s, sub2(t, bp)), sub2(b, bp));
+    s = t;
+    return err;
+}
+
+// xh := fl32(x), xl := fl32(x - xh) for a k x n FP64 array
+__global__ void __launch_bounds__(kThreads) split_kernel(const double* x, int64_t ldx, float* xh,
+                                                         float* xl, int64_t ld, int64_t m,
+                                                         int64_t n) {
+    for (int64_t e = (int64_t)blockIdx.x * kThreads + threadIdx.x; e < m * n;
+         e += (int64_t)gridDim.x * kThreads) {
+        const int64_t i = e % m, j = e / m;
+        const double v = x[i + j * ldx];
+        const float h = (float)v;
+        xh[i + j * ld] = h;
+        xl[i + j * ld] = (float)(v - (double)h);
+    }
+}
 
 template <bool TRANS>
 __global__ void __launch_bounds__(256) residual_df_kernel(const float* __restrict__ A, int64_t lda,
                                                           int64_t k, int lower, int unit,
-                                                          const double* __restrict__ X,
+                                                          const float* __restrict__ Xh,
+                                                          const float* __restrict__ Xl,
                                                           int64_t ldx, const double* __restrict__ B,
                                                           int64_t ldb, double* __restrict__ R,
                                                           int64_t ldr, int64_t n) {
-    __shared__ float4 As[kRK][kRM];   // (a, a, -a, -a): both packed operands in one load
+    __shared__ float4 As[kRK][kRM];          // (a, a, -a, -a): both packed operands in one load
     __shared__ float4 Xs[kRK][2 * 16 + 1];   // [l][pair * 16 + tx] = (xh_a, xh_b, xl_a, xl_b)
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
     const int64_t nrt = (k + kRM - 1) / kRM, nct = (n + kRN - 1) / kRN;
@@ -224,15 +250,11 @@ __global__ void __launch_bounds__(256) residual_df_kernel(const float* __restric
     const int64_t l_begin = lower ? 0 : i0;
     const int64_t l_end = lower ? (i0 + kRM < k ? i0 + kRM : k) : k;
 
-    uint64_t hi[4][2], lo[4][2];
-    double tot[4][4];
+    uint64_t hi[4][2], lo[4][2], mid[4][2], lo2[4][2];
 #pragma unroll
-    for (int r = 0; r < 4; ++r) {
+    for (int r = 0; r < 4; ++r)
 #pragma unroll
-        for (int c = 0; c < 2; ++c) hi[r][c] = lo[r][c] = 0ull;
-#pragma unroll
-        for (int c = 0; c < 4; ++c) tot[r][c] = 0.0;
-    }
+        for (int c = 0; c < 2; ++c) hi[r][c] = lo[r][c] = mid[r][c] = lo2[r][c] = 0ull;
     int stage = 0;
     for (int64_t l0 = l_begin; l0 < l_end; l0 += kRK) {
         // A tile: op(A)(i0 + i, l0 + l), masked to the triangle
@@ -254,18 +276,18 @@ __global__ void __launch_bounds__(256) residual_df_kernel(const float* __restric
             }
             As[l][i] = make_float4(v, v, -v, -v);
         }
-        // X tile: rows l0 .. l0 + 15, columns j0 .. j0 + 63, split into floats
+        // X tile: rows l0 .. l0 + 15, columns j0 .. j0 + 63
         {
             const int l = tid & 15, jj = tid >> 4;
             const int64_t gl = l0 + l;
 #pragma unroll
             for (int pc = 0; pc < 2; ++pc) {
                 const int64_t ja = j0 + jj + 32 * pc, jb = ja + 16;
-                const double xa = (gl < k && ja < n) ? X[gl + ja * ldx] : 0.0;
-                const double xb = (gl < k && jb < n) ? X[gl + jb * ldx] : 0.0;
-                const float ha = (float)xa, hb = (float)xb;
-                Xs[l][pc * 16 + jj] =
-                    make_float4(ha, hb, (float)(xa - (double)ha), (float)(xb - (double)hb));
+                const bool va = gl < k && ja < n, vb = gl < k && jb < n;
+                Xs[l][pc * 16 + jj] = make_float4(va ? Xh[gl + ja * ldx] : 0.0f,
+                                                  vb ? Xh[gl + jb * ldx] : 0.0f,
+                                                  va ? Xl[gl + ja * ldx] : 0.0f,
+                                                  vb ? Xl[gl + jb * ldx] : 0.0f);
             }
         }
         __syncthreads();
@@ -295,16 +317,12 @@ __global__ void __launch_bounds__(256) residual_df_kernel(const float* __restric
         if (++stage == kFold) {
             stage = 0;
 #pragma unroll
-            for (int r = 0; r < 4; ++r) {
+            for (int r = 0; r < 4; ++r)
 #pragma unroll
                 for (int c = 0; c < 2; ++c) {
-                    float u, v;
-                    upk(lo[r][c], u, v);
-                    tot[r][2 * c] += (double)u;
-                    tot[r][2 * c + 1] += (double)v;
+                    lo2[r][c] = add2(lo2[r][c], two_sum2(mid[r][c], lo[r][c]));
                     lo[r][c] = 0ull;
                 }
-            }
         }
     }
 #pragma unroll
@@ -313,15 +331,18 @@ __global__ void __launch_bounds__(256) residual_df_kernel(const float* __restric
         if (gi >= k) continue;
 #pragma unroll
         for (int c = 0; c < 2; ++c) {
-            float h0, h1, l0f, l1f;
-            upk(hi[r][c], h0, h1);
-            upk(lo[r][c], l0f, l1f);
-            const int64_t ja = j0 + tx + 32 * c, jb = ja + 16;
-            if (ja < n)
-                R[gi + ja * ldr] = B[gi + ja * ldb] - ((double)h0 + (tot[r][2 * c] + (double)l0f));
-            if (jb < n)
-                R[gi + jb * ldr] =
-                    B[gi + jb * ldb] - ((double)h1 + (tot[r][2 * c + 1] + (double)l1f));
+            float h[2], m[2], s[2], t[2];
+            upk(hi[r][c], h[0], h[1]);
+            upk(mid[r][c], m[0], m[1]);
+            upk(lo[r][c], s[0], s[1]);
+            upk(lo2[r][c], t[0], t[1]);
+#pragma unroll
+            for (int w = 0; w < 2; ++w) {
+                const int64_t j = j0 + tx + 32 * c + 16 * w;
+                if (j < n)
+                    R[gi + j * ldr] = B[gi + j * ldb] -
+                                      ((double)h[w] + ((double)m[w] + ((double)s[w] + (double)t[w])));
+            }
         }
     }
 }
@@ -378,18 +399,25 @@ cudaError_t refine_transpose_f64(const double* src, int64_t lds, double* dst, in
                                  int64_t rows, int64_t cols, cudaStream_t s) {
     return launch_transpose<double, double>(src, lds, dst, ldd, rows, cols, 1.0, s);
 }
+cudaError_t refine_split(const double* x, int64_t ldx, float* xh, float* xl, int64_t ld,
+                         int64_t m, int64_t n, cudaStream_t s) {
+    if (m <= 0 || n <= 0) return cudaSuccess;
+    split_kernel<<<grid_for(m * n), kThreads, 0, s>>>(x, ldx, xh, xl, ld, m, n);
+    return cudaGetLastError();
+}
 cudaError_t refine_residual_df(const float* A, int64_t lda, int64_t k, bool lower, bool trans,
-                               bool unit, const double* X, int64_t ldx, const double* B,
-                               int64_t ldb, double* R, int64_t ldr, int64_t n, cudaStream_t s) {
+                               bool unit, const float* Xh, const float* Xl, int64_t ldx,
+                               const double* B, int64_t ldb, double* R, int64_t ldr, int64_t n,
+                               cudaStream_t s) {
     if (k <= 0 || n <= 0) return cudaSuccess;
     const int64_t blocks = ((k + kRM - 1) / kRM) * ((n + kRN - 1) / kRN);
     if (blocks > 0x7fffffff) return cudaErrorInvalidValue;
     if (trans)
-        residual_df_kernel<true><<<(unsigned)blocks, 256, 0, s>>>(A, lda, k, lower, unit, X, ldx,
-                                                                  B, ldb, R, ldr, n);
+        residual_df_kernel<true><<<(unsigned)blocks, 256, 0, s>>>(A, lda, k, lower, unit, Xh, Xl,
+                                                                  ldx, B, ldb, R, ldr, n);
     else
-        residual_df_kernel<false><<<(unsigned)blocks, 256, 0, s>>>(A, lda, k, lower, unit, X, ldx,
-                                                                   B, ldb, R, ldr, n);
+        residual_df_kernel<false><<<(unsigned)blocks, 256, 0, s>>>(A, lda, k, lower, unit, Xh, Xl,
+                                                                   ldx, B, ldb, R, ldr, n);
     return cudaGetLastError();
 }
 // out[0] := max column sum of |M| (m x n); sums: n doubles of scratch.
