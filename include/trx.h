@@ -309,6 +309,61 @@ int trx_batched_autotune(trx_handle_t handle, int elem_bytes, int64_t count,
                          const trx_problem_t* problems, void* stream,
                          char* json, size_t json_len);
 
+/* ---- serving: continuous batching over resident factors ----------------
+ * (The paper has no serving layer; this drives the entry points above.)
+ * Factors are registered once and stay resident (the caller keeps A alive
+ * until the factor is released and its requests have completed); requests
+ * name a factor, an operation, a side, alpha and a right-hand side B
+ * (device, overwritten by the result, kept alive by the caller until its
+ * request completes). trx_server_submit only queues. Each trx_server_poll
+ * is one scheduling tick: retire launch groups whose completion event has
+ * fired, admit queued requests oldest first while the in-flight request
+ * count and the device-memory budget allow (B's bytes, plus 4 k (k + nrhs)
+ * for an FP32 call on the tensor-core path; a request larger than the
+ * budget is admitted alone on an idle server), launch the admitted ones —
+ * orders up to small_k as one persistent trx_batched launch per element
+ * type on the server's batch stream, the rest one trx_?trsm / trx_?trmm
+ * each, round-robin over `streams` streams with one handle and workspace
+ * per stream — and report up to `capacity` completed requests with their
+ * status (0 or a TRX_ERR_* code). A request's launch waits for an event
+ * recorded on input_stream at submission, so B may still be in flight
+ * there. The plan a request gets depends only on its own problem, so its
+ * result is bitwise the same alone and in a mix. One thread at a time. */
+typedef struct trx_server_s* trx_server_t;
+typedef struct {
+    int streams;            /* streams (and handles) for large requests, 1..16 (4)  */
+    int small_k;            /* orders up to this go to trx_batched, 0..512 (512)    */
+    int64_t max_inflight;   /* requests admitted and not yet completed (4096)       */
+    size_t budget_bytes;    /* device bytes admitted requests may hold (150 GiB)    */
+} trx_server_config_t;
+/* config NULL: the defaults in brackets above. */
+int trx_server_create(int device, const trx_server_config_t* config, trx_server_t* server);
+/* Synchronises the server's streams, then frees it (queued requests are
+ * dropped unlaunched). */
+int trx_server_destroy(trx_server_t server);
+/* -i for an illegal i-th argument (uplo 2, transa 3, diag 4, k 5,
+ * elem_bytes 6, A 7, lda 8, factor_id 9). */
+int trx_server_register_factor(trx_server_t server, char uplo, char transa, char diag, int64_t k,
+                               int elem_bytes, const void* A, int64_t lda, int* factor_id);
+/* No new requests for the factor; it is dropped once its last request has
+ * completed. */
+int trx_server_release_factor(trx_server_t server, int factor_id);
+/* op 'S' (TRSM) or 'M' (TRMM); B is m x n with k = m (side 'L') or n ('R').
+ * -i for an illegal i-th argument (factor_id 2, op 3, side 4, B 6, m 7,
+ * n 8, ldb 9, request_id 11). */
+int trx_server_submit(trx_server_t server, int factor_id, char op, char side, double alpha,
+                      void* B, int64_t m, int64_t n, int64_t ldb, void* input_stream,
+                      int64_t* request_id);
+/* One tick (above). Returns 0, or the first error of this tick (the
+ * requests it concerns complete with that status). */
+int trx_server_poll(trx_server_t server, int64_t* request_ids, int* status, int capacity,
+                    int* count);
+/* Requests queued, in flight, and completed but not yet reported. */
+int trx_server_pending(trx_server_t server, int64_t* waiting, int64_t* inflight,
+                       int64_t* unreported);
+/* Block until the oldest launch group in flight has finished. */
+int trx_server_wait(trx_server_t server);
+
 /* Set / read an option (TRX_OPT_*). Unknown options or values return
  * TRX_ERR_INVALID_VALUE. */
 int trx_set_option(trx_handle_t handle, int option, int64_t value);

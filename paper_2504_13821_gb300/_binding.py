@@ -58,6 +58,12 @@ class RefineInfo(ctypes.Structure):
                 ("initial_backward_error", ctypes.c_double)]
 
 
+class ServerConfig(ctypes.Structure):
+    """trx_server_config_t."""
+    _fields_ = [("streams", ctypes.c_int), ("small_k", ctypes.c_int),
+                ("max_inflight", ctypes.c_int64), ("budget_bytes", ctypes.c_size_t)]
+
+
 class _Profile(ctypes.Structure):
     _fields_ = [("ms", ctypes.c_double * 6), ("flops", ctypes.c_double * 6),
                 ("bytes", ctypes.c_double * 6), ("launches", ctypes.c_int64 * 6)]
@@ -111,6 +117,19 @@ def load_library() -> ctypes.CDLL:
         lib.trx_strsm_refined.argtypes = [vp, c, c, c, c, i64, i64, ctypes.c_float, vp, i64, vp,
                                           i64, vp, i64, ctypes.c_int, ctypes.c_double,
                                           ctypes.POINTER(RefineInfo), vp]
+        lib.trx_server_create.argtypes = [ctypes.c_int, ctypes.POINTER(ServerConfig),
+                                          ctypes.POINTER(vp)]
+        lib.trx_server_destroy.argtypes = [vp]
+        lib.trx_server_register_factor.argtypes = [vp, c, c, c, i64, ctypes.c_int, vp, i64,
+                                                   ctypes.POINTER(ctypes.c_int)]
+        lib.trx_server_release_factor.argtypes = [vp, ctypes.c_int]
+        lib.trx_server_submit.argtypes = [vp, ctypes.c_int, c, c, ctypes.c_double, vp, i64, i64,
+                                          i64, vp, ctypes.POINTER(i64)]
+        lib.trx_server_poll.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(ctypes.c_int),
+                                        ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
+        lib.trx_server_pending.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(i64),
+                                           ctypes.POINTER(i64)]
+        lib.trx_server_wait.argtypes = [vp]
         lib.trx_version.argtypes = []
         _lib = lib
         return lib

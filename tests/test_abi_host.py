@@ -143,3 +143,37 @@ def test_refined_argument_positions(lib):
     lib.trx_strsm_refined(None, b"L", b"L", b"N", b"N", 4, 3, 1.0, 1, 4, 1, 4, 1, 4, 3, 0.0,
                           ctypes.byref(info), None)
     assert info.iterations == 5          # untouched when the handle is rejected
+
+
+def test_server_calls_reject_bad_arguments(lib):
+    import ctypes
+    fid = ctypes.c_int(-7)
+    r = lib.trx_server_register_factor
+    assert r(None, b"X", b"N", b"N", 4, 4, 1, 4, ctypes.byref(fid)) == -2
+    assert r(None, b"L", b"X", b"N", 4, 4, 1, 4, ctypes.byref(fid)) == -3
+    assert r(None, b"L", b"N", b"X", 4, 4, 1, 4, ctypes.byref(fid)) == -4
+    assert r(None, b"L", b"N", b"N", -1, 4, 1, 4, ctypes.byref(fid)) == -5
+    assert r(None, b"L", b"N", b"N", 4, 2, 1, 4, ctypes.byref(fid)) == -6
+    assert r(None, b"L", b"N", b"N", 4, 4, None, 4, ctypes.byref(fid)) == -7
+    assert r(None, b"L", b"N", b"N", 4, 4, 1, 3, ctypes.byref(fid)) == -8
+    assert r(None, b"L", b"N", b"N", 4, 4, 1, 4, None) == -9
+    assert r(None, b"L", b"N", b"N", 4, 4, 1, 4, ctypes.byref(fid)) == 1     # TRX_ERR_HANDLE
+    assert fid.value == -7
+    rid = ctypes.c_int64()
+    assert lib.trx_server_submit(None, 0, b"S", b"L", 1.0, 1, 4, 4, 4, None,
+                                 ctypes.byref(rid)) == 1
+    cnt = ctypes.c_int()
+    assert lib.trx_server_poll(None, None, None, 0, ctypes.byref(cnt)) == 1
+    assert lib.trx_server_pending(None, None, None, None) == 1
+    assert lib.trx_server_wait(None) == 1
+    assert lib.trx_server_release_factor(None, 0) == 1
+    assert lib.trx_server_destroy(None) == 0
+
+
+@pytest.mark.skipif(torch.cuda.is_available(), reason="host without a GPU only")
+def test_server_create_fails_cleanly_without_gpu(lib):
+    import ctypes
+    s = ctypes.c_void_p(1)
+    assert lib.trx_server_create(0, None, ctypes.byref(s)) != 0 and not s.value
+    cfg = _binding.ServerConfig(0, 512, 16, 1 << 20)            # zero streams
+    assert lib.trx_server_create(0, ctypes.byref(cfg), ctypes.byref(s)) == 7

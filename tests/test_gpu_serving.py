@@ -1,6 +1,7 @@
-"""Serving loop: requests of mixed sizes, element types and operations
-arrive while others are on the GPU and are admitted as budget and slots
-free up (small ones batched per tick, large ones on parallel streams).
+"""Request server (trx_server_*): requests of mixed sizes, element types
+and operations arrive while others are on the GPU and are admitted as budget
+and slots free up (small ones batched per tick, large ones on parallel
+streams).
 Every result must match the FP64 oracle within 8 k u, and be bit-identical
 to the same request served alone."""
 import time
@@ -40,28 +41,31 @@ def build(server, dev, seed):
 
 
 def serve(reqs, facs, dev, spread_s):
+    """Submit the requests spread over spread_s seconds, polling the
+    server between arrivals, then drain it."""
     from paper_2504_13821_gb300 import serving
     srv = serving.Server(0, streams=3, budget_bytes=1 << 30, max_inflight=64)
     ids = [srv.register(to_dev(A, dev), u, t, d) for (_, A, u, t, d, _) in facs]
     t0 = time.perf_counter()
-    out = []
+    outs, status = [], {}
     for i, (fi, op, side, alpha, B) in enumerate(reqs):
         Bt = to_dev(B, dev)
-        req = serving.Request(i, ids[fi], op, side, alpha, Bt, t0 + spread_s * i / len(reqs))
-        srv.submit(req)
-        out.append(req)
-    srv.drain()
+        while time.perf_counter() < t0 + spread_s * i / len(reqs):
+            status.update(srv.poll())
+        rid = srv.submit(ids[fi], op, side, alpha, Bt)
+        outs.append((rid, Bt))
+    status.update(srv.drain())
     torch.cuda.synchronize()
-    stats = serving.latency_stats(srv.completed)
     srv.close()
-    return [r.B.cpu().numpy() for r in out], stats
+    assert sorted(status) == sorted(r for r, _ in outs)
+    assert all(v == 0 for v in status.values()), status
+    return [Bt.cpu().numpy() for _, Bt in outs]
 
 
 def test_serving_mix_matches_oracle_and_solo():
     dev = torch.device("cuda", 0)
     facs, reqs = build(None, dev, seed=3)
-    mixed, stats = serve(reqs, facs, dev, spread_s=0.05)
-    assert stats["count"] == len(reqs) and stats["p99_ms"] >= stats["p50_ms"] > 0
+    mixed = serve(reqs, facs, dev, spread_s=0.05)
     for i, (fi, op, side, alpha, B) in enumerate(reqs):
         _, A, uplo, trans, diag, dtype = facs[fi]
         X = np.asfortranarray(mixed[i])
@@ -72,5 +76,31 @@ def test_serving_mix_matches_oracle_and_solo():
                                   oracle.trmm(side, uplo, trans, diag, alpha, A, B), B)
         assert e <= bound(A.shape[0], dtype), (i, op, side, A.shape[0], e)
     for i in range(0, len(reqs), 9):                   # a sample served alone
-        solo, _ = serve([reqs[i]], facs, dev, spread_s=0.0)
+        solo = serve([reqs[i]], facs, dev, spread_s=0.0)
         assert np.array_equal(solo[0], mixed[i]), f"request {i} differs alone vs in the mix"
+
+
+def test_server_budget_and_release():
+    """A budget that fits one request at a time still serves every request
+    (one admitted per tick, the oversized one alone), and a released
+    factor takes no new requests."""
+    from paper_2504_13821_gb300 import serving
+    dev = torch.device("cuda", 0)
+    A = inputs.tri_matrix(600, "L", seed=8, dtype=np.float32)
+    srv = serving.Server(0, streams=2, budget_bytes=600 * 40 * 4, max_inflight=8)
+    fid = srv.register(to_dev(A, dev), "L")
+    Bs = [to_dev(inputs.rhs(600, n, seed=n, dtype=np.float32), dev) for n in (40, 30, 90)]
+    rids = [srv.submit(fid, "S", "L", 1.0, B) for B in Bs]
+    srv.release(fid)
+    with pytest.raises(Exception):
+        srv.submit(fid, "S", "L", 1.0, Bs[0].clone())
+    got = dict(srv.drain())
+    torch.cuda.synchronize()
+    assert sorted(got) == sorted(rids) and not any(got.values())
+    assert srv.pending() == (0, 0, 0)
+    for n, B in zip((40, 30, 90), Bs):
+        B0 = inputs.rhs(600, n, seed=n, dtype=np.float32)
+        X = np.asfortranarray(B.cpu().numpy())
+        e = oracle.trsm_backward_error("L", "L", "N", "N", 1.0, A, X, B0)["eta"]
+        assert e <= bound(600, np.float32)
+    srv.close()
