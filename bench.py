@@ -636,9 +636,17 @@ def latency_stats(arrival: dict, done: dict) -> dict:
         return {"count": 0}
     lat = np.array([(done[r] - arrival[r]) * 1e3 for r in done])
     span = max(done.values()) - min(arrival[r] for r in done)
+    # the largest latency among the requests arriving in each second
+    t0 = min(arrival[r] for r in done)
+    per_s = {}
+    for r in done:
+        b = int(arrival[r] - t0)
+        per_s[b] = max(per_s.get(b, 0.0), (done[r] - arrival[r]) * 1e3)
     return {"count": len(done), "p50_ms": float(np.percentile(lat, 50)),
-            "p99_ms": float(np.percentile(lat, 99)), "mean_ms": float(lat.mean()),
-            "solves_per_s": len(done) / span if span > 0 else None}
+            "p90_ms": float(np.percentile(lat, 90)), "p99_ms": float(np.percentile(lat, 99)),
+            "max_ms": float(lat.max()), "mean_ms": float(lat.mean()),
+            "solves_per_s": len(done) / span if span > 0 else None,
+            "max_ms_by_arrival_second": [round(per_s[b], 2) for b in sorted(per_s)]}
 
 
 def run_serving(args):
@@ -654,7 +662,11 @@ def run_serving(args):
     from paper_2504_13821_gb300 import serving
     dev = torch.device("cuda", 0)
     rng = np.random.default_rng(5)
-    srv = serving.Server(0, streams=4, budget_bytes=150 << 30, max_inflight=4096)
+    # per-stream workspace for the largest FP32 call of the mix (order 8192,
+    # 1024 right-hand sides: BF16 operand planes of about 0.3 GB), made up
+    # front so no request waits for a workspace to grow
+    srv = serving.Server(0, streams=4, budget_bytes=150 << 30, max_inflight=4096,
+                         workspace_bytes=args.server_workspace_mb << 20)
     arrival, done, failed = {}, {}, []
 
     def collect(items):
@@ -715,7 +727,8 @@ def run_serving(args):
             "config": {"workload": f"Poisson {args.rate}/s for {args.duration} s, 70% TRSM, "
                                    "m log-uniform 64..8192, nrhs log-uniform 1..1024, "
                                    f"{args.fp64_share:.0%} FP64 (rest FP32), factors reused "
-                                   "1..50 times, 150 GB admission cap, native request server",
+                                   "1..50 times, 150 GB admission cap, native request server, "
+                                   f"{args.server_workspace_mb} MB workspace per stream",
                        "requests": submitted, "offered_tflops": flops / args.duration / 1e12,
                        "failed": len(failed)},
             "latency": st}
@@ -752,6 +765,8 @@ def main(argv=None):
                          "arrivals; refined: FP32 TRSM refined in FP64 (k 8192, 256 "
                          "right-hand sides unless --k/--nrhs say otherwise)")
     ap.add_argument("--count", type=int, default=4096, help="problems (batched workload)")
+    ap.add_argument("--server-workspace-mb", type=int, default=512,
+                    help="serving: per-stream workspace made when the server starts")
     ap.add_argument("--kappa", type=float, default=None,
                     help="refined workload: only the factor of this target condition number")
     ap.add_argument("--no-autotune", action="store_true",

@@ -335,6 +335,8 @@ typedef struct {
     int small_k;            /* orders up to this go to trx_batched, 0..512 (512)    */
     int64_t max_inflight;   /* requests admitted and not yet completed (4096)       */
     size_t budget_bytes;    /* device bytes admitted requests may hold (150 GiB)    */
+    size_t workspace_bytes; /* per-stream workspace made at creation (0); a larger
+                               need grows it, which synchronises the device      */
 } trx_server_config_t;
 /* config NULL: the defaults in brackets above. */
 int trx_server_create(int device, const trx_server_config_t* config, trx_server_t* server);

@@ -61,7 +61,8 @@ class RefineInfo(ctypes.Structure):
 class ServerConfig(ctypes.Structure):
     """trx_server_config_t."""
     _fields_ = [("streams", ctypes.c_int), ("small_k", ctypes.c_int),
-                ("max_inflight", ctypes.c_int64), ("budget_bytes", ctypes.c_size_t)]
+                ("max_inflight", ctypes.c_int64), ("budget_bytes", ctypes.c_size_t),
+                ("workspace_bytes", ctypes.c_size_t)]
 
 
 class _Profile(ctypes.Structure):

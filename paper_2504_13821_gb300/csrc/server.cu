@@ -268,6 +268,7 @@ int trx_server_create(int device, const trx_server_config_t* config, trx_server_
     cfg.small_k = TRX_BATCH_MAX_K;
     cfg.max_inflight = 4096;
     cfg.budget_bytes = (size_t)150 << 30;
+    cfg.workspace_bytes = 0;
     if (config) cfg = *config;
     if (cfg.streams < 1 || cfg.streams > 16 || cfg.small_k < 0 ||
         cfg.small_k > TRX_BATCH_MAX_K || cfg.max_inflight < 1)
@@ -298,6 +299,9 @@ int trx_server_create(int device, const trx_server_config_t* config, trx_server_
         else
             rc = trx_create(&s->bhandle, device, 0);
     }
+    for (int i = 0; i < (int)s->handles.size() && rc == TRX_SUCCESS && cfg.workspace_bytes > 0;
+         ++i)
+        rc = ensure_ws(s, i, cfg.workspace_bytes);
     if (rc != TRX_SUCCESS) {
         trx_server_destroy(s);
         return rc;
