@@ -666,7 +666,8 @@ def run_serving(args):
     # 1024 right-hand sides: BF16 operand planes of about 0.3 GB), made up
     # front so no request waits for a workspace to grow
     srv = serving.Server(0, streams=4, budget_bytes=150 << 30, max_inflight=4096,
-                         workspace_bytes=args.server_workspace_mb << 20)
+                         workspace_bytes=args.server_workspace_mb << 20,
+                         graphs=not args.server_direct)
     arrival, done, failed = {}, {}, []
 
     def collect(items):
@@ -728,7 +729,9 @@ def run_serving(args):
                                    "m log-uniform 64..8192, nrhs log-uniform 1..1024, "
                                    f"{args.fp64_share:.0%} FP64 (rest FP32), factors reused "
                                    "1..50 times, 150 GB admission cap, native request server, "
-                                   f"{args.server_workspace_mb} MB workspace per stream",
+                                   f"{args.server_workspace_mb} MB workspace per stream, "
+                                   + ("direct launches" if args.server_direct else
+                                      "cached graphs"),
                        "requests": submitted, "offered_tflops": flops / args.duration / 1e12,
                        "failed": len(failed)},
             "latency": st}
@@ -765,6 +768,8 @@ def main(argv=None):
                          "arrivals; refined: FP32 TRSM refined in FP64 (k 8192, 256 "
                          "right-hand sides unless --k/--nrhs say otherwise)")
     ap.add_argument("--count", type=int, default=4096, help="problems (batched workload)")
+    ap.add_argument("--server-direct", action="store_true",
+                    help="serving: large requests launch directly instead of replaying graphs")
     ap.add_argument("--server-workspace-mb", type=int, default=512,
                     help="serving: per-stream workspace made when the server starts")
     ap.add_argument("--kappa", type=float, default=None,

@@ -337,6 +337,9 @@ typedef struct {
     size_t budget_bytes;    /* device bytes admitted requests may hold (150 GiB)    */
     size_t workspace_bytes; /* per-stream workspace made at creation (0); a larger
                                need grows it, which synchronises the device      */
+    int graphs;             /* 1: large requests replay cached CUDA graphs (one
+                               capture per new problem shape); 0: direct
+                               launches (1)                                      */
 } trx_server_config_t;
 /* config NULL: the defaults in brackets above. */
 int trx_server_create(int device, const trx_server_config_t* config, trx_server_t* server);

@@ -62,7 +62,7 @@ class ServerConfig(ctypes.Structure):
     """trx_server_config_t."""
     _fields_ = [("streams", ctypes.c_int), ("small_k", ctypes.c_int),
                 ("max_inflight", ctypes.c_int64), ("budget_bytes", ctypes.c_size_t),
-                ("workspace_bytes", ctypes.c_size_t)]
+                ("workspace_bytes", ctypes.c_size_t), ("graphs", ctypes.c_int)]
 
 
 class _Profile(ctypes.Structure):

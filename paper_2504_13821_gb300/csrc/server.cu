@@ -269,9 +269,11 @@ int trx_server_create(int device, const trx_server_config_t* config, trx_server_
     cfg.max_inflight = 4096;
     cfg.budget_bytes = (size_t)150 << 30;
     cfg.workspace_bytes = 0;
+    cfg.graphs = 1;
     if (config) cfg = *config;
     if (cfg.streams < 1 || cfg.streams > 16 || cfg.small_k < 0 ||
-        cfg.small_k > TRX_BATCH_MAX_K || cfg.max_inflight < 1)
+        cfg.small_k > TRX_BATCH_MAX_K || cfg.max_inflight < 1 ||
+        (cfg.graphs != 0 && cfg.graphs != 1))
         return TRX_ERR_INVALID_VALUE;
     cudaError_t e = cudaSetDevice(device);
     if (e != cudaSuccess) return fail(e, "cudaSetDevice");
@@ -290,6 +292,7 @@ int trx_server_create(int device, const trx_server_config_t* config, trx_server_
         s->streams.push_back(st);
         if ((rc = trx_create(&h, device, 0)) != TRX_SUCCESS) break;
         s->handles.push_back(h);
+        if ((rc = trx_set_option(h, TRX_OPT_GRAPH, cfg.graphs)) != TRX_SUCCESS) break;
         s->ws.push_back(nullptr);
         s->ws_bytes.push_back(0);
     }

@@ -19,14 +19,15 @@ class Server:
     """trx_server_t over torch tensors (column-major CUDA views)."""
 
     def __init__(self, device=0, streams: int = 4, budget_bytes: int = 150 << 30,
-                 max_inflight: int = 4096, small_k: int = 512, workspace_bytes: int = 0):
+                 max_inflight: int = 4096, small_k: int = 512, workspace_bytes: int = 0,
+                 graphs: bool = True):
         import torch
         self.torch = torch
         self.device = torch.device("cuda", device if isinstance(device, int) else
                                    torch.device(device).index or 0)
         lib = _binding.load_library()
         cfg = _binding.ServerConfig(streams, small_k, max_inflight, budget_bytes,
-                                    workspace_bytes)
+                                    workspace_bytes, int(graphs))
         h = ctypes.c_void_p()
         _binding._check(lib.trx_server_create(self.device.index, ctypes.byref(cfg),
                                               ctypes.byref(h)), "trx_server_create")

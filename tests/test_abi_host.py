@@ -175,5 +175,5 @@ def test_server_create_fails_cleanly_without_gpu(lib):
     import ctypes
     s = ctypes.c_void_p(1)
     assert lib.trx_server_create(0, None, ctypes.byref(s)) != 0 and not s.value
-    cfg = _binding.ServerConfig(0, 512, 16, 1 << 20, 0)         # zero streams
+    cfg = _binding.ServerConfig(0, 512, 16, 1 << 20, 0, 1)      # zero streams
     assert lib.trx_server_create(0, ctypes.byref(cfg), ctypes.byref(s)) == 7

@@ -40,11 +40,11 @@ def build(server, dev, seed):
     return facs, reqs
 
 
-def serve(reqs, facs, dev, spread_s):
+def serve(reqs, facs, dev, spread_s, graphs=True):
     """Submit the requests spread over spread_s seconds, polling the
     server between arrivals, then drain it."""
     from paper_2504_13821_gb300 import serving
-    srv = serving.Server(0, streams=3, budget_bytes=1 << 30, max_inflight=64)
+    srv = serving.Server(0, streams=3, budget_bytes=1 << 30, max_inflight=64, graphs=graphs)
     ids = [srv.register(to_dev(A, dev), u, t, d) for (_, A, u, t, d, _) in facs]
     t0 = time.perf_counter()
     outs, status = [], {}
@@ -62,10 +62,11 @@ def serve(reqs, facs, dev, spread_s):
     return [Bt.cpu().numpy() for _, Bt in outs]
 
 
-def test_serving_mix_matches_oracle_and_solo():
+@pytest.mark.parametrize("graphs", [True, False], ids=["graphs", "direct"])
+def test_serving_mix_matches_oracle_and_solo(graphs):
     dev = torch.device("cuda", 0)
     facs, reqs = build(None, dev, seed=3)
-    mixed = serve(reqs, facs, dev, spread_s=0.05)
+    mixed = serve(reqs, facs, dev, spread_s=0.05, graphs=graphs)
     for i, (fi, op, side, alpha, B) in enumerate(reqs):
         _, A, uplo, trans, diag, dtype = facs[fi]
         X = np.asfortranarray(mixed[i])
@@ -76,7 +77,7 @@ def test_serving_mix_matches_oracle_and_solo():
                                   oracle.trmm(side, uplo, trans, diag, alpha, A, B), B)
         assert e <= bound(A.shape[0], dtype), (i, op, side, A.shape[0], e)
     for i in range(0, len(reqs), 9):                   # a sample served alone
-        solo = serve([reqs[i]], facs, dev, spread_s=0.0)
+        solo = serve([reqs[i]], facs, dev, spread_s=0.0, graphs=graphs)
         assert np.array_equal(solo[0], mixed[i]), f"request {i} differs alone vs in the mix"
 
 
