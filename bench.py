@@ -676,6 +676,23 @@ def run_serving(args):
             done[rid] = now
             if st != 0:
                 failed.append((rid, st))
+    # warm-up before the arrivals start: one small and one large factor per
+    # precision, TRSM and TRMM with few and many right-hand sides, so module
+    # loading and first-use setup are not charged to the first requests
+    warm = []
+    for dtype in (torch.float32, torch.float64):
+        for k in (256, 8192):
+            A = torch.eye(k, device=dev, dtype=dtype)
+            fid = srv.register(A, "L")
+            for nrhs in (1, 1024):
+                for op in ("S", "M"):
+                    warm.append(srv.submit(fid, op, "L", 1.0,
+                                           torch.ones(nrhs, k, device=dev, dtype=dtype).t()))
+            srv.release(fid)
+            del A
+    warm_status = dict(srv.drain())
+    if sorted(warm_status) != sorted(warm) or any(warm_status.values()):
+        raise RuntimeError(f"serving warm-up failed: {warm_status}")
     t_start = time.perf_counter() + 0.5
     t_arr = t_start
     live = {}             # factor id -> [A, uses left, dtype, k, uplo]
