@@ -1080,12 +1080,14 @@ int trx_strsm_refined(trx_handle_t h, char side, char uplo, char transa, char di
     // ||op(A)||_inf of the caller's op(A): row sums of op(A) with its own flag
     e = refine_op_norm_inf(A, lda, k, lower, trans, unit, sm, norms, s);
     if (e != cudaSuccess) return fail_cuda(e, "refine norm");
-    double host[3] = {0, 0, 0};
+    double host[4] = {0, 0, 0, 0};
     double eta0 = 0.0, eta = 0.0, eta_prev = 0.0, rnorm = 0.0;
+    const bool lowerI = lower != (transI == 'T');
     int it = 0;
     for (;; ++it) {
-        // 2. R := alpha B - op(A) X, products of FP32 data exact
+        // 2. the residual R = alpha B - op(A) X, products of FP32 data exact
         if (fp64_residual) {
+            // from X each time, on the FP64 pipe
             if ((e = cudaMemcpyAsync(R64, Xi, (size_t)k * nr * 8, cudaMemcpyDeviceToDevice, s)) !=
                 cudaSuccess)
                 return fail_cuda(e, "refine copy");
@@ -1093,14 +1095,25 @@ int trx_strsm_refined(trx_handle_t h, char side, char uplo, char transa, char di
                                       k, stream)) != TRX_SUCCESS)
                 return rc;
             e = refine_residual(B64, k, R64, k, k, nr, s);
-        } else {
+        } else if (it == 0) {
+            // from X = xh + xl, float-float
             e = refine_split(Xi, k, Xh, Xl, k, k, nr, s);
             if (e == cudaSuccess)
-                e = refine_residual_df(A, lda, k, lower != (transI == 'T'), transI == 'T', unit, Xh,
-                                       Xl, k, B64, k, R64, k, nr, s);
+                e = refine_residual_df(0, A, lda, k, lowerI, transI == 'T', unit, Xh, Xl, k, B64, k,
+                                       R64, k, nr, s);
+        } else {
+            // updated by the last correction D (one float plane, D32):
+            // R := R - op(A) D. The update's rounding is relative to
+            // ||op(A)|| ||D||; plain FP32 accumulation (error about
+            // k 2^-24 of it) once that is below tol / 8 of ||op(A)|| ||X||,
+            // float-float otherwise.
+            const double rho = host[2] > 0 ? host[3] / host[2] : 0.0;
+            const int mode = ((double)k * 0x1p-24 * rho <= tol / 8) ? 2 : 1;
+            e = refine_residual_df(mode, A, lda, k, lowerI, transI == 'T', unit, D32, nullptr, k,
+                                   R64, k, R64, k, nr, s);
         }
         if (e != cudaSuccess || (e = norm(R64, norms + 1)) != cudaSuccess ||
-            (e = norm(Xi, norms + 2)) != cudaSuccess ||
+            (it == 0 && (e = norm(Xi, norms + 2)) != cudaSuccess) ||
             (e = cudaMemcpyAsync(host, norms, 3 * sizeof(double), cudaMemcpyDeviceToHost, s)) !=
                 cudaSuccess ||
             (e = cudaStreamSynchronize(s)) != cudaSuccess)
@@ -1112,13 +1125,20 @@ int trx_strsm_refined(trx_handle_t h, char side, char uplo, char transa, char di
         // stop: converged, out of corrections, NaN, or no progress
         if (eta <= tol || it >= max_iter || !(eta == eta) || (it > 0 && eta >= eta_prev)) break;
         eta_prev = eta;
-        // 3. correction: op(A) D = R solved in FP32, X += D
+        // 3. correction: op(A) D = R solved in FP32, X += D; ||X||, ||D||
         if ((e = refine_cast_f64_f32(R64, k, D32, k, k, nr, s)) != cudaSuccess)
             return fail_cuda(e, "refine cast");
         if ((rc = execute<float>(h, true, 'L', uplo, transI, diag, k, nr, 1.0f, A, lda, D32, k,
                                  stream)) != TRX_SUCCESS)
             return rc;
-        if ((e = refine_add(Xi, k, D32, k, k, nr, s)) != cudaSuccess)
+        if ((e = refine_add(Xi, k, D32, k, k, nr, s)) != cudaSuccess ||
+            (e = norm(Xi, norms + 2)) != cudaSuccess)
+            return fail_cuda(e, "refine update");
+        if (!fp64_residual &&
+            ((e = refine_norm_f32(D32, k, k, nr, !left, sm, norms + 3, s)) != cudaSuccess ||
+             (e = cudaMemcpyAsync(host + 2, norms + 2, 2 * sizeof(double), cudaMemcpyDeviceToHost,
+                                  s)) != cudaSuccess ||
+             (e = cudaStreamSynchronize(s)) != cudaSuccess))
             return fail_cuda(e, "refine update");
     }
     // 4. the caller's X

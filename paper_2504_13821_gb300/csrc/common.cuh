@@ -160,10 +160,15 @@ cudaError_t refine_transpose_f64(const double* src, int64_t lds, double* dst, in
                                  int64_t rows, int64_t cols, cudaStream_t s);
 cudaError_t refine_split(const double* x, int64_t ldx, float* xh, float* xl, int64_t ld,
                          int64_t m, int64_t n, cudaStream_t s);
-cudaError_t refine_residual_df(const float* A, int64_t lda, int64_t k, bool lower, bool trans,
-                               bool unit, const float* Xh, const float* Xl, int64_t ldx,
-                               const double* B, int64_t ldb, double* R, int64_t ldr, int64_t n,
-                               cudaStream_t s);
+// mode 0: R := B - op(A) (Xh + Xl); 1: R := B - op(A) Xh, both with
+// error-free (float-float) accumulation; 2: the same with plain FP32
+// accumulation. R may be B (in place).
+cudaError_t refine_residual_df(int mode, const float* A, int64_t lda, int64_t k, bool lower,
+                               bool trans, bool unit, const float* Xh, const float* Xl,
+                               int64_t ldx, const double* B, int64_t ldb, double* R, int64_t ldr,
+                               int64_t n, cudaStream_t s);
+cudaError_t refine_norm_f32(const float* a, int64_t lda, int64_t m, int64_t n, bool by_cols,
+                            double* sums, double* out, cudaStream_t s);
 cudaError_t refine_norm_one(const double* a, int64_t lda, int64_t m, int64_t n, double* sums,
                             double* out, cudaStream_t s);
 size_t refine_norm_scratch(int64_t k);   // bytes refine_op_norm_inf needs at `sums`

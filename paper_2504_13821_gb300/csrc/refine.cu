@@ -176,9 +176,16 @@ __global__ void __launch_bounds__(kThreads) col_abs_sum_kernel(const double* a, 
 // FP32 dot product, at about six FP32 operations per term on the packed
 // f32x2 path.
 //
+// Three modes: kFull (X = xh + xl, the residual from X), kSingle (X one
+// float plane, e.g. a correction D: the update R - op(A) D keeps the same
+// error-free accumulation without the xl products) and kPlain (one float
+// plane, plain FP32 FMA accumulation: for an update whose D is so small
+// against X that FP32 rounding of op(A) D is below the target).
+//
 // Tiles of 64 rows x 64 columns, 16 terms of l per stage, 256 threads; a
 // thread owns rows ty + 16 r and column pairs (tx + 32 c, tx + 32 c + 16).
 constexpr int kRM = 64, kRN = 64, kRK = 16, kFold = 2;   // fold every 32 terms
+enum { kFull = 0, kSingle = 1, kPlain = 2 };
 
 __device__ __forceinline__ uint64_t pk(float a, float b) {
     uint64_t d;
@@ -231,13 +238,13 @@ __global__ void __launch_bounds__(kThreads) split_kernel(const double* x, int64_
     }
 }
 
-template <bool TRANS>
+template <bool TRANS, int MODE>
 __global__ void __launch_bounds__(256) residual_df_kernel(const float* __restrict__ A, int64_t lda,
                                                           int64_t k, int lower, int unit,
                                                           const float* __restrict__ Xh,
                                                           const float* __restrict__ Xl,
-                                                          int64_t ldx, const double* __restrict__ B,
-                                                          int64_t ldb, double* __restrict__ R,
+                                                          int64_t ldx, const double* B,
+                                                          int64_t ldb, double* R,
                                                           int64_t ldr, int64_t n) {
     __shared__ float4 As[kRK][kRM];          // (a, a, -a, -a): both packed operands in one load
     __shared__ float4 Xs[kRK][2 * 16 + 1];   // [l][pair * 16 + tx] = (xh_a, xh_b, xl_a, xl_b)
@@ -284,10 +291,14 @@ __global__ void __launch_bounds__(256) residual_df_kernel(const float* __restric
             for (int pc = 0; pc < 2; ++pc) {
                 const int64_t ja = j0 + jj + 32 * pc, jb = ja + 16;
                 const bool va = gl < k && ja < n, vb = gl < k && jb < n;
-                Xs[l][pc * 16 + jj] = make_float4(va ? Xh[gl + ja * ldx] : 0.0f,
-                                                  vb ? Xh[gl + jb * ldx] : 0.0f,
-                                                  va ? Xl[gl + ja * ldx] : 0.0f,
-                                                  vb ? Xl[gl + jb * ldx] : 0.0f);
+                if (MODE == kFull)
+                    Xs[l][pc * 16 + jj] = make_float4(va ? Xh[gl + ja * ldx] : 0.0f,
+                                                      vb ? Xh[gl + jb * ldx] : 0.0f,
+                                                      va ? Xl[gl + ja * ldx] : 0.0f,
+                                                      vb ? Xl[gl + jb * ldx] : 0.0f);
+                else
+                    Xs[l][pc * 16 + jj] = make_float4(va ? Xh[gl + ja * ldx] : 0.0f,
+                                                      vb ? Xh[gl + jb * ldx] : 0.0f, 0.0f, 0.0f);
             }
         }
         __syncthreads();
@@ -302,6 +313,10 @@ __global__ void __launch_bounds__(256) residual_df_kernel(const float* __restric
                 const uint64_t a2 = pk(av.x, av.y), na2 = pk(av.z, av.w);
 #pragma unroll
                 for (int c = 0; c < 2; ++c) {
+                    if (MODE == kPlain) {
+                        hi[r][c] = fma2(a2, xh[c], hi[r][c]);
+                        continue;
+                    }
                     const uint64_t np = mul2(na2, xh[c]);         // -p, p = fl(a xh)
                     const uint64_t e = fma2(a2, xh[c], np);        // a xh - p, exact
                     const uint64_t t = sub2(hi[r][c], np);         // hi + p
@@ -309,12 +324,15 @@ __global__ void __launch_bounds__(256) residual_df_kernel(const float* __restric
                     const uint64_t q = add2(np, bp);               // -(p - bp)
                     const uint64_t err = sub2(sub2(hi[r][c], sub2(t, bp)), q);
                     hi[r][c] = t;
-                    lo[r][c] = fma2(a2, xl[c], add2(lo[r][c], add2(err, e)));
+                    if (MODE == kFull)
+                        lo[r][c] = fma2(a2, xl[c], add2(lo[r][c], add2(err, e)));
+                    else
+                        lo[r][c] = add2(lo[r][c], add2(err, e));
                 }
             }
         }
         __syncthreads();
-        if (++stage == kFold) {
+        if (MODE != kPlain && ++stage == kFold) {
             stage = 0;
 #pragma unroll
             for (int r = 0; r < 4; ++r)
@@ -405,19 +423,68 @@ cudaError_t refine_split(const double* x, int64_t ldx, float* xh, float* xl, int
     split_kernel<<<grid_for(m * n), kThreads, 0, s>>>(x, ldx, xh, xl, ld, m, n);
     return cudaGetLastError();
 }
-cudaError_t refine_residual_df(const float* A, int64_t lda, int64_t k, bool lower, bool trans,
-                               bool unit, const float* Xh, const float* Xl, int64_t ldx,
-                               const double* B, int64_t ldb, double* R, int64_t ldr, int64_t n,
-                               cudaStream_t s) {
+template <bool TRANS>
+void launch_residual(int mode, unsigned blocks, const float* A, int64_t lda, int64_t k, bool lower,
+                     bool unit, const float* Xh, const float* Xl, int64_t ldx, const double* B,
+                     int64_t ldb, double* R, int64_t ldr, int64_t n, cudaStream_t s) {
+    if (mode == kFull)
+        residual_df_kernel<TRANS, kFull><<<blocks, 256, 0, s>>>(A, lda, k, lower, unit, Xh, Xl,
+                                                                ldx, B, ldb, R, ldr, n);
+    else if (mode == kSingle)
+        residual_df_kernel<TRANS, kSingle><<<blocks, 256, 0, s>>>(A, lda, k, lower, unit, Xh, Xl,
+                                                                  ldx, B, ldb, R, ldr, n);
+    else
+        residual_df_kernel<TRANS, kPlain><<<blocks, 256, 0, s>>>(A, lda, k, lower, unit, Xh, Xl,
+                                                                 ldx, B, ldb, R, ldr, n);
+}
+cudaError_t refine_residual_df(int mode, const float* A, int64_t lda, int64_t k, bool lower,
+                               bool trans, bool unit, const float* Xh, const float* Xl,
+                               int64_t ldx, const double* B, int64_t ldb, double* R, int64_t ldr,
+                               int64_t n, cudaStream_t s) {
     if (k <= 0 || n <= 0) return cudaSuccess;
+    if (mode < kFull || mode > kPlain || (mode == kFull && Xl == nullptr))
+        return cudaErrorInvalidValue;
     const int64_t blocks = ((k + kRM - 1) / kRM) * ((n + kRN - 1) / kRN);
     if (blocks > 0x7fffffff) return cudaErrorInvalidValue;
     if (trans)
-        residual_df_kernel<true><<<(unsigned)blocks, 256, 0, s>>>(A, lda, k, lower, unit, Xh, Xl,
-                                                                  ldx, B, ldb, R, ldr, n);
+        launch_residual<true>(mode, (unsigned)blocks, A, lda, k, lower, unit, Xh, Xl, ldx, B, ldb,
+                              R, ldr, n, s);
     else
-        residual_df_kernel<false><<<(unsigned)blocks, 256, 0, s>>>(A, lda, k, lower, unit, Xh, Xl,
-                                                                   ldx, B, ldb, R, ldr, n);
+        launch_residual<false>(mode, (unsigned)blocks, A, lda, k, lower, unit, Xh, Xl, ldx, B,
+                               ldb, R, ldr, n, s);
+    return cudaGetLastError();
+}
+// out[0] := ||D||_inf (rows) or max column sum (by_cols) of an FP32 array.
+__global__ void __launch_bounds__(kThreads) row_abs_sum_f32_kernel(const float* a, int64_t lda,
+                                                                   int64_t m, int64_t n,
+                                                                   double* sums) {
+    const int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+    if (i >= m) return;
+    double s = 0.0;
+    for (int64_t j = 0; j < n; ++j) s += fabs((double)a[i + j * lda]);
+    sums[i] = s;
+}
+__global__ void __launch_bounds__(kThreads) col_abs_sum_f32_kernel(const float* a, int64_t lda,
+                                                                   int64_t m, int64_t n,
+                                                                   double* sums) {
+    const int64_t j = ((int64_t)blockIdx.x * kThreads + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (j >= n) return;
+    double s = 0.0;
+    for (int64_t i = lane; i < m; i += 32) s += fabs((double)a[i + j * lda]);
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) sums[j] = s;
+}
+cudaError_t refine_norm_f32(const float* a, int64_t lda, int64_t m, int64_t n, bool by_cols,
+                            double* sums, double* out, cudaStream_t s) {
+    if (m <= 0 || n <= 0) return cudaMemsetAsync(out, 0, sizeof(double), s);
+    if (by_cols)
+        col_abs_sum_f32_kernel<<<(unsigned)((n * 32 + kThreads - 1) / kThreads), kThreads, 0,
+                                 s>>>(a, lda, m, n, sums);
+    else
+        row_abs_sum_f32_kernel<<<(unsigned)((m + kThreads - 1) / kThreads), kThreads, 0, s>>>(
+            a, lda, m, n, sums);
+    max_kernel<<<1, kThreads, 0, s>>>(sums, by_cols ? n : m, out);
     return cudaGetLastError();
 }
 // out[0] := max column sum of |M| (m x n); sums: n doubles of scratch.
