@@ -604,7 +604,7 @@ def run_refined(args):
         rows.append({"kappa_target": e["target"], "kappa_estimate": e["kappa_estimate"],
                      "scale": e["scale"], "ms_refined": ms_ref, "ms_fp32": ms_32,
                      "ms_fp64": ms_64, "iterations": info_ff["iterations"],
-                     "backward_error": info_ff["backward_error"],
+                     "backward_error_updated_residual": info_ff["backward_error"],
                      "backward_error_fp32": info_ff["initial_backward_error"],
                      "fp64_residual": {"ms_refined": ms_ref64,
                                        "iterations": info_64["iterations"],
@@ -621,7 +621,11 @@ def run_refined(args):
         "config": {"workload": f"refined TRSM side L lower, k={k}, {n} right-hand sides, "
                                "alpha 1.5, kappa about 1e2/1e4/1e6, stop at backward error "
                                "sqrt(k) 2^-53 or when a correction stops lowering it; "
-                               "float-float residual (FP64-pipe residual alongside)",
+                               "float-float residual, updated by each correction "
+                               "(its backward error excludes the first residual's own "
+                               "rounding, about 2^-46 relative; the tests check the result's "
+                               "backward error against the FP64 oracle); FP64-pipe residual "
+                               "recomputed from X alongside",
                    "l2": "factor (k^2 FP32 = 256 MB at k = 8192) larger than L2, no flush"},
         "per_kappa": rows,
     }
@@ -682,7 +686,7 @@ def run_serving(args):
     warm = []
     for dtype in (torch.float32, torch.float64):
         for k in (256, 8192):
-            A = torch.eye(k, device=dev, dtype=dtype)
+            A = torch.eye(k, device=dev, dtype=dtype).t()         # column-major view
             fid = srv.register(A, "L")
             for nrhs in (1, 1024):
                 for op in ("S", "M"):

@@ -231,7 +231,9 @@ int trx_batched(trx_handle_t handle, int elem_bytes, int64_t count,
  * trx_strsm (trx_workspace_size 'S') and allocates its own scratch on the
  * handle (about 36 m n bytes, plus 8 k^2 for the FP64 residual; kept for later
  * calls). info (may be NULL): corrections made, the final residual norm
- * and backward error, and the backward error of the plain FP32 solve.
+ * and backward error (of the updated residual on the float-float path: it
+ * leaves out the first residual's own rounding, about 2^-46 relative), and
+ * the backward error of the plain FP32 solve.
  * Returns -i for an illegal i-th argument of this call (side 2, uplo 3,
  * transa 4, diag 5, m 6, n 7, alpha 8, A 9, lda 10, B 11, ldb 12, X 13,
  * ldx 14, max_iter < 0: 15, tol < 0 or NaN: 16), or a TRX_ERR_* code. (The

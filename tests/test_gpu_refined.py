@@ -180,3 +180,19 @@ def test_refined_stored_condition_scales(trx, residual):
         assert eta <= 8 * k * U64, (e, eta, info)
         fwd = oracle.forward_error(Xh, oracle.trsm("L", "L", "N", "N", 1.5, A64, B64))
         assert fwd <= 8 * k * U64 * e["kappa_estimate"], (e, fwd, info)
+
+
+def test_refined_zero_tolerance_stops_on_stagnation(trx):
+    """tol = 0 is never met: every update keeps the float-float
+    accumulation, and the loop ends when a correction stops lowering the
+    backward error (or after max_iter); the result is still FP64-accurate."""
+    k = 500
+    A, B = inputs.problem("L", "U", k, 70, seed=12, dtype=np.float32,
+                          scale=oracle.scale_for_condition(k, 1e5, seed=12, uplo="U"))
+    At, Bt = to_dev(A, "cuda:0"), to_dev(B, "cuda:0")
+    X, info = trx.trsm_refined("L", "U", "N", "N", 1.0, At, Bt, tol=0.0, max_iter=8)
+    assert 1 <= info["iterations"] <= 8
+    eta = oracle.trsm_backward_error("L", "U", "N", "N", 1.0, A.astype(np.float64),
+                                     np.asfortranarray(X.cpu().numpy()),
+                                     B.astype(np.float64))["eta"]
+    assert eta <= 8 * k * U64, (eta, info)
