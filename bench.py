@@ -680,18 +680,26 @@ def run_serving(args):
             done[rid] = now
             if st != 0:
                 failed.append((rid, st))
+    def make_factor(k, uplo, dtype):
+        A = torch.empty(k, k, device=dev, dtype=dtype).uniform_(-1.0 / k, 1.0 / k)
+        A = (torch.tril(A) if uplo == "L" else torch.triu(A))
+        A.diagonal().copy_(1 + torch.randn(k, device=dev, dtype=dtype).abs())
+        return A.t().contiguous().t()
+
     # warm-up before the arrivals start: one small and one large factor per
-    # precision, TRSM and TRMM with few and many right-hand sides, so module
-    # loading and first-use setup are not charged to the first requests
+    # precision and triangle, TRSM and TRMM with few and many right-hand
+    # sides, through the same generator calls as the run, so module loading
+    # (the library's and torch's) and first-use setup are not charged to the
+    # first requests
     warm = []
     for dtype in (torch.float32, torch.float64):
-        for k in (256, 8192):
-            A = torch.eye(k, device=dev, dtype=dtype).t()         # column-major view
-            fid = srv.register(A, "L")
+        for k, uplo in ((256, "L"), (8192, "U")):
+            A = make_factor(k, uplo, dtype)
+            fid = srv.register(A, uplo)
             for nrhs in (1, 1024):
                 for op in ("S", "M"):
                     warm.append(srv.submit(fid, op, "L", 1.0,
-                                           torch.ones(nrhs, k, device=dev, dtype=dtype).t()))
+                                           torch.randn(nrhs, k, device=dev, dtype=dtype).t()))
             srv.release(fid)
             del A
     warm_status = dict(srv.drain())
@@ -713,10 +721,7 @@ def run_serving(args):
         else:
             k = int(round(np.exp(rng.uniform(np.log(64), np.log(8192)))))
             uplo = str(rng.choice(["L", "U"]))
-            A = torch.empty(k, k, device=dev, dtype=dtype).uniform_(-1.0 / k, 1.0 / k)
-            A = (torch.tril(A) if uplo == "L" else torch.triu(A))
-            A.diagonal().copy_(1 + torch.randn(k, device=dev, dtype=dtype).abs())
-            A = A.t().contiguous().t()
+            A = make_factor(k, uplo, dtype)
             fid = srv.register(A, uplo)
             live[fid] = [A, int(rng.integers(1, 51)), dtype, k, uplo]
         live[fid][1] -= 1

@@ -221,8 +221,9 @@ int trx_batched(trx_handle_t handle, int elem_bytes, int64_t count,
  * float-float on the FP32 pipes by default, or FP64 arithmetic), a
  * correction op(A) D = R (or D op(A) = R) solved in FP32 on the same
  * recursive path, X += D in FP64 (float-float: R is then updated as
- * R - op(A) D, with plain FP32 accumulation once k 2^-24 ||D|| / ||X||
- * is below tol / 8; FP64: recomputed from X), until the normwise backward error
+ * R - op(A) D, with plain FP32 accumulation once sqrt(k) 2^-24 ||D|| /
+ * ||X|| is below tol / 8; FP64: recomputed from X), until the normwise
+ * backward error
  * ||R|| / (||op(A)|| ||X||) (infinity norms) is at most tol, max_iter
  * corrections were made, or a correction did not lower it. A (k x k) and
  * B (m x n) are FP32 device arrays as in trx_strsm, B is not modified;

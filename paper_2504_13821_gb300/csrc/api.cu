@@ -8,6 +8,7 @@
 // mapping (side 'R' solves with op(A)^T on B^T; an effectively-upper triangle
 // is index-reversed), so no variant needs its own kernels.
 #include <algorithm>
+#include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -1104,11 +1105,12 @@ int trx_strsm_refined(trx_handle_t h, char side, char uplo, char transa, char di
         } else {
             // updated by the last correction D (one float plane, D32):
             // R := R - op(A) D. The update's rounding is relative to
-            // ||op(A)|| ||D||; plain FP32 accumulation (error about
-            // k 2^-24 of it) once that is below tol / 8 of ||op(A)|| ||X||,
+            // ||op(A)|| ||D||; plain FP32 accumulation (typical error
+            // sqrt(k) 2^-24 of it, the same sqrt(k) reading as the default
+            // tolerance) once that is below tol / 8 of ||op(A)|| ||X||,
             // float-float otherwise.
             const double rho = host[2] > 0 ? host[3] / host[2] : 0.0;
-            const int mode = ((double)k * 0x1p-24 * rho <= tol / 8) ? 2 : 1;
+            const int mode = (std::sqrt((double)k) * 0x1p-24 * rho <= tol / 8) ? 2 : 1;
             e = refine_residual_df(mode, A, lda, k, lowerI, transI == 'T', unit, D32, nullptr, k,
                                    R64, k, R64, k, nr, s);
         }
