@@ -1027,12 +1027,16 @@ int trx_strsm_refined(trx_handle_t h, char side, char uplo, char transa, char di
     const char transI = (left ? trans : !trans) ? 'T' : 'N';
     const bool lower = upc(uplo) == 'L', unit = upc(diag) == 'U';
     const bool fp64_residual = h->opt_residual == 1;
-    // scratch: Xi, B64, R64 (k x nr FP64), D32, Xh, Xl (k x nr FP32),
-    // row/column sums, norms, and for the FP64 residual an FP64 copy of A
+    const bool lowerI = lower != (transI == 'T');
+    // scratch: Xi, B64, R64 (k x nr FP64), D32 (k x nr FP32), row/column
+    // sums, norms, and either the packed op(A) and X of the float-float
+    // residual or an FP64 copy of A
     const size_t mn64 = align256((size_t)k * nr * 8), mn32 = align256((size_t)k * nr * 4);
     const size_t sums = align256(std::max((size_t)std::max(k, nr) * 8, refine_norm_scratch(k)));
     const size_t a64 = fp64_residual ? align256((size_t)k * k * 8) : 0;
-    const size_t need = 3 * mn64 + 3 * mn32 + sums + 256 + a64;
+    const size_t ap = fp64_residual ? 0 : align256(refine_pack_a_bytes(k, lowerI));
+    const size_t xp = fp64_residual ? 0 : align256(refine_pack_x_bytes(k, nr));
+    const size_t need = 3 * mn64 + mn32 + sums + 256 + a64 + ap + xp;
     if (h->rf_bytes < need) {
         if (h->rf_buf) {
             cudaStreamSynchronize(s);
@@ -1051,13 +1055,12 @@ int trx_strsm_refined(trx_handle_t h, char side, char uplo, char transa, char di
     double* B64 = reinterpret_cast<double*>(base + mn64);
     double* R64 = reinterpret_cast<double*>(base + 2 * mn64);
     float* D32 = reinterpret_cast<float*>(base + 3 * mn64);
-    float* Xh = reinterpret_cast<float*>(base + 3 * mn64 + mn32);
-    float* Xl = reinterpret_cast<float*>(base + 3 * mn64 + 2 * mn32);
-    double* sm = reinterpret_cast<double*>(base + 3 * mn64 + 3 * mn32);
-    double* norms = reinterpret_cast<double*>(base + 3 * mn64 + 3 * mn32 + sums);
-    double* A64 =
-        fp64_residual ? reinterpret_cast<double*>(base + 3 * mn64 + 3 * mn32 + sums + 256)
-                      : nullptr;
+    double* sm = reinterpret_cast<double*>(base + 3 * mn64 + mn32);
+    double* norms = reinterpret_cast<double*>(base + 3 * mn64 + mn32 + sums);
+    char* tail = base + 3 * mn64 + mn32 + sums + 256;
+    double* A64 = fp64_residual ? reinterpret_cast<double*>(tail) : nullptr;
+    void* Ap = fp64_residual ? nullptr : tail;
+    void* Xp = fp64_residual ? nullptr : tail + ap;
     // infinity norms of the caller's m x n arrays: row sums of the internal
     // k x nr array for side L, column sums for side R
     auto norm = [&](const double* a, double* out) {
@@ -1076,14 +1079,16 @@ int trx_strsm_refined(trx_handle_t h, char side, char uplo, char transa, char di
         (e = left ? refine_cast_f32_f64(B, ldb, B64, k, k, nr, (double)alpha, s)
                   : refine_transpose_f32_f64(B, ldb, B64, k, m, n, (double)alpha, s)) !=
             cudaSuccess ||
-        (fp64_residual && (e = refine_cast_f32_f64(A, lda, A64, k, k, k, 1.0, s)) != cudaSuccess))
+        (fp64_residual && (e = refine_cast_f32_f64(A, lda, A64, k, k, k, 1.0, s)) != cudaSuccess) ||
+        (!fp64_residual &&
+         (e = refine_pack_a(A, lda, k, lowerI, transI == 'T', unit, Ap, s)) != cudaSuccess))
         return fail_cuda(e, "refine setup");
     // ||op(A)||_inf of the caller's op(A): row sums of op(A) with its own flag
     e = refine_op_norm_inf(A, lda, k, lower, trans, unit, sm, norms, s);
     if (e != cudaSuccess) return fail_cuda(e, "refine norm");
     double host[4] = {0, 0, 0, 0};
+    int dev_err = 0;
     double eta0 = 0.0, eta = 0.0, eta_prev = 0.0, rnorm = 0.0;
-    const bool lowerI = lower != (transI == 'T');
     int it = 0;
     for (;; ++it) {
         // 2. the residual R = alpha B - op(A) X, products of FP32 data exact
@@ -1098,10 +1103,10 @@ int trx_strsm_refined(trx_handle_t h, char side, char uplo, char transa, char di
             e = refine_residual(B64, k, R64, k, k, nr, s);
         } else if (it == 0) {
             // from X = xh + xl, float-float
-            e = refine_split(Xi, k, Xh, Xl, k, k, nr, s);
+            e = refine_pack_x(Xi, nullptr, k, k, nr, Xp, s);
             if (e == cudaSuccess)
-                e = refine_residual_df(0, A, lda, k, lowerI, transI == 'T', unit, Xh, Xl, k, B64, k,
-                                       R64, k, nr, s);
+                e = refine_residual_packed(0, Ap, Xp, k, lowerI, B64, k, R64, k, nr, h->d_err,
+                                           h->wait_ns, s);
         } else {
             // updated by the last correction D (one float plane, D32):
             // R := R - op(A) D. The update's rounding is relative to
@@ -1111,15 +1116,26 @@ int trx_strsm_refined(trx_handle_t h, char side, char uplo, char transa, char di
             // float-float otherwise.
             const double rho = host[2] > 0 ? host[3] / host[2] : 0.0;
             const int mode = (std::sqrt((double)k) * 0x1p-24 * rho <= tol / 8) ? 2 : 1;
-            e = refine_residual_df(mode, A, lda, k, lowerI, transI == 'T', unit, D32, nullptr, k,
-                                   R64, k, R64, k, nr, s);
+            e = refine_pack_x(nullptr, D32, k, k, nr, Xp, s);
+            if (e == cudaSuccess)
+                e = refine_residual_packed(mode, Ap, Xp, k, lowerI, R64, k, R64, k, nr, h->d_err,
+                                           h->wait_ns, s);
         }
         if (e != cudaSuccess || (e = norm(R64, norms + 1)) != cudaSuccess ||
             (it == 0 && (e = norm(Xi, norms + 2)) != cudaSuccess) ||
             (e = cudaMemcpyAsync(host, norms, 3 * sizeof(double), cudaMemcpyDeviceToHost, s)) !=
                 cudaSuccess ||
+            (e = cudaMemcpyAsync(&dev_err, h->d_err, sizeof(int), cudaMemcpyDeviceToHost, s)) !=
+                cudaSuccess ||
             (e = cudaStreamSynchronize(s)) != cudaSuccess)
             return fail_cuda(e, "refine residual");
+        if (dev_err != 0) {
+            // a bounded wait in the residual kernel gave up: clear the word
+            cudaMemsetAsync(h->d_err, 0, sizeof(int), s);
+            cudaStreamSynchronize(s);
+            snprintf(g_detail, sizeof(g_detail), "refine residual: device wait timed out");
+            return TRX_ERR_TIMEOUT;
+        }
         rnorm = host[1];
         const double den = host[0] * host[2];
         eta = den > 0 ? rnorm / den : rnorm;

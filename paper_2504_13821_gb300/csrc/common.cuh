@@ -158,15 +158,22 @@ cudaError_t refine_transpose_f32_f64(const float* src, int64_t lds, double* dst,
                                      int64_t rows, int64_t cols, double scale, cudaStream_t s);
 cudaError_t refine_transpose_f64(const double* src, int64_t lds, double* dst, int64_t ldd,
                                  int64_t rows, int64_t cols, cudaStream_t s);
-cudaError_t refine_split(const double* x, int64_t ldx, float* xh, float* xl, int64_t ld,
-                         int64_t m, int64_t n, cudaStream_t s);
-// mode 0: R := B - op(A) (Xh + Xl); 1: R := B - op(A) Xh, both with
-// error-free (float-float) accumulation; 2: the same with plain FP32
-// accumulation. R may be B (in place).
-cudaError_t refine_residual_df(int mode, const float* A, int64_t lda, int64_t k, bool lower,
-                               bool trans, bool unit, const float* Xh, const float* Xl,
-                               int64_t ldx, const double* B, int64_t ldb, double* R, int64_t ldr,
-                               int64_t n, cudaStream_t s);
+// The float-float residual: op(A) packed once (refine_pack_a_bytes),
+// X packed per step (refine_pack_x_bytes; from FP64 X split into two
+// floats, or from one FP32 plane), then R := B - op(A) X with mode 0
+// (X = xh + xl) or 1 (one plane), error-free accumulation, or 2 (one
+// plane, plain FP32 accumulation). R may be B. Waits bounded by wait_ns;
+// on timeout *err := TRX_ERR_TIMEOUT and R is not written.
+size_t refine_pack_a_bytes(int64_t k, bool lower);
+size_t refine_pack_x_bytes(int64_t k, int64_t n);
+cudaError_t refine_pack_a(const float* A, int64_t lda, int64_t k, bool lower, bool trans,
+                          bool unit, void* Ap, cudaStream_t s);
+cudaError_t refine_pack_x(const double* X64, const float* X32, int64_t ldx, int64_t k,
+                          int64_t n, void* Xp, cudaStream_t s);
+cudaError_t refine_residual_packed(int mode, const void* Ap, const void* Xp, int64_t k,
+                                   bool lower, const double* B, int64_t ldb, double* R,
+                                   int64_t ldr, int64_t n, int* err, long long wait_ns,
+                                   cudaStream_t s);
 cudaError_t refine_norm_f32(const float* a, int64_t lda, int64_t m, int64_t n, bool by_cols,
                             double* sums, double* out, cudaStream_t s);
 cudaError_t refine_norm_one(const double* a, int64_t lda, int64_t m, int64_t n, double* sums,

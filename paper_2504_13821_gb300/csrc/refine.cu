@@ -3,6 +3,7 @@
 // R = alpha B - op(A) X, the correction X += D, and the infinity norms that
 // decide when to stop. All column-major, leading dimensions in elements.
 #include "common.cuh"
+#include "trx.h"
 
 namespace trx {
 namespace {
@@ -161,10 +162,8 @@ __global__ void __launch_bounds__(kThreads) col_abs_sum_kernel(const double* a, 
 }
 
 // ---- residual in float-float on the FP32 pipes ------------------------------
-// R := B - op(A) X, op(A) k x k triangular (FP32, element (i, l) at
-// A[i + l lda], or A[l + i lda] when TRANS), X k x n given as two FP32
-// planes xh + xl (48 significant bits, split once per step by
-// split_kernel), B, R FP64.
+// R := B - op(A) X for op(A) k x k triangular (FP32) and X k x n, B and R
+// FP64 (R may be B).
 //
 // Each product a xh is split exactly into p + e with one FMA
 // (e = a xh - p); p joins the running sum hi through the error-free
@@ -182,9 +181,23 @@ __global__ void __launch_bounds__(kThreads) col_abs_sum_kernel(const double* a, 
 // plane, plain FP32 FMA accumulation: for an update whose D is so small
 // against X that FP32 rounding of op(A) D is below the target).
 //
-// Tiles of 64 rows x 64 columns, 16 terms of l per stage, 256 threads; a
-// thread owns rows ty + 16 r and column pairs (tx + 32 c, tx + 32 c + 16).
+// Operands are packed once into the order the kernel reads them, so every
+// pipeline stage is two contiguous bulk copies (cp.async.bulk, completion
+// counted on an mbarrier) into a three-stage ring:
+//  - op(A) (once per refined solve): per 64-row tile, its 16-column chunks
+//    that meet the triangle, each 16 x 64 float4 (a, a, -a, -a), masked to
+//    the triangle, the unit diagonal written as 1: both packed operands of
+//    a row in one 16-byte load;
+//  - X (once per step): per 64-column tile, rows in 16-row chunks, each row
+//    32 float4 (xh_a, xh_b, xl_a, xl_b) for the thread's column pair
+//    (tx + 32 c, tx + 32 c + 16), zero beyond k and n.
+// Tiles of 64 rows x 64 columns, 16 terms per stage, 256 threads; a thread
+// owns rows ty + 16 r and column pairs (tx + 32 c, tx + 32 c + 16).
 constexpr int kRM = 64, kRN = 64, kRK = 16, kFold = 2;   // fold every 32 terms
+constexpr int kStages = 3;
+constexpr uint32_t kABytes = kRK * kRM * 16, kXBytes = kRK * 32 * 16;
+constexpr uint32_t kStageBytes = kABytes + kXBytes;
+constexpr int kPipeSmem = kStages * (int)kStageBytes + 2 * kStages * 8 + 16;
 enum { kFull = 0, kSingle = 1, kPlain = 2 };
 
 __device__ __forceinline__ uint64_t pk(float a, float b) {
@@ -224,38 +237,162 @@ __device__ __forceinline__ uint64_t two_sum2(uint64_t& s, uint64_t b) {
     return err;
 }
 
-// xh := fl32(x), xl := fl32(x - xh) for a k x n FP64 array
-__global__ void __launch_bounds__(kThreads) split_kernel(const double* x, int64_t ldx, float* xh,
-                                                         float* xl, int64_t ld, int64_t m,
-                                                         int64_t n) {
-    for (int64_t e = (int64_t)blockIdx.x * kThreads + threadIdx.x; e < m * n;
-         e += (int64_t)gridDim.x * kThreads) {
-        const int64_t i = e % m, j = e / m;
-        const double v = x[i + j * ldx];
-        const float h = (float)v;
-        xh[i + j * ld] = h;
-        xl[i + j * ld] = (float)(v - (double)h);
+// mbarrier and bulk-copy wrappers
+__device__ __forceinline__ uint32_t saddr(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void bar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void bar_expect(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void bar_arrive(uint32_t bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ bool bar_try(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ uint64_t now_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+__device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_t bytes,
+                                          uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+        ::"r"(dst), "l"(src), "r"(bytes), "r"(bar)
+        : "memory");
+}
+// Bounded wait for phase `parity`: false once the CTA has aborted or
+// `limit` ns have passed (then it aborts the CTA and sets the error word).
+__device__ bool bar_wait(uint32_t bar, uint32_t parity, volatile int* abort, int* err,
+                         uint64_t limit, bool honour_abort) {
+    if (bar_try(bar, parity)) return true;
+    const uint64_t t0 = now_ns();
+    while (true) {
+        if (bar_try(bar, parity)) return true;
+        if (honour_abort && *abort) return false;
+        if (now_ns() - t0 > limit) {
+            *abort = 1;
+            atomicExch(err, TRX_ERR_TIMEOUT);
+            return false;
+        }
     }
 }
 
-template <bool TRANS, int MODE>
-__global__ void __launch_bounds__(256) residual_df_kernel(const float* __restrict__ A, int64_t lda,
-                                                          int64_t k, int lower, int unit,
-                                                          const float* __restrict__ Xh,
-                                                          const float* __restrict__ Xl,
-                                                          int64_t ldx, const double* B,
-                                                          int64_t ldb, double* R,
-                                                          int64_t ldr, int64_t n) {
-    __shared__ float4 As[kRK][kRM];          // (a, a, -a, -a): both packed operands in one load
-    __shared__ float4 Xs[kRK][2 * 16 + 1];   // [l][pair * 16 + tx] = (xh_a, xh_b, xl_a, xl_b)
-    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-    const int64_t nrt = (k + kRM - 1) / kRM, nct = (n + kRN - 1) / kRN;
+// Chunks of row tile rt (16 columns of op(A) each) and the first one's
+// column index / 16, for K16 = ceil(k / 16) column chunks.
+__host__ __device__ __forceinline__ void tile_chunks(int64_t rt, int64_t K16, bool lower,
+                                                     int64_t& first, int64_t& count,
+                                                     int64_t& offset) {
+    if (lower) {
+        first = 0;
+        count = 4 * (rt + 1) < K16 ? 4 * (rt + 1) : K16;
+        offset = 2 * rt * (rt + 1);                      // sum of 4 (r + 1), r < rt
+    } else {
+        first = 4 * rt;
+        count = K16 - 4 * rt;
+        offset = rt * K16 - 2 * rt * (rt - 1);           // sum of K16 - 4 r, r < rt
+    }
+}
+
+// op(A) packed: block (chunk q of row tile blockIdx.y, quarter blockIdx.x % 4).
+template <bool TRANS>
+__global__ void __launch_bounds__(256) pack_a_kernel(const float* A, int64_t lda, int64_t k,
+                                                     int lower, int unit, float4* Ap) {
+    const int64_t K16 = (k + 15) / 16, rt = blockIdx.y, q = blockIdx.x >> 2;
+    int64_t first, count, offset;
+    tile_chunks(rt, K16, lower != 0, first, count, offset);
+    if (q >= count) return;
+    const int e = (int)(blockIdx.x & 3) * 256 + threadIdx.x;      // element of the chunk
+    // read order: along rows (i) for A[i + l lda], along columns (l) otherwise
+    const int l = TRANS ? (e & 15) : (e >> 6), i = TRANS ? (e >> 4) : (e & 63);
+    const int64_t gi = rt * kRM + i, gl = (first + q) * kRK + l;
+    float v = 0.0f;
+    if (gi < k && gl < k && (lower ? gl <= gi : gl >= gi)) {
+        if (gl == gi && unit) v = 1.0f;
+        else v = TRANS ? A[gl + gi * lda] : A[gi + gl * lda];
+    }
+    Ap[(offset + q) * (kRK * kRM) + l * kRM + i] = make_float4(v, v, -v, -v);
+}
+
+// X packed: row l of column tile blockIdx.y; thread t = (pair pc, lane jj).
+template <bool SPLIT>
+__global__ void __launch_bounds__(32) pack_x_kernel(const double* X64, const float* X32,
+                                                    int64_t ldx, int64_t k, int64_t n,
+                                                    int64_t rows, float4* Xp) {
+    const int64_t l = blockIdx.x, ct = blockIdx.y;
+    const int t = threadIdx.x, pc = t >> 4, jj = t & 15;
+    const int64_t ja = ct * kRN + jj + 32 * pc, jb = ja + 16;
+    float4 v = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    if (l < k) {
+        if (SPLIT) {
+            const double xa = ja < n ? X64[l + ja * ldx] : 0.0, xb = jb < n ? X64[l + jb * ldx] : 0.0;
+            v.x = (float)xa;
+            v.y = (float)xb;
+            v.z = (float)(xa - (double)v.x);
+            v.w = (float)(xb - (double)v.y);
+        } else {
+            v.x = ja < n ? X32[l + ja * ldx] : 0.0f;
+            v.y = jb < n ? X32[l + jb * ldx] : 0.0f;
+        }
+    }
+    Xp[(ct * rows + l) * 32 + t] = v;
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(256) residual_pipe_kernel(const float4* __restrict__ Ap,
+                                                            const float4* __restrict__ Xp,
+                                                            int64_t rows, int64_t k, int lower,
+                                                            const double* B, int64_t ldb,
+                                                            double* R, int64_t ldr, int64_t n,
+                                                            int* err, long long wait_ns) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem + kStages * kStageBytes);
+    uint64_t* empty = full + kStages;
+    volatile int* abort = reinterpret_cast<volatile int*>(empty + kStages);
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4, lane = tid & 31;
+    const int64_t nrt = (k + kRM - 1) / kRM, nct = (n + kRN - 1) / kRN, K16 = (k + 15) / 16;
     const int64_t rt_raw = blockIdx.x / nct, ct = blockIdx.x % nct;
     // heaviest row tiles first: the last ones when lower, the first when upper
     const int64_t rt = lower ? nrt - 1 - rt_raw : rt_raw;
     const int64_t i0 = rt * kRM, j0 = ct * kRN;
-    const int64_t l_begin = lower ? 0 : i0;
-    const int64_t l_end = lower ? (i0 + kRM < k ? i0 + kRM : k) : k;
+    int64_t first, count, offset;
+    tile_chunks(rt, K16, lower != 0, first, count, offset);
+    const float4* a_src = Ap + offset * (kRK * kRM);
+    const float4* x_src = Xp + (ct * rows + first * kRK) * 32;
+    const uint64_t limit = (uint64_t)wait_ns;
+
+    if (tid == 0) {
+        for (int s = 0; s < kStages; ++s) {
+            bar_init(saddr(&full[s]), 1);
+            bar_init(saddr(&empty[s]), 8);       // one arrival per warp
+        }
+        *abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    int64_t issued = 0;                          // thread 0: stages whose copies were issued
+    auto issue = [&](int64_t q) {
+        const int s = (int)(q % kStages);
+        unsigned char* dst = smem + s * kStageBytes;
+        bar_expect(saddr(&full[s]), kStageBytes);
+        bulk_load(saddr(dst), a_src + q * (kRK * kRM), kABytes, saddr(&full[s]));
+        bulk_load(saddr(dst + kABytes), x_src + q * (kRK * 32), kXBytes, saddr(&full[s]));
+    };
+    if (tid == 0)
+        for (; issued < count && issued < kStages; ++issued) issue(issued);
 
     uint64_t hi[4][2], lo[4][2], mid[4][2], lo2[4][2];
 #pragma unroll
@@ -263,53 +400,24 @@ __global__ void __launch_bounds__(256) residual_df_kernel(const float* __restric
 #pragma unroll
         for (int c = 0; c < 2; ++c) hi[r][c] = lo[r][c] = mid[r][c] = lo2[r][c] = 0ull;
     int stage = 0;
-    for (int64_t l0 = l_begin; l0 < l_end; l0 += kRK) {
-        // A tile: op(A)(i0 + i, l0 + l), masked to the triangle
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            int i, l;
-            if (TRANS) {
-                l = tid & 15;
-                i = (tid >> 4) + 16 * q;
-            } else {
-                i = tid & 63;
-                l = (tid >> 6) + 4 * q;
-            }
-            const int64_t gi = i0 + i, gl = l0 + l;
-            float v = 0.0f;
-            if (gi < k && gl < k && (lower ? gl <= gi : gl >= gi)) {
-                if (gl == gi && unit) v = 1.0f;
-                else v = TRANS ? A[gl + gi * lda] : A[gi + gl * lda];
-            }
-            As[l][i] = make_float4(v, v, -v, -v);
+    bool ok = true;
+    for (int64_t q = 0; q < count; ++q) {
+        const int s = (int)(q % kStages);
+        const uint32_t parity = (uint32_t)((q / kStages) & 1);
+        if (!bar_wait(saddr(&full[s]), parity, abort, err, limit, true)) {
+            ok = false;
+            break;
         }
-        // X tile: rows l0 .. l0 + 15, columns j0 .. j0 + 63
-        {
-            const int l = tid & 15, jj = tid >> 4;
-            const int64_t gl = l0 + l;
-#pragma unroll
-            for (int pc = 0; pc < 2; ++pc) {
-                const int64_t ja = j0 + jj + 32 * pc, jb = ja + 16;
-                const bool va = gl < k && ja < n, vb = gl < k && jb < n;
-                if (MODE == kFull)
-                    Xs[l][pc * 16 + jj] = make_float4(va ? Xh[gl + ja * ldx] : 0.0f,
-                                                      vb ? Xh[gl + jb * ldx] : 0.0f,
-                                                      va ? Xl[gl + ja * ldx] : 0.0f,
-                                                      vb ? Xl[gl + jb * ldx] : 0.0f);
-                else
-                    Xs[l][pc * 16 + jj] = make_float4(va ? Xh[gl + ja * ldx] : 0.0f,
-                                                      vb ? Xh[gl + jb * ldx] : 0.0f, 0.0f, 0.0f);
-            }
-        }
-        __syncthreads();
+        const float4* As = reinterpret_cast<const float4*>(smem + s * kStageBytes);
+        const float4* Xs = reinterpret_cast<const float4*>(smem + s * kStageBytes + kABytes);
 #pragma unroll 4
         for (int l = 0; l < kRK; ++l) {
-            const float4 x0 = Xs[l][tx], x1 = Xs[l][16 + tx];
+            const float4 x0 = Xs[l * 32 + tx], x1 = Xs[l * 32 + 16 + tx];
             const uint64_t xh[2] = {pk(x0.x, x0.y), pk(x1.x, x1.y)};
             const uint64_t xl[2] = {pk(x0.z, x0.w), pk(x1.z, x1.w)};
 #pragma unroll
             for (int r = 0; r < 4; ++r) {
-                const float4 av = As[l][ty + 16 * r];
+                const float4 av = As[l * kRM + ty + 16 * r];
                 const uint64_t a2 = pk(av.x, av.y), na2 = pk(av.z, av.w);
 #pragma unroll
                 for (int c = 0; c < 2; ++c) {
@@ -321,17 +429,26 @@ __global__ void __launch_bounds__(256) residual_df_kernel(const float* __restric
                     const uint64_t e = fma2(a2, xh[c], np);        // a xh - p, exact
                     const uint64_t t = sub2(hi[r][c], np);         // hi + p
                     const uint64_t bp = sub2(t, hi[r][c]);
-                    const uint64_t q = add2(np, bp);               // -(p - bp)
-                    const uint64_t err = sub2(sub2(hi[r][c], sub2(t, bp)), q);
+                    const uint64_t qq = add2(np, bp);              // -(p - bp)
+                    const uint64_t er = sub2(sub2(hi[r][c], sub2(t, bp)), qq);
                     hi[r][c] = t;
                     if (MODE == kFull)
-                        lo[r][c] = fma2(a2, xl[c], add2(lo[r][c], add2(err, e)));
+                        lo[r][c] = fma2(a2, xl[c], add2(lo[r][c], add2(er, e)));
                     else
-                        lo[r][c] = add2(lo[r][c], add2(err, e));
+                        lo[r][c] = add2(lo[r][c], add2(er, e));
                 }
             }
         }
-        __syncthreads();
+        __syncwarp();
+        if (lane == 0) bar_arrive(saddr(&empty[s]));
+        // refill this slot with stage q + kStages once every warp is done
+        if (tid == 0 && issued < count) {
+            if (!bar_wait(saddr(&empty[s]), parity, abort, err, limit, true)) {
+                ok = false;
+                break;
+            }
+            issue(issued++);
+        }
         if (MODE != kPlain && ++stage == kFold) {
             stage = 0;
 #pragma unroll
@@ -343,23 +460,34 @@ __global__ void __launch_bounds__(256) residual_df_kernel(const float* __restric
                 }
         }
     }
+    if (!ok || *abort) {
+        // copies still in flight land before the CTA exits (waits of at
+        // least 1 s, whatever the budget)
+        if (tid == 0) {
+            const uint64_t drain = limit > 1000000000ull ? limit : 1000000000ull;
+            for (int64_t q = issued - kStages < 0 ? 0 : issued - kStages; q < issued; ++q)
+                bar_wait(saddr(&full[q % kStages]), (uint32_t)((q / kStages) & 1), abort, err,
+                         drain, false);
+        }
+        return;
+    }
 #pragma unroll
     for (int r = 0; r < 4; ++r) {
         const int64_t gi = i0 + ty + 16 * r;
         if (gi >= k) continue;
 #pragma unroll
         for (int c = 0; c < 2; ++c) {
-            float h[2], m[2], s[2], t[2];
+            float h[2], m[2], sm[2], t[2];
             upk(hi[r][c], h[0], h[1]);
             upk(mid[r][c], m[0], m[1]);
-            upk(lo[r][c], s[0], s[1]);
+            upk(lo[r][c], sm[0], sm[1]);
             upk(lo2[r][c], t[0], t[1]);
 #pragma unroll
             for (int w = 0; w < 2; ++w) {
                 const int64_t j = j0 + tx + 32 * c + 16 * w;
                 if (j < n)
                     R[gi + j * ldr] = B[gi + j * ldb] -
-                                      ((double)h[w] + ((double)m[w] + ((double)s[w] + (double)t[w])));
+                                      ((double)h[w] + ((double)m[w] + ((double)sm[w] + (double)t[w])));
             }
         }
     }
@@ -417,42 +545,74 @@ cudaError_t refine_transpose_f64(const double* src, int64_t lds, double* dst, in
                                  int64_t rows, int64_t cols, cudaStream_t s) {
     return launch_transpose<double, double>(src, lds, dst, ldd, rows, cols, 1.0, s);
 }
-cudaError_t refine_split(const double* x, int64_t ldx, float* xh, float* xl, int64_t ld,
-                         int64_t m, int64_t n, cudaStream_t s) {
-    if (m <= 0 || n <= 0) return cudaSuccess;
-    split_kernel<<<grid_for(m * n), kThreads, 0, s>>>(x, ldx, xh, xl, ld, m, n);
+size_t refine_pack_a_bytes(int64_t k, bool lower) {
+    if (k <= 0) return 0;
+    const int64_t nrt = (k + kRM - 1) / kRM, K16 = (k + 15) / 16;
+    int64_t first, count, offset;
+    tile_chunks(nrt - 1, K16, lower, first, count, offset);
+    return (size_t)(offset + count) * kABytes;
+}
+size_t refine_pack_x_bytes(int64_t k, int64_t n) {
+    if (k <= 0 || n <= 0) return 0;
+    return (size_t)((n + kRN - 1) / kRN) * (size_t)((k + 15) / 16 * 16) * 32 * 16;
+}
+cudaError_t refine_pack_a(const float* A, int64_t lda, int64_t k, bool lower, bool trans,
+                          bool unit, void* Ap, cudaStream_t s) {
+    if (k <= 0) return cudaSuccess;
+    const int64_t nrt = (k + kRM - 1) / kRM, K16 = (k + 15) / 16;
+    if (nrt > 65535 || 4 * K16 > 0x7fffffff) return cudaErrorInvalidValue;
+    const dim3 grid((unsigned)(4 * K16), (unsigned)nrt);
+    if (trans)
+        pack_a_kernel<true><<<grid, 256, 0, s>>>(A, lda, k, lower, unit,
+                                                 static_cast<float4*>(Ap));
+    else
+        pack_a_kernel<false><<<grid, 256, 0, s>>>(A, lda, k, lower, unit,
+                                                  static_cast<float4*>(Ap));
     return cudaGetLastError();
 }
-template <bool TRANS>
-void launch_residual(int mode, unsigned blocks, const float* A, int64_t lda, int64_t k, bool lower,
-                     bool unit, const float* Xh, const float* Xl, int64_t ldx, const double* B,
-                     int64_t ldb, double* R, int64_t ldr, int64_t n, cudaStream_t s) {
-    if (mode == kFull)
-        residual_df_kernel<TRANS, kFull><<<blocks, 256, 0, s>>>(A, lda, k, lower, unit, Xh, Xl,
-                                                                ldx, B, ldb, R, ldr, n);
-    else if (mode == kSingle)
-        residual_df_kernel<TRANS, kSingle><<<blocks, 256, 0, s>>>(A, lda, k, lower, unit, Xh, Xl,
-                                                                  ldx, B, ldb, R, ldr, n);
-    else
-        residual_df_kernel<TRANS, kPlain><<<blocks, 256, 0, s>>>(A, lda, k, lower, unit, Xh, Xl,
-                                                                 ldx, B, ldb, R, ldr, n);
-}
-cudaError_t refine_residual_df(int mode, const float* A, int64_t lda, int64_t k, bool lower,
-                               bool trans, bool unit, const float* Xh, const float* Xl,
-                               int64_t ldx, const double* B, int64_t ldb, double* R, int64_t ldr,
-                               int64_t n, cudaStream_t s) {
+cudaError_t refine_pack_x(const double* X64, const float* X32, int64_t ldx, int64_t k,
+                          int64_t n, void* Xp, cudaStream_t s) {
     if (k <= 0 || n <= 0) return cudaSuccess;
-    if (mode < kFull || mode > kPlain || (mode == kFull && Xl == nullptr))
-        return cudaErrorInvalidValue;
+    const int64_t rows = (k + 15) / 16 * 16, nct = (n + kRN - 1) / kRN;
+    if (nct > 65535 || rows > 0x7fffffff) return cudaErrorInvalidValue;
+    const dim3 grid((unsigned)rows, (unsigned)nct);
+    if (X64)
+        pack_x_kernel<true><<<grid, 32, 0, s>>>(X64, nullptr, ldx, k, n, rows,
+                                                static_cast<float4*>(Xp));
+    else
+        pack_x_kernel<false><<<grid, 32, 0, s>>>(nullptr, X32, ldx, k, n, rows,
+                                                 static_cast<float4*>(Xp));
+    return cudaGetLastError();
+}
+template <int MODE>
+cudaError_t launch_pipe(unsigned blocks, const void* Ap, const void* Xp, int64_t rows, int64_t k,
+                        bool lower, const double* B, int64_t ldb, double* R, int64_t ldr,
+                        int64_t n, int* err, long long wait_ns, cudaStream_t s) {
+    static cudaError_t configured = cudaFuncSetAttribute(
+        residual_pipe_kernel<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, kPipeSmem);
+    if (configured != cudaSuccess) return configured;
+    residual_pipe_kernel<MODE><<<blocks, 256, kPipeSmem, s>>>(
+        static_cast<const float4*>(Ap), static_cast<const float4*>(Xp), rows, k, lower, B, ldb,
+        R, ldr, n, err, wait_ns);
+    return cudaGetLastError();
+}
+cudaError_t refine_residual_packed(int mode, const void* Ap, const void* Xp, int64_t k,
+                                   bool lower, const double* B, int64_t ldb, double* R,
+                                   int64_t ldr, int64_t n, int* err, long long wait_ns,
+                                   cudaStream_t s) {
+    if (k <= 0 || n <= 0) return cudaSuccess;
+    if (mode < kFull || mode > kPlain) return cudaErrorInvalidValue;
     const int64_t blocks = ((k + kRM - 1) / kRM) * ((n + kRN - 1) / kRN);
     if (blocks > 0x7fffffff) return cudaErrorInvalidValue;
-    if (trans)
-        launch_residual<true>(mode, (unsigned)blocks, A, lda, k, lower, unit, Xh, Xl, ldx, B, ldb,
-                              R, ldr, n, s);
-    else
-        launch_residual<false>(mode, (unsigned)blocks, A, lda, k, lower, unit, Xh, Xl, ldx, B,
-                               ldb, R, ldr, n, s);
-    return cudaGetLastError();
+    const int64_t rows = (k + 15) / 16 * 16;
+    if (mode == kFull)
+        return launch_pipe<kFull>((unsigned)blocks, Ap, Xp, rows, k, lower, B, ldb, R, ldr, n, err,
+                                  wait_ns, s);
+    if (mode == kSingle)
+        return launch_pipe<kSingle>((unsigned)blocks, Ap, Xp, rows, k, lower, B, ldb, R, ldr, n,
+                                    err, wait_ns, s);
+    return launch_pipe<kPlain>((unsigned)blocks, Ap, Xp, rows, k, lower, B, ldb, R, ldr, n, err,
+                               wait_ns, s);
 }
 // out[0] := ||D||_inf (rows) or max column sum (by_cols) of an FP32 array.
 __global__ void __launch_bounds__(kThreads) row_abs_sum_f32_kernel(const float* a, int64_t lda,
