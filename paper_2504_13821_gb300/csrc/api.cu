@@ -1036,7 +1036,12 @@ int trx_strsm_refined(trx_handle_t h, char side, char uplo, char transa, char di
     const size_t a64 = fp64_residual ? align256((size_t)k * k * 8) : 0;
     const size_t ap = fp64_residual ? 0 : align256(refine_pack_a_bytes(k, lowerI));
     const size_t xp = fp64_residual ? 0 : align256(refine_pack_x_bytes(k, nr));
-    const size_t need = 3 * mn64 + mn32 + sums + 256 + a64 + ap + xp;
+    std::vector<int4> units, tiles;
+    int64_t slots = 0;
+    if (!fp64_residual) refine_plan_units(k, lowerI, units, tiles, slots);
+    const size_t ub = align256((units.size() + tiles.size()) * sizeof(int4));
+    const size_t pb = align256((size_t)slots * 64 * (size_t)nr * 8);
+    const size_t need = 3 * mn64 + mn32 + sums + 256 + a64 + ap + xp + ub + pb;
     if (h->rf_bytes < need) {
         if (h->rf_buf) {
             cudaStreamSynchronize(s);
@@ -1061,6 +1066,9 @@ int trx_strsm_refined(trx_handle_t h, char side, char uplo, char transa, char di
     double* A64 = fp64_residual ? reinterpret_cast<double*>(tail) : nullptr;
     void* Ap = fp64_residual ? nullptr : tail;
     void* Xp = fp64_residual ? nullptr : tail + ap;
+    int4* Ud = fp64_residual ? nullptr : reinterpret_cast<int4*>(tail + ap + xp);
+    int4* Td = Ud ? Ud + units.size() : nullptr;
+    double* part = fp64_residual ? nullptr : reinterpret_cast<double*>(tail + ap + xp + ub);
     // infinity norms of the caller's m x n arrays: row sums of the internal
     // k x nr array for side L, column sums for side R
     auto norm = [&](const double* a, double* out) {
@@ -1083,6 +1091,14 @@ int trx_strsm_refined(trx_handle_t h, char side, char uplo, char transa, char di
         (!fp64_residual &&
          (e = refine_pack_a(A, lda, k, lowerI, transI == 'T', unit, Ap, s)) != cudaSuccess))
         return fail_cuda(e, "refine setup");
+    if (!fp64_residual) {
+        // the work-unit table (pageable source: staged before the call returns)
+        std::vector<int4> table(units);
+        table.insert(table.end(), tiles.begin(), tiles.end());
+        if ((e = cudaMemcpyAsync(Ud, table.data(), table.size() * sizeof(int4),
+                                 cudaMemcpyHostToDevice, s)) != cudaSuccess)
+            return fail_cuda(e, "refine setup");
+    }
     // ||op(A)||_inf of the caller's op(A): row sums of op(A) with its own flag
     e = refine_op_norm_inf(A, lda, k, lower, trans, unit, sm, norms, s);
     if (e != cudaSuccess) return fail_cuda(e, "refine norm");
@@ -1105,8 +1121,9 @@ int trx_strsm_refined(trx_handle_t h, char side, char uplo, char transa, char di
             // from X = xh + xl, float-float
             e = refine_pack_x(Xi, nullptr, k, k, nr, Xp, s);
             if (e == cudaSuccess)
-                e = refine_residual_packed(0, Ap, Xp, k, lowerI, B64, k, R64, k, nr, h->d_err,
-                                           h->wait_ns, s);
+                e = refine_residual_packed(0, Ap, Xp, Ud, (int64_t)units.size(), Td,
+                                           (int64_t)tiles.size(), part, k, lowerI, B64, k, R64, k,
+                                           nr, h->d_err, h->wait_ns, s);
         } else {
             // updated by the last correction D (one float plane, D32):
             // R := R - op(A) D. The update's rounding is relative to
@@ -1118,8 +1135,9 @@ int trx_strsm_refined(trx_handle_t h, char side, char uplo, char transa, char di
             const int mode = (std::sqrt((double)k) * 0x1p-24 * rho <= tol / 8) ? 2 : 1;
             e = refine_pack_x(nullptr, D32, k, k, nr, Xp, s);
             if (e == cudaSuccess)
-                e = refine_residual_packed(mode, Ap, Xp, k, lowerI, R64, k, R64, k, nr, h->d_err,
-                                           h->wait_ns, s);
+                e = refine_residual_packed(mode, Ap, Xp, Ud, (int64_t)units.size(), Td,
+                                           (int64_t)tiles.size(), part, k, lowerI, R64, k, R64, k,
+                                           nr, h->d_err, h->wait_ns, s);
         }
         if (e != cudaSuccess || (e = norm(R64, norms + 1)) != cudaSuccess ||
             (it == 0 && (e = norm(Xi, norms + 2)) != cudaSuccess) ||

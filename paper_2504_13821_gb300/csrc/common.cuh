@@ -23,6 +23,7 @@
 #include <stdint.h>
 
 #include <utility>
+#include <vector>
 
 namespace trx {
 
@@ -170,10 +171,16 @@ cudaError_t refine_pack_a(const float* A, int64_t lda, int64_t k, bool lower, bo
                           bool unit, void* Ap, cudaStream_t s);
 cudaError_t refine_pack_x(const double* X64, const float* X32, int64_t ldx, int64_t k,
                           int64_t n, void* Xp, cudaStream_t s);
-cudaError_t refine_residual_packed(int mode, const void* Ap, const void* Xp, int64_t k,
-                                   bool lower, const double* B, int64_t ldb, double* R,
-                                   int64_t ldr, int64_t n, int* err, long long wait_ns,
-                                   cudaStream_t s);
+// Work units of the residual (row-tile pieces, heaviest first) and the row
+// tiles whose pieces refine_residual_packed combines; slots = partial
+// blocks of 64 x n doubles the pieces write.
+void refine_plan_units(int64_t k, bool lower, std::vector<int4>& units, std::vector<int4>& tiles,
+                       int64_t& slots);
+cudaError_t refine_residual_packed(int mode, const void* Ap, const void* Xp, const void* units,
+                                   int64_t nunits, const void* tiles, int64_t ntiles,
+                                   double* part, int64_t k, bool lower, const double* B,
+                                   int64_t ldb, double* R, int64_t ldr, int64_t n, int* err,
+                                   long long wait_ns, cudaStream_t s);
 cudaError_t refine_norm_f32(const float* a, int64_t lda, int64_t m, int64_t n, bool by_cols,
                             double* sums, double* out, cudaStream_t s);
 cudaError_t refine_norm_one(const double* a, int64_t lda, int64_t m, int64_t n, double* sums,

@@ -2,6 +2,9 @@
 // refinement in FP64 around the FP32 solve): precision casts, the residual
 // R = alpha B - op(A) X, the correction X += D, and the infinity norms that
 // decide when to stop. All column-major, leading dimensions in elements.
+#include <algorithm>
+#include <vector>
+
 #include "common.cuh"
 #include "trx.h"
 
@@ -351,27 +354,38 @@ __global__ void __launch_bounds__(32) pack_x_kernel(const double* X64, const flo
     Xp[(ct * rows + l) * 32 + t] = v;
 }
 
+// Work units: a row tile's chunks are cut into pieces of at most
+// kUnitChunks, so no CTA carries much more than its share of the triangle
+// (the last row tile alone is k / 16 chunks). Unit = (row tile, first
+// chunk, end chunk, partial slot): slot -1 writes R directly, otherwise the
+// piece's sum goes to partial slot `slot` and refine_combine adds the
+// pieces of a row tile in a fixed order (bitwise repeatable).
+constexpr int kUnitChunks = 128;
+
 template <int MODE>
 __global__ void __launch_bounds__(256) residual_pipe_kernel(const float4* __restrict__ Ap,
                                                             const float4* __restrict__ Xp,
-                                                            int64_t rows, int64_t k, int lower,
-                                                            const double* B, int64_t ldb,
-                                                            double* R, int64_t ldr, int64_t n,
-                                                            int* err, long long wait_ns) {
+                                                            const int4* __restrict__ units,
+                                                            double* part, int64_t rows, int64_t k,
+                                                            int lower, const double* B,
+                                                            int64_t ldb, double* R, int64_t ldr,
+                                                            int64_t n, int* err,
+                                                            long long wait_ns) {
     extern __shared__ __align__(128) unsigned char smem[];
     uint64_t* full = reinterpret_cast<uint64_t*>(smem + kStages * kStageBytes);
     uint64_t* empty = full + kStages;
     volatile int* abort = reinterpret_cast<volatile int*>(empty + kStages);
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4, lane = tid & 31;
-    const int64_t nrt = (k + kRM - 1) / kRM, nct = (n + kRN - 1) / kRN, K16 = (k + 15) / 16;
-    const int64_t rt_raw = blockIdx.x / nct, ct = blockIdx.x % nct;
-    // heaviest row tiles first: the last ones when lower, the first when upper
-    const int64_t rt = lower ? nrt - 1 - rt_raw : rt_raw;
+    const int64_t nct = (n + kRN - 1) / kRN, K16 = (k + 15) / 16;
+    const int4 u = units[blockIdx.x / nct];      // units are sorted heaviest first
+    const int64_t ct = blockIdx.x % nct, rt = u.x;
     const int64_t i0 = rt * kRM, j0 = ct * kRN;
     int64_t first, count, offset;
     tile_chunks(rt, K16, lower != 0, first, count, offset);
-    const float4* a_src = Ap + offset * (kRK * kRM);
-    const float4* x_src = Xp + (ct * rows + first * kRK) * 32;
+    // this unit: chunks u.y .. u.z - 1 of the row tile
+    const float4* a_src = Ap + (offset + u.y) * (kRK * kRM);
+    const float4* x_src = Xp + (ct * rows + (first + u.y) * kRK) * 32;
+    count = u.z - u.y;
     const uint64_t limit = (uint64_t)wait_ns;
 
     if (tid == 0) {
@@ -485,12 +499,30 @@ __global__ void __launch_bounds__(256) residual_pipe_kernel(const float4* __rest
 #pragma unroll
             for (int w = 0; w < 2; ++w) {
                 const int64_t j = j0 + tx + 32 * c + 16 * w;
-                if (j < n)
-                    R[gi + j * ldr] = B[gi + j * ldb] -
-                                      ((double)h[w] + ((double)m[w] + ((double)sm[w] + (double)t[w])));
+                if (j >= n) continue;
+                const double sum = (double)h[w] + ((double)m[w] + ((double)sm[w] + (double)t[w]));
+                if (u.w < 0)
+                    R[gi + j * ldr] = B[gi + j * ldb] - sum;
+                else
+                    part[((int64_t)u.w * n + j) * kRM + (ty + 16 * r)] = sum;
             }
         }
     }
+}
+
+// R := B - (sum of a row tile's pieces), for the row tiles cut into more
+// than one piece: tiles[y] = (row tile, first partial slot, pieces).
+__global__ void __launch_bounds__(256) combine_kernel(const int4* tiles, const double* part,
+                                                      int64_t k, int64_t n, const double* B,
+                                                      int64_t ldb, double* R, int64_t ldr) {
+    const int4 t = tiles[blockIdx.y];
+    const int64_t e = (int64_t)blockIdx.x * 256 + threadIdx.x;
+    if (e >= (int64_t)kRM * n) return;
+    const int64_t il = e % kRM, j = e / kRM, gi = (int64_t)t.x * kRM + il;
+    if (gi >= k) return;
+    double sum = 0.0;
+    for (int p = 0; p < t.z; ++p) sum += part[((int64_t)(t.y + p) * n + j) * kRM + il];
+    R[gi + j * ldr] = B[gi + j * ldb] - sum;
 }
 
 int grid_for(int64_t count) {
@@ -584,35 +616,73 @@ cudaError_t refine_pack_x(const double* X64, const float* X32, int64_t ldx, int6
                                                  static_cast<float4*>(Xp));
     return cudaGetLastError();
 }
+void refine_plan_units(int64_t k, bool lower, std::vector<int4>& units,
+                       std::vector<int4>& tiles, int64_t& slots) {
+    units.clear();
+    tiles.clear();
+    slots = 0;
+    if (k <= 0) return;
+    const int64_t nrt = (k + kRM - 1) / kRM, K16 = (k + 15) / 16;
+    for (int64_t rt = 0; rt < nrt; ++rt) {
+        int64_t first, count, offset;
+        tile_chunks(rt, K16, lower, first, count, offset);
+        const int64_t pieces = (count + kUnitChunks - 1) / kUnitChunks;
+        if (pieces == 1) {
+            units.push_back(make_int4((int)rt, 0, (int)count, -1));
+            continue;
+        }
+        tiles.push_back(make_int4((int)rt, (int)slots, (int)pieces, 0));
+        for (int64_t p = 0; p < pieces; ++p) {
+            const int64_t q0 = count * p / pieces, q1 = count * (p + 1) / pieces;
+            units.push_back(make_int4((int)rt, (int)q0, (int)q1, (int)(slots + p)));
+        }
+        slots += pieces;
+    }
+    // heaviest first, ties by row tile, so the grid drains evenly
+    std::stable_sort(units.begin(), units.end(), [](const int4& a, const int4& b) {
+        return (a.z - a.y) > (b.z - b.y);
+    });
+}
 template <int MODE>
-cudaError_t launch_pipe(unsigned blocks, const void* Ap, const void* Xp, int64_t rows, int64_t k,
-                        bool lower, const double* B, int64_t ldb, double* R, int64_t ldr,
-                        int64_t n, int* err, long long wait_ns, cudaStream_t s) {
+cudaError_t launch_pipe(unsigned blocks, const void* Ap, const void* Xp, const int4* units,
+                        double* part, int64_t rows, int64_t k, bool lower, const double* B,
+                        int64_t ldb, double* R, int64_t ldr, int64_t n, int* err,
+                        long long wait_ns, cudaStream_t s) {
     static cudaError_t configured = cudaFuncSetAttribute(
         residual_pipe_kernel<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, kPipeSmem);
     if (configured != cudaSuccess) return configured;
     residual_pipe_kernel<MODE><<<blocks, 256, kPipeSmem, s>>>(
-        static_cast<const float4*>(Ap), static_cast<const float4*>(Xp), rows, k, lower, B, ldb,
-        R, ldr, n, err, wait_ns);
+        static_cast<const float4*>(Ap), static_cast<const float4*>(Xp), units, part, rows, k,
+        lower, B, ldb, R, ldr, n, err, wait_ns);
     return cudaGetLastError();
 }
-cudaError_t refine_residual_packed(int mode, const void* Ap, const void* Xp, int64_t k,
-                                   bool lower, const double* B, int64_t ldb, double* R,
-                                   int64_t ldr, int64_t n, int* err, long long wait_ns,
-                                   cudaStream_t s) {
+cudaError_t refine_residual_packed(int mode, const void* Ap, const void* Xp, const void* units,
+                                   int64_t nunits, const void* tiles, int64_t ntiles,
+                                   double* part, int64_t k, bool lower, const double* B,
+                                   int64_t ldb, double* R, int64_t ldr, int64_t n, int* err,
+                                   long long wait_ns, cudaStream_t s) {
     if (k <= 0 || n <= 0) return cudaSuccess;
     if (mode < kFull || mode > kPlain) return cudaErrorInvalidValue;
-    const int64_t blocks = ((k + kRM - 1) / kRM) * ((n + kRN - 1) / kRN);
-    if (blocks > 0x7fffffff) return cudaErrorInvalidValue;
+    const int64_t nct = (n + kRN - 1) / kRN, blocks = nunits * nct;
+    if (blocks > 0x7fffffff || ntiles > 65535) return cudaErrorInvalidValue;
     const int64_t rows = (k + 15) / 16 * 16;
+    const int4* u = static_cast<const int4*>(units);
+    cudaError_t e;
     if (mode == kFull)
-        return launch_pipe<kFull>((unsigned)blocks, Ap, Xp, rows, k, lower, B, ldb, R, ldr, n, err,
-                                  wait_ns, s);
-    if (mode == kSingle)
-        return launch_pipe<kSingle>((unsigned)blocks, Ap, Xp, rows, k, lower, B, ldb, R, ldr, n,
-                                    err, wait_ns, s);
-    return launch_pipe<kPlain>((unsigned)blocks, Ap, Xp, rows, k, lower, B, ldb, R, ldr, n, err,
-                               wait_ns, s);
+        e = launch_pipe<kFull>((unsigned)blocks, Ap, Xp, u, part, rows, k, lower, B, ldb, R, ldr,
+                               n, err, wait_ns, s);
+    else if (mode == kSingle)
+        e = launch_pipe<kSingle>((unsigned)blocks, Ap, Xp, u, part, rows, k, lower, B, ldb, R,
+                                 ldr, n, err, wait_ns, s);
+    else
+        e = launch_pipe<kPlain>((unsigned)blocks, Ap, Xp, u, part, rows, k, lower, B, ldb, R, ldr,
+                                n, err, wait_ns, s);
+    if (e != cudaSuccess || ntiles == 0) return e;
+    const int64_t gx = (kRM * n + 255) / 256;
+    if (gx > 0x7fffffff) return cudaErrorInvalidValue;
+    combine_kernel<<<dim3((unsigned)gx, (unsigned)ntiles), 256, 0, s>>>(
+        static_cast<const int4*>(tiles), part, k, n, B, ldb, R, ldr);
+    return cudaGetLastError();
 }
 // out[0] := ||D||_inf (rows) or max column sum (by_cols) of an FP32 array.
 __global__ void __launch_bounds__(kThreads) row_abs_sum_f32_kernel(const float* a, int64_t lda,
