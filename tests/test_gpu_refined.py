@@ -196,3 +196,28 @@ def test_refined_zero_tolerance_stops_on_stagnation(trx):
                                      np.asfortranarray(X.cpu().numpy()),
                                      B.astype(np.float64))["eta"]
     assert eta <= 8 * k * U64, (eta, info)
+
+
+@pytest.mark.parametrize("side,uplo,trans,diag", [("L", "L", "N", "N"), ("L", "U", "N", "N"),
+                                                  ("R", "L", "T", "U"), ("R", "U", "N", "N")])
+def test_refined_cut_row_tiles(trx, side, uplo, trans, diag):
+    """Order 2200: the longest 64-row tiles of the float-float residual span
+    138 chunks of 16 columns and are cut into two pieces whose partial sums
+    are combined. The first residual (max_iter = 0) must match the oracle's
+    to 2^-40 ||op(A)|| ||X||, and the refined result must have an FP64-level
+    backward error, for effectively lower and upper op(A)."""
+    k, nr = 2200, 45
+    m, n = (k, nr) if side == "L" else (nr, k)
+    seed = inputs.variant_seed(k, VARIANTS.index((side, uplo, trans, diag)))
+    A, B = inputs.problem(side, uplo, m, n, seed=seed, dtype=np.float32, scale=40.0,
+                          poison_diag=(diag == "U"))
+    At, Bt = to_dev(A, "cuda:0"), to_dev(B, "cuda:0")
+    A64, B64 = np.asfortranarray(A.astype(np.float64)), np.asfortranarray(B.astype(np.float64))
+    X0, i0 = trx.trsm_refined(side, uplo, trans, diag, 0.5, At, Bt, max_iter=0)
+    ref = oracle.trsm_backward_error(side, uplo, trans, diag, 0.5, A64,
+                                     np.asfortranarray(X0.cpu().numpy()), B64)
+    assert abs(i0["residual_norm"] - ref["res"]) <= 2.0 ** -40 * ref["norm_a"] * ref["norm_x"]
+    X, info = trx.trsm_refined(side, uplo, trans, diag, 0.5, At, Bt)
+    eta = oracle.trsm_backward_error(side, uplo, trans, diag, 0.5, A64,
+                                     np.asfortranarray(X.cpu().numpy()), B64)["eta"]
+    assert eta <= 8 * k * U64, (eta, info)
