@@ -215,6 +215,18 @@ typedef struct {
 int trx_batched(trx_handle_t handle, int elem_bytes, int64_t count,
                 const trx_problem_t* problems, void* stream);
 
+/* The same with one operation and element type per call: every problem's
+ * op must be 'S' (the trsm entry points) or 'M' (the trmm ones), else
+ * TRX_ERR_INVALID_VALUE and nothing is enqueued; s = FP32, d = FP64. */
+int trx_strsm_batched(trx_handle_t handle, int64_t count, const trx_problem_t* problems,
+                      void* stream);
+int trx_dtrsm_batched(trx_handle_t handle, int64_t count, const trx_problem_t* problems,
+                      void* stream);
+int trx_strmm_batched(trx_handle_t handle, int64_t count, const trx_problem_t* problems,
+                      void* stream);
+int trx_dtrmm_batched(trx_handle_t handle, int64_t count, const trx_problem_t* problems,
+                      void* stream);
+
 /* Refined FP32 TRSM (the precision form): the FP32 solve of trx_strsm, then
  * iterative refinement towards an FP64-accurate X: the residual
  * R = alpha B - op(A) X with more than FP32 precision (TRX_OPT_RESIDUAL:

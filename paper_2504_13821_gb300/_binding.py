@@ -104,6 +104,9 @@ def load_library() -> ctypes.CDLL:
         lib.trx_sgemm_update.argtypes = [vp, i64, i64, i64, ctypes.c_float, ctypes.c_float,
                                          vp, i64, vp, i64, vp, i64, ctypes.c_int, vp]
         lib.trx_batched.argtypes = [vp, ctypes.c_int, i64, ctypes.POINTER(Problem), vp]
+        for name in ("trx_strsm_batched", "trx_dtrsm_batched", "trx_strmm_batched",
+                     "trx_dtrmm_batched"):
+            getattr(lib, name).argtypes = [vp, i64, ctypes.POINTER(Problem), vp]
         lib.trx_batch_create.argtypes = [vp, ctypes.c_int, i64, ctypes.POINTER(Problem),
                                          ctypes.POINTER(vp)]
         lib.trx_sfactor_create.argtypes = [vp, c, c, c, c, i64, vp, i64, vp, ctypes.POINTER(vp)]

@@ -799,6 +799,32 @@ int trx_batched(trx_handle_t h, int elem_bytes, int64_t count, const trx_problem
     return batch_run(h, elem_bytes, d, reinterpret_cast<cudaStream_t>(stream), h->opt_graph != 0);
 }
 
+// One operation and element type per call: the problems' op must be the
+// entry point's ('S' for TRSM, 'M' for TRMM); then as trx_batched.
+static int batched_typed(trx_handle_t h, char op, int elem_bytes, int64_t count,
+                         const trx_problem_t* problems, void* stream) {
+    if (count < 0 || (count > 0 && !problems)) return TRX_ERR_INVALID_VALUE;
+    for (int64_t i = 0; i < count; ++i)
+        if (upc(problems[i].op) != op) {
+            snprintf(g_detail, sizeof(g_detail), "problem %lld: op '%c' in a %s batch",
+                     (long long)i, problems[i].op, op == 'S' ? "TRSM" : "TRMM");
+            return TRX_ERR_INVALID_VALUE;
+        }
+    return trx_batched(h, elem_bytes, count, problems, stream);
+}
+int trx_strsm_batched(trx_handle_t h, int64_t count, const trx_problem_t* problems, void* stream) {
+    return batched_typed(h, 'S', 4, count, problems, stream);
+}
+int trx_dtrsm_batched(trx_handle_t h, int64_t count, const trx_problem_t* problems, void* stream) {
+    return batched_typed(h, 'S', 8, count, problems, stream);
+}
+int trx_strmm_batched(trx_handle_t h, int64_t count, const trx_problem_t* problems, void* stream) {
+    return batched_typed(h, 'M', 4, count, problems, stream);
+}
+int trx_dtrmm_batched(trx_handle_t h, int64_t count, const trx_problem_t* problems, void* stream) {
+    return batched_typed(h, 'M', 8, count, problems, stream);
+}
+
 int trx_batched_autotune(trx_handle_t h, int elem_bytes, int64_t count,
                          const trx_problem_t* problems, void* stream, char* json,
                          size_t json_len) {

@@ -177,3 +177,19 @@ def test_server_create_fails_cleanly_without_gpu(lib):
     assert lib.trx_server_create(0, None, ctypes.byref(s)) != 0 and not s.value
     cfg = _binding.ServerConfig(0, 512, 16, 1 << 20, 0, 1)      # zero streams
     assert lib.trx_server_create(0, ctypes.byref(cfg), ctypes.byref(s)) == 7
+
+
+def test_typed_batched_calls_check_the_operation(lib):
+    import ctypes
+    probs = (_binding.Problem * 2)()
+    for p, op in zip(probs, (b"S", b"M")):
+        p.op, p.side, p.uplo, p.transa, p.diag = op, b"L", b"L", b"N", b"N"
+    # a mixed batch is refused by every typed entry point before the handle
+    for name in ("trx_strsm_batched", "trx_dtrsm_batched", "trx_strmm_batched",
+                 "trx_dtrmm_batched"):
+        assert getattr(lib, name)(None, 2, probs, None) == 7
+        assert getattr(lib, name)(None, -1, probs, None) == 7
+    # a uniform batch passes the checks; then the missing handle is reported
+    assert lib.trx_strsm_batched(None, 1, probs, None) == 1
+    assert lib.trx_strmm_batched(None, 1, probs, None) == 7
+    assert lib.trx_dtrmm_batched(None, 0, None, None) == 1

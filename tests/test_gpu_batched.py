@@ -112,3 +112,27 @@ def test_prepared_batch_equals_one_shot_and_reruns():
     check(probs, host, np.float32)
     batch.close()
     h.close()
+
+
+@pytest.mark.parametrize("dtype", [np.float32, np.float64], ids=["f32", "f64"])
+def test_typed_batched_entry_points_equal_mixed_call(dtype):
+    """trx_{s,d}{trsm,trmm}_batched on a one-operation batch give the same
+    bits as trx_batched on the same problems."""
+    import paper_2504_13821_gb300 as trx
+    from paper_2504_13821_gb300 import _binding
+    lib = _binding.load_library()
+    dev = torch.device("cuda", 0)
+    h = trx.Handle(dev)
+    pre = "trx_s" if dtype == np.float32 else "trx_d"
+    for op, name in (("S", pre + "trsm_batched"), ("M", pre + "trmm_batched")):
+        probs, _ = make_batch(60, dtype, seed=11, dev=dev)
+        probs = [(op,) + p[1:] for p in probs]
+        twin = [p[:7] + (p[7].clone(),) for p in probs]
+        arr, elem = _binding._problem_array(probs)
+        s = torch.cuda.current_stream(dev).cuda_stream
+        assert getattr(lib, name)(h.ptr, len(probs), arr, s) == 0
+        trx.batched(twin, handle=h)
+        torch.cuda.synchronize()
+        for p, q in zip(probs, twin):
+            assert torch.equal(p[7], q[7])
+    h.close()
