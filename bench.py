@@ -264,6 +264,10 @@ def run_gpu(args):
         h.set_option(trx.OPT_LEAF, args.leaf)
         global LEAF_USED
         LEAF_USED = args.leaf
+    if args.tc_leaf:
+        h.set_option(trx.OPT_TRSM_TC_LEAF, 1)
+        LEAF_USED = (f"TRSM {args.leaf or 128} as inverse GEMMs on the tensor cores, "
+                     "TRMM 1024-row diagonal blocks on the tensor cores")
     stream = torch.cuda.current_stream(dev)
     # FP32: the factor's operand planes are made once per step (update), then
     # the TRSM and the TRMM both use them. FP64 has no planes: plain calls.
@@ -776,6 +780,8 @@ def main(argv=None):
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
     ap.add_argument("--leaf", type=int, default=0, help="recursion cutoff b (0: library default)")
     ap.add_argument("--pdl", action="store_true", help="launch with programmatic dependent launch")
+    ap.add_argument("--tc-leaf", action="store_true",
+                    help="FP32 TRSM leaves as inverse GEMMs on the tensor cores")
     ap.add_argument("--panels", type=int, default=0, help="TRSM column-panel branches (0: auto)")
     ap.add_argument("--k", type=int, default=None,
                     help="order of A (default 16384, refined workload 8192; smaller only for "

@@ -105,6 +105,14 @@ enum {
                               floats, exact product split and two-sum,
                               about 2^-46 relative); 1: the library's FP64
                               TRMM on an FP64 copy of A (FP64 pipe)        */
+    TRX_OPT_TRSM_TC_LEAF = 10,/* FP32 TRSM on the tensor-core path, leaves of
+                              64 or 128 rows: 1 = each leaf as one GEMM,
+                              X = alpha inv(A_ii) B_i, with the diagonal
+                              blocks inverted in FP32 (substitution) once
+                              per call (per update of a prepared factor) and
+                              the leaf's input planes written by the
+                              preceding update's epilogue; -1 or 0
+                              (default): the substitution leaf kernels      */
 };
 
 /* Kernel classes reported by trx_get_profile(). */
@@ -413,11 +421,13 @@ const char* trx_last_error_detail(void);
  * line ("conv_m", "conv_y", "leaf ...", "gemm ..." with their row ranges in
  * the canonical lower-triangular order), for alpha = 2. elem_bytes 4 or 8,
  * leaf as TRX_OPT_LEAF, gemm_mode as TRX_OPT_GEMM, trmm_dense as
- * TRX_OPT_TRMM_DENSE, op 'S' (TRSM) or 'M' (TRMM). Returns an argument code,
+ * TRX_OPT_TRMM_DENSE, trsm_tc_leaf as TRX_OPT_TRSM_TC_LEAF, op 'S' (TRSM)
+ * or 'M' (TRMM). Returns an argument code,
  * TRX_ERR_INVALID_VALUE if buf is too small, or 0. */
 int trx_debug_plan(char op, char side, char uplo, char transa, char diag,
                    int64_t m, int64_t n, int elem_bytes, int leaf,
-                   int gemm_mode, int trmm_dense, char* buf, size_t buflen);
+                   int gemm_mode, int trmm_dense, int trsm_tc_leaf, char* buf,
+                   size_t buflen);
 
 /* Size of the static device scratch behind trx_strsm_noalloc (64 MiB). */
 #define TRX_NOALLOC_SCRATCH_BYTES ((size_t)64 << 20)

@@ -20,6 +20,7 @@ HEADER = os.path.join(os.path.dirname(_PKG), "include", "trx.h")
 OPT_LEAF, OPT_GEMM, OPT_GRAPH, OPT_PROFILE, OPT_WAIT_LIMIT, OPT_PDL, OPT_PANELS = 1, 2, 3, 4, 5, 6, 7
 OPT_TRMM_DENSE = 8
 OPT_RESIDUAL = 9
+OPT_TRSM_TC_LEAF = 10
 RESIDUAL_AUTO, RESIDUAL_FP64, RESIDUAL_FLOAT_FLOAT = 0, 1, 2
 GEMM_AUTO, GEMM_SIMT, GEMM_TC = 0, 1, 2
 KERNEL_CLASSES = ("leaf_trsm", "leaf_trmm", "gemm_tc", "gemm_simt", "convert", "other")
@@ -99,8 +100,8 @@ def load_library() -> ctypes.CDLL:
         lib.trx_last_error_detail.argtypes = []
         lib.trx_last_error_detail.restype = ctypes.c_char_p
         lib.trx_debug_plan.argtypes = [c, c, c, c, c, i64, i64, ctypes.c_int, ctypes.c_int,
-                                       ctypes.c_int, ctypes.c_int, ctypes.c_char_p,
-                                       ctypes.c_size_t]
+                                       ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                       ctypes.c_char_p, ctypes.c_size_t]
         lib.trx_sgemm_update.argtypes = [vp, i64, i64, i64, ctypes.c_float, ctypes.c_float,
                                          vp, i64, vp, i64, vp, i64, ctypes.c_int, vp]
         lib.trx_batched.argtypes = [vp, ctypes.c_int, i64, ctypes.POINTER(Problem), vp]
@@ -344,13 +345,14 @@ def trsm_refined(side: str, uplo: str, trans: str, diag: str, alpha: float, A, B
 
 
 def debug_plan(op: str, side, uplo, trans, diag, m, n, elem_bytes=4, leaf=0, gemm=0,
-               trmm_dense=0) -> list:
+               trmm_dense=0, trsm_tc_leaf=0) -> list:
     """The launch sequence the library would enqueue, parsed (host only, no
     GPU needed): a list of dicts with the step kind and its row ranges."""
     lib = load_library()
     buf = ctypes.create_string_buffer(1 << 22)
     rc = lib.trx_debug_plan(_char(op), _char(side), _char(uplo), _char(trans), _char(diag),
-                            m, n, elem_bytes, leaf, gemm, trmm_dense, buf, len(buf))
+                            m, n, elem_bytes, leaf, gemm, trmm_dense, trsm_tc_leaf, buf,
+                            len(buf))
     _check(rc, "trx_debug_plan")
     steps = []
     for line in buf.value.decode().splitlines():

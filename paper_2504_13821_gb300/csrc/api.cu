@@ -9,6 +9,7 @@
 // is index-reversed), so no variant needs its own kernels.
 #include <algorithm>
 #include <cmath>
+#include <type_traits>
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -186,6 +187,7 @@ struct trx_handle_s {
     int64_t opt_panels = 0;
     int64_t opt_trmm_dense = 0;
     int64_t opt_residual = 0;
+    int64_t opt_trsm_tc_leaf = 0;
     // refined TRSM scratch (grown on demand)
     void* rf_buf = nullptr;
     size_t rf_bytes = 0;
@@ -221,6 +223,11 @@ struct Exec {
     Canon<T> c;
     Planes pl;
     const void* maps = nullptr;
+    // inverted diagonal blocks (TRSM leaves on the tensor cores): their
+    // planes and the tensor maps over them and the Y planes
+    const void* maps_w = nullptr;
+    __nv_bfloat16* w_hi = nullptr;
+    __nv_bfloat16* w_lo = nullptr;
     cudaStream_t s;
     bool profile;
 
@@ -249,11 +256,18 @@ struct Exec {
                 }
                 case kGemm: {
                     if (st.tc) {
-                        e = launch_gemm_tc(*reinterpret_cast<const Canon<float>*>(&c), maps,
-                                           st.gemms.data(), (int)st.gemms.size(), (float)st.beta,
-                                           (float)st.gamma, h->d_err, h->wait_ns, h->num_sms, s,
-                                           st.dense);
-                        cls = TRX_KERNEL_GEMM_TC;
+                        TcYOut yo;
+                        yo.hi = pl.y_hi;
+                        yo.lo = pl.y_lo;
+                        yo.ld = pl.ldy;
+                        yo.row0 = st.y0;
+                        yo.row1 = st.y1;
+                        e = launch_gemm_tc(*reinterpret_cast<const Canon<float>*>(&c),
+                                           st.inv ? maps_w : maps, st.gemms.data(),
+                                           (int)st.gemms.size(), (float)st.beta, (float)st.gamma,
+                                           h->d_err, h->wait_ns, h->num_sms, s, st.dense,
+                                           st.y1 > st.y0 ? &yo : nullptr);
+                        cls = st.inv ? TRX_KERNEL_LEAF_TRSM : TRX_KERNEL_GEMM_TC;
                     } else {
                         for (const TcGemm& g : st.gemms) {
                             e = launch_gemm_simt<T>(c, c.C, c.c_rs, c.c_cs, g.rc, g.mlen, g.rk,
@@ -286,6 +300,18 @@ struct Exec {
                     cls = TRX_KERNEL_CONVERT;
                     bytes = 8.0 * c.k * c.nrhs;
                     break;
+                case kConvYRows:
+                    e = launch_convert_y_rows(*reinterpret_cast<const Canon<float>*>(&c), pl,
+                                              st.r0, st.b, s);
+                    cls = TRX_KERNEL_CONVERT;
+                    bytes = 8.0 * st.b * c.nrhs;
+                    break;
+                case kInvDiag:
+                    e = launch_invert_diag(*reinterpret_cast<const Canon<float>*>(&c), st.b, w_hi,
+                                           w_lo, pl.ldm, s);
+                    cls = TRX_KERNEL_CONVERT;
+                    bytes = 4.0 * c.k * st.b * 1.5;
+                    break;
             }
             if (e != cudaSuccess) return fail_cuda(e, "kernel launch");
             if (profile) {
@@ -306,7 +332,7 @@ struct GraphKey {
     const void* planes;
     double alpha;
     long long wait_ns;
-    int pdl, panels, dense;
+    int pdl, panels, dense, tc_leaf;
 };
 
 }  // namespace
@@ -322,6 +348,11 @@ struct trx_factor_s {
     __nv_bfloat16* m_hi = nullptr;   // null when k is too small for the tensor-core path
     __nv_bfloat16* m_lo = nullptr;
     int64_t ldm = 0;
+    // inverted diagonal blocks of w_block rows (TRSM leaves on the tensor
+    // cores), made by updates while the handle's TRX_OPT_TRSM_TC_LEAF is on
+    __nv_bfloat16* w_hi = nullptr;
+    __nv_bfloat16* w_lo = nullptr;
+    int w_block = 0;
 };
 
 namespace {
@@ -382,6 +413,17 @@ int execute(trx_handle_t h, bool trsm, char side, char uplo, char transa, char d
             ex.pl.y_lo = reinterpret_cast<__nv_bfloat16*>(base + 2 * w.m_bytes + w.y_bytes);
         }
     }
+    // TRSM leaves on the tensor cores: the inverted diagonal blocks sit in
+    // the M planes' own diagonal blocks (no TRSM update reads inside a leaf
+    // block) or, for a prepared factor, in the factor's W planes made for
+    // this leaf size (its M planes serve TRMM's diagonal blocks too).
+    plan.tc_leaf = std::is_same<T, float>::value && trsm &&
+                   tc_leaf_mode(h->opt_trsm_tc_leaf, plan.tc, b) &&
+                   (!factor_planes || (f->w_hi != nullptr && f->w_block == b));
+    if (plan.tc_leaf) {
+        ex.w_hi = factor_planes ? f->w_hi : ex.pl.m_hi;
+        ex.w_lo = factor_planes ? f->w_lo : ex.pl.m_lo;
+    }
     // TRSM right-hand sides are independent: with many of them the chain runs
     // as P column-panel branches (forked streams, one graph), so the
     // latency-bound bottom of the recursion of one panel overlaps the others'.
@@ -403,20 +445,35 @@ int execute(trx_handle_t h, bool trsm, char side, char uplo, char transa, char d
             if (plan.tc) {
                 x.pl.y_hi = ex.pl.y_hi + j0 * ex.pl.ldy;
                 x.pl.y_lo = ex.pl.y_lo + j0 * ex.pl.ldy;
-                maps[i].resize(tc_maps_size());
+                maps[i].resize(2 * tc_maps_size());
                 e = tc_make_maps(x.pl, k, x.c.nrhs, maps[i].data());
                 if (e != cudaSuccess) return fail_cuda(e, "tensor map encode");
                 x.maps = maps[i].data();
+                x.maps_w = x.maps;
+                if (plan.tc_leaf && ex.w_hi != ex.pl.m_hi) {
+                    Planes wp = x.pl;
+                    wp.m_hi = ex.w_hi;
+                    wp.m_lo = ex.w_lo;
+                    e = tc_make_maps(wp, k, x.c.nrhs, maps[i].data() + tc_maps_size());
+                    if (e != cudaSuccess) return fail_cuda(e, "tensor map encode");
+                    x.maps_w = maps[i].data() + tc_maps_size();
+                }
             }
         }
     }
     const int dense = trsm ? 0 : trmm_dense_mode(h->opt_trmm_dense, h->opt_leaf, plan.tc, k);
     Plan pre, body;
     pre.tc = body.tc = plan.tc;
+    body.tc_leaf = plan.tc_leaf;
     if (plan.tc && !factor_planes) {
         Step cm{kConvM};
         cm.b = dense;
         pre.steps.push_back(cm);
+        if (plan.tc_leaf) {
+            Step iv{kInvDiag};
+            iv.b = b;
+            pre.steps.push_back(iv);
+        }
     }
     make_plan(body, trsm, k, b, (double)alpha, /*conv_m=*/false, dense);
 
@@ -468,6 +525,7 @@ int execute(trx_handle_t h, bool trsm, char side, char uplo, char transa, char d
     key.alpha = (double)alpha;
     key.wait_ns = h->wait_ns;
     key.pdl = (int)h->opt_pdl;
+    key.tc_leaf = (int)plan.tc_leaf;
     key.panels = P;
     key.dense = dense;
     const std::string ks(reinterpret_cast<const char*>(&key), sizeof(key));
@@ -1284,6 +1342,27 @@ int trx_sfactor_update(trx_handle_t h, trx_factor_t f, const float* A, void* str
     }
     e = launch_convert_m(c, pl, kFactorDenseRows, s);
     if (e != cudaSuccess) return fail_cuda(e, "factor planes");
+    // inverted diagonal blocks for TRSM leaves on the tensor cores, at the
+    // leaf size FP32 TRSM calls on this factor take
+    const int wb = leaf_for(h->opt_leaf, f->k, true, 4, 0);
+    if (tc_leaf_mode(h->opt_trsm_tc_leaf, true, wb)) {
+        if (!f->w_hi) {
+            const WsLayout w = ws_layout(f->k, 0);
+            if ((e = cudaMalloc(&f->w_hi, w.m_bytes)) != cudaSuccess ||
+                (e = cudaMalloc(&f->w_lo, w.m_bytes)) != cudaSuccess) {
+                if (f->w_hi) cudaFree(f->w_hi);
+                f->w_hi = f->w_lo = nullptr;
+                snprintf(g_detail, sizeof(g_detail), "factor inverse planes: %s",
+                         cudaGetErrorString(e));
+                return TRX_ERR_ALLOC;
+            }
+        }
+        if ((e = launch_invert_diag(c, wb, f->w_hi, f->w_lo, f->ldm, s)) != cudaSuccess)
+            return fail_cuda(e, "factor inverse planes");
+        f->w_block = wb;
+    } else {
+        f->w_block = 0;               // stale inverses are not used
+    }
     if (h->opt_profile) {
         cudaEventRecord(e1, s);
         h->pending.push_back({TRX_KERNEL_CONVERT, 0.0, 8.0 * f->k * (f->k - 1) / 2, e0, e1});
@@ -1298,6 +1377,8 @@ int trx_factor_destroy(trx_factor_t f) {
     cudaDeviceSynchronize();
     if (f->m_hi) cudaFree(f->m_hi);
     if (f->m_lo) cudaFree(f->m_lo);
+    if (f->w_hi) cudaFree(f->w_hi);
+    if (f->w_lo) cudaFree(f->w_lo);
     f->magic = 0;
     delete f;
     return TRX_SUCCESS;
@@ -1433,6 +1514,10 @@ int trx_set_option(trx_handle_t h, int option, int64_t value) {
             if (value < 0 || value > 2) return TRX_ERR_INVALID_VALUE;
             h->opt_residual = value;
             break;
+        case TRX_OPT_TRSM_TC_LEAF:
+            if (value < -1 || value > 1) return TRX_ERR_INVALID_VALUE;
+            h->opt_trsm_tc_leaf = value;
+            break;
         default:
             return TRX_ERR_INVALID_VALUE;
     }
@@ -1452,6 +1537,7 @@ int trx_get_option(trx_handle_t h, int option, int64_t* value) {
         case TRX_OPT_PANELS: *value = h->opt_panels; break;
         case TRX_OPT_TRMM_DENSE: *value = h->opt_trmm_dense; break;
         case TRX_OPT_RESIDUAL: *value = h->opt_residual; break;
+        case TRX_OPT_TRSM_TC_LEAF: *value = h->opt_trsm_tc_leaf; break;
         default: return TRX_ERR_INVALID_VALUE;
     }
     return TRX_SUCCESS;
@@ -1517,8 +1603,8 @@ const char* trx_error_string(int code) {
 const char* trx_last_error_detail(void) { return g_detail; }
 
 int trx_debug_plan(char op, char side, char uplo, char transa, char diag, int64_t m, int64_t n,
-                   int elem_bytes, int leaf, int gemm_mode, int trmm_dense, char* buf,
-                   size_t buflen) {
+                   int elem_bytes, int leaf, int gemm_mode, int trmm_dense, int trsm_tc_leaf,
+                   char* buf, size_t buflen) {
     const int info = check_args(side, uplo, transa, diag, m, n, "", std::max<int64_t>(1, upc(side) == 'L' ? m : n),
                                 "", std::max<int64_t>(1, m));
     if (info) return info;
@@ -1527,7 +1613,8 @@ int trx_debug_plan(char op, char side, char uplo, char transa, char diag, int64_
         gemm_mode < 0 ||
         gemm_mode > 2 || !buf || buflen == 0 ||
         (trmm_dense != -1 && trmm_dense != 0 && trmm_dense != 64 && trmm_dense != 128 &&
-         trmm_dense != 256 && trmm_dense != 512 && trmm_dense != 1024 && trmm_dense != 2048))
+         trmm_dense != 256 && trmm_dense != 512 && trmm_dense != 1024 && trmm_dense != 2048) ||
+        trsm_tc_leaf < -1 || trsm_tc_leaf > 1)
         return TRX_ERR_INVALID_VALUE;
     buf[0] = 0;
     const int64_t k = upc(side) == 'L' ? m : n;
@@ -1537,6 +1624,7 @@ int trx_debug_plan(char op, char side, char uplo, char transa, char diag, int64_
     const int b = leaf_for(leaf, k, is_trsm, elem_bytes, nrhs);
     Plan plan;
     plan.tc = use_tc_mode(elem_bytes, gemm_mode, k, b);
+    plan.tc_leaf = is_trsm && elem_bytes == 4 && tc_leaf_mode(trsm_tc_leaf, plan.tc, b);
     const int dense = is_trsm ? 0 : trmm_dense_mode(trmm_dense, leaf, plan.tc, k);
     make_plan(plan, is_trsm, k, b, 2.0, true, dense);
     std::string out;
@@ -1548,6 +1636,14 @@ int trx_debug_plan(char op, char side, char uplo, char transa, char diag, int64_
                 out += line;
                 break;
             case kConvY: out += "conv_y\n"; break;
+            case kConvYRows:
+                snprintf(line, sizeof(line), "conv_y_rows r0=%lld b=%d\n", (long long)st.r0, st.b);
+                out += line;
+                break;
+            case kInvDiag:
+                snprintf(line, sizeof(line), "inv_diag b=%d\n", st.b);
+                out += line;
+                break;
             case kLeaf:
                 snprintf(line, sizeof(line), "leaf trsm=%d r0=%lld b=%d nleaves=%lld alpha=%.17g planes=%d\n",
                          (int)st.trsm, (long long)st.r0, st.b, (long long)st.nleaves, st.alpha,
@@ -1558,9 +1654,11 @@ int trx_debug_plan(char op, char side, char uplo, char transa, char diag, int64_
                 for (size_t i = 0; i < st.gemms.size(); ++i) {
                     const TcGemm& g = st.gemms[i];
                     snprintf(line, sizeof(line),
-                             "gemm tc=%d member=%zu rc=%lld mlen=%lld rk=%lld klen=%lld beta=%.17g gamma=%.17g dense=%d\n",
+                             "gemm tc=%d member=%zu rc=%lld mlen=%lld rk=%lld klen=%lld beta=%.17g "
+                             "gamma=%.17g dense=%d inv=%d y0=%lld y1=%lld\n",
                              (int)st.tc, i, (long long)g.rc, (long long)g.mlen, (long long)g.rk,
-                             (long long)g.klen, st.beta, st.gamma, (int)st.dense);
+                             (long long)g.klen, st.beta, st.gamma, (int)st.dense, (int)st.inv,
+                             (long long)st.y0, (long long)st.y1);
                     out += line;
                 }
                 break;

@@ -122,6 +122,14 @@ cudaError_t launch_convert_m(const Canon<float>& p, const Planes& pl, int diag_b
                              cudaStream_t s);
 // Split-BF16 planes of C rows [0,k), all columns (TRMM's original values).
 cudaError_t launch_convert_y(const Canon<float>& p, const Planes& pl, cudaStream_t s);
+// Y planes of C's rows [r0, r0 + rows) (r0 a multiple of 4).
+cudaError_t launch_convert_y_rows(const Canon<float>& p, const Planes& pl, int64_t r0,
+                                  int64_t rows, cudaStream_t s);
+// Inverses of the full b x b diagonal blocks of M (b <= 128) as split
+// planes at rows and columns [r0, r0 + b) of a row-major pair (leading
+// dimension ld), zeros above each block's diagonal.
+cudaError_t launch_invert_diag(const Canon<float>& p, int b, __nv_bfloat16* w_hi,
+                               __nv_bfloat16* w_lo, int64_t ld, cudaStream_t s);
 // Split-BF16 planes of a rows x cols block, src(r, c) = src[r*rs + c*cs];
 // dst(r, c) at dst[r*ld + c] (row_major) or dst[c*ld + r] (otherwise).
 cudaError_t launch_convert_rect(const float* src, int64_t rs, int64_t cs, int64_t rows,
@@ -138,10 +146,19 @@ struct TcGemm {
 struct TcMaps;   // opaque: tensor maps over the planes (gemm_tc.cu)
 int tc_maps_size();
 cudaError_t tc_make_maps(const Planes& pl, int64_t k, int64_t nrhs, void* maps_out);
+// Optional second output of a tensor-core GEMM: the split BF16 planes (hi,
+// lo) of result rows [row0, row1) (canonical rows), element (i, j) at
+// j * ld + i, as the Y planes are laid out.
+struct TcYOut {
+    __nv_bfloat16* hi = nullptr;
+    __nv_bfloat16* lo = nullptr;
+    int64_t ld = 0, row0 = 0, row1 = 0;
+};
 cudaError_t launch_gemm_tc(const Canon<float>& p, const void* maps,
                            const TcGemm* gemms, int ngemms, float beta,
                            float gamma, int* err_word, long long wait_limit,
-                           int num_sms, cudaStream_t s, bool diag_beta = false);
+                           int num_sms, cudaStream_t s, bool diag_beta = false,
+                           const TcYOut* yout = nullptr);
 // Refined TRSM helpers (refine.cu): casts, residual, correction, norms.
 cudaError_t refine_cast_f32_f64(const float* src, int64_t lds, double* dst, int64_t ldd, int64_t m,
                                 int64_t n, double scale, cudaStream_t s);

@@ -151,6 +151,54 @@ __global__ void __launch_bounds__(256) convert_rect_kernel(const float* src, int
     }
 }
 
+// Inverse of each full b x b diagonal block of the canonical lower M,
+// W = inv(M_ii) (lower triangular), as split planes over rows and columns
+// [r0, r0 + b) of a row-major plane pair (element (i, l) at i * ld + l,
+// zeros above the diagonal). One CTA per block: the block is staged in
+// shared memory and thread j solves M_ii w_j = e_j by forward substitution
+// for column j of W.
+__global__ void __launch_bounds__(128) invert_diag_kernel(Canon<float> p, int b,
+                                                          __nv_bfloat16* w_hi,
+                                                          __nv_bfloat16* w_lo, int64_t ld) {
+    pdl_trigger();
+    pdl_wait();
+    extern __shared__ float inv_sm[];
+    float* Ls = inv_sm;                      // b x (b + 1), M_ii row by row
+    float* Ws = inv_sm + b * (b + 1);        // b x b, W row by row
+    const int64_t r0 = (int64_t)blockIdx.x * b;
+    for (int e = threadIdx.x; e < b * b; e += blockDim.x) {
+        const int i = e / b, l = e % b;
+        float v = 0.f;
+        if (l < i)
+            v = p.A[(r0 + i) * p.a_rs + (r0 + l) * p.a_cs];
+        else if (l == i)
+            v = p.unit ? 1.f : p.A[(r0 + i) * (p.a_rs + p.a_cs)];
+        Ls[i * (b + 1) + l] = v;
+    }
+    __syncthreads();
+    const int j = threadIdx.x;
+    if (j < b) {
+        for (int i = 0; i < b; ++i) {
+            float w = 0.f;
+            if (i >= j) {
+                float acc = (i == j) ? 1.f : 0.f;
+                for (int l = j; l < i; ++l) acc -= Ls[i * (b + 1) + l] * Ws[l * b + j];
+                w = acc / Ls[i * (b + 1) + i];
+            }
+            Ws[i * b + j] = w;
+        }
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < b * b; e += blockDim.x) {
+        const int i = e / b, l = e % b;
+        __nv_bfloat16 h, o;
+        split_bf16(Ws[i * b + l], h, o);
+        const int64_t off = (r0 + i) * ld + r0 + l;
+        w_hi[off] = h;
+        w_lo[off] = o;
+    }
+}
+
 template <typename T>
 __global__ void zero_kernel(T* B, int64_t m, int64_t n, int64_t ldb) {
     pdl_trigger();
@@ -186,6 +234,34 @@ cudaError_t launch_convert_y(const Canon<float>& p, const Planes& pl, cudaStream
     if (tj > 65535) return cudaErrorInvalidValue;
     return launch_kernel(convert_y_kernel, dim3((unsigned)tl, (unsigned)tj), dim3(32, 8), 0, s, p,
                          pl);
+}
+
+cudaError_t launch_invert_diag(const Canon<float>& p, int b, __nv_bfloat16* w_hi,
+                               __nv_bfloat16* w_lo, int64_t ld, cudaStream_t s) {
+    if (b < 1 || b > 128) return cudaErrorInvalidValue;
+    const int64_t blocks = p.k / b;          // full blocks only
+    if (blocks <= 0) return cudaSuccess;
+    if (blocks > 0x7fffffff) return cudaErrorInvalidValue;
+    const int smem = (int)((size_t)b * (2 * b + 1) * sizeof(float));
+    static const cudaError_t configured = cudaFuncSetAttribute(
+        invert_diag_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        128 * (2 * 128 + 1) * (int)sizeof(float));
+    if (configured != cudaSuccess) return configured;
+    return launch_kernel(invert_diag_kernel, dim3((unsigned)blocks), dim3(128), smem, s, p, b,
+                         w_hi, w_lo, ld);
+}
+
+// Y planes of C's rows [r0, r0 + rows) only (the rows of one TRSM leaf).
+cudaError_t launch_convert_y_rows(const Canon<float>& p, const Planes& pl, int64_t r0,
+                                  int64_t rows, cudaStream_t s) {
+    if (r0 < 0 || rows < 0 || r0 + rows > p.k || r0 % 4 != 0) return cudaErrorInvalidValue;
+    Canon<float> v = p;
+    v.C = p.C + r0 * p.c_rs;
+    v.k = rows;
+    Planes w = pl;
+    w.y_hi = pl.y_hi + r0;
+    w.y_lo = pl.y_lo + r0;
+    return launch_convert_y(v, w, s);
 }
 
 cudaError_t launch_convert_rect(const float* src, int64_t rs, int64_t cs, int64_t rows,

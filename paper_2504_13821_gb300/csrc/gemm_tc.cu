@@ -83,6 +83,11 @@ struct Params {
     int diag_beta, unit;
     const float* dA;
     int64_t d_step;
+    // optional second output: the split BF16 planes of result rows
+    // [y_row0, y_row1) (canonical rows), element (i, j) at y[j * ldy + i]
+    __nv_bfloat16* y_hi;
+    __nv_bfloat16* y_lo;
+    int64_t ldy, y_row0, y_row1;
     int ngemms, n_tiles_n, total_tiles;
     int* err;
     long long wait_ns;
@@ -348,6 +353,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) gemm_tc_kernel(const __grid_const
             const TcGemm& G = p.g[ti.g];
             const int64_t row = (int64_t)ti.m * BM + q * 32 + lane;
             const bool row_ok = row < G.mlen;
+            const int64_t grow = G.rc + row;
+            const bool yrow = p.y_hi != nullptr && row_ok && grow >= p.y_row0 && grow < p.y_row1;
             float beta = p.beta;
             if (p.diag_beta && row_ok && !p.unit) beta *= __ldg(p.dA + (G.rc + row) * p.d_step);
             const float* crow = p.C + (G.rc + row) * p.c_rs;
@@ -396,7 +403,21 @@ __global__ void __launch_bounds__(NTHREADS, 1) gemm_tc_kernel(const __grid_const
                 }
                 const int64_t j0 = jbase + ch * 32;
                 float* dst = wrow + j0 * p.c_cs;
-                if (row_ok && j0 + 32 <= p.nrhs) {
+                if (yrow) {
+                    // the result and its planes (same split as the conversions)
+                    __nv_bfloat16* yh = p.y_hi + j0 * p.ldy + grow;
+                    __nv_bfloat16* yl = p.y_lo + j0 * p.ldy + grow;
+#pragma unroll
+                    for (int c = 0; c < 32; ++c) {
+                        if (j0 + c < p.nrhs) {
+                            const float o = fmaf(beta, c0[c], p.gamma * v[c]);
+                            dst[c * p.c_cs] = o;
+                            const __nv_bfloat16 h = __float2bfloat16_rn(o);
+                            yh[c * p.ldy] = h;
+                            yl[c * p.ldy] = __float2bfloat16_rn(o - __bfloat162float(h));
+                        }
+                    }
+                } else if (row_ok && j0 + 32 <= p.nrhs) {
 #pragma unroll
                     for (int c = 0; c < 32; ++c) dst[c * p.c_cs] = fmaf(beta, c0[c], p.gamma * v[c]);
                 } else if (row_ok) {
@@ -492,7 +513,8 @@ cudaError_t tc_make_maps(const Planes& pl, int64_t k, int64_t nrhs, void* out) {
 
 cudaError_t launch_gemm_tc(const Canon<float>& p, const void* maps, const TcGemm* gemms,
                            int ngemms, float beta, float gamma, int* err_word,
-                           long long wait_ns, int num_sms, cudaStream_t s, bool diag_beta) {
+                           long long wait_ns, int num_sms, cudaStream_t s, bool diag_beta,
+                           const TcYOut* yout) {
     using namespace tc;
     for (int g0 = 0; g0 < ngemms; g0 += MAXG) {
         const int ng = (ngemms - g0) < MAXG ? (ngemms - g0) : MAXG;
@@ -517,6 +539,11 @@ cudaError_t launch_gemm_tc(const Canon<float>& p, const void* maps, const TcGemm
         prm.unit = p.unit;
         prm.dA = p.A;
         prm.d_step = p.a_rs + p.a_cs;
+        prm.y_hi = yout ? yout->hi : nullptr;
+        prm.y_lo = yout ? yout->lo : nullptr;
+        prm.ldy = yout ? yout->ld : 0;
+        prm.y_row0 = yout ? yout->row0 : 0;
+        prm.y_row1 = yout ? yout->row1 : 0;
         prm.ngemms = ng;
         prm.n_tiles_n = (int)((p.nrhs + bn - 1) / bn);
         prm.err = err_word;

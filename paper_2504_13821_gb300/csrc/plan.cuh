@@ -36,7 +36,7 @@ inline int64_t split_point(int64_t s, int b) {
     return s1;
 }
 
-enum StepKind { kLeaf, kGemm, kConvM, kConvY };
+enum StepKind { kLeaf, kGemm, kConvM, kConvY, kConvYRows, kInvDiag };
 
 struct Step {
     StepKind kind;
@@ -52,11 +52,16 @@ struct Step {
     double beta = 1.0, gamma = 1.0;
     bool dense = false;      // GEMM over dense lower-triangular diagonal blocks (TRMM leaves):
                              // row i's beta is beta * M(i, i)
+    bool inv = false;        // GEMM whose M operand is the inverted b x b diagonal blocks:
+                             // a TRSM leaf on the tensor cores, X = gamma inv(M_ii) Y
+    int64_t y0 = 0, y1 = 0;  // GEMM: also write the split Y planes of result rows [y0, y1)
+    bool tc_leaf = false;    // leaf (while planning): to become an inverse GEMM
 };
 
 struct Plan {
     std::vector<Step> steps;
     bool tc = false;
+    bool tc_leaf = false;    // TRSM leaves of the full size b as inverse GEMMs
 };
 
 inline void plan_trsm(Plan& pl, int64_t r0, int64_t s, bool first, int b, double alpha) {
@@ -67,6 +72,9 @@ inline void plan_trsm(Plan& pl, int64_t r0, int64_t s, bool first, int b, double
         st.b = (int)s;
         st.alpha = first ? alpha : 1.0;
         st.planes = pl.tc;
+        // only full b-row leaves (they start on multiples of b, where the
+        // inverted diagonal blocks are)
+        st.tc_leaf = pl.tc && pl.tc_leaf && s == b && r0 % b == 0;
         pl.steps.push_back(st);
         return;
     }
@@ -168,15 +176,60 @@ inline void plan_trmm_levels(Plan& pl, int64_t k, int b, double alpha, bool dens
 // dense > 0 (TRMM on the tensor-core path only): leaves of that many rows as
 // dense diagonal-block GEMMs, in place of the leaf kernel and of the levels
 // below that size.
+// TRSM leaves on the tensor cores: each marked leaf becomes one GEMM
+// X = gamma inv(M_ii) Y with beta = 0, reading the leaf rows' Y planes and
+// writing X and X's planes. Those input planes come from the epilogue of
+// the tensor-core update right before the leaf (the last step to write the
+// rows: the recursion descends into a second half right after updating
+// it), or, for the first leaf, from a conversion of its rows.
+inline void apply_tc_leaves(Plan& pl) {
+    std::vector<Step> out;
+    out.reserve(pl.steps.size() + 1);
+    for (const Step& st : pl.steps) {
+        if (!(st.kind == kLeaf && st.tc_leaf)) {
+            out.push_back(st);
+            continue;
+        }
+        const bool fed = !out.empty() && out.back().kind == kGemm && out.back().tc &&
+                         !out.back().inv && out.back().gemms.size() == 1 &&
+                         out.back().gemms[0].rc == st.r0;
+        if (fed) {
+            out.back().y0 = st.r0;
+            out.back().y1 = st.r0 + st.b;
+        } else {
+            Step cy{kConvYRows};
+            cy.r0 = st.r0;
+            cy.b = st.b;
+            out.push_back(cy);
+        }
+        Step g{kGemm};
+        g.tc = true;
+        g.inv = true;
+        g.gemms.push_back(TcGemm{st.r0, st.b, st.r0, st.b});
+        g.beta = 0.0;
+        g.gamma = st.alpha;
+        g.y0 = st.r0;
+        g.y1 = st.r0 + st.b;
+        out.push_back(g);
+    }
+    pl.steps.swap(out);
+}
+
 inline void make_plan(Plan& plan, bool trsm, int64_t k, int b, double alpha, bool conv_m = true,
                int dense = 0) {
     if (plan.tc && conv_m) {
         Step cm{kConvM};
         cm.b = trsm ? 0 : dense;
         plan.steps.push_back(cm);
+        if (trsm && plan.tc_leaf) {
+            Step iv{kInvDiag};       // the inverted diagonal blocks, over M's own
+            iv.b = b;
+            plan.steps.push_back(iv);
+        }
     }
     if (trsm) {
         plan_trsm(plan, 0, k, true, b, alpha);
+        if (plan.tc && plan.tc_leaf) apply_tc_leaves(plan);
     } else {
         if (plan.tc) plan.steps.push_back(Step{kConvY});
         if (plan.tc && dense > 0) plan_trmm_levels(plan, k, dense, alpha, true);
@@ -204,6 +257,13 @@ inline int leaf_for(int64_t opt_leaf, int64_t k, bool trsm, int elem, int64_t nr
     if (!trsm && b > kMaxLeaf) b = kMaxLeaf;
     (void)nrhs;
     return (int)std::min<int64_t>(b, std::max<int64_t>(k, 1));
+}
+
+// TRSM leaves on the tensor cores (TRX_OPT_TRSM_TC_LEAF: -1 off, 1 on,
+// 0 automatic = off): tensor-core path, leaves of 64 or 128 rows.
+inline bool tc_leaf_mode(int64_t opt, bool tc, int b) {
+    if (!tc || opt <= 0) return false;
+    return b == 64 || b == 128;
 }
 
 inline bool use_tc_mode(int elem, int64_t gemm_mode, int64_t k, int b) {

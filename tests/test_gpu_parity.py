@@ -294,3 +294,58 @@ def test_bench_size_16384_sampled(trx, op):
     """The benchmark's workload (m = n = 16384, FP32, L L N N, alpha 1.5,
     default handle: tensor cores, cached graph), 32 sampled columns."""
     sampled_case(op, "L", 16384, 16384, 32, np.float32, seed=16384)
+
+
+@pytest.mark.parametrize("side,uplo,trans,diag", VARIANTS)
+def test_trsm_tensor_core_leaves_all_variants(trx, side, uplo, trans, diag):
+    """TRX_OPT_TRSM_TC_LEAF: the full 128-row leaves of an order-1100 FP32
+    TRSM as inverse GEMMs (input planes from the preceding update's
+    epilogue), the ragged 76-row last leaf by substitution; unit diagonals
+    poisoned with NaN in A."""
+    h = trx.Handle(0)
+    h.set_option(trx.OPT_TRSM_TC_LEAF, 1)
+    m, n = (1100, 300) if side == "L" else (300, 1100)
+    run_case("trsm", side, uplo, trans, diag, m, n, 1.5, np.float32,
+             seed=inputs.variant_seed(1101, VARIANTS.index((side, uplo, trans, diag))), handle=h)
+    h.close()
+
+
+@pytest.mark.parametrize("leaf,panels,nrhs", [(64, 0, 700), (128, 0, 2100), (128, 2, 2100)])
+def test_trsm_tensor_core_leaves_sizes(trx, leaf, panels, nrhs):
+    """64- and 128-row inverse-GEMM leaves, many right-hand sides, and two
+    column-panel branches (each with its own planes window)."""
+    h = trx.Handle(0)
+    h.set_option(trx.OPT_TRSM_TC_LEAF, 1)
+    h.set_option(trx.OPT_LEAF, leaf)
+    if panels:
+        h.set_option(trx.OPT_PANELS, panels)
+    for variant in [("L", "L", "N", "N"), ("R", "U", "T", "U")]:
+        m, n = (2048, nrhs) if variant[0] == "L" else (nrhs, 2048)
+        run_case("trsm", *variant, m, n, -0.5, np.float32, seed=leaf + nrhs, handle=h)
+    h.close()
+
+
+def test_trsm_tensor_core_leaves_factor_equals_plain(trx):
+    """A prepared factor made while the option is on carries the inverted
+    diagonal blocks: its TRSM equals the plain call bitwise, its TRMM is the
+    plain TRMM (the option does not touch TRMM)."""
+    dev = torch.device("cuda", 0)
+    h = trx.Handle(dev)
+    h.set_option(trx.OPT_TRSM_TC_LEAF, 1)
+    k, nrhs = 1536, 1000
+    A, B = inputs.problem("L", "U", k, nrhs, seed=31, dtype=np.float32)
+    At = to_dev(A, dev)
+    f = trx.Factor("L", "U", "T", "N", At, handle=h)
+    out = {}
+    for op in ("trsm", "trmm"):
+        plain, via = to_dev(B, dev), to_dev(B, dev)
+        getattr(trx, op)("L", "U", "T", "N", 2.0, At, plain, handle=h)
+        getattr(f, op)(2.0, via, handle=h)
+        torch.cuda.synchronize()
+        assert torch.equal(plain, via), op
+        out[op] = np.asfortranarray(via.cpu().numpy())
+    f.close()
+    h.close()
+    Ak = np.asfortranarray(A[:k, :k])
+    eta = oracle.trsm_backward_error("L", "U", "T", "N", 2.0, Ak, out["trsm"], B)["eta"]
+    assert eta <= bound(k, np.float32), eta

@@ -108,10 +108,20 @@ def replay(op, steps, M, C, alpha_seen=2.0):
     """Execute a plan in FP64 on the canonical lower matrix M (k x k)."""
     C = C.copy()
     k = M.shape[0]
-    Y = C.copy()                     # tensor-core Y planes
+    Y = np.full_like(C, np.nan)      # tensor-core Y planes: unset until written
     for s in steps:
         if s["kind"] == "conv_y":
             Y = C.copy()
+        elif s["kind"] == "conv_y_rows":
+            Y[s["r0"]:s["r0"] + s["b"]] = C[s["r0"]:s["r0"] + s["b"]]
+        elif s["kind"] == "inv_diag":
+            pass                     # the inverses are formed where they are used
+        elif s["kind"] == "gemm" and s.get("inv"):
+            # a TRSM leaf as one GEMM: X = gamma inv(M_ii) Y_i (beta = 0)
+            r, e = s["rc"], min(k, s["rc"] + s["mlen"])
+            assert s["beta"] == 0 and s["rk"] == r and s["klen"] == e - r
+            W = sla.solve_triangular(np.tril(M[r:e, r:e]), np.eye(e - r), lower=True)
+            C[r:e] = s["gamma"] * (W @ Y[r:e])
         elif s["kind"] == "leaf":
             for t in range(s["nleaves"]):
                 r = s["r0"] + t * s["b"]
@@ -136,6 +146,8 @@ def replay(op, steps, M, C, alpha_seen=2.0):
             rc, rk = s["rc"], s["rk"]
             C[rc:rc + s["mlen"]] = (s["beta"] * C[rc:rc + s["mlen"]] + s["gamma"] *
                                     M[rc:rc + s["mlen"], rk:rk + s["klen"]] @ src[rk:rk + s["klen"]])
+        if s["kind"] == "gemm" and s.get("y1", 0) > s.get("y0", 0):
+            Y[s["y0"]:s["y1"]] = C[s["y0"]:s["y1"]]      # the epilogue's planes
     return C
 
 
@@ -248,3 +260,45 @@ def test_fp64_and_small_orders_use_cuda_cores():
     # one leaf covering the whole order: no update, so no operand planes
     assert not any(s["kind"] in ("conv_m", "conv_y") or s.get("tc", 0)
                    for s in debug_plan("S", "L", "L", "N", "N", 100, 8, 4, 0, 0))
+
+
+@pytest.mark.parametrize("k", [256, 300, 1024, 1100, 2049])
+@pytest.mark.parametrize("leaf", [0, 64, 128])
+def test_trsm_tensor_core_leaves_replay_and_feeding(k, leaf):
+    """TRX_OPT_TRSM_TC_LEAF: every full leaf becomes an inverse GEMM whose
+    input planes were written just before it (by the preceding update's
+    epilogue, or a conversion for the first leaf); a ragged last leaf stays
+    a substitution leaf. Replayed in FP64 (unset planes are NaN) it solves
+    the system."""
+    steps = debug_plan("S", "L", "L", "N", "N", k, 7, 4, leaf, 0, 0, 1)
+    b = 128 if leaf == 0 else leaf
+    assert steps[0]["kind"] == "conv_m" and steps[1] == {"kind": "inv_diag", "b": b}
+    inv = [i for i, s in enumerate(steps) if s["kind"] == "gemm" and s["inv"]]
+    assert len(inv) == k // b
+    for n_, i in enumerate(inv):
+        g, prev = steps[i], steps[i - 1]
+        assert g["mlen"] == b and g["rc"] % b == 0 and (g["y0"], g["y1"]) == (g["rc"], g["rc"] + b)
+        if n_ == 0:
+            assert prev == {"kind": "conv_y_rows", "r0": g["rc"], "b": b}
+        else:
+            assert prev["kind"] == "gemm" and not prev["inv"] and prev["rc"] == g["rc"]
+            assert (prev["y0"], prev["y1"]) == (g["rc"], g["rc"] + b)
+    leaves = [s for s in steps if s["kind"] == "leaf"]
+    assert [s["b"] for s in leaves] == ([k % b] if k % b else [])
+    rng = np.random.default_rng(k + leaf)
+    M = np.tril(rng.uniform(-1, 1, (k, k)) / k) + np.diag(1 + rng.random(k))
+    C = rng.standard_normal((k, 7))
+    X = replay("S", steps, M, C)
+    np.testing.assert_allclose(M @ X, 2.0 * C, atol=1e-9)
+
+
+def test_trsm_tensor_core_leaves_only_when_asked():
+    for args in [dict(trsm_tc_leaf=0), dict(trsm_tc_leaf=-1), dict(trsm_tc_leaf=1, elem=8),
+                 dict(trsm_tc_leaf=1, gemm=1), dict(trsm_tc_leaf=1, leaf=32)]:
+        steps = debug_plan("S", "L", "L", "N", "N", 1024, 7, args.get("elem", 4),
+                           args.get("leaf", 0), args.get("gemm", 0), 0, args["trsm_tc_leaf"])
+        assert not any(s["kind"] in ("inv_diag", "conv_y_rows") or s.get("inv") for s in steps)
+    # TRMM is untouched by the option
+    a = debug_plan("M", "L", "L", "N", "N", 1024, 7, 4, 0, 0, 0, 1)
+    b = debug_plan("M", "L", "L", "N", "N", 1024, 7, 4, 0, 0, 0, 0)
+    assert a == b
