@@ -260,7 +260,10 @@ inline int leaf_for(int64_t opt_leaf, int64_t k, bool trsm, int elem, int64_t nr
 }
 
 // TRSM leaves on the tensor cores (TRX_OPT_TRSM_TC_LEAF: -1 off, 1 on,
-// 0 automatic = off): tensor-core path, leaves of 64 or 128 rows.
+// 0 automatic = off): tensor-core path, leaves of 64 or 128 rows. Off by
+// default: measured at m = n = 16384 the step took 18.78 ms against 18.90
+// (the updates before each leaf pay for the planes they now write), and at
+// 256 right-hand sides 1.38 ms against 1.21.
 inline bool tc_leaf_mode(int64_t opt, bool tc, int b) {
     if (!tc || opt <= 0) return false;
     return b == 64 || b == 128;
