@@ -49,8 +49,8 @@ REF_SAMPLE_COLS = 16      # per step of --impl reference
 # taken on only: when the GEMM kernel or the planner has changed since, the
 # line reports null. The capture's summary and command are in profiles/.
 TRAFFIC_SOURCES = ("paper_2504_13821_gb300/csrc/gemm_tc.cu", "paper_2504_13821_gb300/csrc/plan.cuh")
-TRAFFIC_CAPTURE = {"sources_sha256": "7573deb9af1210e0756c3dcf582c64a46288ff1f02a94b8b7380b8001d58d895",
-                   "bytes_per_launch": 226055202, "launches_per_step": 132,
+TRAFFIC_CAPTURE = {"sources_sha256": "6b20c53ee08ba4d42b3548eea914f99f79e23ec0021b4d5abb73627139e0f224",
+                   "bytes_per_launch": 226154380, "launches_per_step": 132,
                    "profile": "profiles/gemm_tc_traffic_trsm_trmm_n16384.md"}
 
 
