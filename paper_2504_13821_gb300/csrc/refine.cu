@@ -56,22 +56,29 @@ __global__ void __launch_bounds__(kThreads) add_f32_kernel(double* x, int64_t ld
     }
 }
 
-// Row sums of |M| (m x n, column-major), one thread per row.
-__global__ void __launch_bounds__(kThreads) row_abs_sum_kernel(const double* a, int64_t lda,
-                                                               int64_t m, int64_t n,
-                                                               double* sums) {
+constexpr int kNormSlices = 32;   // column slices of the row-sum partials
+
+// Row sums of |M| (m x n, column-major) in kNormSlices column slices: the
+// partial of slice blockIdx.y for row i goes to part[blockIdx.y * m + i]
+// (neighbouring threads read neighbouring rows); part_sum_kernel adds the
+// slices in a fixed order.
+template <typename T>
+__global__ void __launch_bounds__(kThreads) row_abs_part_kernel(const T* a, int64_t lda,
+                                                                int64_t m, int64_t n,
+                                                                double* part) {
     const int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x;
     if (i >= m) return;
+    const int64_t slice = (n + kNormSlices - 1) / kNormSlices;
+    const int64_t j0 = blockIdx.y * slice, j1 = j0 + slice < n ? j0 + slice : n;
     double s = 0.0;
-    for (int64_t j = 0; j < n; ++j) s += fabs(a[i + j * lda]);
-    sums[i] = s;
+    for (int64_t j = j0; j < j1; ++j) s += fabs((double)a[i + j * lda]);
+    part[blockIdx.y * m + i] = s;
 }
 
 // Row sums of |op(A)| over A's referenced triangle (the unit diagonal counts
 // 1), A k x k FP32 column-major. Row i of op(A) is row i of A ('N': one
 // thread per row, neighbouring threads read neighbouring rows) or column i
 // (transposed: one warp per column, reading down it).
-constexpr int kNormSlices = 32;   // l-slices of the row-sum partials
 __global__ void __launch_bounds__(kThreads) op_row_abs_part_kernel(const float* a, int64_t lda,
                                                                    int64_t k, int lower, int unit,
                                                                    double* part) {
@@ -330,13 +337,14 @@ __global__ void __launch_bounds__(256) pack_a_kernel(const float* A, int64_t lda
     Ap[(offset + q) * (kRK * kRM) + l * kRM + i] = make_float4(v, v, -v, -v);
 }
 
-// X packed: row l of column tile blockIdx.y; thread t = (pair pc, lane jj).
+// X packed: rows 8 blockIdx.x .. + 7 of column tile blockIdx.y, one row per
+// warp; lane t = (pair pc, lane jj).
 template <bool SPLIT>
-__global__ void __launch_bounds__(32) pack_x_kernel(const double* X64, const float* X32,
-                                                    int64_t ldx, int64_t k, int64_t n,
-                                                    int64_t rows, float4* Xp) {
-    const int64_t l = blockIdx.x, ct = blockIdx.y;
-    const int t = threadIdx.x, pc = t >> 4, jj = t & 15;
+__global__ void __launch_bounds__(256) pack_x_kernel(const double* X64, const float* X32,
+                                                     int64_t ldx, int64_t k, int64_t n,
+                                                     int64_t rows, float4* Xp) {
+    const int64_t l = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5), ct = blockIdx.y;
+    const int t = threadIdx.x & 31, pc = t >> 4, jj = t & 15;
     const int64_t ja = ct * kRN + jj + 32 * pc, jb = ja + 16;
     float4 v = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
     if (l < k) {
@@ -607,13 +615,13 @@ cudaError_t refine_pack_x(const double* X64, const float* X32, int64_t ldx, int6
     if (k <= 0 || n <= 0) return cudaSuccess;
     const int64_t rows = (k + 15) / 16 * 16, nct = (n + kRN - 1) / kRN;
     if (nct > 65535 || rows > 0x7fffffff) return cudaErrorInvalidValue;
-    const dim3 grid((unsigned)rows, (unsigned)nct);
+    const dim3 grid((unsigned)(rows / 8), (unsigned)nct);      // rows: a multiple of 16
     if (X64)
-        pack_x_kernel<true><<<grid, 32, 0, s>>>(X64, nullptr, ldx, k, n, rows,
-                                                static_cast<float4*>(Xp));
-    else
-        pack_x_kernel<false><<<grid, 32, 0, s>>>(nullptr, X32, ldx, k, n, rows,
+        pack_x_kernel<true><<<grid, 256, 0, s>>>(X64, nullptr, ldx, k, n, rows,
                                                  static_cast<float4*>(Xp));
+    else
+        pack_x_kernel<false><<<grid, 256, 0, s>>>(nullptr, X32, ldx, k, n, rows,
+                                                  static_cast<float4*>(Xp));
     return cudaGetLastError();
 }
 void refine_plan_units(int64_t k, bool lower, std::vector<int4>& units,
@@ -684,16 +692,15 @@ cudaError_t refine_residual_packed(int mode, const void* Ap, const void* Xp, con
         static_cast<const int4*>(tiles), part, k, n, B, ldb, R, ldr);
     return cudaGetLastError();
 }
-// out[0] := ||D||_inf (rows) or max column sum (by_cols) of an FP32 array.
-__global__ void __launch_bounds__(kThreads) row_abs_sum_f32_kernel(const float* a, int64_t lda,
-                                                                   int64_t m, int64_t n,
-                                                                   double* sums) {
-    const int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x;
-    if (i >= m) return;
-    double s = 0.0;
-    for (int64_t j = 0; j < n; ++j) s += fabs((double)a[i + j * lda]);
-    sums[i] = s;
+// sums[i] := row i's sum of |M| through kNormSlices partials at sums + m.
+template <typename T>
+void row_sums(const T* a, int64_t lda, int64_t m, int64_t n, double* sums, cudaStream_t s) {
+    double* part = sums + m;
+    row_abs_part_kernel<T><<<dim3((unsigned)((m + kThreads - 1) / kThreads), kNormSlices),
+                             kThreads, 0, s>>>(a, lda, m, n, part);
+    part_sum_kernel<<<(unsigned)((m + kThreads - 1) / kThreads), kThreads, 0, s>>>(part, m, sums);
 }
+// out[0] := ||D||_inf (rows) or max column sum (by_cols) of an FP32 array.
 __global__ void __launch_bounds__(kThreads) col_abs_sum_f32_kernel(const float* a, int64_t lda,
                                                                    int64_t m, int64_t n,
                                                                    double* sums) {
@@ -712,8 +719,7 @@ cudaError_t refine_norm_f32(const float* a, int64_t lda, int64_t m, int64_t n, b
         col_abs_sum_f32_kernel<<<(unsigned)((n * 32 + kThreads - 1) / kThreads), kThreads, 0,
                                  s>>>(a, lda, m, n, sums);
     else
-        row_abs_sum_f32_kernel<<<(unsigned)((m + kThreads - 1) / kThreads), kThreads, 0, s>>>(
-            a, lda, m, n, sums);
+        row_sums<float>(a, lda, m, n, sums, s);
     max_kernel<<<1, kThreads, 0, s>>>(sums, by_cols ? n : m, out);
     return cudaGetLastError();
 }
@@ -726,12 +732,11 @@ cudaError_t refine_norm_one(const double* a, int64_t lda, int64_t m, int64_t n, 
     max_kernel<<<1, kThreads, 0, s>>>(sums, n, out);
     return cudaGetLastError();
 }
-// out[0] := ||M||_inf; sums: m doubles of scratch.
+// out[0] := ||M||_inf; sums: (kNormSlices + 1) m doubles of scratch.
 cudaError_t refine_norm_inf(const double* a, int64_t lda, int64_t m, int64_t n, double* sums,
                             double* out, cudaStream_t s) {
     if (m <= 0 || n <= 0) return cudaMemsetAsync(out, 0, sizeof(double), s);
-    row_abs_sum_kernel<<<(unsigned)((m + kThreads - 1) / kThreads), kThreads, 0, s>>>(a, lda, m, n,
-                                                                                     sums);
+    row_sums<double>(a, lda, m, n, sums, s);
     max_kernel<<<1, kThreads, 0, s>>>(sums, m, out);
     return cudaGetLastError();
 }
