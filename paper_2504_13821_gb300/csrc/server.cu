@@ -174,9 +174,15 @@ int launch_large(trx_server_t s, Req& r) {
     }
     if (rc != TRX_SUCCESS) return rc;
     Flight fl;
-    if ((e = get_event(s, &fl.done)) != cudaSuccess) return fail(e, "event");
+    // the launch is in flight: without a completion event, wait for it here
+    // so the request's buffers are idle when it is reported failed
+    if ((e = get_event(s, &fl.done)) != cudaSuccess) {
+        cudaStreamSynchronize(st);
+        return fail(e, "event");
+    }
     if ((e = cudaEventRecord(fl.done, st)) != cudaSuccess) {
         put_event(s, fl.done);
+        cudaStreamSynchronize(st);
         return fail(e, "record");
     }
     fl.ids.push_back(r.id);
@@ -214,9 +220,13 @@ int launch_small(trx_server_t s, std::vector<Req>& group, int elem) {
     int rc = trx_batched(s->bhandle, elem, (int64_t)probs.size(), probs.data(), s->bstream);
     if (rc != TRX_SUCCESS) return rc;
     Flight fl;
-    if ((e = get_event(s, &fl.done)) != cudaSuccess) return fail(e, "event");
+    if ((e = get_event(s, &fl.done)) != cudaSuccess) {
+        cudaStreamSynchronize(s->bstream);     // see launch_large
+        return fail(e, "event");
+    }
     if ((e = cudaEventRecord(fl.done, s->bstream)) != cudaSuccess) {
         put_event(s, fl.done);
+        cudaStreamSynchronize(s->bstream);
         return fail(e, "record");
     }
     fl.bytes = 0;
