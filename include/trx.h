@@ -103,7 +103,8 @@ enum {
     TRX_OPT_RESIDUAL = 9,  /* residual of trx_strsm_refined: 0 (automatic)
                               or 2: float-float on the FP32 pipes (pairs of
                               floats, exact product split and two-sum,
-                              about 2^-46 relative); 1: the library's FP64
+                              about 2^-46 relative, 2^-44 for adversarial
+                              rows); 1: the library's FP64
                               TRMM on an FP64 copy of A (FP64 pipe)        */
     TRX_OPT_TRSM_TC_LEAF = 10,/* FP32 TRSM on the tensor-core path, leaves of
                               64 or 128 rows: 1 = each leaf as one GEMM,
