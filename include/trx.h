@@ -38,6 +38,26 @@
  * - A handle is not thread-safe: calls sharing one handle must be issued from
  *   one host thread, and calls on different streams that share one handle
  *   must not overlap on the device (they share its workspace).
+ *
+ * Entry points
+ * ------------
+ *   handle and workspace   trx_create, trx_destroy, trx_set_workspace,
+ *                          trx_workspace_size
+ *   the four operations    trx_strsm, trx_dtrsm, trx_strmm, trx_dtrmm
+ *   the GEMM update alone  trx_sgemm_update
+ *   batched problems       trx_batched, trx_{s,d}{trsm,trmm}_batched,
+ *                          trx_batch_create / run / destroy,
+ *                          trx_batched_autotune
+ *   refined FP32 TRSM      trx_strsm_refined (FP64-accurate result)
+ *   prepared factors       trx_sfactor_create / update, trx_factor_destroy,
+ *                          trx_strsm_factor, trx_strmm_factor
+ *   request server         trx_server_create / register_factor /
+ *                          release_factor / submit / poll / pending / wait /
+ *                          destroy
+ *   allocation-free TRSM   trx_strsm_noalloc
+ *   options, diagnostics   trx_set_option, trx_get_option, trx_get_profile,
+ *                          trx_check_device_error, trx_error_string,
+ *                          trx_last_error_detail, trx_debug_plan, trx_version
  */
 #ifndef TRX_H_
 #define TRX_H_
