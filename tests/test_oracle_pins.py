@@ -344,3 +344,68 @@ def test_scale_for_condition_hits_the_target(target):
     A = inputs.tri_matrix(128, "L", seed=5, dtype=np.float64, scale=s)
     kappa = _exact_kappa_one("L", "N", "N", A)
     assert target / 3 <= kappa <= 3 * target
+
+
+# ---- the oracle's norms and error metrics, pinned directly --------------------
+
+def _op_dense(uplo, trans, diag, A):
+    """op(T) as a dense matrix built explicitly from the referenced triangle."""
+    k = A.shape[0]
+    T = np.tril(A, -1) if uplo == "L" else np.triu(A, 1)
+    T = np.nan_to_num(T, nan=0.0)
+    T = T + (np.eye(k) if diag == "U" else np.diag(np.diag(A)))
+    return T.T if trans in ("T", "C") else T
+
+
+@pytest.mark.parametrize("uplo", ["L", "U"])
+@pytest.mark.parametrize("trans", ["N", "T", "C"])
+@pytest.mark.parametrize("diag", ["N", "U"])
+def test_op_norms_match_numpy_on_the_built_triangle(uplo, trans, diag):
+    rng = np.random.default_rng(41)
+    k = 9
+    A = rng.uniform(-3, 3, (k, k))
+    # the unreferenced triangle (and the diagonal for 'U') is poison
+    bad = np.triu(np.ones((k, k), bool), 1) if uplo == "L" else np.tril(np.ones((k, k), bool), -1)
+    A[bad] = np.nan
+    if diag == "U":
+        A[np.arange(k), np.arange(k)] = np.nan
+    A = np.asfortranarray(A)
+    T = _op_dense(uplo, trans, diag, A)
+    assert oracle.op_norm_inf(uplo, trans, diag, A) == pytest.approx(np.linalg.norm(T, np.inf),
+                                                                      rel=1e-15)
+    assert oracle.op_norm_one(uplo, trans, diag, A) == pytest.approx(np.linalg.norm(T, 1),
+                                                                      rel=1e-15)
+
+
+def test_forward_and_trmm_error_closed_forms():
+    X_ref = np.asfortranarray(np.ones((4, 3)))
+    X_hat = X_ref.copy(order="F")
+    X_hat[2, :] += [0.5, -0.25, 0.0]                 # row sums of |X_ref| are 3
+    assert oracle.forward_error(X_hat, X_ref) == pytest.approx(0.75 / 3.0, rel=1e-15)
+    assert oracle.forward_error(X_ref, X_ref) == 0.0
+    # TRMM error: ||C_hat - C_ref||_inf / (|alpha| ||op(A)||_inf ||B||_inf)
+    A = np.asfortranarray(np.tril(np.full((3, 3), 2.0)))     # ||A||_inf = 6
+    B = np.asfortranarray(np.ones((3, 2)))                   # ||B||_inf = 2
+    C_ref = oracle.trmm("L", "L", "N", "N", -1.5, A, B)
+    C_hat = C_ref.copy(order="F")
+    C_hat[1, 0] += 0.9
+    assert oracle.trmm_error("L", "L", "N", "N", -1.5, A, C_hat, C_ref, B) == pytest.approx(
+        0.9 / (1.5 * 6.0 * 2.0), rel=1e-14)
+
+
+@pytest.mark.parametrize("uplo,trans", [("L", "N"), ("U", "T"), ("L", "T")])
+def test_inverse_norm_estimate_is_a_lower_bound_and_exact_when_diagonal(uplo, trans):
+    rng = np.random.default_rng(7)
+    for k in (1, 5, 40):
+        d = 1.0 + rng.random(k) * 9.0
+        D = np.asfortranarray(np.diag(d))
+        exact = 1.0 / d.min()                             # ||D^-1||_1
+        assert oracle.inv_norm_one_estimate(uplo, trans, "N", D) == pytest.approx(exact,
+                                                                                  rel=1e-14)
+        A = np.asfortranarray(np.tril(rng.uniform(-1, 1, (k, k)), -1) * 0.5 + np.diag(d))
+        if uplo == "U":
+            A = np.asfortranarray(A.T)
+        T = _op_dense(uplo, trans, "N", A)
+        true = np.linalg.norm(np.linalg.inv(T), 1)
+        est = oracle.inv_norm_one_estimate(uplo, trans, "N", A)
+        assert est <= true * (1 + 1e-12) and est >= true / (3.0 * k)
