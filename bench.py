@@ -40,6 +40,11 @@ NRHS = 16384
 ALPHA = 1.5
 SEED = 16384
 CPU_SAMPLE_COLS = 32      # cpu_baseline sample (right-hand sides)
+SPLIT_TERMS = 6           # tensor-core split in use (read back from the handle)
+SWEEP_SIZES = "256,512,1024,2048,4096,8192,16384"
+SPLIT_DESC = {6: "3 BF16 slices per operand, every slice product above 2^-24: FP32-grade",
+              3: "2 BF16 slices per operand, about 2^-16 relative per product",
+              1: "1 BF16 slice, about 2^-8 relative per product"}
 REF_SAMPLE_COLS = 16      # per step of --impl reference
 
 
@@ -232,7 +237,8 @@ def workload_config():
             "leaf": LEAF_USED if LEAF_USED is not None else (
                 "TRSM 128 (wide leaf), TRMM 1024-row diagonal blocks on the tensor cores"
                 if DTYPE == np.float32 else 64),
-            "gemm": ("tcgen05 kind::f16, 3-term split BF16, FP32 accumulation"
+            "gemm": (f"tcgen05 kind::f16, {SPLIT_TERMS}-term split BF16 "
+                     f"({SPLIT_DESC[SPLIT_TERMS]}), FP32 accumulation"
                      if DTYPE == np.float32 else "CUDA-core DFMA"),
             "graph": "cached CUDA graph per call",
             "l2": "inputs larger than L2 (A 1 GiB, B 1 GiB); no flush"}
@@ -256,6 +262,10 @@ def run_gpu(args):
     A = colmajor(torch.from_numpy(A_np).to(dev))
     B = colmajor(torch.from_numpy(B_np).to(dev))
     h = trx.Handle(dev)
+    if args.split:
+        h.set_option(trx.OPT_SPLIT, args.split)
+    global SPLIT_TERMS
+    SPLIT_TERMS = h.get_option(trx.OPT_SPLIT)
     if args.pdl:
         h.set_option(trx.OPT_PDL, 1)
     if args.panels:
@@ -321,9 +331,9 @@ def run_gpu(args):
     if DTYPE == np.float32:
         g = prof["gemm_tc"]
         kname = "gemm_tc_kernel (GEMM update, tcgen05)"
-        peak_tc = peaks["bf16_tflops_sustained"] / 3.0
-        peak_src = (f"{src} bf16 sustained {peaks['bf16_tflops_sustained']} TFLOP/s / 3 "
-                    f"split-product terms")
+        peak_tc = peaks["bf16_tflops_sustained"] / SPLIT_TERMS
+        peak_src = (f"{src} bf16 sustained {peaks['bf16_tflops_sustained']} TFLOP/s / "
+                    f"{SPLIT_TERMS} split-product terms")
     else:
         g = prof["gemm_simt"]
         kname = "gemm_simt_kernel<double> (GEMM update, DFMA)"
@@ -340,9 +350,9 @@ def run_gpu(args):
         "algorithmic_bytes_per_launch": g["bytes"] / g["launches"] if g["launches"] else None,
         "peak_source": peak_src,
         # the same kernel against the raw BF16 tensor peak: every algorithmic
-        # flop is three BF16 products on the pipe
-        "tensor_pipe_tflops": 3.0 * achieved if DTYPE == np.float32 else None,
-        "frac_of_raw_bf16_burst": (3.0 * achieved / peaks["bf16_tflops"]
+        # flop is SPLIT_TERMS BF16 products on the pipe
+        "tensor_pipe_tflops": SPLIT_TERMS * achieved if DTYPE == np.float32 else None,
+        "frac_of_raw_bf16_burst": (SPLIT_TERMS * achieved / peaks["bf16_tflops"]
                                    if DTYPE == np.float32 else None),
         "launches_per_step": g["launches"],
         "share_of_kernel_time": g["ms"] / kern_ms if kern_ms else None,
@@ -638,6 +648,295 @@ def run_refined(args):
     return 0
 
 
+def run_sweep(args):
+    """The all-variant size sweep: TRSM and TRMM, all 16 side/uplo/trans/diag
+    variants, FP32 and FP64, m = n in {256, 512, ..., 16384}, alpha = 1.5,
+    the seeded generator with seed k + 1e6 * (variant index). One JSON line
+    per point: device time of one call (CUDA events on the call's stream,
+    B restored from a pristine copy before each call, outside the timed
+    pair), TFLOP/s (m^2 n), and the errors against the FP64 oracle: for
+    orders up to 4096 the whole result (TRSM backward error and forward
+    error, TRMM normwise error), above that a seeded sample of right-hand
+    sides (columns for side L, rows for side R; each is an independent
+    problem), with the oracle's time on the sample. A last line sums it up."""
+    import torch
+    import oracle
+    import paper_2504_13821_gb300 as trx
+    from paper_2504_13821_gb300 import inputs
+    oracle.build()
+    dev = torch.device("cuda", 0)
+    h = trx.Handle(dev)
+    if args.split:
+        h.set_option(trx.OPT_SPLIT, args.split)
+    terms = h.get_option(trx.OPT_SPLIT)
+    stream = torch.cuda.current_stream(dev)
+    sizes = [int(x) for x in args.sizes.split(",")]
+    dtypes = args.dtypes.split(",")
+    ops = args.ops.split(",")
+    vsel = range(16) if args.variants == "all" else [int(x) for x in args.variants.split(",")]
+    cores = oracle.nthreads()
+    worst = {}
+    npoints = 0
+    for k in sizes:
+        for vi in vsel:
+            side, uplo, trans, diag = inputs.VARIANTS[vi]
+            seed = inputs.variant_seed(k, vi)
+            A64, B64 = inputs.problem(side, uplo, k, k, seed=seed, dtype=np.float64,
+                                      poison_diag=(diag == "U"))
+            full = k <= 4096
+            rng = np.random.default_rng(seed + 17)
+            nsamp = 16 if k >= 16384 else 32
+            samp = None if full else np.sort(rng.choice(k, size=nsamp, replace=False))
+            for dt in dtypes:
+                npdt = np.float32 if dt == "f32" else np.float64
+                A, B = A64.astype(npdt), B64.astype(npdt)
+                Ad = trx.to_colmajor(torch.from_numpy(A).to(dev))
+                B0 = trx.to_colmajor(torch.from_numpy(B).to(dev))
+                Bd = B0.clone()
+                fl = float(k) ** 3
+                reps = 1 if (dt == "f64" and k >= 8192) else max(1, args.steps)
+                for op in ops:
+                    fn = trx.trsm if op == "trsm" else trx.trmm
+                    times = []
+                    for r in range(reps + 1):      # the first call warms up (graph capture)
+                        Bd.copy_(B0)
+                        e0 = torch.cuda.Event(enable_timing=True)
+                        e1 = torch.cuda.Event(enable_timing=True)
+                        e0.record(stream)
+                        fn(side, uplo, trans, diag, ALPHA, Ad, Bd, handle=h, stream=stream)
+                        e1.record(stream)
+                        torch.cuda.synchronize()
+                        if r:
+                            times.append(e0.elapsed_time(e1))
+                    ms = statistics.median(times)
+                    X = Bd.cpu().numpy().astype(np.float64)
+                    A_o, B_o = A.astype(np.float64), B.astype(np.float64)
+                    if samp is not None:
+                        if side == "L":
+                            X, B_o = X[:, samp], B_o[:, samp]
+                        else:
+                            X, B_o = X[samp, :], B_o[samp, :]
+                        X, B_o = np.asfortranarray(X), np.asfortranarray(B_o)
+                    t0 = time.perf_counter()
+                    ref = (oracle.trsm if op == "trsm" else oracle.trmm)(
+                        side, uplo, trans, diag, ALPHA, A_o, B_o)
+                    t_or = time.perf_counter() - t0
+                    fwd = oracle.forward_error(X, ref)
+                    if op == "trsm":
+                        err = oracle.trsm_backward_error(side, uplo, trans, diag, ALPHA, A_o, X,
+                                                         B_o)["eta"]
+                    else:
+                        err = oracle.trmm_error(side, uplo, trans, diag, ALPHA, A_o, X, ref, B_o)
+                    u = 2.0 ** -24 if dt == "f32" else 2.0 ** -53
+                    bound = 8 * k * u
+                    ok = bool(np.isfinite(err) and err <= bound)
+                    nrhs_or = k if samp is None else len(samp)
+                    line = {"workload": "sweep", "op": op, "dtype": dt,
+                            "variant": side + uplo + trans + diag, "m": k, "n": k,
+                            "ms": ms, "tflops": fl / (ms * 1e-3) / 1e12,
+                            "error_metric": "backward" if op == "trsm" else "normwise",
+                            "error": err, "bound": bound, "ok": ok, "forward_error": fwd,
+                            "checked": "all" if samp is None else f"{len(samp)} sampled "
+                                       + ("columns" if side == "L" else "rows"),
+                            "oracle_s": t_or, "oracle_gflops": float(k) * k * nrhs_or / t_or / 1e9,
+                            "oracle_cores": cores, "reps": reps,
+                            "split_terms": terms if dt == "f32" else None}
+                    print(json.dumps(line), flush=True)
+                    npoints += 1
+                    key = (op, dt)
+                    w = worst.setdefault(key, {"max_err_over_bound": 0.0, "fails": 0})
+                    w["max_err_over_bound"] = max(w["max_err_over_bound"], err / bound)
+                    w["fails"] += 0 if ok else 1
+                del Ad, B0, Bd
+    print(json.dumps({"workload": "sweep", "summary": True, "points": npoints,
+                      "per_op_dtype": {f"{a}/{b}": v for (a, b), v in worst.items()}}),
+          flush=True)
+    h.close()
+    return 0
+
+
+def run_precision(args):
+    """The precision form against plain FP32 (config 3): FP32 TRSM side L,
+    lower, no transpose, non-unit, alpha 1.5, m in {8192, 16384, 32768}, n in
+    {256, m}, factors with kappa_1 about 1e2, 1e4, 1e6 (the stored scales of
+    tests/golden/condition_scales.json). Per point and form: device time
+    (CUDA events, median), and against the FP64 oracle on a seeded sample of
+    16 right-hand sides (each column of a side-L solve is its own problem):
+    the normwise backward error of the sample and its forward error. Forms:
+      split6        the plain FP32 solve (6-term split: FP32-grade products)
+      split3, split1 the same recursion with 3-term / 1-term BF16 products
+      refine3_1e-6, refine1_1e-6  split-3 / split-1 solve + refinement with
+                    the FP32-grade tensor-core residual, stopping at backward
+                    error 1e-6 (the library's own estimate)
+      refine6_fp64  split-6 solve + float-float residual refinement to an
+                    FP64-level backward error
+      fp64          the library's FP64 solve (CUDA-core DFMA), n = 256 and
+                    m <= 8192 with n = m only (seconds per call beyond)
+    One JSON line per point, then a summary line."""
+    import torch
+    import oracle
+    import paper_2504_13821_gb300 as trx
+    from paper_2504_13821_gb300 import inputs
+    oracle.build()
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    with open(os.path.join(ROOT, "tests", "golden", "condition_scales.json")) as f:
+        entries = json.load(f)["entries"]
+    sizes = [int(x) for x in args.sizes.split(",")]
+    kappas = [1e2, 1e4, 1e6] if args.kappa is None else [args.kappa]
+    nsel = args.nrhs_list.split(",")
+    h = trx.Handle(dev)
+    alpha = 1.5
+
+    def timed(fn, reps):
+        fn()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return statistics.median(ts)
+
+    summary = []
+    for k in sizes:
+        for kap in kappas:
+            e = next((x for x in entries if x["k"] == k and x["target"] == kap), None)
+            if e is None:
+                print(json.dumps({"workload": "precision", "k": k, "kappa": kap,
+                                  "error": "no stored scale"}), flush=True)
+                continue
+            for ns in nsel:
+                n = k if ns == "m" else int(ns)
+                A, B = inputs.problem("L", "L", k, n, seed=e["seed"], dtype=np.float32,
+                                      scale=e["scale"])
+                cols = np.sort(np.random.default_rng(e["seed"] + n).choice(
+                    n, size=min(16, n), replace=False))
+                A64 = A.astype(np.float64)
+                Bs = np.asfortranarray(B[:, cols].astype(np.float64))
+                t0 = time.perf_counter()
+                ref = oracle.trsm("L", "L", "N", "N", alpha, A64, Bs)
+                t_or = time.perf_counter() - t0
+                At = trx.to_colmajor(torch.from_numpy(A).to(dev))
+                Bt = trx.to_colmajor(torch.from_numpy(B).to(dev))
+                del A, B
+                big = float(k) * k * n
+                reps = 3 if big <= 2.0 ** 40 else 1
+                rows = {}
+
+                def check(Xs):
+                    Xs = np.asfortranarray(Xs.astype(np.float64))
+                    eta = oracle.trsm_backward_error("L", "L", "N", "N", alpha, A64, Xs,
+                                                     Bs)["eta"]
+                    return float(eta), float(oracle.forward_error(Xs, ref))
+
+                X32 = torch.empty_like(Bt)
+                for terms in (6, 3, 1):
+                    h.set_option(trx.OPT_SPLIT, terms)
+                    ms = timed(lambda: trx.trsm("L", "L", "N", "N", alpha, At, X32.copy_(Bt),
+                                                handle=h, stream=stream), reps)
+                    eta, fe = check(X32[:, cols].cpu().numpy())
+                    rows[f"split{terms}"] = {"ms": ms, "backward_error": eta,
+                                             "forward_error": fe}
+                del X32
+                X64 = torch.empty((n, k), dtype=torch.float64, device=dev).t()
+                for terms in (3, 1):
+                    h.set_option(trx.OPT_SPLIT, terms)
+                    h.set_option(trx.OPT_RESIDUAL, trx.RESIDUAL_TC)
+                    info = {}
+
+                    def refined():
+                        info.update(trx.trsm_refined("L", "L", "N", "N", alpha, At, Bt, out=X64,
+                                                     handle=h, tol=1e-6, max_iter=10)[1])
+                    ms = timed(refined, reps)
+                    eta, fe = check(X64[:, cols].cpu().numpy())
+                    rows[f"refine{terms}_1e-6"] = {"ms": ms, "backward_error": eta,
+                                                   "forward_error": fe,
+                                                   "corrections": info["iterations"],
+                                                   "library_backward_error":
+                                                       info["backward_error"]}
+                h.set_option(trx.OPT_SPLIT, 6)
+                h.set_option(trx.OPT_RESIDUAL, trx.RESIDUAL_AUTO)
+                if not (k >= 32768 and n == k and not args.all_forms):
+                    info = {}
+
+                    def refined64():
+                        info.update(trx.trsm_refined("L", "L", "N", "N", alpha, At, Bt, out=X64,
+                                                     handle=h)[1])
+                    ms = timed(refined64, 1 if big > 2.0 ** 40 else reps)
+                    eta, fe = check(X64[:, cols].cpu().numpy())
+                    rows["refine6_fp64"] = {"ms": ms, "backward_error": eta, "forward_error": fe,
+                                            "corrections": info["iterations"]}
+                del X64
+                if n == 256 or k <= 8192:
+                    A64d, B64d = At.double(), Bt.double()
+                    Xd = B64d.clone()
+                    ms = timed(lambda: trx.trsm("L", "L", "N", "N", alpha, A64d, Xd.copy_(B64d),
+                                                handle=h, stream=stream), 1)
+                    eta, fe = check(Xd[:, cols].cpu().numpy())
+                    rows["fp64"] = {"ms": ms, "backward_error": eta, "forward_error": fe}
+                    del A64d, B64d, Xd
+                plain = rows["split6"]["ms"]
+                best = min((v["ms"], name) for name, v in rows.items()
+                           if v["backward_error"] <= 1e-6)
+                line = {"workload": "precision", "k": k, "n": n, "kappa_target": kap,
+                        "kappa_estimate": e["kappa_estimate"], "scale": e["scale"],
+                        "seed": e["seed"], "checked_columns": len(cols),
+                        "oracle_s": t_or, "forms": rows,
+                        "fastest_at_1e-6": best[1], "fastest_ms": best[0],
+                        "speedup_vs_split6_at_1e-6": plain / best[0]}
+                print(json.dumps(line), flush=True)
+                summary.append((k, n, kap, best[1], plain / best[0]))
+                del At, Bt
+                torch.cuda.empty_cache()
+    print(json.dumps({"workload": "precision", "summary": [
+        {"k": a, "n": b, "kappa": c, "fastest_at_1e-6": d, "speedup_vs_split6": s_}
+        for a, b, c, d, s_ in summary]}), flush=True)
+    h.close()
+    return 0
+
+
+def run_peaks(args):
+    """Peak rates of the arithmetic units this library's kernels use, with
+    its own probes (trx_peak_probe), under the protocol of the outside BF16
+    and HBM measurements: the launch size calibrated to about 50 ms, best of
+    10 launches ("burst") and launches back to back for about 4 s
+    ("sustained"), SM clocks sampled during the sustained loop. One JSON
+    line per kind."""
+    import torch
+    import paper_2504_13821_gb300 as trx
+    dev = torch.device("cuda", 0)
+    uuid = None
+    try:
+        uuid = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:
+        pass
+    out = {}
+    for kind in ("ffma", "dfma", "dmma", "tc_tf32", "tc_bf16"):
+        iters = 64
+        while True:                              # calibrate: ~50 ms per launch
+            _, ms = trx.peak_probe(kind, iters)
+            if ms >= 50.0 or iters > 1 << 40:
+                break
+            iters = int(iters * max(2.0, min(16.0, 55.0 / max(ms, 1e-3))))
+        burst = max(trx.peak_probe(kind, iters)[0] for _ in range(10))
+        clocks = ClockSampler(uuid)
+        clocks.start()
+        t0, rates = time.perf_counter(), []
+        while time.perf_counter() - t0 < 4.0:
+            rates.append(trx.peak_probe(kind, iters)[0])
+        clk = clocks.stop()
+        line = {"workload": "peaks", "kind": kind, "burst_tflops": burst,
+                "sustained_tflops": float(np.mean(rates)), "launches": len(rates),
+                "iters_per_launch": iters, "clocks": clk}
+        out[kind] = line
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def latency_stats(arrival: dict, done: dict) -> dict:
     """p50 / p99 latency (ms) and completions per second over a run."""
     if not done:
@@ -660,12 +959,17 @@ def latency_stats(arrival: dict, done: dict) -> dict:
 def run_serving(args):
     """Serving workload: open-loop Poisson arrivals (args.rate per second for
     args.duration seconds), 70% TRSM / 30% TRMM, order log-uniform 64..8192,
-    right-hand sides log-uniform 1..1024, half FP32 and half FP64; each
-    factor (same generator) is resident and reused by 1..50 requests;
-    admission capped at 150 GB. Requests go to the library's server
-    (trx_server_*) at their arrival time; a request's latency runs from its
-    scheduled arrival to the poll that reports it complete. Reports p50/p99
-    latency and solves/s."""
+    right-hand sides log-uniform 1..1024, half FP32-refined and half FP64;
+    each factor (same generator) is resident and reused by 1..50 requests;
+    admission capped at 150 GB. FP32 TRSM requests are refined (the FP32
+    solve plus args.refine_corrections float-float corrections, FP64 result)
+    unless --no-refine; FP64 TRSM requests take the server's FP64 engine
+    (args.fp64_corrections > 0: the FP32 solve plus that many float-float
+    corrections; 0: the recursive DFMA solve); TRMM requests run in their
+    factor's precision. Requests go to the library's server (trx_server_*)
+    at their arrival time; a request's latency runs from its scheduled
+    arrival to the poll that reports it complete. Reports p50/p99 latency
+    and solves/s, overall and per request kind."""
     import torch
     from paper_2504_13821_gb300 import serving
     dev = torch.device("cuda", 0)
@@ -675,8 +979,11 @@ def run_serving(args):
     # front so no request waits for a workspace to grow
     srv = serving.Server(0, streams=4, budget_bytes=150 << 30, max_inflight=4096,
                          workspace_bytes=args.server_workspace_mb << 20,
-                         graphs=not args.server_direct)
-    arrival, done, failed = {}, {}, []
+                         graphs=not args.server_direct,
+                         refine_corrections=args.refine_corrections,
+                         fp64_corrections=args.fp64_corrections)
+    refine = not args.no_refine
+    arrival, done, failed, kind = {}, {}, [], {}
 
     def collect(items):
         now = time.perf_counter()
@@ -702,8 +1009,21 @@ def run_serving(args):
             fid = srv.register(A, uplo)
             for nrhs in (1, 1024):
                 for op in ("S", "M"):
-                    warm.append(srv.submit(fid, op, "L", 1.0,
-                                           torch.randn(nrhs, k, device=dev, dtype=dtype).t()))
+                    Bw = torch.randn(nrhs, k, device=dev, dtype=dtype).t()
+                    if op == "S" and dtype == torch.float32 and refine:
+                        Xw = torch.empty(nrhs, k, device=dev, dtype=torch.float64).t()
+                        warm.append(srv.submit_refined(fid, "L", 1.0, Bw, Xw))
+                    else:
+                        warm.append(srv.submit(fid, op, "L", 1.0, Bw))
+            if k == 8192:
+                # the largest solves once per stream: refinement scratch made
+                for _ in range(8):
+                    Bw = torch.randn(1024, k, device=dev, dtype=dtype).t()
+                    if dtype == torch.float32 and refine:
+                        Xw = torch.empty(1024, k, device=dev, dtype=torch.float64).t()
+                        warm.append(srv.submit_refined(fid, "L", 1.0, Bw, Xw))
+                    else:
+                        warm.append(srv.submit(fid, "S", "L", 1.0, Bw))
             srv.release(fid)
             del A
     warm_status = dict(srv.drain())
@@ -736,11 +1056,19 @@ def run_serving(args):
         nrhs = int(round(np.exp(rng.uniform(0, np.log(1024)))))
         op = "S" if rng.random() < 0.7 else "M"
         B = torch.randn(nrhs, k, device=dev, dtype=dtype).t()     # column-major k x nrhs
+        refined = op == "S" and dtype == torch.float32 and refine
+        X = torch.empty(nrhs, k, device=dev, dtype=torch.float64).t() if refined else None
         while time.perf_counter() < t_arr:
             collect(srv.poll())
-        rid = srv.submit(fid, op, "L", 1.5, B)
+        if refined:
+            rid = srv.submit_refined(fid, "L", 1.5, B, X)
+        else:
+            rid = srv.submit(fid, op, "L", 1.5, B)
         arrival[rid] = t_arr
-        del B                       # the server keeps it until the request completes
+        kind[rid] = ("fp32-refined TRSM" if refined else
+                     ("fp64 " if dtype == torch.float64 else "fp32 ") +
+                     ("TRSM" if op == "S" else "TRMM"))
+        del B, X                    # the server keeps them until the request completes
         if last_use:
             srv.release(fid)        # dropped once its submitted requests complete
         submitted += 1
@@ -751,20 +1079,30 @@ def run_serving(args):
         collect(srv.poll())
     torch.cuda.synchronize()
     st = latency_stats(arrival, done)
+    per_kind = {}
+    for name in sorted(set(kind.values())):
+        ids = [r for r in done if kind.get(r) == name]
+        per_kind[name] = latency_stats({r: arrival[r] for r in ids}, {r: done[r] for r in ids})
     line = {"metric": "served solves/s, p50/p99 ms", "value": st.get("solves_per_s"),
             "unit": "solves/s", "n_gpus": 1, "steps": 1, "warmup": 0,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32+f64", "data": "synthetic",
             "config": {"workload": f"Poisson {args.rate}/s for {args.duration} s, 70% TRSM, "
                                    "m log-uniform 64..8192, nrhs log-uniform 1..1024, "
-                                   f"{args.fp64_share:.0%} FP64 (rest FP32), factors reused "
+                                   f"{args.fp64_share:.0%} FP64 (rest FP32), FP32 TRSM "
+                                   + (f"refined ({args.refine_corrections} float-float "
+                                      "corrections, FP64 result)" if refine else "plain")
+                                   + ", FP64 TRSM "
+                                   + (f"FP32 solve + {args.fp64_corrections} float-float "
+                                      "corrections" if args.fp64_corrections else "DFMA")
+                                   + ", factors reused "
                                    "1..50 times, 150 GB admission cap, native request server, "
                                    f"{args.server_workspace_mb} MB workspace per stream, "
                                    + ("direct launches" if args.server_direct else
                                       "cached graphs"),
                        "requests": submitted, "offered_tflops": flops / args.duration / 1e12,
                        "failed": len(failed)},
-            "latency": st}
+            "latency": st, "latency_per_kind": per_kind}
     print(json.dumps(line), flush=True)
     srv.close()
     return 0 if not failed else 1
@@ -789,12 +1127,25 @@ def main(argv=None):
     ap.add_argument("--nrhs", type=int, default=None,
                     help="right-hand sides (default 16384, refined workload 256)")
     ap.add_argument("--dtype", default="f32", choices=["f32", "f64"])
+    ap.add_argument("--split", type=int, default=0, choices=[0, 1, 3, 6],
+                    help="tensor-core split product terms (0: library default, 6)")
     ap.add_argument("--rate", type=float, default=2000.0, help="serving: arrivals per second")
     ap.add_argument("--duration", type=float, default=60.0, help="serving: seconds of arrivals")
     ap.add_argument("--fp64-share", type=float, default=0.5,
                     help="serving: fraction of FP64 requests (the rest FP32)")
+    ap.add_argument("--sizes", default=SWEEP_SIZES,
+                    help="sweep: orders m = n (precision: 8192,16384,32768)")
+    ap.add_argument("--dtypes", default="f32,f64", help="sweep: element types")
+    ap.add_argument("--ops", default="trsm,trmm", help="sweep: operations")
+    ap.add_argument("--variants", default="all",
+                    help="sweep: 'all' or comma-separated variant indices 0..15")
+    ap.add_argument("--nrhs-list", default="256,m",
+                    help="precision: right-hand sides per order ('m' = the order)")
+    ap.add_argument("--all-forms", action="store_true",
+                    help="precision: also the FP64-level refinement at m = n = 32768")
     ap.add_argument("--workload", default="square",
-                    choices=["square", "batched", "serving", "refined"],
+                    choices=["square", "batched", "serving", "refined", "sweep", "precision",
+                             "peaks"],
                     help="square: the n=16384 TRSM+TRMM step (default); batched: "
                          "4096 small uneven problems in one launch; serving: Poisson "
                          "arrivals; refined: FP32 TRSM refined in FP64 (k 8192, 256 "
@@ -802,6 +1153,12 @@ def main(argv=None):
     ap.add_argument("--count", type=int, default=4096, help="problems (batched workload)")
     ap.add_argument("--server-direct", action="store_true",
                     help="serving: large requests launch directly instead of replaying graphs")
+    ap.add_argument("--refine-corrections", type=int, default=2,
+                    help="serving: corrections of a refined FP32 TRSM request")
+    ap.add_argument("--fp64-corrections", type=int, default=3,
+                    help="serving: FP64 TRSM as FP32 solve + this many corrections (0: DFMA)")
+    ap.add_argument("--no-refine", action="store_true",
+                    help="serving: FP32 TRSM requests plain (no refinement)")
     ap.add_argument("--server-workspace-mb", type=int, default=512,
                     help="serving: per-stream workspace made when the server starts")
     ap.add_argument("--kappa", type=float, default=None,
@@ -822,6 +1179,14 @@ def main(argv=None):
         return run_serving(args)
     if args.workload == "refined":
         return run_refined(args)
+    if args.workload == "sweep":
+        return run_sweep(args)
+    if args.workload == "peaks":
+        return run_peaks(args)
+    if args.workload == "precision":
+        if args.sizes == SWEEP_SIZES:
+            args.sizes = "8192,16384,32768"
+        return run_precision(args)
     return run_gpu(args)
 
 

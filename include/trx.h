@@ -48,16 +48,18 @@
  *   batched problems       trx_batched, trx_{s,d}{trsm,trmm}_batched,
  *                          trx_batch_create / run / destroy,
  *                          trx_batched_autotune
- *   refined FP32 TRSM      trx_strsm_refined (FP64-accurate result)
+ *   refined FP32 TRSM      trx_strsm_refined (FP64-accurate result),
+ *                          trx_strsm_refined_async (fixed corrections)
  *   prepared factors       trx_sfactor_create / update, trx_factor_destroy,
  *                          trx_strsm_factor, trx_strmm_factor
  *   request server         trx_server_create / register_factor /
- *                          release_factor / submit / poll / pending / wait /
- *                          destroy
- *   allocation-free TRSM   trx_strsm_noalloc
+ *                          release_factor / submit / submit_refined / poll /
+ *                          pending / wait / destroy
+ *   allocation-free TRSM   trx_strsm_noalloc, trx_noalloc_check_error
  *   options, diagnostics   trx_set_option, trx_get_option, trx_get_profile,
  *                          trx_check_device_error, trx_error_string,
  *                          trx_last_error_detail, trx_debug_plan, trx_version
+ *   peak-rate probes       trx_peak_probe
  */
 #ifndef TRX_H_
 #define TRX_H_
@@ -91,7 +93,8 @@ enum {
                               (default: 128 for FP32 TRSM, else 64)        */
     TRX_OPT_GEMM = 2,      /* FP32 GEMM-update engine: 0 automatic, 1 CUDA
                               cores (FP32 FMA), 2 tensor cores (tcgen05,
-                              3-term split BF16, FP32 accumulation)         */
+                              split BF16 products of TRX_OPT_SPLIT terms,
+                              FP32 accumulation)                            */
     TRX_OPT_GRAPH = 3,     /* 1 (default): replay the launch chain as a
                               cached CUDA graph; 0: launch directly         */
     TRX_OPT_PROFILE = 4,   /* 1: time every launch with CUDA events and
@@ -125,7 +128,13 @@ enum {
                               floats, exact product split and two-sum,
                               about 2^-46 relative, 2^-44 for adversarial
                               rows); 1: the library's FP64
-                              TRMM on an FP64 copy of A (FP64 pipe)        */
+                              TRMM on an FP64 copy of A (FP64 pipe);
+                              3: FP32-grade on the tensor cores, op(A) times
+                              X rounded to FP32 by the library's FP32 TRMM
+                              with the 6-term split, then alpha B minus it in
+                              FP64 (a few units of 2^-24 of |op(A)||X|: for
+                              targets down to about 1e-7; the handle's
+                              workspace must hold the 6-term planes)       */
     TRX_OPT_TRSM_TC_LEAF = 10,/* FP32 TRSM on the tensor-core path, leaves of
                               64 or 128 rows: 1 = each leaf as one GEMM,
                               X = alpha inv(A_ii) B_i, with the diagonal
@@ -134,6 +143,30 @@ enum {
                               the leaf's input planes written by the
                               preceding update's epilogue; -1 or 0
                               (default): the substitution leaf kernels      */
+    TRX_OPT_SPLIT = 11,    /* FP32 on the tensor cores: product terms of the
+                              BF16 split, each FP32 operand carried as 1, 2
+                              or 3 BF16 slices (x0 = bf16(x), x1 =
+                              bf16(x - x0), x2 = bf16(x - x0 - x1)):
+                              6 = three slices, products x0y0 + x0y1 +
+                              x1y0 + x0y2 + x1y1 + x2y0 (every slice
+                              product above 2^-24: FP32-grade);
+                              3 = two slices, x0y0 + x0y1 + x1y0 (about
+                              2^-16 relative per product);
+                              1 = one slice, x0y0 (about 2^-8);
+                              FP32 accumulation in every case; 0 =
+                              automatic (default: 6). trx_get_option
+                              reads back the terms in use. A prepared
+                              factor keeps the split it was created with. */
+    TRX_OPT_FP64_TRSM = 12 /* trx_dtrsm's engine: 0 (default) the recursive
+                              FP64 solve (CUDA-core DFMA updates); n in
+                              1..16: the mixed form, the FP32 solve on
+                              fl32(A) then n corrections with the residual
+                              alpha B - op(A) X in float-float arithmetic on
+                              the FP32 pipes (A and X as float pairs, about
+                              2^-44 of |op(A)||X|) and FP32 correction solves,
+                              X accumulated in FP64 (asynchronous, as
+                              trx_strsm_refined_async; uses the handle's
+                              refinement scratch)                          */
 };
 
 /* Kernel classes reported by trx_get_profile(). */
@@ -178,7 +211,9 @@ int trx_set_workspace(trx_handle_t handle, void* ptr, size_t bytes);
  * op is 'S' (TRSM) or 'M' (TRMM), for which side/m/n are the call's; 'Y' for
  * a call on a prepared factor (TRSM or TRMM, same side/m/n); or 'G' for a
  * tensor-core trx_sgemm_update, with m = M + K and n = N (side 'L').
- * Depends on the handle's options (the CUDA-core and FP64 paths need none).
+ * Depends on the handle's options (the CUDA-core and FP64 paths need none,
+ * except FP64 TRSM on the mixed engine, TRX_OPT_FP64_TRSM, which needs the
+ * FP32 solve's).
  * Returns 0 and sets *bytes, or an argument code as for the compute calls. */
 int trx_workspace_size(trx_handle_t handle, char op, char side, int64_t m,
                        int64_t n, int elem_bytes, size_t* bytes);
@@ -292,6 +327,25 @@ int trx_strsm_refined(trx_handle_t handle, char side, char uplo, char transa, ch
                       const float* B, int64_t ldb, double* X, int64_t ldx, int max_iter,
                       double tol, trx_refine_info_t* info, void* stream);
 
+/* Refined FP32 TRSM with a fixed number of corrections and no host
+ * read-back (for callers that must not synchronise, e.g. a request server):
+ * the FP32 solve, then `corrections` (0..16) steps of the float-float
+ * residual R = alpha B - op(A) X (from X each time), the FP32 correction
+ * solve op(A) D = R and X += D in FP64, all enqueued on `stream`. Arguments
+ * as trx_strsm_refined without max_iter/tol/info (corrections is argument
+ * 15). Nothing is read back: a timed-out device wait shows in
+ * trx_check_device_error. The refinement scratch (as trx_strsm_refined's)
+ * is grown on the handle when a call needs more than any call before it;
+ * that growth synchronises the stream, so a caller that must never block
+ * makes one call of its largest size first. Needs the workspace of
+ * trx_strsm. Two corrections reach an FP64-level backward error for
+ * condition numbers up to about 1e4 (each one gains about
+ * log2(1 / (kappa 2^-24)) bits). */
+int trx_strsm_refined_async(trx_handle_t handle, char side, char uplo, char transa, char diag,
+                            int64_t m, int64_t n, float alpha, const float* A, int64_t lda,
+                            const float* B, int64_t ldb, double* X, int64_t ldx,
+                            int corrections, void* stream);
+
 /* Prepared FP32 factor (no counterpart in the paper: an interface for
  * callers that solve with or multiply by one triangle many times). The
  * tensor-core path multiplies split-BF16 planes of the canonical triangle
@@ -386,6 +440,10 @@ typedef struct {
     int graphs;             /* 1: large requests replay cached CUDA graphs (one
                                capture per new problem shape); 0: direct
                                launches (1)                                      */
+    int refine_corrections; /* corrections of a refined request, 0..16 (2)       */
+    int fp64_corrections;   /* FP64 TRSM requests: 0 the recursive DFMA solve;
+                               n in 1..16 the FP32 solve plus n float-float
+                               corrections (TRX_OPT_FP64_TRSM) (0)             */
 } trx_server_config_t;
 /* config NULL: the defaults in brackets above. */
 int trx_server_create(int device, const trx_server_config_t* config, trx_server_t* server);
@@ -405,6 +463,17 @@ int trx_server_release_factor(trx_server_t server, int factor_id);
 int trx_server_submit(trx_server_t server, int factor_id, char op, char side, double alpha,
                       void* B, int64_t m, int64_t n, int64_t ldb, void* input_stream,
                       int64_t* request_id);
+/* A refined FP32 TRSM request: op(A) X = alpha B (side 'L') or
+ * X op(A) = alpha B ('R') on an FP32 factor, B (FP32, m x n, not modified)
+ * and X (FP64, m x n, leading dimension ldx, the result) device buffers
+ * kept alive by the caller until the request completes; the FP32 solve plus
+ * refine_corrections float-float corrections (trx_strsm_refined_async), on
+ * the streams of the large requests whatever the order. -i for an illegal
+ * i-th argument (factor_id 2, also an FP64 factor; side 3, B 5, m 7, n 8,
+ * ldb 9, X 10, ldx 11, request_id 13). */
+int trx_server_submit_refined(trx_server_t server, int factor_id, char side, double alpha,
+                              const void* B, int64_t m, int64_t n, int64_t ldb, double* X,
+                              int64_t ldx, void* input_stream, int64_t* request_id);
 /* One tick (above). Returns 0, or the first error of this tick (the
  * requests it concerns complete with that status). */
 int trx_server_poll(trx_server_t server, int64_t* request_ids, int* status, int capacity,
@@ -465,20 +534,51 @@ int trx_debug_plan(char op, char side, char uplo, char transa, char diag,
  * directly onto `stream` and calls no cudaMalloc/cudaFree. The tensor-core
  * path's scratch is one file-scope __device__ array of
  * TRX_NOALLOC_SCRATCH_BYTES that every device using this library holds
- * until the process exits; problems needing more (about 4*k*(k + nrhs)
- * bytes, k the order of A, nrhs the other dimension of B, both rounded up to
- * 64) return TRX_ERR_WORKSPACE before anything is enqueued.
+ * until the process exits; problems needing more (the split operand planes:
+ * 2 * s * k * (k + nrhs) bytes with s BF16 slices per operand, 6 k (k + nrhs)
+ * with the default 6-term split; k the order of A, nrhs the other dimension
+ * of B, both rounded up to 64) return TRX_ERR_WORKSPACE before anything is
+ * enqueued.
  * The first call on a device sets that device up (looks up the array's
  * device address, sets kernel attributes): make that first call outside any
  * stream capture. All calls share the one array, so calls whose work
  * overlaps on the GPU (other streams, other host threads) race: serialise
- * them on one stream. A device-side wait that runs out of time (see
- * TRX_OPT_WAIT_LIMIT, fixed here at 2 s) leaves B invalid and is not
- * reported by this entry point. Returns 0, -i for an illegal i-th argument
+ * them on one stream. A device-side wait that runs out of time (2 s; the
+ * environment variable TRX_NOALLOC_WAIT_NS, read at a device's set-up,
+ * overrides it) leaves B invalid and sets the device's error word, which
+ * trx_noalloc_check_error reads. Returns 0, -i for an illegal i-th argument
  * (BLAS numbering as trx_strsm without the handle), or a TRX_ERR_* code. */
 int trx_strsm_noalloc(char side, char uplo, char transa, char diag, int64_t m,
                       int64_t n, float alpha, const float* A, int64_t lda,
                       float* B, int64_t ldb, void* stream);
+
+/* Read and clear the error word of trx_strsm_noalloc on the calling thread's
+ * current device: TRX_SUCCESS, or TRX_ERR_TIMEOUT if a bounded wait of an
+ * earlier call gave up (that call's B is invalid). Call it after the solves'
+ * stream has been synchronised; it copies one int from the device (no
+ * allocation). TRX_SUCCESS if no call has run on the device yet. */
+int trx_noalloc_check_error(void);
+
+/* Peak-rate probes (no counterpart in the paper): the arithmetic rates the
+ * library's rooflines are quoted against, measured by its own kernels.
+ * kind: TRX_PEAK_FFMA (FP32 FMA, CUDA cores), TRX_PEAK_DFMA (FP64 FMA),
+ * TRX_PEAK_DMMA (FP64 mma.sync m8n8k4), TRX_PEAK_TC_TF32 (tcgen05.mma
+ * kind::tf32, 128x256x8), TRX_PEAK_TC_BF16 (tcgen05.mma kind::f16, BF16,
+ * 128x256x16). One launch (one CTA per SM for the tensor-core kinds, eight
+ * of 256 threads per SM otherwise) of `iters` loop steps on `device`,
+ * timed with CUDA events: *tflops = dense TFLOP/s (2 flop per
+ * multiply-add), *ms (may be NULL) = the launch's time. Synchronous;
+ * allocates and frees 64 KiB. Returns 0, TRX_ERR_INVALID_VALUE,
+ * TRX_ERR_DEVICE, TRX_ERR_CUDA, or TRX_ERR_TIMEOUT if the tensor-core
+ * probe's bounded wait (2 s) gave up. */
+enum {
+    TRX_PEAK_FFMA = 0,
+    TRX_PEAK_DFMA = 1,
+    TRX_PEAK_DMMA = 2,
+    TRX_PEAK_TC_TF32 = 3,
+    TRX_PEAK_TC_BF16 = 4
+};
+int trx_peak_probe(int device, int kind, int64_t iters, double* tflops, double* ms);
 
 /* Library version as major*10000 + minor*100 + patch. */
 int trx_version(void);

@@ -21,7 +21,9 @@ OPT_LEAF, OPT_GEMM, OPT_GRAPH, OPT_PROFILE, OPT_WAIT_LIMIT, OPT_PDL, OPT_PANELS 
 OPT_TRMM_DENSE = 8
 OPT_RESIDUAL = 9
 OPT_TRSM_TC_LEAF = 10
-RESIDUAL_AUTO, RESIDUAL_FP64, RESIDUAL_FLOAT_FLOAT = 0, 1, 2
+OPT_SPLIT = 11          # tensor-core split: 1, 3 or 6 product terms (0: automatic, 6)
+OPT_FP64_TRSM = 12      # trx_dtrsm: 0 DFMA recursion; n: FP32 solve + n float-float corrections
+RESIDUAL_AUTO, RESIDUAL_FP64, RESIDUAL_FLOAT_FLOAT, RESIDUAL_TC = 0, 1, 2, 3
 GEMM_AUTO, GEMM_SIMT, GEMM_TC = 0, 1, 2
 KERNEL_CLASSES = ("leaf_trsm", "leaf_trmm", "gemm_tc", "gemm_simt", "convert", "other")
 ERR_TIMEOUT = 4
@@ -63,7 +65,8 @@ class ServerConfig(ctypes.Structure):
     """trx_server_config_t."""
     _fields_ = [("streams", ctypes.c_int), ("small_k", ctypes.c_int),
                 ("max_inflight", ctypes.c_int64), ("budget_bytes", ctypes.c_size_t),
-                ("workspace_bytes", ctypes.c_size_t), ("graphs", ctypes.c_int)]
+                ("workspace_bytes", ctypes.c_size_t), ("graphs", ctypes.c_int),
+                ("refine_corrections", ctypes.c_int), ("fp64_corrections", ctypes.c_int)]
 
 
 class _Profile(ctypes.Structure):
@@ -122,6 +125,8 @@ def load_library() -> ctypes.CDLL:
         lib.trx_strsm_refined.argtypes = [vp, c, c, c, c, i64, i64, ctypes.c_float, vp, i64, vp,
                                           i64, vp, i64, ctypes.c_int, ctypes.c_double,
                                           ctypes.POINTER(RefineInfo), vp]
+        lib.trx_strsm_refined_async.argtypes = [vp, c, c, c, c, i64, i64, ctypes.c_float, vp,
+                                                i64, vp, i64, vp, i64, ctypes.c_int, vp]
         lib.trx_server_create.argtypes = [ctypes.c_int, ctypes.POINTER(ServerConfig),
                                           ctypes.POINTER(vp)]
         lib.trx_server_destroy.argtypes = [vp]
@@ -130,12 +135,18 @@ def load_library() -> ctypes.CDLL:
         lib.trx_server_release_factor.argtypes = [vp, ctypes.c_int]
         lib.trx_server_submit.argtypes = [vp, ctypes.c_int, c, c, ctypes.c_double, vp, i64, i64,
                                           i64, vp, ctypes.POINTER(i64)]
+        lib.trx_server_submit_refined.argtypes = [vp, ctypes.c_int, c, ctypes.c_double, vp, i64,
+                                                  i64, i64, vp, i64, vp, ctypes.POINTER(i64)]
         lib.trx_server_poll.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(ctypes.c_int),
                                         ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
         lib.trx_server_pending.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(i64),
                                            ctypes.POINTER(i64)]
         lib.trx_server_wait.argtypes = [vp]
         lib.trx_version.argtypes = []
+        lib.trx_peak_probe.argtypes = [ctypes.c_int, ctypes.c_int, i64,
+                                       ctypes.POINTER(ctypes.c_double),
+                                       ctypes.POINTER(ctypes.c_double)]
+        lib.trx_noalloc_check_error.argtypes = []
         _lib = lib
         return lib
 
@@ -308,7 +319,9 @@ def trsm_refined(side: str, uplo: str, trans: str, diag: str, alpha: float, A, B
     the recursive path (Section 3.1) and adds it in FP64. ``tol`` bounds the
     normwise backward error ||R|| / (||op(A)|| ||X||) (infinity norms);
     by default sqrt(k) * 2**-53. The residual's arithmetic is the handle's
-    OPT_RESIDUAL (float-float on the FP32 pipes unless set to RESIDUAL_FP64). Returns (X, info) with info a dict:
+    OPT_RESIDUAL (float-float on the FP32 pipes unless set to RESIDUAL_FP64 or
+    RESIDUAL_TC, the FP32-grade tensor-core residual for targets down to about
+    1e-7). Returns (X, info) with info a dict:
     iterations, residual_norm, backward_error, initial_backward_error.
     """
     import torch
@@ -333,7 +346,14 @@ def trsm_refined(side: str, uplo: str, trans: str, diag: str, alpha: float, A, B
     if tol is None:
         tol = max(k, 1) ** 0.5 * 2.0 ** -53
     h = handle if handle is not None else default_handle(B.device)
-    h.ensure_workspace(h.workspace_size("S", side, m, n, 4))
+    need = h.workspace_size("S", side, m, n, 4)
+    if h.get_option(OPT_RESIDUAL) == RESIDUAL_TC:
+        # the tensor-core residual's TRMM uses the 6-term planes
+        terms = h.get_option(OPT_SPLIT)
+        h.set_option(OPT_SPLIT, 6)
+        need = max(need, h.workspace_size("M", side, m, n, 4))
+        h.set_option(OPT_SPLIT, terms)
+    h.ensure_workspace(need)
     info = RefineInfo()
     rc = lib.trx_strsm_refined(h.ptr, _char(side), _char(uplo), _char(trans), _char(diag), m, n,
                                float(alpha), a_ptr, lda, b_ptr, ldb, x_ptr, ldx, int(max_iter),
@@ -342,6 +362,37 @@ def trsm_refined(side: str, uplo: str, trans: str, diag: str, alpha: float, A, B
     return out, {"iterations": info.iterations, "residual_norm": info.residual_norm,
                  "backward_error": info.backward_error,
                  "initial_backward_error": info.initial_backward_error}
+
+
+def trsm_refined_async(side: str, uplo: str, trans: str, diag: str, alpha: float, A, B, *,
+                       corrections: int = 2, out=None, handle: Handle | None = None,
+                       stream=None):
+    """FP32 solve plus a fixed number of float-float corrections, enqueued
+    without any host read-back (trx_strsm_refined_async). A, B float32 CUDA
+    tensors (B unchanged); returns the float64 result tensor (``out`` if
+    given)."""
+    import torch
+    lib = load_library()
+    if A.dtype != torch.float32 or B.dtype != torch.float32:
+        raise TypeError(f"A and B must be float32 (got {A.dtype}, {B.dtype})")
+    if not (A.is_cuda and B.is_cuda) or A.device != B.device:
+        raise ValueError("A and B must be CUDA tensors on one device")
+    m, n = B.shape
+    k = m if side.upper() == "L" else n
+    if tuple(A.shape) != (k, k):
+        raise ValueError(f"A must be {k}x{k} for side {side!r} and B {m}x{n}")
+    if out is None:
+        out = torch.empty((n, m), dtype=torch.float64, device=B.device).t()
+    a_ptr, lda = _colmajor(A, "A")
+    b_ptr, ldb = _colmajor(B, "B")
+    x_ptr, ldx = _colmajor(out, "out")
+    h = handle if handle is not None else default_handle(B.device)
+    h.ensure_workspace(h.workspace_size("S", side, m, n, 4))
+    rc = lib.trx_strsm_refined_async(h.ptr, _char(side), _char(uplo), _char(trans), _char(diag),
+                                     m, n, float(alpha), a_ptr, lda, b_ptr, ldb, x_ptr, ldx,
+                                     int(corrections), _stream_ptr(stream, B.device))
+    _check(rc, "trx_strsm_refined_async")
+    return out
 
 
 def debug_plan(op: str, side, uplo, trans, diag, m, n, elem_bytes=4, leaf=0, gemm=0,
@@ -569,6 +620,19 @@ def batched_autotune(problems, *, handle: Handle | None = None, stream=None) -> 
     _check(lib.trx_batched_autotune(h.ptr, elem, len(problems), arr, s_ptr, buf, len(buf)),
            "trx_batched_autotune")
     return json.loads(buf.value.decode())
+
+
+PEAK_KINDS = {"ffma": 0, "dfma": 1, "dmma": 2, "tc_tf32": 3, "tc_bf16": 4}
+
+
+def peak_probe(kind: str, iters: int, device: int = 0) -> tuple[float, float]:
+    """One launch of the library's peak-rate probe ``kind`` (PEAK_KINDS):
+    (dense TFLOP/s, milliseconds)."""
+    lib = load_library()
+    t, ms = ctypes.c_double(), ctypes.c_double()
+    _check(lib.trx_peak_probe(int(device), PEAK_KINDS[kind], int(iters), ctypes.byref(t),
+                              ctypes.byref(ms)), "trx_peak_probe")
+    return t.value, ms.value
 
 
 def to_colmajor(x):

@@ -133,19 +133,36 @@ Canon<T> canonicalize(char side, char uplo, char transa, char diag, int64_t m, i
     return c;
 }
 
+// Workspace of the tensor-core path: `slices` M planes then `slices` Y
+// planes (m_bytes and y_bytes each).
 struct WsLayout {
     int64_t ldm = 0, ldy = 0;
+    int slices = 2;
     size_t m_bytes = 0, y_bytes = 0, total = 0;
 };
 
-WsLayout ws_layout(int64_t k, int64_t nrhs) {
+WsLayout ws_layout(int64_t k, int64_t nrhs, int slices) {
     WsLayout w;
     w.ldm = round_up(std::max<int64_t>(k, 1), 64);
     w.ldy = w.ldm;
+    w.slices = slices;
     w.m_bytes = align256((size_t)k * w.ldm * 2);
     w.y_bytes = align256((size_t)nrhs * w.ldy * 2);
-    w.total = 2 * w.m_bytes + 2 * w.y_bytes;
+    w.total = (size_t)slices * (w.m_bytes + w.y_bytes);
     return w;
+}
+
+// Plane pointers of a workspace laid out as above (M planes from m_base
+// unless the caller supplies them, Y planes from y_base).
+void set_m_planes(Planes& pl, char* m_base, size_t m_bytes, int slices) {
+    pl.m_hi = reinterpret_cast<__nv_bfloat16*>(m_base);
+    pl.m_lo = slices > 1 ? reinterpret_cast<__nv_bfloat16*>(m_base + m_bytes) : nullptr;
+    pl.m_lo2 = slices > 2 ? reinterpret_cast<__nv_bfloat16*>(m_base + 2 * m_bytes) : nullptr;
+}
+void set_y_planes(Planes& pl, char* y_base, size_t y_bytes, int slices) {
+    pl.y_hi = reinterpret_cast<__nv_bfloat16*>(y_base);
+    pl.y_lo = slices > 1 ? reinterpret_cast<__nv_bfloat16*>(y_base + y_bytes) : nullptr;
+    pl.y_lo2 = slices > 2 ? reinterpret_cast<__nv_bfloat16*>(y_base + 2 * y_bytes) : nullptr;
 }
 
 }  // namespace
@@ -157,6 +174,8 @@ struct trx_handle_s {
     size_t ws_bytes = 0;
     bool ws_owned = false;
     int64_t opt_leaf = 0, opt_gemm = 0, opt_graph = 1, opt_profile = 0, opt_pdl = 0;
+    int64_t opt_split = 0;   // product terms of the tensor-core split (0: automatic)
+    int64_t opt_fp64_trsm = 0;   // FP64 TRSM: 0 DFMA; n > 0 FP32 solve + n corrections
     long long wait_ns = kDefaultWaitNs;
     int* d_err = nullptr;
     cudaStream_t cap_stream = nullptr;
@@ -199,6 +218,9 @@ namespace {
 
 bool valid(trx_handle_t h) { return h != nullptr && h->magic == kMagic; }
 
+// Slices per operand of the handle's tensor-core split.
+int slices_for(const trx_handle_s* h) { return slices_of_terms(split_terms(h->opt_split)); }
+
 cudaEvent_t get_event(trx_handle_t h) {
     if (!h->free_events.empty()) {
         cudaEvent_t e = h->free_events.back();
@@ -228,6 +250,7 @@ struct Exec {
     const void* maps_w = nullptr;
     __nv_bfloat16* w_hi = nullptr;
     __nv_bfloat16* w_lo = nullptr;
+    __nv_bfloat16* w_lo2 = nullptr;
     cudaStream_t s;
     bool profile;
 
@@ -259,11 +282,12 @@ struct Exec {
                         TcYOut yo;
                         yo.hi = pl.y_hi;
                         yo.lo = pl.y_lo;
+                        yo.lo2 = pl.y_lo2;
                         yo.ld = pl.ldy;
                         yo.row0 = st.y0;
                         yo.row1 = st.y1;
                         e = launch_gemm_tc(*reinterpret_cast<const Canon<float>*>(&c),
-                                           st.inv ? maps_w : maps, st.gemms.data(),
+                                           st.inv ? maps_w : maps, pl.slices, st.gemms.data(),
                                            (int)st.gemms.size(), (float)st.beta, (float)st.gamma,
                                            h->d_err, h->wait_ns, h->num_sms, s, st.dense,
                                            st.y1 > st.y0 ? &yo : nullptr);
@@ -308,7 +332,7 @@ struct Exec {
                     break;
                 case kInvDiag:
                     e = launch_invert_diag(*reinterpret_cast<const Canon<float>*>(&c), st.b, w_hi,
-                                           w_lo, pl.ldm, s);
+                                           w_lo, w_lo2, pl.slices, pl.ldm, s);
                     cls = TRX_KERNEL_CONVERT;
                     bytes = 4.0 * c.k * st.b * 1.5;
                     break;
@@ -324,7 +348,7 @@ struct Exec {
 };
 
 struct GraphKey {
-    int op, elem, tc, b;
+    int op, elem, tc, b, slices;
     int64_t k, nrhs, a_rs, a_cs, c_rs, c_cs, unit;
     const void* A;
     const void* C;
@@ -347,11 +371,14 @@ struct trx_factor_s {
     const float* A = nullptr;
     __nv_bfloat16* m_hi = nullptr;   // null when k is too small for the tensor-core path
     __nv_bfloat16* m_lo = nullptr;
+    __nv_bfloat16* m_lo2 = nullptr;
     int64_t ldm = 0;
+    int slices = 2;                  // of the planes (the handle's split at creation)
     // inverted diagonal blocks of w_block rows (TRSM leaves on the tensor
     // cores), made by updates while the handle's TRX_OPT_TRSM_TC_LEAF is on
     __nv_bfloat16* w_hi = nullptr;
     __nv_bfloat16* w_lo = nullptr;
+    __nv_bfloat16* w_lo2 = nullptr;
     int w_block = 0;
 };
 
@@ -362,10 +389,15 @@ constexpr int kFactorMagic = 0x54524631;   // "TRF1"
 // TRMM diagonal-block size up to this one reads them as dense tiles.
 constexpr int kFactorDenseRows = 2048;
 
+int refine_fixed(trx_handle_t h, bool fp64_data, char side, char uplo, char transa, char diag,
+                 int64_t m, int64_t n, double alpha, const void* A, int64_t lda, const void* B,
+                 int64_t ldb, double* X, int64_t ldx, int corrections, void* stream);
+int refine_scratch(trx_handle_t h, size_t need, cudaStream_t s);
+
 template <typename T>
 int execute(trx_handle_t h, bool trsm, char side, char uplo, char transa, char diag, int64_t m,
             int64_t n, T alpha, const T* A, int64_t lda, T* B, int64_t ldb, void* stream,
-            const trx_factor_s* f = nullptr) {
+            const trx_factor_s* f = nullptr, int terms_override = 0) {
     const int info = check_args(side, uplo, transa, diag, m, n, A, lda, B, ldb);
     if (info) return info;
     if (!valid(h)) return TRX_ERR_HANDLE;
@@ -378,6 +410,10 @@ int execute(trx_handle_t h, bool trsm, char side, char uplo, char transa, char d
         e = launch_zero<T>(B, m, n, ldb, s);
         return e == cudaSuccess ? TRX_SUCCESS : fail_cuda(e, "zero");
     }
+    if (std::is_same<T, double>::value && trsm && h->opt_fp64_trsm > 0)
+        return refine_fixed(h, true, side, uplo, transa, diag, m, n, (double)alpha, A, lda, B,
+                            ldb, reinterpret_cast<double*>(B), ldb, (int)h->opt_fp64_trsm,
+                            stream);
     Exec<T> ex;
     ex.h = h;
     ex.c = canonicalize<T>(side, uplo, transa, diag, m, n, A, lda, B, ldb);
@@ -388,11 +424,14 @@ int execute(trx_handle_t h, bool trsm, char side, char uplo, char transa, char d
 
     Plan plan;
     plan.tc = use_tc<T>(h, k, trsm, ex.c.nrhs);
-    // A prepared factor supplies the M planes: the workspace holds Y only.
+    // A prepared factor supplies the M planes (and its split): the workspace
+    // holds Y only.
     const bool factor_planes = plan.tc && f != nullptr && f->m_hi != nullptr;
+    const int slices = factor_planes ? f->slices
+                       : terms_override ? slices_of_terms(terms_override) : slices_for(h);
     if (plan.tc) {
-        const WsLayout w = ws_layout(k, ex.c.nrhs);
-        const size_t need = factor_planes ? 2 * w.y_bytes : w.total;
+        const WsLayout w = ws_layout(k, ex.c.nrhs, slices);
+        const size_t need = factor_planes ? (size_t)slices * w.y_bytes : w.total;
         if (h->ws == nullptr || h->ws_bytes < need) {
             snprintf(g_detail, sizeof(g_detail), "workspace of %zu bytes needed, %zu set",
                      need, h->ws_bytes);
@@ -401,16 +440,15 @@ int execute(trx_handle_t h, bool trsm, char side, char uplo, char transa, char d
         char* base = static_cast<char*>(h->ws);
         ex.pl.ldm = w.ldm;
         ex.pl.ldy = w.ldy;
+        ex.pl.slices = slices;
         if (factor_planes) {
             ex.pl.m_hi = f->m_hi;
             ex.pl.m_lo = f->m_lo;
-            ex.pl.y_hi = reinterpret_cast<__nv_bfloat16*>(base);
-            ex.pl.y_lo = reinterpret_cast<__nv_bfloat16*>(base + w.y_bytes);
+            ex.pl.m_lo2 = f->m_lo2;
+            set_y_planes(ex.pl, base, w.y_bytes, slices);
         } else {
-            ex.pl.m_hi = reinterpret_cast<__nv_bfloat16*>(base);
-            ex.pl.m_lo = reinterpret_cast<__nv_bfloat16*>(base + w.m_bytes);
-            ex.pl.y_hi = reinterpret_cast<__nv_bfloat16*>(base + 2 * w.m_bytes);
-            ex.pl.y_lo = reinterpret_cast<__nv_bfloat16*>(base + 2 * w.m_bytes + w.y_bytes);
+            set_m_planes(ex.pl, base, w.m_bytes, slices);
+            set_y_planes(ex.pl, base + (size_t)slices * w.m_bytes, w.y_bytes, slices);
         }
     }
     // TRSM leaves on the tensor cores: the inverted diagonal blocks sit in
@@ -423,6 +461,7 @@ int execute(trx_handle_t h, bool trsm, char side, char uplo, char transa, char d
     if (plan.tc_leaf) {
         ex.w_hi = factor_planes ? f->w_hi : ex.pl.m_hi;
         ex.w_lo = factor_planes ? f->w_lo : ex.pl.m_lo;
+        ex.w_lo2 = factor_planes ? f->w_lo2 : ex.pl.m_lo2;
     }
     // TRSM right-hand sides are independent: with many of them the chain runs
     // as P column-panel branches (forked streams, one graph), so the
@@ -444,7 +483,8 @@ int execute(trx_handle_t h, bool trsm, char side, char uplo, char transa, char d
             x.c.nrhs = std::min<int64_t>(step, ex.c.nrhs - j0);
             if (plan.tc) {
                 x.pl.y_hi = ex.pl.y_hi + j0 * ex.pl.ldy;
-                x.pl.y_lo = ex.pl.y_lo + j0 * ex.pl.ldy;
+                if (ex.pl.y_lo) x.pl.y_lo = ex.pl.y_lo + j0 * ex.pl.ldy;
+                if (ex.pl.y_lo2) x.pl.y_lo2 = ex.pl.y_lo2 + j0 * ex.pl.ldy;
                 maps[i].resize(2 * tc_maps_size());
                 e = tc_make_maps(x.pl, k, x.c.nrhs, maps[i].data());
                 if (e != cudaSuccess) return fail_cuda(e, "tensor map encode");
@@ -454,6 +494,7 @@ int execute(trx_handle_t h, bool trsm, char side, char uplo, char transa, char d
                     Planes wp = x.pl;
                     wp.m_hi = ex.w_hi;
                     wp.m_lo = ex.w_lo;
+                    wp.m_lo2 = ex.w_lo2;
                     e = tc_make_maps(wp, k, x.c.nrhs, maps[i].data() + tc_maps_size());
                     if (e != cudaSuccess) return fail_cuda(e, "tensor map encode");
                     x.maps_w = maps[i].data() + tc_maps_size();
@@ -511,6 +552,7 @@ int execute(trx_handle_t h, bool trsm, char side, char uplo, char transa, char d
     key.elem = sizeof(T);
     key.tc = plan.tc;
     key.b = b;
+    key.slices = plan.tc ? slices : 0;
     key.k = k;
     key.nrhs = ex.c.nrhs;
     key.a_rs = ex.c.a_rs;
@@ -564,7 +606,25 @@ int execute(trx_handle_t h, bool trsm, char side, char uplo, char transa, char d
 
 }  // namespace
 
+namespace {
+void drop_graphs(trx_handle_t h);
+void free_owned_ws(trx_handle_t h);
+}  // namespace
+
 namespace trx {
+
+// The request server's workspace growth: swap without a device-wide
+// synchronisation (the server has waited for the handle's stream, the only
+// one its work runs on). Cached graphs point into the old buffer: dropped.
+int handle_swap_workspace(trx_handle_t h, void* ptr, size_t bytes) {
+    if (!valid(h)) return TRX_ERR_HANDLE;
+    if ((reinterpret_cast<uintptr_t>(ptr) & 255) != 0) return TRX_ERR_INVALID_VALUE;
+    drop_graphs(h);
+    free_owned_ws(h);
+    h->ws = ptr;
+    h->ws_bytes = ptr ? bytes : 0;
+    return TRX_SUCCESS;
+}
 
 // For trx_strsm_noalloc (noalloc.cu): BLAS argument check, the scratch a
 // call needs on the tensor-core path, and the call itself with a caller-
@@ -579,18 +639,21 @@ size_t noalloc_scratch_bytes(char side, int64_t m, int64_t n) {
     const int64_t k = upc(side) == 'L' ? m : n, nrhs = upc(side) == 'L' ? n : m;
     if (k <= 0 || nrhs <= 0) return 0;
     const int b = leaf_for(0, k, true, 4, nrhs);
-    return use_tc_mode(4, 0, k, b) ? ws_layout(k, nrhs).total : 0;
+    return use_tc_mode(4, 0, k, b) ? ws_layout(k, nrhs, slices_of_terms(split_terms(0))).total
+                                   : 0;
 }
 
 int noalloc_strsm(int device, int num_sms, void* scratch, size_t scratch_bytes, int* err_word,
-                  char side, char uplo, char transa, char diag, int64_t m, int64_t n, float alpha,
-                  const float* A, int64_t lda, float* B, int64_t ldb, void* stream) {
+                  long long wait_ns, char side, char uplo, char transa, char diag, int64_t m,
+                  int64_t n, float alpha, const float* A, int64_t lda, float* B, int64_t ldb,
+                  void* stream) {
     trx_handle_s hs;
     hs.device = device;
     hs.num_sms = num_sms;
     hs.ws = scratch;
     hs.ws_bytes = scratch_bytes;
     hs.d_err = err_word;
+    hs.wait_ns = wait_ns;
     hs.opt_graph = 0;
     hs.opt_panels = 1;   // no handle streams here: one chain on the caller's stream
     return execute<float>(&hs, true, side, uplo, transa, diag, m, n, alpha, A, lda, B, ldb,
@@ -1013,7 +1076,10 @@ int trx_destroy(trx_handle_t h) {
     if (h->b_counter) cudaFree(h->b_counter);
     if (h->b_host) cudaFreeHost(h->b_host);
     if (h->b_uploaded) cudaEventDestroy(h->b_uploaded);
-    if (h->rf_buf) cudaFree(h->rf_buf);
+    if (h->rf_buf) {
+        cudaFreeAsync(h->rf_buf, 0);        // stream-ordered allocation
+        cudaDeviceSynchronize();
+    }
     free_owned_ws(h);
     if (h->d_err) cudaFree(h->d_err);
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
@@ -1054,16 +1120,20 @@ int trx_workspace_size(trx_handle_t h, char op, char side, int64_t m, int64_t n,
     if (o == 'Y') {         // factor calls (TRSM or TRMM): the Y planes only
         const bool tc = elem_bytes == 4 &&
                         (use_tc<float>(h, k, true, nrhs) || use_tc<float>(h, k, false, nrhs));
-        *bytes = (tc && k > 0 && nrhs > 0) ? 2 * ws_layout(k, nrhs).y_bytes : 0;
+        *bytes = (tc && k > 0 && nrhs > 0)
+                     ? (size_t)slices_for(h) * ws_layout(k, nrhs, slices_for(h)).y_bytes
+                     : 0;
         return TRX_SUCCESS;
     }
-    bool tc = elem_bytes == 4 ? use_tc<float>(h, k, o == 'S', nrhs) : false;
+    // FP64 TRSM on the mixed engine solves in FP32: that call's planes
+    const bool mixed64 = elem_bytes == 8 && o == 'S' && h->opt_fp64_trsm > 0;
+    bool tc = (elem_bytes == 4 || mixed64) ? use_tc<float>(h, k, o == 'S', nrhs) : false;
     if (upc(op) == 'G') {   // tensor-core trx_sgemm_update: m = M + K rows, n = N
         k = m;
         nrhs = n;
         tc = true;
     }
-    *bytes = (tc && k > 0 && nrhs > 0) ? ws_layout(k, nrhs).total : 0;
+    *bytes = (tc && k > 0 && nrhs > 0) ? ws_layout(k, nrhs, slices_for(h)).total : 0;
     return TRX_SUCCESS;
 }
 
@@ -1111,6 +1181,11 @@ int trx_strsm_refined(trx_handle_t h, char side, char uplo, char transa, char di
     const char transI = (left ? trans : !trans) ? 'T' : 'N';
     const bool lower = upc(uplo) == 'L', unit = upc(diag) == 'U';
     const bool fp64_residual = h->opt_residual == 1;
+    // FP32-grade residual on the tensor cores: op(A) fl32(X) by the library's
+    // own FP32 TRMM with the 6-term split (accurate to a few units of 2^-24
+    // of |op(A)| |X|: enough for backward errors down to about 1e-7)
+    const bool tc_residual = h->opt_residual == 3;
+    const bool ff_residual = !fp64_residual && !tc_residual;
     const bool lowerI = lower != (transI == 'T');
     // scratch: Xi, B64, R64 (k x nr FP64), D32 (k x nr FP32), row/column
     // sums, norms, and either the packed op(A) and X of the float-float
@@ -1118,27 +1193,16 @@ int trx_strsm_refined(trx_handle_t h, char side, char uplo, char transa, char di
     const size_t mn64 = align256((size_t)k * nr * 8), mn32 = align256((size_t)k * nr * 4);
     const size_t sums = align256(std::max((size_t)std::max(k, nr) * 8, refine_norm_scratch(k)));
     const size_t a64 = fp64_residual ? align256((size_t)k * k * 8) : 0;
-    const size_t ap = fp64_residual ? 0 : align256(refine_pack_a_bytes(k, lowerI));
-    const size_t xp = fp64_residual ? 0 : align256(refine_pack_x_bytes(k, nr));
+    const size_t ap = ff_residual ? align256(refine_pack_a_bytes(k, lowerI)) : 0;
+    const size_t xp = ff_residual ? align256(refine_pack_x_bytes(k, nr)) : 0;
     std::vector<int4> units, tiles;
     int64_t slots = 0;
-    if (!fp64_residual) refine_plan_units(k, lowerI, units, tiles, slots);
+    if (ff_residual) refine_plan_units(k, lowerI, units, tiles, slots);
     const size_t ub = align256((units.size() + tiles.size()) * sizeof(int4));
     const size_t pb = align256((size_t)slots * 64 * (size_t)nr * 8);
     const size_t need = 3 * mn64 + mn32 + sums + 256 + a64 + ap + xp + ub + pb;
-    if (h->rf_bytes < need) {
-        if (h->rf_buf) {
-            cudaStreamSynchronize(s);
-            cudaFree(h->rf_buf);
-        }
-        h->rf_buf = nullptr;
-        h->rf_bytes = 0;
-        if ((e = cudaMalloc(&h->rf_buf, need)) != cudaSuccess) {
-            snprintf(g_detail, sizeof(g_detail), "refine scratch: %s", cudaGetErrorString(e));
-            return TRX_ERR_ALLOC;
-        }
-        h->rf_bytes = need;
-    }
+    int rc0 = refine_scratch(h, need, s);
+    if (rc0 != TRX_SUCCESS) return rc0;
     char* base = static_cast<char*>(h->rf_buf);
     double* Xi = reinterpret_cast<double*>(base);
     double* B64 = reinterpret_cast<double*>(base + mn64);
@@ -1148,11 +1212,11 @@ int trx_strsm_refined(trx_handle_t h, char side, char uplo, char transa, char di
     double* norms = reinterpret_cast<double*>(base + 3 * mn64 + mn32 + sums);
     char* tail = base + 3 * mn64 + mn32 + sums + 256;
     double* A64 = fp64_residual ? reinterpret_cast<double*>(tail) : nullptr;
-    void* Ap = fp64_residual ? nullptr : tail;
-    void* Xp = fp64_residual ? nullptr : tail + ap;
-    int4* Ud = fp64_residual ? nullptr : reinterpret_cast<int4*>(tail + ap + xp);
+    void* Ap = ff_residual ? tail : nullptr;
+    void* Xp = ff_residual ? tail + ap : nullptr;
+    int4* Ud = ff_residual ? reinterpret_cast<int4*>(tail + ap + xp) : nullptr;
     int4* Td = Ud ? Ud + units.size() : nullptr;
-    double* part = fp64_residual ? nullptr : reinterpret_cast<double*>(tail + ap + xp + ub);
+    double* part = ff_residual ? reinterpret_cast<double*>(tail + ap + xp + ub) : nullptr;
     // infinity norms of the caller's m x n arrays: row sums of the internal
     // k x nr array for side L, column sums for side R
     auto norm = [&](const double* a, double* out) {
@@ -1172,10 +1236,10 @@ int trx_strsm_refined(trx_handle_t h, char side, char uplo, char transa, char di
                   : refine_transpose_f32_f64(B, ldb, B64, k, m, n, (double)alpha, s)) !=
             cudaSuccess ||
         (fp64_residual && (e = refine_cast_f32_f64(A, lda, A64, k, k, k, 1.0, s)) != cudaSuccess) ||
-        (!fp64_residual &&
+        (ff_residual &&
          (e = refine_pack_a(A, lda, k, lowerI, transI == 'T', unit, Ap, s)) != cudaSuccess))
         return fail_cuda(e, "refine setup");
-    if (!fp64_residual) {
+    if (ff_residual) {
         // the work-unit table (pageable source: staged before the call returns)
         std::vector<int4> table(units);
         table.insert(table.end(), tiles.begin(), tiles.end());
@@ -1192,7 +1256,17 @@ int trx_strsm_refined(trx_handle_t h, char side, char uplo, char transa, char di
     int it = 0;
     for (;; ++it) {
         // 2. the residual R = alpha B - op(A) X, products of FP32 data exact
-        if (fp64_residual) {
+        if (tc_residual) {
+            // D32 := fl32(X), D32 := op(A) D32 (6-term split TRMM),
+            // R := alpha B - D32 in FP64
+            if ((e = refine_cast_f64_f32(Xi, k, D32, k, k, nr, s)) != cudaSuccess)
+                return fail_cuda(e, "refine cast");
+            if ((rc = execute<float>(h, false, 'L', uplo, transI, diag, k, nr, 1.0f, A, lda, D32,
+                                     k, stream, nullptr, 6)) != TRX_SUCCESS)
+                return rc;
+            e = refine_cast_f32_f64(D32, k, R64, k, k, nr, 1.0, s);
+            if (e == cudaSuccess) e = refine_residual(B64, k, R64, k, k, nr, s);
+        } else if (fp64_residual) {
             // from X each time, on the FP64 pipe
             if ((e = cudaMemcpyAsync(R64, Xi, (size_t)k * nr * 8, cudaMemcpyDeviceToDevice, s)) !=
                 cudaSuccess)
@@ -1254,7 +1328,7 @@ int trx_strsm_refined(trx_handle_t h, char side, char uplo, char transa, char di
         if ((e = refine_add(Xi, k, D32, k, k, nr, s)) != cudaSuccess ||
             (e = norm(Xi, norms + 2)) != cudaSuccess)
             return fail_cuda(e, "refine update");
-        if (!fp64_residual &&
+        if (ff_residual &&
             ((e = refine_norm_f32(D32, k, k, nr, !left, sm, norms + 3, s)) != cudaSuccess ||
              (e = cudaMemcpyAsync(host + 2, norms + 2, 2 * sizeof(double), cudaMemcpyDeviceToHost,
                                   s)) != cudaSuccess ||
@@ -1267,6 +1341,150 @@ int trx_strsm_refined(trx_handle_t h, char side, char uplo, char transa, char di
     if (e != cudaSuccess) return fail_cuda(e, "refine result");
     if (info) *info = trx_refine_info_t{it, rnorm, eta, eta0};
     return TRX_SUCCESS;
+}
+
+}  // extern "C"
+
+namespace {
+
+// Grow the handle's refinement scratch to `need` bytes (a call that needs
+// more than any before it). Stream-ordered: the old buffer is released after
+// the stream's earlier work and the new one allocated in stream order, so
+// neither the host nor the device waits.
+int refine_scratch(trx_handle_t h, size_t need, cudaStream_t s) {
+    if (h->rf_bytes >= need) return TRX_SUCCESS;
+    if (h->rf_buf) cudaFreeAsync(h->rf_buf, s);
+    h->rf_buf = nullptr;
+    h->rf_bytes = 0;
+    cudaError_t e = cudaMallocAsync(&h->rf_buf, need, s);
+    if (e != cudaSuccess) {
+        snprintf(g_detail, sizeof(g_detail), "refine scratch: %s", cudaGetErrorString(e));
+        return TRX_ERR_ALLOC;
+    }
+    h->rf_bytes = need;
+    return TRX_SUCCESS;
+}
+
+// Refinement with a fixed number of corrections and no host read-back:
+// every step is enqueued on the stream. Data FP32 (A, B float) or FP64 (A,
+// B double: the solves run on fl32(A) in FP32, the residual takes A as float
+// pairs). X (FP64, leading dimension ldx) may be B for FP64 data (in place).
+// Steps (side L internally; side R on the transposes, as trx_strsm_refined):
+//   X := the FP32 solve of op(A) X = alpha B
+//   repeat `corrections` times:
+//     R := alpha B - op(A) X   (float-float on the FP32 pipes, from X)
+//     D := the FP32 solve of op(A) D = fl32(R);  X := X + D (FP64)
+int refine_fixed(trx_handle_t h, bool fp64_data, char side, char uplo, char transa, char diag,
+                 int64_t m, int64_t n, double alpha, const void* A, int64_t lda, const void* B,
+                 int64_t ldb, double* X, int64_t ldx, int corrections, void* stream) {
+    if (m == 0 || n == 0) return TRX_SUCCESS;
+    cudaError_t e = cudaSetDevice(h->device);
+    if (e != cudaSuccess) return fail_cuda(e, "cudaSetDevice");
+    const cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const bool left = upc(side) == 'L';
+    const int64_t k = left ? m : n, nr = left ? n : m;
+    const bool trans = upc(transa) != 'N';
+    const char transI = (left ? trans : !trans) ? 'T' : 'N';
+    const bool lower = upc(uplo) == 'L', unit = upc(diag) == 'U';
+    const bool lowerI = lower != (transI == 'T');
+    const size_t mn64 = align256((size_t)k * nr * 8), mn32 = align256((size_t)k * nr * 4);
+    const size_t a32 = fp64_data ? align256((size_t)k * k * 4) : 0;
+    const size_t ap = align256(refine_pack_a_bytes(k, lowerI));
+    const size_t xp = align256(refine_pack_x_bytes(k, nr));
+    std::vector<int4> units, tiles;
+    int64_t slots = 0;
+    refine_plan_units(k, lowerI, units, tiles, slots);     // counts (the table: on the device)
+    const size_t ub = align256((units.size() + tiles.size()) * sizeof(int4));
+    const size_t pb = align256((size_t)slots * 64 * (size_t)nr * 8);
+    const size_t need = 3 * mn64 + mn32 + a32 + ap + xp + ub + pb;
+    int rc = refine_scratch(h, need, s);
+    if (rc != TRX_SUCCESS) return rc;
+    char* base = static_cast<char*>(h->rf_buf);
+    double* Xi = reinterpret_cast<double*>(base);
+    double* B64 = reinterpret_cast<double*>(base + mn64);
+    double* R64 = reinterpret_cast<double*>(base + 2 * mn64);
+    float* D32 = reinterpret_cast<float*>(base + 3 * mn64);
+    char* tail = base + 3 * mn64 + mn32;
+    float* A32 = fp64_data ? reinterpret_cast<float*>(tail) : nullptr;
+    void* Ap = tail + a32;
+    void* Xp = tail + a32 + ap;
+    int4* Ud = reinterpret_cast<int4*>(tail + a32 + ap + xp);
+    int4* Td = Ud + units.size();
+    double* part = reinterpret_cast<double*>(tail + a32 + ap + xp + ub);
+    const float* As = fp64_data ? A32 : static_cast<const float*>(A);
+    const int64_t ldas = fp64_data ? k : lda;
+    const double* Bd = static_cast<const double*>(B);
+    const float* Bf = static_cast<const float*>(B);
+    // operands: fl32(A), D32 := B (for the first solve), B64 := alpha B, packed op(A)
+    if (fp64_data &&
+        (e = refine_cast_f64_f32(static_cast<const double*>(A), lda, A32, k, k, k, s)) !=
+            cudaSuccess)
+        return fail_cuda(e, "refine setup");
+    if (fp64_data)
+        e = left ? refine_cast_f64_f32(Bd, ldb, D32, k, k, nr, s)
+                 : refine_transpose_f64_f32(Bd, ldb, D32, k, m, n, s);
+    else
+        e = left ? cudaMemcpy2DAsync(D32, k * 4, Bf, ldb * 4, k * 4, nr, cudaMemcpyDeviceToDevice,
+                                     s)
+                 : refine_transpose_f32(Bf, ldb, D32, k, m, n, s);
+    if (e == cudaSuccess) {
+        if (fp64_data)
+            e = left ? refine_scale_f64(Bd, ldb, B64, k, k, nr, alpha, s)
+                     : refine_transpose_f64_scaled(Bd, ldb, B64, k, m, n, alpha, s);
+        else
+            e = left ? refine_cast_f32_f64(Bf, ldb, B64, k, k, nr, alpha, s)
+                     : refine_transpose_f32_f64(Bf, ldb, B64, k, m, n, alpha, s);
+    }
+    if (e == cudaSuccess)
+        e = fp64_data ? refine_pack_a64(static_cast<const double*>(A), lda, k, lowerI,
+                                        transI == 'T', unit, Ap, s)
+                      : refine_pack_a(static_cast<const float*>(A), lda, k, lowerI, transI == 'T',
+                                      unit, Ap, s);
+    if (e == cudaSuccess) e = refine_plan_units_device(k, lowerI, Ud, Td, s);
+    if (e != cudaSuccess) return fail_cuda(e, "refine setup");
+    // the FP32 solve, Xi := its result
+    if ((rc = execute<float>(h, true, 'L', uplo, transI, diag, k, nr, (float)alpha, As, ldas,
+                             D32, k, stream)) != TRX_SUCCESS)
+        return rc;
+    if ((e = refine_cast_f32_f64(D32, k, Xi, k, k, nr, 1.0, s)) != cudaSuccess)
+        return fail_cuda(e, "refine cast");
+    for (int it = 0; it < corrections; ++it) {
+        e = refine_pack_x(Xi, nullptr, k, k, nr, Xp, s);
+        if (e == cudaSuccess)
+            e = refine_residual_packed(fp64_data ? 3 : 0, Ap, Xp, Ud, (int64_t)units.size(), Td,
+                                       (int64_t)tiles.size(), part, k, lowerI, B64, k, R64, k, nr,
+                                       h->d_err, h->wait_ns, s);
+        if (e == cudaSuccess) e = refine_cast_f64_f32(R64, k, D32, k, k, nr, s);
+        if (e != cudaSuccess) return fail_cuda(e, "refine residual");
+        if ((rc = execute<float>(h, true, 'L', uplo, transI, diag, k, nr, 1.0f, As, ldas, D32, k,
+                                 stream)) != TRX_SUCCESS)
+            return rc;
+        if ((e = refine_add(Xi, k, D32, k, k, nr, s)) != cudaSuccess)
+            return fail_cuda(e, "refine update");
+    }
+    e = left ? cudaMemcpy2DAsync(X, ldx * 8, Xi, k * 8, k * 8, nr, cudaMemcpyDeviceToDevice, s)
+             : refine_transpose_f64(Xi, k, X, ldx, k, nr, s);
+    return e == cudaSuccess ? TRX_SUCCESS : fail_cuda(e, "refine result");
+}
+
+}  // namespace
+
+extern "C" {
+
+int trx_strsm_refined_async(trx_handle_t h, char side, char uplo, char transa, char diag,
+                            int64_t m, int64_t n, float alpha, const float* A, int64_t lda,
+                            const float* B, int64_t ldb, double* X, int64_t ldx, int corrections,
+                            void* stream) {
+    // argument positions as trx_strsm_refined; corrections 15
+    const int ia = check_args(side, uplo, transa, diag, m, n, A, lda, B, ldb);
+    if (ia) return ia - 1;
+    if (m > 0 && n > 0 && X == nullptr) return -13;
+    if (ldx < std::max<int64_t>(1, m)) return -14;
+    if (corrections < 0 || corrections > 16) return -15;
+    if (!valid(h)) return TRX_ERR_HANDLE;
+    if (m == 0 || n == 0) return TRX_SUCCESS;
+    return refine_fixed(h, false, side, uplo, transa, diag, m, n, (double)alpha, A, lda, B, ldb, X,
+                        ldx, corrections, stream);
 }
 
 int trx_sfactor_create(trx_handle_t h, char side, char uplo, char transa, char diag, int64_t k,
@@ -1293,12 +1511,15 @@ int trx_sfactor_create(trx_handle_t h, char side, char uplo, char transa, char d
     f->k = k;
     f->lda = lda;
     f->A = A;
+    f->slices = slices_for(h);
     if (k > kMaxLeaf) {                 // some call on it may take the tensor-core path
-        const WsLayout w = ws_layout(k, 0);
+        const WsLayout w = ws_layout(k, 0, f->slices);
         f->ldm = w.ldm;
         if ((e = cudaMalloc(&f->m_hi, w.m_bytes)) != cudaSuccess ||
-            (e = cudaMalloc(&f->m_lo, w.m_bytes)) != cudaSuccess) {
+            (f->slices > 1 && (e = cudaMalloc(&f->m_lo, w.m_bytes)) != cudaSuccess) ||
+            (f->slices > 2 && (e = cudaMalloc(&f->m_lo2, w.m_bytes)) != cudaSuccess)) {
             if (f->m_hi) cudaFree(f->m_hi);
+            if (f->m_lo) cudaFree(f->m_lo);
             delete f;
             snprintf(g_detail, sizeof(g_detail), "factor planes: %s", cudaGetErrorString(e));
             return TRX_ERR_ALLOC;
@@ -1330,9 +1551,10 @@ int trx_sfactor_update(trx_handle_t h, trx_factor_t f, const float* A, void* str
     Planes pl;
     pl.ldm = f->ldm;
     pl.ldy = f->ldm;
+    pl.slices = f->slices;
     pl.m_hi = f->m_hi;
     pl.m_lo = f->m_lo;
-    pl.y_hi = pl.y_lo = nullptr;
+    pl.m_lo2 = f->m_lo2;
     const cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (h->opt_profile) {
@@ -1347,17 +1569,20 @@ int trx_sfactor_update(trx_handle_t h, trx_factor_t f, const float* A, void* str
     const int wb = leaf_for(h->opt_leaf, f->k, true, 4, 0);
     if (tc_leaf_mode(h->opt_trsm_tc_leaf, true, wb)) {
         if (!f->w_hi) {
-            const WsLayout w = ws_layout(f->k, 0);
+            const WsLayout w = ws_layout(f->k, 0, f->slices);
             if ((e = cudaMalloc(&f->w_hi, w.m_bytes)) != cudaSuccess ||
-                (e = cudaMalloc(&f->w_lo, w.m_bytes)) != cudaSuccess) {
+                (f->slices > 1 && (e = cudaMalloc(&f->w_lo, w.m_bytes)) != cudaSuccess) ||
+                (f->slices > 2 && (e = cudaMalloc(&f->w_lo2, w.m_bytes)) != cudaSuccess)) {
                 if (f->w_hi) cudaFree(f->w_hi);
-                f->w_hi = f->w_lo = nullptr;
+                if (f->w_lo) cudaFree(f->w_lo);
+                f->w_hi = f->w_lo = f->w_lo2 = nullptr;
                 snprintf(g_detail, sizeof(g_detail), "factor inverse planes: %s",
                          cudaGetErrorString(e));
                 return TRX_ERR_ALLOC;
             }
         }
-        if ((e = launch_invert_diag(c, wb, f->w_hi, f->w_lo, f->ldm, s)) != cudaSuccess)
+        if ((e = launch_invert_diag(c, wb, f->w_hi, f->w_lo, f->w_lo2, f->slices, f->ldm, s)) !=
+            cudaSuccess)
             return fail_cuda(e, "factor inverse planes");
         f->w_block = wb;
     } else {
@@ -1377,8 +1602,10 @@ int trx_factor_destroy(trx_factor_t f) {
     cudaDeviceSynchronize();
     if (f->m_hi) cudaFree(f->m_hi);
     if (f->m_lo) cudaFree(f->m_lo);
+    if (f->m_lo2) cudaFree(f->m_lo2);
     if (f->w_hi) cudaFree(f->w_hi);
     if (f->w_lo) cudaFree(f->w_lo);
+    if (f->w_lo2) cudaFree(f->w_lo2);
     f->magic = 0;
     delete f;
     return TRX_SUCCESS;
@@ -1444,7 +1671,8 @@ int trx_sgemm_update(trx_handle_t h, int64_t M, int64_t N, int64_t K, float beta
         return e == cudaSuccess ? TRX_SUCCESS : fail_cuda(e, "gemm_simt");
     }
     if (K % kTcKQuantum != 0) return -4;
-    const WsLayout w = ws_layout(K + M, N);
+    const int slices = slices_for(h);
+    const WsLayout w = ws_layout(K + M, N, slices);
     if (h->ws == nullptr || h->ws_bytes < w.total) {
         snprintf(g_detail, sizeof(g_detail), "workspace of %zu bytes needed, %zu set", w.total,
                  h->ws_bytes);
@@ -1454,20 +1682,21 @@ int trx_sgemm_update(trx_handle_t h, int64_t M, int64_t N, int64_t K, float beta
     Planes pl;
     pl.ldm = w.ldm;
     pl.ldy = w.ldy;
-    pl.m_hi = reinterpret_cast<__nv_bfloat16*>(base);
-    pl.m_lo = reinterpret_cast<__nv_bfloat16*>(base + w.m_bytes);
-    pl.y_hi = reinterpret_cast<__nv_bfloat16*>(base + 2 * w.m_bytes);
-    pl.y_lo = reinterpret_cast<__nv_bfloat16*>(base + 2 * w.m_bytes + w.y_bytes);
-    if ((e = launch_convert_rect(A, 1, lda, M, K, pl.m_hi + K * pl.ldm, pl.m_lo + K * pl.ldm,
-                                 pl.ldm, true, s)) != cudaSuccess ||
-        (e = launch_convert_rect(Y, 1, ldy, K, N, pl.y_hi, pl.y_lo, pl.ldy, false, s)) !=
-            cudaSuccess)
+    pl.slices = slices;
+    set_m_planes(pl, base, w.m_bytes, slices);
+    set_y_planes(pl, base + (size_t)slices * w.m_bytes, w.y_bytes, slices);
+    auto rowk = [&](__nv_bfloat16* q) { return q ? q + K * pl.ldm : nullptr; };
+    if ((e = launch_convert_rect(A, 1, lda, M, K, rowk(pl.m_hi), rowk(pl.m_lo), rowk(pl.m_lo2),
+                                 slices, pl.ldm, true, s)) != cudaSuccess ||
+        (e = launch_convert_rect(Y, 1, ldy, K, N, pl.y_hi, pl.y_lo, pl.y_lo2, slices, pl.ldy,
+                                 false, s)) != cudaSuccess)
         return fail_cuda(e, "convert");
     h->maps.resize(tc_maps_size());
     if ((e = tc_make_maps(pl, K + M, N, h->maps.data())) != cudaSuccess)
         return fail_cuda(e, "tensor map encode");
     const TcGemm g{K, M, 0, K};
-    e = launch_gemm_tc(c, h->maps.data(), &g, 1, beta, gamma, h->d_err, h->wait_ns, h->num_sms, s);
+    e = launch_gemm_tc(c, h->maps.data(), slices, &g, 1, beta, gamma, h->d_err, h->wait_ns,
+                       h->num_sms, s);
     return e == cudaSuccess ? TRX_SUCCESS : fail_cuda(e, "gemm_tc");
 }
 
@@ -1511,12 +1740,20 @@ int trx_set_option(trx_handle_t h, int option, int64_t value) {
             h->opt_trmm_dense = value;
             break;
         case TRX_OPT_RESIDUAL:
-            if (value < 0 || value > 2) return TRX_ERR_INVALID_VALUE;
+            if (value < 0 || value > 3) return TRX_ERR_INVALID_VALUE;
             h->opt_residual = value;
             break;
         case TRX_OPT_TRSM_TC_LEAF:
             if (value < -1 || value > 1) return TRX_ERR_INVALID_VALUE;
             h->opt_trsm_tc_leaf = value;
+            break;
+        case TRX_OPT_SPLIT:
+            if (value != 0 && value != 1 && value != 3 && value != 6) return TRX_ERR_INVALID_VALUE;
+            h->opt_split = value;
+            break;
+        case TRX_OPT_FP64_TRSM:
+            if (value < 0 || value > 16) return TRX_ERR_INVALID_VALUE;
+            h->opt_fp64_trsm = value;
             break;
         default:
             return TRX_ERR_INVALID_VALUE;
@@ -1538,6 +1775,8 @@ int trx_get_option(trx_handle_t h, int option, int64_t* value) {
         case TRX_OPT_TRMM_DENSE: *value = h->opt_trmm_dense; break;
         case TRX_OPT_RESIDUAL: *value = h->opt_residual; break;
         case TRX_OPT_TRSM_TC_LEAF: *value = h->opt_trsm_tc_leaf; break;
+        case TRX_OPT_SPLIT: *value = split_terms(h->opt_split); break;
+        case TRX_OPT_FP64_TRSM: *value = h->opt_fp64_trsm; break;
         default: return TRX_ERR_INVALID_VALUE;
     }
     return TRX_SUCCESS;

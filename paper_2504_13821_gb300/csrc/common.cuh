@@ -76,15 +76,52 @@ struct Canon {
 //             (K-major A operand of the GEMM update).
 //   Y planes: the GEMM's B operand, element (l, j) at j*ldy + l
 //             (K-major): the solved X rows for TRSM, the original C for TRMM.
-// hi = bf16(x), lo = bf16(x - hi); x = hi + lo to about 2^-17 relative.
+// An FP32 value x is carried as `slices` BF16 values:
+//   x0 = bf16(x), x1 = bf16(x - x0), x2 = bf16(x - x0 - x1)
+// (each difference is exact in FP32). One slice keeps 8 significant bits
+// (2^-9 relative), two about 17 (2^-17), three all 24 of FP32 (x0 + x1 + x2
+// = x for normal x). The GEMM forms a product from the slice products whose
+// weight is above FP32's unit roundoff: 1 term (x0 y0), 3 terms (+ x0 y1 +
+// x1 y0) or 6 terms (+ x0 y2 + x1 y1 + x2 y0), FP32 accumulation.
 struct Planes {
     __nv_bfloat16* m_hi = nullptr;
     __nv_bfloat16* m_lo = nullptr;
+    __nv_bfloat16* m_lo2 = nullptr;
     int64_t ldm = 0;
     __nv_bfloat16* y_hi = nullptr;
     __nv_bfloat16* y_lo = nullptr;
+    __nv_bfloat16* y_lo2 = nullptr;
     int64_t ldy = 0;
+    int slices = 2;
 };
+
+// Product terms of a split (1, 3, 6) <-> slices per operand (1, 2, 3).
+inline int slices_of_terms(int terms) { return terms == 1 ? 1 : terms == 6 ? 3 : 2; }
+inline int terms_of_slices(int slices) { return slices == 1 ? 1 : slices == 3 ? 6 : 3; }
+
+// The slices of x (above) into s0[o], s1[o], s2[o] for the first `slices`.
+__device__ __forceinline__ void put_split(__nv_bfloat16* s0, __nv_bfloat16* s1,
+                                          __nv_bfloat16* s2, int slices, int64_t o, float x) {
+    const __nv_bfloat16 h = __float2bfloat16_rn(x);
+    s0[o] = h;
+    if (slices > 1) {
+        const float r = x - __bfloat162float(h);
+        const __nv_bfloat16 l = __float2bfloat16_rn(r);
+        s1[o] = l;
+        if (slices > 2) s2[o] = __float2bfloat16_rn(r - __bfloat162float(l));
+    }
+}
+// The slices of x as three values (unused ones zero).
+__device__ __forceinline__ void split_slices(float x, int slices, __nv_bfloat16 (&v)[3]) {
+    v[0] = __float2bfloat16_rn(x);
+    const float r = x - __bfloat162float(v[0]);
+    v[1] = slices > 1 ? __float2bfloat16_rn(r) : __float2bfloat16_rn(0.f);
+    v[2] = slices > 2 ? __float2bfloat16_rn(r - __bfloat162float(v[1])) : __float2bfloat16_rn(0.f);
+}
+// Y-plane element o of the result x (solved rows, TRMM originals).
+__device__ __forceinline__ void put_y(const Planes& pl, int64_t o, float x) {
+    put_split(pl.y_hi, pl.y_lo, pl.y_lo2, pl.slices, o, x);
+}
 
 // ---- launchers (host) --------------------------------------------------------
 
@@ -129,16 +166,18 @@ cudaError_t launch_convert_y_rows(const Canon<float>& p, const Planes& pl, int64
 // planes at rows and columns [r0, r0 + b) of a row-major pair (leading
 // dimension ld), zeros above each block's diagonal.
 cudaError_t launch_invert_diag(const Canon<float>& p, int b, __nv_bfloat16* w_hi,
-                               __nv_bfloat16* w_lo, int64_t ld, cudaStream_t s);
+                               __nv_bfloat16* w_lo, __nv_bfloat16* w_lo2, int slices, int64_t ld,
+                               cudaStream_t s);
 // Split-BF16 planes of a rows x cols block, src(r, c) = src[r*rs + c*cs];
 // dst(r, c) at dst[r*ld + c] (row_major) or dst[c*ld + r] (otherwise).
 cudaError_t launch_convert_rect(const float* src, int64_t rs, int64_t cs, int64_t rows,
                                 int64_t cols, __nv_bfloat16* hi, __nv_bfloat16* lo,
-                                int64_t ld, bool row_major, cudaStream_t s);
+                                __nv_bfloat16* lo2, int slices, int64_t ld, bool row_major,
+                                cudaStream_t s);
 
 // Tensor-core GEMM update, one launch for a group of updates that write
-// disjoint row ranges (FP32 in/out, 3-term split BF16 products, FP32
-// accumulation in TMEM):
+// disjoint row ranges (FP32 in/out, split BF16 products of pl.slices slices
+// per operand, FP32 accumulation in TMEM):
 //   C[rc+i, j] = beta*C[rc+i, j] + gamma * sum_l M(rc+i, rk+l) Y(rk+l, j)
 struct TcGemm {
     int64_t rc, mlen, rk, klen;
@@ -146,15 +185,16 @@ struct TcGemm {
 struct TcMaps;   // opaque: tensor maps over the planes (gemm_tc.cu)
 int tc_maps_size();
 cudaError_t tc_make_maps(const Planes& pl, int64_t k, int64_t nrhs, void* maps_out);
-// Optional second output of a tensor-core GEMM: the split BF16 planes (hi,
-// lo) of result rows [row0, row1) (canonical rows), element (i, j) at
+// Optional second output of a tensor-core GEMM: the split BF16 planes (as
+// many slices as the operand planes) of result rows [row0, row1) (canonical rows), element (i, j) at
 // j * ld + i, as the Y planes are laid out.
 struct TcYOut {
     __nv_bfloat16* hi = nullptr;
     __nv_bfloat16* lo = nullptr;
+    __nv_bfloat16* lo2 = nullptr;
     int64_t ld = 0, row0 = 0, row1 = 0;
 };
-cudaError_t launch_gemm_tc(const Canon<float>& p, const void* maps,
+cudaError_t launch_gemm_tc(const Canon<float>& p, const void* maps, int slices,
                            const TcGemm* gemms, int ngemms, float beta,
                            float gamma, int* err_word, long long wait_limit,
                            int num_sms, cudaStream_t s, bool diag_beta = false,
@@ -176,16 +216,29 @@ cudaError_t refine_transpose_f32_f64(const float* src, int64_t lds, double* dst,
                                      int64_t rows, int64_t cols, double scale, cudaStream_t s);
 cudaError_t refine_transpose_f64(const double* src, int64_t lds, double* dst, int64_t ldd,
                                  int64_t rows, int64_t cols, cudaStream_t s);
+cudaError_t refine_transpose_f64_scaled(const double* src, int64_t lds, double* dst, int64_t ldd,
+                                        int64_t rows, int64_t cols, double scale,
+                                        cudaStream_t s);
+cudaError_t refine_transpose_f64_f32(const double* src, int64_t lds, float* dst, int64_t ldd,
+                                     int64_t rows, int64_t cols, cudaStream_t s);
+// dst := scale * src (m x n FP64, leading dimensions lds, ldd)
+cudaError_t refine_scale_f64(const double* src, int64_t lds, double* dst, int64_t ldd, int64_t m,
+                             int64_t n, double scale, cudaStream_t s);
 // The float-float residual: op(A) packed once (refine_pack_a_bytes),
 // X packed per step (refine_pack_x_bytes; from FP64 X split into two
 // floats, or from one FP32 plane), then R := B - op(A) X with mode 0
-// (X = xh + xl) or 1 (one plane), error-free accumulation, or 2 (one
-// plane, plain FP32 accumulation). R may be B. Waits bounded by wait_ns;
+// (X = xh + xl) or 1 (one plane), error-free accumulation, 2 (one
+// plane, plain FP32 accumulation) or 3 (A packed from FP64 as pairs by
+// refine_pack_a64, X = xh + xl). R may be B. Waits bounded by wait_ns;
 // on timeout *err := TRX_ERR_TIMEOUT and R is not written.
 size_t refine_pack_a_bytes(int64_t k, bool lower);
 size_t refine_pack_x_bytes(int64_t k, int64_t n);
 cudaError_t refine_pack_a(const float* A, int64_t lda, int64_t k, bool lower, bool trans,
                           bool unit, void* Ap, cudaStream_t s);
+// op(A) of FP64 data as float pairs (ah, al), for mode 3 (A and X both
+// pairs: the residual of FP64 data).
+cudaError_t refine_pack_a64(const double* A, int64_t lda, int64_t k, bool lower, bool trans,
+                            bool unit, void* Ap, cudaStream_t s);
 cudaError_t refine_pack_x(const double* X64, const float* X32, int64_t ldx, int64_t k,
                           int64_t n, void* Xp, cudaStream_t s);
 // Work units of the residual (row-tile pieces, heaviest first) and the row
@@ -193,6 +246,10 @@ cudaError_t refine_pack_x(const double* X64, const float* X32, int64_t ldx, int6
 // blocks of 64 x n doubles the pieces write.
 void refine_plan_units(int64_t k, bool lower, std::vector<int4>& units, std::vector<int4>& tiles,
                        int64_t& slots);
+// The same table built on the device (units, then tiles; the counts and
+// slots are refine_plan_units's): no host copy on the asynchronous path.
+cudaError_t refine_plan_units_device(int64_t k, bool lower, void* units, void* tiles,
+                                     cudaStream_t s);
 cudaError_t refine_residual_packed(int mode, const void* Ap, const void* Xp, const void* units,
                                    int64_t nunits, const void* tiles, int64_t ntiles,
                                    double* part, int64_t k, bool lower, const double* B,

@@ -2,10 +2,11 @@
 // quick return.
 //
 // The tcgen05 GEMM update multiplies BF16 operands. An FP32 value x is carried
-// as two BF16 planes, hi = bf16(x) and lo = bf16(x - hi) (x = hi + lo to about
-// 2^-17 relative), and a product as hi*hi + hi*lo + lo*hi with FP32
-// accumulation (the lo*lo term is below that error). These kernels write the
-// planes in the canonical K-major order the GEMM's TMA loads expect:
+// as one, two or three BF16 slices (x0 = bf16(x), x1 = bf16(x - x0), x2 =
+// bf16(x - x0 - x1); Planes in common.cuh) and a product as the slice
+// products above FP32's rounding level, with FP32 accumulation. These
+// kernels write the planes in the canonical K-major order the GEMM's TMA
+// loads expect:
 //   M planes: strictly-lower part of M, (i, l) at i*ldm + l; with diagonal
 //             blocks requested, also explicit zeros on and above the
 //             diagonal inside each block, so a block can be used as a dense
@@ -19,9 +20,12 @@
 namespace trx {
 namespace {
 
-__device__ __forceinline__ void split_bf16(float x, __nv_bfloat16& hi, __nv_bfloat16& lo) {
-    hi = __float2bfloat16_rn(x);
-    lo = __float2bfloat16_rn(x - __bfloat162float(hi));
+// Planes of slice q (0, 1, 2) of an M or Y plane set.
+__device__ __forceinline__ __nv_bfloat16* m_plane(const Planes& pl, int q) {
+    return q == 0 ? pl.m_hi : q == 1 ? pl.m_lo : pl.m_lo2;
+}
+__device__ __forceinline__ __nv_bfloat16* y_plane(const Planes& pl, int q) {
+    return q == 0 ? pl.y_hi : q == 1 ? pl.y_lo : pl.y_lo2;
 }
 
 // M planes: 64x64 tiles of the lower triangle (tiles above it exit at once,
@@ -50,16 +54,16 @@ __global__ void __launch_bounds__(256) convert_m_kernel(Canon<float> p, Planes p
         const int ii = e >> 5, lp = (e & 31) * 2;
         const int64_t i = i0 + ii, l = l0 + lp;
         if (i >= p.k || l >= p.k) continue;
-        __nv_bfloat16 h0, o0, h1, o1;
-        split_bf16(tile[ii][lp], h0, o0);
+        __nv_bfloat16 v0[3], v1[3];
+        split_slices(tile[ii][lp], pl.slices, v0);
         const int64_t off = i * pl.ldm + l;
         if (l + 1 < p.k) {
-            split_bf16(tile[ii][lp + 1], h1, o1);
-            *reinterpret_cast<__nv_bfloat162*>(pl.m_hi + off) = __halves2bfloat162(h0, h1);
-            *reinterpret_cast<__nv_bfloat162*>(pl.m_lo + off) = __halves2bfloat162(o0, o1);
+            split_slices(tile[ii][lp + 1], pl.slices, v1);
+            for (int q = 0; q < pl.slices; ++q)
+                *reinterpret_cast<__nv_bfloat162*>(m_plane(pl, q) + off) =
+                    __halves2bfloat162(v0[q], v1[q]);
         } else {
-            pl.m_hi[off] = h0;
-            pl.m_lo[off] = o0;
+            for (int q = 0; q < pl.slices; ++q) m_plane(pl, q)[off] = v0[q];
         }
     }
 }
@@ -76,20 +80,19 @@ __global__ void __launch_bounds__(256) convert_y_contig_kernel(Canon<float> p, P
         float v[4];
 #pragma unroll
         for (int q = 0; q < 4; ++q) v[q] = (l + q < p.k) ? src[(l + q) * p.c_rs] : 0.f;
-        __nv_bfloat16 h[4], o[4];
+        __nv_bfloat16 sl[4][3];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) split_bf16(v[q], h[q], o[q]);
+        for (int q = 0; q < 4; ++q) split_slices(v[q], pl.slices, sl[q]);
         const int64_t off = j * pl.ldy + l;
         if (l + 3 < p.k) {
-            __nv_bfloat162 hv[2] = {__halves2bfloat162(h[0], h[1]), __halves2bfloat162(h[2], h[3])};
-            __nv_bfloat162 ov[2] = {__halves2bfloat162(o[0], o[1]), __halves2bfloat162(o[2], o[3])};
-            *reinterpret_cast<uint2*>(pl.y_hi + off) = *reinterpret_cast<uint2*>(hv);
-            *reinterpret_cast<uint2*>(pl.y_lo + off) = *reinterpret_cast<uint2*>(ov);
-        } else {
-            for (int q = 0; l + q < p.k; ++q) {
-                pl.y_hi[off + q] = h[q];
-                pl.y_lo[off + q] = o[q];
+            for (int s = 0; s < pl.slices; ++s) {
+                __nv_bfloat162 hv[2] = {__halves2bfloat162(sl[0][s], sl[1][s]),
+                                        __halves2bfloat162(sl[2][s], sl[3][s])};
+                *reinterpret_cast<uint2*>(y_plane(pl, s) + off) = *reinterpret_cast<uint2*>(hv);
             }
+        } else {
+            for (int q = 0; l + q < p.k; ++q)
+                for (int s = 0; s < pl.slices; ++s) y_plane(pl, s)[off + q] = sl[q][s];
         }
     }
 }
@@ -112,12 +115,7 @@ __global__ void __launch_bounds__(256) convert_y_kernel(Canon<float> p, Planes p
     __syncthreads();
     for (int r = threadIdx.y; r < 32; r += 8) {
         const int64_t j = j0 + r, l = l0 + threadIdx.x;
-        if (l < p.k && j < p.nrhs) {
-            __nv_bfloat16 hi, lo;
-            split_bf16(tile[r][threadIdx.x], hi, lo);
-            pl.y_hi[j * pl.ldy + l] = hi;
-            pl.y_lo[j * pl.ldy + l] = lo;
-        }
+        if (l < p.k && j < p.nrhs) put_y(pl, j * pl.ldy + l, tile[r][threadIdx.x]);
     }
 }
 
@@ -125,6 +123,7 @@ __global__ void __launch_bounds__(256) convert_y_kernel(Canon<float> p, Planes p
 __global__ void __launch_bounds__(256) convert_rect_kernel(const float* src, int64_t rs,
                                                            int64_t cs, int64_t rows, int64_t cols,
                                                            __nv_bfloat16* hi, __nv_bfloat16* lo,
+                                                           __nv_bfloat16* lo2, int slices,
                                                            int64_t ld, int row_major) {
     pdl_trigger();
     pdl_wait();
@@ -141,13 +140,8 @@ __global__ void __launch_bounds__(256) convert_rect_kernel(const float* src, int
         // destination contiguous index runs along threadIdx.x
         const int rr = row_major ? t : threadIdx.x, cc = row_major ? threadIdx.x : t;
         const int64_t r = r0 + rr, c = c0 + cc;
-        if (r < rows && c < cols) {
-            __nv_bfloat16 h, l;
-            split_bf16(tile[rr][cc], h, l);
-            const int64_t o = row_major ? r * ld + c : c * ld + r;
-            hi[o] = h;
-            lo[o] = l;
-        }
+        if (r < rows && c < cols)
+            put_split(hi, lo, lo2, slices, row_major ? r * ld + c : c * ld + r, tile[rr][cc]);
     }
 }
 
@@ -159,7 +153,9 @@ __global__ void __launch_bounds__(256) convert_rect_kernel(const float* src, int
 // for column j of W.
 __global__ void __launch_bounds__(128) invert_diag_kernel(Canon<float> p, int b,
                                                           __nv_bfloat16* w_hi,
-                                                          __nv_bfloat16* w_lo, int64_t ld) {
+                                                          __nv_bfloat16* w_lo,
+                                                          __nv_bfloat16* w_lo2, int slices,
+                                                          int64_t ld) {
     pdl_trigger();
     pdl_wait();
     extern __shared__ float inv_sm[];
@@ -191,11 +187,7 @@ __global__ void __launch_bounds__(128) invert_diag_kernel(Canon<float> p, int b,
     __syncthreads();
     for (int e = threadIdx.x; e < b * b; e += blockDim.x) {
         const int i = e / b, l = e % b;
-        __nv_bfloat16 h, o;
-        split_bf16(Ws[i * b + l], h, o);
-        const int64_t off = (r0 + i) * ld + r0 + l;
-        w_hi[off] = h;
-        w_lo[off] = o;
+        put_split(w_hi, w_lo, w_lo2, slices, (r0 + i) * ld + r0 + l, Ws[i * b + l]);
     }
 }
 
@@ -237,18 +229,23 @@ cudaError_t launch_convert_y(const Canon<float>& p, const Planes& pl, cudaStream
 }
 
 cudaError_t launch_invert_diag(const Canon<float>& p, int b, __nv_bfloat16* w_hi,
-                               __nv_bfloat16* w_lo, int64_t ld, cudaStream_t s) {
+                               __nv_bfloat16* w_lo, __nv_bfloat16* w_lo2, int slices, int64_t ld,
+                               cudaStream_t s) {
     if (b < 1 || b > 128) return cudaErrorInvalidValue;
     const int64_t blocks = p.k / b;          // full blocks only
     if (blocks <= 0) return cudaSuccess;
     if (blocks > 0x7fffffff) return cudaErrorInvalidValue;
     const int smem = (int)((size_t)b * (2 * b + 1) * sizeof(float));
-    static const cudaError_t configured = cudaFuncSetAttribute(
-        invert_diag_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-        128 * (2 * 128 + 1) * (int)sizeof(float));
-    if (configured != cudaSuccess) return configured;
     return launch_kernel(invert_diag_kernel, dim3((unsigned)blocks), dim3(128), smem, s, p, b,
-                         w_hi, w_lo, ld);
+                         w_hi, w_lo, w_lo2, slices, ld);
+}
+
+// Shared-memory limit of the inversion kernel; like every kernel attribute
+// it applies to the current device only, so it runs once per device (from
+// the per-device set-up of handles and of the allocation-free entry).
+cudaError_t convert_configure() {
+    return cudaFuncSetAttribute(invert_diag_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                128 * (2 * 128 + 1) * (int)sizeof(float));
 }
 
 // Y planes of C's rows [r0, r0 + rows) only (the rows of one TRSM leaf).
@@ -260,18 +257,20 @@ cudaError_t launch_convert_y_rows(const Canon<float>& p, const Planes& pl, int64
     v.k = rows;
     Planes w = pl;
     w.y_hi = pl.y_hi + r0;
-    w.y_lo = pl.y_lo + r0;
+    w.y_lo = pl.y_lo ? pl.y_lo + r0 : nullptr;
+    w.y_lo2 = pl.y_lo2 ? pl.y_lo2 + r0 : nullptr;
     return launch_convert_y(v, w, s);
 }
 
 cudaError_t launch_convert_rect(const float* src, int64_t rs, int64_t cs, int64_t rows,
                                 int64_t cols, __nv_bfloat16* hi, __nv_bfloat16* lo,
-                                int64_t ld, bool row_major, cudaStream_t s) {
+                                __nv_bfloat16* lo2, int slices, int64_t ld, bool row_major,
+                                cudaStream_t s) {
     if (rows <= 0 || cols <= 0) return cudaSuccess;
     const int64_t gy = (rows + 31) / 32, gx = (cols + 31) / 32;
     if (gy > 65535) return cudaErrorInvalidValue;
     return launch_kernel(convert_rect_kernel, dim3((unsigned)gx, (unsigned)gy), dim3(32, 8), 0, s,
-                         src, rs, cs, rows, cols, hi, lo, ld, row_major ? 1 : 0);
+                         src, rs, cs, rows, cols, hi, lo, lo2, slices, ld, row_major ? 1 : 0);
 }
 
 template <typename T>

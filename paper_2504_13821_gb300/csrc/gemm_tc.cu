@@ -8,10 +8,14 @@
 // This is the off-diagonal step of the recursion of Section 3.1 (TRSM:
 // B2 := beta*B2 - M21 X1; TRMM: B2 += alpha M21 B1), where the paper's
 // speed comes from (Section 3.3: the base kernels must stay small next to the
-// GEMMs). FP32 operands are carried as split BF16 planes (convert.cu, leaf
-// kernels) and every product is formed as hi*hi + hi*lo + lo*hi with FP32
-// accumulation in tensor memory, which keeps the update at about 2^-16
-// relative error per product instead of BF16's 2^-8.
+// GEMMs). FP32 operands are carried as S split BF16 planes (convert.cu, leaf
+// kernels; S = 1, 2 or 3 slices per operand) and every product is formed
+// from the slice products above FP32's rounding level with FP32
+// accumulation in tensor memory:
+//   S = 1: x0 y0                                (1 term, about 2^-8 relative)
+//   S = 2: + x0 y1 + x1 y0                      (3 terms, about 2^-16)
+//   S = 3: + x0 y2 + x1 y1 + x2 y0              (6 terms, a few units of
+//                                                FP32's 2^-24: FP32-grade)
 //
 // One launch handles a group of updates whose output rows are disjoint (one
 // recursion node for TRSM, one whole recursion level for TRMM); the tiles of
@@ -20,9 +24,10 @@
 // Structure (one CTA per SM, 192 threads, warp-specialised), for an output
 // tile of 128 rows x BN right-hand sides (BN = 256, or 128 / 64 when the
 // group has too few tiles to cover the SMs):
-//   warp 0     TMA producer: 4 tiles per K step (A hi/lo 128x32, Y hi/lo
-//              BNx32, 64-byte swizzle) into a 4-stage shared-memory ring
-//   warp 1     TMEM allocator and MMA issuer: per K step 2 x 3
+//   warp 0     TMA producer: 2S tiles per K step (A slices 128x32, Y slices
+//              BNx32, 64-byte swizzle) into a shared-memory ring of 3-4
+//              stages
+//   warp 1     TMEM allocator and MMA issuer: per K step 2 x terms
 //              tcgen05.mma (M=128, N=BN, K=16, BF16 in, FP32 accumulate),
 //              tcgen05.commit frees the ring slot
 //   warps 2-5  epilogue: tcgen05.ld of the accumulator (warp w reads TMEM
@@ -43,22 +48,41 @@ namespace trx {
 namespace tc {
 
 constexpr int BM = 128, BK = 32;                    // BK in BF16 elements (64 B)
-constexpr int STAGES = 4;
+constexpr int MAX_STAGES = 4;
 constexpr int A_TILE = BM * BK * 2;                 // 8 KiB
 constexpr int MAXG = 256;
 constexpr int NTHREADS = 192;
+// Precise accumulation (the 6-term split, S = 3): K is taken in chunks of
+// CH K steps; in each chunk the dominant slice product x0 y0 accumulates in
+// TMEM columns [0, BN) and the five smaller ones in [BN, 2 BN), both from
+// zero, and eight epilogue warps add the two into FP32 register sums
+// (round-to-nearest) before the next chunk. The tensor core's own
+// accumulation thus runs over at most CH * BK = 256 terms per value, and
+// the small products never round against the large running sum: measured
+// against the FP32 FMA engine, accumulating whole K ranges in TMEM made
+// long updates about ten times less accurate, whatever the split.
+constexpr int NTHREADS_P = 320;
+constexpr int CH = 8;
+template <int S>
+struct Precise {
+    static constexpr bool value = S == 3;
+};
 constexpr int kTimeout = 4;                          // TRX_ERR_TIMEOUT
 
-// Per N tile (256, 128 or 64 columns of the right-hand side): ring-stage
-// size, tensor memory (two accumulators of BN FP32 columns) and the
-// kind::f16 instruction descriptor (FP32 accumulator, BF16 A and B, both
+// Per N tile (256, 128 or 64 columns of the right-hand side) and slice
+// count S: ring-stage size and depth (4 stages, 3 when four do not fit in
+// shared memory), tensor memory (two accumulators of BN FP32 columns) and
+// the kind::f16 instruction descriptor (FP32 accumulator, BF16 A and B, both
 // K-major, M = 128, N = BN).
-template <int BN>
+template <int BN, int S>
 struct Cfg {
     static constexpr int B_TILE = BN * BK * 2;
-    static constexpr int STAGE_BYTES = 2 * A_TILE + 2 * B_TILE;
+    static constexpr int STAGE_BYTES = S * A_TILE + S * B_TILE;
+    static constexpr int STAGES =
+        (1024 + MAX_STAGES * STAGE_BYTES + 256 <= 227 * 1024) ? MAX_STAGES : 3;
     static constexpr int TMEM_COLS = 2 * BN;
     static constexpr int SMEM_BYTES = 1024 + STAGES * STAGE_BYTES + 256;
+    static_assert(SMEM_BYTES <= 227 * 1024, "ring does not fit in shared memory");
     static constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) |
                                       ((uint32_t)(BN >> 3) << 17) |
                                       ((uint32_t)(BM >> 4) << 24);
@@ -66,8 +90,8 @@ struct Cfg {
 };
 
 struct Maps {
-    CUtensorMap a_hi, a_lo;
-    CUtensorMap b_hi[3], b_lo[3];   // boxes of 256, 128, 64 rows
+    CUtensorMap a[3];               // A slices 0..2
+    CUtensorMap b[3][3];            // [slice][box of 256, 128, 64 rows]
 };
 
 struct Params {
@@ -87,6 +111,7 @@ struct Params {
     // [y_row0, y_row1) (canonical rows), element (i, j) at y[j * ldy + i]
     __nv_bfloat16* y_hi;
     __nv_bfloat16* y_lo;
+    __nv_bfloat16* y_lo2;
     int64_t ldy, y_row0, y_row1;
     int ngemms, n_tiles_n, total_tiles;
     int* err;
@@ -177,8 +202,22 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
     for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+          "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
 struct Smem {
-    uint64_t full[STAGES], empty[STAGES], acc_full[2], acc_empty[2], drain;
+    uint64_t full[MAX_STAGES], empty[MAX_STAGES], acc_full[2], acc_empty[2], drain;
     uint32_t tmem_base;
     int abort;
 };
@@ -235,9 +274,12 @@ __device__ __forceinline__ Tile map_tile(const Params& p, int t) {
     return r;
 }
 
-template <int BN>
-__global__ void __launch_bounds__(NTHREADS, 1) gemm_tc_kernel(const __grid_constant__ Params p) {
-    using C = Cfg<BN>;
+template <int BN, int S>
+__global__ void __launch_bounds__(Precise<S>::value ? NTHREADS_P : NTHREADS, 1)
+    gemm_tc_kernel(const __grid_constant__ Params p) {
+    using C = Cfg<BN, S>;
+    constexpr bool P = Precise<S>::value;
+    constexpr int STAGES = C::STAGES;
     constexpr int STAGE_BYTES = C::STAGE_BYTES;
     constexpr int B_TILE = C::B_TILE;
     constexpr int TMEM_COLS = C::TMEM_COLS;
@@ -256,7 +298,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) gemm_tc_kernel(const __grid_const
         }
         for (int a = 0; a < 2; ++a) {
             mbar_init(smem_u32(&sm->acc_full[a]), 1);
-            mbar_init(smem_u32(&sm->acc_empty[a]), 4);
+            mbar_init(smem_u32(&sm->acc_empty[a]), P ? 8 : 4);   // epilogue warps
         }
         mbar_init(smem_u32(&sm->drain), 1);
         sm->abort = 0;
@@ -295,10 +337,11 @@ __global__ void __launch_bounds__(NTHREADS, 1) gemm_tc_kernel(const __grid_const
                 mbar_expect_tx(fb, STAGE_BYTES);
                 const int x = (int)(G.rk + (int64_t)kb * BK);
                 const uint32_t base = ring + stage * STAGE_BYTES;
-                tma_load_2d(base, &p.maps.a_hi, fb, x, ya);
-                tma_load_2d(base + A_TILE, &p.maps.a_lo, fb, x, ya);
-                tma_load_2d(base + 2 * A_TILE, &p.maps.b_hi[C::MAP], fb, x, yb);
-                tma_load_2d(base + 2 * A_TILE + B_TILE, &p.maps.b_lo[C::MAP], fb, x, yb);
+#pragma unroll
+                for (int q = 0; q < S; ++q) {
+                    tma_load_2d(base + q * A_TILE, &p.maps.a[q], fb, x, ya);
+                    tma_load_2d(base + S * A_TILE + q * B_TILE, &p.maps.b[q][C::MAP], fb, x, yb);
+                }
                 ++issued;
                 if (++stage == STAGES) { stage = 0; phase ^= 1u; }
             }
@@ -308,7 +351,139 @@ __global__ void __launch_bounds__(NTHREADS, 1) gemm_tc_kernel(const __grid_const
             if (--stage < 0) { stage = STAGES - 1; phase ^= 1u; }
             wait_bounded(smem_u32(&sm->full[stage]), phase, p, abort, false);
         }
-    } else if (warp == 1 && lane == 0) {
+    } else if (P && warp == 1 && lane == 0) {
+        // ---------------- MMA issuer, precise accumulation ----------------
+        int stage = 0;
+        uint32_t phase = 0, acc_phase = 0;
+        const uint32_t dbig = tmem, dsmall = tmem + BN;
+        for (int t = blockIdx.x; t < p.total_tiles && !*abort; t += gridDim.x) {
+            const Tile ti = map_tile(p, t);
+            const int nkb = (int)(p.g[ti.g].klen / BK);
+            bool ok = true;
+            for (int kb0 = 0; kb0 < nkb && ok; kb0 += CH) {
+                if (!wait_bounded(smem_u32(&sm->acc_empty[0]), acc_phase ^ 1u, p, abort)) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const int kb1 = min(nkb, kb0 + CH);
+                for (int kb = kb0; kb < kb1; ++kb) {
+                    if (!wait_bounded(smem_u32(&sm->full[stage]), phase, p, abort)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t base = ring + stage * STAGE_BYTES;
+#pragma unroll
+                    for (int kk = 0; kk < BK / 16; ++kk) {
+                        const uint32_t acc_on = (kb == kb0 && kk == 0) ? 0u : 1u;
+                        const uint64_t a0 = sdesc(base + kk * 32);
+                        const uint64_t b0 = sdesc(base + S * A_TILE + kk * 32);
+                        umma(dbig, a0, b0, C::IDESC, acc_on);
+                        if constexpr (S >= 2) {
+                            const uint64_t a1 = sdesc(base + A_TILE + kk * 32);
+                            const uint64_t b1 = sdesc(base + S * A_TILE + B_TILE + kk * 32);
+                            umma(dsmall, a0, b1, C::IDESC, acc_on);
+                            umma(dsmall, a1, b0, C::IDESC, 1u);
+                            if constexpr (S >= 3) {
+                                const uint64_t a2 = sdesc(base + 2 * A_TILE + kk * 32);
+                                const uint64_t b2 =
+                                    sdesc(base + S * A_TILE + 2 * B_TILE + kk * 32);
+                                umma(dsmall, a0, b2, C::IDESC, 1u);
+                                umma(dsmall, a1, b1, C::IDESC, 1u);
+                                umma(dsmall, a2, b0, C::IDESC, 1u);
+                            }
+                        }
+                    }
+                    umma_commit(smem_u32(&sm->empty[stage]));
+                    if (++stage == STAGES) { stage = 0; phase ^= 1u; }
+                }
+                if (!ok) break;
+                umma_commit(smem_u32(&sm->acc_full[0]));
+                acc_phase ^= 1u;
+            }
+            if (!ok) break;
+        }
+        umma_commit(smem_u32(&sm->drain));
+        wait_bounded(smem_u32(&sm->drain), 0, p, abort, false);
+    } else if (P && warp >= 2) {
+        // ---------------- epilogue, precise accumulation ----------------
+        // warp w: TMEM lanes 32 (w % 4) .., columns [half * HC, half * HC + HC)
+        constexpr int HC = BN / 2;
+        const int q = warp & 3, half = (warp - 2) >> 2;
+        uint32_t acc_phase = 0;
+        for (int t = blockIdx.x; t < p.total_tiles; t += gridDim.x) {
+            const Tile ti = map_tile(p, t);
+            const TcGemm& G = p.g[ti.g];
+            const int nkb = (int)(G.klen / BK);
+            const int64_t row = (int64_t)ti.m * BM + q * 32 + lane;
+            const bool row_ok = row < G.mlen;
+            const int64_t grow = G.rc + row;
+            const bool yrow = p.y_hi != nullptr && row_ok && grow >= p.y_row0 && grow < p.y_row1;
+            float beta = p.beta;
+            if (p.diag_beta && row_ok && !p.unit) beta *= __ldg(p.dA + grow * p.d_step);
+            float* wrow = p.C + grow * p.c_rs;
+            const int64_t jbase = (int64_t)ti.n * BN + half * HC;
+            float sum[HC];
+#pragma unroll
+            for (int c = 0; c < HC; ++c) sum[c] = 0.f;
+            bool ok = true;
+            for (int kb0 = 0; kb0 < nkb; kb0 += CH) {
+                int w = 1;
+                if (lane == 0) w = wait_bounded(smem_u32(&sm->acc_full[0]), acc_phase, p, abort);
+                w = __shfl_sync(0xffffffffu, w, 0);
+                if (!w) { ok = false; break; }
+                tc_fence_after();
+#pragma unroll
+                for (int cc = 0; cc < HC / 16; ++cc) {
+                    float v[16];
+                    const uint32_t ta = tmem + (uint32_t)(half * HC + cc * 16) +
+                                        ((uint32_t)(q * 32) << 16);
+                    tmem_ld16(ta, v);
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) sum[cc * 16 + i] += v[i];
+                    if constexpr (S >= 2) {
+                        tmem_ld16(ta + BN, v);
+#pragma unroll
+                        for (int i = 0; i < 16; ++i) sum[cc * 16 + i] += v[i];
+                    }
+                }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(smem_u32(&sm->acc_empty[0]));
+                acc_phase ^= 1u;
+            }
+            if (!ok) break;
+            // C := beta C + gamma sum over this thread's row and columns
+#pragma unroll
+            for (int cc = 0; cc < HC / 16; ++cc) {
+                const int64_t j0 = jbase + cc * 16;
+                float* dst = wrow + j0 * p.c_cs;
+                float cv[16];
+                if (!p.read_c || !row_ok) {
+#pragma unroll
+                    for (int c = 0; c < 16; ++c) cv[c] = 0.f;
+                } else if (j0 + 16 <= p.nrhs) {
+#pragma unroll
+                    for (int c = 0; c < 16; ++c) cv[c] = __ldcg(dst + c * p.c_cs);
+                } else {
+#pragma unroll
+                    for (int c = 0; c < 16; ++c)
+                        cv[c] = (j0 + c < p.nrhs) ? __ldcg(dst + c * p.c_cs) : 0.f;
+                }
+                if (!row_ok) continue;
+                const int64_t yo = j0 * p.ldy + grow;
+#pragma unroll
+                for (int c = 0; c < 16; ++c) {
+                    if (j0 + c < p.nrhs) {
+                        const float o = fmaf(beta, cv[c], p.gamma * sum[cc * 16 + c]);
+                        dst[c * p.c_cs] = o;
+                        if (yrow) put_split(p.y_hi, p.y_lo, p.y_lo2, S, yo + c * p.ldy, o);
+                    }
+                }
+            }
+        }
+    } else if (!P && warp == 1 && lane == 0) {
         // ---------------- MMA issuer ----------------
         int stage = 0, acc = 0;
         uint32_t phase = 0, acc_phase = 0;
@@ -325,13 +500,23 @@ __global__ void __launch_bounds__(NTHREADS, 1) gemm_tc_kernel(const __grid_const
                 const uint32_t base = ring + stage * STAGE_BYTES;
 #pragma unroll
                 for (int kk = 0; kk < BK / 16; ++kk) {
-                    const uint64_t ahi = sdesc(base + kk * 32);
-                    const uint64_t alo = sdesc(base + A_TILE + kk * 32);
-                    const uint64_t bhi = sdesc(base + 2 * A_TILE + kk * 32);
-                    const uint64_t blo = sdesc(base + 2 * A_TILE + B_TILE + kk * 32);
-                    umma(d, ahi, bhi, C::IDESC, (kb | kk) != 0 ? 1u : 0u);
-                    umma(d, ahi, blo, C::IDESC, 1u);
-                    umma(d, alo, bhi, C::IDESC, 1u);
+                    // slice products of weight 1, 2^-8 and 2^-16 (S = 1, 2, 3)
+                    const uint64_t a0 = sdesc(base + kk * 32);
+                    const uint64_t b0 = sdesc(base + S * A_TILE + kk * 32);
+                    umma(d, a0, b0, C::IDESC, (kb | kk) != 0 ? 1u : 0u);
+                    if constexpr (S >= 2) {
+                        const uint64_t a1 = sdesc(base + A_TILE + kk * 32);
+                        const uint64_t b1 = sdesc(base + S * A_TILE + B_TILE + kk * 32);
+                        umma(d, a0, b1, C::IDESC, 1u);
+                        umma(d, a1, b0, C::IDESC, 1u);
+                        if constexpr (S >= 3) {
+                            const uint64_t a2 = sdesc(base + 2 * A_TILE + kk * 32);
+                            const uint64_t b2 = sdesc(base + S * A_TILE + 2 * B_TILE + kk * 32);
+                            umma(d, a0, b2, C::IDESC, 1u);
+                            umma(d, a1, b1, C::IDESC, 1u);
+                            umma(d, a2, b0, C::IDESC, 1u);
+                        }
+                    }
                 }
                 umma_commit(smem_u32(&sm->empty[stage]));
                 if (++stage == STAGES) { stage = 0; phase ^= 1u; }
@@ -343,7 +528,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) gemm_tc_kernel(const __grid_const
         // All MMAs issued by this CTA complete before TMEM is released.
         umma_commit(smem_u32(&sm->drain));
         wait_bounded(smem_u32(&sm->drain), 0, p, abort, false);
-    } else if (warp >= 2) {
+    } else if (!P && warp >= 2) {
         // ---------------- epilogue ----------------
         const int q = warp & 3;                 // TMEM lanes 32q .. 32q+31
         int acc = 0;
@@ -405,16 +590,13 @@ __global__ void __launch_bounds__(NTHREADS, 1) gemm_tc_kernel(const __grid_const
                 float* dst = wrow + j0 * p.c_cs;
                 if (yrow) {
                     // the result and its planes (same split as the conversions)
-                    __nv_bfloat16* yh = p.y_hi + j0 * p.ldy + grow;
-                    __nv_bfloat16* yl = p.y_lo + j0 * p.ldy + grow;
+                    const int64_t yo = j0 * p.ldy + grow;
 #pragma unroll
                     for (int c = 0; c < 32; ++c) {
                         if (j0 + c < p.nrhs) {
                             const float o = fmaf(beta, c0[c], p.gamma * v[c]);
                             dst[c * p.c_cs] = o;
-                            const __nv_bfloat16 h = __float2bfloat16_rn(o);
-                            yh[c * p.ldy] = h;
-                            yl[c * p.ldy] = __float2bfloat16_rn(o - __bfloat162float(h));
+                            put_split(p.y_hi, p.y_lo, p.y_lo2, S, yo + c * p.ldy, o);
                         }
                     }
                 } else if (row_ok && j0 + 32 <= p.nrhs) {
@@ -482,39 +664,50 @@ static bool encode(CUtensorMap* m, void* base, uint64_t inner, uint64_t outer, u
 
 int tc_maps_size() { return (int)sizeof(tc::Maps); }
 
+template <int S>
+static cudaError_t tc_configure_s() {
+    cudaError_t e;
+    if ((e = cudaFuncSetAttribute(tc::gemm_tc_kernel<256, S>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  tc::Cfg<256, S>::SMEM_BYTES)) != cudaSuccess)
+        return e;
+    if ((e = cudaFuncSetAttribute(tc::gemm_tc_kernel<128, S>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  tc::Cfg<128, S>::SMEM_BYTES)) != cudaSuccess)
+        return e;
+    return cudaFuncSetAttribute(tc::gemm_tc_kernel<64, S>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                tc::Cfg<64, S>::SMEM_BYTES);
+}
+
 cudaError_t tc_configure() {
     cudaError_t e;
-    if ((e = cudaFuncSetAttribute(tc::gemm_tc_kernel<256>,
-                                  cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  tc::Cfg<256>::SMEM_BYTES)) != cudaSuccess)
-        return e;
-    if ((e = cudaFuncSetAttribute(tc::gemm_tc_kernel<128>,
-                                  cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  tc::Cfg<128>::SMEM_BYTES)) != cudaSuccess)
-        return e;
-    return cudaFuncSetAttribute(tc::gemm_tc_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                tc::Cfg<64>::SMEM_BYTES);
+    if ((e = tc_configure_s<1>()) != cudaSuccess) return e;
+    if ((e = tc_configure_s<2>()) != cudaSuccess) return e;
+    return tc_configure_s<3>();
 }
 
 cudaError_t tc_make_maps(const Planes& pl, int64_t k, int64_t nrhs, void* out) {
     tc::Maps* m = reinterpret_cast<tc::Maps*>(out);
-    if (k <= 0 || nrhs <= 0) return cudaErrorInvalidValue;
-    if (!tc::encode(&m->a_hi, pl.m_hi, k, k, pl.ldm, tc::BM) ||
-        !tc::encode(&m->a_lo, pl.m_lo, k, k, pl.ldm, tc::BM) ||
-        !tc::encode(&m->b_hi[0], pl.y_hi, k, nrhs, pl.ldy, 256) ||
-        !tc::encode(&m->b_lo[0], pl.y_lo, k, nrhs, pl.ldy, 256) ||
-        !tc::encode(&m->b_hi[1], pl.y_hi, k, nrhs, pl.ldy, 128) ||
-        !tc::encode(&m->b_lo[1], pl.y_lo, k, nrhs, pl.ldy, 128) ||
-        !tc::encode(&m->b_hi[2], pl.y_hi, k, nrhs, pl.ldy, 64) ||
-        !tc::encode(&m->b_lo[2], pl.y_lo, k, nrhs, pl.ldy, 64))
-        return cudaErrorInvalidValue;
+    if (k <= 0 || nrhs <= 0 || pl.slices < 1 || pl.slices > 3) return cudaErrorInvalidValue;
+    __nv_bfloat16* const ma[3] = {pl.m_hi, pl.m_lo, pl.m_lo2};
+    __nv_bfloat16* const yb[3] = {pl.y_hi, pl.y_lo, pl.y_lo2};
+    const uint32_t boxes[3] = {256, 128, 64};
+    for (int q = 0; q < pl.slices; ++q) {
+        if (!ma[q] || !yb[q] || !tc::encode(&m->a[q], ma[q], k, k, pl.ldm, tc::BM))
+            return cudaErrorInvalidValue;
+        for (int b = 0; b < 3; ++b)
+            if (!tc::encode(&m->b[q][b], yb[q], k, nrhs, pl.ldy, boxes[b]))
+                return cudaErrorInvalidValue;
+    }
     return cudaSuccess;
 }
 
-cudaError_t launch_gemm_tc(const Canon<float>& p, const void* maps, const TcGemm* gemms,
-                           int ngemms, float beta, float gamma, int* err_word,
-                           long long wait_ns, int num_sms, cudaStream_t s, bool diag_beta,
-                           const TcYOut* yout) {
+cudaError_t launch_gemm_tc(const Canon<float>& p, const void* maps, int slices,
+                           const TcGemm* gemms, int ngemms, float beta, float gamma,
+                           int* err_word, long long wait_ns, int num_sms, cudaStream_t s,
+                           bool diag_beta, const TcYOut* yout) {
+    if (slices < 1 || slices > 3) return cudaErrorInvalidValue;
     using namespace tc;
     for (int g0 = 0; g0 < ngemms; g0 += MAXG) {
         const int ng = (ngemms - g0) < MAXG ? (ngemms - g0) : MAXG;
@@ -541,6 +734,7 @@ cudaError_t launch_gemm_tc(const Canon<float>& p, const void* maps, const TcGemm
         prm.d_step = p.a_rs + p.a_cs;
         prm.y_hi = yout ? yout->hi : nullptr;
         prm.y_lo = yout ? yout->lo : nullptr;
+        prm.y_lo2 = yout ? yout->lo2 : nullptr;
         prm.ldy = yout ? yout->ld : 0;
         prm.y_row0 = yout ? yout->row0 : 0;
         prm.y_row1 = yout ? yout->row1 : 0;
@@ -562,12 +756,20 @@ cudaError_t launch_gemm_tc(const Canon<float>& p, const void* maps, const TcGemm
         prm.total_tiles = (int)tiles;
         const int grid = (int)(tiles < num_sms ? tiles : num_sms);
         cudaError_t e;
-        if (bn == 256)
-            e = launch_kernel(gemm_tc_kernel<256>, dim3(grid), dim3(NTHREADS), Cfg<256>::SMEM_BYTES, s, prm);
-        else if (bn == 128)
-            e = launch_kernel(gemm_tc_kernel<128>, dim3(grid), dim3(NTHREADS), Cfg<128>::SMEM_BYTES, s, prm);
+#define TRX_TC_LAUNCH(BNV, SV)                                                            \
+    launch_kernel(gemm_tc_kernel<BNV, SV>, dim3(grid),                                     \
+                  dim3(Precise<SV>::value ? NTHREADS_P : NTHREADS),                        \
+                  Cfg<BNV, SV>::SMEM_BYTES, s, prm)
+        if (slices == 1)
+            e = bn == 256 ? TRX_TC_LAUNCH(256, 1) : bn == 128 ? TRX_TC_LAUNCH(128, 1)
+                                                              : TRX_TC_LAUNCH(64, 1);
+        else if (slices == 2)
+            e = bn == 256 ? TRX_TC_LAUNCH(256, 2) : bn == 128 ? TRX_TC_LAUNCH(128, 2)
+                                                              : TRX_TC_LAUNCH(64, 2);
         else
-            e = launch_kernel(gemm_tc_kernel<64>, dim3(grid), dim3(NTHREADS), Cfg<64>::SMEM_BYTES, s, prm);
+            e = bn == 256 ? TRX_TC_LAUNCH(256, 3) : bn == 128 ? TRX_TC_LAUNCH(128, 3)
+                                                              : TRX_TC_LAUNCH(64, 3);
+#undef TRX_TC_LAUNCH
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;

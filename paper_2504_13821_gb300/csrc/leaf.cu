@@ -46,7 +46,12 @@ extern template cudaError_t leaf_b256_launch<double>(const LeafArgs<double>&, cu
 
 cudaError_t leaf_wide_configure();
 cudaError_t leaf_wide_launch(const LeafArgs<float>& a, int num_sms, cudaStream_t s);
+cudaError_t convert_configure();
+cudaError_t refine_configure();
 
+// Kernel attributes (dynamic shared-memory limits) for the current device:
+// run once per device by every handle's and the allocation-free entry's
+// set-up, since an attribute set on one device does not carry to another.
 cudaError_t leaf_configure_all() {
     cudaError_t e;
     if ((e = leaf_configure<float, true>()) != cudaSuccess) return e;
@@ -58,6 +63,8 @@ cudaError_t leaf_configure_all() {
     if ((e = leaf_b256_configure<float>()) != cudaSuccess) return e;
     if ((e = leaf_b256_configure<double>()) != cudaSuccess) return e;
     if ((e = leaf_wide_configure()) != cudaSuccess) return e;
+    if ((e = convert_configure()) != cudaSuccess) return e;
+    if ((e = refine_configure()) != cudaSuccess) return e;
     return tc_configure();
 }
 

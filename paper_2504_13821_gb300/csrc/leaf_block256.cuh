@@ -183,11 +183,7 @@ __global__ void __launch_bounds__(256) leaf_trsm_b256_kernel(LeafArgs<T> a) {
                 for (int e = tid; e < kb * S::NC; e += S::NT) {
                     const int i = e % kb, c = e / kb;
                     if (j0 + c < p.nrhs) {
-                        const float xv = sP[i * S::LDP + c];
-                        const __nv_bfloat16 hi = __float2bfloat16_rn(xv);
-                        const int64_t o = (j0 + c) * a.pl.ldy + r0 + i;
-                        a.pl.y_hi[o] = hi;
-                        a.pl.y_lo[o] = __float2bfloat16_rn(xv - __bfloat162float(hi));
+                        put_y(a.pl, (j0 + c) * a.pl.ldy + r0 + i, sP[i * S::LDP + c]);
                     }
                 }
             }

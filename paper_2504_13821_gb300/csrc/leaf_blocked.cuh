@@ -192,11 +192,7 @@ __global__ void __launch_bounds__(256, B == 64 ? 2 : 1) leaf_trsm_blocked_kernel
 #pragma unroll
                 for (int c = pc; c < S::NCOL; c += PADV) {
                     if (pi < bs && j0 + c < p.nrhs) {
-                        const float xval = sC[pi * S::LDC + c];
-                        const __nv_bfloat16 hi = __float2bfloat16_rn(xval);
-                        const int64_t o = (j0 + c) * a.pl.ldy + r0 + pi;
-                        a.pl.y_hi[o] = hi;
-                        a.pl.y_lo[o] = __float2bfloat16_rn(xval - __bfloat162float(hi));
+                        put_y(a.pl, (j0 + c) * a.pl.ldy + r0 + pi, sC[pi * S::LDC + c]);
                     }
                 }
             }

@@ -260,20 +260,13 @@ leaf_kernel(LeafArgs<T> a) {
             if (TRSM && a.planes) {
                 // Y planes, element (l, j) at j*ldy + l: rows fastest.
                 const int pi = tid % B, pc = tid / B;
-                __nv_bfloat16* yh = a.pl.y_hi + (j0 + pc) * a.pl.ldy + r0 + pi;
-                __nv_bfloat16* yl = a.pl.y_lo + (j0 + pc) * a.pl.ldy + r0 + pi;
+                int64_t yo = (j0 + pc) * a.pl.ldy + r0 + pi;
                 const int64_t ystep = (int64_t)(S::NT / B) * a.pl.ldy;
 #pragma unroll
                 for (int u = 0; u < np; ++u) {
                     const int cc = pc + u * (S::NT / B);
-                    if (pi < bs && j0 + cc < p.nrhs) {
-                        const float x = sC[cc * S::LDS + pi];
-                        const __nv_bfloat16 hi = __float2bfloat16_rn(x);
-                        *yh = hi;
-                        *yl = __float2bfloat16_rn(x - __bfloat162float(hi));
-                    }
-                    yh += ystep;
-                    yl += ystep;
+                    if (pi < bs && j0 + cc < p.nrhs) put_y(a.pl, yo, sC[cc * S::LDS + pi]);
+                    yo += ystep;
                 }
             }
         }

@@ -253,12 +253,7 @@ __global__ void __launch_bounds__(Wide::NT, 1) leaf_trsm_wide_kernel(LeafArgs<fl
                         const int c = 4 * c4 + e;
                         if (c < ncols) {
                             dst[(int64_t)c * p.c_cs] = v[e];
-                            if (a.planes) {
-                                const __nv_bfloat16 hi = __float2bfloat16_rn(v[e]);
-                                const int64_t o = (j0 + c) * a.pl.ldy + r0 + i;
-                                a.pl.y_hi[o] = hi;
-                                a.pl.y_lo[o] = __float2bfloat16_rn(v[e] - __bfloat162float(hi));
-                            }
+                            if (a.planes) put_y(a.pl, (j0 + c) * a.pl.ldy + r0 + i, v[e]);
                         }
                     }
                 }
@@ -276,11 +271,7 @@ __global__ void __launch_bounds__(Wide::NT, 1) leaf_trsm_wide_kernel(LeafArgs<fl
                 const int i = gt;
                 if (i < bs) {
                     for (int c2 = 0; c2 < ncols; ++c2) {
-                        const float v = sC[i * S::LDC + c2];
-                        const __nv_bfloat16 hi = __float2bfloat16_rn(v);
-                        const int64_t o = (j0 + c2) * a.pl.ldy + r0 + i;
-                        a.pl.y_hi[o] = hi;
-                        a.pl.y_lo[o] = __float2bfloat16_rn(v - __bfloat162float(hi));
+                        put_y(a.pl, (j0 + c2) * a.pl.ldy + r0 + i, sC[i * S::LDC + c2]);
                     }
                 }
             }

@@ -16,6 +16,7 @@
 // device address: the set-up below asks the runtime for the real address
 // (cudaGetSymbolAddress, once per device, with that device current) and the
 // kernels are given that pointer.
+#include <cstdlib>
 #include <mutex>
 
 #include "common.cuh"
@@ -27,13 +28,15 @@ int noalloc_check_args(char side, char uplo, char transa, char diag, int64_t m, 
                        const void* A, int64_t lda, const void* B, int64_t ldb);
 size_t noalloc_scratch_bytes(char side, int64_t m, int64_t n);
 int noalloc_strsm(int device, int num_sms, void* scratch, size_t scratch_bytes, int* err_word,
-                  char side, char uplo, char transa, char diag, int64_t m, int64_t n, float alpha,
-                  const float* A, int64_t lda, float* B, int64_t ldb, void* stream);
+                  long long wait_ns, char side, char uplo, char transa, char diag, int64_t m,
+                  int64_t n, float alpha, const float* A, int64_t lda, float* B, int64_t ldb,
+                  void* stream);
 const char* set_detail(const char* msg);
 }  // namespace trx
 
 static __device__ __align__(256) unsigned char trx_noalloc_scratch[TRX_NOALLOC_SCRATCH_BYTES];
-// Error word of the bounded device-side waits (cleared by every call).
+// Error word of the bounded device-side waits: cleared by every call, read
+// and cleared by trx_noalloc_check_error.
 static __device__ __align__(256) int trx_noalloc_err_word[64];
 
 namespace {
@@ -43,6 +46,7 @@ struct DeviceSetup {
     void* scratch = nullptr;
     int* err = nullptr;
     int num_sms = 0;
+    long long wait_ns = 2000000000LL;
 };
 
 constexpr int kMaxDevices = 64;
@@ -67,6 +71,12 @@ int setup_device(int dev, DeviceSetup** out) {
         s.scratch = scratch;
         s.err = static_cast<int*>(err);
         s.num_sms = prop.multiProcessorCount;
+        // budget of each bounded device-side wait (2 s; TRX_NOALLOC_WAIT_NS
+        // overrides it, at least 1000 ns, read once per device here)
+        if (const char* v = std::getenv("TRX_NOALLOC_WAIT_NS")) {
+            const long long w = std::atoll(v);
+            if (w >= 1000) s.wait_ns = w;
+        }
         s.ready = true;
     }
     *out = &s;
@@ -96,5 +106,27 @@ extern "C" int trx_strsm_noalloc(char side, char uplo, char transa, char diag, i
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     if (cudaMemsetAsync(s->err, 0, sizeof(int), st) != cudaSuccess) return TRX_ERR_CUDA;
     return trx::noalloc_strsm(dev, s->num_sms, s->scratch, TRX_NOALLOC_SCRATCH_BYTES, s->err,
-                              side, uplo, transa, diag, m, n, alpha, A, lda, B, ldb, stream);
+                              s->wait_ns, side, uplo, transa, diag, m, n, alpha, A, lda, B, ldb,
+                              stream);
+}
+
+// Read and clear the error word of the current device (a plain copy from the
+// symbol: nothing is allocated). 0 if no call has run on this device yet.
+extern "C" int trx_noalloc_check_error(void) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return TRX_ERR_CUDA;
+    if (dev < 0 || dev >= kMaxDevices) return TRX_ERR_DEVICE;
+    {
+        std::lock_guard<std::mutex> lock(g_setup_mu);
+        if (!g_setup[dev].ready) return TRX_SUCCESS;
+    }
+    int v = 0;
+    if (cudaMemcpyFromSymbol(&v, trx_noalloc_err_word, sizeof(int)) != cudaSuccess)
+        return TRX_ERR_CUDA;
+    if (v != 0) {
+        const int zero = 0;
+        if (cudaMemcpyToSymbol(trx_noalloc_err_word, &zero, sizeof(int)) != cudaSuccess)
+            return TRX_ERR_CUDA;
+    }
+    return v;
 }

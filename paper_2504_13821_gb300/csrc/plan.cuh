@@ -269,6 +269,13 @@ inline bool tc_leaf_mode(int64_t opt, bool tc, int b) {
     return b == 64 || b == 128;
 }
 
+// Product terms of the tensor-core split (TRX_OPT_SPLIT: 1, 3 or 6; 0 =
+// automatic, 6: three BF16 slices per operand, the FP32-grade form).
+constexpr int kDefaultSplitTerms = 6;
+inline int split_terms(int64_t opt) {
+    return (opt == 1 || opt == 3 || opt == 6) ? (int)opt : kDefaultSplitTerms;
+}
+
 inline bool use_tc_mode(int elem, int64_t gemm_mode, int64_t k, int b) {
     if (elem != 4 || gemm_mode == 1 || k <= b) return false;   // k <= b: one leaf, no update
     if (gemm_mode == 2) return k > b;

@@ -35,6 +35,15 @@ __global__ void __launch_bounds__(kThreads) cast_f64_f32_kernel(const double* sr
 }
 
 // r := b - r (b already holds alpha B in FP64)
+__global__ void __launch_bounds__(kThreads) scale_f64_kernel(const double* src, int64_t lds,
+                                                             double* dst, int64_t ldd, int64_t m,
+                                                             int64_t n, double scale) {
+    for (int64_t e = (int64_t)blockIdx.x * kThreads + threadIdx.x; e < m * n;
+         e += (int64_t)gridDim.x * kThreads) {
+        const int64_t i = e % m, j = e / m;
+        dst[i + j * ldd] = scale * src[i + j * lds];
+    }
+}
 __global__ void __launch_bounds__(kThreads) residual_kernel(const double* b, int64_t ldb,
                                                             double* r, int64_t ldr, int64_t m,
                                                             int64_t n) {
@@ -209,7 +218,12 @@ constexpr int kStages = 3;
 constexpr uint32_t kABytes = kRK * kRM * 16, kXBytes = kRK * 32 * 16;
 constexpr uint32_t kStageBytes = kABytes + kXBytes;
 constexpr int kPipeSmem = kStages * (int)kStageBytes + 2 * kStages * 8 + 16;
-enum { kFull = 0, kSingle = 1, kPlain = 2 };
+enum { kFull = 0, kSingle = 1, kPlain = 2, kPair = 3 };
+// kPair: FP64 data. op(A) is packed as float pairs (ah, ah, al, al) with
+// ah = fl32(a), al = fl32(a - ah), X = xh + xl as in kFull; the term
+// ah xh is split exactly (FMA) and two-summed into hi, and ah xl + al xh go
+// to lo (al xl, below 2^-48 of a x, is left out).
+constexpr uint64_t kSign2 = 0x8000000080000000ull;
 
 __device__ __forceinline__ uint64_t pk(float a, float b) {
     uint64_t d;
@@ -319,6 +333,26 @@ __host__ __device__ __forceinline__ void tile_chunks(int64_t rt, int64_t K16, bo
 }
 
 // op(A) packed: block (chunk q of row tile blockIdx.y, quarter blockIdx.x % 4).
+// op(A) of FP64 data packed as (ah, ah, al, al), same layout as above.
+template <bool TRANS>
+__global__ void __launch_bounds__(256) pack_a64_kernel(const double* A, int64_t lda, int64_t k,
+                                                       int lower, int unit, float4* Ap) {
+    const int64_t K16 = (k + 15) / 16, rt = blockIdx.y, q = blockIdx.x >> 2;
+    int64_t first, count, offset;
+    tile_chunks(rt, K16, lower != 0, first, count, offset);
+    if (q >= count) return;
+    const int e = (int)(blockIdx.x & 3) * 256 + threadIdx.x;
+    const int l = TRANS ? (e & 15) : (e >> 6), i = TRANS ? (e >> 4) : (e & 63);
+    const int64_t gi = rt * kRM + i, gl = (first + q) * kRK + l;
+    double v = 0.0;
+    if (gi < k && gl < k && (lower ? gl <= gi : gl >= gi)) {
+        if (gl == gi && unit) v = 1.0;
+        else v = TRANS ? A[gl + gi * lda] : A[gi + gl * lda];
+    }
+    const float h = (float)v, lo = (float)(v - (double)h);
+    Ap[(offset + q) * (kRK * kRM) + l * kRM + i] = make_float4(h, h, lo, lo);
+}
+
 template <bool TRANS>
 __global__ void __launch_bounds__(256) pack_a_kernel(const float* A, int64_t lda, int64_t k,
                                                      int lower, int unit, float4* Ap) {
@@ -444,6 +478,16 @@ __global__ void __launch_bounds__(256) residual_pipe_kernel(const float4* __rest
                 const uint64_t a2 = pk(av.x, av.y), na2 = pk(av.z, av.w);
 #pragma unroll
                 for (int c = 0; c < 2; ++c) {
+                    if (MODE == kPair) {                           // na2 holds (al, al)
+                        const uint64_t p = mul2(a2, xh[c]);
+                        const uint64_t e = fma2(a2, xh[c], p ^ kSign2);   // ah xh - p, exact
+                        const uint64_t t = add2(hi[r][c], p);
+                        const uint64_t bp = sub2(t, hi[r][c]);
+                        const uint64_t er = add2(sub2(hi[r][c], sub2(t, bp)), sub2(p, bp));
+                        hi[r][c] = t;
+                        lo[r][c] = fma2(na2, xh[c], fma2(a2, xl[c], add2(lo[r][c], add2(er, e))));
+                        continue;
+                    }
                     if (MODE == kPlain) {
                         hi[r][c] = fma2(a2, xh[c], hi[r][c]);
                         continue;
@@ -586,6 +630,21 @@ cudaError_t refine_transpose_f64(const double* src, int64_t lds, double* dst, in
                                  int64_t rows, int64_t cols, cudaStream_t s) {
     return launch_transpose<double, double>(src, lds, dst, ldd, rows, cols, 1.0, s);
 }
+cudaError_t refine_transpose_f64_scaled(const double* src, int64_t lds, double* dst, int64_t ldd,
+                                        int64_t rows, int64_t cols, double scale,
+                                        cudaStream_t s) {
+    return launch_transpose<double, double>(src, lds, dst, ldd, rows, cols, scale, s);
+}
+cudaError_t refine_transpose_f64_f32(const double* src, int64_t lds, float* dst, int64_t ldd,
+                                     int64_t rows, int64_t cols, cudaStream_t s) {
+    return launch_transpose<double, float>(src, lds, dst, ldd, rows, cols, 1.0, s);
+}
+cudaError_t refine_scale_f64(const double* src, int64_t lds, double* dst, int64_t ldd, int64_t m,
+                             int64_t n, double scale, cudaStream_t s) {
+    if (m <= 0 || n <= 0) return cudaSuccess;
+    scale_f64_kernel<<<grid_for(m * n), kThreads, 0, s>>>(src, lds, dst, ldd, m, n, scale);
+    return cudaGetLastError();
+}
 size_t refine_pack_a_bytes(int64_t k, bool lower) {
     if (k <= 0) return 0;
     const int64_t nrt = (k + kRM - 1) / kRM, K16 = (k + 15) / 16;
@@ -609,6 +668,20 @@ cudaError_t refine_pack_a(const float* A, int64_t lda, int64_t k, bool lower, bo
     else
         pack_a_kernel<false><<<grid, 256, 0, s>>>(A, lda, k, lower, unit,
                                                   static_cast<float4*>(Ap));
+    return cudaGetLastError();
+}
+cudaError_t refine_pack_a64(const double* A, int64_t lda, int64_t k, bool lower, bool trans,
+                            bool unit, void* Ap, cudaStream_t s) {
+    if (k <= 0) return cudaSuccess;
+    const int64_t nrt = (k + kRM - 1) / kRM, K16 = (k + 15) / 16;
+    if (nrt > 65535 || 4 * K16 > 0x7fffffff) return cudaErrorInvalidValue;
+    const dim3 grid((unsigned)(4 * K16), (unsigned)nrt);
+    if (trans)
+        pack_a64_kernel<true><<<grid, 256, 0, s>>>(A, lda, k, lower, unit,
+                                                   static_cast<float4*>(Ap));
+    else
+        pack_a64_kernel<false><<<grid, 256, 0, s>>>(A, lda, k, lower, unit,
+                                                    static_cast<float4*>(Ap));
     return cudaGetLastError();
 }
 cudaError_t refine_pack_x(const double* X64, const float* X32, int64_t ldx, int64_t k,
@@ -657,21 +730,38 @@ cudaError_t launch_pipe(unsigned blocks, const void* Ap, const void* Xp, const i
                         double* part, int64_t rows, int64_t k, bool lower, const double* B,
                         int64_t ldb, double* R, int64_t ldr, int64_t n, int* err,
                         long long wait_ns, cudaStream_t s) {
-    static cudaError_t configured = cudaFuncSetAttribute(
-        residual_pipe_kernel<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, kPipeSmem);
-    if (configured != cudaSuccess) return configured;
     residual_pipe_kernel<MODE><<<blocks, 256, kPipeSmem, s>>>(
         static_cast<const float4*>(Ap), static_cast<const float4*>(Xp), units, part, rows, k,
         lower, B, ldb, R, ldr, n, err, wait_ns);
     return cudaGetLastError();
 }
+// Shared-memory limits of the residual kernels, for the current device
+// (kernel attributes are per device; called from each device's set-up).
+cudaError_t refine_configure() {
+    cudaError_t e;
+    if ((e = cudaFuncSetAttribute(residual_pipe_kernel<kFull>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, kPipeSmem)) !=
+        cudaSuccess)
+        return e;
+    if ((e = cudaFuncSetAttribute(residual_pipe_kernel<kSingle>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, kPipeSmem)) !=
+        cudaSuccess)
+        return e;
+    if ((e = cudaFuncSetAttribute(residual_pipe_kernel<kPlain>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, kPipeSmem)) !=
+        cudaSuccess)
+        return e;
+    return cudaFuncSetAttribute(residual_pipe_kernel<kPair>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, kPipeSmem);
+}
+
 cudaError_t refine_residual_packed(int mode, const void* Ap, const void* Xp, const void* units,
                                    int64_t nunits, const void* tiles, int64_t ntiles,
                                    double* part, int64_t k, bool lower, const double* B,
                                    int64_t ldb, double* R, int64_t ldr, int64_t n, int* err,
                                    long long wait_ns, cudaStream_t s) {
     if (k <= 0 || n <= 0) return cudaSuccess;
-    if (mode < kFull || mode > kPlain) return cudaErrorInvalidValue;
+    if (mode < kFull || mode > kPair) return cudaErrorInvalidValue;
     const int64_t nct = (n + kRN - 1) / kRN, blocks = nunits * nct;
     if (blocks > 0x7fffffff || ntiles > 65535) return cudaErrorInvalidValue;
     const int64_t rows = (k + 15) / 16 * 16;
@@ -683,6 +773,9 @@ cudaError_t refine_residual_packed(int mode, const void* Ap, const void* Xp, con
     else if (mode == kSingle)
         e = launch_pipe<kSingle>((unsigned)blocks, Ap, Xp, u, part, rows, k, lower, B, ldb, R,
                                  ldr, n, err, wait_ns, s);
+    else if (mode == kPair)
+        e = launch_pipe<kPair>((unsigned)blocks, Ap, Xp, u, part, rows, k, lower, B, ldb, R, ldr,
+                               n, err, wait_ns, s);
     else
         e = launch_pipe<kPlain>((unsigned)blocks, Ap, Xp, u, part, rows, k, lower, B, ldb, R, ldr,
                                 n, err, wait_ns, s);
@@ -691,6 +784,53 @@ cudaError_t refine_residual_packed(int mode, const void* Ap, const void* Xp, con
     if (gx > 0x7fffffff) return cudaErrorInvalidValue;
     combine_kernel<<<dim3((unsigned)gx, (unsigned)ntiles), 256, 0, s>>>(
         static_cast<const int4*>(tiles), part, k, n, B, ldb, R, ldr);
+    return cudaGetLastError();
+}
+// The work-unit table of refine_plan_units built on the device (one thread:
+// at most a few thousand entries), so an asynchronous caller needs no host
+// copy. Row tiles are taken heaviest first (the triangle's long rows) rather
+// than sorted by piece size; the order only balances the grid, the pieces
+// and their partial slots (numbered in row-tile order) are the host plan's,
+// so the residual is bitwise the same.
+__global__ void plan_units_kernel(int64_t k, int lower, int4* units, int4* tiles) {
+    const int64_t nrt = (k + kRM - 1) / kRM, K16 = (k + 15) / 16;
+    int64_t nu = 0, nt = 0, slot = 0;
+    // the split row tiles and their first slots, in row-tile order
+    for (int64_t rt = 0; rt < nrt; ++rt) {
+        int64_t first, count, offset;
+        tile_chunks(rt, K16, lower != 0, first, count, offset);
+        const int64_t pieces = (count + kUnitChunks - 1) / kUnitChunks;
+        if (pieces > 1) {
+            tiles[nt++] = make_int4((int)rt, (int)slot, (int)pieces, 0);
+            slot += pieces;
+        }
+    }
+    // units, long rows first (descending row tiles for a lower triangle):
+    // the split tiles are then met in the reverse of the order above
+    int64_t ti = lower ? nt - 1 : 0;
+    for (int64_t v = 0; v < nrt; ++v) {
+        const int64_t rt = lower ? nrt - 1 - v : v;
+        int64_t first, count, offset;
+        tile_chunks(rt, K16, lower != 0, first, count, offset);
+        const int64_t pieces = (count + kUnitChunks - 1) / kUnitChunks;
+        if (pieces == 1) {
+            units[nu++] = make_int4((int)rt, 0, (int)count, -1);
+            continue;
+        }
+        const int64_t s0 = tiles[ti].y;
+        ti += lower ? -1 : 1;
+        for (int64_t q = 0; q < pieces; ++q) {
+            const int64_t q0 = count * q / pieces, q1 = count * (q + 1) / pieces;
+            units[nu++] = make_int4((int)rt, (int)q0, (int)q1, (int)(s0 + q));
+        }
+    }
+}
+
+cudaError_t refine_plan_units_device(int64_t k, bool lower, void* units, void* tiles,
+                                     cudaStream_t s) {
+    if (k <= 0) return cudaSuccess;
+    plan_units_kernel<<<1, 1, 0, s>>>(k, lower ? 1 : 0, static_cast<int4*>(units),
+                                      static_cast<int4*>(tiles));
     return cudaGetLastError();
 }
 // sums[i] := row i's sum of |M| through kNormSlices partials at sums + m.

@@ -18,6 +18,13 @@
 //   4. report: completed request ids and their status codes.
 // The plan a request gets depends only on its own problem, never on what
 // else is in flight, so a result is the same alone and in the mix.
+//
+// Request kinds: TRSM and TRMM in the factor's precision (trx_server_submit)
+// and the refined FP32 TRSM (trx_server_submit_refined: FP32 factor and
+// right-hand side, FP64 result, the FP32 solve plus a fixed number of
+// float-float corrections, trx_strsm_refined_async, with no host read-back).
+// FP64 TRSM requests take the handles' FP64 engine (config fp64_corrections:
+// the recursive DFMA solve, or the FP32 solve plus corrections).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -30,6 +37,9 @@
 
 namespace trx {
 const char* set_detail(const char* msg);   // the thread's error detail string (api.cu)
+// swap a handle's workspace without synchronising the device: the caller
+// has made sure no earlier work of the handle still runs (api.cu)
+int handle_swap_workspace(trx_handle_t h, void* ptr, size_t bytes);
 }
 
 namespace {
@@ -51,10 +61,12 @@ struct Fac {
 struct Req {
     int64_t id;
     int fid;
-    char op, side;
+    char op, side;          // op 'S', 'M', or 'R' (refined FP32 TRSM)
     double alpha;
     void* B;
     int64_t m, n, ldb;
+    double* X = nullptr;    // refined: the FP64 result
+    int64_t ldx = 0;
     cudaEvent_t ready;   // recorded on the caller's stream at submission
     size_t cost = 0;
 };
@@ -110,12 +122,17 @@ cudaError_t get_event(trx_server_t s, cudaEvent_t* ev) {
 }
 void put_event(trx_server_t s, cudaEvent_t ev) { s->pool.push_back(ev); }
 
+// Device bytes a request holds while in flight: its right-hand side (and
+// result), plus the operand planes of a tensor-core FP32 call (three BF16
+// slices of the k x k triangle and of the k x nrhs right-hand side).
 size_t cost_bytes(const trx_server_s* s, const Req& r) {
     const Fac& f = s->facs[r.fid];
     const int64_t nrhs = upc(r.side) == 'L' ? r.n : r.m;
     size_t b = (size_t)r.m * (size_t)r.n * (size_t)f.elem;
-    if (f.k > s->cfg.small_k && f.elem == 4)   // operand planes of a tensor-core call
-        b += 4 * (size_t)f.k * (size_t)(f.k + nrhs);
+    if (r.op == 'R') b += (size_t)r.m * (size_t)r.n * 8;
+    const bool tc_call = f.k > s->cfg.small_k || r.op == 'R';
+    const bool fp32_solve = f.elem == 4 || (upc(r.op) == 'S' && s->cfg.fp64_corrections > 0);
+    if (tc_call && fp32_solve) b += 6 * (size_t)f.k * (size_t)(f.k + nrhs);
     return b;
 }
 
@@ -126,27 +143,34 @@ void complete_now(trx_server_t s, const Req& r, int code) {
     put_event(s, r.ready);
 }
 
+// Grow stream i's workspace. Only that stream is waited for (its handle's
+// cached graphs point into the old buffer and are dropped); the buffers are
+// stream-ordered allocations, so neither the allocation nor the release of
+// the old one synchronises the device and the other streams keep running.
 int ensure_ws(trx_server_t s, int i, size_t need) {
     if (need <= s->ws_bytes[i]) return TRX_SUCCESS;
+    cudaStream_t st = s->streams[i];
     size_t bytes = std::max(need, s->ws_bytes[i] * 2);
     void* p = nullptr;
-    cudaError_t e = cudaMalloc(&p, bytes);
+    cudaError_t e = cudaMallocAsync(&p, bytes, st);
     if (e != cudaSuccess) {
         cudaGetLastError();
         bytes = need;
-        if ((e = cudaMalloc(&p, bytes)) != cudaSuccess) {
-            trx::set_detail("server workspace: cudaMalloc failed");
+        if ((e = cudaMallocAsync(&p, bytes, st)) != cudaSuccess) {
+            trx::set_detail("server workspace: cudaMallocAsync failed");
             return TRX_ERR_ALLOC;
         }
     }
-    // trx_set_workspace synchronises the device before swapping, so the old
-    // buffer is idle once it returns
-    const int rc = trx_set_workspace(s->handles[i], p, bytes);
+    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) {
+        cudaFreeAsync(p, st);
+        return fail(e, "workspace swap");
+    }
+    const int rc = trx::handle_swap_workspace(s->handles[i], p, bytes);
     if (rc != TRX_SUCCESS) {
-        cudaFree(p);
+        cudaFreeAsync(p, st);
         return rc;
     }
-    if (s->ws[i]) cudaFree(s->ws[i]);
+    if (s->ws[i]) cudaFreeAsync(s->ws[i], st);
     s->ws[i] = p;
     s->ws_bytes[i] = bytes;
     return TRX_SUCCESS;
@@ -157,13 +181,19 @@ int launch_large(trx_server_t s, Req& r) {
     const Fac& f = s->facs[r.fid];
     cudaStream_t st = s->streams[i];
     size_t need = 0;
-    int rc = trx_workspace_size(s->handles[i], r.op, r.side, r.m, r.n, f.elem, &need);
+    const char wop = r.op == 'R' ? 'S' : r.op;
+    int rc = trx_workspace_size(s->handles[i], wop, r.side, r.m, r.n, f.elem, &need);
     if (rc == TRX_SUCCESS) rc = ensure_ws(s, i, need);
     if (rc != TRX_SUCCESS) return rc;
     cudaError_t e = cudaStreamWaitEvent(st, r.ready, 0);
     if (e != cudaSuccess) return fail(e, "wait");
     const bool trsm = upc(r.op) == 'S';
-    if (f.elem == 4) {
+    if (r.op == 'R') {
+        rc = trx_strsm_refined_async(s->handles[i], r.side, f.uplo, f.trans, f.diag, r.m, r.n,
+                                     (float)r.alpha, static_cast<const float*>(f.A), f.lda,
+                                     static_cast<const float*>(r.B), r.ldb, r.X, r.ldx,
+                                     s->cfg.refine_corrections, st);
+    } else if (f.elem == 4) {
         auto fn = trsm ? trx_strsm : trx_strmm;
         rc = fn(s->handles[i], r.side, f.uplo, f.trans, f.diag, r.m, r.n, (float)r.alpha,
                 static_cast<const float*>(f.A), f.lda, static_cast<float*>(r.B), r.ldb, st);
@@ -172,7 +202,12 @@ int launch_large(trx_server_t s, Req& r) {
         rc = fn(s->handles[i], r.side, f.uplo, f.trans, f.diag, r.m, r.n, r.alpha,
                 static_cast<const double*>(f.A), f.lda, static_cast<double*>(r.B), r.ldb, st);
     }
-    if (rc != TRX_SUCCESS) return rc;
+    if (rc != TRX_SUCCESS) {
+        // part of the call may already be enqueued: the request's buffers
+        // are idle before it is reported failed
+        cudaStreamSynchronize(st);
+        return rc;
+    }
     Flight fl;
     // the launch is in flight: without a completion event, wait for it here
     // so the request's buffers are idle when it is reported failed
@@ -218,7 +253,10 @@ int launch_small(trx_server_t s, std::vector<Req>& group, int elem) {
         probs.push_back(p);
     }
     int rc = trx_batched(s->bhandle, elem, (int64_t)probs.size(), probs.data(), s->bstream);
-    if (rc != TRX_SUCCESS) return rc;
+    if (rc != TRX_SUCCESS) {
+        cudaStreamSynchronize(s->bstream);     // see launch_large
+        return rc;
+    }
     Flight fl;
     if ((e = get_event(s, &fl.done)) != cudaSuccess) {
         cudaStreamSynchronize(s->bstream);     // see launch_large
@@ -280,10 +318,13 @@ int trx_server_create(int device, const trx_server_config_t* config, trx_server_
     cfg.budget_bytes = (size_t)150 << 30;
     cfg.workspace_bytes = 0;
     cfg.graphs = 1;
+    cfg.refine_corrections = 2;
+    cfg.fp64_corrections = 0;
     if (config) cfg = *config;
     if (cfg.streams < 1 || cfg.streams > 16 || cfg.small_k < 0 ||
         cfg.small_k > TRX_BATCH_MAX_K || cfg.max_inflight < 1 ||
-        (cfg.graphs != 0 && cfg.graphs != 1))
+        (cfg.graphs != 0 && cfg.graphs != 1) || cfg.refine_corrections < 0 ||
+        cfg.refine_corrections > 16 || cfg.fp64_corrections < 0 || cfg.fp64_corrections > 16)
         return TRX_ERR_INVALID_VALUE;
     cudaError_t e = cudaSetDevice(device);
     if (e != cudaSuccess) return fail(e, "cudaSetDevice");
@@ -303,6 +344,8 @@ int trx_server_create(int device, const trx_server_config_t* config, trx_server_
         if ((rc = trx_create(&h, device, 0)) != TRX_SUCCESS) break;
         s->handles.push_back(h);
         if ((rc = trx_set_option(h, TRX_OPT_GRAPH, cfg.graphs)) != TRX_SUCCESS) break;
+        if ((rc = trx_set_option(h, TRX_OPT_FP64_TRSM, cfg.fp64_corrections)) != TRX_SUCCESS)
+            break;
         s->ws.push_back(nullptr);
         s->ws_bytes.push_back(0);
     }
@@ -331,8 +374,9 @@ int trx_server_destroy(trx_server_t s) {
     if (s->bstream) cudaStreamSynchronize(s->bstream);
     for (trx_handle_t h : s->handles) trx_destroy(h);
     if (s->bhandle) trx_destroy(s->bhandle);
-    for (void* p : s->ws)
-        if (p) cudaFree(p);
+    for (size_t i = 0; i < s->ws.size(); ++i)   // stream-ordered allocations
+        if (s->ws[i]) cudaFreeAsync(s->ws[i], s->streams[i]);
+    for (cudaStream_t st : s->streams) cudaStreamSynchronize(st);
     for (cudaStream_t st : s->streams) cudaStreamDestroy(st);
     if (s->bstream) cudaStreamDestroy(s->bstream);
     for (Flight& fl : s->inflight) cudaEventDestroy(fl.done);
@@ -419,6 +463,51 @@ int trx_server_submit(trx_server_t s, int factor_id, char op, char side, double 
     return TRX_SUCCESS;
 }
 
+int trx_server_submit_refined(trx_server_t s, int factor_id, char side, double alpha,
+                              const void* B, int64_t m, int64_t n, int64_t ldb, double* X,
+                              int64_t ldx, void* input_stream, int64_t* request_id) {
+    if (!valid(s)) return TRX_ERR_HANDLE;
+    if (factor_id < 0 || factor_id >= (int)s->facs.size() || !s->facs[factor_id].live ||
+        s->facs[factor_id].released || s->facs[factor_id].elem != 4)
+        return -2;
+    const int sd = upc(side);
+    if (sd != 'L' && sd != 'R') return -3;
+    const Fac& f = s->facs[factor_id];
+    if (m < 0 || (sd == 'L' && m != f.k)) return -7;
+    if (n < 0 || (sd == 'R' && n != f.k)) return -8;
+    if (m > 0 && n > 0 && B == nullptr) return -5;
+    if (ldb < std::max<int64_t>(1, m)) return -9;
+    if (m > 0 && n > 0 && X == nullptr) return -10;
+    if (ldx < std::max<int64_t>(1, m)) return -11;
+    if (!request_id) return -13;
+    Req r;
+    r.id = s->next_id;
+    r.fid = factor_id;
+    r.op = 'R';
+    r.side = (char)sd;
+    r.alpha = alpha;
+    r.B = const_cast<void*>(B);
+    r.m = m;
+    r.n = n;
+    r.ldb = ldb;
+    r.X = X;
+    r.ldx = ldx;
+    cudaError_t e = cudaSetDevice(s->device);
+    if (e != cudaSuccess) return fail(e, "cudaSetDevice");
+    if ((e = get_event(s, &r.ready)) != cudaSuccess) return fail(e, "event");
+    if ((e = cudaEventRecord(r.ready, reinterpret_cast<cudaStream_t>(input_stream))) !=
+        cudaSuccess) {
+        put_event(s, r.ready);
+        return fail(e, "record");
+    }
+    r.cost = cost_bytes(s, r);
+    s->next_id += 1;
+    s->facs[factor_id].outstanding += 1;
+    s->waiting.push_back(r);
+    *request_id = r.id;
+    return TRX_SUCCESS;
+}
+
 int trx_server_poll(trx_server_t s, int64_t* ids, int* status, int capacity, int* count) {
     if (!valid(s)) return TRX_ERR_HANDLE;
     if (!count || capacity < 0 || (capacity > 0 && (!ids || !status)))
@@ -439,7 +528,7 @@ int trx_server_poll(trx_server_t s, int64_t* ids, int* status, int capacity, int
         }
         s->inflight_bytes += r.cost;
         const Fac& f = s->facs[r.fid];
-        if (f.k <= s->cfg.small_k)
+        if (f.k <= s->cfg.small_k && r.op != 'R')   // the batched kernel has no refinement
             (f.elem == 4 ? small4 : small8).push_back(r);
         else
             large.push_back(r);

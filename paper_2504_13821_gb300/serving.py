@@ -20,14 +20,15 @@ class Server:
 
     def __init__(self, device=0, streams: int = 4, budget_bytes: int = 150 << 30,
                  max_inflight: int = 4096, small_k: int = 512, workspace_bytes: int = 0,
-                 graphs: bool = True):
+                 graphs: bool = True, refine_corrections: int = 2, fp64_corrections: int = 0):
         import torch
         self.torch = torch
         self.device = torch.device("cuda", device if isinstance(device, int) else
                                    torch.device(device).index or 0)
         lib = _binding.load_library()
         cfg = _binding.ServerConfig(streams, small_k, max_inflight, budget_bytes,
-                                    workspace_bytes, int(graphs))
+                                    workspace_bytes, int(graphs), refine_corrections,
+                                    fp64_corrections)
         h = ctypes.c_void_p()
         _binding._check(lib.trx_server_create(self.device.index, ctypes.byref(cfg),
                                               ctypes.byref(h)), "trx_server_create")
@@ -80,6 +81,28 @@ class Server:
             self._s, fid, _binding._char(op), _binding._char(side), float(alpha), ptr, m, n, ldb,
             _binding._stream_ptr(stream, B.device), ctypes.byref(rid)), "trx_server_submit")
         self._requests[rid.value] = (fid, B)
+        self._outstanding[fid] += 1
+        return rid.value
+
+    def submit_refined(self, fid: int, side: str, alpha: float, B, X, stream=None) -> int:
+        """Queue a refined FP32 TRSM: X (float64) := the solution of
+        op(A) X = alpha B (side 'L') or X op(A) = alpha B, B float32 (not
+        modified); returns the request id."""
+        torch = self.torch
+        A = self._factors[fid]
+        if A.dtype != torch.float32 or B.dtype != torch.float32 or X.dtype != torch.float64:
+            raise TypeError("refined requests: float32 factor and B, float64 X")
+        if tuple(X.shape) != tuple(B.shape):
+            raise ValueError("X must have B's shape")
+        bptr, ldb = _binding._colmajor(B, "B")
+        xptr, ldx = _binding._colmajor(X, "X")
+        m, n = B.shape
+        rid = ctypes.c_int64()
+        _binding._check(_binding.load_library().trx_server_submit_refined(
+            self._s, fid, _binding._char(side), float(alpha), bptr, m, n, ldb, xptr, ldx,
+            _binding._stream_ptr(stream, B.device), ctypes.byref(rid)),
+            "trx_server_submit_refined")
+        self._requests[rid.value] = (fid, (B, X))
         self._outstanding[fid] += 1
         return rid.value
 

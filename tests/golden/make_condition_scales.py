@@ -2,7 +2,8 @@
 factor generator (strict triangle uniform(-1,1) * s / k, diagonal
 1 + |N(0,1)|) at which the factor's 1-norm condition number, as the oracle
 estimates it (Hager's method with Higham's refinements), reaches the target
-kappa. The refined-TRSM workload reads these scales for its inputs.
+kappa. The precision-form workloads (refined TRSM, split-product
+comparisons) and the engine tests read these scales for their inputs.
 
 Run from the repository root: python tests/golden/make_condition_scales.py
 """
@@ -18,7 +19,7 @@ import numpy as np  # noqa: E402
 import oracle  # noqa: E402
 from paper_2504_13821_gb300 import inputs  # noqa: E402
 
-ORDERS = (8192,)
+ORDERS = (1024, 4096, 8192, 16384, 32768)
 TARGETS = (1e2, 1e4, 1e6)
 
 
@@ -39,10 +40,11 @@ def main():
             out["entries"].append({"k": k, "target": t, "seed": seed, "scale": s,
                                    "kappa_estimate": kappa})
             print(k, t, seed, s, kappa, flush=True)
-    with open(os.path.join(os.path.dirname(os.path.abspath(__file__)),
-                           "condition_scales.json"), "w") as f:
-        json.dump(out, f, indent=1)
-        f.write("\n")
+            # written after every entry: the large orders take minutes each
+            with open(os.path.join(os.path.dirname(os.path.abspath(__file__)),
+                                   "condition_scales.json"), "w") as f:
+                json.dump(out, f, indent=1)
+                f.write("\n")
 
 
 if __name__ == "__main__":

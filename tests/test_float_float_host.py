@@ -107,3 +107,60 @@ def test_split_of_x_keeps_48_bits():
     xh, xl = split(x)
     rel = np.abs(x - (xh.astype(np.float64) + xl.astype(np.float64))) / np.abs(x)
     assert rel.max() <= 2.0 ** -47
+
+
+def emulate_pair(ah, al, xh, xl, fold=32):
+    """The FP64-data mode: a = ah + al as well. Per term p = fl(ah xh) and
+    e = ah xh - p exactly; p two-summed into hi; err + e, then ah xl and
+    al xh (two FMAs, in that order) into lo; folds as above."""
+    rows = ah.shape[1]
+    hi = np.zeros(rows, F)
+    lo = np.zeros(rows, F)
+    mid = np.zeros(rows, F)
+    lo2 = np.zeros(rows, F)
+    d = np.float64
+    for t in range(ah.shape[0]):
+        ax = ah[t].astype(d) * xh[t].astype(d)
+        p = ax.astype(F)
+        e = (ax - p.astype(d)).astype(F)
+        hi, err = two_sum(hi, p)
+        s = F(lo + F(err + e))
+        s = (ah[t].astype(d) * xl[t].astype(d) + s.astype(d)).astype(F)
+        lo = (al[t].astype(d) * xh[t].astype(d) + s.astype(d)).astype(F)
+        if (t + 1) % fold == 0:
+            mid, err2 = two_sum(mid, lo)
+            lo2 = F(lo2 + err2)
+            lo = np.zeros(rows, F)
+    return hi.astype(d) + (mid.astype(d) + (lo.astype(d) + lo2.astype(d)))
+
+
+def test_pair_mode_fp64_data_keeps_44_bits():
+    """A and X both FP64 data, each carried as two floats: the residual of
+    an FP64 system on the FP32 pipes. Against the exact sum of the FP64
+    products a x (math.fsum of products split exactly), the error stays
+    below 2^-44 of sum |a x| on random and on cancelling rows (the dropped
+    al xl term alone is about 2^-48)."""
+    rng = np.random.default_rng(4)
+    K, R = 2048, 32
+    a = rng.uniform(-1, 1, (K, R)) * 2.0 ** rng.integers(-10, 11, (K, R))
+    x = rng.standard_normal((K, R))
+    x[K // 2:] = -x[:K // 2] * a[:K // 2] / a[K // 2:]    # pairs that cancel
+    ah, al = split(a)
+    xh, xl = split(x)
+    got = emulate_pair(ah, al, xh, xl)
+    ref = []
+    for r in range(R):
+        terms = []
+        for t in range(K):
+            # a x exactly as a sum of FP64 pieces: (ah + al)(xh + xl)
+            for u in (ah[t, r], al[t, r]):
+                for v in (xh[t, r], xl[t, r]):
+                    terms.append(float(u) * float(v))      # exact: 24 x 24 bits
+        ref.append(math.fsum(terms))
+    ref = np.array(ref)
+    scale = np.sum(np.abs(a * x), axis=0)
+    rel = np.abs(got - ref) / scale
+    assert rel.max() <= 2.0 ** -44, np.log2(rel.max())
+    # the same data with A rounded to one float (mode 0) is ~2^-24 off
+    coarse = emulate(ah, xh, xl)
+    assert np.max(np.abs(coarse - ref) / scale) > 2.0 ** 16 * rel.max()

@@ -105,3 +105,72 @@ def test_server_budget_and_release():
         e = oracle.trsm_backward_error("L", "L", "N", "N", 1.0, A, X, B0)["eta"]
         assert e <= bound(600, np.float32)
     srv.close()
+
+
+def test_serving_refined_and_mixed_fp64_kinds():
+    """Refined FP32 TRSM requests (FP64 result, two float-float corrections)
+    and FP64 TRSM on the mixed engine (FP32 solve + three corrections) in
+    one mix with plain FP32/FP64 TRMM: every refined result has the
+    backward error of an FP64 solve (8 k 2^-53 against the oracle), every
+    FP64 TRSM too, and each result is bit-identical to the same request
+    served alone."""
+    from paper_2504_13821_gb300 import serving
+    dev = torch.device("cuda", 0)
+    rng = np.random.default_rng(41)
+    facs = []
+    for i, (k, dtype) in enumerate([(120, np.float32), (700, np.float32), (400, np.float64),
+                                    (1100, np.float64)]):
+        uplo, trans = str(rng.choice(["L", "U"])), str(rng.choice(["N", "T"]))
+        A = inputs.tri_matrix(k, uplo, seed=500 + i, dtype=dtype)
+        facs.append((A, uplo, trans, dtype))
+    reqs = []
+    for r in range(40):
+        fi = int(rng.integers(len(facs)))
+        A, uplo, trans, dtype = facs[fi]
+        k = A.shape[0]
+        op = "S" if rng.random() < 0.7 else "M"
+        side = str(rng.choice(["L", "R"]))
+        nrhs = int(rng.integers(1, 150))
+        m, n = (k, nrhs) if side == "L" else (nrhs, k)
+        reqs.append((fi, op, side, inputs.rhs(m, n, seed=9000 + r, dtype=dtype)))
+
+    def run(sel, spread):
+        srv = serving.Server(0, streams=3, budget_bytes=1 << 30, max_inflight=64,
+                             refine_corrections=2, fp64_corrections=3)
+        ids = [srv.register(to_dev(A, dev), u, t, "N") for (A, u, t, _) in facs]
+        outs, status = [], {}
+        t0 = time.perf_counter()
+        for j, i in enumerate(sel):
+            fi, op, side, B = reqs[i]
+            Bt = to_dev(B, dev)
+            while time.perf_counter() < t0 + spread * j / len(sel):
+                status.update(srv.poll())
+            if op == "S" and facs[fi][3] == np.float32:
+                X = torch.empty(B.shape[1], B.shape[0], device=dev, dtype=torch.float64).t()
+                rid = srv.submit_refined(ids[fi], side, 1.5, Bt, X)
+                outs.append((rid, X))
+            else:
+                rid = srv.submit(ids[fi], op, side, 1.5, Bt)
+                outs.append((rid, Bt))
+        status.update(srv.drain())
+        torch.cuda.synchronize()
+        srv.close()
+        assert sorted(status) == sorted(r for r, _ in outs) and not any(status.values()), status
+        return [o.cpu().numpy() for _, o in outs]
+
+    mixed = run(range(len(reqs)), 0.05)
+    for i, (fi, op, side, B) in enumerate(reqs):
+        A, uplo, trans, dtype = facs[fi]
+        k = A.shape[0]
+        X = np.asfortranarray(mixed[i].astype(np.float64))
+        A64, B64 = A.astype(np.float64), B.astype(np.float64)
+        if op == "S":
+            e = oracle.trsm_backward_error(side, uplo, trans, "N", 1.5, A64, X, B64)["eta"]
+            assert e <= 8 * k * 2.0 ** -53, (i, dtype, k, e)
+        else:
+            e = oracle.trmm_error(side, uplo, trans, "N", 1.5, A64, X,
+                                  oracle.trmm(side, uplo, trans, "N", 1.5, A64, B64), B64)
+            assert e <= bound(k, dtype), (i, dtype, k, e)
+    for i in range(0, len(reqs), 7):
+        solo = run([i], 0.0)
+        assert np.array_equal(solo[0], mixed[i]), f"request {i} differs alone vs in the mix"

@@ -305,6 +305,71 @@ def test_backward_error_residual_is_twice_working_precision():
     assert abs(r["res"] - exact) <= 1e-6 * exact
 
 
+def _op_exact(uplo, trans, diag, A, k):
+    """op(A) of the referenced triangle as a k x k list of Fractions (unit
+    diagonal 1, the other triangle 0)."""
+    T = [[Fraction(0)] * k for _ in range(k)]
+    for i in range(k):
+        for l in range(k):
+            if i == l:
+                T[i][l] = Fraction(1) if diag == "U" else Fraction(float(A[i, l]))
+            elif (uplo == "L" and i > l) or (uplo == "U" and i < l):
+                T[i][l] = Fraction(float(A[i, l]))
+    if trans != "N":
+        T = [[T[l][i] for l in range(k)] for i in range(k)]
+    return T
+
+
+@pytest.mark.parametrize("uplo,trans,diag", [("U", "T", "U"), ("L", "N", "N"),
+                                             ("U", "N", "N"), ("L", "T", "U")])
+def test_backward_error_side_right_exact_residual(uplo, trans, diag):
+    # Side R: R = X op(A) - alpha B (Eq. 4), eta = ||R|| / (||op(A)|| ||X||).
+    # Every quantity is recomputed here in exact rationals from the stored
+    # floating-point numbers (X perturbed away from the solution so that R is
+    # well above rounding); a transposed residual, a row/column mix-up in
+    # either norm or a wrong triangle all fail.
+    m, k = 7, 6
+    alpha = 1.5
+    A, B = inputs.problem("R", uplo, m, k, seed=77, dtype=np.float64,
+                          poison_diag=(diag == "U"))
+    X = oracle.trsm("R", uplo, trans, diag, alpha, A, B)
+    rng = np.random.default_rng(78)
+    X = np.asfortranarray(X + rng.standard_normal(X.shape) * 1e-6)
+    r = oracle.trsm_backward_error("R", uplo, trans, diag, alpha, A, X, B)
+    T = _op_exact(uplo, trans, diag, A, k)
+    res_rows = []
+    for i in range(m):
+        row = Fraction(0)
+        for j in range(k):
+            v = sum(Fraction(float(X[i, l])) * T[l][j] for l in range(k))
+            row += abs(v - Fraction(alpha) * Fraction(float(B[i, j])))
+        res_rows.append(row)
+    res = max(res_rows)
+    norm_a = max(sum(abs(T[i][j]) for j in range(k)) for i in range(k))
+    norm_x = max(sum(abs(Fraction(float(X[i, j]))) for j in range(k)) for i in range(m))
+    assert r["res"] == pytest.approx(float(res), rel=1e-12)
+    assert r["norm_a"] == pytest.approx(float(norm_a), rel=1e-15)
+    assert r["norm_x"] == pytest.approx(float(norm_x), rel=1e-15)
+    assert r["eta"] == pytest.approx(float(res / (norm_a * norm_x)), rel=1e-12)
+
+
+def test_backward_error_side_right_exact_zero_and_identity():
+    # Exact integer system on side R: X op(A) = B solved exactly -> eta 0;
+    # identity factor: eta = ||X - B|| / ||X|| with the row-sum norm.
+    rng = np.random.default_rng(5)
+    A, B = int_problem(rng, "R", "U", "U", 4, 6)
+    X = oracle.trsm("R", "U", "N", "U", 1.0, A, B)
+    assert oracle.trsm_backward_error("R", "U", "N", "U", 1.0, A, X, B)["eta"] == 0.0
+    m, k = 4, 5
+    Id = np.asfortranarray(np.eye(k))
+    B = np.asfortranarray(rng.standard_normal((m, k)))
+    Xp = np.asfortranarray(B + rng.standard_normal((m, k)) * 2.0**-30)
+    Ex = Xp - B
+    r = oracle.trsm_backward_error("R", "L", "T", "N", 1.0, Id, Xp, B)
+    want = np.abs(Ex).sum(1).max() / np.abs(Xp).sum(1).max()
+    assert abs(r["eta"] - want) <= 1e-12 * want
+
+
 # ---- condition estimate (inputs of the precision-form configuration) ------
 
 def _exact_kappa_one(uplo, trans, diag, A):

@@ -10,6 +10,10 @@ Collected last on purpose (file name), so a failure here comes after every
 other test has run.
 """
 import ctypes
+import os
+import subprocess
+import sys
+import textwrap
 
 import numpy as np
 import pytest
@@ -71,7 +75,7 @@ def test_noalloc_rejects_oversized_problem_before_launch():
     lib = trx.load_library()
     f = _noalloc(lib)
     dev = torch.device("cuda", 0)
-    # k = 4096, nrhs = 4096 needs about 128 MiB of planes > 64 MiB
+    # k = 4096, nrhs = 4096 needs 192 MiB of planes (6-term split) > 64 MiB
     A = trx.to_colmajor(torch.eye(4096, device=dev))
     B = trx.to_colmajor(torch.ones(4096, 4096, device=dev))
     rc = f(b"L", b"L", b"N", b"N", 4096, 4096, 1.0, A.data_ptr(), 4096, B.data_ptr(), 4096,
@@ -83,3 +87,40 @@ def test_noalloc_rejects_oversized_problem_before_launch():
     # BLAS argument positions come first
     assert f(b"X", b"L", b"N", b"N", 4, 4, 1.0, None, 4, None, 4, None) == -1
     assert f(b"L", b"L", b"N", b"N", 4, 4, 1.0, None, 4, None, 4, None) == -8
+
+
+def test_noalloc_check_error_reports_a_timed_out_wait():
+    """A bounded device-side wait that runs out is reported by
+    trx_noalloc_check_error (read and clear), without a GPU fault: a child
+    process sets the wait budget to 1 microsecond (TRX_NOALLOC_WAIT_NS, read
+    at the device's set-up), so the tensor-core update's waits give up, the
+    kernel records TRX_ERR_TIMEOUT and returns; the word reads 4 once, then
+    0. The child exits normally (the context stays usable)."""
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    code = textwrap.dedent("""
+        import ctypes, sys
+        import torch
+        sys.path.insert(0, ROOT)
+        import paper_2504_13821_gb300 as trx
+        lib = trx.load_library()
+        f = lib.trx_strsm_noalloc
+        c, i64, vp = ctypes.c_char, ctypes.c_int64, ctypes.c_void_p
+        f.argtypes = [c, c, c, c, i64, i64, ctypes.c_float, vp, i64, vp, i64, vp]
+        dev = torch.device("cuda", 0)
+        k = 1024
+        A = trx.to_colmajor(torch.eye(k, device=dev) * 2 + torch.rand(k, k, device=dev).tril(-1) / k)
+        B = trx.to_colmajor(torch.ones(k, 2048 // 4, device=dev))
+        assert lib.trx_noalloc_check_error() == 0
+        rc = f(b"L", b"L", b"N", b"N", k, B.shape[1], 1.0, A.data_ptr(), k, B.data_ptr(), k,
+               torch.cuda.current_stream(dev).cuda_stream)
+        assert rc == 0, rc
+        torch.cuda.synchronize()
+        first, second = lib.trx_noalloc_check_error(), lib.trx_noalloc_check_error()
+        print("check_error", first, second)
+        assert (first, second) == (4, 0), (first, second)
+    """).replace("ROOT", repr(root))
+    env = dict(os.environ, TRX_NOALLOC_WAIT_NS="1000")
+    r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True,
+                       timeout=600)
+    assert r.returncode == 0, r.stdout + r.stderr
+    assert "check_error 4 0" in r.stdout
