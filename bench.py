@@ -10,8 +10,10 @@ tensor-core GEMM updates. Metric: TFLOP/s with the m^2 n convention per call
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 For N > 1 launch under torch.distributed.run; every rank runs its own copy
-of the workload (right-hand sides of TRSM/TRMM are independent, so the work
-shards with no exchange) and rank 0 prints one JSON line.
+of the workload (weak scaling), or with --shard its panel of the one
+problem's right-hand sides (strong scaling: right-hand sides of TRSM/TRMM
+are independent, so the work shards with no exchange); rank 0 prints one
+JSON line.
 
 --impl reference times the FP64 CPU oracle (plain substitution / triple
 loop, OpenMP) on a bounded sample of the same workload's right-hand sides.
@@ -19,7 +21,6 @@ loop, OpenMP) on a bounded sample of the same workload's right-hand sides.
 from __future__ import annotations
 
 import argparse
-import hashlib
 import json
 import os
 import statistics
@@ -48,29 +49,18 @@ SPLIT_DESC = {6: "3 BF16 slices per operand, every slice product above 2^-24: FP
 REF_SAMPLE_COLS = 16      # per step of --impl reference
 
 
-# DRAM traffic of gemm_tc_kernel per launch on this workload, from one ncu
-# capture (dram__bytes_read.sum + dram__bytes_write.sum summed over one step's
-# gemm_tc launches, divided by their number). It holds for the sources it was
-# taken on only: when the GEMM kernel or the planner has changed since, the
-# line reports null. The capture's summary and command are in profiles/.
-TRAFFIC_SOURCES = ("paper_2504_13821_gb300/csrc/gemm_tc.cu", "paper_2504_13821_gb300/csrc/plan.cuh")
-TRAFFIC_CAPTURE = {"sources_sha256": "6b20c53ee08ba4d42b3548eea914f99f79e23ec0021b4d5abb73627139e0f224",
-                   "bytes_per_launch": 226154380, "launches_per_step": 132,
-                   "profile": "profiles/gemm_tc_traffic_trsm_trmm_n16384.md"}
-
-
-def sources_sha256():
-    h = hashlib.sha256()
-    for f in TRAFFIC_SOURCES:
-        with open(os.path.join(ROOT, f), "rb") as fh:
-            h.update(fh.read())
-    return h.hexdigest()
+# DRAM traffic of gemm_tc_kernel per launch on this workload. Counters beyond
+# the launch time are only ever captured on a small case (one kernel, one to
+# three launches, a few GB on the device): the dominant kernel's launches on
+# this workload range from the 8192 x 16384 x 8192 top update down to K = 128,
+# so no small capture scales to "one launch" of this step and the line
+# reports null; the small-case figures (DRAM bytes against the algorithmic
+# bytes of the captured update) are in the profiles/ summary of the kernel.
+TRAFFIC_PER_LAUNCH = None
 
 
 def captured_traffic():
-    if not TRAFFIC_CAPTURE or TRAFFIC_CAPTURE["sources_sha256"] != sources_sha256():
-        return None
-    return TRAFFIC_CAPTURE["bytes_per_launch"]
+    return TRAFFIC_PER_LAUNCH
 
 
 def flops_per_call(k, nrhs):
@@ -258,6 +248,14 @@ def run_gpu(args):
 
     A_np, B_np = host_inputs()
     k, n = K_ORDER, NRHS
+    if args.shard:
+        # strong scaling: this rank's panel of the one problem's right-hand
+        # sides (independent columns, no exchange); the whole job's work is
+        # fixed as the rank count grows
+        from paper_2504_13821_gb300.sharding import panel
+        j0, j1 = panel(NRHS, world, rank)
+        B_np = np.asfortranarray(B_np[:, j0:j1])
+        n = j1 - j0
     colmajor = trx.to_colmajor
     A = colmajor(torch.from_numpy(A_np).to(dev))
     B = colmajor(torch.from_numpy(B_np).to(dev))
@@ -317,7 +315,9 @@ def run_gpu(args):
     ms_total = max_over_ranks(ev0.elapsed_time(ev1), world)
     ms_step = ms_total / args.steps
     flops_step = 2.0 * flops_per_call(k, n)
-    value = world * flops_step * args.steps / (ms_total * 1e-3) / 1e12
+    # whole job: every rank's copy (weak scaling) or the one sharded problem
+    job_flops_step = 2.0 * flops_per_call(k, NRHS) if args.shard else world * flops_step
+    value = job_flops_step * args.steps / (ms_total * 1e-3) / 1e12
 
     # Per-kernel durations: one instrumented step (direct launches with a
     # CUDA event pair around every launch on the call's stream).
@@ -440,13 +440,13 @@ def run_gpu(args):
         torch.cuda.synchronize()
         dts = max_over_ranks(time.perf_counter() - t0, world)
         ok = bool(torch.equal(out_h[0], out_h[1]))    # both slots returned the same result
-        e2e = {"value": world * flops_step * e_steps / dt / 1e12, "unit": "TFLOP/s",
+        e2e = {"value": job_flops_step * e_steps / dt / 1e12, "unit": "TFLOP/s",
                "h2d_bytes_per_step": 2 * nbytes, "d2h_bytes_per_step": nbytes,
                "ms_per_step": 1e3 * dt / e_steps, "steps": e_steps,
                "pipelined": "upload of step i+1 (A and B on two copy streams) and download of "
                             "step i-1 overlap step i",
                "slots_agree": ok,
-               "serial": {"value": world * flops_step * s_steps / dts / 1e12,
+               "serial": {"value": job_flops_step * s_steps / dts / 1e12,
                           "ms_per_step": 1e3 * dts / s_steps, "steps": s_steps}}
         for fc in fac:
             if fc is not None:
@@ -472,9 +472,12 @@ def run_gpu(args):
         line = {
             "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "higher_is_better": True, "scaling": "strong" if args.shard else "weak",
+            "vs_baseline": None,
             "dtype": "f32" if DTYPE == np.float32 else "f64", "data": "synthetic",
-            "config": workload_config(),
+            "config": dict(workload_config(), parallelism=(
+                f"right-hand-side panels over {world} ranks (one problem, no exchange)"
+                if args.shard else f"{world} independent copies, one per rank")),
             "clocks": clk, "gpu_launches": launches_step * args.steps,
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
             "round_trip_drift": drift,
@@ -498,7 +501,8 @@ def run_batched(args):
     from paper_2504_13821_gb300 import inputs
     dev = torch.device("cuda", 0)
     rng = np.random.default_rng(4096)
-    probs, flops = [], 0.0
+    probs, flops, nbytes, fmas = [], 0.0, 0.0, 0.0
+    w = np.dtype(DTYPE).itemsize
     for i in range(args.count):
         k = int(round(np.exp(rng.uniform(np.log(16), np.log(512)))))
         nrhs = int(rng.integers(1, 65))
@@ -510,6 +514,10 @@ def run_batched(args):
         Bt = trx.to_colmajor(torch.from_numpy(B).to(dev))
         probs.append((op, side, uplo, "N", "N", 1.5 if op == "S" else 1 / 1.5, At, Bt))
         flops += float(k) * k * nrhs
+        # algorithmic work per problem: the referenced triangle read once, B
+        # read and written once; k (k + 1) / 2 multiply-adds per right-hand side
+        nbytes += w * (k * (k + 1) / 2.0 + 2.0 * k * nrhs)
+        fmas += k * (k + 1) / 2.0 * nrhs
     h = trx.Handle(dev)
     table = None
     if not args.no_autotune:
@@ -537,6 +545,25 @@ def run_batched(args):
         for (o, s_, u, t, d, a, A, B) in probs:
             (trx.trsm if o == "S" else trx.trmm)(s_, u, t, d, a, A, B, handle=h, stream=stream)
     ms_loop = timed(loop, max(1, min(args.steps, 2)))
+    # the kernel's two ceilings: HBM (measured copy peak) and the CUDA-core
+    # FMA pipe of its element type (the library's own probe, measured here)
+    peaks, src = load_peaks()
+    kind = "ffma" if DTYPE == np.float32 else "dfma"
+    probe_iters = 52905 if kind == "ffma" else 721
+    fma_peak = max(trx.peak_probe(kind, probe_iters)[0] for _ in range(3))
+    gbs = nbytes / (ms_batched * 1e-3) / 1e9
+    tfl = 2.0 * fmas / (ms_batched * 1e-3) / 1e12
+    hbm_frac, fma_frac = gbs / peaks["hbm_gbs"], tfl / fma_peak
+    roofline = {"bound": "hbm" if hbm_frac >= fma_frac else "alu",
+                "kernel": "batched_kernel (one persistent launch)",
+                "achieved": gbs if hbm_frac >= fma_frac else tfl,
+                "peak": peaks["hbm_gbs"] if hbm_frac >= fma_frac else fma_peak,
+                "unit": "GB/s" if hbm_frac >= fma_frac else "TFLOP/s",
+                "frac": max(hbm_frac, fma_frac), "traffic": None,
+                "hbm": {"achieved_gbs": gbs, "peak_gbs": peaks["hbm_gbs"], "frac": hbm_frac,
+                        "algorithmic_bytes": nbytes, "peak_source": src},
+                "fma": {"achieved_tflops": tfl, "peak_tflops": fma_peak, "frac": fma_frac,
+                        "peak_source": f"trx_peak_probe {kind}, measured in this run"}}
     line = {
         "metric": "batched uneven TRSM/TRMM problems/s", "value": args.count / (ms_batched * 1e-3),
         "unit": "problems/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
@@ -549,6 +576,7 @@ def run_batched(args):
                    "autotune": table},
         "loop_of_single_calls": {"ms": ms_loop, "problems_per_s": args.count / (ms_loop * 1e-3)},
         "speedup_vs_loop": ms_loop / ms_batched,
+        "roofline": roofline,
     }
     print(json.dumps(line), flush=True)
     h.close()
@@ -899,6 +927,47 @@ def run_precision(args):
     return 0
 
 
+def run_gemm(args):
+    """The recursion's top-level GEMM update alone (trx_sgemm_update, tensor
+    cores): C := C - A Y with M = K = k / 2 and N = nrhs (the largest update
+    of an order-k TRSM), FP32 data, the handle's split. Times the call (its
+    operand-plane conversions included) with CUDA events; the kernel alone
+    is what a profiler capture of gemm_tc_kernel isolates."""
+    import torch
+    import paper_2504_13821_gb300 as trx
+    dev = torch.device("cuda", 0)
+    h = trx.Handle(dev)
+    if args.split:
+        h.set_option(trx.OPT_SPLIT, args.split)
+    terms = h.get_option(trx.OPT_SPLIT)
+    M = K = K_ORDER // 2
+    N = NRHS
+    g = torch.Generator(device=dev)
+    g.manual_seed(7)
+    A = trx.to_colmajor(torch.rand(M, K, device=dev, generator=g) / K)
+    Y = trx.to_colmajor(torch.randn(K, N, device=dev, generator=g))
+    C = trx.to_colmajor(torch.randn(M, N, device=dev, generator=g))
+    stream = torch.cuda.current_stream(dev)
+    for _ in range(max(args.warmup, 1)):
+        trx.gemm_update(1.0, -1.0, A, Y, C, handle=h, stream=stream)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        trx.gemm_update(1.0, -1.0, A, Y, C, handle=h, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    peaks, src = load_peaks()
+    tflops = 2.0 * M * N * K / (ms * 1e-3) / 1e12
+    print(json.dumps({"workload": "gemm", "M": M, "N": N, "K": K, "split_terms": terms,
+                      "ms": ms, "tflops_with_conversion": tflops,
+                      "peak": peaks["bf16_tflops_sustained"] / terms,
+                      "peak_source": f"{src} bf16 sustained / {terms}"}), flush=True)
+    h.close()
+    return 0
+
+
 def run_peaks(args):
     """Peak rates of the arithmetic units this library's kernels use, with
     its own probes (trx_peak_probe), under the protocol of the outside BF16
@@ -1033,6 +1102,7 @@ def run_serving(args):
     t_arr = t_start
     live = {}             # factor id -> [A, uses left, dtype, k, uplo]
     submitted = 0
+    rejected = 0
     flops = 0.0
     while True:
         t_arr += rng.exponential(1.0 / args.rate)
@@ -1055,6 +1125,14 @@ def run_serving(args):
             live.pop(fid)
         nrhs = int(round(np.exp(rng.uniform(0, np.log(1024)))))
         op = "S" if rng.random() < 0.7 else "M"
+        if submitted - len(done) >= args.max_queue:
+            # overload: the arrival is turned away (its buffers are never
+            # made), so a server that falls behind ends the run with a count
+            # of rejections instead of exhausting device memory
+            rejected += 1
+            if last_use:
+                srv.release(fid)
+            continue
         B = torch.randn(nrhs, k, device=dev, dtype=dtype).t()     # column-major k x nrhs
         refined = op == "S" and dtype == torch.float32 and refine
         X = torch.empty(nrhs, k, device=dev, dtype=torch.float64).t() if refined else None
@@ -1101,7 +1179,8 @@ def run_serving(args):
                                    + ("direct launches" if args.server_direct else
                                       "cached graphs"),
                        "requests": submitted, "offered_tflops": flops / args.duration / 1e12,
-                       "failed": len(failed)},
+                       "failed": len(failed), "rejected_overload": rejected,
+                       "max_queue": args.max_queue},
             "latency": st, "latency_per_kind": per_kind}
     print(json.dumps(line), flush=True)
     srv.close()
@@ -1127,6 +1206,9 @@ def main(argv=None):
     ap.add_argument("--nrhs", type=int, default=None,
                     help="right-hand sides (default 16384, refined workload 256)")
     ap.add_argument("--dtype", default="f32", choices=["f32", "f64"])
+    ap.add_argument("--shard", action="store_true",
+                    help="N > 1: split the one problem's right-hand sides over the ranks "
+                         "(strong scaling) instead of one full copy per rank")
     ap.add_argument("--split", type=int, default=0, choices=[0, 1, 3, 6],
                     help="tensor-core split product terms (0: library default, 6)")
     ap.add_argument("--rate", type=float, default=2000.0, help="serving: arrivals per second")
@@ -1145,7 +1227,7 @@ def main(argv=None):
                     help="precision: also the FP64-level refinement at m = n = 32768")
     ap.add_argument("--workload", default="square",
                     choices=["square", "batched", "serving", "refined", "sweep", "precision",
-                             "peaks"],
+                             "peaks", "gemm"],
                     help="square: the n=16384 TRSM+TRMM step (default); batched: "
                          "4096 small uneven problems in one launch; serving: Poisson "
                          "arrivals; refined: FP32 TRSM refined in FP64 (k 8192, 256 "
@@ -1157,6 +1239,9 @@ def main(argv=None):
                     help="serving: corrections of a refined FP32 TRSM request")
     ap.add_argument("--fp64-corrections", type=int, default=3,
                     help="serving: FP64 TRSM as FP32 solve + this many corrections (0: DFMA)")
+    ap.add_argument("--max-queue", type=int, default=5000,
+                    help="serving: requests submitted and not yet completed beyond which "
+                         "arrivals are rejected")
     ap.add_argument("--no-refine", action="store_true",
                     help="serving: FP32 TRSM requests plain (no refinement)")
     ap.add_argument("--server-workspace-mb", type=int, default=512,
@@ -1183,6 +1268,8 @@ def main(argv=None):
         return run_sweep(args)
     if args.workload == "peaks":
         return run_peaks(args)
+    if args.workload == "gemm":
+        return run_gemm(args)
     if args.workload == "precision":
         if args.sizes == SWEEP_SIZES:
             args.sizes = "8192,16384,32768"

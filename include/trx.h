@@ -47,7 +47,8 @@
  *   the GEMM update alone  trx_sgemm_update
  *   batched problems       trx_batched, trx_{s,d}{trsm,trmm}_batched,
  *                          trx_batch_create / run / destroy,
- *                          trx_batched_autotune
+ *                          trx_batched_autotune, trx_batched_get_tuning /
+ *                          set_tuning
  *   refined FP32 TRSM      trx_strsm_refined (FP64-accurate result),
  *                          trx_strsm_refined_async (fixed corrections)
  *   prepared factors       trx_sfactor_create / update, trx_factor_destroy,
@@ -157,7 +158,7 @@ enum {
                               automatic (default: 6). trx_get_option
                               reads back the terms in use. A prepared
                               factor keeps the split it was created with. */
-    TRX_OPT_FP64_TRSM = 12 /* trx_dtrsm's engine: 0 (default) the recursive
+    TRX_OPT_FP64_TRSM = 12,/* trx_dtrsm's engine: 0 (default) the recursive
                               FP64 solve (CUDA-core DFMA updates); n in
                               1..16: the mixed form, the FP32 solve on
                               fl32(A) then n corrections with the residual
@@ -167,6 +168,20 @@ enum {
                               X accumulated in FP64 (asynchronous, as
                               trx_strsm_refined_async; uses the handle's
                               refinement scratch)                          */
+    TRX_OPT_CHECKED = 13,  /* 1: check every call's launch plan before
+                              enqueueing it (every leaf block, GEMM row and K
+                              range inside the order of A, each update's K
+                              range before its rows, tensor-core K ranges on
+                              whole K steps); a violation returns
+                              TRX_ERR_INVALID_VALUE with the reason in
+                              trx_last_error_detail and enqueues nothing.
+                              trx_debug_plan always checks. 0 (default) off */
+    TRX_OPT_NVTX = 14      /* 1: an NVTX range around each launch step
+                              ("trx leaf ...", "trx gemm ...": kind and row
+                              ranges) for an attached profiler; with graph
+                              replay (TRX_OPT_GRAPH 1) they mark the capture
+                              only, so pair it with TRX_OPT_GRAPH 0 or
+                              TRX_OPT_PROFILE 1. 0 (default) off          */
 };
 
 /* Kernel classes reported by trx_get_profile(). */
@@ -399,15 +414,30 @@ int trx_batch_create(trx_handle_t handle, int elem_bytes, int64_t count,
 int trx_batch_run(trx_handle_t handle, trx_batch_t batch, void* stream);
 int trx_batch_destroy(trx_batch_t batch);
 
-/* Time the batch with each sub-block height (4, 8, 16 rows) per order
- * bucket (k <= 64, 128, 256, 512), keep the fastest per bucket in the
- * handle for later trx_batched calls, and write the table as JSON into
- * json (if not NULL). The problems' B arrays are overwritten (the batch
- * runs several times): tune on representative scratch data. Synchronises
- * the stream. */
+/* Tuning table of the batched kernel: the substitution block height (4, 8
+ * or 16 rows) per order bucket (k <= 64, 128, 256, 512) and right-hand-side
+ * bucket (nrhs <= 8, 24, more), for each element type; 8 everywhere on a new
+ * handle. */
+#define TRX_TUNE_K_BUCKETS 4
+#define TRX_TUNE_N_BUCKETS 3
+
+/* Time the batch with each block height per (order, right-hand-side) bucket,
+ * keep the fastest per bucket in the handle for later batched calls and
+ * prepared batches, and write the table as JSON into json (if not NULL):
+ * {"dtype", "buckets": [{"kmax", "nrhs_max", "problems", "sb", "ms": {"4",
+ * "8", "16"}}, ...]} in order-major bucket order. The problems' B arrays are
+ * overwritten (the batch runs several times): tune on representative
+ * scratch data. Synchronises the stream. */
 int trx_batched_autotune(trx_handle_t handle, int elem_bytes, int64_t count,
                          const trx_problem_t* problems, void* stream,
                          char* json, size_t json_len);
+
+/* Read / replace the handle's tuning table for one element type (count =
+ * TRX_TUNE_K_BUCKETS * TRX_TUNE_N_BUCKETS entries, order-major), e.g. to
+ * persist a tuned table and restore it in a later process. set rejects
+ * entries other than 4, 8, 16 (TRX_ERR_INVALID_VALUE). */
+int trx_batched_get_tuning(trx_handle_t handle, int elem_bytes, int* table, int count);
+int trx_batched_set_tuning(trx_handle_t handle, int elem_bytes, const int* table, int count);
 
 /* ---- serving: continuous batching over resident factors ----------------
  * (The paper has no serving layer; this drives the entry points above.)

@@ -23,6 +23,8 @@ OPT_RESIDUAL = 9
 OPT_TRSM_TC_LEAF = 10
 OPT_SPLIT = 11          # tensor-core split: 1, 3 or 6 product terms (0: automatic, 6)
 OPT_FP64_TRSM = 12      # trx_dtrsm: 0 DFMA recursion; n: FP32 solve + n float-float corrections
+OPT_CHECKED = 13        # 1: validate every launch plan before enqueueing
+OPT_NVTX = 14           # 1: NVTX range per launch step
 RESIDUAL_AUTO, RESIDUAL_FP64, RESIDUAL_FLOAT_FLOAT, RESIDUAL_TC = 0, 1, 2, 3
 GEMM_AUTO, GEMM_SIMT, GEMM_TC = 0, 1, 2
 KERNEL_CLASSES = ("leaf_trsm", "leaf_trmm", "gemm_tc", "gemm_simt", "convert", "other")
@@ -143,6 +145,10 @@ def load_library() -> ctypes.CDLL:
                                            ctypes.POINTER(i64)]
         lib.trx_server_wait.argtypes = [vp]
         lib.trx_version.argtypes = []
+        lib.trx_batched_get_tuning.argtypes = [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                               ctypes.c_int]
+        lib.trx_batched_set_tuning.argtypes = [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                               ctypes.c_int]
         lib.trx_peak_probe.argtypes = [ctypes.c_int, ctypes.c_int, i64,
                                        ctypes.POINTER(ctypes.c_double),
                                        ctypes.POINTER(ctypes.c_double)]
@@ -248,6 +254,11 @@ def default_handle(device=None) -> Handle:
     h = _handles.get(idx)
     if h is None:
         h = _handles[idx] = Handle(idx)
+        # a persisted batched tuning table (save_tuning) named by the
+        # environment is loaded into every default handle
+        path = os.environ.get("TRX_TUNING_FILE")
+        if path:
+            load_tuning(path, handle=h)
     return h
 
 
@@ -616,10 +627,42 @@ def batched_autotune(problems, *, handle: Handle | None = None, stream=None) -> 
     if stream is None:
         stream = torch.cuda.current_stream(dev)
     s_ptr = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
-    buf = ctypes.create_string_buffer(4096)
+    buf = ctypes.create_string_buffer(16384)
     _check(lib.trx_batched_autotune(h.ptr, elem, len(problems), arr, s_ptr, buf, len(buf)),
            "trx_batched_autotune")
     return json.loads(buf.value.decode())
+
+
+TUNE_ENTRIES = 4 * 3      # TRX_TUNE_K_BUCKETS * TRX_TUNE_N_BUCKETS
+
+
+def save_tuning(path: str, *, handle: Handle | None = None):
+    """Write the handle's batched tuning tables (both element types) as JSON."""
+    import json
+    lib = load_library()
+    h = handle if handle is not None else default_handle()
+    out = {}
+    for name, elem in (("f32", 4), ("f64", 8)):
+        t = (ctypes.c_int * TUNE_ENTRIES)()
+        _check(lib.trx_batched_get_tuning(h.ptr, elem, t, TUNE_ENTRIES), "trx_batched_get_tuning")
+        out[name] = list(t)
+    out["layout"] = "order buckets k<=64,128,256,512 x right-hand-side buckets <=8,24,more"
+    with open(path, "w") as f:
+        json.dump(out, f, indent=1)
+
+
+def load_tuning(path: str, *, handle: Handle | None = None):
+    """Restore tables written by save_tuning into the handle."""
+    import json
+    lib = load_library()
+    h = handle if handle is not None else default_handle()
+    with open(path) as f:
+        d = json.load(f)
+    for name, elem in (("f32", 4), ("f64", 8)):
+        if name in d:
+            t = (ctypes.c_int * TUNE_ENTRIES)(*d[name])
+            _check(lib.trx_batched_set_tuning(h.ptr, elem, t, TUNE_ENTRIES),
+                   "trx_batched_set_tuning")
 
 
 PEAK_KINDS = {"ffma": 0, "dfma": 1, "dmma": 2, "tc_tf32": 3, "tc_bf16": 4}

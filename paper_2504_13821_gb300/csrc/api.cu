@@ -16,6 +16,8 @@
 #include <new>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "common.cuh"
 #include "plan.cuh"
 #include "trx.h"
@@ -176,6 +178,8 @@ struct trx_handle_s {
     int64_t opt_leaf = 0, opt_gemm = 0, opt_graph = 1, opt_profile = 0, opt_pdl = 0;
     int64_t opt_split = 0;   // product terms of the tensor-core split (0: automatic)
     int64_t opt_fp64_trsm = 0;   // FP64 TRSM: 0 DFMA; n > 0 FP32 solve + n corrections
+    int64_t opt_checked = 0;     // validate every plan before enqueueing it
+    int64_t opt_nvtx = 0;        // an NVTX range around every launch step
     long long wait_ns = kDefaultWaitNs;
     int* d_err = nullptr;
     cudaStream_t cap_stream = nullptr;
@@ -201,7 +205,9 @@ struct trx_handle_s {
     BatchDesc* b_host = nullptr;
     int64_t b_cap = 0;
     cudaEvent_t b_uploaded = nullptr;
-    int tune_sb[2][4] = {{8, 8, 8, 8}, {8, 8, 8, 8}};   // autotuned on GB300: 8 everywhere
+    // batched substitution block height per [element type][order bucket]
+    // [right-hand-side bucket] (trx_batched_autotune); 8 until tuned
+    int tune_sb[2][TRX_TUNE_K_BUCKETS][TRX_TUNE_N_BUCKETS] = {};
     // column-panel branches of a TRSM: streams and fork/join events
     int64_t opt_panels = 0;
     int64_t opt_trmm_dense = 0;
@@ -254,12 +260,36 @@ struct Exec {
     cudaStream_t s;
     bool profile;
 
+    // NVTX range name of a step (TRX_OPT_NVTX): kind and its row ranges
+    static void nvtx_push(const Step& st) {
+        char name[128];
+        switch (st.kind) {
+            case kLeaf:
+                snprintf(name, sizeof(name), "trx leaf %s rows %lld+%dx%lld",
+                         st.trsm ? "trsm" : "trmm", (long long)st.r0, st.b,
+                         (long long)st.nleaves);
+                break;
+            case kGemm:
+                snprintf(name, sizeof(name), "trx gemm%s x%zu rows %lld+%lld K %lld",
+                         st.tc ? " tc" : "", st.gemms.size(),
+                         (long long)(st.gemms.empty() ? 0 : st.gemms[0].rc),
+                         (long long)(st.gemms.empty() ? 0 : st.gemms[0].mlen),
+                         (long long)(st.gemms.empty() ? 0 : st.gemms[0].klen));
+                break;
+            default:
+                snprintf(name, sizeof(name), "trx planes");
+                break;
+        }
+        nvtxRangePushA(name);
+    }
+
     int run(const Plan& plan) {
         for (const Step& st : plan.steps) {
             int cls = TRX_KERNEL_OTHER;
             double flops = 0, bytes = 0;
             const double w = sizeof(T);
             cudaEvent_t e0 = nullptr, e1 = nullptr;
+            if (h->opt_nvtx) nvtx_push(st);
             if (profile) {
                 e0 = get_event(h);
                 e1 = get_event(h);
@@ -337,6 +367,7 @@ struct Exec {
                     bytes = 4.0 * c.k * st.b * 1.5;
                     break;
             }
+            if (h->opt_nvtx) nvtxRangePop();
             if (e != cudaSuccess) return fail_cuda(e, "kernel launch");
             if (profile) {
                 cudaEventRecord(e1, s);
@@ -517,6 +548,12 @@ int execute(trx_handle_t h, bool trsm, char side, char uplo, char transa, char d
         }
     }
     make_plan(body, trsm, k, b, (double)alpha, /*conv_m=*/false, dense);
+    if (h->opt_checked) {
+        if (const char* why = validate_plan(body, k)) {
+            snprintf(g_detail, sizeof(g_detail), "checked plan: %s", why);
+            return TRX_ERR_INVALID_VALUE;
+        }
+    }
 
     // The whole call on stream st: prelude, then the panels (forked when P > 1).
     auto run_all = [&](cudaStream_t st) -> int {
@@ -677,6 +714,8 @@ void drop_graphs(trx_handle_t h) {
 }
 
 int bucket_of(int64_t k) { return k <= 64 ? 0 : k <= 128 ? 1 : k <= 256 ? 2 : 3; }
+int nbucket_of(int64_t nrhs) { return nrhs <= 8 ? 0 : nrhs <= 24 ? 1 : 2; }
+int tune_index(int64_t k, int64_t nrhs) { return bucket_of(k) * TRX_TUNE_N_BUCKETS + nbucket_of(nrhs); }
 
 // Validate and map the problems to sorted canonical descriptors (host).
 int batch_descs(trx_handle_t h, int elem_bytes, int64_t count, const trx_problem_t* probs,
@@ -717,8 +756,9 @@ int batch_descs(trx_handle_t h, int elem_bytes, int64_t count, const trx_problem
         }
         d.alpha = q.alpha;
         d.trsm = q.alpha == 0.0 ? 2 : (op == 'S' ? 1 : 0);   // 2: B := 0, A not read
-        const int b = bucket_of(d.k);
-        d.sb = sb_override ? sb_override[b] : h->tune_sb[elem_bytes == 4 ? 0 : 1][b];
+        const int b = tune_index(d.k, d.nrhs);
+        d.sb = sb_override ? sb_override[b]
+                           : (&h->tune_sb[elem_bytes == 4 ? 0 : 1][0][0])[b];
         out.push_back(d);
     }
     std::stable_sort(out.begin(), out.end(), [](const BatchDesc& x, const BatchDesc& y) {
@@ -955,19 +995,28 @@ int trx_batched_autotune(trx_handle_t h, int elem_bytes, int64_t count,
     cudaError_t e = cudaSetDevice(h->device);
     if (e != cudaSuccess) return fail_cuda(e, "cudaSetDevice");
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    constexpr int NB = TRX_TUNE_K_BUCKETS * TRX_TUNE_N_BUCKETS;
     const int sbs[3] = {4, 8, 16};
-    double best_ms[4] = {1e30, 1e30, 1e30, 1e30}, all_ms[4][3];
-    int best[4] = {16, 16, 16, 16};
+    double best_ms[NB], all_ms[NB][3];
+    int best[NB], count_b[NB];
+    const int t = elem_bytes == 4 ? 0 : 1;
+    for (int b = 0; b < NB; ++b) {
+        best_ms[b] = 1e30;
+        best[b] = (&h->tune_sb[t][0][0])[b];
+        count_b[b] = 0;
+    }
     cudaEvent_t e0 = get_event(h), e1 = get_event(h);
-    for (int bkt = 0; bkt < 4; ++bkt) {
+    for (int bkt = 0; bkt < NB; ++bkt) {
         for (int v = 0; v < 3; ++v) {
-            int ov[4] = {sbs[v], sbs[v], sbs[v], sbs[v]};
+            int ov[NB];
+            for (int b = 0; b < NB; ++b) ov[b] = sbs[v];
             std::vector<BatchDesc> all, mine;
             int rc = batch_descs(h, elem_bytes, count, problems, all, ov);
             if (rc != TRX_SUCCESS) return rc;
             for (auto& x : all)
-                if (bucket_of(x.k) == bkt) mine.push_back(x);
+                if (tune_index(x.k, x.nrhs) == bkt) mine.push_back(x);
             all_ms[bkt][v] = 0.0;
+            count_b[bkt] = (int)mine.size();
             if (mine.empty()) continue;
             double ms_sum = 0.0;
             for (int rep = 0; rep < 4; ++rep) {
@@ -989,24 +1038,47 @@ int trx_batched_autotune(trx_handle_t h, int elem_bytes, int64_t count,
     }
     h->free_events.push_back(e0);
     h->free_events.push_back(e1);
-    const int t = elem_bytes == 4 ? 0 : 1;
-    for (int bkt = 0; bkt < 4; ++bkt) h->tune_sb[t][bkt] = best[bkt];
+    for (int b = 0; b < NB; ++b) (&h->tune_sb[t][0][0])[b] = best[b];
     drop_graphs(h);
     if (json && json_len) {
         std::string out = std::string("{\"dtype\": \"") + (t ? "f64" : "f32") + "\", \"buckets\": [";
         const int kmax[4] = {64, 128, 256, 512};
-        char buf[256];
-        for (int bkt = 0; bkt < 4; ++bkt) {
+        const int nmax[3] = {8, 24, 64};
+        char buf[320];
+        for (int b = 0; b < NB; ++b) {
             snprintf(buf, sizeof(buf),
-                     "%s{\"kmax\": %d, \"sb\": %d, \"ms\": {\"4\": %.5f, \"8\": %.5f, \"16\": %.5f}}",
-                     bkt ? ", " : "", kmax[bkt], best[bkt], all_ms[bkt][0], all_ms[bkt][1],
-                     all_ms[bkt][2]);
+                     "%s{\"kmax\": %d, \"nrhs_max\": %d, \"problems\": %d, \"sb\": %d, "
+                     "\"ms\": {\"4\": %.5f, \"8\": %.5f, \"16\": %.5f}}",
+                     b ? ", " : "", kmax[b / TRX_TUNE_N_BUCKETS],
+                     nmax[b % TRX_TUNE_N_BUCKETS], count_b[b], best[b], all_ms[b][0],
+                     all_ms[b][1], all_ms[b][2]);
             out += buf;
         }
         out += "]}";
         if (out.size() + 1 > json_len) return TRX_ERR_INVALID_VALUE;
         std::memcpy(json, out.c_str(), out.size() + 1);
     }
+    return TRX_SUCCESS;
+}
+
+int trx_batched_get_tuning(trx_handle_t h, int elem_bytes, int* table, int count) {
+    if (!valid(h)) return TRX_ERR_HANDLE;
+    if ((elem_bytes != 4 && elem_bytes != 8) || !table ||
+        count != TRX_TUNE_K_BUCKETS * TRX_TUNE_N_BUCKETS)
+        return TRX_ERR_INVALID_VALUE;
+    std::memcpy(table, &h->tune_sb[elem_bytes == 4 ? 0 : 1][0][0], sizeof(int) * count);
+    return TRX_SUCCESS;
+}
+
+int trx_batched_set_tuning(trx_handle_t h, int elem_bytes, const int* table, int count) {
+    if (!valid(h)) return TRX_ERR_HANDLE;
+    if ((elem_bytes != 4 && elem_bytes != 8) || !table ||
+        count != TRX_TUNE_K_BUCKETS * TRX_TUNE_N_BUCKETS)
+        return TRX_ERR_INVALID_VALUE;
+    for (int i = 0; i < count; ++i)
+        if (table[i] != 4 && table[i] != 8 && table[i] != 16) return TRX_ERR_INVALID_VALUE;
+    std::memcpy(&h->tune_sb[elem_bytes == 4 ? 0 : 1][0][0], table, sizeof(int) * count);
+    drop_graphs(h);
     return TRX_SUCCESS;
 }
 
@@ -1031,6 +1103,9 @@ int trx_create(trx_handle_t* handle, int device, size_t workspace_bytes) {
     if (!h) return TRX_ERR_ALLOC;
     h->device = device;
     h->num_sms = prop.multiProcessorCount;
+    for (int t = 0; t < 2; ++t)
+        for (int b = 0; b < TRX_TUNE_K_BUCKETS; ++b)
+            for (int c = 0; c < TRX_TUNE_N_BUCKETS; ++c) h->tune_sb[t][b][c] = 8;
     if ((e = cudaMalloc(&h->d_err, 256)) != cudaSuccess ||
         (e = cudaMemset(h->d_err, 0, 256)) != cudaSuccess ||
         (e = cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking)) != cudaSuccess ||
@@ -1399,6 +1474,15 @@ int refine_fixed(trx_handle_t h, bool fp64_data, char side, char uplo, char tran
     const size_t need = 3 * mn64 + mn32 + a32 + ap + xp + ub + pb;
     int rc = refine_scratch(h, need, s);
     if (rc != TRX_SUCCESS) return rc;
+    // The solves launch directly: their graph key would hold this call's
+    // right-hand-side count, so a server's stream of differently shaped
+    // requests would capture and instantiate a new graph every time.
+    struct GraphOff {
+        trx_handle_t h;
+        int64_t saved;
+        ~GraphOff() { h->opt_graph = saved; }
+    } graph_off{h, h->opt_graph};
+    h->opt_graph = 0;
     char* base = static_cast<char*>(h->rf_buf);
     double* Xi = reinterpret_cast<double*>(base);
     double* B64 = reinterpret_cast<double*>(base + mn64);
@@ -1755,6 +1839,14 @@ int trx_set_option(trx_handle_t h, int option, int64_t value) {
             if (value < 0 || value > 16) return TRX_ERR_INVALID_VALUE;
             h->opt_fp64_trsm = value;
             break;
+        case TRX_OPT_CHECKED:
+            if (value != 0 && value != 1) return TRX_ERR_INVALID_VALUE;
+            h->opt_checked = value;
+            break;
+        case TRX_OPT_NVTX:
+            if (value != 0 && value != 1) return TRX_ERR_INVALID_VALUE;
+            h->opt_nvtx = value;
+            break;
         default:
             return TRX_ERR_INVALID_VALUE;
     }
@@ -1777,6 +1869,8 @@ int trx_get_option(trx_handle_t h, int option, int64_t* value) {
         case TRX_OPT_TRSM_TC_LEAF: *value = h->opt_trsm_tc_leaf; break;
         case TRX_OPT_SPLIT: *value = split_terms(h->opt_split); break;
         case TRX_OPT_FP64_TRSM: *value = h->opt_fp64_trsm; break;
+        case TRX_OPT_CHECKED: *value = h->opt_checked; break;
+        case TRX_OPT_NVTX: *value = h->opt_nvtx; break;
         default: return TRX_ERR_INVALID_VALUE;
     }
     return TRX_SUCCESS;
@@ -1866,6 +1960,10 @@ int trx_debug_plan(char op, char side, char uplo, char transa, char diag, int64_
     plan.tc_leaf = is_trsm && elem_bytes == 4 && tc_leaf_mode(trsm_tc_leaf, plan.tc, b);
     const int dense = is_trsm ? 0 : trmm_dense_mode(trmm_dense, leaf, plan.tc, k);
     make_plan(plan, is_trsm, k, b, 2.0, true, dense);
+    if (const char* why = validate_plan(plan, k)) {
+        snprintf(g_detail, sizeof(g_detail), "plan check: %s", why);
+        return TRX_ERR_INVALID_VALUE;
+    }
     std::string out;
     char line[256];
     for (const Step& st : plan.steps) {

@@ -238,6 +238,55 @@ inline void make_plan(Plan& plan, bool trsm, int64_t k, int b, double alpha, boo
     }
 }
 
+// Structural check of a plan against the problem (the checked mode,
+// TRX_OPT_CHECKED, and every host plan dump): every leaf block and every
+// GEMM row and K range lies inside [0, k) (a tensor-core K range may run
+// into the zero-filled rest of its last K step); an off-diagonal update reads a
+// K range that ends at or before its rows (the recursion's disjoint blocks),
+// a dense diagonal-block tile reads from its block's first row up to its own
+// rows; tensor-core updates have K a multiple of the 32-element K step and
+// start on an 8-element boundary; plane windows lie inside [0, k). Returns
+// nullptr, or a description of the first violation.
+inline const char* validate_plan(const Plan& plan, int64_t k) {
+    for (const Step& st : plan.steps) {
+        switch (st.kind) {
+            case kLeaf:
+                if (st.b < 1 || st.nleaves < 1 || st.r0 < 0 || st.r0 >= k ||
+                    st.r0 + (int64_t)st.b * (st.nleaves - 1) >= k)
+                    return "leaf block outside the triangle";
+                break;
+            case kConvYRows:
+                if (st.r0 < 0 || st.b < 1 || st.r0 + st.b > k) return "plane rows outside [0, k)";
+                break;
+            case kGemm:
+                if (st.y0 < 0 || st.y1 < st.y0 || st.y1 > k) return "plane window outside [0, k)";
+                for (const TcGemm& g : st.gemms) {
+                    // a tensor-core K range may end past k inside its last
+                    // 32-element step: the operand loads fill zeros there
+                    const int64_t kend = st.tc ? round_up(k, 32) : k;
+                    if (g.rc < 0 || g.mlen < 1 || g.rc + g.mlen > k || g.rk < 0 || g.klen < 1 ||
+                        g.rk + g.klen > kend)
+                        return "GEMM block outside the triangle";
+                    if (st.dense) {
+                        if (g.rk > g.rc || g.rc + g.mlen > g.rk + g.klen + 31)
+                            return "dense diagonal tile reads outside its block";
+                    } else if (st.inv) {
+                        if (g.rk != g.rc || g.klen != g.mlen)
+                            return "inverse leaf GEMM not square on its rows";
+                    } else if (g.rk + g.klen > g.rc) {
+                        return "update reads rows it writes";
+                    }
+                    if (st.tc && (g.klen % 32 != 0 || g.rk % 8 != 0))
+                        return "tensor-core K range not a multiple of the K step";
+                }
+                break;
+            default:
+                break;
+        }
+    }
+    return nullptr;
+}
+
 // Rows of the dense TRMM diagonal blocks: the handle's TRX_OPT_TRMM_DENSE
 // (-1 off, else the size), or automatically 1024 once the order reaches 1024
 // and the leaf size was left automatic. Tensor-core path only.

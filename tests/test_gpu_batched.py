@@ -63,8 +63,25 @@ def test_batched_graph_replay_and_autotune():
     h = trx.Handle(0)
     probs, host = make_batch(120, np.float32, seed=8, dev=dev)
     table = trx.batched_autotune(probs, handle=h)     # clobbers B
-    assert [b["kmax"] for b in table["buckets"]] == [64, 128, 256, 512]
+    assert [b["kmax"] for b in table["buckets"]] == [k for k in (64, 128, 256, 512)
+                                                     for _ in range(3)]
+    assert [b["nrhs_max"] for b in table["buckets"]] == [8, 24, 64] * 4
     assert all(b["sb"] in (4, 8, 16) for b in table["buckets"])
+    assert sum(b["problems"] for b in table["buckets"]) == len(probs)
+    # the table persists and restores (another handle, same results bitwise)
+    import tempfile
+    with tempfile.TemporaryDirectory() as d:
+        path = d + "/tuning.json"
+        _binding_save = trx._binding.save_tuning
+        _binding_save(path, handle=h)
+        h2 = trx.Handle(0)
+        trx._binding.load_tuning(path, handle=h2)
+        for (_, _, _, _, _, _, _, Bt), (_, B) in zip(probs, host):
+            Bt.copy_(torch.from_numpy(np.asfortranarray(B)))
+        trx.batched(probs, handle=h2)
+        torch.cuda.synchronize()
+        via_loaded = [p[7].cpu().clone() for p in probs]
+        h2.close()
     outs = []
     for _ in range(2):                               # second call replays the cached graph
         for (_, _, _, _, _, _, _, Bt), (_, B) in zip(probs, host):
@@ -74,6 +91,7 @@ def test_batched_graph_replay_and_autotune():
         check(probs, host, np.float32)
         outs.append([p[7].cpu().clone() for p in probs])
     assert all(torch.equal(a, b) for a, b in zip(*outs))
+    assert all(torch.equal(a, b) for a, b in zip(outs[0], via_loaded))
     h.close()
 
 

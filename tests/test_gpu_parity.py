@@ -349,3 +349,17 @@ def test_trsm_tensor_core_leaves_factor_equals_plain(trx):
     Ak = np.asfortranarray(A[:k, :k])
     eta = oracle.trsm_backward_error("L", "U", "T", "N", 2.0, Ak, out["trsm"], B)["eta"]
     assert eta <= bound(k, np.float32), eta
+
+
+@pytest.mark.parametrize("op", ["trsm", "trmm"])
+def test_checked_plans_and_nvtx_ranges(trx, op):
+    """TRX_OPT_CHECKED validates every launch plan before enqueueing it and
+    TRX_OPT_NVTX wraps each launch step in an NVTX range (direct launches):
+    results unchanged, parity holds."""
+    h = trx.Handle(0)
+    h.set_option(trx.OPT_CHECKED, 1)
+    h.set_option(trx.OPT_NVTX, 1)
+    h.set_option(trx.OPT_GRAPH, 0)
+    for variant, (m, n) in ((("L", "L", "N", "N"), (1100, 300)), (("R", "U", "T", "U"), (90, 700))):
+        run_case(op, *variant, m, n, 1.5, np.float32, seed=m + n, handle=h)
+    h.close()

@@ -78,8 +78,30 @@ def _rank_main(rank, world, port, outdir):
             p = parts[r].numpy()
             pieces.append(p[:, :a1 - a0] if side == "L" else p[:a1 - a0, :])
         out[side] = np.concatenate(pieces, axis=1 if side == "L" else 0)
+    # the same partition through the library's own host plan: each rank
+    # replays (FP64, on the host) the launch sequence the library would
+    # enqueue for its panel of a side-L TRSM and TRMM on the tensor-core
+    # path, and the gathered panels match the oracle's single-rank result
+    from test_plan_host import replay
+    from paper_2504_13821_gb300 import debug_plan
+    k, nr = 300, 257
+    A, B = inputs.problem("L", "L", k, nr, seed=78, dtype=np.float64)
+    M = np.where(np.isnan(A), 0.0, A)
+    j0, j1 = panel(nr, world, rank)
+    width = panel(nr, world, 0)[1]
+    for op in ("S", "M"):
+        pad = np.zeros((k, width))
+        if j1 > j0:
+            steps = debug_plan(op, "L", "L", "N", "N", k, j1 - j0, 4, 0, 2)
+            pad[:, :j1 - j0] = replay(op, steps, M, B[:, j0:j1])
+        parts = [torch.zeros(pad.shape, dtype=torch.float64) for _ in range(world)]
+        dist.all_gather(parts, torch.from_numpy(pad))
+        out["plan_" + op] = np.concatenate(
+            [parts[r].numpy()[:, :panel(nr, world, r)[1] - panel(nr, world, r)[0]]
+             for r in range(world)], axis=1)
     dist.destroy_process_group()
-    np.savez(os.path.join(outdir, f"rank{rank}.npz"), maxv=got, L=out["L"], R=out["R"])
+    np.savez(os.path.join(outdir, f"rank{rank}.npz"), maxv=got, L=out["L"], R=out["R"],
+             plan_S=out["plan_S"], plan_M=out["plan_M"])
 
 
 def test_two_gloo_ranks_reproduce_single_rank(tmp_path):
@@ -97,3 +119,8 @@ def test_two_gloo_ranks_reproduce_single_rank(tmp_path):
             A, B = inputs.problem(side, "U", m, n, seed=77, dtype=np.float64)
             want = oracle.trsm(side, "U", "T", "N", 1.5, A, B)
             np.testing.assert_array_equal(d[side], want)
+        A, B = inputs.problem("L", "L", 300, 257, seed=78, dtype=np.float64)
+        for op, fn in (("S", oracle.trsm), ("M", oracle.trmm)):
+            want = fn("L", "L", "N", "N", 2.0, A, B)     # the plan dump's alpha
+            np.testing.assert_allclose(d["plan_" + op], want, rtol=1e-10,
+                                       atol=1e-10 * np.abs(want).max())
