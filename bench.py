@@ -262,6 +262,8 @@ def run_gpu(args):
     h = trx.Handle(dev)
     if args.split:
         h.set_option(trx.OPT_SPLIT, args.split)
+    if args.dag:
+        h.set_option(trx.OPT_TRSM_DAG, args.dag)
     global SPLIT_TERMS
     SPLIT_TERMS = h.get_option(trx.OPT_SPLIT)
     if args.pdl:
@@ -544,7 +546,7 @@ def run_batched(args):
     def loop():
         for (o, s_, u, t, d, a, A, B) in probs:
             (trx.trsm if o == "S" else trx.trmm)(s_, u, t, d, a, A, B, handle=h, stream=stream)
-    ms_loop = timed(loop, max(1, min(args.steps, 2)))
+    ms_loop = None if args.no_loop else timed(loop, max(1, min(args.steps, 2)))
     # the kernel's two ceilings: HBM (measured copy peak) and the CUDA-core
     # FMA pipe of its element type (the library's own probe, measured here)
     peaks, src = load_peaks()
@@ -574,8 +576,9 @@ def run_batched(args):
                                "right-hand sides, random side/uplo, TRSM/TRMM alternating",
                    "tflops_m2n": flops / (ms_batched * 1e-3) / 1e12,
                    "autotune": table},
-        "loop_of_single_calls": {"ms": ms_loop, "problems_per_s": args.count / (ms_loop * 1e-3)},
-        "speedup_vs_loop": ms_loop / ms_batched,
+        "loop_of_single_calls": None if ms_loop is None else {
+            "ms": ms_loop, "problems_per_s": args.count / (ms_loop * 1e-3)},
+        "speedup_vs_loop": None if ms_loop is None else ms_loop / ms_batched,
         "roofline": roofline,
     }
     print(json.dumps(line), flush=True)
@@ -684,7 +687,7 @@ def run_sweep(args):
     B restored from a pristine copy before each call, outside the timed
     pair), TFLOP/s (m^2 n), and the errors against the FP64 oracle: for
     orders up to 4096 the whole result (TRSM backward error and forward
-    error, TRMM normwise error), above that a seeded sample of right-hand
+    error, TRMM normwise error) up to order 2048, above that a seeded sample of right-hand
     sides (columns for side L, rows for side R; each is an independent
     problem), with the oracle's time on the sample. A last line sums it up."""
     import torch
@@ -711,9 +714,9 @@ def run_sweep(args):
             seed = inputs.variant_seed(k, vi)
             A64, B64 = inputs.problem(side, uplo, k, k, seed=seed, dtype=np.float64,
                                       poison_diag=(diag == "U"))
-            full = k <= 4096
+            full = k <= 2048
             rng = np.random.default_rng(seed + 17)
-            nsamp = 16 if k >= 16384 else 32
+            nsamp = 16 if k >= 16384 else 32 if k >= 8192 else 64
             samp = None if full else np.sort(rng.choice(k, size=nsamp, replace=False))
             for dt in dtypes:
                 npdt = np.float32 if dt == "f32" else np.float64
@@ -1206,6 +1209,8 @@ def main(argv=None):
     ap.add_argument("--nrhs", type=int, default=None,
                     help="right-hand sides (default 16384, refined workload 256)")
     ap.add_argument("--dtype", default="f32", choices=["f32", "f64"])
+    ap.add_argument("--dag", type=int, default=0, choices=[-1, 0, 1],
+                    help="FP32 TRSM: 1 device-scheduled solve, -1 recursive chain, 0 library default")
     ap.add_argument("--shard", action="store_true",
                     help="N > 1: split the one problem's right-hand sides over the ranks "
                          "(strong scaling) instead of one full copy per rank")
@@ -1248,6 +1253,8 @@ def main(argv=None):
                     help="serving: per-stream workspace made when the server starts")
     ap.add_argument("--kappa", type=float, default=None,
                     help="refined workload: only the factor of this target condition number")
+    ap.add_argument("--no-loop", action="store_true",
+                    help="batched workload: skip the loop of single calls (profiling runs)")
     ap.add_argument("--no-autotune", action="store_true",
                     help="batched workload: keep the default block sizes (for profiling runs)")
     args = ap.parse_args(argv)

@@ -176,12 +176,26 @@ enum {
                               TRX_ERR_INVALID_VALUE with the reason in
                               trx_last_error_detail and enqueues nothing.
                               trx_debug_plan always checks. 0 (default) off */
-    TRX_OPT_NVTX = 14      /* 1: an NVTX range around each launch step
+    TRX_OPT_NVTX = 14,     /* 1: an NVTX range around each launch step
                               ("trx leaf ...", "trx gemm ...": kind and row
                               ranges) for an attached profiler; with graph
                               replay (TRX_OPT_GRAPH 1) they mark the capture
                               only, so pair it with TRX_OPT_GRAPH 0 or
                               TRX_OPT_PROFILE 1. 0 (default) off          */
+    TRX_OPT_TRSM_DAG = 15  /* FP32 TRSM on the tensor-core path with the
+                              order a multiple of 128 (at least 256): 1 =
+                              one persistent device-scheduled launch in place
+                              of the recursion's launch chain (128-row blocks
+                              x 64-column panels taken in order from a
+                              counter; a block's off-diagonal products start
+                              as soon as the blocks it needs are published,
+                              its diagonal solve is a product with the
+                              block's inverse, made once per call; bounded
+                              waits); -1 = the recursive chain; 0 =
+                              automatic (default: the device-scheduled solve
+                              with at most 1024 right-hand sides). Needs the
+                              workspace trx_workspace_size reports (planes
+                              + inverses + flags)                         */
 };
 
 /* Kernel classes reported by trx_get_profile(). */

@@ -25,6 +25,7 @@ OPT_SPLIT = 11          # tensor-core split: 1, 3 or 6 product terms (0: automat
 OPT_FP64_TRSM = 12      # trx_dtrsm: 0 DFMA recursion; n: FP32 solve + n float-float corrections
 OPT_CHECKED = 13        # 1: validate every launch plan before enqueueing
 OPT_NVTX = 14           # 1: NVTX range per launch step
+OPT_TRSM_DAG = 15       # FP32 TRSM: 1 device-scheduled, -1 recursive chain, 0 automatic
 RESIDUAL_AUTO, RESIDUAL_FP64, RESIDUAL_FLOAT_FLOAT, RESIDUAL_TC = 0, 1, 2, 3
 GEMM_AUTO, GEMM_SIMT, GEMM_TC = 0, 1, 2
 KERNEL_CLASSES = ("leaf_trsm", "leaf_trmm", "gemm_tc", "gemm_simt", "convert", "other")

@@ -154,6 +154,14 @@ WsLayout ws_layout(int64_t k, int64_t nrhs, int slices) {
     return w;
 }
 
+// Extra workspace of the device-scheduled TRSM after the planes: the
+// diagonal blocks' inverses as `slices` compact k x 128 planes, then the
+// block flags and the task counter.
+size_t dag_extra_bytes(int64_t k, int64_t nrhs, int slices) {
+    return (size_t)slices * align256((size_t)k * kDagBlock * 2) +
+           align256(dag_flag_bytes(k, nrhs));
+}
+
 // Plane pointers of a workspace laid out as above (M planes from m_base
 // unless the caller supplies them, Y planes from y_base).
 void set_m_planes(Planes& pl, char* m_base, size_t m_bytes, int slices) {
@@ -179,6 +187,7 @@ struct trx_handle_s {
     int64_t opt_split = 0;   // product terms of the tensor-core split (0: automatic)
     int64_t opt_fp64_trsm = 0;   // FP64 TRSM: 0 DFMA; n > 0 FP32 solve + n corrections
     int64_t opt_checked = 0;     // validate every plan before enqueueing it
+    int64_t opt_trsm_dag = 0;    // device-scheduled TRSM: -1 off, 0 automatic, 1 on
     int64_t opt_nvtx = 0;        // an NVTX range around every launch step
     long long wait_ns = kDefaultWaitNs;
     int* d_err = nullptr;
@@ -257,6 +266,7 @@ struct Exec {
     __nv_bfloat16* w_hi = nullptr;
     __nv_bfloat16* w_lo = nullptr;
     __nv_bfloat16* w_lo2 = nullptr;
+    int* dag_flags = nullptr;      // device-scheduled TRSM: block flags + task counter
     cudaStream_t s;
     bool profile;
 
@@ -366,6 +376,22 @@ struct Exec {
                     cls = TRX_KERNEL_CONVERT;
                     bytes = 4.0 * c.k * st.b * 1.5;
                     break;
+                case kInvCompact:
+                    e = launch_invert_diag(*reinterpret_cast<const Canon<float>*>(&c), st.b, w_hi,
+                                           w_lo, w_lo2, pl.slices, st.b, s, true);
+                    cls = TRX_KERNEL_CONVERT;
+                    bytes = 4.0 * c.k * st.b * 1.5;
+                    break;
+                case kDag: {
+                    __nv_bfloat16* const w3[3] = {w_hi, w_lo, w_lo2};
+                    e = launch_trsm_dag(*reinterpret_cast<const Canon<float>*>(&c), pl, w3,
+                                        (float)st.alpha, dag_flags, h->d_err, h->wait_ns,
+                                        h->num_sms, s);
+                    cls = TRX_KERNEL_GEMM_TC;
+                    flops = (double)c.k * c.k * c.nrhs;
+                    bytes = 4.0 * ((double)c.k * (c.k + 1) / 2 + 2.0 * c.k * c.nrhs);
+                    break;
+                }
             }
             if (h->opt_nvtx) nvtxRangePop();
             if (e != cudaSuccess) return fail_cuda(e, "kernel launch");
@@ -379,7 +405,7 @@ struct Exec {
 };
 
 struct GraphKey {
-    int op, elem, tc, b, slices;
+    int op, elem, tc, b, slices, dag;
     int64_t k, nrhs, a_rs, a_cs, c_rs, c_cs, unit;
     const void* A;
     const void* C;
@@ -460,9 +486,12 @@ int execute(trx_handle_t h, bool trsm, char side, char uplo, char transa, char d
     const bool factor_planes = plan.tc && f != nullptr && f->m_hi != nullptr;
     const int slices = factor_planes ? f->slices
                        : terms_override ? slices_of_terms(terms_override) : slices_for(h);
+    const bool dag = std::is_same<T, float>::value &&
+                     use_dag_mode(h->opt_trsm_dag, plan.tc, trsm, (int)sizeof(T), k, ex.c.nrhs);
     if (plan.tc) {
         const WsLayout w = ws_layout(k, ex.c.nrhs, slices);
-        const size_t need = factor_planes ? (size_t)slices * w.y_bytes : w.total;
+        const size_t planes = factor_planes ? (size_t)slices * w.y_bytes : w.total;
+        const size_t need = planes + (dag ? dag_extra_bytes(k, ex.c.nrhs, slices) : 0);
         if (h->ws == nullptr || h->ws_bytes < need) {
             snprintf(g_detail, sizeof(g_detail), "workspace of %zu bytes needed, %zu set",
                      need, h->ws_bytes);
@@ -481,12 +510,21 @@ int execute(trx_handle_t h, bool trsm, char side, char uplo, char transa, char d
             set_m_planes(ex.pl, base, w.m_bytes, slices);
             set_y_planes(ex.pl, base + (size_t)slices * w.m_bytes, w.y_bytes, slices);
         }
+        if (dag) {
+            // compact inverses and the flags after the planes
+            char* d = base + planes;
+            const size_t wb = align256((size_t)k * kDagBlock * 2);
+            ex.w_hi = reinterpret_cast<__nv_bfloat16*>(d);
+            ex.w_lo = slices > 1 ? reinterpret_cast<__nv_bfloat16*>(d + wb) : nullptr;
+            ex.w_lo2 = slices > 2 ? reinterpret_cast<__nv_bfloat16*>(d + 2 * wb) : nullptr;
+            ex.dag_flags = reinterpret_cast<int*>(d + (size_t)slices * wb);
+        }
     }
     // TRSM leaves on the tensor cores: the inverted diagonal blocks sit in
     // the M planes' own diagonal blocks (no TRSM update reads inside a leaf
     // block) or, for a prepared factor, in the factor's W planes made for
     // this leaf size (its M planes serve TRMM's diagonal blocks too).
-    plan.tc_leaf = std::is_same<T, float>::value && trsm &&
+    plan.tc_leaf = std::is_same<T, float>::value && trsm && !dag &&
                    tc_leaf_mode(h->opt_trsm_tc_leaf, plan.tc, b) &&
                    (!factor_planes || (f->w_hi != nullptr && f->w_block == b));
     if (plan.tc_leaf) {
@@ -498,7 +536,7 @@ int execute(trx_handle_t h, bool trsm, char side, char uplo, char transa, char d
     // as P column-panel branches (forked streams, one graph), so the
     // latency-bound bottom of the recursion of one panel overlaps the others'.
     int P = 1;
-    if (trsm) {
+    if (trsm && !dag) {
         if (h->opt_panels > 0) P = (int)h->opt_panels;
         const int64_t step = round_up((ex.c.nrhs + P - 1) / P, 256);
         P = (int)std::max<int64_t>(1, (ex.c.nrhs + step - 1) / step);
@@ -547,7 +585,18 @@ int execute(trx_handle_t h, bool trsm, char side, char uplo, char transa, char d
             pre.steps.push_back(iv);
         }
     }
-    make_plan(body, trsm, k, b, (double)alpha, /*conv_m=*/false, dense);
+    if (dag) {
+        // the device-scheduled solve in place of the recursion's chain: the
+        // diagonal blocks' inverses, then one persistent launch
+        Step iv{kInvCompact};
+        iv.b = kDagBlock;
+        body.steps.push_back(iv);
+        Step dg{kDag};
+        dg.alpha = (double)alpha;
+        body.steps.push_back(dg);
+    } else {
+        make_plan(body, trsm, k, b, (double)alpha, /*conv_m=*/false, dense);
+    }
     if (h->opt_checked) {
         if (const char* why = validate_plan(body, k)) {
             snprintf(g_detail, sizeof(g_detail), "checked plan: %s", why);
@@ -590,6 +639,7 @@ int execute(trx_handle_t h, bool trsm, char side, char uplo, char transa, char d
     key.tc = plan.tc;
     key.b = b;
     key.slices = plan.tc ? slices : 0;
+    key.dag = dag;
     key.k = k;
     key.nrhs = ex.c.nrhs;
     key.a_rs = ex.c.a_rs;
@@ -693,6 +743,7 @@ int noalloc_strsm(int device, int num_sms, void* scratch, size_t scratch_bytes, 
     hs.wait_ns = wait_ns;
     hs.opt_graph = 0;
     hs.opt_panels = 1;   // no handle streams here: one chain on the caller's stream
+    hs.opt_trsm_dag = -1;   // the recursive chain only: its scratch is the planes
     return execute<float>(&hs, true, side, uplo, transa, diag, m, n, alpha, A, lda, B, ldb,
                           stream);
 }
@@ -1193,11 +1244,12 @@ int trx_workspace_size(trx_handle_t h, char op, char side, int64_t m, int64_t n,
         return TRX_ERR_INVALID_VALUE;
     int64_t k = upc(side) == 'L' ? m : n, nrhs = upc(side) == 'L' ? n : m;
     if (o == 'Y') {         // factor calls (TRSM or TRMM): the Y planes only
-        const bool tc = elem_bytes == 4 &&
-                        (use_tc<float>(h, k, true, nrhs) || use_tc<float>(h, k, false, nrhs));
-        *bytes = (tc && k > 0 && nrhs > 0)
-                     ? (size_t)slices_for(h) * ws_layout(k, nrhs, slices_for(h)).y_bytes
-                     : 0;
+        const bool tc_s = elem_bytes == 4 && use_tc<float>(h, k, true, nrhs);
+        const bool tc = tc_s || (elem_bytes == 4 && use_tc<float>(h, k, false, nrhs));
+        const int sl = slices_for(h);
+        *bytes = (tc && k > 0 && nrhs > 0) ? (size_t)sl * ws_layout(k, nrhs, sl).y_bytes : 0;
+        if (tc_s && k > 0 && nrhs > 0 && use_dag_mode(h->opt_trsm_dag, true, true, 4, k, nrhs))
+            *bytes += dag_extra_bytes(k, nrhs, sl);
         return TRX_SUCCESS;
     }
     // FP64 TRSM on the mixed engine solves in FP32: that call's planes
@@ -1209,6 +1261,8 @@ int trx_workspace_size(trx_handle_t h, char op, char side, int64_t m, int64_t n,
         tc = true;
     }
     *bytes = (tc && k > 0 && nrhs > 0) ? ws_layout(k, nrhs, slices_for(h)).total : 0;
+    if (*bytes && o == 'S' && use_dag_mode(h->opt_trsm_dag, true, true, 4, k, nrhs))
+        *bytes += dag_extra_bytes(k, nrhs, slices_for(h));
     return TRX_SUCCESS;
 }
 
@@ -1847,6 +1901,10 @@ int trx_set_option(trx_handle_t h, int option, int64_t value) {
             if (value != 0 && value != 1) return TRX_ERR_INVALID_VALUE;
             h->opt_nvtx = value;
             break;
+        case TRX_OPT_TRSM_DAG:
+            if (value < -1 || value > 1) return TRX_ERR_INVALID_VALUE;
+            h->opt_trsm_dag = value;
+            break;
         default:
             return TRX_ERR_INVALID_VALUE;
     }
@@ -1871,6 +1929,7 @@ int trx_get_option(trx_handle_t h, int option, int64_t* value) {
         case TRX_OPT_FP64_TRSM: *value = h->opt_fp64_trsm; break;
         case TRX_OPT_CHECKED: *value = h->opt_checked; break;
         case TRX_OPT_NVTX: *value = h->opt_nvtx; break;
+        case TRX_OPT_TRSM_DAG: *value = h->opt_trsm_dag; break;
         default: return TRX_ERR_INVALID_VALUE;
     }
     return TRX_SUCCESS;

@@ -167,7 +167,7 @@ cudaError_t launch_convert_y_rows(const Canon<float>& p, const Planes& pl, int64
 // dimension ld), zeros above each block's diagonal.
 cudaError_t launch_invert_diag(const Canon<float>& p, int b, __nv_bfloat16* w_hi,
                                __nv_bfloat16* w_lo, __nv_bfloat16* w_lo2, int slices, int64_t ld,
-                               cudaStream_t s);
+                               cudaStream_t s, bool compact = false);
 // Split-BF16 planes of a rows x cols block, src(r, c) = src[r*rs + c*cs];
 // dst(r, c) at dst[r*ld + c] (row_major) or dst[c*ld + r] (otherwise).
 cudaError_t launch_convert_rect(const float* src, int64_t rs, int64_t cs, int64_t rows,
@@ -262,6 +262,23 @@ cudaError_t refine_norm_one(const double* a, int64_t lda, int64_t m, int64_t n, 
 size_t refine_norm_scratch(int64_t k);   // bytes refine_op_norm_inf needs at `sums`
 cudaError_t refine_op_norm_inf(const float* a, int64_t lda, int64_t k, bool lower, bool trans,
                                bool unit, double* sums, double* out, cudaStream_t s);
+
+// A BF16 plane (inner index contiguous, leading dimension ld elements) as a
+// 2-D tensor map with boxes of 32 x box_outer and the 64-byte swizzle (map:
+// a CUtensorMap, 64-byte aligned).
+bool tc_encode_bf16_2d(void* map, void* base, uint64_t inner, uint64_t outer, uint64_t ld,
+                       uint32_t box_outer);
+
+// Device-scheduled TRSM for few right-hand sides (trsm_dag.cu): applies to
+// the canonical lower solve when the order is a multiple of kDagBlock.
+// w: the inverted diagonal blocks as compact planes (row r of the k x 128
+// plane holds row r of its block's inverse); flags: blocks * panels ints
+// and a task counter after them (zeroed by the launch).
+constexpr int kDagBlock = 128, kDagPanel = 64;
+size_t dag_flag_bytes(int64_t k, int64_t nrhs);
+cudaError_t launch_trsm_dag(const Canon<float>& p, const Planes& pl, __nv_bfloat16* const w[3],
+                            float alpha, int* flags, int* err, long long wait_ns, int num_sms,
+                            cudaStream_t s);
 
 // K granularity the tensor-core GEMM needs (klen and rk multiples of this).
 constexpr int kTcKQuantum = 64;

@@ -148,14 +148,15 @@ __global__ void __launch_bounds__(256) convert_rect_kernel(const float* src, int
 // Inverse of each full b x b diagonal block of the canonical lower M,
 // W = inv(M_ii) (lower triangular), as split planes over rows and columns
 // [r0, r0 + b) of a row-major plane pair (element (i, l) at i * ld + l,
-// zeros above the diagonal). One CTA per block: the block is staged in
+// zeros above the diagonal), or, compact, at rows [r0, r0 + b) and columns
+// [0, b) of a k x ld plane. One CTA per block: the block is staged in
 // shared memory and thread j solves M_ii w_j = e_j by forward substitution
 // for column j of W.
 __global__ void __launch_bounds__(128) invert_diag_kernel(Canon<float> p, int b,
                                                           __nv_bfloat16* w_hi,
                                                           __nv_bfloat16* w_lo,
                                                           __nv_bfloat16* w_lo2, int slices,
-                                                          int64_t ld) {
+                                                          int64_t ld, int compact) {
     pdl_trigger();
     pdl_wait();
     extern __shared__ float inv_sm[];
@@ -187,7 +188,8 @@ __global__ void __launch_bounds__(128) invert_diag_kernel(Canon<float> p, int b,
     __syncthreads();
     for (int e = threadIdx.x; e < b * b; e += blockDim.x) {
         const int i = e / b, l = e % b;
-        put_split(w_hi, w_lo, w_lo2, slices, (r0 + i) * ld + r0 + l, Ws[i * b + l]);
+        put_split(w_hi, w_lo, w_lo2, slices, (r0 + i) * ld + (compact ? 0 : r0) + l,
+                  Ws[i * b + l]);
     }
 }
 
@@ -230,14 +232,14 @@ cudaError_t launch_convert_y(const Canon<float>& p, const Planes& pl, cudaStream
 
 cudaError_t launch_invert_diag(const Canon<float>& p, int b, __nv_bfloat16* w_hi,
                                __nv_bfloat16* w_lo, __nv_bfloat16* w_lo2, int slices, int64_t ld,
-                               cudaStream_t s) {
-    if (b < 1 || b > 128) return cudaErrorInvalidValue;
+                               cudaStream_t s, bool compact) {
+    if (b < 1 || b > 128 || (compact && ld < b)) return cudaErrorInvalidValue;
     const int64_t blocks = p.k / b;          // full blocks only
     if (blocks <= 0) return cudaSuccess;
     if (blocks > 0x7fffffff) return cudaErrorInvalidValue;
     const int smem = (int)((size_t)b * (2 * b + 1) * sizeof(float));
     return launch_kernel(invert_diag_kernel, dim3((unsigned)blocks), dim3(128), smem, s, p, b,
-                         w_hi, w_lo, w_lo2, slices, ld);
+                         w_hi, w_lo, w_lo2, slices, ld, compact ? 1 : 0);
 }
 
 // Shared-memory limit of the inversion kernel; like every kernel attribute

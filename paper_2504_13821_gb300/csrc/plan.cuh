@@ -36,7 +36,7 @@ inline int64_t split_point(int64_t s, int b) {
     return s1;
 }
 
-enum StepKind { kLeaf, kGemm, kConvM, kConvY, kConvYRows, kInvDiag };
+enum StepKind { kLeaf, kGemm, kConvM, kConvY, kConvYRows, kInvDiag, kInvCompact, kDag };
 
 struct Step {
     StepKind kind;
@@ -323,6 +323,18 @@ inline bool tc_leaf_mode(int64_t opt, bool tc, int b) {
 constexpr int kDefaultSplitTerms = 6;
 inline int split_terms(int64_t opt) {
     return (opt == 1 || opt == 3 || opt == 6) ? (int)opt : kDefaultSplitTerms;
+}
+
+// The device-scheduled TRSM (trsm_dag.cu) in place of the recursion's launch
+// chain (TRX_OPT_TRSM_DAG: -1 off, 1 on where it applies, 0 automatic): FP32
+// TRSM on the tensor-core path with the order a multiple of 128 (at least
+// 256); automatically with at most kDagMaxNrhs right-hand sides, where the
+// chain's launch and leaf latency bound the recursive path.
+constexpr int64_t kDagMaxNrhs = 1024;
+constexpr bool kDagAuto = false;
+inline bool use_dag_mode(int64_t opt, bool tc, bool trsm, int elem, int64_t k, int64_t nrhs) {
+    if (opt < 0 || !tc || !trsm || elem != 4 || k < 256 || k % kDagBlock != 0) return false;
+    return opt > 0 || (kDagAuto && nrhs <= kDagMaxNrhs);
 }
 
 inline bool use_tc_mode(int elem, int64_t gemm_mode, int64_t k, int b) {
