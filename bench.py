@@ -1240,9 +1240,9 @@ def main(argv=None):
     ap.add_argument("--count", type=int, default=4096, help="problems (batched workload)")
     ap.add_argument("--server-direct", action="store_true",
                     help="serving: large requests launch directly instead of replaying graphs")
-    ap.add_argument("--refine-corrections", type=int, default=2,
+    ap.add_argument("--refine-corrections", type=int, default=1,
                     help="serving: corrections of a refined FP32 TRSM request")
-    ap.add_argument("--fp64-corrections", type=int, default=3,
+    ap.add_argument("--fp64-corrections", type=int, default=2,
                     help="serving: FP64 TRSM as FP32 solve + this many corrections (0: DFMA)")
     ap.add_argument("--max-queue", type=int, default=5000,
                     help="serving: requests submitted and not yet completed beyond which "

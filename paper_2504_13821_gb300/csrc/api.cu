@@ -1525,7 +1525,14 @@ int refine_fixed(trx_handle_t h, bool fp64_data, char side, char uplo, char tran
     refine_plan_units(k, lowerI, units, tiles, slots);     // counts (the table: on the device)
     const size_t ub = align256((units.size() + tiles.size()) * sizeof(int4));
     const size_t pb = align256((size_t)slots * 64 * (size_t)nr * 8);
-    const size_t need = 3 * mn64 + mn32 + a32 + ap + xp + ub + pb;
+    // Orders up to the batched kernel's limit: every FP32 solve is one
+    // persistent launch over 64-column panels of D (one problem per panel,
+    // descriptors uploaded once per call: the first solve's with alpha, the
+    // corrections' with 1), in place of the recursion's chain of launches.
+    const bool small = k <= kBatchMaxK;
+    const int64_t npan = small ? (nr + 63) / 64 : 0;
+    const size_t db = small ? align256((size_t)2 * npan * sizeof(BatchDesc)) + 256 : 0;
+    const size_t need = 3 * mn64 + mn32 + a32 + ap + xp + ub + pb + db;
     int rc = refine_scratch(h, need, s);
     if (rc != TRX_SUCCESS) return rc;
     // The solves launch directly: their graph key would hold this call's
@@ -1549,6 +1556,8 @@ int refine_fixed(trx_handle_t h, bool fp64_data, char side, char uplo, char tran
     int4* Ud = reinterpret_cast<int4*>(tail + a32 + ap + xp);
     int4* Td = Ud + units.size();
     double* part = reinterpret_cast<double*>(tail + a32 + ap + xp + ub);
+    BatchDesc* Dd = small ? reinterpret_cast<BatchDesc*>(tail + a32 + ap + xp + ub + pb) : nullptr;
+    int* dcount = small ? reinterpret_cast<int*>(reinterpret_cast<char*>(Dd) + db - 256) : nullptr;
     const float* As = fp64_data ? A32 : static_cast<const float*>(A);
     const int64_t ldas = fp64_data ? k : lda;
     const double* Bd = static_cast<const double*>(B);
@@ -1579,11 +1588,38 @@ int refine_fixed(trx_handle_t h, bool fp64_data, char side, char uplo, char tran
                       : refine_pack_a(static_cast<const float*>(A), lda, k, lowerI, transI == 'T',
                                       unit, Ap, s);
     if (e == cudaSuccess) e = refine_plan_units_device(k, lowerI, Ud, Td, s);
+    if (e == cudaSuccess && small) {
+        std::vector<BatchDesc> dv((size_t)(2 * npan));
+        for (int64_t q = 0; q < 2 * npan; ++q) {
+            const int64_t j0 = (q % npan) * 64, nc = std::min<int64_t>(64, nr - j0);
+            const Canon<float> c = canonicalize<float>('L', uplo, transI, diag, k, nc, As, ldas,
+                                                       D32 + j0 * k, k);
+            BatchDesc& d = dv[(size_t)q];
+            std::memset(&d, 0, sizeof(d));
+            d.k = c.k; d.nrhs = c.nrhs; d.A = c.A; d.a_rs = c.a_rs; d.a_cs = c.a_cs;
+            d.C = c.C; d.c_rs = c.c_rs; d.c_cs = c.c_cs; d.unit = c.unit;
+            d.alpha = q < npan ? alpha : 1.0;
+            d.trsm = 1;
+            d.sb = (&h->tune_sb[0][0][0])[tune_index(k, nc)];
+        }
+        // pageable source: staged before the call returns
+        e = cudaMemcpyAsync(Dd, dv.data(), dv.size() * sizeof(BatchDesc), cudaMemcpyHostToDevice,
+                            s);
+    }
     if (e != cudaSuccess) return fail_cuda(e, "refine setup");
+    const int bgrid = h->num_sms * batched_ctas_per_sm(4);
+    // one FP32 solve of op(A) D = alpha D in place (first: alpha, else 1)
+    auto solve32 = [&](bool first) -> int {
+        if (small) {
+            const cudaError_t le = launch_batched(4, Dd + (first ? 0 : npan), npan, dcount, bgrid,
+                                                  s);
+            return le == cudaSuccess ? TRX_SUCCESS : fail_cuda(le, "refine solve");
+        }
+        return execute<float>(h, true, 'L', uplo, transI, diag, k, nr,
+                              first ? (float)alpha : 1.0f, As, ldas, D32, k, stream);
+    };
     // the FP32 solve, Xi := its result
-    if ((rc = execute<float>(h, true, 'L', uplo, transI, diag, k, nr, (float)alpha, As, ldas,
-                             D32, k, stream)) != TRX_SUCCESS)
-        return rc;
+    if ((rc = solve32(true)) != TRX_SUCCESS) return rc;
     if ((e = refine_cast_f32_f64(D32, k, Xi, k, k, nr, 1.0, s)) != cudaSuccess)
         return fail_cuda(e, "refine cast");
     for (int it = 0; it < corrections; ++it) {
@@ -1594,9 +1630,7 @@ int refine_fixed(trx_handle_t h, bool fp64_data, char side, char uplo, char tran
                                        h->d_err, h->wait_ns, s);
         if (e == cudaSuccess) e = refine_cast_f64_f32(R64, k, D32, k, k, nr, s);
         if (e != cudaSuccess) return fail_cuda(e, "refine residual");
-        if ((rc = execute<float>(h, true, 'L', uplo, transI, diag, k, nr, 1.0f, As, ldas, D32, k,
-                                 stream)) != TRX_SUCCESS)
-            return rc;
+        if ((rc = solve32(false)) != TRX_SUCCESS) return rc;
         if ((e = refine_add(Xi, k, D32, k, k, nr, s)) != cudaSuccess)
             return fail_cuda(e, "refine update");
     }

@@ -5,9 +5,8 @@
 - FP32 data: the FP32 solve plus two float-float corrections reaches the
   backward error of an FP64 solve, eta <= 8 k 2^-53, on factors with
   kappa_1 about 1e2 and 1e4 (stored scales at order 1024, and the default
-  generator at ragged orders), all 16 variants; zero corrections is the
-  plain FP32 solve (bitwise equal to trx_strsm's result widened); runs are
-  bitwise repeatable.
+  generator at ragged orders), all 16 variants; zero corrections is an
+  FP32-grade solve (8 k 2^-24); runs are bitwise repeatable.
 - FP64 data through the mixed engine (FP32 solve on fl32(A), residual with
   A and X as float pairs): trx_dtrsm's result meets the FP64 bound
   8 k 2^-53 on every variant at orders 64 .. 700, in place in B, padding
@@ -72,14 +71,17 @@ def test_async_all_variants(trx, side, uplo, trans, diag):
     At, Bt = to_dev(A, "cuda:0"), to_dev(B, "cuda:0")
     X = trx.trsm_refined_async(side, uplo, trans, diag, -0.75, At, Bt, corrections=2)
     X0 = trx.trsm_refined_async(side, uplo, trans, diag, -0.75, At, Bt, corrections=0)
-    P = Bt.clone()
-    trx.trsm(side, uplo, trans, diag, -0.75, At, P)
     torch.cuda.synchronize()
-    assert torch.equal(X0, P.double()), "zero corrections differ from the plain solve"
-    A64 = np.where(np.isnan(A), np.nan, A.astype(np.float64))
+    A64 = A.astype(np.float64)
     eta = oracle.trsm_backward_error(side, uplo, trans, diag, -0.75, A64,
                                      np.asfortranarray(X.cpu().numpy()), B.astype(np.float64))["eta"]
     assert eta <= 8 * k * U64, eta
+    # zero corrections: the FP32 solve alone (orders up to 512 run it as one
+    # batched launch over 64-column panels), FP32-grade
+    eta0 = oracle.trsm_backward_error(side, uplo, trans, diag, -0.75, A64,
+                                      np.asfortranarray(X0.cpu().numpy()),
+                                      B.astype(np.float64))["eta"]
+    assert eta0 <= 8 * k * 2.0 ** -24, eta0
 
 
 @pytest.mark.parametrize("side,uplo,trans,diag", VARIANTS)
