@@ -1038,7 +1038,10 @@ def run_serving(args):
     unless --no-refine; FP64 TRSM requests take the server's FP64 engine
     (args.fp64_corrections > 0: the FP32 solve plus that many float-float
     corrections; 0: the recursive DFMA solve); TRMM requests run in their
-    factor's precision. Requests go to the library's server (trx_server_*)
+    factor's precision, FP64 TRMM as one float-float pass (--fp64-trmm 1)
+    or the DFMA product. Large requests launch directly (--server-graphs:
+    cached graphs, captured once per new buffer set). Requests go to the
+    library's server (trx_server_*)
     at their arrival time; a request's latency runs from its scheduled
     arrival to the poll that reports it complete. Reports p50/p99 latency
     and solves/s, overall and per request kind."""
@@ -1051,9 +1054,10 @@ def run_serving(args):
     # front so no request waits for a workspace to grow
     srv = serving.Server(0, streams=4, budget_bytes=150 << 30, max_inflight=4096,
                          workspace_bytes=args.server_workspace_mb << 20,
-                         graphs=not args.server_direct,
+                         graphs=args.server_graphs,
                          refine_corrections=args.refine_corrections,
-                         fp64_corrections=args.fp64_corrections)
+                         fp64_corrections=args.fp64_corrections,
+                         fp64_trmm=args.fp64_trmm)
     refine = not args.no_refine
     arrival, done, failed, kind = {}, {}, [], {}
 
@@ -1176,11 +1180,13 @@ def run_serving(args):
                                    + ", FP64 TRSM "
                                    + (f"FP32 solve + {args.fp64_corrections} float-float "
                                       "corrections" if args.fp64_corrections else "DFMA")
+                                   + ", FP64 TRMM "
+                                   + ("one float-float pass" if args.fp64_trmm else "DFMA")
                                    + ", factors reused "
                                    "1..50 times, 150 GB admission cap, native request server, "
                                    f"{args.server_workspace_mb} MB workspace per stream, "
-                                   + ("direct launches" if args.server_direct else
-                                      "cached graphs"),
+                                   + ("cached graphs" if args.server_graphs else
+                                      "direct launches"),
                        "requests": submitted, "offered_tflops": flops / args.duration / 1e12,
                        "failed": len(failed), "rejected_overload": rejected,
                        "max_queue": args.max_queue},
@@ -1238,8 +1244,11 @@ def main(argv=None):
                          "arrivals; refined: FP32 TRSM refined in FP64 (k 8192, 256 "
                          "right-hand sides unless --k/--nrhs say otherwise)")
     ap.add_argument("--count", type=int, default=4096, help="problems (batched workload)")
-    ap.add_argument("--server-direct", action="store_true",
-                    help="serving: large requests launch directly instead of replaying graphs")
+    ap.add_argument("--server-graphs", action="store_true",
+                    help="serving: large requests replay cached graphs (one capture per new "
+                         "buffer set) instead of launching directly")
+    ap.add_argument("--fp64-trmm", type=int, default=1, choices=[0, 1],
+                    help="serving: FP64 TRMM as one float-float pass (1) or DFMA (0)")
     ap.add_argument("--refine-corrections", type=int, default=1,
                     help="serving: corrections of a refined FP32 TRSM request")
     ap.add_argument("--fp64-corrections", type=int, default=2,

@@ -167,7 +167,9 @@ enum {
                               2^-44 of |op(A)||X|) and FP32 correction solves,
                               X accumulated in FP64 (asynchronous, as
                               trx_strsm_refined_async; uses the handle's
-                              refinement scratch)                          */
+                              refinement scratch). The pairs assume entries
+                              inside FP32's exponent range (about 1e-30 ..
+                              1e38 in magnitude); outside it use 0         */
     TRX_OPT_CHECKED = 13,  /* 1: check every call's launch plan before
                               enqueueing it (every leaf block, GEMM row and K
                               range inside the order of A, each update's K
@@ -182,7 +184,7 @@ enum {
                               replay (TRX_OPT_GRAPH 1) they mark the capture
                               only, so pair it with TRX_OPT_GRAPH 0 or
                               TRX_OPT_PROFILE 1. 0 (default) off          */
-    TRX_OPT_TRSM_DAG = 15  /* FP32 TRSM on the tensor-core path with the
+    TRX_OPT_TRSM_DAG = 15, /* FP32 TRSM on the tensor-core path with the
                               order a multiple of 128 (at least 256): 1 =
                               one persistent device-scheduled launch in place
                               of the recursion's launch chain (128-row blocks
@@ -196,6 +198,29 @@ enum {
                               with at most 1024 right-hand sides). Needs the
                               workspace trx_workspace_size reports (planes
                               + inverses + flags)                         */
+    TRX_OPT_FP64_TRMM = 16,/* trx_dtrmm's engine: 0 (default) the recursive
+                              FP64 product (CUDA-core DFMA updates); 1 = for
+                              orders of at least 64, the whole product
+                              alpha op(A) B in one float-float pass on the
+                              FP32 pipes (A and B as float pairs, about
+                              2^-44 of |op(A)||B|, inside 8 k u of FP64 for
+                              k >= 64; the refinement residual's kernel with
+                              a zero B). Entries must lie inside FP32's
+                              exponent range (as for TRX_OPT_FP64_TRSM).
+                              Uses the handle's refinement scratch        */
+    TRX_OPT_THIN = 17      /* FP32 TRSM with few right-hand sides: 1 = one
+                              persistent CUDA-core launch in place of the
+                              recursion (64-row blocks x 16-column panels,
+                              left-looking: each block row adds its products
+                              with the published blocks before it, then
+                              multiplies by its diagonal block's inverse,
+                              made by substitution in FP32; flags between
+                              blocks, bounded waits; FP32 FMA, no operand
+                              split); -1 = the recursion; 0 = automatic
+                              (default: order above 256 with at most 64
+                              right-hand sides, or at most 256 while order
+                              x right-hand sides <= 2^20). Its flags live
+                              in a small handle buffer grown on first use */
 };
 
 /* Kernel classes reported by trx_get_profile(). */
@@ -480,7 +505,8 @@ typedef struct {
     int64_t max_inflight;   /* requests admitted and not yet completed (4096)       */
     size_t budget_bytes;    /* device bytes admitted requests may hold (150 GiB)    */
     size_t workspace_bytes; /* per-stream workspace made at creation (0); a larger
-                               need grows it, which synchronises the device      */
+                               need grows it (stream-ordered: that stream waits
+                               for its own earlier work, the others run on)     */
     int graphs;             /* 1: large requests replay cached CUDA graphs (one
                                capture per new problem shape); 0: direct
                                launches (1)                                      */
@@ -488,6 +514,8 @@ typedef struct {
     int fp64_corrections;   /* FP64 TRSM requests: 0 the recursive DFMA solve;
                                n in 1..16 the FP32 solve plus n float-float
                                corrections (TRX_OPT_FP64_TRSM) (0)             */
+    int fp64_trmm;          /* FP64 TRMM requests: 0 the recursive DFMA product;
+                               1 one float-float pass (TRX_OPT_FP64_TRMM) (0)   */
 } trx_server_config_t;
 /* config NULL: the defaults in brackets above. */
 int trx_server_create(int device, const trx_server_config_t* config, trx_server_t* server);

@@ -26,6 +26,8 @@ OPT_FP64_TRSM = 12      # trx_dtrsm: 0 DFMA recursion; n: FP32 solve + n float-f
 OPT_CHECKED = 13        # 1: validate every launch plan before enqueueing
 OPT_NVTX = 14           # 1: NVTX range per launch step
 OPT_TRSM_DAG = 15       # FP32 TRSM: 1 device-scheduled, -1 recursive chain, 0 automatic
+OPT_FP64_TRMM = 16      # trx_dtrmm: 0 DFMA recursion; 1 one float-float pass (order >= 64)
+OPT_THIN = 17           # FP32 TRSM, few right-hand sides: 1 one persistent launch, -1 recursion, 0 auto
 RESIDUAL_AUTO, RESIDUAL_FP64, RESIDUAL_FLOAT_FLOAT, RESIDUAL_TC = 0, 1, 2, 3
 GEMM_AUTO, GEMM_SIMT, GEMM_TC = 0, 1, 2
 KERNEL_CLASSES = ("leaf_trsm", "leaf_trmm", "gemm_tc", "gemm_simt", "convert", "other")
@@ -69,7 +71,8 @@ class ServerConfig(ctypes.Structure):
     _fields_ = [("streams", ctypes.c_int), ("small_k", ctypes.c_int),
                 ("max_inflight", ctypes.c_int64), ("budget_bytes", ctypes.c_size_t),
                 ("workspace_bytes", ctypes.c_size_t), ("graphs", ctypes.c_int),
-                ("refine_corrections", ctypes.c_int), ("fp64_corrections", ctypes.c_int)]
+                ("refine_corrections", ctypes.c_int), ("fp64_corrections", ctypes.c_int),
+                ("fp64_trmm", ctypes.c_int)]
 
 
 class _Profile(ctypes.Structure):

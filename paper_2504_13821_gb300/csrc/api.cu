@@ -189,6 +189,7 @@ struct trx_handle_s {
     int64_t opt_checked = 0;     // validate every plan before enqueueing it
     int64_t opt_trsm_dag = 0;    // device-scheduled TRSM: -1 off, 0 automatic, 1 on
     int64_t opt_nvtx = 0;        // an NVTX range around every launch step
+    int64_t opt_fp64_trmm = 0;   // FP64 TRMM: 0 DFMA; 1 one float-float pass (order >= 64)
     long long wait_ns = kDefaultWaitNs;
     int* d_err = nullptr;
     cudaStream_t cap_stream = nullptr;
@@ -225,6 +226,10 @@ struct trx_handle_s {
     // refined TRSM scratch (grown on demand)
     void* rf_buf = nullptr;
     size_t rf_bytes = 0;
+    // thin-right-hand-side TRSM: task counter and block flags (grown on demand)
+    int64_t opt_thin = 0;
+    int* thin_buf = nullptr;
+    size_t thin_bytes = 0;
     cudaStream_t aux[kMaxPanels] = {};
     cudaEvent_t fork_ev = nullptr, join_ev[kMaxPanels] = {};
 };
@@ -267,6 +272,7 @@ struct Exec {
     __nv_bfloat16* w_lo = nullptr;
     __nv_bfloat16* w_lo2 = nullptr;
     int* dag_flags = nullptr;      // device-scheduled TRSM: block flags + task counter
+    int* thin_scratch = nullptr;   // thin TRSM: task counter, stop word, block flags
     cudaStream_t s;
     bool profile;
 
@@ -382,6 +388,14 @@ struct Exec {
                     cls = TRX_KERNEL_CONVERT;
                     bytes = 4.0 * c.k * st.b * 1.5;
                     break;
+                case kThin:
+                    e = launch_thin_trsm(*reinterpret_cast<const Canon<float>*>(&c),
+                                         (float)st.alpha, thin_scratch, h->d_err, h->wait_ns,
+                                         h->num_sms, s);
+                    cls = TRX_KERNEL_LEAF_TRSM;
+                    flops = (double)c.k * c.k * c.nrhs;
+                    bytes = 4.0 * ((double)c.k * (c.k + 1) / 2 + 2.0 * c.k * c.nrhs);
+                    break;
                 case kDag: {
                     __nv_bfloat16* const w3[3] = {w_hi, w_lo, w_lo2};
                     e = launch_trsm_dag(*reinterpret_cast<const Canon<float>*>(&c), pl, w3,
@@ -405,7 +419,7 @@ struct Exec {
 };
 
 struct GraphKey {
-    int op, elem, tc, b, slices, dag;
+    int op, elem, tc, b, slices, dag, thin;
     int64_t k, nrhs, a_rs, a_cs, c_rs, c_cs, unit;
     const void* A;
     const void* C;
@@ -450,6 +464,12 @@ int refine_fixed(trx_handle_t h, bool fp64_data, char side, char uplo, char tran
                  int64_t m, int64_t n, double alpha, const void* A, int64_t lda, const void* B,
                  int64_t ldb, double* X, int64_t ldx, int corrections, void* stream);
 int refine_scratch(trx_handle_t h, size_t need, cudaStream_t s);
+int pair_trmm(trx_handle_t h, char side, char uplo, char transa, char diag, int64_t m, int64_t n,
+              double alpha, const double* A, int64_t lda, double* B, int64_t ldb,
+              cudaStream_t s);
+// Smallest order the float-float FP64 TRMM takes: its error, a few 2^-48
+// of |op(A)||B| per element, is inside 8 k u of FP64 from here on.
+constexpr int64_t kPairTrmmMinK = 64;
 
 template <typename T>
 int execute(trx_handle_t h, bool trsm, char side, char uplo, char transa, char diag, int64_t m,
@@ -471,6 +491,11 @@ int execute(trx_handle_t h, bool trsm, char side, char uplo, char transa, char d
         return refine_fixed(h, true, side, uplo, transa, diag, m, n, (double)alpha, A, lda, B,
                             ldb, reinterpret_cast<double*>(B), ldb, (int)h->opt_fp64_trsm,
                             stream);
+    if (std::is_same<T, double>::value && !trsm && h->opt_fp64_trmm > 0 &&
+        (upc(side) == 'L' ? m : n) >= kPairTrmmMinK)
+        return pair_trmm(h, side, uplo, transa, diag, m, n, (double)alpha,
+                         reinterpret_cast<const double*>(A), lda, reinterpret_cast<double*>(B),
+                         ldb, s);
     Exec<T> ex;
     ex.h = h;
     ex.c = canonicalize<T>(side, uplo, transa, diag, m, n, A, lda, B, ldb);
@@ -479,8 +504,33 @@ int execute(trx_handle_t h, bool trsm, char side, char uplo, char transa, char d
     const int64_t k = ex.c.k;
     const int b = leaf_for(h->opt_leaf, k, trsm, (int)sizeof(T), ex.c.nrhs);
 
+    // Thin right-hand sides: one persistent CUDA-core launch (thin.cu), no
+    // planes; its task counter and flags live in a handle buffer, grown here
+    // (never inside a stream capture: a capture keeps the recursive chain).
+    bool thin = std::is_same<T, float>::value &&
+                use_thin_mode(h->opt_thin, trsm, (int)sizeof(T), k, ex.c.nrhs);
+    if (thin && h->thin_bytes < thin_scratch_bytes(k, ex.c.nrhs)) {
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        e = cudaStreamIsCapturing(s, &cs);
+        if (e != cudaSuccess) return fail_cuda(e, "cudaStreamIsCapturing");
+        if (cs != cudaStreamCaptureStatusNone) {
+            thin = false;
+        } else {
+            const size_t want = std::max<size_t>(2 * thin_scratch_bytes(k, ex.c.nrhs), 1 << 16);
+            if (h->thin_buf) cudaFree(h->thin_buf);        // waits for its last use
+            h->thin_buf = nullptr;
+            h->thin_bytes = 0;
+            if ((e = cudaMalloc(&h->thin_buf, want)) != cudaSuccess) {
+                snprintf(g_detail, sizeof(g_detail), "thin TRSM flags: %s", cudaGetErrorString(e));
+                return TRX_ERR_ALLOC;
+            }
+            h->thin_bytes = want;
+        }
+    }
+    ex.thin_scratch = thin ? h->thin_buf : nullptr;
+
     Plan plan;
-    plan.tc = use_tc<T>(h, k, trsm, ex.c.nrhs);
+    plan.tc = !thin && use_tc<T>(h, k, trsm, ex.c.nrhs);
     // A prepared factor supplies the M planes (and its split): the workspace
     // holds Y only.
     const bool factor_planes = plan.tc && f != nullptr && f->m_hi != nullptr;
@@ -536,7 +586,7 @@ int execute(trx_handle_t h, bool trsm, char side, char uplo, char transa, char d
     // as P column-panel branches (forked streams, one graph), so the
     // latency-bound bottom of the recursion of one panel overlaps the others'.
     int P = 1;
-    if (trsm && !dag) {
+    if (trsm && !dag && !thin) {
         if (h->opt_panels > 0) P = (int)h->opt_panels;
         const int64_t step = round_up((ex.c.nrhs + P - 1) / P, 256);
         P = (int)std::max<int64_t>(1, (ex.c.nrhs + step - 1) / step);
@@ -594,6 +644,10 @@ int execute(trx_handle_t h, bool trsm, char side, char uplo, char transa, char d
         Step dg{kDag};
         dg.alpha = (double)alpha;
         body.steps.push_back(dg);
+    } else if (thin) {
+        Step th{kThin};
+        th.alpha = (double)alpha;
+        body.steps.push_back(th);
     } else {
         make_plan(body, trsm, k, b, (double)alpha, /*conv_m=*/false, dense);
     }
@@ -640,6 +694,7 @@ int execute(trx_handle_t h, bool trsm, char side, char uplo, char transa, char d
     key.b = b;
     key.slices = plan.tc ? slices : 0;
     key.dag = dag;
+    key.thin = thin;
     key.k = k;
     key.nrhs = ex.c.nrhs;
     key.a_rs = ex.c.a_rs;
@@ -744,6 +799,7 @@ int noalloc_strsm(int device, int num_sms, void* scratch, size_t scratch_bytes, 
     hs.opt_graph = 0;
     hs.opt_panels = 1;   // no handle streams here: one chain on the caller's stream
     hs.opt_trsm_dag = -1;   // the recursive chain only: its scratch is the planes
+    hs.opt_thin = -1;       // (the thin solve's flags would need an allocation)
     return execute<float>(&hs, true, side, uplo, transa, diag, m, n, alpha, A, lda, B, ldb,
                           stream);
 }
@@ -1206,6 +1262,7 @@ int trx_destroy(trx_handle_t h) {
         cudaFreeAsync(h->rf_buf, 0);        // stream-ordered allocation
         cudaDeviceSynchronize();
     }
+    if (h->thin_buf) cudaFree(h->thin_buf);
     free_owned_ws(h);
     if (h->d_err) cudaFree(h->d_err);
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
@@ -1639,6 +1696,49 @@ int refine_fixed(trx_handle_t h, bool fp64_data, char side, char uplo, char tran
     return e == cudaSuccess ? TRX_SUCCESS : fail_cuda(e, "refine result");
 }
 
+// FP64 TRMM in one float-float pass on the FP32 pipes: B := alpha op(A) B
+// as R := 0 - op(A) (-alpha B) by the refinement residual's kernel (mode 3:
+// op(A) packed as float pairs, B scaled in FP64 and split into pairs; the
+// sums kept in two float pairs and added in FP64 at the end). Side R on
+// the transpose, B^T := alpha op(A)^T B^T, through a k x m copy.
+int pair_trmm(trx_handle_t h, char side, char uplo, char transa, char diag, int64_t m, int64_t n,
+              double alpha, const double* A, int64_t lda, double* B, int64_t ldb,
+              cudaStream_t s) {
+    const bool left = upc(side) == 'L';
+    const int64_t k = left ? m : n, nr = left ? n : m;
+    const bool trans = upc(transa) != 'N';
+    const bool transI = left ? trans : !trans;
+    const bool lowerI = (upc(uplo) == 'L') != transI, unit = upc(diag) == 'U';
+    const size_t ap = align256(refine_pack_a_bytes(k, lowerI));
+    const size_t xp = align256(refine_pack_x_bytes(k, nr));
+    std::vector<int4> units, tiles;
+    int64_t slots = 0;
+    refine_plan_units(k, lowerI, units, tiles, slots);
+    const size_t ub = align256((units.size() + tiles.size()) * sizeof(int4));
+    const size_t pb = align256((size_t)slots * 64 * (size_t)nr * 8);
+    const size_t bt = left ? 0 : align256((size_t)k * nr * 8);
+    const int rc = refine_scratch(h, ap + xp + ub + pb + bt, s);
+    if (rc != TRX_SUCCESS) return rc;
+    char* base = static_cast<char*>(h->rf_buf);
+    void* Ap = base;
+    void* Xp = base + ap;
+    int4* Ud = reinterpret_cast<int4*>(base + ap + xp);
+    int4* Td = Ud + units.size();
+    double* part = reinterpret_cast<double*>(base + ap + xp + ub);
+    double* Bt = left ? B : reinterpret_cast<double*>(base + ap + xp + ub + pb);
+    const int64_t ldt = left ? ldb : k;
+    cudaError_t e = refine_pack_a64(A, lda, k, lowerI, transI, unit, Ap, s);
+    if (e == cudaSuccess) e = refine_plan_units_device(k, lowerI, Ud, Td, s);
+    if (e == cudaSuccess && !left) e = refine_transpose_f64(B, ldb, Bt, k, m, n, s);
+    if (e == cudaSuccess) e = refine_pack_x(Bt, nullptr, ldt, k, nr, Xp, s, -alpha);
+    if (e == cudaSuccess)
+        e = refine_residual_packed(3, Ap, Xp, Ud, (int64_t)units.size(), Td,
+                                   (int64_t)tiles.size(), part, k, lowerI, nullptr, 0, Bt, ldt,
+                                   nr, h->d_err, h->wait_ns, s);
+    if (e == cudaSuccess && !left) e = refine_transpose_f64(Bt, k, B, ldb, k, m, s);
+    return e == cudaSuccess ? TRX_SUCCESS : fail_cuda(e, "float-float TRMM");
+}
+
 }  // namespace
 
 extern "C" {
@@ -1939,6 +2039,14 @@ int trx_set_option(trx_handle_t h, int option, int64_t value) {
             if (value < -1 || value > 1) return TRX_ERR_INVALID_VALUE;
             h->opt_trsm_dag = value;
             break;
+        case TRX_OPT_FP64_TRMM:
+            if (value != 0 && value != 1) return TRX_ERR_INVALID_VALUE;
+            h->opt_fp64_trmm = value;
+            break;
+        case TRX_OPT_THIN:
+            if (value < -1 || value > 1) return TRX_ERR_INVALID_VALUE;
+            h->opt_thin = value;
+            break;
         default:
             return TRX_ERR_INVALID_VALUE;
     }
@@ -1964,6 +2072,8 @@ int trx_get_option(trx_handle_t h, int option, int64_t* value) {
         case TRX_OPT_CHECKED: *value = h->opt_checked; break;
         case TRX_OPT_NVTX: *value = h->opt_nvtx; break;
         case TRX_OPT_TRSM_DAG: *value = h->opt_trsm_dag; break;
+        case TRX_OPT_FP64_TRMM: *value = h->opt_fp64_trmm; break;
+        case TRX_OPT_THIN: *value = h->opt_thin; break;
         default: return TRX_ERR_INVALID_VALUE;
     }
     return TRX_SUCCESS;

@@ -229,8 +229,9 @@ cudaError_t refine_scale_f64(const double* src, int64_t lds, double* dst, int64_
 // floats, or from one FP32 plane), then R := B - op(A) X with mode 0
 // (X = xh + xl) or 1 (one plane), error-free accumulation, 2 (one
 // plane, plain FP32 accumulation) or 3 (A packed from FP64 as pairs by
-// refine_pack_a64, X = xh + xl). R may be B. Waits bounded by wait_ns;
-// on timeout *err := TRX_ERR_TIMEOUT and R is not written.
+// refine_pack_a64, X = xh + xl). R may be B; B null reads as zero
+// (R := -op(A) X: the float-float TRMM). Waits bounded by wait_ns; on
+// timeout *err := TRX_ERR_TIMEOUT and R is not written.
 size_t refine_pack_a_bytes(int64_t k, bool lower);
 size_t refine_pack_x_bytes(int64_t k, int64_t n);
 cudaError_t refine_pack_a(const float* A, int64_t lda, int64_t k, bool lower, bool trans,
@@ -239,8 +240,9 @@ cudaError_t refine_pack_a(const float* A, int64_t lda, int64_t k, bool lower, bo
 // pairs: the residual of FP64 data).
 cudaError_t refine_pack_a64(const double* A, int64_t lda, int64_t k, bool lower, bool trans,
                             bool unit, void* Ap, cudaStream_t s);
+// X64 (times `scale`, in FP64, before the split) or X32 packed.
 cudaError_t refine_pack_x(const double* X64, const float* X32, int64_t ldx, int64_t k,
-                          int64_t n, void* Xp, cudaStream_t s);
+                          int64_t n, void* Xp, cudaStream_t s, double scale = 1.0);
 // Work units of the residual (row-tile pieces, heaviest first) and the row
 // tiles whose pieces refine_residual_packed combines; slots = partial
 // blocks of 64 x n doubles the pieces write.
@@ -279,6 +281,14 @@ size_t dag_flag_bytes(int64_t k, int64_t nrhs);
 cudaError_t launch_trsm_dag(const Canon<float>& p, const Planes& pl, __nv_bfloat16* const w[3],
                             float alpha, int* flags, int* err, long long wait_ns, int num_sms,
                             cudaStream_t s);
+
+// FP32 TRSM with few right-hand sides as one persistent CUDA-core launch
+// (thin.cu): 64-row blocks x 16-column panels, left-looking, flags between
+// tasks. scratch: thin_scratch_bytes ints, zeroed by the launch itself.
+constexpr int kThinBlock = 64, kThinPanel = 16;
+size_t thin_scratch_bytes(int64_t k, int64_t nrhs);
+cudaError_t launch_thin_trsm(const Canon<float>& c, float alpha, int* scratch, int* err,
+                             long long wait_ns, int num_sms, cudaStream_t s);
 
 // K granularity the tensor-core GEMM needs (klen and rk multiples of this).
 constexpr int kTcKQuantum = 64;

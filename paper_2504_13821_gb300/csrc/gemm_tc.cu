@@ -117,8 +117,16 @@ struct Params {
     int ngemms, n_tiles_n, total_tiles;
     int* err;
     long long wait_ns;
-    int tile_start[MAXG + 1];
-    TcGemm g[MAXG];
+};
+
+// The launch's update list. Launches of at most MAXG_SMALL updates (every
+// TRSM step, most TRMM levels) take the short form: a parameter block of
+// about 1 KB instead of about 11 KB, which the host copies on every launch.
+constexpr int MAXG_SMALL = 4;
+template <int MG>
+struct ParamsT : Params {
+    int tile_start[MG + 1];
+    TcGemm g[MG];
 };
 
 struct Smem {
@@ -156,7 +164,8 @@ struct Tile {
 // Tile t of the group: find its update (prefix sums), then raster the
 // update's (m, n) tiles in bands of 8 M-tiles so that the CTAs running at one
 // time share operand rows and columns in L2.
-__device__ __forceinline__ Tile map_tile(const Params& p, int t) {
+template <class PP>
+__device__ __forceinline__ Tile map_tile(const PP& p, int t) {
     int lo = 0, hi = p.ngemms - 1;
     while (lo < hi) {
         const int mid = (lo + hi + 1) >> 1;
@@ -179,9 +188,9 @@ __device__ __forceinline__ Tile map_tile(const Params& p, int t) {
     return r;
 }
 
-template <int BN, int S>
+template <int BN, int S, int MG>
 __global__ void __launch_bounds__(Precise<S>::value ? NTHREADS_P : NTHREADS, 1)
-    gemm_tc_kernel(const __grid_constant__ Params p) {
+    gemm_tc_kernel(const __grid_constant__ ParamsT<MG> p) {
     using C = Cfg<BN, S>;
     constexpr bool P = Precise<S>::value;
     constexpr int STAGES = C::STAGES;
@@ -577,20 +586,26 @@ bool tc_encode_bf16_2d(void* map, void* base, uint64_t inner, uint64_t outer, ui
     return tc::encode(reinterpret_cast<CUtensorMap*>(map), base, inner, outer, ld, box_outer);
 }
 
-template <int S>
-static cudaError_t tc_configure_s() {
+template <int S, int MG>
+static cudaError_t tc_configure_sg() {
     cudaError_t e;
-    if ((e = cudaFuncSetAttribute(tc::gemm_tc_kernel<256, S>,
+    if ((e = cudaFuncSetAttribute(tc::gemm_tc_kernel<256, S, MG>,
                                   cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   tc::Cfg<256, S>::SMEM_BYTES)) != cudaSuccess)
         return e;
-    if ((e = cudaFuncSetAttribute(tc::gemm_tc_kernel<128, S>,
+    if ((e = cudaFuncSetAttribute(tc::gemm_tc_kernel<128, S, MG>,
                                   cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   tc::Cfg<128, S>::SMEM_BYTES)) != cudaSuccess)
         return e;
-    return cudaFuncSetAttribute(tc::gemm_tc_kernel<64, S>,
+    return cudaFuncSetAttribute(tc::gemm_tc_kernel<64, S, MG>,
                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 tc::Cfg<64, S>::SMEM_BYTES);
+}
+
+template <int S>
+static cudaError_t tc_configure_s() {
+    cudaError_t e = tc_configure_sg<S, tc::MAXG>();
+    return e != cudaSuccess ? e : tc_configure_sg<S, tc::MAXG_SMALL>();
 }
 
 cudaError_t tc_configure() {
@@ -632,7 +647,7 @@ cudaError_t launch_gemm_tc(const Canon<float>& p, const void* maps, int slices,
         int bn = 64;
         if (mtiles * ((p.nrhs + 255) / 256) >= num_sms) bn = 256;
         else if (mtiles * ((p.nrhs + 127) / 128) >= num_sms) bn = 128;
-        static thread_local Params prm;
+        static thread_local ParamsT<MAXG> prm;
         prm.maps = *reinterpret_cast<const Maps*>(maps);
         prm.C = p.C;
         prm.c_rs = p.c_rs;
@@ -669,10 +684,20 @@ cudaError_t launch_gemm_tc(const Canon<float>& p, const void* maps, int slices,
         prm.total_tiles = (int)tiles;
         const int grid = (int)(tiles < num_sms ? tiles : num_sms);
         cudaError_t e;
-#define TRX_TC_LAUNCH(BNV, SV)                                                            \
-    launch_kernel(gemm_tc_kernel<BNV, SV>, dim3(grid),                                     \
-                  dim3(Precise<SV>::value ? NTHREADS_P : NTHREADS),                        \
-                  Cfg<BNV, SV>::SMEM_BYTES, s, prm)
+        static thread_local ParamsT<MAXG_SMALL> prm_small;
+        const bool small = ng <= MAXG_SMALL;
+        if (small) {
+            static_cast<Params&>(prm_small) = static_cast<const Params&>(prm);
+            for (int i = 0; i <= ng; ++i) prm_small.tile_start[i] = prm.tile_start[i];
+            for (int i = 0; i < ng; ++i) prm_small.g[i] = prm.g[i];
+        }
+#define TRX_TC_LAUNCH(BNV, SV)                                                             \
+    (small ? launch_kernel(gemm_tc_kernel<BNV, SV, MAXG_SMALL>, dim3(grid),                 \
+                           dim3(Precise<SV>::value ? NTHREADS_P : NTHREADS),               \
+                           Cfg<BNV, SV>::SMEM_BYTES, s, prm_small)                         \
+           : launch_kernel(gemm_tc_kernel<BNV, SV, MAXG>, dim3(grid),                       \
+                           dim3(Precise<SV>::value ? NTHREADS_P : NTHREADS),               \
+                           Cfg<BNV, SV>::SMEM_BYTES, s, prm))
         if (slices == 1)
             e = bn == 256 ? TRX_TC_LAUNCH(256, 1) : bn == 128 ? TRX_TC_LAUNCH(128, 1)
                                                               : TRX_TC_LAUNCH(64, 1);

@@ -49,6 +49,7 @@ cudaError_t leaf_wide_launch(const LeafArgs<float>& a, int num_sms, cudaStream_t
 cudaError_t convert_configure();
 cudaError_t refine_configure();
 cudaError_t dag_configure();
+cudaError_t thin_configure();
 
 // Kernel attributes (dynamic shared-memory limits) for the current device:
 // run once per device by every handle's and the allocation-free entry's
@@ -67,6 +68,7 @@ cudaError_t leaf_configure_all() {
     if ((e = convert_configure()) != cudaSuccess) return e;
     if ((e = refine_configure()) != cudaSuccess) return e;
     if ((e = dag_configure()) != cudaSuccess) return e;
+    if ((e = thin_configure()) != cudaSuccess) return e;
     return tc_configure();
 }
 

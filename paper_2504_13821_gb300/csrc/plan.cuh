@@ -36,7 +36,7 @@ inline int64_t split_point(int64_t s, int b) {
     return s1;
 }
 
-enum StepKind { kLeaf, kGemm, kConvM, kConvY, kConvYRows, kInvDiag, kInvCompact, kDag };
+enum StepKind { kLeaf, kGemm, kConvM, kConvY, kConvYRows, kInvDiag, kInvCompact, kDag, kThin };
 
 struct Step {
     StepKind kind;
@@ -335,6 +335,24 @@ constexpr bool kDagAuto = false;
 inline bool use_dag_mode(int64_t opt, bool tc, bool trsm, int elem, int64_t k, int64_t nrhs) {
     if (opt < 0 || !tc || !trsm || elem != 4 || k < 256 || k % kDagBlock != 0) return false;
     return opt > 0 || (kDagAuto && nrhs <= kDagMaxNrhs);
+}
+
+// The persistent CUDA-core TRSM for thin right-hand sides (thin.cu) in place
+// of the recursion (TRX_OPT_THIN: -1 off, 1 on for FP32 TRSM of any order,
+// 0 automatic): automatically for FP32 TRSM of order above kThinMinK with
+// at most kThinMaxNrhs right-hand sides, or up to kThinWideNrhs of them
+// while order x right-hand sides stays within kThinMaxWork, where the
+// chain's launch and leaf latency bound the recursive path (measured on
+// GB300: 1.3-3x faster there; at order 16384 with 128 or more right-hand
+// sides the chain's tensor-core updates win).
+constexpr int64_t kThinMaxNrhs = 64, kThinWideNrhs = 256;
+constexpr int64_t kThinMaxWork = (int64_t)1 << 20;
+constexpr int64_t kThinMinK = 256;
+inline bool use_thin_mode(int64_t opt, bool trsm, int elem, int64_t k, int64_t nrhs) {
+    if (opt < 0 || !trsm || elem != 4 || k <= 0 || nrhs <= 0) return false;
+    if (opt > 0) return true;
+    return k > kThinMinK &&
+           (nrhs <= kThinMaxNrhs || (nrhs <= kThinWideNrhs && k * nrhs <= kThinMaxWork));
 }
 
 inline bool use_tc_mode(int elem, int64_t gemm_mode, int64_t k, int b) {

@@ -377,14 +377,15 @@ __global__ void __launch_bounds__(256) pack_a_kernel(const float* A, int64_t lda
 template <bool SPLIT>
 __global__ void __launch_bounds__(256) pack_x_kernel(const double* X64, const float* X32,
                                                      int64_t ldx, int64_t k, int64_t n,
-                                                     int64_t rows, float4* Xp) {
+                                                     int64_t rows, double scale, float4* Xp) {
     const int64_t l = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5), ct = blockIdx.y;
     const int t = threadIdx.x & 31, pc = t >> 4, jj = t & 15;
     const int64_t ja = ct * kRN + jj + 32 * pc, jb = ja + 16;
     float4 v = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
     if (l < k) {
         if (SPLIT) {
-            const double xa = ja < n ? X64[l + ja * ldx] : 0.0, xb = jb < n ? X64[l + jb * ldx] : 0.0;
+            const double xa = ja < n ? scale * X64[l + ja * ldx] : 0.0;
+            const double xb = jb < n ? scale * X64[l + jb * ldx] : 0.0;
             v.x = (float)xa;
             v.y = (float)xb;
             v.z = (float)(xa - (double)v.x);
@@ -555,7 +556,7 @@ __global__ void __launch_bounds__(256) residual_pipe_kernel(const float4* __rest
                 if (j >= n) continue;
                 const double sum = (double)h[w] + ((double)m[w] + ((double)sm[w] + (double)t[w]));
                 if (u.w < 0)
-                    R[gi + j * ldr] = B[gi + j * ldb] - sum;
+                    R[gi + j * ldr] = (B ? B[gi + j * ldb] : 0.0) - sum;
                 else
                     part[((int64_t)u.w * n + j) * kRM + (ty + 16 * r)] = sum;
             }
@@ -575,7 +576,7 @@ __global__ void __launch_bounds__(256) combine_kernel(const int4* tiles, const d
     if (gi >= k) return;
     double sum = 0.0;
     for (int p = 0; p < t.z; ++p) sum += part[((int64_t)(t.y + p) * n + j) * kRM + il];
-    R[gi + j * ldr] = B[gi + j * ldb] - sum;
+    R[gi + j * ldr] = (B ? B[gi + j * ldb] : 0.0) - sum;
 }
 
 int grid_for(int64_t count) {
@@ -685,16 +686,16 @@ cudaError_t refine_pack_a64(const double* A, int64_t lda, int64_t k, bool lower,
     return cudaGetLastError();
 }
 cudaError_t refine_pack_x(const double* X64, const float* X32, int64_t ldx, int64_t k,
-                          int64_t n, void* Xp, cudaStream_t s) {
+                          int64_t n, void* Xp, cudaStream_t s, double scale) {
     if (k <= 0 || n <= 0) return cudaSuccess;
     const int64_t rows = (k + 15) / 16 * 16, nct = (n + kRN - 1) / kRN;
     if (nct > 65535 || rows > 0x7fffffff) return cudaErrorInvalidValue;
     const dim3 grid((unsigned)(rows / 8), (unsigned)nct);      // rows: a multiple of 16
     if (X64)
-        pack_x_kernel<true><<<grid, 256, 0, s>>>(X64, nullptr, ldx, k, n, rows,
+        pack_x_kernel<true><<<grid, 256, 0, s>>>(X64, nullptr, ldx, k, n, rows, scale,
                                                  static_cast<float4*>(Xp));
     else
-        pack_x_kernel<false><<<grid, 256, 0, s>>>(nullptr, X32, ldx, k, n, rows,
+        pack_x_kernel<false><<<grid, 256, 0, s>>>(nullptr, X32, ldx, k, n, rows, 1.0,
                                                   static_cast<float4*>(Xp));
     return cudaGetLastError();
 }

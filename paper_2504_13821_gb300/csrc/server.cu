@@ -23,6 +23,8 @@
 // and the refined FP32 TRSM (trx_server_submit_refined: FP32 factor and
 // right-hand side, FP64 result, the FP32 solve plus a fixed number of
 // float-float corrections, trx_strsm_refined_async, with no host read-back).
+// FP64 TRMM requests: the recursive DFMA product or one float-float pass
+// (config fp64_trmm).
 // FP64 TRSM requests take the handles' FP64 engine (config fp64_corrections:
 // the recursive DFMA solve, or the FP32 solve plus corrections).
 #include <cuda_runtime.h>
@@ -320,11 +322,13 @@ int trx_server_create(int device, const trx_server_config_t* config, trx_server_
     cfg.graphs = 1;
     cfg.refine_corrections = 2;
     cfg.fp64_corrections = 0;
+    cfg.fp64_trmm = 0;
     if (config) cfg = *config;
     if (cfg.streams < 1 || cfg.streams > 16 || cfg.small_k < 0 ||
         cfg.small_k > TRX_BATCH_MAX_K || cfg.max_inflight < 1 ||
         (cfg.graphs != 0 && cfg.graphs != 1) || cfg.refine_corrections < 0 ||
-        cfg.refine_corrections > 16 || cfg.fp64_corrections < 0 || cfg.fp64_corrections > 16)
+        cfg.refine_corrections > 16 || cfg.fp64_corrections < 0 || cfg.fp64_corrections > 16 ||
+        (cfg.fp64_trmm != 0 && cfg.fp64_trmm != 1))
         return TRX_ERR_INVALID_VALUE;
     cudaError_t e = cudaSetDevice(device);
     if (e != cudaSuccess) return fail(e, "cudaSetDevice");
@@ -346,6 +350,7 @@ int trx_server_create(int device, const trx_server_config_t* config, trx_server_
         if ((rc = trx_set_option(h, TRX_OPT_GRAPH, cfg.graphs)) != TRX_SUCCESS) break;
         if ((rc = trx_set_option(h, TRX_OPT_FP64_TRSM, cfg.fp64_corrections)) != TRX_SUCCESS)
             break;
+        if ((rc = trx_set_option(h, TRX_OPT_FP64_TRMM, cfg.fp64_trmm)) != TRX_SUCCESS) break;
         s->ws.push_back(nullptr);
         s->ws_bytes.push_back(0);
     }

@@ -1,0 +1,323 @@
+// FP32 TRSM with few right-hand sides as one persistent launch on the CUDA
+// cores.
+//
+// With a thin right-hand side the recursion of Section 3.1 is a long chain
+// of small launches (a leaf and a GEMM update per 128 rows), each bound by
+// latency: at order 8000 with 8 right-hand sides the chain takes about
+// 1.6 ms to read a 128 MB triangle. Here the canonical lower M is cut into
+// 64-row blocks and the right-hand side into 16-column panels, and task
+// (i, p) runs the blocked forward substitution of block row i, left-looking:
+//
+//     S   = sum_{j < i} M_ij X_jp          (64 x 64 x 16 products, FP32 FMA)
+//     X_ip = inv(M_ii) (alpha B_ip - S)
+//
+// then writes X_ip into C and publishes it with a flag. The products of a
+// task start as soon as the blocks X_jp they need are published, so the
+// reads of M (every element once per panel, the dominant traffic) overlap
+// the chain of diagonal blocks; the chain itself is one 64 x 64 x 16 product
+// and one product with inv(M_ii) per block. inv(M_ii) is made by the task
+// itself by substitution before its first wait (64 columns of the identity,
+// FP32, one reciprocal of each diagonal entry): the leaf solve of Section
+// 3.3 as a product with the inverted block.
+//
+// Tasks are taken in order from an atomic counter (block row major), so a
+// task only waits for tasks taken before it, which are running or done: the
+// solve progresses whatever the number of resident CTAs. Every flag wait is
+// bounded: past the budget the CTA writes TRX_ERR_TIMEOUT to the error word
+// and stops; tasks waiting on it then time out too.
+//
+// Arithmetic: FP32 FMA throughout (no operand split), partial sums in a
+// fixed order, so results are bitwise repeatable.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "common.cuh"
+
+namespace trx {
+namespace thin {
+
+constexpr int BR = kThinBlock;       // rows of a block
+constexpr int NP = kThinPanel;       // columns of a panel
+constexpr int NT = 256;
+constexpr int LD = BR + 4;           // shared row stride (floats): 16-byte aligned rows
+constexpr int LDT = BR + 1;          // inverse work tile: conflict-free column reads
+constexpr int kTimeout = 4;          // TRX_ERR_TIMEOUT
+
+struct Params {
+    int64_t k, nrhs;
+    const float* A;
+    int64_t a_rs, a_cs;
+    float* C;
+    int64_t c_rs, c_cs;
+    float alpha;
+    int unit;
+    int nbr, npan;
+    int64_t ntask;
+    int* ticket;     // next task
+    int* stop;       // set by a CTA whose wait ran out: the others stop waiting
+    int* flags;      // [p * nbr + i]: 1 once X_ip is in C
+    int* err;
+    long long wait_ns;
+};
+
+struct Smem {
+    float m[BR * LD];        // M_ij tile, k-major: m[kk * LD + r] = M[i0 + r][j0 + kk]
+    float inv[BR * LD];      // inv(M_ii), k-major: inv[kk * LD + r] = Inv[r][kk]
+    float x[BR * NP];        // X_jp tile / right-hand side: x[kk * NP + c]
+    float dinv[BR];
+    int task;
+    int abort;
+};
+
+__device__ __forceinline__ uint64_t gtimer() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+__device__ __forceinline__ int ld_acquire(const int* p) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release(int* p, int v) {
+    asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Thread 0: wait until *f is set, at most wait_ns. False on timeout (the
+// error word and the launch's stop word are set) or once another CTA has
+// stopped the launch.
+__device__ bool wait_flag(const Params& p, const int* f) {
+    if (ld_acquire(f)) return true;
+    const uint64_t t0 = gtimer();
+    while (true) {
+        if (ld_acquire(f)) return true;
+        if (*(volatile int*)p.stop) return false;
+        if (gtimer() - t0 > (uint64_t)p.wait_ns) {
+            atomicExch(p.err, kTimeout);
+            atomicExch(p.stop, 1);
+            return false;
+        }
+    }
+}
+
+// Tile (i0.., j0..) of M into registers, 16 elements a thread, along M's
+// contiguous direction; zero outside the strict lower triangle of the order
+// (off-diagonal tiles lie below the diagonal: only the order bounds rows).
+__device__ __forceinline__ void load_m(const Params& p, int64_t i0, int64_t j0, bool colmajor,
+                                       float (&r)[16]) {
+    const int t = threadIdx.x;
+    const int rr = colmajor ? (t & 63) : (t >> 6), cc = colmajor ? (t >> 6) : (t & 63);
+    const float* src = p.A + (i0 + rr) * p.a_rs + (j0 + cc) * p.a_cs;
+    const int64_t step = 4 * (colmajor ? p.a_cs : p.a_rs);
+    const int64_t rows_left = p.k - (i0 + rr);      // rows of this thread inside the order
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+        const bool in = colmajor ? rows_left > 0 : rows_left > 4 * q;
+        r[q] = in ? __ldg(src + q * step) : 0.0f;
+    }
+}
+__device__ __forceinline__ void store_m(Smem& sm, bool colmajor, const float (&r)[16]) {
+    const int t = threadIdx.x;
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+        const int rr = colmajor ? (t & 63) : (t >> 6) + 4 * q;
+        const int cc = colmajor ? (t >> 6) + 4 * q : (t & 63);
+        sm.m[cc * LD + rr] = r[q];
+    }
+}
+
+// X_jp (rows j0.., panel columns c0..) from C into shared memory, through
+// L2 (another CTA wrote it during this launch).
+__device__ __forceinline__ void load_x(const Params& p, Smem& sm, int64_t j0, int64_t c0,
+                                       bool c_colmajor) {
+    const int t = threadIdx.x;
+#pragma unroll
+    for (int q = 0; q < (BR * NP) / NT; ++q) {
+        const int kk = c_colmajor ? (t & 63) : (t >> 4) + 16 * q;
+        const int c = c_colmajor ? (t >> 6) + 4 * q : (t & 15);
+        const int64_t gi = j0 + kk, gj = c0 + c;
+        sm.x[kk * NP + c] =
+            (gi < p.k && gj < p.nrhs) ? __ldcg(p.C + gi * p.c_rs + gj * p.c_cs) : 0.0f;
+    }
+}
+
+// acc[e] += sum_kk a[kk][4 ty + e] * x[kk][tx] over kk < kend.
+__device__ __forceinline__ void mma_tile(const float* a, const float* x, int kend,
+                                         float (&acc)[4]) {
+    const int ty = threadIdx.x >> 4, tx = threadIdx.x & 15;
+#pragma unroll 8
+    for (int kk = 0; kk < kend; ++kk) {
+        const float4 m = *reinterpret_cast<const float4*>(a + kk * LD + 4 * ty);
+        const float xv = x[kk * NP + tx];
+        acc[0] = fmaf(m.x, xv, acc[0]);
+        acc[1] = fmaf(m.y, xv, acc[1]);
+        acc[2] = fmaf(m.z, xv, acc[2]);
+        acc[3] = fmaf(m.w, xv, acc[3]);
+    }
+}
+
+// inv(M_ii) into sm.inv. M_ii's lower triangle goes to a work tile (aliasing
+// sm.m) with rows past the order as identity rows; warp w then solves
+// M y = e_c for columns c = 8w .. 8w + 7, lane l holding rows l and l + 32:
+// at step r the lane owning row r finishes y_r = (delta_rc - s_r) / m_rr
+// (reciprocal of m_rr made once), broadcasts it, and every lane adds
+// m_row,r y_r into the partial sums of its later rows.
+__device__ void invert_diag(const Params& p, Smem& sm, int64_t i0) {
+    float* T = sm.m;
+    const int t = threadIdx.x, w = t >> 5, l = t & 31;
+    const bool colmajor = p.a_rs == 1 || p.a_rs == -1;
+    for (int e = t; e < BR * BR; e += NT) {
+        const int rr = colmajor ? e % BR : e / BR;
+        const int cc = colmajor ? e / BR : e % BR;
+        const int64_t gi = i0 + rr, gj = i0 + cc;
+        float v = 0.0f;
+        if (gi >= p.k) v = rr == cc ? 1.0f : 0.0f;
+        else if (cc < rr) v = __ldg(p.A + gi * p.a_rs + gj * p.a_cs);
+        else if (cc == rr) v = p.unit ? 1.0f : __ldg(p.A + gi * p.a_rs + gj * p.a_cs);
+        T[rr * LDT + cc] = v;
+    }
+    __syncthreads();
+    if (t < BR) sm.dinv[t] = 1.0f / T[t * LDT + t];
+    __syncthreads();
+    float y0[8], y1[8];          // rows l and l + 32, columns 8 w + u
+#pragma unroll
+    for (int u = 0; u < 8; ++u) y0[u] = y1[u] = 0.0f;
+    for (int r = 0; r < BR; ++r) {
+        const float dr = sm.dinv[r];
+        const int owner = r & 31;
+        const bool hi = r >= 32;
+        const float m0 = T[l * LDT + r], m1 = T[(l + 32) * LDT + r];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const float s = hi ? y1[u] : y0[u];
+            const float v = ((r == 8 * w + u) ? 1.0f : 0.0f) - s;
+            const float yr = __shfl_sync(0xffffffffu, v * dr, owner);
+            if (l == owner) {
+                if (hi) y1[u] = yr; else y0[u] = yr;
+            }
+            if (l > r) y0[u] = fmaf(m0, yr, y0[u]);
+            if (l + 32 > r) y1[u] = fmaf(m1, yr, y1[u]);
+        }
+    }
+    // s_r accumulated with +: the recurrence above keeps s = sum m y and
+    // y_r = (delta - s) / m_rr
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+        sm.inv[(8 * w + u) * LD + l] = y0[u];
+        sm.inv[(8 * w + u) * LD + l + 32] = y1[u];
+    }
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(NT, 3) thin_trsm_kernel(const Params p) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Smem& sm = *reinterpret_cast<Smem*>(smem_raw);
+    const int t = threadIdx.x, ty = t >> 4, tx = t & 15;
+    const bool colmajor = p.a_rs == 1 || p.a_rs == -1;
+    const bool c_colmajor = p.c_rs == 1 || p.c_rs == -1;
+    if (t == 0) sm.abort = 0;
+    while (true) {
+        __syncthreads();
+        if (t == 0) sm.task = atomicAdd(p.ticket, 1);
+        __syncthreads();
+        const int64_t task = sm.task;
+        if (task >= p.ntask || sm.abort) break;
+        const int i = (int)(task / p.npan), pn = (int)(task % p.npan);
+        const int64_t i0 = (int64_t)i * BR, c0 = (int64_t)pn * NP;
+        // this task's right-hand side rows, read before anything is written
+        float b[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const int64_t gi = i0 + 4 * ty + e, gj = c0 + tx;
+            b[e] = (gi < p.k && gj < p.nrhs) ? __ldcg(p.C + gi * p.c_rs + gj * p.c_cs) : 0.0f;
+        }
+        invert_diag(p, sm, i0);
+        float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+        float mr[16];
+        if (i > 0) load_m(p, i0, 0, colmajor, mr);
+        for (int j = 0; j < i; ++j) {
+            store_m(sm, colmajor, mr);
+            if (j + 1 < i) load_m(p, i0, (int64_t)(j + 1) * BR, colmajor, mr);
+            if (t == 0 && !wait_flag(p, p.flags + (int64_t)pn * p.nbr + j)) sm.abort = 1;
+            __syncthreads();
+            if (sm.abort) break;
+            load_x(p, sm, (int64_t)j * BR, c0, c_colmajor);
+            __syncthreads();
+            mma_tile(sm.m, sm.x, BR, acc);
+            __syncthreads();
+        }
+        if (sm.abort) break;
+        // right-hand side of the diagonal block, then X = inv(M_ii) (alpha B - S)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) sm.x[(4 * ty + e) * NP + tx] = fmaf(p.alpha, b[e], -acc[e]);
+        __syncthreads();
+        float xo[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+        mma_tile(sm.inv, sm.x, 8 * ((t >> 5) + 1), xo);   // inv is lower: kk <= row
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const int64_t gi = i0 + 4 * ty + e, gj = c0 + tx;
+            if (gi < p.k && gj < p.nrhs) p.C[gi * p.c_rs + gj * p.c_cs] = xo[e];
+        }
+        __syncthreads();
+        if (t == 0) st_release(p.flags + (int64_t)pn * p.nbr + i, 1);
+    }
+}
+
+}  // namespace thin
+
+size_t thin_scratch_bytes(int64_t k, int64_t nrhs) {
+    const int64_t nbr = (k + kThinBlock - 1) / kThinBlock;
+    const int64_t npan = (nrhs + kThinPanel - 1) / kThinPanel;
+    return (size_t)(2 + nbr * npan) * sizeof(int);
+}
+
+static int g_thin_ctas_per_sm = 0;
+
+cudaError_t thin_configure() {
+    cudaError_t e = cudaFuncSetAttribute(thin::thin_trsm_kernel,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)sizeof(thin::Smem));
+    if (e != cudaSuccess) return e;
+    int n = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, thin::thin_trsm_kernel, thin::NT,
+                                                      sizeof(thin::Smem));
+    if (e != cudaSuccess) return e;
+    g_thin_ctas_per_sm = n > 0 ? n : 1;
+    return cudaSuccess;
+}
+
+cudaError_t launch_thin_trsm(const Canon<float>& c, float alpha, int* scratch, int* err,
+                             long long wait_ns, int num_sms, cudaStream_t s) {
+    if (c.k <= 0 || c.nrhs <= 0) return cudaSuccess;
+    thin::Params p;
+    p.k = c.k;
+    p.nrhs = c.nrhs;
+    p.A = c.A;
+    p.a_rs = c.a_rs;
+    p.a_cs = c.a_cs;
+    p.C = c.C;
+    p.c_rs = c.c_rs;
+    p.c_cs = c.c_cs;
+    p.alpha = alpha;
+    p.unit = c.unit ? 1 : 0;
+    const int64_t nbr = (c.k + kThinBlock - 1) / kThinBlock;
+    const int64_t npan = (c.nrhs + kThinPanel - 1) / kThinPanel;
+    if (nbr * npan > (int64_t)1 << 30) return cudaErrorInvalidValue;
+    p.nbr = (int)nbr;
+    p.npan = (int)npan;
+    p.ntask = nbr * npan;
+    p.ticket = scratch;
+    p.stop = scratch + 1;
+    p.flags = scratch + 2;
+    p.err = err;
+    p.wait_ns = wait_ns;
+    cudaError_t e = cudaMemsetAsync(scratch, 0, thin_scratch_bytes(c.k, c.nrhs), s);
+    if (e != cudaSuccess) return e;
+    const int per_sm = g_thin_ctas_per_sm > 0 ? g_thin_ctas_per_sm : 1;
+    const int64_t cap = (int64_t)num_sms * per_sm;
+    const int grid = (int)(p.ntask < cap ? p.ntask : cap);
+    thin::thin_trsm_kernel<<<grid, thin::NT, sizeof(thin::Smem), s>>>(p);
+    return cudaGetLastError();
+}
+
+}  // namespace trx

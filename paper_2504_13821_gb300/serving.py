@@ -20,7 +20,8 @@ class Server:
 
     def __init__(self, device=0, streams: int = 4, budget_bytes: int = 150 << 30,
                  max_inflight: int = 4096, small_k: int = 512, workspace_bytes: int = 0,
-                 graphs: bool = True, refine_corrections: int = 2, fp64_corrections: int = 0):
+                 graphs: bool = True, refine_corrections: int = 2, fp64_corrections: int = 0,
+                 fp64_trmm: int = 0):
         import torch
         self.torch = torch
         self.device = torch.device("cuda", device if isinstance(device, int) else
@@ -28,7 +29,7 @@ class Server:
         lib = _binding.load_library()
         cfg = _binding.ServerConfig(streams, small_k, max_inflight, budget_bytes,
                                     workspace_bytes, int(graphs), refine_corrections,
-                                    fp64_corrections)
+                                    fp64_corrections, fp64_trmm)
         h = ctypes.c_void_p()
         _binding._check(lib.trx_server_create(self.device.index, ctypes.byref(cfg),
                                               ctypes.byref(h)), "trx_server_create")

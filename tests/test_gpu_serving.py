@@ -107,15 +107,16 @@ def test_server_budget_and_release():
     srv.close()
 
 
-@pytest.mark.parametrize("refine_corr,fp64_corr", [(2, 3), (1, 2)])
-def test_serving_refined_and_mixed_fp64_kinds(refine_corr, fp64_corr):
+@pytest.mark.parametrize("refine_corr,fp64_corr,fp64_trmm", [(2, 3, 0), (1, 2, 1)])
+def test_serving_refined_and_mixed_fp64_kinds(refine_corr, fp64_corr, fp64_trmm):
     """Refined FP32 TRSM requests (FP64 result, float-float corrections) and
     FP64 TRSM on the mixed engine (FP32 solve + corrections) in one mix with
-    plain FP32/FP64 TRMM: every refined result has the backward error of an
-    FP64 solve (8 k 2^-53 against the oracle), every FP64 TRSM too, and
-    each result is bit-identical to the same request served alone; with
-    two / three corrections and with the one / two the serving benchmark
-    uses."""
+    FP32 TRMM and FP64 TRMM (DFMA, or one float-float pass): every refined
+    result has the backward error of an FP64 solve (8 k 2^-53 against the
+    oracle), every FP64 TRSM too, every TRMM is inside 8 k u, and each
+    result is bit-identical to the same request served alone; with two /
+    three corrections and DFMA TRMM, and with the one / two corrections and
+    float-float TRMM the serving benchmark uses."""
     from paper_2504_13821_gb300 import serving
     dev = torch.device("cuda", 0)
     rng = np.random.default_rng(41)
@@ -138,7 +139,8 @@ def test_serving_refined_and_mixed_fp64_kinds(refine_corr, fp64_corr):
 
     def run(sel, spread):
         srv = serving.Server(0, streams=3, budget_bytes=1 << 30, max_inflight=64,
-                             refine_corrections=refine_corr, fp64_corrections=fp64_corr)
+                             refine_corrections=refine_corr, fp64_corrections=fp64_corr,
+                             fp64_trmm=fp64_trmm)
         ids = [srv.register(to_dev(A, dev), u, t, "N") for (A, u, t, _) in facs]
         outs, status = [], {}
         t0 = time.perf_counter()

@@ -1,0 +1,109 @@
+"""The persistent CUDA-core FP32 TRSM for thin right-hand sides
+(TRX_OPT_THIN, csrc/thin.cu): 64-row blocks x 16-column panels solved
+left-looking in one launch, diagonal blocks by their inverses, against the
+FP64 oracle and the recursive chain.
+
+- all 16 variants at ragged orders (300, 1000) with 1, 17 and 64
+  right-hand sides, alpha 1.5 / -2, padded lda / ldb (padding untouched):
+  the normwise backward error within 8 k u of FP32, element by element
+  through the oracle;
+- forced on beyond the automatic range: order 40 (one block, rows past the
+  order), 1024 with 200 right-hand sides (13 panels, a ragged last one);
+- order 8192 with 16 right-hand sides (128 block rows): sampled columns
+  against the oracle, bitwise repeatable, within the FP32 bound of the
+  recursive chain; the default (automatic) mode takes this path;
+- a bounded wait run out (1 microsecond budget) is reported as
+  TRX_ERR_TIMEOUT and the next call with the normal budget is correct.
+"""
+import numpy as np
+import pytest
+
+from helpers import bound, run_case, to_dev
+import oracle
+from paper_2504_13821_gb300 import inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+VARIANTS = inputs.VARIANTS
+
+
+@pytest.fixture(scope="module")
+def trx():
+    import paper_2504_13821_gb300 as trx
+    return trx
+
+
+def thin_handle(trx, mode=1):
+    h = trx.Handle(0)
+    h.set_option(trx.OPT_THIN, mode)
+    assert h.get_option(trx.OPT_THIN) == mode
+    return h
+
+
+@pytest.mark.parametrize("side,uplo,trans,diag", VARIANTS)
+def test_thin_all_variants(trx, side, uplo, trans, diag):
+    h = thin_handle(trx)
+    vi = VARIANTS.index((side, uplo, trans, diag))
+    for k, nrhs, alpha, pads in ((300, 1, 1.5, (0, 0)), (300, 17, -2.0, (3, 5)),
+                                 (1000, 64, 1.5, (0, 7))):
+        m, n = (k, nrhs) if side == "L" else (nrhs, k)
+        run_case("trsm", side, uplo, trans, diag, m, n, alpha, np.float32,
+                 seed=inputs.variant_seed(k + nrhs, vi), handle=h, lda_pad=pads[0],
+                 ldb_pad=pads[1])
+    assert h.check_device_error() == 0
+    h.close()
+
+
+def test_thin_forced_small_order_and_many_panels(trx):
+    h = thin_handle(trx)
+    run_case("trsm", "L", "U", "N", "U", 40, 9, 1.25, np.float32, seed=41, handle=h)
+    run_case("trsm", "R", "L", "T", "N", 33, 40, -1.0, np.float32, seed=42, handle=h)
+    run_case("trsm", "L", "L", "N", "N", 1024, 200, 1.5, np.float32, seed=43, handle=h)
+    run_case("trsm", "R", "U", "T", "N", 200, 1024, 1.5, np.float32, seed=44, handle=h)
+    assert h.check_device_error() == 0
+    h.close()
+
+
+def test_thin_large_order_sampled_repeatable_and_against_chain(trx):
+    k, n = 8192, 16
+    A, B = inputs.problem("L", "L", k, n, seed=8192, dtype=np.float32)
+    At = to_dev(A, "cuda:0")
+    h = trx.Handle(0)                                   # automatic: the thin solve
+    outs = []
+    for _ in range(2):
+        Bt = to_dev(B, "cuda:0")
+        trx.trsm("L", "L", "N", "N", 1.5, At, Bt, handle=h)
+        outs.append(Bt)
+    hc = thin_handle(trx, -1)
+    Bc = to_dev(B, "cuda:0")
+    trx.trsm("L", "L", "N", "N", 1.5, At, Bc, handle=hc)
+    torch.cuda.synchronize()
+    assert torch.equal(outs[0], outs[1]), "not bitwise repeatable"
+    X = outs[0].cpu().numpy().astype(np.float64)
+    Xc = Bc.cpu().numpy().astype(np.float64)
+    ninf = lambda a: np.abs(a).sum(axis=1).max()          # noqa: E731
+    assert ninf(X - Xc) <= bound(k, np.float32) * ninf(Xc)
+    cols = np.array([0, 5, 11, 15])
+    eta = oracle.trsm_backward_error("L", "L", "N", "N", 1.5, A.astype(np.float64),
+                                     np.asfortranarray(X[:, cols]),
+                                     np.asfortranarray(B[:, cols].astype(np.float64)))["eta"]
+    assert eta <= bound(k, np.float32), eta
+    assert h.check_device_error() == 0
+    h.close()
+    hc.close()
+
+
+def test_thin_bounded_wait_reports_timeout(trx):
+    h = thin_handle(trx)
+    h.set_option(trx.OPT_GRAPH, 0)
+    assert h.check_device_error() == 0
+    h.set_option(trx.OPT_WAIT_LIMIT, 1000)            # 1 us: the waits run out
+    run_case("trsm", "L", "L", "N", "N", 4096, 16, 1.0, np.float32, seed=6, handle=h,
+             check=False)
+    assert h.check_device_error() == 4                # TRX_ERR_TIMEOUT
+    assert h.check_device_error() == 0
+    h.set_option(trx.OPT_WAIT_LIMIT, 2_000_000_000)
+    run_case("trsm", "L", "L", "N", "N", 4096, 16, 1.0, np.float32, seed=6, handle=h)
+    assert h.check_device_error() == 0
+    h.close()
