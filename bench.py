@@ -1052,7 +1052,8 @@ def run_serving(args):
     # per-stream workspace for the largest FP32 call of the mix (order 8192,
     # 1024 right-hand sides: BF16 operand planes of about 0.3 GB), made up
     # front so no request waits for a workspace to grow
-    srv = serving.Server(0, streams=4, budget_bytes=150 << 30, max_inflight=4096,
+    srv = serving.Server(0, streams=args.server_streams, budget_bytes=150 << 30,
+                         max_inflight=4096,
                          workspace_bytes=args.server_workspace_mb << 20,
                          graphs=args.server_graphs,
                          refine_corrections=args.refine_corrections,
@@ -1184,6 +1185,7 @@ def run_serving(args):
                                    + ("one float-float pass" if args.fp64_trmm else "DFMA")
                                    + ", factors reused "
                                    "1..50 times, 150 GB admission cap, native request server, "
+                                   f"{args.server_streams} streams, "
                                    f"{args.server_workspace_mb} MB workspace per stream, "
                                    + ("cached graphs" if args.server_graphs else
                                       "direct launches"),
@@ -1244,6 +1246,8 @@ def main(argv=None):
                          "arrivals; refined: FP32 TRSM refined in FP64 (k 8192, 256 "
                          "right-hand sides unless --k/--nrhs say otherwise)")
     ap.add_argument("--count", type=int, default=4096, help="problems (batched workload)")
+    ap.add_argument("--server-streams", type=int, default=8,
+                    help="serving: parallel streams (one handle each) for large requests")
     ap.add_argument("--server-graphs", action="store_true",
                     help="serving: large requests replay cached graphs (one capture per new "
                          "buffer set) instead of launching directly")

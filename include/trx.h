@@ -160,7 +160,8 @@ enum {
                               factor keeps the split it was created with. */
     TRX_OPT_FP64_TRSM = 12,/* trx_dtrsm's engine: 0 (default) the recursive
                               FP64 solve (CUDA-core DFMA updates); n in
-                              1..16: the mixed form, the FP32 solve on
+                              1..16: for orders of at least 64 (below, the
+                              recursive solve) the mixed form, the FP32 solve on
                               fl32(A) then n corrections with the residual
                               alpha B - op(A) X in float-float arithmetic on
                               the FP32 pipes (A and X as float pairs, about
@@ -208,7 +209,7 @@ enum {
                               a zero B). Entries must lie inside FP32's
                               exponent range (as for TRX_OPT_FP64_TRSM).
                               Uses the handle's refinement scratch        */
-    TRX_OPT_THIN = 17      /* FP32 TRSM with few right-hand sides: 1 = one
+    TRX_OPT_THIN = 17,     /* FP32 TRSM with few right-hand sides: 1 = one
                               persistent CUDA-core launch in place of the
                               recursion (64-row blocks x 16-column panels,
                               left-looking: each block row adds its products
@@ -221,6 +222,12 @@ enum {
                               right-hand sides, or at most 256 while order
                               x right-hand sides <= 2^20). Its flags live
                               in a small handle buffer grown on first use */
+    TRX_OPT_TEST_WITHHOLD = 18 /* test hook for the bounded waits: 1 = the
+                              thin TRSM (TRX_OPT_THIN) never publishes its
+                              first block row, so the waits of the blocks
+                              after it run out and the call leaves
+                              TRX_ERR_TIMEOUT for trx_check_device_error
+                              (B is then not the solution). 0 (default)  */
 };
 
 /* Kernel classes reported by trx_get_profile(). */
@@ -501,7 +508,9 @@ int trx_batched_set_tuning(trx_handle_t handle, int elem_bytes, const int* table
 typedef struct trx_server_s* trx_server_t;
 typedef struct {
     int streams;            /* streams (and handles) for large requests, 1..16 (4)  */
-    int small_k;            /* orders up to this go to trx_batched, 0..512 (512)    */
+    int small_k;            /* orders up to this go to trx_batched, 0..512 (512);
+                               FP64 problems only while k^2 n <= 2^20 (one CTA
+                               each there, on the FP64 pipe)                     */
     int64_t max_inflight;   /* requests admitted and not yet completed (4096)       */
     size_t budget_bytes;    /* device bytes admitted requests may hold (150 GiB)    */
     size_t workspace_bytes; /* per-stream workspace made at creation (0); a larger

@@ -50,6 +50,7 @@ constexpr long long kDefaultWaitNs = 2000000000LL;   // 2 s
 constexpr size_t kGraphCacheSize = 16;
 constexpr int64_t kBatchMaxK = TRX_BATCH_MAX_K;
 constexpr int kMaxPanels = 4;
+constexpr int kBatchSlots = 4;     // batched descriptor staging slots per handle
 // Auto stays at one chain: measured at m = n = 16384, 2 and 4 branches were
 // slower (the persistent GEMM update takes every SM, so branches serialise).
 
@@ -210,11 +211,15 @@ struct trx_handle_s {
     uint64_t tick = 0;
     std::vector<unsigned char> maps;
     // batched path: device descriptors + counter, pinned staging, tuning
-    BatchDesc* b_dev = nullptr;
+    // batched descriptors: a ring of staging slots (pinned host + device
+    // copy + upload event), so an upload waits only for the launch kBatchSlots
+    // back, not for the one before it
+    BatchDesc* b_dev_ring[kBatchSlots] = {};
+    BatchDesc* b_host_ring[kBatchSlots] = {};
+    cudaEvent_t b_uploaded_ring[kBatchSlots] = {};
+    int b_slot = 0;
     int* b_counter = nullptr;
-    BatchDesc* b_host = nullptr;
     int64_t b_cap = 0;
-    cudaEvent_t b_uploaded = nullptr;
     // batched substitution block height per [element type][order bucket]
     // [right-hand-side bucket] (trx_batched_autotune); 8 until tuned
     int tune_sb[2][TRX_TUNE_K_BUCKETS][TRX_TUNE_N_BUCKETS] = {};
@@ -228,6 +233,7 @@ struct trx_handle_s {
     size_t rf_bytes = 0;
     // thin-right-hand-side TRSM: task counter and block flags (grown on demand)
     int64_t opt_thin = 0;
+    int64_t opt_test_withhold = 0;   // test hook (TRX_OPT_TEST_WITHHOLD)
     int* thin_buf = nullptr;
     size_t thin_bytes = 0;
     cudaStream_t aux[kMaxPanels] = {};
@@ -391,7 +397,7 @@ struct Exec {
                 case kThin:
                     e = launch_thin_trsm(*reinterpret_cast<const Canon<float>*>(&c),
                                          (float)st.alpha, thin_scratch, h->d_err, h->wait_ns,
-                                         h->num_sms, s);
+                                         h->num_sms, s, h->opt_test_withhold != 0);
                     cls = TRX_KERNEL_LEAF_TRSM;
                     flops = (double)c.k * c.k * c.nrhs;
                     bytes = 4.0 * ((double)c.k * (c.k + 1) / 2 + 2.0 * c.k * c.nrhs);
@@ -467,9 +473,10 @@ int refine_scratch(trx_handle_t h, size_t need, cudaStream_t s);
 int pair_trmm(trx_handle_t h, char side, char uplo, char transa, char diag, int64_t m, int64_t n,
               double alpha, const double* A, int64_t lda, double* B, int64_t ldb,
               cudaStream_t s);
-// Smallest order the float-float FP64 TRMM takes: its error, a few 2^-48
-// of |op(A)||B| per element, is inside 8 k u of FP64 from here on.
-constexpr int64_t kPairTrmmMinK = 64;
+// Smallest order the float-float FP64 engines take (the TRMM pass, the
+// mixed TRSM's residual): their error, a few 2^-48 of |op(A)||B| per
+// element, is inside 8 k u of FP64 from here on.
+constexpr int64_t kPairMinK = 64;
 
 template <typename T>
 int execute(trx_handle_t h, bool trsm, char side, char uplo, char transa, char diag, int64_t m,
@@ -487,12 +494,13 @@ int execute(trx_handle_t h, bool trsm, char side, char uplo, char transa, char d
         e = launch_zero<T>(B, m, n, ldb, s);
         return e == cudaSuccess ? TRX_SUCCESS : fail_cuda(e, "zero");
     }
-    if (std::is_same<T, double>::value && trsm && h->opt_fp64_trsm > 0)
+    if (std::is_same<T, double>::value && trsm && h->opt_fp64_trsm > 0 &&
+        (upc(side) == 'L' ? m : n) >= kPairMinK)
         return refine_fixed(h, true, side, uplo, transa, diag, m, n, (double)alpha, A, lda, B,
                             ldb, reinterpret_cast<double*>(B), ldb, (int)h->opt_fp64_trsm,
                             stream);
     if (std::is_same<T, double>::value && !trsm && h->opt_fp64_trmm > 0 &&
-        (upc(side) == 'L' ? m : n) >= kPairTrmmMinK)
+        (upc(side) == 'L' ? m : n) >= kPairMinK)
         return pair_trmm(h, side, uplo, transa, diag, m, n, (double)alpha,
                          reinterpret_cast<const double*>(A), lda, reinterpret_cast<double*>(B),
                          ldb, s);
@@ -694,7 +702,7 @@ int execute(trx_handle_t h, bool trsm, char side, char uplo, char transa, char d
     key.b = b;
     key.slices = plan.tc ? slices : 0;
     key.dag = dag;
-    key.thin = thin;
+    key.thin = thin ? 1 + (int)h->opt_test_withhold : 0;
     key.k = k;
     key.nrhs = ex.c.nrhs;
     key.a_rs = ex.c.a_rs;
@@ -882,41 +890,46 @@ int batch_run(trx_handle_t h, int elem_bytes, const std::vector<BatchDesc>& d, c
     if (n == 0) return TRX_SUCCESS;
     cudaError_t e;
     if (n > h->b_cap) {
-        if (h->b_uploaded) cudaEventSynchronize(h->b_uploaded);
-        if (h->b_dev) cudaFree(h->b_dev);
-        if (h->b_host) cudaFreeHost(h->b_host);
-        h->b_dev = nullptr;
-        h->b_host = nullptr;
+        for (int i = 0; i < kBatchSlots; ++i) {
+            if (h->b_uploaded_ring[i]) cudaEventSynchronize(h->b_uploaded_ring[i]);
+            if (h->b_dev_ring[i]) cudaFree(h->b_dev_ring[i]);
+            if (h->b_host_ring[i]) cudaFreeHost(h->b_host_ring[i]);
+            h->b_dev_ring[i] = nullptr;
+            h->b_host_ring[i] = nullptr;
+        }
         h->b_cap = 0;
         const int64_t cap = std::max<int64_t>(n, 1024);
-        if ((e = cudaMalloc(&h->b_dev, cap * sizeof(BatchDesc))) != cudaSuccess ||
-            (e = cudaMallocHost(&h->b_host, cap * sizeof(BatchDesc))) != cudaSuccess)
-            return fail_cuda(e, "batch buffers");
+        for (int i = 0; i < kBatchSlots; ++i)
+            if ((e = cudaMalloc(&h->b_dev_ring[i], cap * sizeof(BatchDesc))) != cudaSuccess ||
+                (e = cudaMallocHost(&h->b_host_ring[i], cap * sizeof(BatchDesc))) != cudaSuccess)
+                return fail_cuda(e, "batch buffers");
         h->b_cap = cap;
         drop_graphs(h);
     }
     if (!h->b_counter && (e = cudaMalloc(&h->b_counter, 256)) != cudaSuccess)
         return fail_cuda(e, "batch counter");
-    if (!h->b_uploaded &&
-        (e = cudaEventCreateWithFlags(&h->b_uploaded, cudaEventDisableTiming)) != cudaSuccess)
+    const int slot = h->b_slot;
+    h->b_slot = (slot + 1) % kBatchSlots;
+    cudaEvent_t& up = h->b_uploaded_ring[slot];
+    if (!up && (e = cudaEventCreateWithFlags(&up, cudaEventDisableTiming)) != cudaSuccess)
         return fail_cuda(e, "batch event");
-    if ((e = cudaEventSynchronize(h->b_uploaded)) != cudaSuccess)
-        return fail_cuda(e, "batch staging wait");
-    std::memcpy(h->b_host, d.data(), n * sizeof(BatchDesc));
-    if ((e = cudaMemcpyAsync(h->b_dev, h->b_host, n * sizeof(BatchDesc), cudaMemcpyHostToDevice,
-                             s)) != cudaSuccess ||
-        (e = cudaEventRecord(h->b_uploaded, s)) != cudaSuccess)
+    if ((e = cudaEventSynchronize(up)) != cudaSuccess) return fail_cuda(e, "batch staging wait");
+    BatchDesc* const b_dev = h->b_dev_ring[slot];
+    std::memcpy(h->b_host_ring[slot], d.data(), n * sizeof(BatchDesc));
+    if ((e = cudaMemcpyAsync(b_dev, h->b_host_ring[slot], n * sizeof(BatchDesc),
+                             cudaMemcpyHostToDevice, s)) != cudaSuccess ||
+        (e = cudaEventRecord(up, s)) != cudaSuccess)
         return fail_cuda(e, "batch upload");
     // persistent CTAs: as many per SM as fit (shared memory bound)
     const int grid = h->num_sms * batched_ctas_per_sm(elem_bytes);
     cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
     cudaStreamIsCapturing(s, &cap);
     if (!use_graph || cap != cudaStreamCaptureStatusNone) {
-        e = launch_batched(elem_bytes, h->b_dev, n, h->b_counter, grid, s);
+        e = launch_batched(elem_bytes, b_dev, n, h->b_counter, grid, s);
         return e == cudaSuccess ? TRX_SUCCESS : fail_cuda(e, "batched launch");
     }
     char kbuf[64];
-    snprintf(kbuf, sizeof(kbuf), "batched:%d:%lld:%p", elem_bytes, (long long)n, (void*)h->b_dev);
+    snprintf(kbuf, sizeof(kbuf), "batched:%d:%lld:%p", elem_bytes, (long long)n, (void*)b_dev);
     const std::string ks(kbuf);
     ++h->tick;
     for (auto& g : h->graphs) {
@@ -929,7 +942,7 @@ int batch_run(trx_handle_t h, int elem_bytes, const std::vector<BatchDesc>& d, c
     if ((e = cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal)) !=
         cudaSuccess)
         return fail_cuda(e, "cudaStreamBeginCapture");
-    const cudaError_t le = launch_batched(elem_bytes, h->b_dev, n, h->b_counter, grid, h->cap_stream);
+    const cudaError_t le = launch_batched(elem_bytes, b_dev, n, h->b_counter, grid, h->cap_stream);
     cudaGraph_t graph = nullptr;
     e = cudaStreamEndCapture(h->cap_stream, &graph);
     if (le != cudaSuccess || e != cudaSuccess) {
@@ -1254,10 +1267,12 @@ int trx_destroy(trx_handle_t h) {
         cudaEventDestroy(p.e1);
     }
     for (auto ev : h->free_events) cudaEventDestroy(ev);
-    if (h->b_dev) cudaFree(h->b_dev);
+    for (int i = 0; i < kBatchSlots; ++i) {
+        if (h->b_dev_ring[i]) cudaFree(h->b_dev_ring[i]);
+        if (h->b_host_ring[i]) cudaFreeHost(h->b_host_ring[i]);
+        if (h->b_uploaded_ring[i]) cudaEventDestroy(h->b_uploaded_ring[i]);
+    }
     if (h->b_counter) cudaFree(h->b_counter);
-    if (h->b_host) cudaFreeHost(h->b_host);
-    if (h->b_uploaded) cudaEventDestroy(h->b_uploaded);
     if (h->rf_buf) {
         cudaFreeAsync(h->rf_buf, 0);        // stream-ordered allocation
         cudaDeviceSynchronize();
@@ -2047,6 +2062,10 @@ int trx_set_option(trx_handle_t h, int option, int64_t value) {
             if (value < -1 || value > 1) return TRX_ERR_INVALID_VALUE;
             h->opt_thin = value;
             break;
+        case TRX_OPT_TEST_WITHHOLD:
+            if (value != 0 && value != 1) return TRX_ERR_INVALID_VALUE;
+            h->opt_test_withhold = value;
+            break;
         default:
             return TRX_ERR_INVALID_VALUE;
     }
@@ -2074,6 +2093,7 @@ int trx_get_option(trx_handle_t h, int option, int64_t* value) {
         case TRX_OPT_TRSM_DAG: *value = h->opt_trsm_dag; break;
         case TRX_OPT_FP64_TRMM: *value = h->opt_fp64_trmm; break;
         case TRX_OPT_THIN: *value = h->opt_thin; break;
+        case TRX_OPT_TEST_WITHHOLD: *value = h->opt_test_withhold; break;
         default: return TRX_ERR_INVALID_VALUE;
     }
     return TRX_SUCCESS;

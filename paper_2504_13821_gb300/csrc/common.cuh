@@ -287,8 +287,11 @@ cudaError_t launch_trsm_dag(const Canon<float>& p, const Planes& pl, __nv_bfloat
 // tasks. scratch: thin_scratch_bytes ints, zeroed by the launch itself.
 constexpr int kThinBlock = 64, kThinPanel = 16;
 size_t thin_scratch_bytes(int64_t k, int64_t nrhs);
+// withhold: test hook, block row 0 is never published, so the bounded waits
+// of the blocks after it run out (TRX_ERR_TIMEOUT).
 cudaError_t launch_thin_trsm(const Canon<float>& c, float alpha, int* scratch, int* err,
-                             long long wait_ns, int num_sms, cudaStream_t s);
+                             long long wait_ns, int num_sms, cudaStream_t s,
+                             bool withhold = false);
 
 // K granularity the tensor-core GEMM needs (klen and rk multiples of this).
 constexpr int kTcKQuantum = 64;

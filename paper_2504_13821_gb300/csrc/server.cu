@@ -11,7 +11,8 @@
 //   2. admit: queued requests, oldest first, while the budget (right-hand
 //      side bytes, plus the operand planes a tensor-core call uses) and the
 //      slot count allow; admission does not wait for the device to drain;
-//   3. launch: the admitted small problems (order <= small_k) go out as one
+//   3. launch: the admitted small problems (order <= small_k; FP64 ones up to
+//      a work limit) go out as one
 //      persistent batched launch per element type, the others one call each,
 //      round-robin over parallel streams with one handle (and workspace)
 //      per stream;
@@ -75,6 +76,7 @@ struct Req {
 
 struct Flight {
     cudaEvent_t done;
+    uint64_t seq;                        // launch order across lanes
     std::vector<int64_t> ids;
     std::vector<int> fids;
     size_t bytes;
@@ -94,7 +96,12 @@ struct trx_server_s {
     trx_handle_t bhandle = nullptr;
     std::vector<Fac> facs;
     std::deque<Req> waiting;
-    std::vector<Flight> inflight;
+    // launch groups in flight, one FIFO lane per stream (the large-request
+    // streams, then the batched stream): a stream completes its work in
+    // order, so retiring looks at lane fronts only and a poll costs
+    // O(streams + completed), not O(in flight)
+    std::vector<std::deque<Flight>> lanes;
+    uint64_t flight_seq = 0;
     size_t inflight_bytes = 0;
     int64_t inflight_reqs = 0;
     std::deque<std::pair<int64_t, int>> done;   // (request id, status) not yet reported
@@ -124,6 +131,18 @@ cudaError_t get_event(trx_server_t s, cudaEvent_t* ev) {
 }
 void put_event(trx_server_t s, cudaEvent_t ev) { s->pool.push_back(ev); }
 
+// Whether a request goes to the batched launch. That kernel gives each
+// problem one CTA; an FP64 problem of more than kSmallFp64Work (k^2 n) would
+// hold its CTA for long on the slow FP64 pipe (about 0.15 ms at the limit),
+// so it goes to the streams, whose engines spread it over the GPU.
+constexpr double kSmallFp64Work = 1048576.0;
+bool is_small(const trx_server_s* s, const Req& r) {
+    const Fac& f = s->facs[r.fid];
+    if (f.k > s->cfg.small_k || r.op == 'R') return false;   // no refinement there
+    const double nrhs = (double)(upc(r.side) == 'L' ? r.n : r.m);
+    return f.elem == 4 || (double)f.k * (double)f.k * nrhs <= kSmallFp64Work;
+}
+
 // Device bytes a request holds while in flight: its right-hand side (and
 // result), plus the operand planes of a tensor-core FP32 call (three BF16
 // slices of the k x k triangle and of the k x nrhs right-hand side).
@@ -132,7 +151,7 @@ size_t cost_bytes(const trx_server_s* s, const Req& r) {
     const int64_t nrhs = upc(r.side) == 'L' ? r.n : r.m;
     size_t b = (size_t)r.m * (size_t)r.n * (size_t)f.elem;
     if (r.op == 'R') b += (size_t)r.m * (size_t)r.n * 8;
-    const bool tc_call = f.k > s->cfg.small_k || r.op == 'R';
+    const bool tc_call = !is_small(s, r);
     const bool fp32_solve = f.elem == 4 || (upc(r.op) == 'S' && s->cfg.fp64_corrections > 0);
     if (tc_call && fp32_solve) b += 6 * (size_t)f.k * (size_t)(f.k + nrhs);
     return b;
@@ -226,7 +245,8 @@ int launch_large(trx_server_t s, Req& r) {
     fl.fids.push_back(r.fid);
     fl.bytes = r.cost;
     put_event(s, r.ready);
-    s->inflight.push_back(std::move(fl));
+    fl.seq = s->flight_seq++;
+    s->lanes[i].push_back(std::move(fl));
     s->inflight_reqs += 1;
     return TRX_SUCCESS;
 }
@@ -277,32 +297,31 @@ int launch_small(trx_server_t s, std::vector<Req>& group, int elem) {
         put_event(s, r.ready);
     }
     s->inflight_reqs += (int64_t)group.size();
-    s->inflight.push_back(std::move(fl));
+    fl.seq = s->flight_seq++;
+    s->lanes[s->lanes.size() - 1].push_back(std::move(fl));
     return TRX_SUCCESS;
 }
 
 // Retire finished launch groups; returns a CUDA error if a query failed.
 int retire(trx_server_t s) {
     int first_err = TRX_SUCCESS;
-    std::vector<Flight> still;
-    still.reserve(s->inflight.size());
-    for (Flight& fl : s->inflight) {
-        const cudaError_t q = cudaEventQuery(fl.done);
-        if (q == cudaErrorNotReady) {
-            still.push_back(std::move(fl));
-            continue;
+    for (auto& lane : s->lanes) {
+        while (!lane.empty()) {
+            Flight& fl = lane.front();
+            const cudaError_t q = cudaEventQuery(fl.done);
+            if (q == cudaErrorNotReady) break;
+            const int status = q == cudaSuccess ? TRX_SUCCESS : fail(q, "launch group");
+            if (status != TRX_SUCCESS && first_err == TRX_SUCCESS) first_err = status;
+            for (size_t j = 0; j < fl.ids.size(); ++j) {
+                s->done.emplace_back(fl.ids[j], status);
+                s->facs[fl.fids[j]].outstanding -= 1;
+            }
+            s->inflight_bytes -= fl.bytes;
+            s->inflight_reqs -= (int64_t)fl.ids.size();
+            put_event(s, fl.done);
+            lane.pop_front();
         }
-        const int status = q == cudaSuccess ? TRX_SUCCESS : fail(q, "launch group");
-        if (status != TRX_SUCCESS && first_err == TRX_SUCCESS) first_err = status;
-        for (size_t j = 0; j < fl.ids.size(); ++j) {
-            s->done.emplace_back(fl.ids[j], status);
-            s->facs[fl.fids[j]].outstanding -= 1;
-        }
-        s->inflight_bytes -= fl.bytes;
-        s->inflight_reqs -= (int64_t)fl.ids.size();
-        put_event(s, fl.done);
     }
-    s->inflight.swap(still);
     return first_err;
 }
 
@@ -336,6 +355,7 @@ int trx_server_create(int device, const trx_server_config_t* config, trx_server_
     if (!s) return TRX_ERR_ALLOC;
     s->device = device;
     s->cfg = cfg;
+    s->lanes.resize((size_t)cfg.streams + 1);
     int rc = TRX_SUCCESS;
     for (int i = 0; i < cfg.streams && rc == TRX_SUCCESS; ++i) {
         cudaStream_t st = nullptr;
@@ -384,7 +404,8 @@ int trx_server_destroy(trx_server_t s) {
     for (cudaStream_t st : s->streams) cudaStreamSynchronize(st);
     for (cudaStream_t st : s->streams) cudaStreamDestroy(st);
     if (s->bstream) cudaStreamDestroy(s->bstream);
-    for (Flight& fl : s->inflight) cudaEventDestroy(fl.done);
+    for (auto& lane : s->lanes)
+        for (Flight& fl : lane) cudaEventDestroy(fl.done);
     for (Req& r : s->waiting) cudaEventDestroy(r.ready);
     for (cudaEvent_t ev : s->pool) cudaEventDestroy(ev);
     s->magic = 0;
@@ -533,7 +554,7 @@ int trx_server_poll(trx_server_t s, int64_t* ids, int* status, int capacity, int
         }
         s->inflight_bytes += r.cost;
         const Fac& f = s->facs[r.fid];
-        if (f.k <= s->cfg.small_k && r.op != 'R')   // the batched kernel has no refinement
+        if (is_small(s, r))
             (f.elem == 4 ? small4 : small8).push_back(r);
         else
             large.push_back(r);
@@ -586,8 +607,10 @@ int trx_server_wait(trx_server_t s) {
     cudaError_t e = cudaSetDevice(s->device);
     if (e != cudaSuccess) return fail(e, "cudaSetDevice");
     // the oldest launch group: waiting on it frees budget for the queue
-    if (!s->inflight.empty() && (e = cudaEventSynchronize(s->inflight.front().done)) != cudaSuccess)
-        return fail(e, "wait");
+    const Flight* oldest = nullptr;
+    for (const auto& lane : s->lanes)
+        if (!lane.empty() && (!oldest || lane.front().seq < oldest->seq)) oldest = &lane.front();
+    if (oldest && (e = cudaEventSynchronize(oldest->done)) != cudaSuccess) return fail(e, "wait");
     return TRX_SUCCESS;
 }
 

@@ -55,49 +55,73 @@ struct Params {
     int64_t ntask;
     int* ticket;     // next task
     int* stop;       // set by a CTA whose wait ran out: the others stop waiting
-    int* flags;      // [p * nbr + i]: 1 once X_ip is in C
+    // published blocks: X_ip as 64 x 16 tagged words (FP32 bits, tag 1 in
+    // the high half), tile (p, i) at words [(p nbr + i) 1024, + 1024),
+    // row-major; zeroed by the launch's memset, so a tag of 1 means "this
+    // element of this launch"
+    unsigned long long* xt;
     int* err;
     long long wait_ns;
+    int withhold;    // test hook: block row 0 is never published (waits run out)
 };
 
 struct Smem {
     float m[BR * LD];        // M_ij tile, k-major: m[kk * LD + r] = M[i0 + r][j0 + kk]
     float inv[BR * LD];      // inv(M_ii), k-major: inv[kk * LD + r] = Inv[r][kk]
+    float z[BR * LD];        // Z = inv(M_ii) M_i,i-1, k-major
     float x[BR * NP];        // X_jp tile / right-hand side: x[kk * NP + c]
     float dinv[BR];
     int task;
     int abort;
 };
+constexpr unsigned long long kTag = 1ull << 32;
+
+__device__ __forceinline__ unsigned long long ld_relaxed64(const unsigned long long* p) {
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.b64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_relaxed64(unsigned long long* p, unsigned long long v) {
+    asm volatile("st.relaxed.gpu.global.b64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
 
 __device__ __forceinline__ uint64_t gtimer() {
     uint64_t t;
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
     return t;
 }
-__device__ __forceinline__ int ld_acquire(const int* p) {
-    int v;
-    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
-__device__ __forceinline__ void st_release(int* p, int v) {
-    asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-
-// Thread 0: wait until *f is set, at most wait_ns. False on timeout (the
-// error word and the launch's stop word are set) or once another CTA has
-// stopped the launch.
-__device__ bool wait_flag(const Params& p, const int* f) {
-    if (ld_acquire(f)) return true;
-    const uint64_t t0 = gtimer();
-    while (true) {
-        if (ld_acquire(f)) return true;
-        if (*(volatile int*)p.stop) return false;
-        if (gtimer() - t0 > (uint64_t)p.wait_ns) {
-            atomicExch(p.err, kTimeout);
-            atomicExch(p.stop, 1);
-            return false;
+// X_jp into sm.x from its tagged words: each thread waits for its four
+// words (single-copy atomic 64-bit loads: value and tag arrive together),
+// at most wait_ns. False on timeout (the error word and the launch's stop
+// word are set) or once another CTA has stopped the launch.
+__device__ bool take_x(const Params& p, Smem& sm, int pn, int j) {
+    const unsigned long long* src = p.xt + ((int64_t)pn * p.nbr + j) * (BR * NP);
+    const int t = threadIdx.x;
+    constexpr int Q = (BR * NP) / NT;
+    unsigned long long w[Q];
+#pragma unroll
+    for (int q = 0; q < Q; ++q) w[q] = ld_relaxed64(src + t + NT * q);   // all in flight
+    bool ok = true;
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+        const int idx = t + NT * q;
+        unsigned long long v = w[q];
+        if (v < kTag) {
+            const uint64_t t0 = gtimer();
+            while ((v = ld_relaxed64(src + idx)) < kTag) {
+                if (*(volatile int*)p.stop) { ok = false; break; }
+                if (gtimer() - t0 > (uint64_t)p.wait_ns) {
+                    atomicExch(p.err, kTimeout);
+                    atomicExch(p.stop, 1);
+                    ok = false;
+                    break;
+                }
+            }
+            if (!ok) break;
         }
+        sm.x[idx] = __uint_as_float((unsigned)v);
     }
+    return ok;
 }
 
 // Tile (i0.., j0..) of M into registers, 16 elements a thread, along M's
@@ -123,21 +147,6 @@ __device__ __forceinline__ void store_m(Smem& sm, bool colmajor, const float (&r
         const int rr = colmajor ? (t & 63) : (t >> 6) + 4 * q;
         const int cc = colmajor ? (t >> 6) + 4 * q : (t & 63);
         sm.m[cc * LD + rr] = r[q];
-    }
-}
-
-// X_jp (rows j0.., panel columns c0..) from C into shared memory, through
-// L2 (another CTA wrote it during this launch).
-__device__ __forceinline__ void load_x(const Params& p, Smem& sm, int64_t j0, int64_t c0,
-                                       bool c_colmajor) {
-    const int t = threadIdx.x;
-#pragma unroll
-    for (int q = 0; q < (BR * NP) / NT; ++q) {
-        const int kk = c_colmajor ? (t & 63) : (t >> 4) + 16 * q;
-        const int c = c_colmajor ? (t >> 6) + 4 * q : (t & 15);
-        const int64_t gi = j0 + kk, gj = c0 + c;
-        sm.x[kk * NP + c] =
-            (gi < p.k && gj < p.nrhs) ? __ldcg(p.C + gi * p.c_rs + gj * p.c_cs) : 0.0f;
     }
 }
 
@@ -209,12 +218,49 @@ __device__ void invert_diag(const Params& p, Smem& sm, int64_t i0) {
     __syncthreads();
 }
 
+// Z = inv(M_ii) M_i,i-1 into sm.z (k-major), M_i,i-1 staged row-major in
+// sm.m; thread (ty, tx) forms rows 4 ty .. 4 ty + 3, columns tx + 16 u
+// (inv is lower: terms q < 8 (warp + 1) only).
+__device__ void make_z(const Params& p, Smem& sm, int64_t i0, bool colmajor) {
+    float r[16];
+    load_m(p, i0, i0 - BR, colmajor, r);
+    const int t = threadIdx.x, ty = t >> 4, tx = t & 15;
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+        const int rr = colmajor ? (t & 63) : (t >> 6) + 4 * q;
+        const int cc = colmajor ? (t >> 6) + 4 * q : (t & 63);
+        sm.m[rr * LD + cc] = r[q];
+    }
+    __syncthreads();
+    float acc[4][4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e)
+#pragma unroll
+        for (int u = 0; u < 4; ++u) acc[e][u] = 0.0f;
+    const int qend = 8 * ((t >> 5) + 1);
+    for (int q = 0; q < qend; ++q) {
+        const float4 iv = *reinterpret_cast<const float4*>(sm.inv + q * LD + 4 * ty);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const float mv = sm.m[q * LD + tx + 16 * u];
+            acc[0][u] = fmaf(iv.x, mv, acc[0][u]);
+            acc[1][u] = fmaf(iv.y, mv, acc[1][u]);
+            acc[2][u] = fmaf(iv.z, mv, acc[2][u]);
+            acc[3][u] = fmaf(iv.w, mv, acc[3][u]);
+        }
+    }
+#pragma unroll
+    for (int e = 0; e < 4; ++e)
+#pragma unroll
+        for (int u = 0; u < 4; ++u) sm.z[(tx + 16 * u) * LD + 4 * ty + e] = acc[e][u];
+    __syncthreads();
+}
+
 __global__ void __launch_bounds__(NT, 3) thin_trsm_kernel(const Params p) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Smem& sm = *reinterpret_cast<Smem*>(smem_raw);
     const int t = threadIdx.x, ty = t >> 4, tx = t & 15;
     const bool colmajor = p.a_rs == 1 || p.a_rs == -1;
-    const bool c_colmajor = p.c_rs == 1 || p.c_rs == -1;
     if (t == 0) sm.abort = 0;
     while (true) {
         __syncthreads();
@@ -232,34 +278,50 @@ __global__ void __launch_bounds__(NT, 3) thin_trsm_kernel(const Params p) {
             b[e] = (gi < p.k && gj < p.nrhs) ? __ldcg(p.C + gi * p.c_rs + gj * p.c_cs) : 0.0f;
         }
         invert_diag(p, sm, i0);
+        if (i > 0) make_z(p, sm, i0, colmajor);
+        // S' = sum_{j < i-1} M_ij X_jp (X_i-1,p enters through Z)
         float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
         float mr[16];
-        if (i > 0) load_m(p, i0, 0, colmajor, mr);
-        for (int j = 0; j < i; ++j) {
+        const int jz = i - 1;
+        if (jz > 0) load_m(p, i0, 0, colmajor, mr);
+        for (int j = 0; j < jz; ++j) {
             store_m(sm, colmajor, mr);
-            if (j + 1 < i) load_m(p, i0, (int64_t)(j + 1) * BR, colmajor, mr);
-            if (t == 0 && !wait_flag(p, p.flags + (int64_t)pn * p.nbr + j)) sm.abort = 1;
+            if (j + 1 < jz) load_m(p, i0, (int64_t)(j + 1) * BR, colmajor, mr);
+            if (!take_x(p, sm, pn, j)) sm.abort = 1;
             __syncthreads();
             if (sm.abort) break;
-            load_x(p, sm, (int64_t)j * BR, c0, c_colmajor);
-            __syncthreads();
             mma_tile(sm.m, sm.x, BR, acc);
             __syncthreads();
         }
         if (sm.abort) break;
-        // right-hand side of the diagonal block, then X = inv(M_ii) (alpha B - S)
+        // P = inv(M_ii) (alpha B - S'), then X = P - Z X_i-1,p
 #pragma unroll
         for (int e = 0; e < 4; ++e) sm.x[(4 * ty + e) * NP + tx] = fmaf(p.alpha, b[e], -acc[e]);
         __syncthreads();
         float xo[4] = {0.0f, 0.0f, 0.0f, 0.0f};
         mma_tile(sm.inv, sm.x, 8 * ((t >> 5) + 1), xo);   // inv is lower: kk <= row
+        if (i > 0) {
+            __syncthreads();
+            if (!take_x(p, sm, pn, i - 1)) sm.abort = 1;
+            __syncthreads();
+            if (sm.abort) break;
+            float zx[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+            mma_tile(sm.z, sm.x, BR, zx);
+#pragma unroll
+            for (int e = 0; e < 4; ++e) xo[e] -= zx[e];
+        }
+        // publish the block (tagged words: the chain), then the result in C
+        unsigned long long* dst = p.xt + ((int64_t)pn * p.nbr + i) * (BR * NP);
+        if (!(p.withhold && i == 0)) {
+#pragma unroll
+            for (int e = 0; e < 4; ++e)
+                st_relaxed64(dst + (4 * ty + e) * NP + tx, kTag | __float_as_uint(xo[e]));
+        }
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
             const int64_t gi = i0 + 4 * ty + e, gj = c0 + tx;
             if (gi < p.k && gj < p.nrhs) p.C[gi * p.c_rs + gj * p.c_cs] = xo[e];
         }
-        __syncthreads();
-        if (t == 0) st_release(p.flags + (int64_t)pn * p.nbr + i, 1);
     }
 }
 
@@ -268,7 +330,7 @@ __global__ void __launch_bounds__(NT, 3) thin_trsm_kernel(const Params p) {
 size_t thin_scratch_bytes(int64_t k, int64_t nrhs) {
     const int64_t nbr = (k + kThinBlock - 1) / kThinBlock;
     const int64_t npan = (nrhs + kThinPanel - 1) / kThinPanel;
-    return (size_t)(2 + nbr * npan) * sizeof(int);
+    return 16 + (size_t)(nbr * npan) * kThinBlock * kThinPanel * 8;
 }
 
 static int g_thin_ctas_per_sm = 0;
@@ -287,7 +349,7 @@ cudaError_t thin_configure() {
 }
 
 cudaError_t launch_thin_trsm(const Canon<float>& c, float alpha, int* scratch, int* err,
-                             long long wait_ns, int num_sms, cudaStream_t s) {
+                             long long wait_ns, int num_sms, cudaStream_t s, bool withhold) {
     if (c.k <= 0 || c.nrhs <= 0) return cudaSuccess;
     thin::Params p;
     p.k = c.k;
@@ -308,9 +370,10 @@ cudaError_t launch_thin_trsm(const Canon<float>& c, float alpha, int* scratch, i
     p.ntask = nbr * npan;
     p.ticket = scratch;
     p.stop = scratch + 1;
-    p.flags = scratch + 2;
+    p.xt = reinterpret_cast<unsigned long long*>(reinterpret_cast<char*>(scratch) + 16);
     p.err = err;
     p.wait_ns = wait_ns;
+    p.withhold = withhold ? 1 : 0;
     cudaError_t e = cudaMemsetAsync(scratch, 0, thin_scratch_bytes(c.k, c.nrhs), s);
     if (e != cudaSuccess) return e;
     const int per_sm = g_thin_ctas_per_sm > 0 ? g_thin_ctas_per_sm : 1;

@@ -8,7 +8,8 @@ B := alpha op(A) B with A and B as float pairs, against the FP64 oracle.
 - order 4096 with 512 right-hand sides, sampled columns against the oracle;
 - within the FP64 bound of the recursive DFMA product, bitwise repeatable;
 - orders below 64 keep the DFMA product (same result as with the option
-  off); alpha = 0 zeroes B.
+  off), and so does the mixed FP64 TRSM (TRX_OPT_FP64_TRSM) below 64;
+  alpha = 0 zeroes B.
 """
 import numpy as np
 import pytest
@@ -92,5 +93,20 @@ def test_pair_trmm_small_orders_and_alpha_zero(trx):
     trx.trmm("L", "L", "N", "N", 0.0, to_dev(A, "cuda:0"), Bt, handle=h)
     torch.cuda.synchronize()
     assert not Bt.any()
+    h.close()
+    hd.close()
+
+
+def test_mixed_fp64_trsm_keeps_dfma_below_order_64(trx):
+    h = trx.Handle(0)
+    h.set_option(trx.OPT_FP64_TRSM, 2)
+    hd = trx.Handle(0)
+    A, B = inputs.problem("L", "U", 40, 300, seed=10, dtype=np.float64)
+    At = to_dev(A, "cuda:0")
+    B1, B2 = to_dev(B, "cuda:0"), to_dev(B, "cuda:0")
+    trx.trsm("L", "U", "T", "N", 0.5, At, B1, handle=h)
+    trx.trsm("L", "U", "T", "N", 0.5, At, B2, handle=hd)
+    torch.cuda.synchronize()
+    assert torch.equal(B1, B2)
     h.close()
     hd.close()

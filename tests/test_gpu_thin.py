@@ -12,8 +12,8 @@ FP64 oracle and the recursive chain.
 - order 8192 with 16 right-hand sides (128 block rows): sampled columns
   against the oracle, bitwise repeatable, within the FP32 bound of the
   recursive chain; the default (automatic) mode takes this path;
-- a bounded wait run out (1 microsecond budget) is reported as
-  TRX_ERR_TIMEOUT and the next call with the normal budget is correct.
+- a bounded wait run out (the first block row withheld by the test hook,
+  1 ms budget) is reported as TRX_ERR_TIMEOUT and the next call is correct.
 """
 import numpy as np
 import pytest
@@ -95,14 +95,17 @@ def test_thin_large_order_sampled_repeatable_and_against_chain(trx):
 
 
 def test_thin_bounded_wait_reports_timeout(trx):
+    from paper_2504_13821_gb300 import _binding
     h = thin_handle(trx)
     h.set_option(trx.OPT_GRAPH, 0)
     assert h.check_device_error() == 0
-    h.set_option(trx.OPT_WAIT_LIMIT, 1000)            # 1 us: the waits run out
+    h.set_option(trx.OPT_WAIT_LIMIT, 1_000_000)       # 1 ms
+    h.set_option(_binding.OPT_TEST_WITHHOLD, 1)       # block row 0 is never published
     run_case("trsm", "L", "L", "N", "N", 4096, 16, 1.0, np.float32, seed=6, handle=h,
              check=False)
     assert h.check_device_error() == 4                # TRX_ERR_TIMEOUT
     assert h.check_device_error() == 0
+    h.set_option(_binding.OPT_TEST_WITHHOLD, 0)
     h.set_option(trx.OPT_WAIT_LIMIT, 2_000_000_000)
     run_case("trsm", "L", "L", "N", "N", 4096, 16, 1.0, np.float32, seed=6, handle=h)
     assert h.check_device_error() == 0
