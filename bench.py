@@ -1033,7 +1033,9 @@ def run_serving(args):
     args.duration seconds), 70% TRSM / 30% TRMM, order log-uniform 64..8192,
     right-hand sides log-uniform 1..1024, half FP32-refined and half FP64;
     each factor (same generator) is resident and reused by 1..50 requests;
-    admission capped at 150 GB. FP32 TRSM requests are refined (the FP32
+    admission capped at 150 GB; a request takes one of 32 live factors of
+    its precision at random, and a factor is replaced by a new one after its
+    1..50 uses. FP32 TRSM requests are refined (the FP32
     solve plus args.refine_corrections float-float corrections, FP64 result)
     unless --no-refine; FP64 TRSM requests take the server's FP64 engine
     (args.fp64_corrections > 0: the FP32 solve plus that many float-float
@@ -1109,6 +1111,7 @@ def run_serving(args):
     t_start = time.perf_counter() + 0.5
     t_arr = t_start
     live = {}             # factor id -> [A, uses left, dtype, k, uplo]
+    SERVING_POOL = 32
     submitted = 0
     rejected = 0
     flops = 0.0
@@ -1117,8 +1120,12 @@ def run_serving(args):
         if t_arr - t_start > args.duration:
             break
         dtype = torch.float64 if rng.random() < args.fp64_share else torch.float32
-        cands = [f for f, v in live.items() if v[2] == dtype and v[1] > 0]
-        if cands and rng.random() < 0.9:
+        # a pool of POOL live factors per precision: a request takes one at
+        # random, and a factor leaves the pool after its 1..50 uses, replaced
+        # by a new one (so factors are made at the rate their uses run out
+        # and the resident set stays bounded)
+        cands = [f for f, v in live.items() if v[2] == dtype]
+        if len(cands) >= SERVING_POOL:
             fid = cands[int(rng.integers(len(cands)))]
         else:
             k = int(round(np.exp(rng.uniform(np.log(64), np.log(8192)))))
@@ -1184,7 +1191,8 @@ def run_serving(args):
                                    + ", FP64 TRMM "
                                    + ("one float-float pass" if args.fp64_trmm else "DFMA")
                                    + ", factors reused "
-                                   "1..50 times, 150 GB admission cap, native request server, "
+                                   f"1..50 times (pool of {SERVING_POOL} live factors per "
+                                   "precision), 150 GB admission cap, native request server, "
                                    f"{args.server_streams} streams, "
                                    f"{args.server_workspace_mb} MB workspace per stream, "
                                    + ("cached graphs" if args.server_graphs else
