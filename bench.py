@@ -817,6 +817,9 @@ def run_precision(args):
     kappas = [1e2, 1e4, 1e6] if args.kappa is None else [args.kappa]
     nsel = args.nrhs_list.split(",")
     h = trx.Handle(dev)
+    # the forms compare the recursion's update arithmetic: the thin CUDA-core
+    # solve (no split) is kept out of the table
+    h.set_option(trx.OPT_THIN, -1)
     alpha = 1.5
 
     def timed(fn, reps):

@@ -220,8 +220,9 @@ enum {
                               split); -1 = the recursion; 0 = automatic
                               (default: order above 256 with at most 64
                               right-hand sides, or at most 256 while order
-                              x right-hand sides <= 2^20). Its flags live
-                              in a small handle buffer grown on first use */
+                              x right-hand sides <= 2^21). Its published
+                              blocks live in a handle buffer grown on first
+                              use                                         */
     TRX_OPT_TEST_WITHHOLD = 18 /* test hook for the bounded waits: 1 = the
                               thin TRSM (TRX_OPT_THIN) never publishes its
                               first block row, so the waits of the blocks

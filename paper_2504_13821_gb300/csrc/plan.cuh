@@ -343,10 +343,10 @@ inline bool use_dag_mode(int64_t opt, bool tc, bool trsm, int elem, int64_t k, i
 // at most kThinMaxNrhs right-hand sides, or up to kThinWideNrhs of them
 // while order x right-hand sides stays within kThinMaxWork, where the
 // chain's launch and leaf latency bound the recursive path (measured on
-// GB300: 1.3-3x faster there; at order 16384 with 128 or more right-hand
-// sides the chain's tensor-core updates win).
+// GB300: 1.04-4.2x faster there; at order 16384 with 256 right-hand sides
+// the chain's tensor-core updates win).
 constexpr int64_t kThinMaxNrhs = 64, kThinWideNrhs = 256;
-constexpr int64_t kThinMaxWork = (int64_t)1 << 20;
+constexpr int64_t kThinMaxWork = (int64_t)1 << 21;
 constexpr int64_t kThinMinK = 256;
 inline bool use_thin_mode(int64_t opt, bool trsm, int elem, int64_t k, int64_t nrhs) {
     if (opt < 0 || !trsm || elem != 4 || k <= 0 || nrhs <= 0) return false;

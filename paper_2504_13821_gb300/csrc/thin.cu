@@ -3,28 +3,34 @@
 //
 // With a thin right-hand side the recursion of Section 3.1 is a long chain
 // of small launches (a leaf and a GEMM update per 128 rows), each bound by
-// latency: at order 8000 with 8 right-hand sides the chain takes about
-// 1.6 ms to read a 128 MB triangle. Here the canonical lower M is cut into
+// latency: at order 8192 with 16 right-hand sides the chain takes about
+// 1.4 ms to read a 128 MB triangle. Here the canonical lower M is cut into
 // 64-row blocks and the right-hand side into 16-column panels, and task
 // (i, p) runs the blocked forward substitution of block row i, left-looking:
 //
-//     S   = sum_{j < i} M_ij X_jp          (64 x 64 x 16 products, FP32 FMA)
-//     X_ip = inv(M_ii) (alpha B_ip - S)
+//     S'   = sum_{j < i-1} M_ij X_jp        (64 x 64 x 16 products, FP32 FMA)
+//     P    = inv(M_ii) (alpha B_ip - S')
+//     X_ip = P - Z X_i-1,p,   Z = inv(M_ii) M_i,i-1
 //
-// then writes X_ip into C and publishes it with a flag. The products of a
-// task start as soon as the blocks X_jp they need are published, so the
-// reads of M (every element once per panel, the dominant traffic) overlap
-// the chain of diagonal blocks; the chain itself is one 64 x 64 x 16 product
-// and one product with inv(M_ii) per block. inv(M_ii) is made by the task
-// itself by substitution before its first wait (64 columns of the identity,
-// FP32, one reciprocal of each diagonal entry): the leaf solve of Section
-// 3.3 as a product with the inverted block.
+// then writes X_ip into C and publishes it. inv(M_ii) (substitution against
+// the identity, FP32, one reciprocal of each diagonal entry: the leaf solve
+// of Section 3.3 as a product with the inverted block) and Z are made by
+// the task before its first wait, and the products of a task start as soon
+// as the blocks X_jp they need are published, so the reads of M (every
+// element once per panel, the dominant traffic) overlap the chain of
+// diagonal blocks; the chain itself is one 64 x 64 x 16 product per block.
+//
+// A block is published as 1024 tagged 64-bit words (FP32 bits in the low
+// half, 1 in the high half; a 64-bit access is single-copy atomic, so value
+// and tag arrive together): a consumer polls the words themselves, one L2
+// round trip, with no flag and no fence between data and signal. The words
+// are zeroed by a memset before each launch.
 //
 // Tasks are taken in order from an atomic counter (block row major), so a
 // task only waits for tasks taken before it, which are running or done: the
-// solve progresses whatever the number of resident CTAs. Every flag wait is
+// solve progresses whatever the number of resident CTAs. Every wait is
 // bounded: past the budget the CTA writes TRX_ERR_TIMEOUT to the error word
-// and stops; tasks waiting on it then time out too.
+// and the launch's stop word, and every waiting CTA then stops.
 //
 // Arithmetic: FP32 FMA throughout (no operand split), partial sums in a
 // fixed order, so results are bitwise repeatable.
@@ -65,8 +71,13 @@ struct Params {
     int withhold;    // test hook: block row 0 is never published (waits run out)
 };
 
+constexpr int STAGES = 3;            // M tiles in flight (cp.async ring)
+
 struct Smem {
-    float m[BR * LD];        // M_ij tile, k-major: m[kk * LD + r] = M[i0 + r][j0 + kk]
+    // M_ij tiles, k-major: m[s][kk * LD + r] = M[i0 + r][j0 + kk]; tile j of
+    // a task's sum sits in stage (j + 1) % STAGES (stage 0 also serves as the
+    // work tile of the inverse and of Z before the ring reaches it)
+    float m[STAGES][BR * LD];
     float inv[BR * LD];      // inv(M_ii), k-major: inv[kk * LD + r] = Inv[r][kk]
     float z[BR * LD];        // Z = inv(M_ii) M_i,i-1, k-major
     float x[BR * NP];        // X_jp tile / right-hand side: x[kk * NP + c]
@@ -90,17 +101,26 @@ __device__ __forceinline__ uint64_t gtimer() {
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
     return t;
 }
-// X_jp into sm.x from its tagged words: each thread waits for its four
-// words (single-copy atomic 64-bit loads: value and tag arrive together),
-// at most wait_ns. False on timeout (the error word and the launch's stop
-// word are set) or once another CTA has stopped the launch.
-__device__ bool take_x(const Params& p, Smem& sm, int pn, int j) {
+constexpr int Q = (BR * NP) / NT;    // tagged words of a block per thread
+
+// Issue the loads of this thread's four words of X_jp (all in flight; the
+// values are checked by finish_x, so they can be issued a step ahead).
+__device__ __forceinline__ void issue_x(const Params& p, int pn, int j,
+                                        unsigned long long (&w)[Q]) {
+    const unsigned long long* src = p.xt + ((int64_t)pn * p.nbr + j) * (BR * NP);
+#pragma unroll
+    for (int q = 0; q < Q; ++q) w[q] = ld_relaxed64(src + threadIdx.x + NT * q);
+}
+
+// X_jp into sm.x from its tagged words: a word loaded before it was
+// published (tag 0) is polled again (single-copy atomic 64-bit loads: value
+// and tag arrive together), at most wait_ns. False on timeout (the error
+// word and the launch's stop word are set) or once another CTA has stopped
+// the launch.
+__device__ bool finish_x(const Params& p, Smem& sm, int pn, int j,
+                         const unsigned long long (&w)[Q]) {
     const unsigned long long* src = p.xt + ((int64_t)pn * p.nbr + j) * (BR * NP);
     const int t = threadIdx.x;
-    constexpr int Q = (BR * NP) / NT;
-    unsigned long long w[Q];
-#pragma unroll
-    for (int q = 0; q < Q; ++q) w[q] = ld_relaxed64(src + t + NT * q);   // all in flight
     bool ok = true;
 #pragma unroll
     for (int q = 0; q < Q; ++q) {
@@ -140,14 +160,32 @@ __device__ __forceinline__ void load_m(const Params& p, int64_t i0, int64_t j0, 
         r[q] = in ? __ldg(src + q * step) : 0.0f;
     }
 }
-__device__ __forceinline__ void store_m(Smem& sm, bool colmajor, const float (&r)[16]) {
+__device__ __forceinline__ void cp_async4(float* dst, const float* src, bool valid) {
+    const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(d), "l"(src),
+                 "r"(valid ? 4 : 0)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_wait_1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+
+// Tile (i0.., j0..) of M into ring stage `dst` by cp.async (element by
+// element along M's contiguous direction, into the k-major layout); rows
+// past the order are zero-filled (no read). Commits one group.
+__device__ __forceinline__ void issue_m(const Params& p, float* dst, int64_t i0, int64_t j0,
+                                        bool colmajor) {
     const int t = threadIdx.x;
+    const int rr0 = colmajor ? (t & 63) : (t >> 6), cc0 = colmajor ? (t >> 6) : (t & 63);
+    const float* src = p.A + (i0 + rr0) * p.a_rs + (j0 + cc0) * p.a_cs;
+    const int64_t step = 4 * (colmajor ? p.a_cs : p.a_rs);
+    const int64_t rows_left = p.k - (i0 + rr0);
 #pragma unroll
     for (int q = 0; q < 16; ++q) {
-        const int rr = colmajor ? (t & 63) : (t >> 6) + 4 * q;
-        const int cc = colmajor ? (t >> 6) + 4 * q : (t & 63);
-        sm.m[cc * LD + rr] = r[q];
+        const int rr = colmajor ? rr0 : rr0 + 4 * q, cc = colmajor ? cc0 + 4 * q : cc0;
+        const bool in = colmajor ? rows_left > 0 : rows_left > 4 * q;
+        cp_async4(dst + cc * LD + rr, in ? src + q * step : p.A, in);
     }
+    cp_commit();
 }
 
 // acc[e] += sum_kk a[kk][4 ty + e] * x[kk][tx] over kk < kend.
@@ -172,7 +210,7 @@ __device__ __forceinline__ void mma_tile(const float* a, const float* x, int ken
 // (reciprocal of m_rr made once), broadcasts it, and every lane adds
 // m_row,r y_r into the partial sums of its later rows.
 __device__ void invert_diag(const Params& p, Smem& sm, int64_t i0) {
-    float* T = sm.m;
+    float* T = sm.m[0];
     const int t = threadIdx.x, w = t >> 5, l = t & 31;
     const bool colmajor = p.a_rs == 1 || p.a_rs == -1;
     for (int e = t; e < BR * BR; e += NT) {
@@ -229,7 +267,7 @@ __device__ void make_z(const Params& p, Smem& sm, int64_t i0, bool colmajor) {
     for (int q = 0; q < 16; ++q) {
         const int rr = colmajor ? (t & 63) : (t >> 6) + 4 * q;
         const int cc = colmajor ? (t >> 6) + 4 * q : (t & 63);
-        sm.m[rr * LD + cc] = r[q];
+        sm.m[0][rr * LD + cc] = r[q];
     }
     __syncthreads();
     float acc[4][4];
@@ -242,7 +280,7 @@ __device__ void make_z(const Params& p, Smem& sm, int64_t i0, bool colmajor) {
         const float4 iv = *reinterpret_cast<const float4*>(sm.inv + q * LD + 4 * ty);
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
-            const float mv = sm.m[q * LD + tx + 16 * u];
+            const float mv = sm.m[0][q * LD + tx + 16 * u];
             acc[0][u] = fmaf(iv.x, mv, acc[0][u]);
             acc[1][u] = fmaf(iv.y, mv, acc[1][u]);
             acc[2][u] = fmaf(iv.z, mv, acc[2][u]);
@@ -256,7 +294,7 @@ __device__ void make_z(const Params& p, Smem& sm, int64_t i0, bool colmajor) {
     __syncthreads();
 }
 
-__global__ void __launch_bounds__(NT, 3) thin_trsm_kernel(const Params p) {
+__global__ void __launch_bounds__(NT, 2) thin_trsm_kernel(const Params p) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Smem& sm = *reinterpret_cast<Smem*>(smem_raw);
     const int t = threadIdx.x, ty = t >> 4, tx = t & 15;
@@ -277,23 +315,31 @@ __global__ void __launch_bounds__(NT, 3) thin_trsm_kernel(const Params p) {
             const int64_t gi = i0 + 4 * ty + e, gj = c0 + tx;
             b[e] = (gi < p.k && gj < p.nrhs) ? __ldcg(p.C + gi * p.c_rs + gj * p.c_cs) : 0.0f;
         }
+        // S' = sum_{j < i-1} M_ij X_jp (X_i-1,p enters through Z): tile j of M
+        // arrives through the cp.async ring (two tiles ahead), X_jp's words
+        // are loaded one step ahead
+        float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+        unsigned long long w[Q];
+        const int jz = i - 1;
+        if (jz > 0) issue_m(p, sm.m[1], i0, 0, colmajor); else cp_commit();
+        if (jz > 1) issue_m(p, sm.m[2], i0, BR, colmajor); else cp_commit();
         invert_diag(p, sm, i0);
         if (i > 0) make_z(p, sm, i0, colmajor);
-        // S' = sum_{j < i-1} M_ij X_jp (X_i-1,p enters through Z)
-        float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-        float mr[16];
-        const int jz = i - 1;
-        if (jz > 0) load_m(p, i0, 0, colmajor, mr);
+        if (jz > 0) issue_x(p, pn, 0, w);
         for (int j = 0; j < jz; ++j) {
-            store_m(sm, colmajor, mr);
-            if (j + 1 < jz) load_m(p, i0, (int64_t)(j + 1) * BR, colmajor, mr);
-            if (!take_x(p, sm, pn, j)) sm.abort = 1;
+            cp_wait_1();                                  // this thread's copies of tile j
+            if (!finish_x(p, sm, pn, j, w)) sm.abort = 1;
             __syncthreads();
             if (sm.abort) break;
-            mma_tile(sm.m, sm.x, BR, acc);
+            // tile j - 1's stage is free: tile j + 2 goes there
+            if (j + 2 < jz) issue_m(p, sm.m[j % STAGES], i0, (int64_t)(j + 2) * BR, colmajor);
+            else cp_commit();
+            if (j + 1 < jz) issue_x(p, pn, j + 1, w);
+            mma_tile(sm.m[(j + 1) % STAGES], sm.x, BR, acc);
             __syncthreads();
         }
         if (sm.abort) break;
+        if (i > 0) issue_x(p, pn, i - 1, w);
         // P = inv(M_ii) (alpha B - S'), then X = P - Z X_i-1,p
 #pragma unroll
         for (int e = 0; e < 4; ++e) sm.x[(4 * ty + e) * NP + tx] = fmaf(p.alpha, b[e], -acc[e]);
@@ -302,7 +348,7 @@ __global__ void __launch_bounds__(NT, 3) thin_trsm_kernel(const Params p) {
         mma_tile(sm.inv, sm.x, 8 * ((t >> 5) + 1), xo);   // inv is lower: kk <= row
         if (i > 0) {
             __syncthreads();
-            if (!take_x(p, sm, pn, i - 1)) sm.abort = 1;
+            if (!finish_x(p, sm, pn, i - 1, w)) sm.abort = 1;
             __syncthreads();
             if (sm.abort) break;
             float zx[4] = {0.0f, 0.0f, 0.0f, 0.0f};
@@ -323,6 +369,7 @@ __global__ void __launch_bounds__(NT, 3) thin_trsm_kernel(const Params p) {
             if (gi < p.k && gj < p.nrhs) p.C[gi * p.c_rs + gj * p.c_cs] = xo[e];
         }
     }
+    asm volatile("cp.async.wait_group 0;" ::: "memory");   // nothing in flight at exit
 }
 
 }  // namespace thin
