@@ -66,6 +66,9 @@ __device__ __forceinline__ void group_sync(int g) {
     asm volatile("bar.sync %0, %1;" ::"r"(1 + g), "r"(Wide::GT) : "memory");
 }
 
+// ROWS: C's rows are contiguous (side L); one layout per instance keeps the
+// kernel's code small (instruction fetch was its largest stall).
+template <bool ROWS>
 __global__ void __launch_bounds__(Wide::NT, 1) leaf_trsm_wide_kernel(LeafArgs<float> a,
                                                                    int64_t npanels) {
     using S = Wide;
@@ -85,10 +88,10 @@ __global__ void __launch_bounds__(Wide::NT, 1) leaf_trsm_wide_kernel(LeafArgs<fl
 
     // Panel staging (alpha * C, zeros outside the leaf): thread = row when
     // C's rows are contiguous, else thread = column.
-    const bool c_row_fast = (p.c_rs == 1 || p.c_rs == -1);
+    constexpr bool c_row_fast = ROWS;
     auto load_panel = [&](int64_t j0, float (&v)[S::NC]) {
         const int ncols = (int)(p.nrhs - j0 < S::NC ? p.nrhs - j0 : S::NC);
-        if (c_row_fast) {
+        if constexpr (c_row_fast) {
             const int i = gt;
             const float* src = p.C + (r0 + i) * p.c_rs + j0 * p.c_cs;
 #pragma unroll
@@ -105,7 +108,7 @@ __global__ void __launch_bounds__(Wide::NT, 1) leaf_trsm_wide_kernel(LeafArgs<fl
         }
     };
     auto store_panel = [&](const float (&v)[S::NC]) {
-        if (c_row_fast) {
+        if constexpr (c_row_fast) {
 #pragma unroll
             for (int c4 = 0; c4 < S::NC / 4; ++c4)
                 *reinterpret_cast<float4*>(sC + gt * S::LDC + 4 * c4) =
@@ -240,7 +243,7 @@ __global__ void __launch_bounds__(Wide::NT, 1) leaf_trsm_wide_kernel(LeafArgs<fl
 
         // Write back (and the Y planes on the tensor-core path). The last
         // barrier above follows the last substitution, so every row is final.
-        if (c_row_fast) {
+        if constexpr (c_row_fast) {
             const int i = gt;
             if (i < bs) {
                 float* dst = p.C + (r0 + i) * p.c_rs + j0 * p.c_cs;
@@ -283,8 +286,12 @@ __global__ void __launch_bounds__(Wide::NT, 1) leaf_trsm_wide_kernel(LeafArgs<fl
 }  // namespace
 
 cudaError_t leaf_wide_configure() {
-    return cudaFuncSetAttribute(leaf_trsm_wide_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)Wide::smem);
+    const cudaError_t e = cudaFuncSetAttribute(leaf_trsm_wide_kernel<true>,
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)Wide::smem);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(leaf_trsm_wide_kernel<false>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Wide::smem);
 }
 
 // One FP32 TRSM leaf of up to 128 rows (a.r0, a.b), one CTA per SM at most,
@@ -294,7 +301,9 @@ cudaError_t leaf_wide_launch(const LeafArgs<float>& a, int num_sms, cudaStream_t
     const int64_t npanels = (a.p.nrhs + Wide::NC - 1) / Wide::NC;
     const int64_t sms = num_sms > 0 ? num_sms : 1;
     const int64_t grid = npanels < sms ? npanels : sms;
-    return launch_kernel(leaf_trsm_wide_kernel, dim3((unsigned)grid), dim3(Wide::NT), Wide::smem, s,
+    const bool rows = a.p.c_rs == 1 || a.p.c_rs == -1;
+    return launch_kernel(rows ? leaf_trsm_wide_kernel<true> : leaf_trsm_wide_kernel<false>,
+                         dim3((unsigned)grid), dim3(Wide::NT), Wide::smem, s,
                          a, npanels);
 }
 
