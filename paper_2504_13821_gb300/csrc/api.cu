@@ -347,7 +347,8 @@ struct Exec {
                     } else {
                         for (const TcGemm& g : st.gemms) {
                             e = launch_gemm_simt<T>(c, c.C, c.c_rs, c.c_cs, g.rc, g.mlen, g.rk,
-                                                    g.klen, (T)st.beta, (T)st.gamma, s);
+                                                    g.klen, (T)st.beta, (T)st.gamma, s,
+                                                    h->num_sms);
                             if (e != cudaSuccess) break;
                         }
                         cls = TRX_KERNEL_GEMM_SIMT;
@@ -1954,7 +1955,8 @@ int trx_sgemm_update(trx_handle_t h, int64_t M, int64_t N, int64_t K, float beta
     c.c_rs = 1;
     c.c_cs = ldc;
     if (engine == 1 || K == 0) {
-        e = launch_gemm_simt<float>(c, Y, 1, ldy, K, M, 0, K, beta, K == 0 ? 0.f : gamma, s);
+        e = launch_gemm_simt<float>(c, Y, 1, ldy, K, M, 0, K, beta, K == 0 ? 0.f : gamma, s,
+                                    h->num_sms);
         return e == cudaSuccess ? TRX_SUCCESS : fail_cuda(e, "gemm_simt");
     }
     if (K % kTcKQuantum != 0) return -4;

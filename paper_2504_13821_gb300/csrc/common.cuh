@@ -146,7 +146,7 @@ constexpr int kMaxBlockLeaf = 256;
 template <typename T>
 cudaError_t launch_gemm_simt(const Canon<T>& p, const T* Y, int64_t y_rs, int64_t y_cs,
                              int64_t rc, int64_t mlen, int64_t rk, int64_t klen, T beta,
-                             T gamma, cudaStream_t s);
+                             T gamma, cudaStream_t s, int num_sms = 152);
 
 // B := 0 over an m x n column-major block (alpha == 0 quick return).
 template <typename T>
