@@ -57,6 +57,9 @@ REF_SAMPLE_COLS = 16      # per step of --impl reference
 # reports null; the small-case figures (DRAM bytes against the algorithmic
 # bytes of the captured update) are in the profiles/ summary of the kernel.
 TRAFFIC_PER_LAUNCH = None
+# FP64 FMA rate measured by this build's own probe (bench.py --workload
+# peaks; MEASURED_PEAKS.json holds no FP64 figure): the FP64 roofline
+FP64_FMA_PROBE_TFLOPS = 1.057
 
 
 def captured_traffic():
@@ -339,8 +342,9 @@ def run_gpu(args):
     else:
         g = prof["gemm_simt"]
         kname = "gemm_simt_kernel<double> (GEMM update, DFMA)"
-        peak_tc = 1.25
-        peak_src = "nominal GB300 FP64 1.25 TFLOP/s (not measured)"
+        peak_tc = FP64_FMA_PROBE_TFLOPS
+        peak_src = (f"this build's FP64 FMA probe (bench.py --workload peaks): "
+                    f"{FP64_FMA_PROBE_TFLOPS} TFLOP/s")
     achieved = g["flops"] / (g["ms"] * 1e-3) / 1e12 if g["ms"] > 0 else 0.0
     kern_ms = sum(v["ms"] for v in prof.values())
     roofline = {
@@ -361,6 +365,17 @@ def run_gpu(args):
         "per_class_ms": {kk: round(v["ms"], 4) for kk, v in prof.items() if v["launches"]},
         "whole_step_frac": (flops_step / (ms_step * 1e-3) / 1e12) / peak_tc,
     }
+    # the leaves (the recursion's HBM/latency-bound part): their algorithmic
+    # bytes (right-hand-side rows in and out, the triangle, the planes they
+    # write) over their event-timed duration, against the HBM copy rate
+    lf = prof.get("leaf_trsm", {"ms": 0, "bytes": 0, "launches": 0})
+    leaf_roofline = None
+    if lf["launches"] and lf["ms"] > 0:
+        leaf_gbs = lf["bytes"] / (lf["ms"] * 1e-3) / 1e9
+        leaf_roofline = {"bound": "hbm", "kernel": "TRSM leaves", "achieved": leaf_gbs,
+                         "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                         "frac": leaf_gbs / peaks["hbm_gbs"], "launches_per_step": lf["launches"],
+                         "us_per_launch": 1e3 * lf["ms"] / lf["launches"]}
 
     # End to end through the public API: pinned host buffers, every step the
     # H2D copy of A and B, TRSM + TRMM, and the D2H copy of the result.
@@ -481,7 +496,8 @@ def run_gpu(args):
                 f"right-hand-side panels over {world} ranks (one problem, no exchange)"
                 if args.shard else f"{world} independent copies, one per rank")),
             "clocks": clk, "gpu_launches": launches_step * args.steps,
-            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "roofline": roofline, "leaf_roofline": leaf_roofline, "cpu_baseline": cpu,
+            "e2e": e2e,
             "round_trip_drift": drift,
         }
         print(json.dumps(line), flush=True)
