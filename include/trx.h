@@ -500,8 +500,9 @@ int trx_batched_set_tuning(trx_handle_t handle, int elem_bytes, const int* table
  * budget is admitted alone on an idle server), launch the admitted ones —
  * orders up to small_k as one persistent trx_batched launch per element
  * type on the server's batch stream, the rest one trx_?trsm / trx_?trmm
- * each, round-robin over `streams` streams with one handle and workspace
- * per stream — and report up to `capacity` completed requests with their
+ * each, on whichever of the `streams` streams has the least estimated cost
+ * in flight (k^2 n plus a fixed latency term per request), one handle and
+ * workspace per stream — and report up to `capacity` completed requests with their
  * status (0 or a TRX_ERR_* code). A request's launch waits for an event
  * recorded on input_stream at submission, so B may still be in flight
  * there. The plan a request gets depends only on its own problem, so its

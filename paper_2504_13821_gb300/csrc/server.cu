@@ -14,8 +14,8 @@
 //   3. launch: the admitted small problems (order <= small_k; FP64 ones up to
 //      a work limit) go out as one
 //      persistent batched launch per element type, the others one call each,
-//      round-robin over parallel streams with one handle (and workspace)
-//      per stream;
+//      on the parallel stream with the least estimated cost in flight, one
+//      handle (and workspace) per stream;
 //   4. report: completed request ids and their status codes.
 // The plan a request gets depends only on its own problem, never on what
 // else is in flight, so a result is the same alone and in the mix.
@@ -77,6 +77,7 @@ struct Req {
 struct Flight {
     cudaEvent_t done;
     uint64_t seq;                        // launch order across lanes
+    double cost = 0;                     // its requests' estimated cost (stream choice)
     std::vector<int64_t> ids;
     std::vector<int> fids;
     size_t bytes;
@@ -107,7 +108,9 @@ struct trx_server_s {
     std::deque<std::pair<int64_t, int>> done;   // (request id, status) not yet reported
     std::vector<cudaEvent_t> pool;
     int64_t next_id = 0;
-    int rr = 0;
+    // estimated cost in flight per stream: k^2 n plus kLaunchCost for each
+    // request (a request's fixed latency, in k^2 n units)
+    std::vector<double> lane_cost;
 };
 
 namespace {
@@ -136,6 +139,9 @@ void put_event(trx_server_t s, cudaEvent_t ev) { s->pool.push_back(ev); }
 // hold its CTA for long on the slow FP64 pipe (about 0.15 ms at the limit),
 // so it goes to the streams, whose engines spread it over the GPU.
 constexpr double kSmallFp64Work = 1048576.0;
+// A request's fixed latency (its launches, about 0.1-0.3 ms) in k^2 n units
+// at the few TFLOP/s a latency-bound call reaches.
+constexpr double kLaunchCost = 5e8;
 bool is_small(const trx_server_s* s, const Req& r) {
     const Fac& f = s->facs[r.fid];
     if (f.k > s->cfg.small_k || r.op == 'R') return false;   // no refinement there
@@ -198,8 +204,15 @@ int ensure_ws(trx_server_t s, int i, size_t need) {
 }
 
 int launch_large(trx_server_t s, Req& r) {
-    const int i = s->rr++ % (int)s->streams.size();
+    // the stream with the least estimated cost in flight: a request's cost is
+    // its k^2 n plus a fixed term for its launches' latency, so neither a
+    // large request nor a queue of small ones holds up what comes next
+    int i = 0;
+    for (int q = 1; q < (int)s->streams.size(); ++q)
+        if (s->lane_cost[q] < s->lane_cost[i]) i = q;
     const Fac& f = s->facs[r.fid];
+    const double cost = (double)f.k * (double)f.k * (double)(upc(r.side) == 'L' ? r.n : r.m) +
+                        kLaunchCost;
     cudaStream_t st = s->streams[i];
     size_t need = 0;
     const char wop = r.op == 'R' ? 'S' : r.op;
@@ -246,6 +259,8 @@ int launch_large(trx_server_t s, Req& r) {
     fl.bytes = r.cost;
     put_event(s, r.ready);
     fl.seq = s->flight_seq++;
+    fl.cost = cost;
+    s->lane_cost[i] += cost;
     s->lanes[i].push_back(std::move(fl));
     s->inflight_reqs += 1;
     return TRX_SUCCESS;
@@ -305,7 +320,8 @@ int launch_small(trx_server_t s, std::vector<Req>& group, int elem) {
 // Retire finished launch groups; returns a CUDA error if a query failed.
 int retire(trx_server_t s) {
     int first_err = TRX_SUCCESS;
-    for (auto& lane : s->lanes) {
+    for (size_t li = 0; li < s->lanes.size(); ++li) {
+        auto& lane = s->lanes[li];
         while (!lane.empty()) {
             Flight& fl = lane.front();
             const cudaError_t q = cudaEventQuery(fl.done);
@@ -319,6 +335,8 @@ int retire(trx_server_t s) {
             s->inflight_bytes -= fl.bytes;
             s->inflight_reqs -= (int64_t)fl.ids.size();
             put_event(s, fl.done);
+            if (li < s->lane_cost.size())
+                s->lane_cost[li] = lane.size() == 1 ? 0.0 : s->lane_cost[li] - fl.cost;
             lane.pop_front();
         }
     }
@@ -356,6 +374,7 @@ int trx_server_create(int device, const trx_server_config_t* config, trx_server_
     s->device = device;
     s->cfg = cfg;
     s->lanes.resize((size_t)cfg.streams + 1);
+    s->lane_cost.assign((size_t)cfg.streams, 0.0);
     int rc = TRX_SUCCESS;
     for (int i = 0; i < cfg.streams && rc == TRX_SUCCESS; ++i) {
         cudaStream_t st = nullptr;

@@ -1,7 +1,7 @@
 """Binding of the library's request server (trx_server_* in include/trx.h).
 
 The scheduling (admission by slots and device-memory budget, small problems
-batched per tick, large ones round-robin over parallel streams, completion
+batched per tick, large ones on the least-loaded of parallel streams, completion
 by events) runs in the C library; this class marshals arguments and keeps
 the tensors the device is still using alive: a right-hand side until its
 request has completed, a factor until it is released and its last request
