@@ -209,20 +209,22 @@ enum {
                               a zero B). Entries must lie inside FP32's
                               exponent range (as for TRX_OPT_FP64_TRSM).
                               Uses the handle's refinement scratch        */
-    TRX_OPT_THIN = 17,     /* FP32 TRSM with few right-hand sides: 1 = one
-                              persistent CUDA-core launch in place of the
-                              recursion (64-row blocks x 16-column panels,
-                              left-looking: each block row adds its products
-                              with the published blocks before it, then
-                              multiplies by its diagonal block's inverse,
-                              made by substitution in FP32; flags between
-                              blocks, bounded waits; FP32 FMA, no operand
-                              split); -1 = the recursion; 0 = automatic
-                              (default: order above 256 with at most 64
+    TRX_OPT_THIN = 17,     /* FP32 TRSM and TRMM with few right-hand sides:
+                              1 = one persistent CUDA-core launch in place of
+                              the recursion (64-row blocks x 16-column
+                              panels; TRSM left-looking: each block row adds
+                              its products with the published blocks before
+                              it, then multiplies by its diagonal block's
+                              inverse, made by substitution in FP32, blocks
+                              published as tagged words, bounded waits;
+                              TRMM: every block row's sum from a packed copy
+                              of B, no waits; FP32 FMA, no operand split);
+                              -1 = the recursion; 0 = automatic (default:
+                              order above 256; TRSM with at most 64
                               right-hand sides, or at most 256 while order
-                              x right-hand sides <= 2^21). Its published
-                              blocks live in a handle buffer grown on first
-                              use                                         */
+                              x right-hand sides <= 2^21; TRMM with at most
+                              16). Its scratch lives in a handle buffer
+                              grown on first use                          */
     TRX_OPT_TEST_WITHHOLD = 18 /* test hook for the bounded waits: 1 = the
                               thin TRSM (TRX_OPT_THIN) never publishes its
                               first block row, so the waits of the blocks

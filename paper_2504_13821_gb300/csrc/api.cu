@@ -396,10 +396,15 @@ struct Exec {
                     bytes = 4.0 * c.k * st.b * 1.5;
                     break;
                 case kThin:
-                    e = launch_thin_trsm(*reinterpret_cast<const Canon<float>*>(&c),
-                                         (float)st.alpha, thin_scratch, h->d_err, h->wait_ns,
-                                         h->num_sms, s, h->opt_test_withhold != 0);
-                    cls = TRX_KERNEL_LEAF_TRSM;
+                    if (st.trsm)
+                        e = launch_thin_trsm(*reinterpret_cast<const Canon<float>*>(&c),
+                                             (float)st.alpha, thin_scratch, h->d_err,
+                                             h->wait_ns, h->num_sms, s,
+                                             h->opt_test_withhold != 0);
+                    else
+                        e = launch_thin_trmm(*reinterpret_cast<const Canon<float>*>(&c),
+                                             (float)st.alpha, thin_scratch, h->num_sms, s);
+                    cls = st.trsm ? TRX_KERNEL_LEAF_TRSM : TRX_KERNEL_LEAF_TRMM;
                     flops = (double)c.k * c.k * c.nrhs;
                     bytes = 4.0 * ((double)c.k * (c.k + 1) / 2 + 2.0 * c.k * c.nrhs);
                     break;
@@ -655,6 +660,7 @@ int execute(trx_handle_t h, bool trsm, char side, char uplo, char transa, char d
         body.steps.push_back(dg);
     } else if (thin) {
         Step th{kThin};
+        th.trsm = trsm;
         th.alpha = (double)alpha;
         body.steps.push_back(th);
     } else {

@@ -292,6 +292,10 @@ size_t thin_scratch_bytes(int64_t k, int64_t nrhs);
 cudaError_t launch_thin_trsm(const Canon<float>& c, float alpha, int* scratch, int* err,
                              long long wait_ns, int num_sms, cudaStream_t s,
                              bool withhold = false);
+// The thin TRMM (thin.cu): C := alpha M C in one launch after a packing
+// pass of C's original rows (no waits; the same scratch size suffices).
+cudaError_t launch_thin_trmm(const Canon<float>& c, float alpha, int* scratch, int num_sms,
+                             cudaStream_t s);
 
 // K granularity the tensor-core GEMM needs (klen and rk multiples of this).
 constexpr int kTcKQuantum = 64;

@@ -348,9 +348,15 @@ inline bool use_dag_mode(int64_t opt, bool tc, bool trsm, int elem, int64_t k, i
 constexpr int64_t kThinMaxNrhs = 64, kThinWideNrhs = 256;
 constexpr int64_t kThinMaxWork = (int64_t)1 << 21;
 constexpr int64_t kThinMinK = 256;
+// TRMM (thin.cu's one-launch product): automatically with at most
+// kThinTrmmMaxNrhs right-hand sides above order kThinMinK (measured on
+// GB300: 1.1-1.5x the recursion's grouped product up to 16 right-hand
+// sides; from 64 on the tensor-core product is faster).
+constexpr int64_t kThinTrmmMaxNrhs = 16;
 inline bool use_thin_mode(int64_t opt, bool trsm, int elem, int64_t k, int64_t nrhs) {
-    if (opt < 0 || !trsm || elem != 4 || k <= 0 || nrhs <= 0) return false;
+    if (opt < 0 || elem != 4 || k <= 0 || nrhs <= 0) return false;
     if (opt > 0) return true;
+    if (!trsm) return k > kThinMinK && nrhs <= kThinTrmmMaxNrhs;
     return k > kThinMinK &&
            (nrhs <= kThinMaxNrhs || (nrhs <= kThinWideNrhs && k * nrhs <= kThinMaxWork));
 }

@@ -372,6 +372,110 @@ __global__ void __launch_bounds__(NT, 2) thin_trsm_kernel(const Params p) {
     asm volatile("cp.async.wait_group 0;" ::: "memory");   // nothing in flight at exit
 }
 
+// ---- TRMM with few right-hand sides ---------------------------------------
+// C := alpha M C (canonical lower), one persistent launch after a packing
+// pass: task (i, p) forms the 64 x 16 block
+//     alpha (sum_{j < i} M_ij B_jp + tril(M_ii) B_ip)
+// from a packed copy of C's original rows (so no task reads a block another
+// task has overwritten) and writes it into C. The tasks need nothing from
+// one another; they are taken longest first (block rows from the bottom),
+// M tiles and packed B tiles through a three-stage cp.async ring.
+
+struct SmemM {
+    float m[STAGES][BR * LD];        // M_ij, k-major (as the TRSM's)
+    float x[STAGES][BR * NP];        // packed B_jp tiles, row-major
+    float d[BR * LD];                // M_ii's lower triangle (unit: diagonal 1), k-major
+    int task;
+};
+
+// C's original rows as tiles: tile (p, j) at Bp[(p nbr + j) * BR * NP],
+// element (kk, c) at kk * NP + c; zero past the order and the columns.
+__global__ void __launch_bounds__(256) thin_pack_kernel(const Params p, float* Bp) {
+    const int64_t e = (int64_t)blockIdx.x * 256 + threadIdx.x;
+    const int64_t total = (int64_t)p.npan * p.nbr * (BR * NP);
+    if (e >= total) return;
+    const int c = (int)(e % NP), kk = (int)((e / NP) % BR);
+    const int64_t tile = e / (BR * NP), j = tile % p.nbr, pn = tile / p.nbr;
+    const int64_t gi = j * BR + kk, gj = pn * NP + c;
+    Bp[e] = (gi < p.k && gj < p.nrhs) ? p.C[gi * p.c_rs + gj * p.c_cs] : 0.0f;
+}
+
+__device__ __forceinline__ void cp_async16(float* dst, const float* src) {
+    const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src) : "memory");
+}
+
+// M_ij and B_jp into ring stage s (one commit group).
+__device__ __forceinline__ void issue_mb(const Params& p, SmemM& sm, int s, int64_t i0, int j,
+                                         const float* btiles, bool colmajor) {
+    const int t = threadIdx.x;
+    const int rr0 = colmajor ? (t & 63) : (t >> 6), cc0 = colmajor ? (t >> 6) : (t & 63);
+    const float* src = p.A + (i0 + rr0) * p.a_rs + ((int64_t)j * BR + cc0) * p.a_cs;
+    const int64_t step = 4 * (colmajor ? p.a_cs : p.a_rs);
+    const int64_t rows_left = p.k - (i0 + rr0);
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+        const int rr = colmajor ? rr0 : rr0 + 4 * q, cc = colmajor ? cc0 + 4 * q : cc0;
+        const bool in = colmajor ? rows_left > 0 : rows_left > 4 * q;
+        cp_async4(sm.m[s] + cc * LD + rr, in ? src + q * step : p.A, in);
+    }
+    cp_async16(sm.x[s] + 4 * t, btiles + (int64_t)j * (BR * NP) + 4 * t);   // 256 x 16 B
+    cp_commit();
+}
+
+__global__ void __launch_bounds__(NT, 2) thin_trmm_kernel(const Params p, const float* Bp) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    SmemM& sm = *reinterpret_cast<SmemM*>(smem_raw);
+    const int t = threadIdx.x, ty = t >> 4, tx = t & 15;
+    const bool colmajor = p.a_rs == 1 || p.a_rs == -1;
+    while (true) {
+        __syncthreads();
+        if (t == 0) sm.task = atomicAdd(p.ticket, 1);
+        __syncthreads();
+        const int64_t task = sm.task;
+        if (task >= p.ntask) break;
+        const int i = p.nbr - 1 - (int)(task / p.npan), pn = (int)(task % p.npan);
+        const int64_t i0 = (int64_t)i * BR, c0 = (int64_t)pn * NP;
+        const float* btiles = Bp + (int64_t)pn * p.nbr * (BR * NP);
+        if (i > 0) issue_mb(p, sm, 0, i0, 0, btiles, colmajor); else cp_commit();
+        if (i > 1) issue_mb(p, sm, 1, i0, 1, btiles, colmajor); else cp_commit();
+        // M_ii's lower triangle, k-major: d[kk][r] = M(r, kk) for kk <= r
+        for (int e = t; e < BR * BR; e += NT) {
+            const int rr = colmajor ? e % BR : e / BR, cc = colmajor ? e / BR : e % BR;
+            const int64_t gi = i0 + rr, gj = i0 + cc;
+            float v = 0.0f;
+            if (gi < p.k) {
+                if (cc < rr) v = __ldg(p.A + gi * p.a_rs + gj * p.a_cs);
+                else if (cc == rr) v = p.unit ? 1.0f : __ldg(p.A + gi * p.a_rs + gj * p.a_cs);
+            }
+            sm.d[cc * LD + rr] = v;
+        }
+        float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+        for (int j = 0; j < i; ++j) {
+            cp_wait_1();                             // this thread's copies of tile j
+            __syncthreads();
+            // tile j - 1's stage is free: tile j + 2 goes there
+            if (j + 2 < i) issue_mb(p, sm, (j + 2) % STAGES, i0, j + 2, btiles, colmajor);
+            else cp_commit();
+            mma_tile(sm.m[j % STAGES], sm.x[j % STAGES], BR, acc);
+            __syncthreads();
+        }
+        // the diagonal block with B_ip (plain loads into stage 0's x)
+        asm volatile("cp.async.wait_group 0;" ::: "memory");
+        __syncthreads();
+        *reinterpret_cast<float4*>(sm.x[0] + 4 * t) =
+            *reinterpret_cast<const float4*>(btiles + (int64_t)i * (BR * NP) + 4 * t);
+        __syncthreads();
+        mma_tile(sm.d, sm.x[0], 8 * ((t >> 5) + 1), acc);   // lower: kk <= row
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const int64_t gi = i0 + 4 * ty + e, gj = c0 + tx;
+            if (gi < p.k && gj < p.nrhs) p.C[gi * p.c_rs + gj * p.c_cs] = p.alpha * acc[e];
+        }
+    }
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+}
+
 }  // namespace thin
 
 size_t thin_scratch_bytes(int64_t k, int64_t nrhs) {
@@ -380,9 +484,18 @@ size_t thin_scratch_bytes(int64_t k, int64_t nrhs) {
     return 16 + (size_t)(nbr * npan) * kThinBlock * kThinPanel * 8;
 }
 
-static int g_thin_ctas_per_sm = 0;
+static int g_thin_ctas_per_sm = 0, g_thin_trmm_ctas_per_sm = 0;
 
 cudaError_t thin_configure() {
+    cudaError_t e0 = cudaFuncSetAttribute(thin::thin_trmm_kernel,
+                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)sizeof(thin::SmemM));
+    if (e0 != cudaSuccess) return e0;
+    int nm = 0;
+    e0 = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nm, thin::thin_trmm_kernel, thin::NT,
+                                                       sizeof(thin::SmemM));
+    if (e0 != cudaSuccess) return e0;
+    g_thin_trmm_ctas_per_sm = nm > 0 ? nm : 1;
     cudaError_t e = cudaFuncSetAttribute(thin::thin_trsm_kernel,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)sizeof(thin::Smem));
@@ -427,6 +540,42 @@ cudaError_t launch_thin_trsm(const Canon<float>& c, float alpha, int* scratch, i
     const int64_t cap = (int64_t)num_sms * per_sm;
     const int grid = (int)(p.ntask < cap ? p.ntask : cap);
     thin::thin_trsm_kernel<<<grid, thin::NT, sizeof(thin::Smem), s>>>(p);
+    return cudaGetLastError();
+}
+
+// The thin TRMM: ticket, then C's rows packed by tiles (thin_scratch_bytes
+// covers both), zeroed / written by the launch itself.
+cudaError_t launch_thin_trmm(const Canon<float>& c, float alpha, int* scratch, int num_sms,
+                             cudaStream_t s) {
+    if (c.k <= 0 || c.nrhs <= 0) return cudaSuccess;
+    thin::Params p{};
+    p.k = c.k;
+    p.nrhs = c.nrhs;
+    p.A = c.A;
+    p.a_rs = c.a_rs;
+    p.a_cs = c.a_cs;
+    p.C = c.C;
+    p.c_rs = c.c_rs;
+    p.c_cs = c.c_cs;
+    p.alpha = alpha;
+    p.unit = c.unit ? 1 : 0;
+    const int64_t nbr = (c.k + kThinBlock - 1) / kThinBlock;
+    const int64_t npan = (c.nrhs + kThinPanel - 1) / kThinPanel;
+    if (nbr * npan > (int64_t)1 << 30) return cudaErrorInvalidValue;
+    p.nbr = (int)nbr;
+    p.npan = (int)npan;
+    p.ntask = nbr * npan;
+    p.ticket = scratch;
+    float* Bp = reinterpret_cast<float*>(reinterpret_cast<char*>(scratch) + 16);
+    cudaError_t e = cudaMemsetAsync(scratch, 0, 16, s);
+    if (e != cudaSuccess) return e;
+    const int64_t total = p.ntask * (kThinBlock * kThinPanel);
+    thin::thin_pack_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(p, Bp);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    const int per_sm = g_thin_trmm_ctas_per_sm > 0 ? g_thin_trmm_ctas_per_sm : 1;
+    const int64_t cap = (int64_t)num_sms * per_sm;
+    const int grid = (int)(p.ntask < cap ? p.ntask : cap);
+    thin::thin_trmm_kernel<<<grid, thin::NT, sizeof(thin::SmemM), s>>>(p, Bp);
     return cudaGetLastError();
 }
 

@@ -1,7 +1,8 @@
-"""The persistent CUDA-core FP32 TRSM for thin right-hand sides
-(TRX_OPT_THIN, csrc/thin.cu): 64-row blocks x 16-column panels solved
-left-looking in one launch, diagonal blocks by their inverses, against the
-FP64 oracle and the recursive chain.
+"""The persistent CUDA-core FP32 TRSM and TRMM for thin right-hand sides
+(TRX_OPT_THIN, csrc/thin.cu): 64-row blocks x 16-column panels; TRSM solved
+left-looking in one launch, diagonal blocks by their inverses; TRMM summed
+per block row from a packed copy of B. Against the FP64 oracle and the
+recursive chain.
 
 - all 16 variants at ragged orders (300, 1000) with 1, 17 and 64
   right-hand sides, alpha 1.5 / -2, padded lda / ldb (padding untouched):
@@ -13,7 +14,11 @@ FP64 oracle and the recursive chain.
   against the oracle, bitwise repeatable, within the FP32 bound of the
   recursive chain; the default (automatic) mode takes this path;
 - a bounded wait run out (the first block row withheld by the test hook,
-  1 ms budget) is reported as TRX_ERR_TIMEOUT and the next call is correct.
+  1 ms budget) is reported as TRX_ERR_TIMEOUT and the next call is correct;
+- TRMM: all 16 variants at the same shapes (normwise error within 8 k u),
+  order 40 and 1024 x 200 forced on, order 8192 with 16 right-hand sides
+  against the oracle (sampled), bitwise repeatable, within the FP32 bound
+  of the recursive product.
 """
 import numpy as np
 import pytest
@@ -110,3 +115,50 @@ def test_thin_bounded_wait_reports_timeout(trx):
     run_case("trsm", "L", "L", "N", "N", 4096, 16, 1.0, np.float32, seed=6, handle=h)
     assert h.check_device_error() == 0
     h.close()
+
+
+@pytest.mark.parametrize("side,uplo,trans,diag", VARIANTS)
+def test_thin_trmm_all_variants(trx, side, uplo, trans, diag):
+    h = thin_handle(trx)
+    vi = VARIANTS.index((side, uplo, trans, diag))
+    for k, nrhs, alpha, pads in ((300, 1, 1.5, (0, 0)), (300, 17, -2.0, (3, 5)),
+                                 (1000, 64, 1.5, (0, 7))):
+        m, n = (k, nrhs) if side == "L" else (nrhs, k)
+        run_case("trmm", side, uplo, trans, diag, m, n, alpha, np.float32,
+                 seed=inputs.variant_seed(k + nrhs + 7, vi), handle=h, lda_pad=pads[0],
+                 ldb_pad=pads[1])
+    h.close()
+
+
+def test_thin_trmm_forced_and_large(trx):
+    h = thin_handle(trx)
+    run_case("trmm", "L", "U", "N", "U", 40, 9, 1.25, np.float32, seed=51, handle=h)
+    run_case("trmm", "R", "L", "T", "N", 200, 1024, -0.5, np.float32, seed=52, handle=h)
+    h.close()
+    k, n = 8192, 16
+    A, B = inputs.problem("L", "U", k, n, seed=8193, dtype=np.float32)
+    At = to_dev(A, "cuda:0")
+    h = trx.Handle(0)                                   # automatic: the thin product
+    outs = []
+    for _ in range(2):
+        Bt = to_dev(B, "cuda:0")
+        trx.trmm("L", "U", "T", "N", 0.75, At, Bt, handle=h)
+        outs.append(Bt)
+    hc = thin_handle(trx, -1)
+    Bc = to_dev(B, "cuda:0")
+    trx.trmm("L", "U", "T", "N", 0.75, At, Bc, handle=hc)
+    torch.cuda.synchronize()
+    assert torch.equal(outs[0], outs[1]), "not bitwise repeatable"
+    X = outs[0].cpu().numpy().astype(np.float64)
+    Xc = Bc.cpu().numpy().astype(np.float64)
+    ninf = lambda a: np.abs(a).sum(axis=1).max()          # noqa: E731
+    A64 = np.triu(np.nan_to_num(A.astype(np.float64)))
+    assert ninf(X - Xc) <= bound(k, np.float32) * ninf(A64) * ninf(B.astype(np.float64))
+    cols = np.array([1, 8, 15])
+    Bs = np.asfortranarray(B[:, cols].astype(np.float64))
+    C_ref = oracle.trmm("L", "U", "T", "N", 0.75, A.astype(np.float64), Bs)
+    err = oracle.trmm_error("L", "U", "T", "N", 0.75, A.astype(np.float64),
+                            np.asfortranarray(X[:, cols]), C_ref, Bs)
+    assert err <= bound(k, np.float32), err
+    h.close()
+    hc.close()
