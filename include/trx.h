@@ -218,12 +218,13 @@ enum {
                               inverse, made by substitution in FP32, blocks
                               published as tagged words, bounded waits;
                               TRMM: every block row's sum from a packed copy
-                              of B, no waits; FP32 FMA, no operand split);
+                              of B, long rows in pieces added in a fixed
+                              order, no waits; FP32 FMA, no operand split);
                               -1 = the recursion; 0 = automatic (default:
                               order above 256; TRSM with at most 64
                               right-hand sides, or at most 256 while order
                               x right-hand sides <= 2^21; TRMM with at most
-                              16). Its scratch lives in a handle buffer
+                              32). Its scratch lives in a handle buffer
                               grown on first use                          */
     TRX_OPT_TEST_WITHHOLD = 18 /* test hook for the bounded waits: 1 = the
                               thin TRSM (TRX_OPT_THIN) never publishes its

@@ -523,14 +523,17 @@ int execute(trx_handle_t h, bool trsm, char side, char uplo, char transa, char d
     // (never inside a stream capture: a capture keeps the recursive chain).
     bool thin = std::is_same<T, float>::value &&
                 use_thin_mode(h->opt_thin, trsm, (int)sizeof(T), k, ex.c.nrhs);
-    if (thin && h->thin_bytes < thin_scratch_bytes(k, ex.c.nrhs)) {
+    const size_t thin_need = !thin ? 0
+                             : trsm ? thin_scratch_bytes(k, ex.c.nrhs)
+                                    : thin_trmm_scratch_bytes(k, ex.c.nrhs);
+    if (thin && h->thin_bytes < thin_need) {
         cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
         e = cudaStreamIsCapturing(s, &cs);
         if (e != cudaSuccess) return fail_cuda(e, "cudaStreamIsCapturing");
         if (cs != cudaStreamCaptureStatusNone) {
             thin = false;
         } else {
-            const size_t want = std::max<size_t>(2 * thin_scratch_bytes(k, ex.c.nrhs), 1 << 16);
+            const size_t want = std::max<size_t>(2 * thin_need, 1 << 16);
             if (h->thin_buf) cudaFree(h->thin_buf);        // waits for its last use
             h->thin_buf = nullptr;
             h->thin_bytes = 0;

@@ -293,7 +293,8 @@ cudaError_t launch_thin_trsm(const Canon<float>& c, float alpha, int* scratch, i
                              long long wait_ns, int num_sms, cudaStream_t s,
                              bool withhold = false);
 // The thin TRMM (thin.cu): C := alpha M C in one launch after a packing
-// pass of C's original rows (no waits; the same scratch size suffices).
+// pass of C's original rows (no waits); scratch: thin_trmm_scratch_bytes.
+size_t thin_trmm_scratch_bytes(int64_t k, int64_t nrhs);
 cudaError_t launch_thin_trmm(const Canon<float>& c, float alpha, int* scratch, int num_sms,
                              cudaStream_t s);
 

@@ -350,9 +350,9 @@ constexpr int64_t kThinMaxWork = (int64_t)1 << 21;
 constexpr int64_t kThinMinK = 256;
 // TRMM (thin.cu's one-launch product): automatically with at most
 // kThinTrmmMaxNrhs right-hand sides above order kThinMinK (measured on
-// GB300: 1.1-1.5x the recursion's grouped product up to 16 right-hand
-// sides; from 64 on the tensor-core product is faster).
-constexpr int64_t kThinTrmmMaxNrhs = 16;
+// GB300: 1.1-2.9x the recursion's grouped product up to 32 right-hand
+// sides; from 64 on the tensor-core product is as fast or faster).
+constexpr int64_t kThinTrmmMaxNrhs = 32;
 inline bool use_thin_mode(int64_t opt, bool trsm, int elem, int64_t k, int64_t nrhs) {
     if (opt < 0 || elem != 4 || k <= 0 || nrhs <= 0) return false;
     if (opt > 0) return true;

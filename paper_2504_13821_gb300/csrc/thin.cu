@@ -386,6 +386,7 @@ struct SmemM {
     float x[STAGES][BR * NP];        // packed B_jp tiles, row-major
     float d[BR * LD];                // M_ii's lower triangle (unit: diagonal 1), k-major
     int task;
+    int last;                        // this CTA's piece arrived last in its row
 };
 
 // C's original rows as tiles: tile (p, j) at Bp[(p nbr + j) * BR * NP],
@@ -423,50 +424,106 @@ __device__ __forceinline__ void issue_mb(const Params& p, SmemM& sm, int s, int6
     cp_commit();
 }
 
-__global__ void __launch_bounds__(NT, 2) thin_trmm_kernel(const Params p, const float* Bp) {
+// Long block rows are cut into pieces of at most kPiece off-diagonal tiles
+// (the last piece also takes the diagonal block), so no task streams more
+// than kPiece + 1 tiles; a row of several pieces writes their partial sums
+// to slots, and the piece that arrives last (an atomic count per row)
+// adds them in piece order, so the result does not depend on which CTA
+// finishes when. Pieces of row i: P_i = max(1, ceil(i / kPiece)).
+constexpr int kPiece = 32;
+__host__ __device__ __forceinline__ int64_t pieces_of(int64_t i) {
+    return i == 0 ? 1 : (i + kPiece - 1) / kPiece;
+}
+// pieces of rows 0 .. r (r >= -1)
+__host__ __device__ __forceinline__ int64_t pieces_upto(int64_t r) {
+    if (r < 0) return 0;
+    const int64_t a = r / kPiece, b = r % kPiece;
+    return 1 + (int64_t)kPiece / 2 * a * (a + 1) + b * (a + 1);
+}
+
+__global__ void __launch_bounds__(NT, 2) thin_trmm_kernel(const Params p, const float* Bp,
+                                                          float* part, int* count) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     SmemM& sm = *reinterpret_cast<SmemM*>(smem_raw);
     const int t = threadIdx.x, ty = t >> 4, tx = t & 15;
     const bool colmajor = p.a_rs == 1 || p.a_rs == -1;
+    const int64_t total = pieces_upto(p.nbr - 1);
     while (true) {
         __syncthreads();
         if (t == 0) sm.task = atomicAdd(p.ticket, 1);
         __syncthreads();
         const int64_t task = sm.task;
         if (task >= p.ntask) break;
-        const int i = p.nbr - 1 - (int)(task / p.npan), pn = (int)(task % p.npan);
+        // pieces are taken from the bottom row up: piece index tp counts
+        // down from the last row's pieces
+        const int64_t tp = task / p.npan;
+        const int pn = (int)(task % p.npan);
+        int lo = 0, hi = p.nbr - 1;                  // largest i with pieces of rows >= i > tp
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (total - pieces_upto(mid - 1) > tp) lo = mid; else hi = mid - 1;
+        }
+        const int i = lo;
+        const int64_t np_i = pieces_of(i);
+        const int q = (int)(tp - (total - pieces_upto(i)));
+        const bool last_piece = q == np_i - 1;
+        const int jb = q * kPiece, je = (int)((q + 1) * kPiece < i ? (q + 1) * kPiece : i);
         const int64_t i0 = (int64_t)i * BR, c0 = (int64_t)pn * NP;
         const float* btiles = Bp + (int64_t)pn * p.nbr * (BR * NP);
-        if (i > 0) issue_mb(p, sm, 0, i0, 0, btiles, colmajor); else cp_commit();
-        if (i > 1) issue_mb(p, sm, 1, i0, 1, btiles, colmajor); else cp_commit();
-        // M_ii's lower triangle, k-major: d[kk][r] = M(r, kk) for kk <= r
-        for (int e = t; e < BR * BR; e += NT) {
-            const int rr = colmajor ? e % BR : e / BR, cc = colmajor ? e / BR : e % BR;
-            const int64_t gi = i0 + rr, gj = i0 + cc;
-            float v = 0.0f;
-            if (gi < p.k) {
-                if (cc < rr) v = __ldg(p.A + gi * p.a_rs + gj * p.a_cs);
-                else if (cc == rr) v = p.unit ? 1.0f : __ldg(p.A + gi * p.a_rs + gj * p.a_cs);
+        if (jb < je) issue_mb(p, sm, jb % STAGES, i0, jb, btiles, colmajor); else cp_commit();
+        if (jb + 1 < je) issue_mb(p, sm, (jb + 1) % STAGES, i0, jb + 1, btiles, colmajor);
+        else cp_commit();
+        if (last_piece) {
+            // M_ii's lower triangle, k-major: d[kk][r] = M(r, kk) for kk <= r
+            for (int e = t; e < BR * BR; e += NT) {
+                const int rr = colmajor ? e % BR : e / BR, cc = colmajor ? e / BR : e % BR;
+                const int64_t gi = i0 + rr, gj = i0 + cc;
+                float v = 0.0f;
+                if (gi < p.k) {
+                    if (cc < rr) v = __ldg(p.A + gi * p.a_rs + gj * p.a_cs);
+                    else if (cc == rr) v = p.unit ? 1.0f : __ldg(p.A + gi * p.a_rs + gj * p.a_cs);
+                }
+                sm.d[cc * LD + rr] = v;
             }
-            sm.d[cc * LD + rr] = v;
         }
         float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-        for (int j = 0; j < i; ++j) {
+        for (int j = jb; j < je; ++j) {
             cp_wait_1();                             // this thread's copies of tile j
             __syncthreads();
             // tile j - 1's stage is free: tile j + 2 goes there
-            if (j + 2 < i) issue_mb(p, sm, (j + 2) % STAGES, i0, j + 2, btiles, colmajor);
+            if (j + 2 < je) issue_mb(p, sm, (j + 2) % STAGES, i0, j + 2, btiles, colmajor);
             else cp_commit();
             mma_tile(sm.m[j % STAGES], sm.x[j % STAGES], BR, acc);
             __syncthreads();
         }
-        // the diagonal block with B_ip (plain loads into stage 0's x)
         asm volatile("cp.async.wait_group 0;" ::: "memory");
         __syncthreads();
-        *reinterpret_cast<float4*>(sm.x[0] + 4 * t) =
-            *reinterpret_cast<const float4*>(btiles + (int64_t)i * (BR * NP) + 4 * t);
-        __syncthreads();
-        mma_tile(sm.d, sm.x[0], 8 * ((t >> 5) + 1), acc);   // lower: kk <= row
+        if (last_piece) {
+            // the diagonal block with B_ip (plain loads into stage 0's x)
+            *reinterpret_cast<float4*>(sm.x[0] + 4 * t) =
+                *reinterpret_cast<const float4*>(btiles + (int64_t)i * (BR * NP) + 4 * t);
+            __syncthreads();
+            mma_tile(sm.d, sm.x[0], 8 * ((t >> 5) + 1), acc);   // lower: kk <= row
+        }
+        if (np_i > 1) {
+            // partial sums to this piece's slot; the last to arrive combines
+            float* slots = part + ((int64_t)pn * total + pieces_upto(i - 1)) * (BR * NP);
+#pragma unroll
+            for (int e = 0; e < 4; ++e) __stcg(slots + q * (BR * NP) + (4 * ty + e) * NP + tx, acc[e]);
+            __threadfence();
+            __syncthreads();
+            if (t == 0) sm.last = atomicAdd(count + (int64_t)pn * p.nbr + i, 1) == np_i - 1;
+            __syncthreads();
+            if (!sm.last) continue;
+            __threadfence();
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                float sum = 0.0f;
+                for (int64_t r = 0; r < np_i; ++r)
+                    sum += __ldcg(slots + r * (BR * NP) + (4 * ty + e) * NP + tx);
+                acc[e] = sum;
+            }
+        }
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
             const int64_t gi = i0 + 4 * ty + e, gj = c0 + tx;
@@ -543,8 +600,19 @@ cudaError_t launch_thin_trsm(const Canon<float>& c, float alpha, int* scratch, i
     return cudaGetLastError();
 }
 
-// The thin TRMM: ticket, then C's rows packed by tiles (thin_scratch_bytes
-// covers both), zeroed / written by the launch itself.
+// The thin TRMM's scratch: ticket (16 bytes), per-row piece counts, C's
+// rows packed by tiles, the pieces' partial sums; zeroed / written by the
+// launch itself.
+static int64_t align_words(int64_t n) { return (n + 3) / 4 * 4; }   // 16-byte steps (4-byte words)
+
+size_t thin_trmm_scratch_bytes(int64_t k, int64_t nrhs) {
+    const int64_t nbr = (k + kThinBlock - 1) / kThinBlock;
+    const int64_t npan = (nrhs + kThinPanel - 1) / kThinPanel;
+    const int64_t tile = (int64_t)kThinBlock * kThinPanel;
+    return 4 * (size_t)(4 + align_words(nbr * npan) + nbr * npan * tile +
+                        thin::pieces_upto(nbr - 1) * npan * tile);
+}
+
 cudaError_t launch_thin_trmm(const Canon<float>& c, float alpha, int* scratch, int num_sms,
                              cudaStream_t s) {
     if (c.k <= 0 || c.nrhs <= 0) return cudaSuccess;
@@ -561,21 +629,24 @@ cudaError_t launch_thin_trmm(const Canon<float>& c, float alpha, int* scratch, i
     p.unit = c.unit ? 1 : 0;
     const int64_t nbr = (c.k + kThinBlock - 1) / kThinBlock;
     const int64_t npan = (c.nrhs + kThinPanel - 1) / kThinPanel;
-    if (nbr * npan > (int64_t)1 << 30) return cudaErrorInvalidValue;
+    const int64_t total = thin::pieces_upto(nbr - 1);
+    if (total * npan > (int64_t)1 << 30) return cudaErrorInvalidValue;
     p.nbr = (int)nbr;
     p.npan = (int)npan;
-    p.ntask = nbr * npan;
+    p.ntask = total * npan;
     p.ticket = scratch;
-    float* Bp = reinterpret_cast<float*>(reinterpret_cast<char*>(scratch) + 16);
-    cudaError_t e = cudaMemsetAsync(scratch, 0, 16, s);
+    int* count = scratch + 4;
+    float* Bp = reinterpret_cast<float*>(scratch + 4 + align_words(nbr * npan));
+    float* part = Bp + nbr * npan * (int64_t)(kThinBlock * kThinPanel);
+    cudaError_t e = cudaMemsetAsync(scratch, 0, 4 * (size_t)(4 + align_words(nbr * npan)), s);
     if (e != cudaSuccess) return e;
-    const int64_t total = p.ntask * (kThinBlock * kThinPanel);
-    thin::thin_pack_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(p, Bp);
+    const int64_t packed = nbr * npan * (kThinBlock * kThinPanel);
+    thin::thin_pack_kernel<<<(unsigned)((packed + 255) / 256), 256, 0, s>>>(p, Bp);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     const int per_sm = g_thin_trmm_ctas_per_sm > 0 ? g_thin_trmm_ctas_per_sm : 1;
     const int64_t cap = (int64_t)num_sms * per_sm;
     const int grid = (int)(p.ntask < cap ? p.ntask : cap);
-    thin::thin_trmm_kernel<<<grid, thin::NT, sizeof(thin::SmemM), s>>>(p, Bp);
+    thin::thin_trmm_kernel<<<grid, thin::NT, sizeof(thin::SmemM), s>>>(p, Bp, part, count);
     return cudaGetLastError();
 }
 
