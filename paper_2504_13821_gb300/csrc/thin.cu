@@ -71,7 +71,9 @@ struct Params {
     int withhold;    // test hook: block row 0 is never published (waits run out)
 };
 
-constexpr int STAGES = 3;            // M tiles in flight (cp.async ring)
+// Ring stages: STAGES - 1 tiles in flight (cp.async); four stages measured
+// the same as three.
+constexpr int STAGES = 3;
 
 struct Smem {
     // M_ij tiles, k-major: m[s][kk * LD + r] = M[i0 + r][j0 + kk]; tile j of
@@ -167,7 +169,10 @@ __device__ __forceinline__ void cp_async4(float* dst, const float* src, bool val
                  : "memory");
 }
 __device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void cp_wait_1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+// all but the newest STAGES - 2 groups complete: the oldest tile in flight has landed
+__device__ __forceinline__ void cp_wait_ring() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(STAGES - 2) : "memory");
+}
 
 // Tile (i0.., j0..) of M into ring stage `dst` by cp.async (element by
 // element along M's contiguous direction, into the k-major layout); rows
@@ -188,19 +193,39 @@ __device__ __forceinline__ void issue_m(const Params& p, float* dst, int64_t i0,
     cp_commit();
 }
 
-// acc[e] += sum_kk a[kk][4 ty + e] * x[kk][tx] over kk < kend.
+// Packed FP32 pairs: fma.rn.f32x2 does two independent round-to-nearest
+// FMAs in one instruction (the same results as two fmaf).
+__device__ __forceinline__ uint64_t pk2(float a, float b) {
+    uint64_t r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ void upk2(uint64_t r, float& a, float& b) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(r));
+}
+__device__ __forceinline__ uint64_t fma2(uint64_t a, uint64_t b, uint64_t c) {
+    uint64_t d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+
+// acc[e] += sum_kk a[kk][4 ty + e] * x[kk][tx] over kk < kend (rows in
+// packed pairs (4 ty, 4 ty + 1), (4 ty + 2, 4 ty + 3): two FMA
+// instructions per kk instead of four).
 __device__ __forceinline__ void mma_tile(const float* a, const float* x, int kend,
                                          float (&acc)[4]) {
     const int ty = threadIdx.x >> 4, tx = threadIdx.x & 15;
+    uint64_t s01 = pk2(acc[0], acc[1]), s23 = pk2(acc[2], acc[3]);
 #pragma unroll 8
     for (int kk = 0; kk < kend; ++kk) {
         const float4 m = *reinterpret_cast<const float4*>(a + kk * LD + 4 * ty);
         const float xv = x[kk * NP + tx];
-        acc[0] = fmaf(m.x, xv, acc[0]);
-        acc[1] = fmaf(m.y, xv, acc[1]);
-        acc[2] = fmaf(m.z, xv, acc[2]);
-        acc[3] = fmaf(m.w, xv, acc[3]);
+        const uint64_t xx = pk2(xv, xv);
+        s01 = fma2(pk2(m.x, m.y), xx, s01);
+        s23 = fma2(pk2(m.z, m.w), xx, s23);
     }
+    upk2(s01, acc[0], acc[1]);
+    upk2(s23, acc[2], acc[3]);
 }
 
 // inv(M_ii) into sm.inv. M_ii's lower triangle goes to a work tile (aliasing
@@ -316,23 +341,27 @@ __global__ void __launch_bounds__(NT, 2) thin_trsm_kernel(const Params p) {
             b[e] = (gi < p.k && gj < p.nrhs) ? __ldcg(p.C + gi * p.c_rs + gj * p.c_cs) : 0.0f;
         }
         // S' = sum_{j < i-1} M_ij X_jp (X_i-1,p enters through Z): tile j of M
-        // arrives through the cp.async ring (two tiles ahead), X_jp's words
+        // arrives through the cp.async ring (STAGES - 1 tiles ahead), X_jp's words
         // are loaded one step ahead
         float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
         unsigned long long w[Q];
         const int jz = i - 1;
-        if (jz > 0) issue_m(p, sm.m[1], i0, 0, colmajor); else cp_commit();
-        if (jz > 1) issue_m(p, sm.m[2], i0, BR, colmajor); else cp_commit();
+#pragma unroll
+        for (int q = 0; q < STAGES - 1; ++q) {      // tiles 0 .. STAGES - 2
+            if (q < jz) issue_m(p, sm.m[(q + 1) % STAGES], i0, (int64_t)q * BR, colmajor);
+            else cp_commit();
+        }
         invert_diag(p, sm, i0);
         if (i > 0) make_z(p, sm, i0, colmajor);
         if (jz > 0) issue_x(p, pn, 0, w);
         for (int j = 0; j < jz; ++j) {
-            cp_wait_1();                                  // this thread's copies of tile j
+            cp_wait_ring();                               // this thread's copies of tile j
             if (!finish_x(p, sm, pn, j, w)) sm.abort = 1;
             __syncthreads();
             if (sm.abort) break;
-            // tile j - 1's stage is free: tile j + 2 goes there
-            if (j + 2 < jz) issue_m(p, sm.m[j % STAGES], i0, (int64_t)(j + 2) * BR, colmajor);
+            // tile j - 1's stage is free: tile j + STAGES - 1 goes there
+            if (j + STAGES - 1 < jz)
+                issue_m(p, sm.m[j % STAGES], i0, (int64_t)(j + STAGES - 1) * BR, colmajor);
             else cp_commit();
             if (j + 1 < jz) issue_x(p, pn, j + 1, w);
             mma_tile(sm.m[(j + 1) % STAGES], sm.x, BR, acc);
@@ -379,7 +408,7 @@ __global__ void __launch_bounds__(NT, 2) thin_trsm_kernel(const Params p) {
 // from a packed copy of C's original rows (so no task reads a block another
 // task has overwritten) and writes it into C. The tasks need nothing from
 // one another; they are taken longest first (block rows from the bottom),
-// M tiles and packed B tiles through a three-stage cp.async ring.
+// M tiles and packed B tiles through a cp.async ring.
 
 struct SmemM {
     float m[STAGES][BR * LD];        // M_ij, k-major (as the TRSM's)
@@ -470,9 +499,11 @@ __global__ void __launch_bounds__(NT, 2) thin_trmm_kernel(const Params p, const 
         const int jb = q * kPiece, je = (int)((q + 1) * kPiece < i ? (q + 1) * kPiece : i);
         const int64_t i0 = (int64_t)i * BR, c0 = (int64_t)pn * NP;
         const float* btiles = Bp + (int64_t)pn * p.nbr * (BR * NP);
-        if (jb < je) issue_mb(p, sm, jb % STAGES, i0, jb, btiles, colmajor); else cp_commit();
-        if (jb + 1 < je) issue_mb(p, sm, (jb + 1) % STAGES, i0, jb + 1, btiles, colmajor);
-        else cp_commit();
+#pragma unroll
+        for (int q = 0; q < STAGES - 1; ++q) {      // tiles jb .. jb + STAGES - 2
+            if (jb + q < je) issue_mb(p, sm, (jb + q) % STAGES, i0, jb + q, btiles, colmajor);
+            else cp_commit();
+        }
         if (last_piece) {
             // M_ii's lower triangle, k-major: d[kk][r] = M(r, kk) for kk <= r
             for (int e = t; e < BR * BR; e += NT) {
@@ -488,10 +519,11 @@ __global__ void __launch_bounds__(NT, 2) thin_trmm_kernel(const Params p, const 
         }
         float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
         for (int j = jb; j < je; ++j) {
-            cp_wait_1();                             // this thread's copies of tile j
+            cp_wait_ring();                          // this thread's copies of tile j
             __syncthreads();
-            // tile j - 1's stage is free: tile j + 2 goes there
-            if (j + 2 < je) issue_mb(p, sm, (j + 2) % STAGES, i0, j + 2, btiles, colmajor);
+            // tile j - 1's stage is free: tile j + STAGES - 1 goes there
+            if (j + STAGES - 1 < je)
+                issue_mb(p, sm, (j + STAGES - 1) % STAGES, i0, j + STAGES - 1, btiles, colmajor);
             else cp_commit();
             mma_tile(sm.m[j % STAGES], sm.x[j % STAGES], BR, acc);
             __syncthreads();
