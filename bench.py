@@ -49,14 +49,14 @@ SPLIT_DESC = {6: "3 BF16 slices per operand, every slice product above 2^-24: FP
 REF_SAMPLE_COLS = 16      # per step of --impl reference
 
 
-# DRAM traffic of gemm_tc_kernel per launch on this workload. Counters beyond
-# the launch time are only ever captured on a small case (one kernel, one to
-# three launches, a few GB on the device): the dominant kernel's launches on
-# this workload range from the 8192 x 16384 x 8192 top update down to K = 128,
-# so no small capture scales to "one launch" of this step and the line
-# reports null; the small-case figures (DRAM bytes against the algorithmic
-# bytes of the captured update) are in the profiles/ summary of the kernel.
-TRAFFIC_PER_LAUNCH = None
+# DRAM traffic of gemm_tc_kernel per launch on this workload (m = n = 16384,
+# 6-term split): dram__bytes_read.sum + dram__bytes_write.sum summed over the
+# 132 GEMM launches of one step and divided by 132. The two counters take one
+# ncu pass (checked on a small case first), so the capture is the full-size
+# launch list with two metrics; command and figures in
+# profiles/gemm_tc_traffic_step_n16384.md. To be set back to None (null in
+# the line) whenever gemm_tc.cu or the plan changes, until captured again.
+TRAFFIC_PER_LAUNCH = 316.27e6
 # FP64 FMA rate measured by this build's own probe (bench.py --workload
 # peaks; MEASURED_PEAKS.json holds no FP64 figure): the FP64 roofline
 FP64_FMA_PROBE_TFLOPS = 1.057
