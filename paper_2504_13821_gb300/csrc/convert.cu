@@ -28,9 +28,20 @@ __device__ __forceinline__ __nv_bfloat16* y_plane(const Planes& pl, int q) {
     return q == 0 ? pl.y_hi : q == 1 ? pl.y_lo : pl.y_lo2;
 }
 
+// Two floats to BF16 (round to nearest even, as __float2bfloat16_rn), a in
+// the high half; and the halves back to float (exact).
+__device__ __forceinline__ uint32_t bf16x2(float a, float b) {
+    uint32_t r;
+    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ float bf_hi(uint32_t u) { return __uint_as_float(u & 0xffff0000u); }
+__device__ __forceinline__ float bf_lo(uint32_t u) { return __uint_as_float(u << 16); }
+
 // M planes: 64x64 tiles of the lower triangle (tiles above it exit at once,
 // except inside a diagonal block of zdb tiles when zdb > 0), read along A's
-// contiguous index, written as BF16 pairs along l.
+// contiguous index (every load of a thread issued before its first shared
+// store), written four l values at a time: 8-byte stores of packed slices.
 __global__ void __launch_bounds__(256) convert_m_kernel(Canon<float> p, Planes pl, int zdb) {
     pdl_trigger();
     pdl_wait();
@@ -40,30 +51,54 @@ __global__ void __launch_bounds__(256) convert_m_kernel(Canon<float> p, Planes p
     const int64_t i0 = ti * 64, l0 = tl * 64;
     const int tid = threadIdx.x;
     const bool row_fast = (p.a_rs == 1 || p.a_rs == -1);
+    float v[16];
 #pragma unroll
     for (int u = 0; u < 16; ++u) {
         const int e = tid + 256 * u;
         const int ii = row_fast ? (e & 63) : (e >> 6), ll = row_fast ? (e >> 6) : (e & 63);
         const int64_t i = i0 + ii, l = l0 + ll;
-        tile[ii][ll] = (i < p.k && l < i) ? p.A[i * p.a_rs + l * p.a_cs] : 0.f;
+        v[u] = (i < p.k && l < i) ? p.A[i * p.a_rs + l * p.a_cs] : 0.f;
+    }
+#pragma unroll
+    for (int u = 0; u < 16; ++u) {
+        const int e = tid + 256 * u;
+        const int ii = row_fast ? (e & 63) : (e >> 6), ll = row_fast ? (e >> 6) : (e & 63);
+        tile[ii][ll] = v[u];
     }
     __syncthreads();
+    const bool vec = (pl.ldm & 3) == 0 && (reinterpret_cast<uintptr_t>(pl.m_hi) & 7) == 0 &&
+                     (reinterpret_cast<uintptr_t>(pl.m_lo) & 7) == 0 &&
+                     (reinterpret_cast<uintptr_t>(pl.m_lo2) & 7) == 0;
 #pragma unroll
-    for (int u = 0; u < 8; ++u) {
+    for (int u = 0; u < 4; ++u) {
         const int e = tid + 256 * u;
-        const int ii = e >> 5, lp = (e & 31) * 2;
-        const int64_t i = i0 + ii, l = l0 + lp;
+        const int ii = e >> 4, lq = (e & 15) * 4;
+        const int64_t i = i0 + ii, l = l0 + lq;
         if (i >= p.k || l >= p.k) continue;
-        __nv_bfloat16 v0[3], v1[3];
-        split_slices(tile[ii][lp], pl.slices, v0);
         const int64_t off = i * pl.ldm + l;
-        if (l + 1 < p.k) {
-            split_slices(tile[ii][lp + 1], pl.slices, v1);
-            for (int q = 0; q < pl.slices; ++q)
-                *reinterpret_cast<__nv_bfloat162*>(m_plane(pl, q) + off) =
-                    __halves2bfloat162(v0[q], v1[q]);
+        const float x[4] = {tile[ii][lq], tile[ii][lq + 1], tile[ii][lq + 2], tile[ii][lq + 3]};
+        if (vec && l + 3 < p.k) {
+            uint32_t h[2];
+            h[0] = bf16x2(x[1], x[0]);
+            h[1] = bf16x2(x[3], x[2]);
+            *reinterpret_cast<uint2*>(pl.m_hi + off) = make_uint2(h[0], h[1]);
+            if (pl.slices < 2) continue;
+            const float r[4] = {x[0] - bf_lo(h[0]), x[1] - bf_hi(h[0]), x[2] - bf_lo(h[1]),
+                                x[3] - bf_hi(h[1])};
+            uint32_t q[2];
+            q[0] = bf16x2(r[1], r[0]);
+            q[1] = bf16x2(r[3], r[2]);
+            *reinterpret_cast<uint2*>(pl.m_lo + off) = make_uint2(q[0], q[1]);
+            if (pl.slices < 3) continue;
+            q[0] = bf16x2(r[1] - bf_hi(q[0]), r[0] - bf_lo(q[0]));
+            q[1] = bf16x2(r[3] - bf_hi(q[1]), r[2] - bf_lo(q[1]));
+            *reinterpret_cast<uint2*>(pl.m_lo2 + off) = make_uint2(q[0], q[1]);
         } else {
-            for (int q = 0; q < pl.slices; ++q) m_plane(pl, q)[off] = v0[q];
+            for (int c = 0; c < 4 && l + c < p.k; ++c) {
+                __nv_bfloat16 sl[3];
+                split_slices(x[c], pl.slices, sl);
+                for (int s = 0; s < pl.slices; ++s) m_plane(pl, s)[off + c] = sl[s];
+            }
         }
     }
 }
