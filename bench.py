@@ -66,6 +66,12 @@ def captured_traffic():
     return TRAFFIC_PER_LAUNCH
 
 
+def triangle_upload_bytes(k, elem):
+    """Bytes trx_copy_triangle_h2d moves for a lower k x k triangle: one
+    rectangle of rows j0..k-1 per block of 256 columns."""
+    return sum((k - j0) * (min(k, j0 + 256) - j0) for j0 in range(0, k, 256)) * elem
+
+
 def flops_per_call(k, nrhs):
     return float(k) * k * nrhs
 
@@ -378,7 +384,8 @@ def run_gpu(args):
                          "us_per_launch": 1e3 * lf["ms"] / lf["launches"]}
 
     # End to end through the public API: pinned host buffers, every step the
-    # H2D copy of A and B, TRSM + TRMM, and the D2H copy of the result.
+    # H2D copy of A's lower triangle (trx_copy_triangle_h2d: the part the
+    # calls read) and of B, TRSM + TRMM, and the D2H copy of the result.
     # Pipelined over steps the way a stream of independent jobs would run:
     # two device slots, uploads on one copy stream, compute on the call's
     # stream, downloads on another copy stream, so step i+1's upload and step
@@ -413,11 +420,10 @@ def run_gpu(args):
 
         def e2e_step(i):
             sl = i % 2
-            # A and B go up on two streams at once (two copy engines)
+            # A's triangle and B go up on two streams
             up.wait_event(ev_down[sl])                 # slot's last result read back
             up_b.wait_event(ev_down[sl])
-            with torch.cuda.stream(up):
-                Ad[sl].copy_(A_h, non_blocking=True)
+            trx.copy_triangle_h2d("L", A_h, Ad[sl], stream=up)   # the triangle the calls read
             with torch.cuda.stream(up_b):
                 Bd[sl].copy_(B_h, non_blocking=True)
             ev_up[sl].record(up)
@@ -432,7 +438,7 @@ def run_gpu(args):
             ev_down[sl].record(down)
 
         def e2e_serial_step():
-            Ad[0].copy_(A_h, non_blocking=True)
+            trx.copy_triangle_h2d("L", A_h, Ad[0], stream=stream)
             Bd[0].copy_(B_h, non_blocking=True)
             solve_slot(0)
             out_h[0].copy_(Bd[0], non_blocking=True)
@@ -441,7 +447,8 @@ def run_gpu(args):
             e2e_step(i)
         e2e_serial_step()
         torch.cuda.synchronize()
-        nbytes = A_h.numel() * 4
+        nbytes = B_h.numel() * B_h.element_size()
+        a_bytes = triangle_upload_bytes(K_ORDER, A_h.element_size())
         e_steps = max(2, args.steps)
         barrier(world)
         t0 = time.perf_counter()
@@ -458,10 +465,10 @@ def run_gpu(args):
         dts = max_over_ranks(time.perf_counter() - t0, world)
         ok = bool(torch.equal(out_h[0], out_h[1]))    # both slots returned the same result
         e2e = {"value": job_flops_step * e_steps / dt / 1e12, "unit": "TFLOP/s",
-               "h2d_bytes_per_step": 2 * nbytes, "d2h_bytes_per_step": nbytes,
+               "h2d_bytes_per_step": a_bytes + nbytes, "d2h_bytes_per_step": nbytes,
                "ms_per_step": 1e3 * dt / e_steps, "steps": e_steps,
-               "pipelined": "upload of step i+1 (A and B on two copy streams) and download of "
-                            "step i-1 overlap step i",
+               "pipelined": "upload of step i+1 (A's lower triangle and B, two copy streams) "
+                            "and download of step i-1 overlap step i",
                "slots_agree": ok,
                "serial": {"value": job_flops_step * s_steps / dts / 1e12,
                           "ms_per_step": 1e3 * dts / s_steps, "steps": s_steps}}

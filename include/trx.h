@@ -53,6 +53,7 @@
  *                          trx_strsm_refined_async (fixed corrections)
  *   prepared factors       trx_sfactor_create / update, trx_factor_destroy,
  *                          trx_strsm_factor, trx_strmm_factor
+ *   host triangle upload   trx_copy_triangle_h2d
  *   request server         trx_server_create / register_factor /
  *                          release_factor / submit / submit_refined / poll /
  *                          pending / wait / destroy
@@ -445,6 +446,24 @@ int trx_strsm_factor(trx_handle_t handle, trx_factor_t factor, int64_t nrhs, flo
 int trx_strmm_factor(trx_handle_t handle, trx_factor_t factor, int64_t nrhs, float alpha,
                      float* B, int64_t ldb, void* stream);
 int trx_factor_destroy(trx_factor_t factor);
+
+/* Upload of the triangle the four operations read (no counterpart in the
+ * paper, whose operands are on the device: Eq. 1-4 reference one triangle of
+ * A, so a caller whose A is in host memory need not send the other one).
+ * Copies the k x k triangle uplo of the column-major host array A_host
+ * (leading dimension lda_host, elements of elem = 4 or 8 bytes), diagonal
+ * included ('L': rows j..k-1 of column j; 'U': rows 0..j), into the
+ * column-major device array A_dev (leading dimension lda_dev). It runs as one
+ * rectangular cudaMemcpy2DAsync per block of 256 columns, so inside the
+ * 256 x 256 diagonal blocks the other triangle's host values are copied too;
+ * everything else of the other triangle in A_dev is left as it was. About
+ * k^2 / 2 + 128 k elements move instead of k^2. Enqueued on stream (a
+ * cudaStream_t, NULL for the legacy stream); with pinned host memory it is
+ * asynchronous, otherwise CUDA stages it. The caller owns both arrays.
+ * Returns 0, -i for an illegal i-th argument (uplo 1, k 2, elem 3, A_host 4,
+ * lda_host 5, A_dev 6, lda_dev 7), TRX_ERR_CUDA. */
+int trx_copy_triangle_h2d(char uplo, int64_t k, int elem, const void* A_host, int64_t lda_host,
+                          void* A_dev, int64_t lda_dev, void* stream);
 
 /* Prepared batch: the same problems run many times (fixed pointers; the
  * contents of A and B may change between runs). trx_batch_create checks,

@@ -158,6 +158,7 @@ def load_library() -> ctypes.CDLL:
                                        ctypes.POINTER(ctypes.c_double),
                                        ctypes.POINTER(ctypes.c_double)]
         lib.trx_noalloc_check_error.argtypes = []
+        lib.trx_copy_triangle_h2d.argtypes = [c, i64, ctypes.c_int, vp, i64, vp, i64, vp]
         _lib = lib
         return lib
 
@@ -524,6 +525,25 @@ class Factor:
             self.close()
         except Exception:
             pass
+
+
+def copy_triangle_h2d(uplo: str, A_host, A_dev, *, stream=None):
+    """Upload the triangle `uplo` (diagonal included) of the column-major
+    k x k host tensor A_host into the column-major CUDA tensor A_dev
+    (trx_copy_triangle_h2d): about half of A's bytes. Pinned A_host makes the
+    copy asynchronous on `stream`."""
+    import torch
+    if A_host.device.type != "cpu" or A_dev.device.type != "cuda":
+        raise ValueError("copy_triangle_h2d: A_host must be a CPU tensor and A_dev a CUDA one")
+    if A_host.dtype != A_dev.dtype or A_host.dtype not in (torch.float32, torch.float64):
+        raise TypeError("copy_triangle_h2d: A_host and A_dev must both be float32 or float64")
+    if tuple(A_host.shape) != tuple(A_dev.shape) or A_host.shape[0] != A_host.shape[1]:
+        raise ValueError("copy_triangle_h2d: A_host and A_dev must be the same square shape")
+    hp, hld = _colmajor(A_host, "A_host")
+    dp, dld = _colmajor(A_dev, "A_dev")
+    _check(load_library().trx_copy_triangle_h2d(
+        uplo.encode(), A_host.shape[0], A_host.element_size(), hp, hld, dp, dld,
+        _stream_ptr(stream, A_dev.device)), "trx_copy_triangle_h2d")
 
 
 def _stream_ptr(stream, device):

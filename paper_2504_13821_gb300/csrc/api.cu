@@ -8,6 +8,7 @@
 // mapping (side 'R' solves with op(A)^T on B^T; an effectively-upper triangle
 // is index-reversed), so no variant needs its own kernels.
 #include <algorithm>
+#include <cctype>
 #include <cmath>
 #include <type_traits>
 #include <cstdio>
@@ -2241,5 +2242,35 @@ int trx_debug_plan(char op, char side, char uplo, char transa, char diag, int64_
 }
 
 int trx_version(void) { return 100; }
+
+// Upload of the triangle a call reads: one rectangular copy per block of
+// 256 columns (rows j0..k-1 of the block for 'L', 0..j1-1 for 'U'), so the
+// other triangle's bytes, all but the parts inside the 256 x 256 diagonal
+// blocks, stay on the host.
+int trx_copy_triangle_h2d(char uplo, int64_t k, int elem, const void* A_host, int64_t lda_host,
+                          void* A_dev, int64_t lda_dev, void* stream) {
+    const char u = (char)std::toupper((unsigned char)uplo);
+    if (u != 'L' && u != 'U') return -1;
+    if (k < 0) return -2;
+    if (elem != 4 && elem != 8) return -3;
+    if (k > 0 && A_host == nullptr) return -4;
+    if (lda_host < std::max<int64_t>(1, k)) return -5;
+    if (k > 0 && A_dev == nullptr) return -6;
+    if (lda_dev < std::max<int64_t>(1, k)) return -7;
+    const cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    constexpr int64_t kBlock = 256;
+    for (int64_t j0 = 0; j0 < k; j0 += kBlock) {
+        const int64_t j1 = std::min(k, j0 + kBlock);
+        const int64_t r0 = u == 'L' ? j0 : 0, r1 = u == 'L' ? k : j1;
+        const char* src = static_cast<const char*>(A_host) + (r0 + j0 * lda_host) * elem;
+        char* dst = static_cast<char*>(A_dev) + (r0 + j0 * lda_dev) * elem;
+        const cudaError_t e =
+            cudaMemcpy2DAsync(dst, (size_t)(lda_dev * elem), src, (size_t)(lda_host * elem),
+                              (size_t)((r1 - r0) * elem), (size_t)(j1 - j0),
+                              cudaMemcpyHostToDevice, s);
+        if (e != cudaSuccess) return fail_cuda(e, "triangle upload");
+    }
+    return TRX_SUCCESS;
+}
 
 }  // extern "C"

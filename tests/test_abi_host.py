@@ -193,3 +193,21 @@ def test_typed_batched_calls_check_the_operation(lib):
     assert lib.trx_strsm_batched(None, 1, probs, None) == 1
     assert lib.trx_strmm_batched(None, 1, probs, None) == 7
     assert lib.trx_dtrmm_batched(None, 0, None, None) == 1
+
+
+def test_copy_triangle_argument_positions(lib):
+    f = lib.trx_copy_triangle_h2d
+
+    def up(uplo="L", k=4, elem=4, host=1, ldh=4, dev=1, ldd=4):
+        return f(uplo.encode(), k, elem, host, ldh, dev, ldd, None)
+
+    assert up(uplo="X") == -1
+    assert up(k=-1) == -2
+    assert up(elem=2) == -3
+    assert up(host=None) == -4
+    assert up(ldh=3) == -5
+    assert up(dev=None) == -6
+    assert up(ldd=3) == -7
+    # an empty triangle copies nothing and needs no pointers
+    assert up(k=0, host=None, dev=None, ldh=1, ldd=1) == 0
+    assert up(uplo="u", k=0, host=None, dev=None, ldh=1, ldd=1) == 0
