@@ -63,6 +63,10 @@ FP64_FMA_PROBE_TFLOPS = 1.057
 
 
 def captured_traffic():
+    # the capture is of the default workload (m = n = 16384, 6-term split,
+    # automatic leaves); any other configuration reports null
+    if (K_ORDER, NRHS, SPLIT_TERMS) != (16384, 16384, 6) or LEAF_USED is not None:
+        return None
     return TRAFFIC_PER_LAUNCH
 
 
@@ -226,6 +230,26 @@ def run_reference(args):
 LEAF_USED = None
 
 
+def auto_path_desc(k, n):
+    """What the library's automatic choices (plan.cuh: use_thin_mode,
+    thin_leaf_rows, the leaf kernel by right-hand-side count) run for FP32
+    side-L TRSM and TRMM of order k with n right-hand sides."""
+    thin_leaf = 0
+    if k >= 4096 and 64 < n <= 512:
+        thin_leaf = 2048 if n <= 256 else 1024
+    if thin_leaf and k > thin_leaf:
+        trsm = f"TRSM leaves of {thin_leaf} rows as thin solves (64-row blocks, 16-column panels)"
+    elif k > 256 and (n <= 64 or (n <= 256 and k * n <= 1 << 21)):
+        trsm = "TRSM as one thin solve (64-row blocks, 16-column panels, one launch)"
+    else:
+        trsm = f"TRSM 128 ({'wide leaf' if n >= 1024 else 'lane-split leaf'})"
+    if k > 256 and n <= 32:
+        trmm = "TRMM as one thin product"
+    else:
+        trmm = "TRMM 1024-row diagonal blocks on the tensor cores" if k >= 1024 else "TRMM 64"
+    return f"{trsm}, {trmm}"
+
+
 def workload_config():
     prec = "FP32" if DTYPE == np.float32 else "FP64"
     return {"workload": f"{prec} TRSM(alpha=1.5) then TRMM(alpha=1/1.5), side L, lower, "
@@ -234,8 +258,7 @@ def workload_config():
                            if DTYPE == np.float32 else ""),
             "m": K_ORDER, "n": NRHS,
             "leaf": LEAF_USED if LEAF_USED is not None else (
-                "TRSM 128 (wide leaf), TRMM 1024-row diagonal blocks on the tensor cores"
-                if DTYPE == np.float32 else 64),
+                auto_path_desc(K_ORDER, NRHS) if DTYPE == np.float32 else 64),
             "gemm": (f"tcgen05 kind::f16, {SPLIT_TERMS}-term split BF16 "
                      f"({SPLIT_DESC[SPLIT_TERMS]}), FP32 accumulation"
                      if DTYPE == np.float32 else "CUDA-core DFMA"),

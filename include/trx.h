@@ -224,15 +224,32 @@ enum {
                               -1 = the recursion; 0 = automatic (default:
                               order above 256; TRSM with at most 64
                               right-hand sides, or at most 256 while order
-                              x right-hand sides <= 2^21; TRMM with at most
-                              32). Its scratch lives in a handle buffer
-                              grown on first use                          */
-    TRX_OPT_TEST_WITHHOLD = 18 /* test hook for the bounded waits: 1 = the
+                              x right-hand sides <= 2^21 and the thin
+                              leaves of TRX_OPT_THIN_LEAF do not apply;
+                              TRMM with at most 32). Its scratch lives in a
+                              handle buffer grown on first use (cached
+                              graphs are dropped when it grows)           */
+    TRX_OPT_TEST_WITHHOLD = 18, /* test hook for the bounded waits: 1 = the
                               thin TRSM (TRX_OPT_THIN) never publishes its
                               first block row, so the waits of the blocks
                               after it run out and the call leaves
                               TRX_ERR_TIMEOUT for trx_check_device_error
                               (B is then not the solution). 0 (default)  */
+    TRX_OPT_THIN_LEAF = 19 /* FP32 TRSM on the tensor-core path: the
+                              recursion stops at leaves of this many rows
+                              (256 .. 8192, a multiple of 128) and each
+                              leaf runs as the thin solve of TRX_OPT_THIN
+                              (one persistent CUDA-core launch) on its own
+                              rows, its result converted to the GEMM
+                              operand planes for the updates after it;
+                              -1 = off; 0 = automatic (default: from
+                              order 4096, leaves of 2048 rows for 65 .. 256
+                              right-hand sides, of 1024 rows for 257 ..
+                              512). Where this and an automatic whole-call
+                              thin solve (TRX_OPT_THIN 0) both apply, the
+                              leaves are taken; a forced one (TRX_OPT_THIN
+                              1) wins over them. Shares TRX_OPT_THIN's
+                              scratch buffer                              */
 };
 
 /* Kernel classes reported by trx_get_profile(). */

@@ -8,7 +8,7 @@ over torch tensors); the CUDA library is built in-tree by ``build.py``.
 """
 from ._binding import (  # noqa: F401
     Batch, Factor, GEMM_AUTO, GEMM_SIMT, GEMM_TC, OPT_GEMM, OPT_GRAPH, OPT_LEAF, OPT_PANELS, OPT_PDL, OPT_PROFILE,
-    OPT_CHECKED, OPT_FP64_TRMM, OPT_FP64_TRSM, OPT_NVTX, OPT_RESIDUAL, OPT_SPLIT, OPT_THIN, OPT_TRMM_DENSE, OPT_TRSM_DAG, OPT_TRSM_TC_LEAF, OPT_WAIT_LIMIT, RESIDUAL_AUTO, RESIDUAL_FLOAT_FLOAT,
+    OPT_CHECKED, OPT_FP64_TRMM, OPT_FP64_TRSM, OPT_NVTX, OPT_RESIDUAL, OPT_SPLIT, OPT_THIN, OPT_THIN_LEAF, OPT_TRMM_DENSE, OPT_TRSM_DAG, OPT_TRSM_TC_LEAF, OPT_WAIT_LIMIT, RESIDUAL_AUTO, RESIDUAL_FLOAT_FLOAT,
     RESIDUAL_FP64, RESIDUAL_TC, Handle, TrxError, batched, batched_autotune, copy_triangle_h2d,
     debug_plan,
     default_handle,

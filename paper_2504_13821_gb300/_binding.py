@@ -29,6 +29,7 @@ OPT_TRSM_DAG = 15       # FP32 TRSM: 1 device-scheduled, -1 recursive chain, 0 a
 OPT_FP64_TRMM = 16      # trx_dtrmm: 0 DFMA recursion; 1 one float-float pass (order >= 64)
 OPT_THIN = 17           # FP32 TRSM, few right-hand sides: 1 one persistent launch, -1 recursion, 0 auto
 OPT_TEST_WITHHOLD = 18  # test hook: the thin TRSM withholds its first block (waits run out)
+OPT_THIN_LEAF = 19      # FP32 TRSM, tensor-core path: leaves of this many rows as thin solves (-1 off, 0 auto)
 RESIDUAL_AUTO, RESIDUAL_FP64, RESIDUAL_FLOAT_FLOAT, RESIDUAL_TC = 0, 1, 2, 3
 GEMM_AUTO, GEMM_SIMT, GEMM_TC = 0, 1, 2
 KERNEL_CLASSES = ("leaf_trsm", "leaf_trmm", "gemm_tc", "gemm_simt", "convert", "other")

@@ -234,6 +234,7 @@ struct trx_handle_s {
     size_t rf_bytes = 0;
     // thin-right-hand-side TRSM: task counter and block flags (grown on demand)
     int64_t opt_thin = 0;
+    int64_t opt_thin_leaf = 0;       // TRSM leaves as thin solves (TRX_OPT_THIN_LEAF)
     int64_t opt_test_withhold = 0;   // test hook (TRX_OPT_TEST_WITHHOLD)
     int* thin_buf = nullptr;
     size_t thin_bytes = 0;
@@ -396,19 +397,30 @@ struct Exec {
                     cls = TRX_KERNEL_CONVERT;
                     bytes = 4.0 * c.k * st.b * 1.5;
                     break;
-                case kThin:
+                case kThin: {
+                    // b == 0: the whole problem; else the leaf on rows
+                    // [r0, r0 + b): the same canonical problem restricted
+                    // to those rows and columns of M and rows of C
+                    Canon<float> tc = *reinterpret_cast<const Canon<float>*>(&c);
+                    if (st.b > 0) {
+                        tc.A += st.r0 * (tc.a_rs + tc.a_cs);
+                        tc.C += st.r0 * tc.c_rs;
+                        tc.k = st.b;
+                    }
                     if (st.trsm)
-                        e = launch_thin_trsm(*reinterpret_cast<const Canon<float>*>(&c),
-                                             (float)st.alpha, thin_scratch, h->d_err,
+                        e = launch_thin_trsm(tc, (float)st.alpha, thin_scratch, h->d_err,
                                              h->wait_ns, h->num_sms, s,
                                              h->opt_test_withhold != 0);
                     else
-                        e = launch_thin_trmm(*reinterpret_cast<const Canon<float>*>(&c),
-                                             (float)st.alpha, thin_scratch, h->num_sms, s);
+                        e = launch_thin_trmm(tc, (float)st.alpha, thin_scratch, h->num_sms, s);
+                    if (e == cudaSuccess && st.b > 0 && st.planes && st.r0 + st.b < c.k)
+                        e = launch_convert_y_rows(*reinterpret_cast<const Canon<float>*>(&c), pl,
+                                                  st.r0, st.b, s);
                     cls = st.trsm ? TRX_KERNEL_LEAF_TRSM : TRX_KERNEL_LEAF_TRMM;
-                    flops = (double)c.k * c.k * c.nrhs;
-                    bytes = 4.0 * ((double)c.k * (c.k + 1) / 2 + 2.0 * c.k * c.nrhs);
+                    flops = (double)tc.k * tc.k * tc.nrhs;
+                    bytes = 4.0 * ((double)tc.k * (tc.k + 1) / 2 + 2.0 * tc.k * tc.nrhs);
                     break;
+                }
                 case kDag: {
                     __nv_bfloat16* const w3[3] = {w_hi, w_lo, w_lo2};
                     e = launch_trsm_dag(*reinterpret_cast<const Canon<float>*>(&c), pl, w3,
@@ -467,6 +479,7 @@ struct trx_factor_s {
 };
 
 namespace {
+void drop_graphs(trx_handle_t h);   // defined below
 
 constexpr int kFactorMagic = 0x54524631;   // "TRF1"
 // Diagonal blocks zeroed above the diagonal in a factor's planes: every
@@ -517,24 +530,43 @@ int execute(trx_handle_t h, bool trsm, char side, char uplo, char transa, char d
     ex.s = s;
     ex.profile = h->opt_profile != 0;
     const int64_t k = ex.c.k;
-    const int b = leaf_for(h->opt_leaf, k, trsm, (int)sizeof(T), ex.c.nrhs);
+    int b = leaf_for(h->opt_leaf, k, trsm, (int)sizeof(T), ex.c.nrhs);
 
     // Thin right-hand sides: one persistent CUDA-core launch (thin.cu), no
-    // planes; its task counter and flags live in a handle buffer, grown here
-    // (never inside a stream capture: a capture keeps the recursive chain).
+    // planes, for the whole call; or, on the tensor-core path, the same
+    // solve for each leaf of thin_leaf rows. Its task counter and flags live
+    // in a handle buffer, grown here (never inside a stream capture: a
+    // capture keeps the recursive chain with the ordinary leaves).
+    const bool tc_ok = use_tc<T>(h, k, trsm, ex.c.nrhs);
     bool thin = std::is_same<T, float>::value &&
                 use_thin_mode(h->opt_thin, trsm, (int)sizeof(T), k, ex.c.nrhs);
-    const size_t thin_need = !thin ? 0
-                             : trsm ? thin_scratch_bytes(k, ex.c.nrhs)
-                                    : thin_trmm_scratch_bytes(k, ex.c.nrhs);
-    if (thin && h->thin_bytes < thin_need) {
+    int thin_leaf = std::is_same<T, float>::value
+                        ? thin_leaf_rows(h->opt_thin_leaf, tc_ok, trsm, (int)sizeof(T), k,
+                                         ex.c.nrhs)
+                        : 0;
+    // both apply: a forced whole-call solve wins, else the thin leaves
+    if (thin && thin_leaf > 0) {
+        if (h->opt_thin > 0) thin_leaf = 0;
+        else thin = false;
+    }
+    Plan plan;
+    plan.tc = !thin && tc_ok;
+    const size_t thin_need = thin ? (trsm ? thin_scratch_bytes(k, ex.c.nrhs)
+                                          : thin_trmm_scratch_bytes(k, ex.c.nrhs))
+                             : thin_leaf > 0 ? thin_scratch_bytes(thin_leaf, ex.c.nrhs)
+                                             : 0;
+    if (thin_need > 0 && h->thin_bytes < thin_need) {
         cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
         e = cudaStreamIsCapturing(s, &cs);
         if (e != cudaSuccess) return fail_cuda(e, "cudaStreamIsCapturing");
         if (cs != cudaStreamCaptureStatusNone) {
             thin = false;
+            thin_leaf = 0;
+            plan.tc = tc_ok;
         } else {
             const size_t want = std::max<size_t>(2 * thin_need, 1 << 16);
+            // cached graphs hold the old buffer's address: dropped with it
+            drop_graphs(h);
             if (h->thin_buf) cudaFree(h->thin_buf);        // waits for its last use
             h->thin_buf = nullptr;
             h->thin_bytes = 0;
@@ -545,10 +577,9 @@ int execute(trx_handle_t h, bool trsm, char side, char uplo, char transa, char d
             h->thin_bytes = want;
         }
     }
-    ex.thin_scratch = thin ? h->thin_buf : nullptr;
-
-    Plan plan;
-    plan.tc = !thin && use_tc<T>(h, k, trsm, ex.c.nrhs);
+    ex.thin_scratch = (thin || thin_leaf > 0) ? h->thin_buf : nullptr;
+    if (thin_leaf > 0) b = thin_leaf;
+    plan.thin_leaf = thin_leaf > 0;
     // A prepared factor supplies the M planes (and its split): the workspace
     // holds Y only.
     const bool factor_planes = plan.tc && f != nullptr && f->m_hi != nullptr;
@@ -592,7 +623,7 @@ int execute(trx_handle_t h, bool trsm, char side, char uplo, char transa, char d
     // the M planes' own diagonal blocks (no TRSM update reads inside a leaf
     // block) or, for a prepared factor, in the factor's W planes made for
     // this leaf size (its M planes serve TRMM's diagonal blocks too).
-    plan.tc_leaf = std::is_same<T, float>::value && trsm && !dag &&
+    plan.tc_leaf = std::is_same<T, float>::value && trsm && !dag && !plan.thin_leaf &&
                    tc_leaf_mode(h->opt_trsm_tc_leaf, plan.tc, b) &&
                    (!factor_planes || (f->w_hi != nullptr && f->w_block == b));
     if (plan.tc_leaf) {
@@ -604,7 +635,7 @@ int execute(trx_handle_t h, bool trsm, char side, char uplo, char transa, char d
     // as P column-panel branches (forked streams, one graph), so the
     // latency-bound bottom of the recursion of one panel overlaps the others'.
     int P = 1;
-    if (trsm && !dag && !thin) {
+    if (trsm && !dag && !thin && !plan.thin_leaf) {
         if (h->opt_panels > 0) P = (int)h->opt_panels;
         const int64_t step = round_up((ex.c.nrhs + P - 1) / P, 256);
         P = (int)std::max<int64_t>(1, (ex.c.nrhs + step - 1) / step);
@@ -643,6 +674,7 @@ int execute(trx_handle_t h, bool trsm, char side, char uplo, char transa, char d
     Plan pre, body;
     pre.tc = body.tc = plan.tc;
     body.tc_leaf = plan.tc_leaf;
+    body.thin_leaf = plan.thin_leaf;
     if (plan.tc && !factor_planes) {
         Step cm{kConvM};
         cm.b = dense;
@@ -713,7 +745,8 @@ int execute(trx_handle_t h, bool trsm, char side, char uplo, char transa, char d
     key.b = b;
     key.slices = plan.tc ? slices : 0;
     key.dag = dag;
-    key.thin = thin ? 1 + (int)h->opt_test_withhold : 0;
+    key.thin = thin ? 1 + (int)h->opt_test_withhold
+               : plan.thin_leaf ? 3 + (int)h->opt_test_withhold : 0;
     key.k = k;
     key.nrhs = ex.c.nrhs;
     key.a_rs = ex.c.a_rs;
@@ -819,6 +852,7 @@ int noalloc_strsm(int device, int num_sms, void* scratch, size_t scratch_bytes, 
     hs.opt_panels = 1;   // no handle streams here: one chain on the caller's stream
     hs.opt_trsm_dag = -1;   // the recursive chain only: its scratch is the planes
     hs.opt_thin = -1;       // (the thin solve's flags would need an allocation)
+    hs.opt_thin_leaf = -1;
     return execute<float>(&hs, true, side, uplo, transa, diag, m, n, alpha, A, lda, B, ldb,
                           stream);
 }
@@ -2078,6 +2112,11 @@ int trx_set_option(trx_handle_t h, int option, int64_t value) {
             if (value != 0 && value != 1) return TRX_ERR_INVALID_VALUE;
             h->opt_test_withhold = value;
             break;
+        case TRX_OPT_THIN_LEAF:
+            if (!(value == -1 || value == 0 || (value >= 256 && value <= 8192 && value % 128 == 0)))
+                return TRX_ERR_INVALID_VALUE;
+            h->opt_thin_leaf = value;
+            break;
         default:
             return TRX_ERR_INVALID_VALUE;
     }
@@ -2106,6 +2145,7 @@ int trx_get_option(trx_handle_t h, int option, int64_t* value) {
         case TRX_OPT_FP64_TRMM: *value = h->opt_fp64_trmm; break;
         case TRX_OPT_THIN: *value = h->opt_thin; break;
         case TRX_OPT_TEST_WITHHOLD: *value = h->opt_test_withhold; break;
+        case TRX_OPT_THIN_LEAF: *value = h->opt_thin_leaf; break;
         default: return TRX_ERR_INVALID_VALUE;
     }
     return TRX_SUCCESS;

@@ -62,9 +62,22 @@ struct Plan {
     std::vector<Step> steps;
     bool tc = false;
     bool tc_leaf = false;    // TRSM leaves of the full size b as inverse GEMMs
+    bool thin_leaf = false;  // TRSM leaves as thin solves on their rows (kThin, b > 0)
 };
 
 inline void plan_trsm(Plan& pl, int64_t r0, int64_t s, bool first, int b, double alpha) {
+    if (s <= b && pl.thin_leaf) {
+        // the leaf as the thin solve on rows [r0, r0 + s); its result goes
+        // to the Y planes for the updates after it
+        Step st{kThin};
+        st.trsm = true;
+        st.r0 = r0;
+        st.b = (int)s;
+        st.alpha = first ? alpha : 1.0;
+        st.planes = pl.tc;
+        pl.steps.push_back(st);
+        return;
+    }
     if (s <= b) {
         Step st{kLeaf};
         st.trsm = true;
@@ -258,6 +271,11 @@ inline const char* validate_plan(const Plan& plan, int64_t k) {
             case kConvYRows:
                 if (st.r0 < 0 || st.b < 1 || st.r0 + st.b > k) return "plane rows outside [0, k)";
                 break;
+            case kThin:
+                // b == 0: the whole problem; else a leaf on rows [r0, r0 + b)
+                if (st.b < 0 || st.r0 < 0 || (st.b > 0 && st.r0 + st.b > k))
+                    return "thin leaf outside the triangle";
+                break;
             case kGemm:
                 if (st.y0 < 0 || st.y1 < st.y0 || st.y1 > k) return "plane window outside [0, k)";
                 for (const TcGemm& g : st.gemms) {
@@ -344,7 +362,8 @@ inline bool use_dag_mode(int64_t opt, bool tc, bool trsm, int elem, int64_t k, i
 // while order x right-hand sides stays within kThinMaxWork, where the
 // chain's launch and leaf latency bound the recursive path (measured on
 // GB300: 1.04-4.2x faster there; at order 16384 with 256 right-hand sides
-// the chain's tensor-core updates win).
+// the chain's tensor-core updates win). Where the thin leaves below also
+// apply automatically, the call takes those instead (execute in api.cu).
 constexpr int64_t kThinMaxNrhs = 64, kThinWideNrhs = 256;
 constexpr int64_t kThinMaxWork = (int64_t)1 << 21;
 constexpr int64_t kThinMinK = 256;
@@ -359,6 +378,23 @@ inline bool use_thin_mode(int64_t opt, bool trsm, int elem, int64_t k, int64_t n
     if (!trsm) return k > kThinMinK && nrhs <= kThinTrmmMaxNrhs;
     return k > kThinMinK &&
            (nrhs <= kThinMaxNrhs || (nrhs <= kThinWideNrhs && k * nrhs <= kThinMaxWork));
+}
+
+// Leaves of the recursion as thin solves (TRX_OPT_THIN_LEAF: -1 off, a row
+// count 256 .. 8192 (multiple of 128) on, 0 automatic): FP32 TRSM on the
+// tensor-core path whose order exceeds the leaf. Automatically from order
+// kThinLeafMinK: leaves of 2048 rows for 65 .. 256 right-hand sides, of
+// 1024 rows for 257 .. 512 (measured on GB300 against the chain of 128-row
+// leaves and the whole-call thin solve: 1.45x the chain at order 16384 with
+// 256 right-hand sides, 1.64x the whole-call thin solve with 128, 1.1-1.2x
+// the chain at 512; from 1024 on the chain is faster). Returns the leaf
+// rows, or 0.
+constexpr int64_t kThinLeafMinK = 4096;
+inline int thin_leaf_rows(int64_t opt, bool tc, bool trsm, int elem, int64_t k, int64_t nrhs) {
+    if (opt < 0 || !tc || !trsm || elem != 4) return 0;
+    if (opt > 0) return k > opt ? (int)opt : 0;
+    if (k < kThinLeafMinK || nrhs <= kThinMaxNrhs || nrhs > 512) return 0;
+    return nrhs <= kThinWideNrhs ? 2048 : 1024;
 }
 
 inline bool use_tc_mode(int elem, int64_t gemm_mode, int64_t k, int b) {

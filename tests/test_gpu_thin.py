@@ -18,7 +18,11 @@ recursive chain.
 - TRMM: all 16 variants at the same shapes (normwise error within 8 k u),
   order 40 and 1024 x 200 forced on, order 8192 with 16 right-hand sides
   against the oracle (sampled), bitwise repeatable, within the FP32 bound
-  of the recursive product.
+  of the recursive product;
+- thin solves as the recursion's leaves (TRX_OPT_THIN_LEAF) under
+  tensor-core updates: all 16 variants at ragged orders (256-row leaves),
+  order 8192 x 256 with 2048-row leaves sampled against the oracle,
+  bitwise repeatable, within the FP32 bound of the ordinary recursion.
 """
 import numpy as np
 import pytest
@@ -162,3 +166,73 @@ def test_thin_trmm_forced_and_large(trx):
     assert err <= bound(k, np.float32), err
     h.close()
     hc.close()
+
+
+# ---- thin solves as the recursion's leaves (TRX_OPT_THIN_LEAF) -------------
+
+def thin_leaf_handle(trx, rows):
+    h = trx.Handle(0)
+    h.set_option(trx.OPT_THIN, -1)
+    h.set_option(trx.OPT_THIN_LEAF, rows)
+    assert h.get_option(trx.OPT_THIN_LEAF) == rows
+    return h
+
+
+def test_thin_leaf_option_values(trx):
+    h = trx.Handle(0)
+    for bad in (-2, 1, 255, 300, 8320):
+        with pytest.raises(trx.TrxError):
+            h.set_option(trx.OPT_THIN_LEAF, bad)
+    for ok in (-1, 0, 256, 2048, 8192):
+        h.set_option(trx.OPT_THIN_LEAF, ok)
+    h.close()
+
+
+@pytest.mark.parametrize("side,uplo,trans,diag", VARIANTS)
+def test_thin_leaves_all_variants(trx, side, uplo, trans, diag):
+    """Leaves of 256 rows as thin solves under tensor-core updates: ragged
+    orders (the last leaf shorter), padded storage, both alphas."""
+    h = thin_leaf_handle(trx, 256)
+    vi = VARIANTS.index((side, uplo, trans, diag))
+    for k, nrhs, alpha, pads in ((1100, 40, 1.5, (0, 0)), (700, 130, -2.0, (3, 5))):
+        m, n = (k, nrhs) if side == "L" else (nrhs, k)
+        run_case("trsm", side, uplo, trans, diag, m, n, alpha, np.float32,
+                 seed=inputs.variant_seed(k + nrhs + 7, vi), handle=h, lda_pad=pads[0],
+                 ldb_pad=pads[1])
+    assert h.check_device_error() == 0
+    h.close()
+
+
+def test_thin_leaves_large_sampled_repeatable(trx):
+    """Order 8192, 256 right-hand sides, leaves of 2048 rows: sampled columns
+    against the oracle, bitwise repeatable (graph replay included), within
+    the FP32 bound of the ordinary recursion."""
+    k, n = 8192, 256
+    A, B = inputs.problem("L", "L", k, n, seed=8193, dtype=np.float32)
+    At = to_dev(A, "cuda:0")
+    h = thin_leaf_handle(trx, 2048)
+    outs = []
+    for _ in range(3):
+        Bt = to_dev(B, "cuda:0")
+        trx.trsm("L", "L", "N", "N", 1.5, At, Bt, handle=h)
+        torch.cuda.synchronize()
+        outs.append(Bt.cpu().numpy())
+    assert h.check_device_error() == 0
+    assert np.array_equal(outs[0], outs[1]) and np.array_equal(outs[1], outs[2])
+    X = np.asfortranarray(outs[0])
+    cols = [0, 1, 100, 255]
+    eta = oracle.trsm_backward_error("L", "L", "N", "N", 1.5, A.astype(np.float64),
+                                     X[:, cols].astype(np.float64),
+                                     np.asfortranarray(B[:, cols]).astype(np.float64))["eta"]
+    assert eta <= bound(k, np.float32)
+    h.close()
+    hc = trx.Handle(0)
+    hc.set_option(trx.OPT_THIN, -1)
+    hc.set_option(trx.OPT_THIN_LEAF, -1)
+    Bt = to_dev(B, "cuda:0")
+    trx.trsm("L", "L", "N", "N", 1.5, At, Bt, handle=hc)
+    torch.cuda.synchronize()
+    Xc = Bt.cpu().numpy().astype(np.float64)
+    hc.close()
+    ninf = lambda a: np.abs(a).sum(axis=1).max()          # noqa: E731
+    assert ninf(X.astype(np.float64) - Xc) <= bound(k, np.float32) * ninf(Xc)
