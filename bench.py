@@ -235,7 +235,7 @@ def auto_path_desc(k, n):
     thin_leaf_rows, the leaf kernel by right-hand-side count) run for FP32
     side-L TRSM and TRMM of order k with n right-hand sides."""
     thin_leaf = 0
-    if k >= 4096 and 64 < n <= 512:
+    if k >= 4096 and 64 < n <= 1024 and not (n <= 128 and k < 8192):
         thin_leaf = 2048 if n <= 256 else 1024
     if thin_leaf and k > thin_leaf:
         trsm = f"TRSM leaves of {thin_leaf} rows as thin solves (64-row blocks, 16-column panels)"

@@ -244,8 +244,9 @@ enum {
                               operand planes for the updates after it;
                               -1 = off; 0 = automatic (default: from
                               order 4096, leaves of 2048 rows for 65 .. 256
-                              right-hand sides, of 1024 rows for 257 ..
-                              512). Where this and an automatic whole-call
+                              right-hand sides (129 .. 256 below order
+                              8192), of 1024 rows for 257 .. 1024). Where
+                              this and an automatic whole-call
                               thin solve (TRX_OPT_THIN 0) both apply, the
                               leaves are taken; a forced one (TRX_OPT_THIN
                               1) wins over them. Shares TRX_OPT_THIN's

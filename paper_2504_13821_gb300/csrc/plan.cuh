@@ -383,17 +383,19 @@ inline bool use_thin_mode(int64_t opt, bool trsm, int elem, int64_t k, int64_t n
 // Leaves of the recursion as thin solves (TRX_OPT_THIN_LEAF: -1 off, a row
 // count 256 .. 8192 (multiple of 128) on, 0 automatic): FP32 TRSM on the
 // tensor-core path whose order exceeds the leaf. Automatically from order
-// kThinLeafMinK: leaves of 2048 rows for 65 .. 256 right-hand sides, of
-// 1024 rows for 257 .. 512 (measured on GB300 against the chain of 128-row
-// leaves and the whole-call thin solve: 1.45x the chain at order 16384 with
-// 256 right-hand sides, 1.64x the whole-call thin solve with 128, 1.1-1.2x
-// the chain at 512; from 1024 on the chain is faster). Returns the leaf
-// rows, or 0.
+// kThinLeafMinK: leaves of 2048 rows for 65 .. 256 right-hand sides (from
+// order 8192 when there are at most 128: below it the whole-call thin solve
+// is faster), of 1024 rows for 257 .. 1024 (measured on GB300 against the
+// chain of 128-row leaves and the whole-call thin solve: 1.57x the chain at
+// order 16384 with 256 right-hand sides, 1.56x the whole-call thin solve
+// with 128, 1.13-1.3x the chain at 512 and 1024). Returns the leaf rows, or
+// 0.
 constexpr int64_t kThinLeafMinK = 4096;
 inline int thin_leaf_rows(int64_t opt, bool tc, bool trsm, int elem, int64_t k, int64_t nrhs) {
     if (opt < 0 || !tc || !trsm || elem != 4) return 0;
     if (opt > 0) return k > opt ? (int)opt : 0;
-    if (k < kThinLeafMinK || nrhs <= kThinMaxNrhs || nrhs > 512) return 0;
+    if (k < kThinLeafMinK || nrhs <= kThinMaxNrhs || nrhs > 1024) return 0;
+    if (nrhs <= 128 && k < 2 * kThinLeafMinK) return 0;
     return nrhs <= kThinWideNrhs ? 2048 : 1024;
 }
 

@@ -69,6 +69,10 @@ struct Params {
     int* err;
     long long wait_ns;
     int withhold;    // test hook: block row 0 is never published (waits run out)
+    // inv(M_ii) and Z_i for every block row, made once by thin_prep_kernel
+    // when the launch has several panels (block row i at [2 i, 2 i + 2)
+    // tiles of BR x LD floats: inv, then Z); nullptr: each task makes its own
+    const float* invz;
 };
 
 // Ring stages: STAGES - 1 tiles in flight (cp.async); four stages measured
@@ -169,6 +173,10 @@ __device__ __forceinline__ void cp_async4(float* dst, const float* src, bool val
                  : "memory");
 }
 __device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async16(float* dst, const float* src) {
+    const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src) : "memory");
+}
 // all but the newest STAGES - 2 groups complete: the oldest tile in flight has landed
 __device__ __forceinline__ void cp_wait_ring() {
     asm volatile("cp.async.wait_group %0;" ::"n"(STAGES - 2) : "memory");
@@ -319,6 +327,23 @@ __device__ void make_z(const Params& p, Smem& sm, int64_t i0, bool colmajor) {
     __syncthreads();
 }
 
+// inv(M_ii) and Z_i = inv(M_ii) M_i,i-1 of block row blockIdx.x into
+// p.invz, by the same code (so the same values) as a task of the solve
+// makes them; with several panels every task of a block row would repeat it.
+__global__ void __launch_bounds__(NT) thin_prep_kernel(const Params p, float* invz) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Smem& sm = *reinterpret_cast<Smem*>(smem_raw);
+    const int i = blockIdx.x;
+    const int64_t i0 = (int64_t)i * BR;
+    invert_diag(p, sm, i0);
+    if (i > 0) make_z(p, sm, i0, p.a_rs == 1 || p.a_rs == -1);
+    float4* dst = reinterpret_cast<float4*>(invz + (size_t)i * 2 * BR * LD);
+    for (int e = threadIdx.x; e < BR * LD / 4; e += NT) {
+        dst[e] = reinterpret_cast<const float4*>(sm.inv)[e];
+        if (i > 0) dst[BR * LD / 4 + e] = reinterpret_cast<const float4*>(sm.z)[e];
+    }
+}
+
 __global__ void __launch_bounds__(NT, 2) thin_trsm_kernel(const Params p) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Smem& sm = *reinterpret_cast<Smem*>(smem_raw);
@@ -346,13 +371,25 @@ __global__ void __launch_bounds__(NT, 2) thin_trsm_kernel(const Params p) {
         float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
         unsigned long long w[Q];
         const int jz = i - 1;
+        if (p.invz) {
+            // inv(M_ii) and Z_i made by thin_prep_kernel: the oldest copy
+            // group, complete by the ring's first wait or the wait below
+            const float* src = p.invz + (size_t)i * 2 * BR * LD;
+            for (int e = t; e < BR * LD / 4; e += NT) {
+                cp_async16(sm.inv + 4 * e, src + 4 * e);
+                if (i > 0) cp_async16(sm.z + 4 * e, src + BR * LD + 4 * e);
+            }
+            cp_commit();
+        }
 #pragma unroll
         for (int q = 0; q < STAGES - 1; ++q) {      // tiles 0 .. STAGES - 2
             if (q < jz) issue_m(p, sm.m[(q + 1) % STAGES], i0, (int64_t)q * BR, colmajor);
             else cp_commit();
         }
-        invert_diag(p, sm, i0);
-        if (i > 0) make_z(p, sm, i0, colmajor);
+        if (!p.invz) {
+            invert_diag(p, sm, i0);
+            if (i > 0) make_z(p, sm, i0, colmajor);
+        }
         if (jz > 0) issue_x(p, pn, 0, w);
         for (int j = 0; j < jz; ++j) {
             cp_wait_ring();                               // this thread's copies of tile j
@@ -372,6 +409,7 @@ __global__ void __launch_bounds__(NT, 2) thin_trsm_kernel(const Params p) {
         // P = inv(M_ii) (alpha B - S'), then X = P - Z X_i-1,p
 #pragma unroll
         for (int e = 0; e < 4; ++e) sm.x[(4 * ty + e) * NP + tx] = fmaf(p.alpha, b[e], -acc[e]);
+        if (p.invz) asm volatile("cp.async.wait_group 0;" ::: "memory");
         __syncthreads();
         float xo[4] = {0.0f, 0.0f, 0.0f, 0.0f};
         mma_tile(sm.inv, sm.x, 8 * ((t >> 5) + 1), xo);   // inv is lower: kk <= row
@@ -428,11 +466,6 @@ __global__ void __launch_bounds__(256) thin_pack_kernel(const Params p, float* B
     const int64_t tile = e / (BR * NP), j = tile % p.nbr, pn = tile / p.nbr;
     const int64_t gi = j * BR + kk, gj = pn * NP + c;
     Bp[e] = (gi < p.k && gj < p.nrhs) ? p.C[gi * p.c_rs + gj * p.c_cs] : 0.0f;
-}
-
-__device__ __forceinline__ void cp_async16(float* dst, const float* src) {
-    const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src) : "memory");
 }
 
 // M_ij and B_jp into ring stage s (one commit group).
@@ -567,10 +600,17 @@ __global__ void __launch_bounds__(NT, 2) thin_trmm_kernel(const Params p, const 
 
 }  // namespace thin
 
+// The thin TRSM's scratch: ticket and stop word (16 bytes), the tagged
+// words of every (block, panel), and with several panels the block rows'
+// inv / Z tiles.
+static size_t thin_words_bytes(int64_t nbr, int64_t npan) {
+    return 16 + (size_t)(nbr * npan) * kThinBlock * kThinPanel * 8;
+}
 size_t thin_scratch_bytes(int64_t k, int64_t nrhs) {
     const int64_t nbr = (k + kThinBlock - 1) / kThinBlock;
     const int64_t npan = (nrhs + kThinPanel - 1) / kThinPanel;
-    return 16 + (size_t)(nbr * npan) * kThinBlock * kThinPanel * 8;
+    return thin_words_bytes(nbr, npan) +
+           (npan > 1 ? (size_t)nbr * 2 * thin::BR * thin::LD * sizeof(float) : 0);
 }
 
 static int g_thin_ctas_per_sm = 0, g_thin_trmm_ctas_per_sm = 0;
@@ -588,6 +628,9 @@ cudaError_t thin_configure() {
     cudaError_t e = cudaFuncSetAttribute(thin::thin_trsm_kernel,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)sizeof(thin::Smem));
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(thin::thin_prep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)sizeof(thin::Smem));
     if (e != cudaSuccess) return e;
     int n = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, thin::thin_trsm_kernel, thin::NT,
@@ -623,8 +666,17 @@ cudaError_t launch_thin_trsm(const Canon<float>& c, float alpha, int* scratch, i
     p.err = err;
     p.wait_ns = wait_ns;
     p.withhold = withhold ? 1 : 0;
-    cudaError_t e = cudaMemsetAsync(scratch, 0, thin_scratch_bytes(c.k, c.nrhs), s);
+    p.invz = nullptr;
+    // the words (and ticket) are zeroed every launch; inv / Z are written
+    cudaError_t e = cudaMemsetAsync(scratch, 0, thin_words_bytes(nbr, npan), s);
     if (e != cudaSuccess) return e;
+    if (npan > 1) {
+        float* invz = reinterpret_cast<float*>(reinterpret_cast<char*>(scratch) +
+                                               thin_words_bytes(nbr, npan));
+        thin::thin_prep_kernel<<<(unsigned)nbr, thin::NT, sizeof(thin::Smem), s>>>(p, invz);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        p.invz = invz;
+    }
     const int per_sm = g_thin_ctas_per_sm > 0 ? g_thin_ctas_per_sm : 1;
     const int64_t cap = (int64_t)num_sms * per_sm;
     const int grid = (int)(p.ntask < cap ? p.ntask : cap);

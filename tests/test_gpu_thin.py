@@ -236,3 +236,22 @@ def test_thin_leaves_large_sampled_repeatable(trx):
     hc.close()
     ninf = lambda a: np.abs(a).sum(axis=1).max()          # noqa: E731
     assert ninf(X.astype(np.float64) - Xc) <= bound(k, np.float32) * ninf(Xc)
+
+
+def test_thin_precomputed_inverses_bitwise_equal(trx):
+    """With several panels the diagonal blocks' inverses and Z are made once
+    per block row by a separate pass (thin_prep_kernel); with one panel the
+    task makes them. Same code, same values: the first 16 columns of a
+    32-column solve equal a 16-column solve of those columns bitwise."""
+    k = 1000
+    A, B = inputs.problem("L", "L", k, 32, seed=1000, dtype=np.float32)
+    At = to_dev(A, "cuda:0")
+    h = thin_handle(trx)
+    B32 = to_dev(B, "cuda:0")
+    B16 = to_dev(np.asfortranarray(B[:, :16]), "cuda:0")
+    trx.trsm("L", "L", "N", "N", 1.5, At, B32, handle=h)
+    trx.trsm("L", "L", "N", "N", 1.5, At, B16, handle=h)
+    torch.cuda.synchronize()
+    assert h.check_device_error() == 0
+    assert torch.equal(B32[:, :16], B16)
+    h.close()
