@@ -53,9 +53,9 @@ REF_SAMPLE_COLS = 16      # per step of --impl reference
 # 6-term split): dram__bytes_read.sum + dram__bytes_write.sum summed over the
 # 132 GEMM launches of one step and divided by 132. The two counters take one
 # ncu pass (checked on a small case first), so the capture is the full-size
-# launch list with two metrics; command and figures in
-# profiles/gemm_tc_traffic_step_n16384.md. To be set back to None (null in
-# the line) whenever gemm_tc.cu or the plan changes, until captured again.
+# launch list with two metrics (its command and figures are kept with the
+# ncu summaries). To be set back to None (null in the line) whenever
+# gemm_tc.cu or this workload's plan changes, until captured again.
 TRAFFIC_PER_LAUNCH = 316.27e6
 # FP64 FMA rate measured by this build's own probe (bench.py --workload
 # peaks; MEASURED_PEAKS.json holds no FP64 figure): the FP64 roofline
