@@ -242,7 +242,8 @@ def test_thin_precomputed_inverses_bitwise_equal(trx):
     """With several panels the diagonal blocks' inverses and Z are made once
     per block row by a separate pass (thin_prep_kernel); with one panel the
     task makes them. Same code, same values: the first 16 columns of a
-    32-column solve equal a 16-column solve of those columns bitwise."""
+    32-column solve equal a 16-column solve of those columns bitwise, and
+    the last 8 of a 40-column solve (three panels) an 8-column one."""
     k = 1000
     A, B = inputs.problem("L", "L", k, 32, seed=1000, dtype=np.float32)
     At = to_dev(A, "cuda:0")
@@ -251,7 +252,15 @@ def test_thin_precomputed_inverses_bitwise_equal(trx):
     B16 = to_dev(np.asfortranarray(B[:, :16]), "cuda:0")
     trx.trsm("L", "L", "N", "N", 1.5, At, B32, handle=h)
     trx.trsm("L", "L", "N", "N", 1.5, At, B16, handle=h)
+    # 40 columns: tasks over panel pairs, the last pair with one panel only
+    A40, B40h = inputs.problem("L", "L", k, 40, seed=1001, dtype=np.float32)
+    B40 = to_dev(B40h, "cuda:0")
+    B8 = to_dev(np.asfortranarray(B40h[:, 32:]), "cuda:0")
+    A40t = to_dev(A40, "cuda:0")
+    trx.trsm("L", "L", "N", "N", -2.0, A40t, B40, handle=h)
+    trx.trsm("L", "L", "N", "N", -2.0, A40t, B8, handle=h)
     torch.cuda.synchronize()
     assert h.check_device_error() == 0
     assert torch.equal(B32[:, :16], B16)
+    assert torch.equal(B40[:, 32:], B8)
     h.close()
