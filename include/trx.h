@@ -245,7 +245,8 @@ enum {
                               -1 = off; 0 = automatic (default: from
                               order 4096, leaves of 2048 rows for 65 .. 256
                               right-hand sides (129 .. 256 below order
-                              8192), of 1024 rows for 257 .. 1024). Where
+                              8192), of 1024 rows for 257 .. 1024; off
+                              when TRX_OPT_LEAF sets the cutoff). Where
                               this and an automatic whole-call
                               thin solve (TRX_OPT_THIN 0) both apply, the
                               leaves are taken; a forced one (TRX_OPT_THIN
@@ -631,16 +632,16 @@ const char* trx_last_error_detail(void);
 
 /* Diagnostic, host only (no device work, no handle): write into buf the
  * launch sequence a call would enqueue for the given problem, one step per
- * line ("conv_m", "conv_y", "leaf ...", "gemm ..." with their row ranges in
- * the canonical lower-triangular order), for alpha = 2. elem_bytes 4 or 8,
- * leaf as TRX_OPT_LEAF, gemm_mode as TRX_OPT_GEMM, trmm_dense as
- * TRX_OPT_TRMM_DENSE, trsm_tc_leaf as TRX_OPT_TRSM_TC_LEAF, op 'S' (TRSM)
- * or 'M' (TRMM). Returns an argument code,
- * TRX_ERR_INVALID_VALUE if buf is too small, or 0. */
-int trx_debug_plan(char op, char side, char uplo, char transa, char diag,
-                   int64_t m, int64_t n, int elem_bytes, int leaf,
-                   int gemm_mode, int trmm_dense, int trsm_tc_leaf, char* buf,
-                   size_t buflen);
+ * line ("conv_m", "conv_y", "leaf ...", "thin ...", "gemm ..." with their row
+ * ranges in the canonical lower-triangular order), for alpha = 2. elem_bytes
+ * 4 or 8, leaf as TRX_OPT_LEAF, gemm_mode as TRX_OPT_GEMM, trmm_dense as
+ * TRX_OPT_TRMM_DENSE, trsm_tc_leaf as TRX_OPT_TRSM_TC_LEAF, thin_leaf as
+ * TRX_OPT_THIN_LEAF (the recursion's plan: the whole-call thin solve of
+ * TRX_OPT_THIN is not shown), op 'S' (TRSM) or 'M' (TRMM). Returns an
+ * argument code, TRX_ERR_INVALID_VALUE if buf is too small, or 0. */
+int trx_debug_plan(char op, char side, char uplo, char transa, char diag, int64_t m, int64_t n,
+                   int elem_bytes, int leaf, int gemm_mode, int trmm_dense, int trsm_tc_leaf,
+                   int thin_leaf, char* buf, size_t buflen);
 
 /* Size of the static device scratch behind trx_strsm_noalloc (64 MiB). */
 #define TRX_NOALLOC_SCRATCH_BYTES ((size_t)64 << 20)

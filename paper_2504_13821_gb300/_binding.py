@@ -111,7 +111,7 @@ def load_library() -> ctypes.CDLL:
         lib.trx_last_error_detail.argtypes = []
         lib.trx_last_error_detail.restype = ctypes.c_char_p
         lib.trx_debug_plan.argtypes = [c, c, c, c, c, i64, i64, ctypes.c_int, ctypes.c_int,
-                                       ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                       ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                        ctypes.c_char_p, ctypes.c_size_t]
         lib.trx_sgemm_update.argtypes = [vp, i64, i64, i64, ctypes.c_float, ctypes.c_float,
                                          vp, i64, vp, i64, vp, i64, ctypes.c_int, vp]
@@ -414,14 +414,14 @@ def trsm_refined_async(side: str, uplo: str, trans: str, diag: str, alpha: float
 
 
 def debug_plan(op: str, side, uplo, trans, diag, m, n, elem_bytes=4, leaf=0, gemm=0,
-               trmm_dense=0, trsm_tc_leaf=0) -> list:
+               trmm_dense=0, trsm_tc_leaf=0, thin_leaf=0) -> list:
     """The launch sequence the library would enqueue, parsed (host only, no
     GPU needed): a list of dicts with the step kind and its row ranges."""
     lib = load_library()
     buf = ctypes.create_string_buffer(1 << 22)
     rc = lib.trx_debug_plan(_char(op), _char(side), _char(uplo), _char(trans), _char(diag),
-                            m, n, elem_bytes, leaf, gemm, trmm_dense, trsm_tc_leaf, buf,
-                            len(buf))
+                            m, n, elem_bytes, leaf, gemm, trmm_dense, trsm_tc_leaf, thin_leaf,
+                            buf, len(buf))
     _check(rc, "trx_debug_plan")
     steps = []
     for line in buf.value.decode().splitlines():

@@ -540,9 +540,10 @@ int execute(trx_handle_t h, bool trsm, char side, char uplo, char transa, char d
     const bool tc_ok = use_tc<T>(h, k, trsm, ex.c.nrhs);
     bool thin = std::is_same<T, float>::value &&
                 use_thin_mode(h->opt_thin, trsm, (int)sizeof(T), k, ex.c.nrhs);
+    // (an explicit leaf size turns the automatic thin leaves off)
+    const int64_t tl_opt = (h->opt_leaf != 0 && h->opt_thin_leaf == 0) ? -1 : h->opt_thin_leaf;
     int thin_leaf = std::is_same<T, float>::value
-                        ? thin_leaf_rows(h->opt_thin_leaf, tc_ok, trsm, (int)sizeof(T), k,
-                                         ex.c.nrhs)
+                        ? thin_leaf_rows(tl_opt, tc_ok, trsm, (int)sizeof(T), k, ex.c.nrhs)
                         : 0;
     // both apply: a forced whole-call solve wins, else the thin leaves
     if (thin && thin_leaf > 0) {
@@ -2212,7 +2213,7 @@ const char* trx_last_error_detail(void) { return g_detail; }
 
 int trx_debug_plan(char op, char side, char uplo, char transa, char diag, int64_t m, int64_t n,
                    int elem_bytes, int leaf, int gemm_mode, int trmm_dense, int trsm_tc_leaf,
-                   char* buf, size_t buflen) {
+                   int thin_leaf, char* buf, size_t buflen) {
     const int info = check_args(side, uplo, transa, diag, m, n, "", std::max<int64_t>(1, upc(side) == 'L' ? m : n),
                                 "", std::max<int64_t>(1, m));
     if (info) return info;
@@ -2222,17 +2223,24 @@ int trx_debug_plan(char op, char side, char uplo, char transa, char diag, int64_
         gemm_mode > 2 || !buf || buflen == 0 ||
         (trmm_dense != -1 && trmm_dense != 0 && trmm_dense != 64 && trmm_dense != 128 &&
          trmm_dense != 256 && trmm_dense != 512 && trmm_dense != 1024 && trmm_dense != 2048) ||
-        trsm_tc_leaf < -1 || trsm_tc_leaf > 1)
+        trsm_tc_leaf < -1 || trsm_tc_leaf > 1 ||
+        !(thin_leaf == -1 || thin_leaf == 0 ||
+          (thin_leaf >= 256 && thin_leaf <= 8192 && thin_leaf % 128 == 0)))
         return TRX_ERR_INVALID_VALUE;
     buf[0] = 0;
     const int64_t k = upc(side) == 'L' ? m : n;
     if (m == 0 || n == 0) return TRX_SUCCESS;
     const bool is_trsm = upc(op) == 'S';
     const int64_t nrhs = upc(side) == 'L' ? n : m;
-    const int b = leaf_for(leaf, k, is_trsm, elem_bytes, nrhs);
+    int b = leaf_for(leaf, k, is_trsm, elem_bytes, nrhs);
     Plan plan;
     plan.tc = use_tc_mode(elem_bytes, gemm_mode, k, b);
-    plan.tc_leaf = is_trsm && elem_bytes == 4 && tc_leaf_mode(trsm_tc_leaf, plan.tc, b);
+    const int tl = thin_leaf_rows((leaf != 0 && thin_leaf == 0) ? -1 : thin_leaf, plan.tc,
+                                  is_trsm, elem_bytes, k, nrhs);
+    if (tl > 0) b = tl;
+    plan.thin_leaf = tl > 0;
+    plan.tc_leaf = is_trsm && elem_bytes == 4 && !plan.thin_leaf &&
+                   tc_leaf_mode(trsm_tc_leaf, plan.tc, b);
     const int dense = is_trsm ? 0 : trmm_dense_mode(trmm_dense, leaf, plan.tc, k);
     make_plan(plan, is_trsm, k, b, 2.0, true, dense);
     if (const char* why = validate_plan(plan, k)) {
@@ -2254,6 +2262,11 @@ int trx_debug_plan(char op, char side, char uplo, char transa, char diag, int64_
                 break;
             case kInvDiag:
                 snprintf(line, sizeof(line), "inv_diag b=%d\n", st.b);
+                out += line;
+                break;
+            case kThin:
+                snprintf(line, sizeof(line), "thin trsm=%d r0=%lld b=%d alpha=%.17g planes=%d\n",
+                         (int)st.trsm, (long long)st.r0, st.b, st.alpha, (int)st.planes);
                 out += line;
                 break;
             case kLeaf:

@@ -141,8 +141,17 @@ def replay(op, steps, M, C, alpha_seen=2.0):
             d = np.diag(M[r:e, r:e])[:, None]
             C[r:e] = s["beta"] * d * C[r:e] + s["gamma"] * (
                 M[r:e, rk:r] @ Y[rk:r] + np.tril(M[r:e, r:e], -1) @ Y[r:e])
+        elif s["kind"] == "thin":
+            # the thin solve on rows [r0, r0 + b), then (planes) their Y planes
+            r, e = s["r0"], min(k, s["r0"] + s["b"])
+            assert s["trsm"] == 1
+            C[r:e] = sla.solve_triangular(np.tril(M[r:e, r:e]), s["alpha"] * C[r:e], lower=True)
+            if s["planes"]:
+                Y[r:e] = C[r:e]
         elif s["kind"] == "gemm":
-            src = Y if (s["tc"] and op == "M") else C
+            # tensor-core updates read the Y planes (X for TRSM, the original
+            # right-hand side for TRMM), the CUDA-core ones C itself
+            src = Y if s["tc"] else C
             rc, rk = s["rc"], s["rk"]
             C[rc:rc + s["mlen"]] = (s["beta"] * C[rc:rc + s["mlen"]] + s["gamma"] *
                                     M[rc:rc + s["mlen"], rk:rk + s["klen"]] @ src[rk:rk + s["klen"]])
@@ -236,9 +245,10 @@ def test_trsm_block_leaves_on_request():
     leaves = [s for s in debug_plan("S", "L", "L", "N", "N", 16384, 16384, 4, 256, 0)
               if s["kind"] == "leaf"]
     assert len(leaves) == 64 and all(s["b"] == 256 for s in leaves)
-    # automatic: 128-row leaves for FP32 TRSM (any number of right-hand
-    # sides), 64-row leaves for FP64
-    for args in [("L", 16384, 16384), ("L", 16384, 256), ("R", 300, 3000)]:
+    # automatic: 128-row leaves for FP32 TRSM (outside the thin leaves'
+    # range of right-hand sides, test_thin_leaf_automatic_rule), 64-row
+    # leaves for FP64
+    for args in [("L", 16384, 16384), ("L", 16384, 2048), ("L", 2048, 256), ("R", 300, 3000)]:
         side, m, n = args
         leaves = [s for s in debug_plan("S", side, "L", "N", "N", m, n, 4, 0, 0)
                   if s["kind"] == "leaf"]
@@ -302,3 +312,43 @@ def test_trsm_tensor_core_leaves_only_when_asked():
     a = debug_plan("M", "L", "L", "N", "N", 1024, 7, 4, 0, 0, 0, 1)
     b = debug_plan("M", "L", "L", "N", "N", 1024, 7, 4, 0, 0, 0, 0)
     assert a == b
+
+
+@pytest.mark.parametrize("gemm", [1, 2])
+@pytest.mark.parametrize("tl", [256, 512, 1024])
+@pytest.mark.parametrize("k", [300, 1100, 2500])
+def test_thin_leaf_plan_replay_matches_oracle(gemm, tl, k):
+    # TRSM leaves of tl rows as thin solves (TRX_OPT_THIN_LEAF), tensor-core
+    # path only: the leaves tile the order in sequence, alpha enters the
+    # first, every leaf but none of the updates' inputs lacks its Y planes
+    n = 7
+    A, B = inputs.problem("L", "L", k, n, seed=k + tl, dtype=np.float64)
+    M = np.where(np.isnan(A), 0.0, A)
+    steps = debug_plan("S", "L", "L", "N", "N", k, n, 4, 0, gemm, 0, 0, tl)
+    thin = [s for s in steps if s["kind"] == "thin"]
+    if gemm == 1 or k <= tl:
+        assert not thin
+    else:
+        assert not any(s["kind"] == "leaf" for s in steps)
+        assert [s["r0"] for s in thin] == sorted(s["r0"] for s in thin)
+        assert thin[0]["r0"] == 0 and all(
+            a["r0"] + a["b"] == b["r0"] for a, b in zip(thin, thin[1:]))
+        assert thin[-1]["r0"] + thin[-1]["b"] == k and all(s["b"] <= tl for s in thin)
+        assert thin[0]["alpha"] == 2.0 and all(s["alpha"] == 1.0 for s in thin[1:])
+        assert all(s["planes"] == 1 for s in thin)
+    got = replay("S", steps, M, B)
+    want = oracle.trsm("L", "L", "N", "N", 2.0, A, B)
+    np.testing.assert_allclose(got, want, rtol=1e-10, atol=1e-10 * np.abs(want).max())
+
+
+@pytest.mark.parametrize("k,n,leaf,want", [
+    (8192, 256, 0, 2048), (16384, 128, 0, 2048), (16384, 512, 0, 1024), (4096, 1024, 0, 1024),
+    (4096, 128, 0, 0), (4096, 256, 0, 2048), (16384, 64, 0, 0), (16384, 2048, 0, 0),
+    (2048, 256, 0, 0), (8192, 256, 128, 0)])
+def test_thin_leaf_automatic_rule(k, n, leaf, want):
+    # the automatic thin leaves: order from 4096, 65..1024 right-hand sides
+    # (129.. below order 8192), 2048 rows up to 256, 1024 above; off when
+    # the leaf size is set explicitly
+    steps = debug_plan("S", "L", "L", "N", "N", k, n, 4, leaf, 0)
+    sizes = {s["b"] for s in steps if s["kind"] == "thin"}
+    assert sizes == ({want} if want else set())
