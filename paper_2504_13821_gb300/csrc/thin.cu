@@ -15,10 +15,17 @@
 // then writes X_ip into C and publishes it. inv(M_ii) (substitution against
 // the identity, FP32, one reciprocal of each diagonal entry: the leaf solve
 // of Section 3.3 as a product with the inverted block) and Z are made by
-// the task before its first wait, and the products of a task start as soon
-// as the blocks X_jp they need are published, so the reads of M (every
-// element once per panel, the dominant traffic) overlap the chain of
-// diagonal blocks; the chain itself is one 64 x 64 x 16 product per block.
+// the task before its first wait when the right-hand side is one panel,
+// and by a preparatory pass (thin_prep_kernel, one CTA per block row, the
+// same code) when it is several, so the panels' tasks of a block row do not
+// each repeat them; the products of a task start as soon as the blocks X_jp
+// they need are published, so the reads of M (every element once per
+// panel, the dominant traffic) overlap the chain of diagonal blocks; the
+// chain itself is one 64 x 64 x 16 product per block.
+//
+// The same launch also serves as the recursion's leaf for 65 .. 1024
+// right-hand sides (the thin leaves): on a leaf's rows, its columns of M
+// and its rows of C, with the tensor-core updates between leaves.
 //
 // A block is published as 1024 tagged 64-bit words (FP32 bits in the low
 // half, 1 in the high half; a 64-bit access is single-copy atomic, so value
