@@ -864,8 +864,9 @@ def run_precision(args):
     nsel = args.nrhs_list.split(",")
     h = trx.Handle(dev)
     # the forms compare the recursion's update arithmetic: the thin CUDA-core
-    # solve (no split) is kept out of the table
+    # solve (no split), whole-call or as the leaves, is kept out of the table
     h.set_option(trx.OPT_THIN, -1)
+    h.set_option(trx.OPT_THIN_LEAF, -1)
     alpha = 1.5
 
     def timed(fn, reps):

@@ -69,6 +69,7 @@ def column_errors(X, Xref):
 def run_engine(trx, op, engine, terms, A, B, alpha, dev):
     h = trx.Handle(0)
     h.set_option(trx.OPT_THIN, -1)          # the recursion's GEMM updates are compared
+    h.set_option(trx.OPT_THIN_LEAF, -1)     # on the same plan for both engines
     h.set_option(trx.OPT_GEMM, engine)
     if terms:
         h.set_option(trx.OPT_SPLIT, terms)
